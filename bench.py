@@ -1,0 +1,343 @@
+"""Throughput benchmark: amplitudes/s of the sliced QAOA tensor-network
+contraction on the 80-qubit, p = 1, 16-cut workload (65536 slices per
+amplitude, 8 bit strings per step, one graph and plan).
+
+One step = one pass of the whole hot path over one batch: the gate tensors
+of 8 bit strings built in FP64, all 8 x 65536 slices contracted, the slice
+sums (FP64, compensated) and the normalisation -- one replay of the plan's
+CUDA graph.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp32|fp64]
+                  [--impl ours|reference]
+
+Prints ONE JSON line on rank 0.  --impl reference times the CPU oracle (the
+paper's scheme on the host cores: worker threads over slice ranges, master
+sum) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(name="qaoa80_p1_k16", n=80, p=1, k=16, seed=3, bitstrings=8)
+METRIC = "amplitudes/sec, n=80 QAOA p=1, 16 cut edges (65536 slices)"
+FP32_LANES_PER_SM = 128
+NUM_SMS = 152
+FP64_TFLOPS_NOMINAL = 1.25
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except OSError:
+        return {}
+
+
+def alu_peak_tflops(prec: str, sm_mhz: float) -> float:
+    """FP32: 152 SMs x 128 FMA lanes x 2 flops x clock; FP64: nominal."""
+    if prec == "fp64":
+        return FP64_TFLOPS_NOMINAL
+    return NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_2010_14962_gb300", "csrc", "kernels.cu"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(prec: str):
+    """DRAM bytes per executor launch from the committed ncu summary, if it
+    was taken on the current kernel source; else None."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)
+    except OSError:
+        return None
+    e = t.get(prec)
+    if not e or e.get("kernels_cu_sha256_16") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def setup_workload(rank: int):
+    from paper_2010_14962_gb300 import instances as I
+    from paper_2010_14962_gb300 import qtn
+
+    w = WORKLOAD
+    inst = I.qaoa_instance(w["n"], w["p"], w["seed"])
+    net = qtn.Network(w["n"], inst.edges, inst.gamma, inst.beta)
+    plan = qtn.Plan(net, k=w["k"])
+    xs = I.bitstrings(w["n"], w["bitstrings"], w["seed"] + 1000 * rank)
+    return inst, net, plan, xs
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+
+    from paper_2010_14962_gb300 import qtn
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    inst, net, plan, xs = setup_workload(rank)
+    nx = xs.shape[0]
+    cost = plan.cost()
+    flops_per_amp = (2 ** cost["k"]) * 8 * cost["macs_per_slice"]
+    stream = torch.cuda.current_stream()
+    d_x = torch.from_numpy(np.ascontiguousarray(xs)).cuda()
+    d_out = torch.zeros((nx, 2), dtype=torch.float64, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 129 MB L2
+    plan.set_kernel_timing(True)
+
+    def step():
+        plan.contract_amplitudes_device(d_x, d_out, args.precision, stream)
+
+    for _ in range(args.warmup):
+        step()
+        flush.zero_()
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    kernel_ms = []
+    with ClockSampler(local_rank) as clk:
+        time.sleep(0.3)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for i in range(args.steps):
+            starts[i].record(stream)
+            step()
+            ends[i].record(stream)
+            stream.synchronize()
+            kernel_ms.append(plan.kernel_ms())
+            flush.zero_()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        wall = time.perf_counter() - t0
+        time.sleep(0.3)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_ms = float(sum(step_ms))
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    amps = nx * args.steps * world
+    value = amps / (total_ms / 1e3)
+
+    # End to end through the public host API: pinned host x in, host results out.
+    plans = [plan] * nx
+    xl = [xs[i] for i in range(nx)]
+    plan.set_kernel_timing(False)
+    for _ in range(2):
+        qtn.contract_batch(plans, xl, args.precision)
+    e2e_steps = max(3, min(args.steps, 50))
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        qtn.contract_batch(plans, xl, args.precision)
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = nx * e2e_steps * world / e2e_s
+
+    clocks = clk.summary()
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    peaks = measured_peaks()
+    sm_for_peak = peaks.get("sm_max_mhz", 2070.0)
+    peak = alu_peak_tflops(args.precision, sm_for_peak)
+    avg_kernel_s = statistics.mean(kernel_ms) / 1e3
+    achieved = flops_per_amp * nx / avg_kernel_s / 1e12
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "amplitudes/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "c64" if args.precision == "fp32" else "c128",
+        "data": "synthetic: seeded random 3-regular graph, gamma/beta ~ U[0,pi), seeded bit strings",
+        "config": {"workload": WORKLOAD["name"], "n": WORKLOAD["n"], "p": WORKLOAD["p"], "cuts": WORKLOAD["k"],
+                   "slices_per_amplitude": 2 ** cost["k"], "bitstrings_per_step": nx, "precision": args.precision,
+                   "executor": plan.executor, "plan_width": cost["width"],
+                   "macs_per_slice": cost["macs_per_slice"], "effective_tflops": flops_per_amp * value / 1e12,
+                   "slices_per_s": value * 2 ** cost["k"], "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": f"weak: {nx} bit strings per GPU, slices across CTAs/threads"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": profiled_traffic(args.precision),
+                     "kernel": "lane_exec_kernel" if plan.executor == "lane" else "block_exec_kernel",
+                     "peak_source": ("FP32: 152 SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock of measured peaks)"
+                                     % sm_for_peak) if args.precision != "fp64" else "FP64 nominal 1.25 TFLOP/s",
+                     "kernel_ms_avg": avg_kernel_s * 1e3},
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": "amplitudes/s", "h2d_bytes_per_step": int(nx * WORKLOAD["n"]),
+                "d2h_bytes_per_step": int(nx * 16), "api": "qtn_contract_batch (host x in, host amplitudes out)"},
+        "gpu_launches": 3 * args.steps,
+        "wall_s_timed_region": wall,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(seconds: float, plan_bundle=None):
+    """The oracle (as it stands) on a bounded sample of the workload's slices,
+    all host cores, scaled to amplitudes/s."""
+    from oracle import oracle as O
+
+    inst, net, plan, xs = plan_bundle or setup_workload(0)
+    cuts = plan.cut_names()
+    cores = os.cpu_count() or 1
+    S = 2 ** len(cuts)
+    chunk = 64 * cores
+    done = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds and done < S:
+        hi = min(S, done + chunk)
+        O.tn_amplitude(WORKLOAD["n"], inst.edges, inst.gamma, inst.beta, xs[0], cuts=cuts, slices=(done, hi),
+                       threads=cores)
+        done = hi
+    dt = time.perf_counter() - t0
+    return {"value": (done / S) / dt, "unit": "amplitudes/s", "cores": cores, "kind": "oracle",
+            "sample": f"{done} of {S} slices of one amplitude ({WORKLOAD['name']}), {dt:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    from paper_2010_14962_gb300 import instances  # noqa: F401
+
+    bundle = setup_workload_cpu()
+    for _ in range(args.warmup):
+        cpu_baseline(0.2, bundle)
+    vals = []
+    t0 = time.perf_counter()
+    per_step = max(0.5, min(10.0, 60.0 / max(args.steps, 1)))
+    last = None
+    for _ in range(args.steps):
+        last = cpu_baseline(per_step, bundle)
+        vals.append(last["value"])
+    wall = time.perf_counter() - t0
+    value = statistics.mean(vals)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "amplitudes/s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall / max(args.steps, 1) * 1e3,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+           "data": "synthetic", "config": {"workload": WORKLOAD["name"], "n": WORKLOAD["n"], "p": WORKLOAD["p"],
+                                           "cuts": WORKLOAD["k"]},
+           "cpu_baseline": {"value": value, "unit": "amplitudes/s", "cores": last["cores"], "kind": "oracle",
+                            "sample": last["sample"] + " per step"},
+           "e2e": {"value": value, "unit": "amplitudes/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def setup_workload_cpu():
+    """Plan on the host only (the reference arm needs no GPU)."""
+    return setup_workload(0)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,198 @@
+/*
+ * qtn.h -- C ABI of the GB300 slice-parallel tensor-network amplitude library.
+ *
+ * Method (arXiv 2010.14962, "Simulation of Quantum Computing on Classical
+ * Supercomputers"): a QAOA circuit is turned into an undirected-graph tensor
+ * network (Sec. II.A, Fig. 1: gates/inputs/measurements are vertices, wire
+ * segments are edges); k edges are cut, which splits the contraction into
+ * 2^k independent subnetworks of smaller width whose scalar results add up to
+ * the full contraction (Sec. III.A, Eq. 2); each subnetwork is contracted by
+ * pairwise contractions (Sec. II.A, Eq. 1) along an elimination order
+ * (Sec. II.B); the cut set is searched greedily or by the genetic algorithm
+ * of Sec. III.B (Algorithm 1).  Edges carry dimension 2 here: the library
+ * computes amplitudes <x|C|0^n>, where the paper's density-matrix form uses
+ * dimension 4 and gives |<x|C|0^n>|^2.
+ *
+ * Circuit: C = U_B(beta_p) U_C(gamma_p) ... U_B(beta_1) U_C(gamma_1) H^n with
+ *   U_C(g) = prod_{(i,j) in E} exp(-i g Z_i Z_j)  (ZZ gates in lexicographic
+ *   edge order) and U_B(b) = prod_q exp(-i b X_q) = RX(2b) on every qubit.
+ * Bit strings: x[q] is the measured bit of qubit q (0 or 1).
+ *
+ * Conventions for every entry point:
+ *   - Inputs are read (and copied where kept); the caller keeps ownership.
+ *   - Handles are created by qtn_build_network / qtn_plan, owned by the
+ *     library, immutable for the caller and freed by the *_destroy calls.
+ *     Contraction calls on one plan from several host threads at once are
+ *     serialised internally.
+ *   - Every call returns a qtn_status; on failure nothing is written to the
+ *     outputs and qtn_last_error() (per host thread) explains why.  The
+ *     library never aborts the process.
+ *   - Pointers documented as "device" must be CUDA device pointers on the
+ *     current device; "host" pointers are ordinary host memory.
+ *   - A NULL stream means the legacy default stream.  Calls that return
+ *     results to host memory synchronise the stream before returning.
+ */
+#ifndef QTN_H_
+#define QTN_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  QTN_OK = 0,
+  QTN_ERR_INVALID_ARG = 1,      /* bad graph, cut, order, precision, size */
+  QTN_ERR_OOM = 2,              /* host or device allocation failed */
+  QTN_ERR_PLAN_EXCEEDS_CAP = 3, /* plan needs more memory than allowed */
+  QTN_ERR_CUDA = 4,             /* a CUDA runtime call failed */
+  QTN_ERR_TIMEOUT = 5,          /* a bounded device wait gave up */
+  QTN_ERR_UNSUPPORTED = 6       /* valid request this build cannot run */
+} qtn_status;
+
+/* Arithmetic of the elimination steps.  Gate phases (sincos of gamma, beta)
+ * and the sum over slices are FP64 in every mode (Kahan-compensated). */
+typedef enum {
+  QTN_FP64 = 0,   /* complex128 contractions (the plain FP64 GPU form) */
+  QTN_FP32 = 1,   /* complex64 contractions, FP32 FMA */
+  QTN_TF32 = 2,   /* tensor cores: operands rounded to TF32, FP32 accumulate */
+  QTN_BF16X3 = 3, /* tensor cores: split-BF16 (hi*hi + hi*lo + lo*hi), FP32 acc */
+  QTN_TF32X3 = 4, /* tensor cores: split-TF32 3-term, FP32 accumulate */
+  QTN_BF16X6 = 5  /* tensor cores: 3-way split BF16, 6 products, FP32 acc */
+} qtn_precision;
+
+typedef struct qtn_network qtn_network_t;
+typedef struct qtn_plan qtn_plan_t;
+
+/* Builds the network of the p-layer QAOA circuit on graph (n, edges).
+ *   edges : host, m pairs (i, j), 0 <= i, j < n, i != j, no duplicates (in
+ *           either orientation); every qubit must appear in an edge.
+ *   gamma, beta : host, p angles each.
+ * Vertices are the ZZ gates; H|0>, the mixers and <x| are absorbed into
+ * their neighbouring ZZ gate (rank <= 2 tensors), so the network has p*m
+ * tensors and sum_q (p*deg(q) - 1) indices (Sec. II.A, Fig. 1). */
+qtn_status qtn_build_network(int n, int p, const int32_t* edges, int m, const double* gamma,
+                             const double* beta, qtn_network_t** out);
+void qtn_network_destroy(qtn_network_t* net);
+
+/* Counts of tensors and indices.  Index ids 0..n_indices-1 are stable. */
+qtn_status qtn_network_info(const qtn_network_t* net, int* n_tensors, int* n_indices);
+
+/* Names index `index`: it is the wire segment of qubit *qubit that enters the
+ * (*pos + 1)-th ZZ gate (0-based count) acting on that qubit; *tensor_a and
+ * *tensor_b are its endpoint gates (earlier first).  Any output may be NULL. */
+qtn_status qtn_network_index(const qtn_network_t* net, int index, int* qubit, int* pos, int* tensor_a,
+                             int* tensor_b);
+
+/* Cut-set search used when qtn_plan gets cuts == NULL. */
+typedef enum {
+  QTN_SEARCH_GREEDY = 0, /* cut the index that most lowers the width, k times */
+  QTN_SEARCH_GA = 1      /* Algorithm 1 (Sec. III.B), seeded with the greedy set */
+} qtn_search;
+
+typedef struct {
+  qtn_search search; /* default QTN_SEARCH_GREEDY */
+  int k;             /* number of cuts to search for (cuts == NULL) */
+  uint64_t seed;     /* GA seed (default 1) */
+  int ga_T;          /* GA maximum iteration counter (default 4) */
+  int ga_N;          /* GA population size (default 11) */
+  double max_slice_bytes; /* 0 = no cap; else largest per-slice working set */
+} qtn_plan_opts;
+
+/* Fills `opts` with the defaults (greedy search, k = 0, T = 4, N = 11). */
+void qtn_plan_opts_default(qtn_plan_opts* opts);
+
+/* Plans the sliced contraction (Sec. III.A) of `net`.
+ *   cuts  : host, k distinct index ids to cut (slice bit j fixes cuts[j]);
+ *           NULL = search opts->k cuts with opts->search.
+ *   order : host, elimination order over the non-cut indices (each exactly
+ *           once); NULL = min-fill (ties: fill, bag size, lowest id).
+ *   opts  : NULL = defaults.
+ * Fails with QTN_ERR_PLAN_EXCEEDS_CAP when opts->max_slice_bytes is set and
+ * the plan's per-slice working set is larger. */
+qtn_status qtn_plan(const qtn_network_t* net, const int32_t* cuts, int k, const int32_t* order,
+                    int order_len, const qtn_plan_opts* opts, qtn_plan_t** out);
+void qtn_plan_destroy(qtn_plan_t* plan);
+
+/* Runs the cut-set search alone (no plan is built).
+ *   opts->k cuts are written to `cuts` (host, opts->k entries).
+ *   trace (host, trace_cap doubles, may be NULL): the search's fitness after
+ *     each greedy cut, or the best fitness of each GA generation (Algorithm 1
+ *     Step 1, then Step 5); fitness = width + log2(total flops) / 128.
+ *   *trace_len, *evaluations: entries written and fitness evaluations done. */
+qtn_status qtn_search_cuts(const qtn_network_t* net, const qtn_plan_opts* opts, int32_t* cuts,
+                           double* trace, int trace_cap, int* trace_len, int* evaluations);
+
+/* Exact cost of the plan (the method's own counter, Sec. II.B):
+ *   log2_flops      : log2(2^k * 8 * complex MACs per slice)
+ *   log2_peak_bytes : log2 of the largest live set of one slice (complex64)
+ *   width           : largest |A u B| over the pairwise contractions
+ *   k               : number of cuts.  Any output may be NULL. */
+qtn_status qtn_plan_cost(const qtn_plan_t* plan, double* log2_flops, double* log2_peak_bytes,
+                         int* width, int* k);
+
+/* The plan's cut index ids (k entries, host) and MACs per slice. */
+qtn_status qtn_plan_cuts(const qtn_plan_t* plan, int32_t* cuts);
+qtn_status qtn_plan_macs_per_slice(const qtn_plan_t* plan, double* macs);
+
+/* One amplitude a(x) = <x|C|0^n>, host in / host out.
+ *   x   : host, n bytes.   out : host, out[0] = Re a, out[1] = Im a. */
+qtn_status qtn_contract_amplitude(const qtn_plan_t* plan, const uint8_t* x, qtn_precision prec,
+                                  cudaStream_t stream, double out[2]);
+
+/* nx amplitudes of one plan with device-resident data (the throughput path).
+ *   d_x   : device, nx * n bytes (row j = bit string j).
+ *   d_out : device, nx * 2 doubles (Re, Im per bit string).
+ * Asynchronous on `stream`; the first call for a given (d_x, d_out, nx,
+ * prec) records a CUDA graph that later calls replay. */
+qtn_status qtn_contract_amplitudes_device(const qtn_plan_t* plan, const uint8_t* d_x, int nx,
+                                          qtn_precision prec, cudaStream_t stream, double* d_out);
+
+/* Slices [slice_lo, slice_hi) of one amplitude, e.g. to recompute the slices
+ * of a lost worker (Sec. V: fault tolerance at the level of subgraphs).
+ *   x         : host, n bytes.
+ *   out       : host, 4 doubles: the Kahan sum (Re, Im) of the range and its
+ *               compensation terms (Re, Im), NOT scaled by 2^{-n/2}.
+ *   d_slices  : optional device buffer of 2 * (slice_hi - slice_lo) doubles
+ *               receiving every slice's scalar (unscaled), or NULL.
+ * Synchronises `stream`. */
+qtn_status qtn_contract_slices(const qtn_plan_t* plan, const uint8_t* x, uint64_t slice_lo,
+                               uint64_t slice_hi, qtn_precision prec, cudaStream_t stream,
+                               double out[4], double* d_slices);
+
+/* Amplitudes of njobs independent (plan, x) jobs in one persistent launch.
+ *   plans : host, njobs plan handles (different networks allowed).
+ *   xs    : host, njobs pointers to host bit strings.
+ *   out   : host, 2 * njobs doubles. */
+qtn_status qtn_contract_batch(const qtn_plan_t* const* plans, const uint8_t* const* xs, int njobs,
+                              qtn_precision prec, cudaStream_t stream, double* out);
+
+/* Which executor the plan runs on ("lane": one slice per GPU thread, for
+ * plans with every tensor rank <= 5; "block": one slice per thread block). */
+qtn_status qtn_plan_executor(const qtn_plan_t* plan, const char** name);
+
+/* Kernel timing for measurement: when on, contraction calls record CUDA
+ * events on the launching stream just before and after the executor kernel
+ * (inside the replayed graph as well); qtn_plan_kernel_ms returns the
+ * executor's duration in the most recent call once that call's stream has
+ * been synchronised.  Switching it changes the recorded graphs. */
+qtn_status qtn_plan_set_kernel_timing(const qtn_plan_t* plan, int on);
+qtn_status qtn_plan_kernel_ms(const qtn_plan_t* plan, float* ms);
+
+/* Introspection: a JSON description of the plan (cuts, elimination order,
+ * merges, tensor index sets, both executors' step programs, gate legs), for
+ * tests and tooling.  Writes at most `cap` bytes (NUL-terminated) to `buf`
+ * when `cap` is large enough; always sets *len to the size needed. */
+qtn_status qtn_plan_describe(const qtn_plan_t* plan, char* buf, size_t cap, size_t* len);
+
+const char* qtn_status_string(qtn_status s);
+const char* qtn_last_error(void); /* per host thread; "" if none */
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QTN_H_ */

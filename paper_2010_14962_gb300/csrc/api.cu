@@ -1,0 +1,654 @@
+// C-ABI layer: handles, validation, device residency of plans, workspace,
+// CUDA-graph replay and the host <-> device entry points of qtn.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <sstream>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/qtn.h"
+#include "kernels.cuh"
+#include "network.hpp"
+#include "plan.hpp"
+#include "program.hpp"
+
+using namespace qtn;
+
+struct qtn_network {
+  Network net;
+};
+
+namespace {
+
+thread_local std::string g_last_error;
+
+qtn_status fail(qtn_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+
+qtn_status cuda_fail(cudaError_t e, const char* what) {
+  return fail(QTN_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define QTN_CUDA(call)                                  \
+  do {                                                  \
+    cudaError_t e_ = (call);                            \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+  } while (0)
+
+template <class T>
+cudaError_t upload(T** dst, const std::vector<T>& v) {
+  size_t bytes = std::max<size_t>(v.size() * sizeof(T), 16);
+  cudaError_t e = cudaMalloc((void**)dst, bytes);
+  if (e != cudaSuccess) return e;
+  if (!v.empty()) e = cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+  return e;
+}
+
+struct GraphKey {
+  const void* x;
+  const void* out;
+  int nx;
+  int prec;
+  bool operator<(const GraphKey& o) const {
+    return std::tie(x, out, nx, prec) < std::tie(o.x, o.out, o.nx, o.prec);
+  }
+};
+
+bool precision_supported(qtn_precision p) { return p == QTN_FP64 || p == QTN_FP32; }
+
+}  // namespace
+
+struct qtn_plan {
+  Network net;
+  Plan plan;
+  Program lane_prog, block_prog;
+  Executor exec = Executor::Lane;
+  double log2_flops = 0, log2_peak_bytes = 0;
+  std::mutex mu;
+
+  // Device state, created on first use on the then-current device.
+  int device = -1;
+  std::vector<void*> dev_allocs;
+  DeviceProgram dprog;
+  int cap_nx = 0, cap_blocks = 0;
+  void* d_leaf_tables = nullptr;
+  Partial* d_partials = nullptr;
+  int* d_err = nullptr;
+  uint8_t* d_x_stage = nullptr;
+  double2* d_out_stage = nullptr;
+  Partial* d_raw_stage = nullptr;
+  uint8_t* h_x_pinned = nullptr;
+  double* h_out_pinned = nullptr;
+  cudaStream_t capture_stream = nullptr;
+  std::map<GraphKey, cudaGraphExec_t> graphs;
+  bool timing = false;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+
+  ~qtn_plan() {
+    for (auto& g : graphs) cudaGraphExecDestroy(g.second);
+    for (void* p : dev_allocs) cudaFree(p);
+    free_workspace();
+    if (capture_stream) cudaStreamDestroy(capture_stream);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+  }
+
+  void free_workspace() {
+    cudaFree(d_leaf_tables);
+    cudaFree(d_partials);
+    cudaFree(d_err);
+    cudaFree(d_x_stage);
+    cudaFree(d_out_stage);
+    cudaFree(d_raw_stage);
+    cudaFreeHost(h_x_pinned);
+    cudaFreeHost(h_out_pinned);
+    d_leaf_tables = nullptr;
+    d_partials = nullptr;
+    d_err = nullptr;
+    d_x_stage = nullptr;
+    d_out_stage = nullptr;
+    d_raw_stage = nullptr;
+    h_x_pinned = nullptr;
+    h_out_pinned = nullptr;
+    cap_nx = cap_blocks = 0;
+  }
+
+  const Program& program() const { return exec == Executor::Lane ? lane_prog : block_prog; }
+
+  qtn_status ensure_device() {
+    int dev = 0;
+    QTN_CUDA(cudaGetDevice(&dev));
+    if (device >= 0) {
+      if (dev != device) return fail(QTN_ERR_INVALID_ARG, "plan was first used on another device");
+      return QTN_OK;
+    }
+    const Program& pg = program();
+    DevLeaf* leaves;
+    DevStep* steps;
+    int32_t* gq;
+    int8_t *gl, *gi, *go;
+    double *ga, *be;
+    QTN_CUDA(upload(&leaves, pg.leaves));
+    dev_allocs.push_back(leaves);
+    QTN_CUDA(upload(&steps, pg.steps));
+    dev_allocs.push_back(steps);
+    QTN_CUDA(upload(&gq, pg.gate_q));
+    dev_allocs.push_back(gq);
+    QTN_CUDA(upload(&gl, pg.gate_layer));
+    dev_allocs.push_back(gl);
+    QTN_CUDA(upload(&gi, pg.gate_in_h));
+    dev_allocs.push_back(gi);
+    QTN_CUDA(upload(&go, pg.gate_out_kind));
+    dev_allocs.push_back(go);
+    QTN_CUDA(upload(&ga, net.gamma));
+    dev_allocs.push_back(ga);
+    QTN_CUDA(upload(&be, net.beta));
+    dev_allocs.push_back(be);
+    QTN_CUDA(cudaStreamCreateWithFlags(&capture_stream, cudaStreamNonBlocking));
+    dprog.n = pg.n;
+    dprog.p = pg.p;
+    dprog.k = pg.k;
+    dprog.n_leaves = (int)pg.leaves.size();
+    dprog.n_steps = (int)pg.steps.size();
+    dprog.leaf_elems = pg.leaf_elems;
+    dprog.arena_elems = pg.arena_elems;
+    dprog.exec = exec;
+    dprog.leaves = leaves;
+    dprog.steps = steps;
+    dprog.gate_q = gq;
+    dprog.gate_layer = gl;
+    dprog.gate_in_h = gi;
+    dprog.gate_out_kind = go;
+    dprog.gamma = ga;
+    dprog.beta = be;
+    device = dev;
+    return QTN_OK;
+  }
+
+  qtn_status ensure_workspace(int nx, int blocks) {
+    if (nx <= cap_nx && blocks <= cap_blocks) return QTN_OK;
+    for (auto& g : graphs) cudaGraphExecDestroy(g.second);
+    graphs.clear();
+    int nnx = std::max(nx, cap_nx), nb = std::max(blocks, cap_blocks);
+    free_workspace();
+    size_t lt = (size_t)nnx * program().leaf_elems * sizeof(double2);
+    QTN_CUDA(cudaMalloc(&d_leaf_tables, std::max<size_t>(lt, 16)));
+    QTN_CUDA(cudaMalloc((void**)&d_partials, (size_t)nnx * nb * sizeof(Partial)));
+    QTN_CUDA(cudaMalloc((void**)&d_err, sizeof(int)));
+    QTN_CUDA(cudaMemset(d_err, 0, sizeof(int)));
+    QTN_CUDA(cudaMalloc((void**)&d_x_stage, (size_t)nnx * net.n));
+    QTN_CUDA(cudaMalloc((void**)&d_out_stage, (size_t)nnx * sizeof(double2)));
+    QTN_CUDA(cudaMalloc((void**)&d_raw_stage, (size_t)nnx * sizeof(Partial)));
+    QTN_CUDA(cudaMallocHost((void**)&h_x_pinned, (size_t)nnx * net.n));
+    QTN_CUDA(cudaMallocHost((void**)&h_out_pinned, (size_t)nnx * 4 * sizeof(double)));
+    cap_nx = nnx;
+    cap_blocks = nb;
+    return QTN_OK;
+  }
+
+  double scale() const { return std::pow(2.0, -0.5 * net.n); }
+
+  qtn_status shape_for(qtn_precision prec, int nx, uint64_t slices, ExecShape* sh) {
+    if (!exec_shape(dprog, prec == QTN_FP64 ? 16 : 8, nx, slices, sh))
+      return fail(QTN_ERR_UNSUPPORTED, "the plan's per-slice working set does not fit in shared memory");
+    return QTN_OK;
+  }
+
+  LaunchBuffers buffers() const {
+    LaunchBuffers b;
+    b.leaf_tables = d_leaf_tables;
+    b.partials = d_partials;
+    b.err = d_err;
+    return b;
+  }
+
+  // Enqueue the graph for (d_x, d_out, nx, prec) on `stream`.
+  qtn_status run_graph(const uint8_t* d_x, int nx, qtn_precision prec, double2* d_out, cudaStream_t stream) {
+    const uint64_t S = 1ull << plan.cuts.size();
+    ExecShape sh;
+    qtn_status st = shape_for(prec, nx, S, &sh);
+    if (st != QTN_OK) return st;
+    st = ensure_workspace(nx, sh.blocks_per_x);
+    if (st != QTN_OK) return st;
+    GraphKey key{d_x, d_out, nx, (int)prec};
+    auto it = graphs.find(key);
+    if (it == graphs.end()) {
+      cudaGraph_t g;
+      QTN_CUDA(cudaStreamBeginCapture(capture_stream, cudaStreamCaptureModeThreadLocal));
+      cudaError_t le = launch_contraction(dprog, prec == QTN_FP64, d_x, nx, 0, S, buffers(), sh, scale(), d_out,
+                                          nullptr, nullptr, capture_stream, timing ? ev0 : nullptr,
+                                          timing ? ev1 : nullptr);
+      cudaError_t ce = cudaStreamEndCapture(capture_stream, &g);
+      if (le != cudaSuccess) return cuda_fail(le, "launch_contraction (capture)");
+      if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
+      cudaGraphExec_t ge;
+      cudaError_t ie = cudaGraphInstantiate(&ge, g, 0);
+      cudaGraphDestroy(g);
+      if (ie != cudaSuccess) return cuda_fail(ie, "cudaGraphInstantiate");
+      it = graphs.emplace(key, ge).first;
+    }
+    QTN_CUDA(cudaGraphLaunch(it->second, stream));
+    return QTN_OK;
+  }
+
+  qtn_status check_err_flag() {
+    int h = 0;
+    QTN_CUDA(cudaMemcpy(&h, d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h != 0) {
+      cudaMemset(d_err, 0, sizeof(int));
+      return fail(QTN_ERR_UNSUPPORTED, "the executor met a merge shape it does not implement");
+    }
+    return QTN_OK;
+  }
+};
+
+namespace {
+
+qtn_status validate_x(const qtn_plan_t* plan, const uint8_t* x) {
+  if (!x) return fail(QTN_ERR_INVALID_ARG, "x is NULL");
+  for (int q = 0; q < plan->net.n; ++q)
+    if (x[q] > 1) return fail(QTN_ERR_INVALID_ARG, "x must hold bytes 0 or 1");
+  return QTN_OK;
+}
+
+void json_ints(std::ostringstream& o, const int* v, size_t n) {
+  o << "[";
+  for (size_t i = 0; i < n; ++i) o << (i ? "," : "") << v[i];
+  o << "]";
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* qtn_status_string(qtn_status s) {
+  switch (s) {
+    case QTN_OK: return "ok";
+    case QTN_ERR_INVALID_ARG: return "invalid argument";
+    case QTN_ERR_OOM: return "out of memory";
+    case QTN_ERR_PLAN_EXCEEDS_CAP: return "plan exceeds memory cap";
+    case QTN_ERR_CUDA: return "CUDA error";
+    case QTN_ERR_TIMEOUT: return "timeout";
+    case QTN_ERR_UNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+const char* qtn_last_error(void) { return g_last_error.c_str(); }
+
+qtn_status qtn_build_network(int n, int p, const int32_t* edges, int m, const double* gamma, const double* beta,
+                             qtn_network_t** out) {
+  if (!out) return fail(QTN_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  qtn_network_t* h = new (std::nothrow) qtn_network_t;
+  if (!h) return fail(QTN_ERR_OOM, "host allocation failed");
+  std::string err = build_network(n, p, edges, m, gamma, beta, &h->net);
+  if (!err.empty()) {
+    delete h;
+    return fail(QTN_ERR_INVALID_ARG, err);
+  }
+  *out = h;
+  return QTN_OK;
+}
+
+void qtn_network_destroy(qtn_network_t* net) { delete net; }
+
+qtn_status qtn_network_info(const qtn_network_t* net, int* n_tensors, int* n_indices) {
+  if (!net) return fail(QTN_ERR_INVALID_ARG, "net is NULL");
+  if (n_tensors) *n_tensors = (int)net->net.gates.size();
+  if (n_indices) *n_indices = (int)net->net.indices.size();
+  return QTN_OK;
+}
+
+qtn_status qtn_network_index(const qtn_network_t* net, int index, int* qubit, int* pos, int* tensor_a,
+                             int* tensor_b) {
+  if (!net) return fail(QTN_ERR_INVALID_ARG, "net is NULL");
+  if (index < 0 || index >= (int)net->net.indices.size()) return fail(QTN_ERR_INVALID_ARG, "index out of range");
+  const Index& ix = net->net.indices[index];
+  if (qubit) *qubit = ix.qubit;
+  if (pos) *pos = ix.pos;
+  if (tensor_a) *tensor_a = ix.tensor[0];
+  if (tensor_b) *tensor_b = ix.tensor[1];
+  return QTN_OK;
+}
+
+void qtn_plan_opts_default(qtn_plan_opts* o) {
+  if (!o) return;
+  o->search = QTN_SEARCH_GREEDY;
+  o->k = 0;
+  o->seed = 1;
+  o->ga_T = 4;
+  o->ga_N = 11;
+  o->max_slice_bytes = 0;
+}
+
+qtn_status qtn_plan(const qtn_network_t* net, const int32_t* cuts, int k, const int32_t* order, int order_len,
+                    const qtn_plan_opts* opts_in, qtn_plan_t** out) {
+  if (!net || !out) return fail(QTN_ERR_INVALID_ARG, "net or out is NULL");
+  *out = nullptr;
+  qtn_plan_opts opts;
+  qtn_plan_opts_default(&opts);
+  if (opts_in) opts = *opts_in;
+  std::vector<int> cutv;
+  if (cuts) {
+    if (k < 0) return fail(QTN_ERR_INVALID_ARG, "k < 0");
+    cutv.assign(cuts, cuts + k);
+  } else {
+    if (opts.k < 0 || opts.k > (int)net->net.indices.size()) return fail(QTN_ERR_INVALID_ARG, "opts.k out of range");
+    cutv = greedy_cuts(net->net, opts.k);
+    if (opts.search == QTN_SEARCH_GA && opts.k > 0) {
+      GAOptions ga;
+      ga.T = opts.ga_T;
+      ga.N = opts.ga_N;
+      ga.seed = opts.seed;
+      GAResult r = genetic_cuts(net->net, opts.k, ga, {cutv}, default_fitness, nullptr);
+      cutv = r.best;
+    } else if (opts.search != QTN_SEARCH_GREEDY && opts.search != QTN_SEARCH_GA) {
+      return fail(QTN_ERR_INVALID_ARG, "unknown search");
+    }
+  }
+  if (cutv.size() > 62) return fail(QTN_ERR_INVALID_ARG, "at most 62 cuts");
+  std::vector<int> ord;
+  if (order) {
+    if (order_len < 0) return fail(QTN_ERR_INVALID_ARG, "order_len < 0");
+    ord.assign(order, order + order_len);
+  }
+  qtn_plan_t* h = new (std::nothrow) qtn_plan_t;
+  if (!h) return fail(QTN_ERR_OOM, "host allocation failed");
+  h->net = net->net;
+  std::string err = make_plan(h->net, cutv, ord, &h->plan);
+  if (err.empty()) err = compile_program(h->net, h->plan, true, &h->lane_prog);
+  if (err.empty()) err = compile_program(h->net, h->plan, false, &h->block_prog);
+  if (!err.empty()) {
+    delete h;
+    return fail(QTN_ERR_INVALID_ARG, err);
+  }
+  h->exec = h->lane_prog.max_rank <= kLaneMaxRank ? Executor::Lane : Executor::Block;
+  h->log2_flops = h->plan.log2_flops_total();
+  h->log2_peak_bytes = std::log2(h->plan.peak_elems * 8.0);
+  if (opts.max_slice_bytes > 0 && h->plan.peak_elems * 8.0 > opts.max_slice_bytes) {
+    delete h;
+    return fail(QTN_ERR_PLAN_EXCEEDS_CAP, "per-slice working set exceeds max_slice_bytes");
+  }
+  *out = h;
+  return QTN_OK;
+}
+
+void qtn_plan_destroy(qtn_plan_t* plan) { delete plan; }
+
+qtn_status qtn_plan_set_kernel_timing(const qtn_plan_t* cplan, int on) {
+  qtn_plan_t* plan = const_cast<qtn_plan_t*>(cplan);
+  if (!plan) return fail(QTN_ERR_INVALID_ARG, "plan is NULL");
+  std::lock_guard<std::mutex> lk(plan->mu);
+  if (on && !plan->ev0) {
+    QTN_CUDA(cudaEventCreate(&plan->ev0));
+    QTN_CUDA(cudaEventCreate(&plan->ev1));
+  }
+  if ((on != 0) != plan->timing) {
+    for (auto& g : plan->graphs) cudaGraphExecDestroy(g.second);
+    plan->graphs.clear();
+    plan->timing = on != 0;
+  }
+  return QTN_OK;
+}
+
+qtn_status qtn_plan_kernel_ms(const qtn_plan_t* cplan, float* ms) {
+  qtn_plan_t* plan = const_cast<qtn_plan_t*>(cplan);
+  if (!plan || !ms) return fail(QTN_ERR_INVALID_ARG, "NULL argument");
+  if (!plan->timing || !plan->ev0) return fail(QTN_ERR_INVALID_ARG, "kernel timing is not enabled");
+  QTN_CUDA(cudaEventElapsedTime(ms, plan->ev0, plan->ev1));
+  return QTN_OK;
+}
+
+qtn_status qtn_search_cuts(const qtn_network_t* net, const qtn_plan_opts* opts, int32_t* cuts, double* trace,
+                           int trace_cap, int* trace_len, int* evaluations) {
+  if (!net || !opts || !cuts) return fail(QTN_ERR_INVALID_ARG, "NULL argument");
+  if (opts->k < 0 || opts->k > (int)net->net.indices.size()) return fail(QTN_ERR_INVALID_ARG, "opts.k out of range");
+  std::vector<double> tr;
+  std::vector<int> best;
+  int evals = 0;
+  if (opts->search == QTN_SEARCH_GREEDY) {
+    std::vector<int> cur;
+    for (int j = 0; j < opts->k; ++j) {
+      cur = greedy_cuts(net->net, j + 1, cur);
+      tr.push_back(default_fitness(net->net, cur, nullptr));
+    }
+    best = cur;
+  } else if (opts->search == QTN_SEARCH_GA) {
+    GAOptions ga;
+    ga.T = opts->ga_T;
+    ga.N = opts->ga_N;
+    ga.seed = opts->seed;
+    std::vector<std::vector<int>> seeds;
+    if (opts->k > 0) seeds.push_back(greedy_cuts(net->net, opts->k));
+    GAResult r = genetic_cuts(net->net, opts->k, ga, seeds, default_fitness, nullptr);
+    best = r.best;
+    tr = r.best_fitness_per_generation;
+    evals = r.evaluations;
+  } else {
+    return fail(QTN_ERR_INVALID_ARG, "unknown search");
+  }
+  for (int j = 0; j < opts->k; ++j) cuts[j] = best[j];
+  int nt = 0;
+  if (trace)
+    for (; nt < trace_cap && nt < (int)tr.size(); ++nt) trace[nt] = tr[nt];
+  if (trace_len) *trace_len = nt;
+  if (evaluations) *evaluations = evals;
+  return QTN_OK;
+}
+
+qtn_status qtn_plan_cost(const qtn_plan_t* plan, double* log2_flops, double* log2_peak_bytes, int* width, int* k) {
+  if (!plan) return fail(QTN_ERR_INVALID_ARG, "plan is NULL");
+  if (log2_flops) *log2_flops = plan->log2_flops;
+  if (log2_peak_bytes) *log2_peak_bytes = plan->log2_peak_bytes;
+  if (width) *width = plan->plan.width;
+  if (k) *k = (int)plan->plan.cuts.size();
+  return QTN_OK;
+}
+
+qtn_status qtn_plan_cuts(const qtn_plan_t* plan, int32_t* cuts) {
+  if (!plan || !cuts) return fail(QTN_ERR_INVALID_ARG, "NULL argument");
+  for (size_t j = 0; j < plan->plan.cuts.size(); ++j) cuts[j] = plan->plan.cuts[j];
+  return QTN_OK;
+}
+
+qtn_status qtn_plan_macs_per_slice(const qtn_plan_t* plan, double* macs) {
+  if (!plan || !macs) return fail(QTN_ERR_INVALID_ARG, "NULL argument");
+  *macs = plan->plan.macs;
+  return QTN_OK;
+}
+
+qtn_status qtn_plan_executor(const qtn_plan_t* plan, const char** name) {
+  if (!plan || !name) return fail(QTN_ERR_INVALID_ARG, "NULL argument");
+  *name = plan->exec == Executor::Lane ? "lane" : "block";
+  return QTN_OK;
+}
+
+qtn_status qtn_contract_amplitudes_device(const qtn_plan_t* cplan, const uint8_t* d_x, int nx, qtn_precision prec,
+                                          cudaStream_t stream, double* d_out) {
+  qtn_plan_t* plan = const_cast<qtn_plan_t*>(cplan);
+  if (!plan || !d_x || !d_out || nx <= 0) return fail(QTN_ERR_INVALID_ARG, "bad argument");
+  if (!precision_supported(prec)) return fail(QTN_ERR_UNSUPPORTED, "precision not available on this plan's executor");
+  std::lock_guard<std::mutex> lk(plan->mu);
+  qtn_status st = plan->ensure_device();
+  if (st != QTN_OK) return st;
+  return plan->run_graph(d_x, nx, prec, reinterpret_cast<double2*>(d_out), stream);
+}
+
+qtn_status qtn_contract_amplitude(const qtn_plan_t* cplan, const uint8_t* x, qtn_precision prec, cudaStream_t stream,
+                                  double out[2]) {
+  qtn_plan_t* plan = const_cast<qtn_plan_t*>(cplan);
+  if (!plan || !out) return fail(QTN_ERR_INVALID_ARG, "bad argument");
+  qtn_status st = validate_x(plan, x);
+  if (st != QTN_OK) return st;
+  if (!precision_supported(prec)) return fail(QTN_ERR_UNSUPPORTED, "precision not available on this plan's executor");
+  std::lock_guard<std::mutex> lk(plan->mu);
+  st = plan->ensure_device();
+  if (st != QTN_OK) return st;
+  ExecShape sh;
+  st = plan->shape_for(prec, 1, 1ull << plan->plan.cuts.size(), &sh);
+  if (st != QTN_OK) return st;
+  st = plan->ensure_workspace(1, sh.blocks_per_x);
+  if (st != QTN_OK) return st;
+  std::memcpy(plan->h_x_pinned, x, plan->net.n);
+  QTN_CUDA(cudaMemcpyAsync(plan->d_x_stage, plan->h_x_pinned, plan->net.n, cudaMemcpyHostToDevice, stream));
+  st = plan->run_graph(plan->d_x_stage, 1, prec, plan->d_out_stage, stream);
+  if (st != QTN_OK) return st;
+  QTN_CUDA(cudaMemcpyAsync(plan->h_out_pinned, plan->d_out_stage, sizeof(double2), cudaMemcpyDeviceToHost, stream));
+  QTN_CUDA(cudaStreamSynchronize(stream));
+  st = plan->check_err_flag();
+  if (st != QTN_OK) return st;
+  out[0] = plan->h_out_pinned[0];
+  out[1] = plan->h_out_pinned[1];
+  return QTN_OK;
+}
+
+qtn_status qtn_contract_slices(const qtn_plan_t* cplan, const uint8_t* x, uint64_t slice_lo, uint64_t slice_hi,
+                               qtn_precision prec, cudaStream_t stream, double out[4], double* d_slices) {
+  qtn_plan_t* plan = const_cast<qtn_plan_t*>(cplan);
+  if (!plan || !out) return fail(QTN_ERR_INVALID_ARG, "bad argument");
+  const uint64_t S = 1ull << plan->plan.cuts.size();
+  if (slice_lo > slice_hi || slice_hi > S) return fail(QTN_ERR_INVALID_ARG, "slice range outside [0, 2^k)");
+  qtn_status st = validate_x(plan, x);
+  if (st != QTN_OK) return st;
+  if (!precision_supported(prec)) return fail(QTN_ERR_UNSUPPORTED, "precision not available on this plan's executor");
+  std::lock_guard<std::mutex> lk(plan->mu);
+  st = plan->ensure_device();
+  if (st != QTN_OK) return st;
+  if (slice_lo == slice_hi) {
+    out[0] = out[1] = out[2] = out[3] = 0.0;
+    return QTN_OK;
+  }
+  ExecShape sh;
+  st = plan->shape_for(prec, 1, slice_hi - slice_lo, &sh);
+  if (st != QTN_OK) return st;
+  st = plan->ensure_workspace(1, sh.blocks_per_x);
+  if (st != QTN_OK) return st;
+  std::memcpy(plan->h_x_pinned, x, plan->net.n);
+  QTN_CUDA(cudaMemcpyAsync(plan->d_x_stage, plan->h_x_pinned, plan->net.n, cudaMemcpyHostToDevice, stream));
+  cudaError_t le = launch_contraction(plan->dprog, prec == QTN_FP64, plan->d_x_stage, 1, slice_lo, slice_hi,
+                                      plan->buffers(), sh, 1.0, nullptr, plan->d_raw_stage,
+                                      reinterpret_cast<double2*>(d_slices), stream);
+  if (le != cudaSuccess) return cuda_fail(le, "launch_contraction");
+  QTN_CUDA(cudaMemcpyAsync(plan->h_out_pinned, plan->d_raw_stage, sizeof(Partial), cudaMemcpyDeviceToHost, stream));
+  QTN_CUDA(cudaStreamSynchronize(stream));
+  st = plan->check_err_flag();
+  if (st != QTN_OK) return st;
+  for (int i = 0; i < 4; ++i) out[i] = plan->h_out_pinned[i];
+  return QTN_OK;
+}
+
+qtn_status qtn_contract_batch(const qtn_plan_t* const* plans, const uint8_t* const* xs, int njobs, qtn_precision prec,
+                              cudaStream_t stream, double* out) {
+  if (!plans || !xs || !out || njobs < 0) return fail(QTN_ERR_INVALID_ARG, "bad argument");
+  for (int j = 0; j < njobs; ++j) {
+    if (!plans[j]) return fail(QTN_ERR_INVALID_ARG, "NULL plan in batch");
+    qtn_status st = validate_x(plans[j], xs[j]);
+    if (st != QTN_OK) return st;
+  }
+  // Jobs of one plan run as one multi-bit-string launch.
+  std::map<const qtn_plan_t*, std::vector<int>> groups;
+  for (int j = 0; j < njobs; ++j) groups[plans[j]].push_back(j);
+  for (auto& [cp, jobs] : groups) {
+    qtn_plan_t* plan = const_cast<qtn_plan_t*>(cp);
+    std::lock_guard<std::mutex> lk(plan->mu);
+    qtn_status st = plan->ensure_device();
+    if (st != QTN_OK) return st;
+    int nx = (int)jobs.size();
+    ExecShape sh;
+    st = plan->shape_for(prec, nx, 1ull << plan->plan.cuts.size(), &sh);
+    if (st != QTN_OK) return st;
+    st = plan->ensure_workspace(nx, sh.blocks_per_x);
+    if (st != QTN_OK) return st;
+    for (int i = 0; i < nx; ++i) std::memcpy(plan->h_x_pinned + (size_t)i * plan->net.n, xs[jobs[i]], plan->net.n);
+    QTN_CUDA(cudaMemcpyAsync(plan->d_x_stage, plan->h_x_pinned, (size_t)nx * plan->net.n, cudaMemcpyHostToDevice,
+                             stream));
+    st = plan->run_graph(plan->d_x_stage, nx, prec, plan->d_out_stage, stream);
+    if (st != QTN_OK) return st;
+    QTN_CUDA(cudaMemcpyAsync(plan->h_out_pinned, plan->d_out_stage, (size_t)nx * sizeof(double2),
+                             cudaMemcpyDeviceToHost, stream));
+    QTN_CUDA(cudaStreamSynchronize(stream));
+    st = plan->check_err_flag();
+    if (st != QTN_OK) return st;
+    for (int i = 0; i < nx; ++i) {
+      out[2 * jobs[i]] = plan->h_out_pinned[2 * i];
+      out[2 * jobs[i] + 1] = plan->h_out_pinned[2 * i + 1];
+    }
+  }
+  return QTN_OK;
+}
+
+qtn_status qtn_plan_describe(const qtn_plan_t* plan, char* buf, size_t cap, size_t* len) {
+  if (!plan || !len) return fail(QTN_ERR_INVALID_ARG, "NULL argument");
+  std::ostringstream o;
+  o.precision(17);
+  const Plan& P = plan->plan;
+  o << "{\"n\":" << plan->net.n << ",\"p\":" << plan->net.p << ",\"n_leaves\":" << P.n_leaves << ",\"cuts\":";
+  json_ints(o, P.cuts.data(), P.cuts.size());
+  o << ",\"order\":";
+  json_ints(o, P.order.data(), P.order.size());
+  o << ",\"merges\":[";
+  for (size_t i = 0; i < P.merges.size(); ++i)
+    o << (i ? "," : "") << "[" << P.merges[i].a << "," << P.merges[i].b << "," << P.merges[i].c << "]";
+  o << "],\"tensors\":[";
+  for (size_t i = 0; i < P.tensors.size(); ++i) {
+    o << (i ? "," : "");
+    json_ints(o, P.tensors[i].data(), P.tensors[i].size());
+  }
+  o << "],\"width\":" << P.width << ",\"max_rank\":" << P.max_rank << ",\"macs\":" << P.macs
+    << ",\"peak_elems\":" << P.peak_elems << ",\"executor\":\"" << (plan->exec == Executor::Lane ? "lane" : "block")
+    << "\",\"programs\":{";
+  for (int which = 0; which < 2; ++which) {
+    const Program& pg = which == 0 ? plan->lane_prog : plan->block_prog;
+    o << (which ? "," : "") << "\"" << (which == 0 ? "lane" : "block") << "\":{\"leaf_elems\":" << pg.leaf_elems
+      << ",\"arena_elems\":" << pg.arena_elems << ",\"width\":" << pg.width << ",\"max_rank\":" << pg.max_rank
+      << ",\"macs_per_slice\":" << pg.macs_per_slice << ",\"leaves\":[";
+    for (size_t i = 0; i < pg.leaves.size(); ++i) {
+      const DevLeaf& L = pg.leaves[i];
+      int cb[kMaxLeafCuts], sb[8];
+      for (int j = 0; j < L.ncut; ++j) cb[j] = L.cut_bit[j];
+      for (int j = 0; j < L.rank_nc + L.ncut; ++j) sb[j] = L.slot_of_bit[j];
+      o << (i ? "," : "") << "{\"base\":" << L.base << ",\"rank_nc\":" << (int)L.rank_nc << ",\"gate\":" << L.gate
+        << ",\"cut_bit\":";
+      json_ints(o, cb, L.ncut);
+      o << ",\"slot_of_bit\":";
+      json_ints(o, sb, L.rank_nc + L.ncut);
+      o << "}";
+    }
+    o << "],\"steps\":[";
+    for (size_t i = 0; i < pg.steps.size(); ++i) {
+      const DevStep& s = pg.steps[i];
+      int w[kMaxRank];
+      for (int j = 0; j < s.ma + s.nb; ++j) w[j] = s.w[j];
+      o << (i ? "," : "") << "{\"ma\":" << (int)s.ma << ",\"nb\":" << (int)s.nb << ",\"kb\":" << (int)s.kb
+        << ",\"flags\":" << (int)s.flags << ",\"a\":" << s.a << ",\"b\":" << s.b << ",\"c\":" << s.c << ",\"w\":";
+      json_ints(o, w, s.ma + s.nb);
+      o << "}";
+    }
+    o << "]}";
+  }
+  o << "},\"gates\":[";
+  for (size_t g = 0; g < plan->net.gates.size(); ++g) {
+    const Gate& G = plan->net.gates[g];
+    o << (g ? "," : "") << "{\"layer\":" << G.layer << ",\"q\":[" << G.q[0] << "," << G.q[1] << "],\"in_h\":["
+      << (int)G.in_h[0] << "," << (int)G.in_h[1] << "],\"out_kind\":[" << (int)G.out_kind[0] << ","
+      << (int)G.out_kind[1] << "],\"leg\":[" << G.leg[0] << "," << G.leg[1] << "," << G.leg[2] << "," << G.leg[3]
+      << "]}";
+  }
+  o << "]}";
+  std::string s = o.str();
+  *len = s.size() + 1;
+  if (buf && cap >= s.size() + 1) std::memcpy(buf, s.c_str(), s.size() + 1);
+  return QTN_OK;
+}
+
+}  // extern "C"

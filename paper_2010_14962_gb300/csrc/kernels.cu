@@ -1,0 +1,496 @@
+// Sliced tensor-network contraction on sm_103a.
+//
+//   leaf_build_kernel   evaluates every gate tensor of the network once per
+//                       bit string in FP64 (sincos of gamma_l, beta_l) and
+//                       rounds it to the working precision (Sec. II.A: the
+//                       tensors of the circuit's vertices).
+//   lane_exec_kernel    one slice per GPU thread.  All slices share one step
+//                       program (Sec. III.A: the subnetworks have identical
+//                       topology, only the fixed cut values differ), so a warp
+//                       runs 32 slices in lock step; each thread keeps its
+//                       intermediates in a private column of shared memory
+//                       and every merge (Eq. 1) is a fully unrolled
+//                       register-resident product specialised on its shape.
+//   block_exec_kernel   one slice per thread block, for programs with larger
+//                       tensors; threads split the output elements of each
+//                       merge.
+//   finalize_kernel     fixed-order compensated FP64 sum of the per-block
+//                       partial sums over slices (Eq. 2) and the 2^{-n/2}
+//                       normalisation of the unnormalised H|0> = (1, 1).
+#include "kernels.cuh"
+
+namespace qtn {
+namespace {
+
+struct ExecParams {
+  const DevStep* steps;
+  const DevLeaf* leaves;
+  const void* leaf_tables;
+  Partial* partials;
+  double2* slices;  // optional per-slice output
+  uint64_t slice_lo, slice_hi;
+  uint32_t leaf_elems;
+  uint32_t arena_elems;
+  int n_steps, n_leaves;
+  int blocks_per_x;  // blocks per bit string; blockIdx.x = xi * blocks_per_x + b
+};
+
+template <class V>
+struct CplxOps;
+template <>
+struct CplxOps<float2> {
+  using R = float;
+  static __device__ __forceinline__ float2 zero() { return make_float2(0.f, 0.f); }
+  static __device__ __forceinline__ void fma(float2& acc, float2 a, float2 b) {
+    acc.x = fmaf(a.x, b.x, acc.x);
+    acc.x = fmaf(-a.y, b.y, acc.x);
+    acc.y = fmaf(a.x, b.y, acc.y);
+    acc.y = fmaf(a.y, b.x, acc.y);
+  }
+  static __device__ __forceinline__ float2 from(double re, double im) {
+    return make_float2((float)re, (float)im);
+  }
+};
+template <>
+struct CplxOps<double2> {
+  using R = double;
+  static __device__ __forceinline__ double2 zero() { return make_double2(0.0, 0.0); }
+  static __device__ __forceinline__ void fma(double2& acc, double2 a, double2 b) {
+    acc.x = ::fma(a.x, b.x, acc.x);
+    acc.x = ::fma(-a.y, b.y, acc.x);
+    acc.y = ::fma(a.x, b.y, acc.y);
+    acc.y = ::fma(a.y, b.x, acc.y);
+  }
+  static __device__ __forceinline__ double2 from(double re, double im) { return make_double2(re, im); }
+};
+
+__device__ __forceinline__ void kahan_add(double& sum, double& comp, double v) {
+  double y = v - comp;
+  double t = sum + y;
+  comp = (t - sum) - y;
+  sum = t;
+}
+
+// Offset of slice s's sub-block inside a leaf: cut legs are the high bits.
+__device__ __forceinline__ uint32_t leaf_offset(const DevLeaf& L, uint64_t s) {
+  uint32_t off = L.base;
+  for (int j = 0; j < L.ncut; ++j) off += (uint32_t)((s >> L.cut_bit[j]) & 1u) << (L.rank_nc + j);
+  return off;
+}
+
+// Copies `bytes` (multiple of 4) from global to shared memory.
+__device__ __forceinline__ void copy_words(void* dst, const void* src, size_t bytes) {
+  const uint32_t* s = static_cast<const uint32_t*>(src);
+  uint32_t* d = static_cast<uint32_t*>(dst);
+  for (size_t i = threadIdx.x; i < bytes / 4; i += blockDim.x) d[i] = s[i];
+}
+
+struct SmemLayout {
+  size_t leaves, table, arena, red, total;
+};
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+__host__ __device__ inline SmemLayout smem_layout(int n_steps, int n_leaves, uint32_t leaf_elems,
+                                                  uint32_t arena_elems, int elem_bytes, int threads,
+                                                  bool per_thread_arena) {
+  SmemLayout L;
+  L.leaves = align16((size_t)n_steps * sizeof(DevStep));
+  L.table = L.leaves + align16((size_t)n_leaves * sizeof(DevLeaf));
+  L.arena = L.table + align16((size_t)leaf_elems * elem_bytes);
+  size_t arena_bytes = (size_t)arena_elems * elem_bytes * (per_thread_arena ? threads : 1);
+  L.red = L.arena + align16(arena_bytes);
+  L.total = L.red + (size_t)threads * sizeof(Partial);
+  return L;
+}
+
+// ------------------------------------------------------------ leaf build --
+
+template <class V>
+__global__ void leaf_build_kernel(const DevLeaf* __restrict__ leaves, const int32_t* __restrict__ gate_q,
+                                  const int8_t* __restrict__ gate_layer, const int8_t* __restrict__ gate_in_h,
+                                  const int8_t* __restrict__ gate_out_kind, const double* __restrict__ gamma,
+                                  const double* __restrict__ beta, const uint8_t* __restrict__ x, int n,
+                                  uint32_t leaf_elems, int n_leaves, V* __restrict__ out) {
+  const DevLeaf L = leaves[blockIdx.x % n_leaves];
+  const int xi = blockIdx.x / n_leaves;
+  const int r = L.rank_nc + L.ncut;
+  for (int e = threadIdx.x; e < (1 << r); e += blockDim.x) {
+    double re = 1.0, im = 0.0;
+    if (L.gate >= 0) {
+      const int g = L.gate;
+      const int l = gate_layer[g];
+      int v[4] = {-1, -1, -1, -1};
+      for (int b = 0; b < r; ++b) v[L.slot_of_bit[b]] = (e >> b) & 1;
+      double sg, cg, sb, cb;
+      sincos(gamma[l], &sg, &cg);
+      sincos(beta[l], &sb, &cb);
+      re = 0.0;
+      im = 0.0;
+      // T = sum over the wire values (u0, u1) inside the diagonal ZZ gate of
+      //   exp(-i gamma s0 s1) * prod_w [in leg: delta] * [out leg: delta or
+      //   RX(2 beta)[out, u] or <x_q|RX(2 beta)|u>];  absorbed H|0> = (1, 1).
+      for (int u0 = 0; u0 < 2; ++u0)
+        for (int u1 = 0; u1 < 2; ++u1) {
+          const int u[2] = {u0, u1};
+          const double s = (double)((1 - 2 * u0) * (1 - 2 * u1));
+          double tre = cg, tim = -s * sg;
+          bool ok = true;
+          for (int w = 0; w < 2; ++w) {
+            if (!gate_in_h[2 * g + w] && v[w] != u[w]) ok = false;
+            const int kind = gate_out_kind[2 * g + w];
+            if (kind == OUT_PLAIN) {
+              if (v[2 + w] != u[w]) ok = false;
+            } else {
+              const int row = (kind == OUT_RX) ? v[2 + w] : (int)x[(size_t)xi * n + gate_q[2 * g + w]];
+              if (row != u[w]) {  // multiply by -i sin(beta)
+                const double nre = tim * sb, nim = -tre * sb;
+                tre = nre;
+                tim = nim;
+              } else {
+                tre *= cb;
+                tim *= cb;
+              }
+            }
+          }
+          if (ok) {
+            re += tre;
+            im += tim;
+          }
+        }
+    }
+    out[(size_t)xi * leaf_elems + L.base + e] = CplxOps<V>::from(re, im);
+  }
+}
+
+// ------------------------------------------------------------- lane exec --
+
+// C[m, n] = sum_k A[m + (k << MA)] * B[k + (n << KB)], stored at the bit
+// weights w of C's layout.  A stays in registers while B is streamed one
+// column (fixed n) at a time.  Operands stride sa / sb elements, C strides sc.
+template <int MA, int NB, int KB, class V>
+__device__ __forceinline__ V lane_merge(const V* __restrict__ A, int sa, const V* __restrict__ B, int sb,
+                                        V* __restrict__ C, int sc, const uint16_t* __restrict__ w,
+                                        bool store) {
+  constexpr int NA = 1 << (MA + KB);
+  constexpr int RC = MA + NB;
+  V a[NA];
+#pragma unroll
+  for (int i = 0; i < NA; ++i) a[i] = A[i * sa];
+  uint32_t wl[RC > 0 ? RC : 1];
+#pragma unroll
+  for (int j = 0; j < RC; ++j) wl[j] = w[j];
+  V acc = CplxOps<V>::zero();
+#pragma unroll
+  for (int n = 0; n < (1 << NB); ++n) {
+    V b[1 << KB];
+#pragma unroll
+    for (int k = 0; k < (1 << KB); ++k) b[k] = B[(k + (n << KB)) * sb];
+#pragma unroll
+    for (int m = 0; m < (1 << MA); ++m) {
+      acc = CplxOps<V>::zero();
+#pragma unroll
+      for (int k = 0; k < (1 << KB); ++k) CplxOps<V>::fma(acc, a[m + (k << MA)], b[k]);
+      if (store) {
+        const uint32_t o = (uint32_t)(m + (n << MA));
+        uint32_t pos = 0;
+#pragma unroll
+        for (int j = 0; j < RC; ++j)
+          if ((o >> j) & 1u) pos += wl[j];
+        C[pos * sc] = acc;
+      }
+    }
+  }
+  return acc;
+}
+
+#define QTN_SHAPE(MA, NB, KB) ((MA) | ((NB) << 3) | ((KB) << 6))
+#define QTN_LANE_CASE(MA, NB, KB)                                 \
+  case QTN_SHAPE(MA, NB, KB):                                     \
+    r = lane_merge<MA, NB, KB, V>(A, sa, B, sb, C, sc, w, store); \
+    break;
+// Every (ma, nb, kb) whose three tensors have rank <= kLaneMaxRank (5).
+#define QTN_LANE_CASES \
+  QTN_LANE_CASE(0, 0, 0) QTN_LANE_CASE(0, 1, 0) QTN_LANE_CASE(0, 2, 0) QTN_LANE_CASE(0, 3, 0) \
+  QTN_LANE_CASE(0, 4, 0) QTN_LANE_CASE(0, 5, 0) QTN_LANE_CASE(1, 0, 0) QTN_LANE_CASE(1, 1, 0) \
+  QTN_LANE_CASE(1, 2, 0) QTN_LANE_CASE(1, 3, 0) QTN_LANE_CASE(1, 4, 0) QTN_LANE_CASE(2, 0, 0) \
+  QTN_LANE_CASE(2, 1, 0) QTN_LANE_CASE(2, 2, 0) QTN_LANE_CASE(2, 3, 0) QTN_LANE_CASE(3, 0, 0) \
+  QTN_LANE_CASE(3, 1, 0) QTN_LANE_CASE(3, 2, 0) QTN_LANE_CASE(4, 0, 0) QTN_LANE_CASE(4, 1, 0) \
+  QTN_LANE_CASE(5, 0, 0) QTN_LANE_CASE(0, 0, 1) QTN_LANE_CASE(0, 1, 1) QTN_LANE_CASE(0, 2, 1) \
+  QTN_LANE_CASE(0, 3, 1) QTN_LANE_CASE(0, 4, 1) QTN_LANE_CASE(1, 0, 1) QTN_LANE_CASE(1, 1, 1) \
+  QTN_LANE_CASE(1, 2, 1) QTN_LANE_CASE(1, 3, 1) QTN_LANE_CASE(1, 4, 1) QTN_LANE_CASE(2, 0, 1) \
+  QTN_LANE_CASE(2, 1, 1) QTN_LANE_CASE(2, 2, 1) QTN_LANE_CASE(2, 3, 1) QTN_LANE_CASE(3, 0, 1) \
+  QTN_LANE_CASE(3, 1, 1) QTN_LANE_CASE(3, 2, 1) QTN_LANE_CASE(4, 0, 1) QTN_LANE_CASE(4, 1, 1) \
+  QTN_LANE_CASE(0, 0, 2) QTN_LANE_CASE(0, 1, 2) QTN_LANE_CASE(0, 2, 2) QTN_LANE_CASE(0, 3, 2) \
+  QTN_LANE_CASE(1, 0, 2) QTN_LANE_CASE(1, 1, 2) QTN_LANE_CASE(1, 2, 2) QTN_LANE_CASE(1, 3, 2) \
+  QTN_LANE_CASE(2, 0, 2) QTN_LANE_CASE(2, 1, 2) QTN_LANE_CASE(2, 2, 2) QTN_LANE_CASE(2, 3, 2) \
+  QTN_LANE_CASE(3, 0, 2) QTN_LANE_CASE(3, 1, 2) QTN_LANE_CASE(3, 2, 2) QTN_LANE_CASE(0, 0, 3) \
+  QTN_LANE_CASE(0, 1, 3) QTN_LANE_CASE(0, 2, 3) QTN_LANE_CASE(1, 0, 3) QTN_LANE_CASE(1, 1, 3) \
+  QTN_LANE_CASE(1, 2, 3) QTN_LANE_CASE(2, 0, 3) QTN_LANE_CASE(2, 1, 3) QTN_LANE_CASE(2, 2, 3) \
+  QTN_LANE_CASE(0, 0, 4) QTN_LANE_CASE(0, 1, 4) QTN_LANE_CASE(1, 0, 4) QTN_LANE_CASE(1, 1, 4) \
+  QTN_LANE_CASE(0, 0, 5)
+
+template <class V>
+__global__ void __launch_bounds__(128) lane_exec_kernel(ExecParams P, int* err) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int T = blockDim.x;
+  const SmemLayout lay = smem_layout(P.n_steps, P.n_leaves, P.leaf_elems, P.arena_elems, (int)sizeof(V), T, true);
+  DevStep* s_steps = reinterpret_cast<DevStep*>(smem);
+  DevLeaf* s_leaves = reinterpret_cast<DevLeaf*>(smem + lay.leaves);
+  V* s_lt = reinterpret_cast<V*>(smem + lay.table);
+  V* s_arena = reinterpret_cast<V*>(smem + lay.arena);
+  Partial* s_red = reinterpret_cast<Partial*>(smem + lay.red);
+  const int xi = blockIdx.x / P.blocks_per_x;
+  const int bx = blockIdx.x % P.blocks_per_x;
+  copy_words(s_steps, P.steps, (size_t)P.n_steps * sizeof(DevStep));
+  copy_words(s_leaves, P.leaves, (size_t)P.n_leaves * sizeof(DevLeaf));
+  copy_words(s_lt, static_cast<const V*>(P.leaf_tables) + (size_t)xi * P.leaf_elems,
+             (size_t)P.leaf_elems * sizeof(V));
+  __syncthreads();
+
+  V* ar = s_arena + threadIdx.x;
+  double sr = 0.0, si = 0.0, cr = 0.0, ci = 0.0;
+  const uint64_t S = P.slice_hi - P.slice_lo;
+  for (uint64_t i = (uint64_t)bx * T + threadIdx.x; i < S; i += (uint64_t)P.blocks_per_x * T) {
+    const uint64_t s = P.slice_lo + i;
+    V res = CplxOps<V>::zero();
+    for (int j = 0; j < P.n_steps; ++j) {
+      const DevStep& st = s_steps[j];
+      const V* A;
+      const V* B;
+      int sa, sb;
+      if (st.flags & STEP_A_LEAF) {
+        A = s_lt + leaf_offset(s_leaves[st.a], s);
+        sa = 1;
+      } else {
+        A = ar + (size_t)st.a * T;
+        sa = T;
+      }
+      if (st.flags & STEP_B_LEAF) {
+        B = s_lt + leaf_offset(s_leaves[st.b], s);
+        sb = 1;
+      } else {
+        B = ar + (size_t)st.b * T;
+        sb = T;
+      }
+      V* C = ar + (size_t)st.c * T;
+      const int sc = T;
+      const uint16_t* w = st.w;
+      const bool store = !(st.flags & STEP_ROOT);
+      V r = CplxOps<V>::zero();
+      switch (QTN_SHAPE(st.ma, st.nb, st.kb)) {
+        QTN_LANE_CASES
+        default:
+          atomicOr(err, 1);
+          break;
+      }
+      if (!store) res = r;
+    }
+    kahan_add(sr, cr, (double)res.x);
+    kahan_add(si, ci, (double)res.y);
+    if (P.slices) P.slices[(size_t)xi * S + i] = make_double2((double)res.x, (double)res.y);
+  }
+  s_red[threadIdx.x] = Partial::make(sr, si, cr, ci);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, b = 0, ca = 0, cb = 0;
+    for (int t = 0; t < T; ++t) {
+      const Partial v = s_red[t];
+      kahan_add(a, ca, v.re);
+      kahan_add(a, ca, -v.cre);
+      kahan_add(b, cb, v.im);
+      kahan_add(b, cb, -v.cim);
+    }
+    P.partials[(size_t)xi * P.blocks_per_x + bx] = Partial::make(a, b, ca, cb);
+  }
+}
+
+// ------------------------------------------------------------ block exec --
+
+template <class V>
+__global__ void __launch_bounds__(256) block_exec_kernel(ExecParams P) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int T = blockDim.x;
+  const SmemLayout lay = smem_layout(P.n_steps, P.n_leaves, P.leaf_elems, P.arena_elems, (int)sizeof(V), T, false);
+  DevStep* s_steps = reinterpret_cast<DevStep*>(smem);
+  DevLeaf* s_leaves = reinterpret_cast<DevLeaf*>(smem + lay.leaves);
+  V* s_lt = reinterpret_cast<V*>(smem + lay.table);
+  V* s_arena = reinterpret_cast<V*>(smem + lay.arena);
+  const int xi = blockIdx.x / P.blocks_per_x;
+  const int bx = blockIdx.x % P.blocks_per_x;
+  copy_words(s_steps, P.steps, (size_t)P.n_steps * sizeof(DevStep));
+  copy_words(s_leaves, P.leaves, (size_t)P.n_leaves * sizeof(DevLeaf));
+  copy_words(s_lt, static_cast<const V*>(P.leaf_tables) + (size_t)xi * P.leaf_elems,
+             (size_t)P.leaf_elems * sizeof(V));
+  __syncthreads();
+
+  double sr = 0.0, si = 0.0, cr = 0.0, ci = 0.0;
+  const uint64_t S = P.slice_hi - P.slice_lo;
+  for (uint64_t i = bx; i < S; i += P.blocks_per_x) {
+    const uint64_t s = P.slice_lo + i;
+    V res = CplxOps<V>::zero();
+    for (int j = 0; j < P.n_steps; ++j) {
+      const DevStep& st = s_steps[j];
+      const V* A = (st.flags & STEP_A_LEAF) ? s_lt + leaf_offset(s_leaves[st.a], s) : s_arena + st.a;
+      const V* B = (st.flags & STEP_B_LEAF) ? s_lt + leaf_offset(s_leaves[st.b], s) : s_arena + st.b;
+      const int ma = st.ma, kb = st.kb, rc = st.ma + st.nb;
+      const uint32_t NC = 1u << rc, K = 1u << kb, mmask = (1u << ma) - 1u;
+      for (uint32_t o = threadIdx.x; o < NC; o += T) {
+        const uint32_t m = o & mmask, n = o >> ma;
+        const V* ap = A + m;
+        const V* bp = B + (n << kb);
+        V acc = CplxOps<V>::zero();
+        for (uint32_t k = 0; k < K; ++k) CplxOps<V>::fma(acc, ap[k << ma], bp[k]);
+        if (st.flags & STEP_ROOT) {
+          res = acc;
+        } else {
+          uint32_t pos = 0;
+          for (int b = 0; b < rc; ++b)
+            if ((o >> b) & 1u) pos += st.w[b];
+          s_arena[st.c + pos] = acc;
+        }
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      kahan_add(sr, cr, (double)res.x);
+      kahan_add(si, ci, (double)res.y);
+      if (P.slices) P.slices[(size_t)xi * S + i] = make_double2((double)res.x, (double)res.y);
+    }
+  }
+  if (threadIdx.x == 0) P.partials[(size_t)xi * P.blocks_per_x + bx] = Partial::make(sr, si, cr, ci);
+}
+
+// -------------------------------------------------------------- finalize --
+
+__global__ void finalize_kernel(const Partial* __restrict__ partials, int blocks, int nx, double scale,
+                                double2* __restrict__ out, Partial* __restrict__ raw) {
+  const int xi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (xi >= nx) return;
+  double a = 0, b = 0, ca = 0, cb = 0;
+  for (int t = 0; t < blocks; ++t) {  // fixed order: deterministic result
+    const Partial v = partials[(size_t)xi * blocks + t];
+    kahan_add(a, ca, v.re);
+    kahan_add(a, ca, -v.cre);
+    kahan_add(b, cb, v.im);
+    kahan_add(b, cb, -v.cim);
+  }
+  if (out) out[xi] = make_double2((a - ca) * scale, (b - cb) * scale);
+  if (raw) raw[xi] = Partial::make(a, b, ca, cb);
+}
+
+int g_num_sms = 0;
+
+}  // namespace
+
+bool exec_shape(const DeviceProgram& prog, int elem_bytes, int nx, uint64_t slices_per_x, ExecShape* out) {
+  if (g_num_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 1;
+  }
+  int max_optin = 0;
+  {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  }
+  ExecShape sh;
+  const bool lane = prog.exec == Executor::Lane;
+  sh.threads = lane ? 128 : 256;
+  SmemLayout L = smem_layout(prog.n_steps, prog.n_leaves, prog.leaf_elems, prog.arena_elems, elem_bytes,
+                             sh.threads, lane);
+  if (lane && L.total > (size_t)max_optin) {
+    sh.threads = 64;
+    L = smem_layout(prog.n_steps, prog.n_leaves, prog.leaf_elems, prog.arena_elems, elem_bytes, sh.threads, lane);
+  }
+  if (L.total > (size_t)max_optin) return false;
+  sh.smem = L.total;
+  int occ = 1;
+  cudaError_t e;
+  if (lane) {
+    if (elem_bytes == 8) {
+      cudaFuncSetAttribute(lane_exec_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lane_exec_kernel<float2>, sh.threads, sh.smem);
+    } else {
+      cudaFuncSetAttribute(lane_exec_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lane_exec_kernel<double2>, sh.threads, sh.smem);
+    }
+  } else {
+    if (elem_bytes == 8) {
+      cudaFuncSetAttribute(block_exec_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, block_exec_kernel<float2>, sh.threads, sh.smem);
+    } else {
+      cudaFuncSetAttribute(block_exec_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, block_exec_kernel<double2>, sh.threads, sh.smem);
+    }
+  }
+  if (e != cudaSuccess || occ < 1) return false;
+  const uint64_t total_blocks = (uint64_t)g_num_sms * (uint64_t)occ;
+  uint64_t per_x = total_blocks / (uint64_t)(nx > 0 ? nx : 1);
+  if (per_x < 1) per_x = 1;
+  const uint64_t units = lane ? (slices_per_x + sh.threads - 1) / sh.threads : slices_per_x;
+  if (per_x > units) per_x = units;
+  if (per_x < 1) per_x = 1;
+  sh.blocks_per_x = (int)per_x;
+  *out = sh;
+  return true;
+}
+
+cudaError_t launch_contraction(const DeviceProgram& prog, bool fp64, const uint8_t* d_x, int nx,
+                               uint64_t slice_lo, uint64_t slice_hi, const LaunchBuffers& buf,
+                               const ExecShape& shape, double scale, double2* d_out, Partial* d_raw,
+                               double2* d_slices, cudaStream_t stream, cudaEvent_t ev0, cudaEvent_t ev1) {
+  if (nx <= 0) return cudaSuccess;
+  const unsigned lgrid = (unsigned)prog.n_leaves * (unsigned)nx;
+  if (fp64)
+    leaf_build_kernel<double2><<<lgrid, 32, 0, stream>>>(prog.leaves, prog.gate_q, prog.gate_layer, prog.gate_in_h,
+                                                          prog.gate_out_kind, prog.gamma, prog.beta, d_x, prog.n,
+                                                          prog.leaf_elems, prog.n_leaves,
+                                                          static_cast<double2*>(buf.leaf_tables));
+  else
+    leaf_build_kernel<float2><<<lgrid, 32, 0, stream>>>(prog.leaves, prog.gate_q, prog.gate_layer, prog.gate_in_h,
+                                                         prog.gate_out_kind, prog.gamma, prog.beta, d_x, prog.n,
+                                                         prog.leaf_elems, prog.n_leaves,
+                                                         static_cast<float2*>(buf.leaf_tables));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  ExecParams P;
+  P.steps = prog.steps;
+  P.leaves = prog.leaves;
+  P.leaf_tables = buf.leaf_tables;
+  P.partials = buf.partials;
+  P.slices = d_slices;
+  P.slice_lo = slice_lo;
+  P.slice_hi = slice_hi;
+  P.leaf_elems = prog.leaf_elems;
+  P.arena_elems = prog.arena_elems;
+  P.n_steps = prog.n_steps;
+  P.n_leaves = prog.n_leaves;
+  P.blocks_per_x = shape.blocks_per_x;
+  const unsigned grid = (unsigned)shape.blocks_per_x * (unsigned)nx;
+  if (ev0) {
+    e = cudaEventRecord(ev0, stream);
+    if (e != cudaSuccess) return e;
+  }
+  if (prog.exec == Executor::Lane) {
+    if (fp64)
+      lane_exec_kernel<double2><<<grid, shape.threads, shape.smem, stream>>>(P, buf.err);
+    else
+      lane_exec_kernel<float2><<<grid, shape.threads, shape.smem, stream>>>(P, buf.err);
+  } else {
+    if (fp64)
+      block_exec_kernel<double2><<<grid, shape.threads, shape.smem, stream>>>(P);
+    else
+      block_exec_kernel<float2><<<grid, shape.threads, shape.smem, stream>>>(P);
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (ev1) {
+    e = cudaEventRecord(ev1, stream);
+    if (e != cudaSuccess) return e;
+  }
+  finalize_kernel<<<(nx + 127) / 128, 128, 0, stream>>>(buf.partials, shape.blocks_per_x, nx, scale, d_out, d_raw);
+  return cudaGetLastError();
+}
+
+}  // namespace qtn

@@ -1,0 +1,71 @@
+// Device side of the sliced contraction: launch interface shared by the
+// C-ABI layer and the kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "program.hpp"
+
+namespace qtn {
+
+enum class Executor : int { Lane = 0, Block = 1 };
+
+// Compensated (Kahan) partial sum of complex slice results: the running sums
+// (re, im) and their compensations (cre, cim).
+struct alignas(16) Partial {
+  double re, im, cre, cim;
+  __host__ __device__ static Partial make(double a, double b, double c, double d) { return Partial{a, b, c, d}; }
+};
+
+// Device copy of one plan's program.
+struct DeviceProgram {
+  int n = 0, p = 0, k = 0;
+  int n_leaves = 0, n_steps = 0;
+  uint32_t leaf_elems = 0;
+  uint32_t arena_elems = 0;  // of the executor's program
+  Executor exec = Executor::Lane;
+  const DevLeaf* leaves = nullptr;
+  const DevStep* steps = nullptr;
+  const int32_t* gate_q = nullptr;
+  const int8_t* gate_layer = nullptr;
+  const int8_t* gate_in_h = nullptr;
+  const int8_t* gate_out_kind = nullptr;
+  const double* gamma = nullptr;
+  const double* beta = nullptr;
+};
+
+// One launch sequence: leaf tables for nx bit strings, the slice range
+// [slice_lo, slice_hi) of each, per-block Kahan partials, and the final sum.
+struct LaunchBuffers {
+  void* leaf_tables = nullptr;   // nx * leaf_elems elements (float2 / double2)
+  Partial* partials = nullptr;   // nx * blocks_per_x
+  int* err = nullptr;            // set non-zero by a kernel that met a bad step
+};
+
+// Grid shape and dynamic shared memory of the executor for `prog`, `nx` and
+// element size `elem_bytes` (8: complex64, 16: complex128).  Returns false if
+// the program does not fit on chip.
+struct ExecShape {
+  int threads = 0;
+  int blocks_per_x = 0;
+  size_t smem = 0;
+};
+bool exec_shape(const DeviceProgram& prog, int elem_bytes, int nx, uint64_t slices_per_x, ExecShape* out);
+
+// Enqueues leaf build + execution + finalisation on `stream`.
+//   d_x       : nx * n bit bytes (device)
+//   d_out     : nx double2 (scaled amplitude), may be null
+//   d_raw     : nx Partial (unscaled Kahan sum and compensation), may be null
+//   d_slices  : nx * (slice_hi - slice_lo) double2, may be null
+//   ev0, ev1  : optional events recorded just before / after the executor
+cudaError_t launch_contraction(const DeviceProgram& prog, bool fp64, const uint8_t* d_x, int nx,
+                               uint64_t slice_lo, uint64_t slice_hi, const LaunchBuffers& buf,
+                               const ExecShape& shape, double scale, double2* d_out, Partial* d_raw,
+                               double2* d_slices, cudaStream_t stream, cudaEvent_t ev0 = nullptr,
+                               cudaEvent_t ev1 = nullptr);
+
+// Largest tensor rank the lane executor accepts.
+constexpr int kLaneMaxRank = 5;
+
+}  // namespace qtn

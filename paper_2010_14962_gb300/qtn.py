@@ -1,0 +1,301 @@
+"""Python binding of the qtn C ABI (``include/qtn.h``).
+
+Argument marshalling only: every step of the contraction runs in the CUDA
+library ``_build/libqtn.so``.  Loading fails loudly when the library has not
+been built (``python -c "import __graft_entry__ as g; g.build()"``); there is
+no CPU fallback.  PyTorch is used only to hand device buffers and streams to
+the library.
+"""
+from __future__ import annotations
+
+import ctypes
+import json
+import os
+import re
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libqtn.so")
+HEADER = os.path.join(os.path.dirname(_HERE), "include", "qtn.h")
+
+PRECISIONS = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16x3": 3, "tf32x3": 4, "bf16x6": 5}
+SEARCHES = {"greedy": 0, "ga": 1}
+
+
+class QTNError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"qtn status {status}: {message}")
+        self.status = status
+
+
+class _PlanOpts(ctypes.Structure):
+    _fields_ = [("search", ctypes.c_int), ("k", ctypes.c_int), ("seed", ctypes.c_uint64), ("ga_T", ctypes.c_int),
+                ("ga_N", ctypes.c_int), ("max_slice_bytes", ctypes.c_double)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def declared_symbols() -> list[str]:
+    """Every function declared in include/qtn.h."""
+    with open(HEADER) as f:
+        text = f.read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(qtn_[a-z0-9_]+)\s*\(", text)))
+
+
+def lib():
+    """The loaded library (raises if it is missing)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"qtn CUDA library not built: {LIB_PATH} is missing; run __graft_entry__.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        P = ctypes.POINTER
+        i32p, f64p, u8p, vp = P(ctypes.c_int32), P(ctypes.c_double), P(ctypes.c_uint8), ctypes.c_void_p
+        sig = {
+            "qtn_build_network": [ctypes.c_int, ctypes.c_int, i32p, ctypes.c_int, f64p, f64p, P(vp)],
+            "qtn_network_destroy": [vp],
+            "qtn_network_info": [vp, P(ctypes.c_int), P(ctypes.c_int)],
+            "qtn_network_index": [vp, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int),
+                                  P(ctypes.c_int)],
+            "qtn_plan_opts_default": [P(_PlanOpts)],
+            "qtn_plan": [vp, i32p, ctypes.c_int, i32p, ctypes.c_int, P(_PlanOpts), P(vp)],
+            "qtn_plan_destroy": [vp],
+            "qtn_plan_cost": [vp, f64p, f64p, P(ctypes.c_int), P(ctypes.c_int)],
+            "qtn_plan_cuts": [vp, i32p],
+            "qtn_plan_macs_per_slice": [vp, f64p],
+            "qtn_contract_amplitude": [vp, u8p, ctypes.c_int, vp, f64p],
+            "qtn_contract_amplitudes_device": [vp, vp, ctypes.c_int, ctypes.c_int, vp, vp],
+            "qtn_contract_slices": [vp, u8p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, vp, f64p, vp],
+            "qtn_contract_batch": [P(vp), P(u8p), ctypes.c_int, ctypes.c_int, vp, f64p],
+            "qtn_plan_executor": [vp, P(ctypes.c_char_p)],
+            "qtn_plan_describe": [vp, ctypes.c_char_p, ctypes.c_size_t, P(ctypes.c_size_t)],
+            "qtn_plan_set_kernel_timing": [vp, ctypes.c_int],
+            "qtn_plan_kernel_ms": [vp, P(ctypes.c_float)],
+            "qtn_search_cuts": [vp, P(_PlanOpts), i32p, f64p, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int)],
+            "qtn_status_string": [ctypes.c_int],
+            "qtn_last_error": [],
+        }
+        for name, args in sig.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = ctypes.c_int
+        L.qtn_plan_opts_default.restype = None
+        L.qtn_network_destroy.restype = None
+        L.qtn_plan_destroy.restype = None
+        L.qtn_status_string.restype = ctypes.c_char_p
+        L.qtn_last_error.restype = ctypes.c_char_p
+        _lib = L
+        return L
+
+
+def _check(status: int):
+    if status != 0:
+        raise QTNError(status, lib().qtn_last_error().decode())
+
+
+def _ptr(a: np.ndarray, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def _stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+
+            if torch.cuda.is_available() and torch.cuda.is_initialized():
+                return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except Exception:
+            pass
+        return ctypes.c_void_p(0)
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+class Network:
+    """qtn_build_network: the ZZ-gate tensor network of a p-layer QAOA circuit."""
+
+    def __init__(self, n: int, edges, gamma, beta):
+        e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
+        g = np.ascontiguousarray(np.atleast_1d(np.asarray(gamma, dtype=np.float64)))
+        b = np.ascontiguousarray(np.atleast_1d(np.asarray(beta, dtype=np.float64)))
+        if g.shape != b.shape:
+            raise ValueError("gamma and beta need the same length p")
+        self.n, self.p = int(n), int(g.size)
+        h = ctypes.c_void_p()
+        _check(lib().qtn_build_network(self.n, self.p, _ptr(e, ctypes.c_int32), len(e), _ptr(g, ctypes.c_double),
+                                       _ptr(b, ctypes.c_double), ctypes.byref(h)))
+        self._h = h
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.qtn_network_destroy(self._h)
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def info(self):
+        nt, ni = ctypes.c_int(), ctypes.c_int()
+        _check(lib().qtn_network_info(self._h, ctypes.byref(nt), ctypes.byref(ni)))
+        return nt.value, ni.value
+
+    def index(self, i: int):
+        """(qubit, pos, tensor_a, tensor_b) of index i."""
+        q, p, a, b = ctypes.c_int(), ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().qtn_network_index(self._h, int(i), ctypes.byref(q), ctypes.byref(p), ctypes.byref(a),
+                                       ctypes.byref(b)))
+        return q.value, p.value, a.value, b.value
+
+
+def search_cuts(network: Network, k: int, search: str = "greedy", seed: int = 1, ga_T: int = 4, ga_N: int = 11):
+    """qtn_search_cuts: (cuts, fitness trace, fitness evaluations)."""
+    opts = _PlanOpts()
+    lib().qtn_plan_opts_default(ctypes.byref(opts))
+    opts.search, opts.k, opts.seed, opts.ga_T, opts.ga_N = SEARCHES[search], int(k), int(seed), int(ga_T), int(ga_N)
+    cuts = np.zeros(max(k, 1), dtype=np.int32)
+    trace = np.zeros(256)
+    tl, ev = ctypes.c_int(), ctypes.c_int()
+    _check(lib().qtn_search_cuts(network.handle, ctypes.byref(opts), _ptr(cuts, ctypes.c_int32),
+                                 _ptr(trace, ctypes.c_double), len(trace), ctypes.byref(tl), ctypes.byref(ev)))
+    return cuts[:k], trace[: tl.value], ev.value
+
+
+class Plan:
+    """qtn_plan: cut set + elimination order + compiled step program."""
+
+    def __init__(self, network: Network, cuts=None, k: int = 0, order=None, search: str = "greedy", seed: int = 1,
+                 ga_T: int = 4, ga_N: int = 11, max_slice_bytes: float = 0.0):
+        self.network = network
+        opts = _PlanOpts()
+        lib().qtn_plan_opts_default(ctypes.byref(opts))
+        opts.search = SEARCHES[search]
+        opts.k = int(k)
+        opts.seed = int(seed)
+        opts.ga_T = int(ga_T)
+        opts.ga_N = int(ga_N)
+        opts.max_slice_bytes = float(max_slice_bytes)
+        c = None if cuts is None else np.ascontiguousarray(np.asarray(cuts, dtype=np.int32))
+        o = None if order is None else np.ascontiguousarray(np.asarray(order, dtype=np.int32))
+        h = ctypes.c_void_p()
+        _check(lib().qtn_plan(network.handle, None if c is None else _ptr(c, ctypes.c_int32),
+                              0 if c is None else len(c), None if o is None else _ptr(o, ctypes.c_int32),
+                              0 if o is None else len(o), ctypes.byref(opts), ctypes.byref(h)))
+        self._h = h
+        self.n = network.n
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.qtn_plan_destroy(self._h)
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def cost(self) -> dict:
+        f, m, w, k = ctypes.c_double(), ctypes.c_double(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().qtn_plan_cost(self._h, ctypes.byref(f), ctypes.byref(m), ctypes.byref(w), ctypes.byref(k)))
+        macs = ctypes.c_double()
+        _check(lib().qtn_plan_macs_per_slice(self._h, ctypes.byref(macs)))
+        return dict(log2_flops=f.value, log2_peak_bytes=m.value, width=w.value, k=k.value, macs_per_slice=macs.value)
+
+    @property
+    def k(self) -> int:
+        return self.cost()["k"]
+
+    @property
+    def cuts(self) -> np.ndarray:
+        out = np.zeros(max(self.k, 1), dtype=np.int32)
+        _check(lib().qtn_plan_cuts(self._h, _ptr(out, ctypes.c_int32)))
+        return out[: self.k]
+
+    @property
+    def executor(self) -> str:
+        s = ctypes.c_char_p()
+        _check(lib().qtn_plan_executor(self._h, ctypes.byref(s)))
+        return s.value.decode()
+
+    def describe(self) -> dict:
+        need = ctypes.c_size_t()
+        _check(lib().qtn_plan_describe(self._h, None, 0, ctypes.byref(need)))
+        buf = ctypes.create_string_buffer(need.value)
+        _check(lib().qtn_plan_describe(self._h, buf, need.value, ctypes.byref(need)))
+        return json.loads(buf.value.decode())
+
+    def set_kernel_timing(self, on: bool = True):
+        _check(lib().qtn_plan_set_kernel_timing(self._h, int(bool(on))))
+
+    def kernel_ms(self) -> float:
+        """Executor kernel duration of the latest (synchronised) call."""
+        ms = ctypes.c_float()
+        _check(lib().qtn_plan_kernel_ms(self._h, ctypes.byref(ms)))
+        return float(ms.value)
+
+    def cut_names(self):
+        """The cuts as (qubit, pos) wire-segment names."""
+        return [self.network.index(int(c))[:2] for c in self.cuts]
+
+    def contract_amplitude(self, x, precision: str = "fp32", stream=None) -> complex:
+        xb = np.ascontiguousarray(np.asarray(x, dtype=np.uint8).reshape(-1))
+        if xb.size != self.n:
+            raise ValueError("x must have n entries")
+        out = np.zeros(2)
+        _check(lib().qtn_contract_amplitude(self._h, _ptr(xb, ctypes.c_uint8), PRECISIONS[precision],
+                                            _stream_handle(stream), _ptr(out, ctypes.c_double)))
+        return complex(out[0], out[1])
+
+    def contract_amplitudes_device(self, d_x, d_out, precision: str = "fp32", stream=None):
+        """d_x: CUDA uint8 tensor (nx, n); d_out: CUDA float64 tensor (nx, 2).
+        Asynchronous on `stream` (default: torch's current stream)."""
+        if not (d_x.is_cuda and d_out.is_cuda) or d_x.dtype.itemsize != 1 or d_out.element_size() != 8:
+            raise ValueError("d_x must be a CUDA uint8 tensor and d_out a CUDA float64 tensor")
+        nx = int(d_x.shape[0])
+        if d_x.numel() != nx * self.n or d_out.numel() != 2 * nx or not d_x.is_contiguous() or not d_out.is_contiguous():
+            raise ValueError("shapes must be (nx, n) and (nx, 2), contiguous")
+        _check(lib().qtn_contract_amplitudes_device(self._h, ctypes.c_void_p(d_x.data_ptr()), nx,
+                                                    PRECISIONS[precision], _stream_handle(stream),
+                                                    ctypes.c_void_p(d_out.data_ptr())))
+
+    def contract_slices(self, x, lo: int, hi: int, precision: str = "fp32", per_slice: bool = False, stream=None):
+        """Kahan sum (and compensation) of slices [lo, hi), unscaled; optionally
+        every slice's value (unscaled, as a complex128 numpy array)."""
+        xb = np.ascontiguousarray(np.asarray(x, dtype=np.uint8).reshape(-1))
+        out = np.zeros(4)
+        dev = None
+        if per_slice:
+            import torch
+
+            dev = torch.empty((max(hi - lo, 1), 2), dtype=torch.float64, device="cuda")
+        _check(lib().qtn_contract_slices(self._h, _ptr(xb, ctypes.c_uint8), int(lo), int(hi), PRECISIONS[precision],
+                                         _stream_handle(stream), _ptr(out, ctypes.c_double),
+                                         None if dev is None else ctypes.c_void_p(dev.data_ptr())))
+        total = complex(out[0], out[1])
+        comp = complex(out[2], out[3])
+        if per_slice:
+            v = dev[: hi - lo].cpu().numpy()
+            return total, comp, v[:, 0] + 1j * v[:, 1]
+        return total, comp
+
+
+def contract_batch(plans, xs, precision: str = "fp32", stream=None) -> np.ndarray:
+    """Amplitudes of independent (plan, x) jobs."""
+    n = len(plans)
+    arrs = [np.ascontiguousarray(np.asarray(x, dtype=np.uint8).reshape(-1)) for x in xs]
+    for p, a in zip(plans, arrs):
+        if a.size != p.n:
+            raise ValueError("every x must have its plan's n entries")
+    hp = (ctypes.c_void_p * n)(*[p.handle for p in plans])
+    xp = (ctypes.POINTER(ctypes.c_uint8) * n)(*[_ptr(a, ctypes.c_uint8) for a in arrs])
+    out = np.zeros(2 * max(n, 1))
+    _check(lib().qtn_contract_batch(hp, xp, n, PRECISIONS[precision], _stream_handle(stream),
+                                    _ptr(out, ctypes.c_double)))
+    return out[0:2 * n:2] + 1j * out[1:2 * n:2]

@@ -1,0 +1,219 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Tolerances (relative error |a - a*| / |a*| unless stated):
+  * complex128 path: 1e-10 (the FP64 form's bound).
+  * complex64 path: 1e-6 for amplitudes whose slice sum does not cancel
+    strongly; every comparison also bounds the absolute error by
+    2e-6 * sum_s |a_s| (FP32 unit roundoff 6e-8 times the depth of the merge
+    chain, ~30, applied to the cancellation-free magnitude).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2010_14962_gb300 import instances as I
+from paper_2010_14962_gb300 import qtn
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def rel(a, b):
+    return abs(a - b) / abs(b)
+
+
+def device_amplitudes(plan, xs, prec):
+    d_x = torch.from_numpy(np.ascontiguousarray(xs.astype(np.uint8))).cuda()
+    d_out = torch.zeros((xs.shape[0], 2), dtype=torch.float64, device="cuda")
+    plan.contract_amplitudes_device(d_x, d_out, prec)
+    torch.cuda.synchronize()
+    o = d_out.cpu().numpy()
+    return o[:, 0] + 1j * o[:, 1]
+
+
+@pytest.fixture(scope="module")
+def config16():
+    n, p, k = 16, 1, 2
+    inst = I.qaoa_instance(n, p, 1)
+    net = qtn.Network(n, inst.edges, inst.gamma, inst.beta)
+    plan = qtn.Plan(net, k=k)
+    sv = O.statevector(n, inst.edges, inst.gamma, inst.beta)
+    return inst, net, plan, sv
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
+def test_every_amplitude_n16(gpu, config16, prec, tol):
+    # All 2^16 amplitudes of the n = 16, p = 1, 2-cut workload against the
+    # state vector; and the total probability.
+    inst, net, plan, sv = config16
+    n = 16
+    xs = ((np.arange(1 << n)[:, None] >> np.arange(n)[None, :]) & 1).astype(np.uint8)
+    got = device_amplitudes(plan, xs, prec)
+    err = np.abs(got - sv)
+    scale = 2.0 ** (-n / 2)
+    big = np.abs(sv) > 1e-2 * scale
+    assert np.max(err[big] / np.abs(sv[big])) < tol
+    assert np.max(err) < tol * scale
+    assert abs(np.sum(np.abs(got) ** 2) - 1.0) < (1e-12 if prec == "fp64" else 1e-5)
+
+
+def test_host_and_device_entry_points_agree(gpu, config16):
+    inst, net, plan, sv = config16
+    for x in I.bitstrings(16, 3, 9):
+        a = plan.contract_amplitude(x, "fp64")
+        b = device_amplitudes(plan, x[None, :], "fp64")[0]
+        assert a == b
+        assert rel(a, sv[O.bits_to_int(x)]) < 1e-10
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+@pytest.mark.parametrize("n,p,k,seed", [(24, 1, 6, 2), (20, 2, 5, 4)])
+def test_per_slice_values(gpu, prec, n, p, k, seed):
+    # Every slice scalar (Sec. III.A, Eq. 2) against the oracle's, with the
+    # same cut edges and slice numbering.
+    inst = I.qaoa_instance(n, p, seed)
+    net = qtn.Network(n, inst.edges, inst.gamma, inst.beta)
+    plan = qtn.Plan(net, k=k)
+    x = I.bitstrings(n, 1, seed)[0]
+    ref = O.tn_amplitude(n, inst.edges, inst.gamma, inst.beta, x, cuts=plan.cut_names(), per_slice=True)
+    s, c, per = plan.contract_slices(x, 0, 1 << k, prec, per_slice=True)
+    scale = 2.0 ** (-n / 2)
+    per = per * scale
+    mag = np.max(np.abs(ref.per_slice))
+    tol = 1e-12 if prec == "fp64" else 2e-6
+    assert np.max(np.abs(per - ref.per_slice)) < tol * mag
+    assert abs((s - c) * scale - ref.value) < tol * np.sum(np.abs(ref.per_slice))
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_block_executor_n40_p2(gpu, prec):
+    # n = 40, p = 2 with 10 greedy cuts (1024 slices): tensors of rank > 5 run
+    # on the block executor.
+    n, p, k = 40, 2, 10
+    inst = I.qaoa_instance(n, p, 2)
+    net = qtn.Network(n, inst.edges, inst.gamma, inst.beta)
+    plan = qtn.Plan(net, k=k)
+    assert plan.executor == "block"
+    xs = I.bitstrings(n, 2, 2)
+    got = device_amplitudes(plan, xs, prec)
+    for x, g in zip(xs, got):
+        ref = O.tn_amplitude(n, inst.edges, inst.gamma, inst.beta, x, cuts=plan.cut_names()[:3], threads=4)
+        assert rel(g, ref.value) < (1e-10 if prec == "fp64" else 1e-5)
+
+
+@pytest.fixture(scope="module")
+def config80():
+    n, p, k = 80, 1, 16
+    inst = I.qaoa_instance(n, p, 3)
+    net = qtn.Network(n, inst.edges, inst.gamma, inst.beta)
+    plan = qtn.Plan(net, k=k)
+    xs = I.bitstrings(n, 8, 3)
+    refs = [O.tn_amplitude(n, inst.edges, inst.gamma, inst.beta, x, threads=4).value for x in xs]
+    return inst, plan, xs, np.array(refs)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
+def test_n80_eight_bitstrings(gpu, config80, prec, tol):
+    # The 80-qubit, 16-cut (65536-slice) workload in the launch configuration
+    # the benchmark times (8 bit strings, one graph).
+    inst, plan, xs, refs = config80
+    got = device_amplitudes(plan, xs, prec)
+    errs = np.abs(got - refs) / np.abs(refs)
+    print(prec, "max rel err", errs.max())
+    assert errs.max() < tol
+
+
+def test_n80_sampled_slices(gpu, config80):
+    inst, plan, xs, refs = config80
+    x = xs[0]
+    n = 80
+    _, _, per = plan.contract_slices(x, 0, 1 << 16, "fp64", per_slice=True)
+    scale = 2.0 ** (-n / 2)
+    for s in (0, 1, 31, 32, 4097, 40000, 65535):
+        ref = O.tn_amplitude(n, inst.edges, inst.gamma, inst.beta, x, cuts=plan.cut_names(), slices=(s, s + 1))
+        assert abs(per[s] * scale - ref.value) <= 1e-12 * abs(ref.value) + 1e-300
+
+
+def test_slice_ranges_add_up(gpu, config80):
+    # Sec. V: a lost range of slices can be recomputed alone; ranges add up.
+    inst, plan, xs, refs = config80
+    x = xs[1]
+    full, cf = plan.contract_slices(x, 0, 1 << 16, "fp64")
+    parts = [plan.contract_slices(x, lo, hi, "fp64") for lo, hi in [(0, 1000), (1000, 1001), (1001, 65536)]]
+    tot = sum(s - c for s, c in parts)
+    assert abs(tot - (full - cf)) < 1e-13 * abs(full)
+    empty = plan.contract_slices(x, 5, 5, "fp64")
+    assert empty == (0j, 0j)
+
+
+@pytest.mark.parametrize("which", ["gamma0", "beta0", "beta_pi2"])
+def test_closed_forms_n120(gpu, which):
+    n, p, k = 120, 1, 12
+    inst = I.qaoa_instance(n, p, 5)
+    g, b = inst.gamma.copy(), inst.beta.copy()
+    if which == "gamma0":
+        g[:] = 0
+    elif which == "beta0":
+        b[:] = 0
+    else:
+        b[:] = math.pi / 2
+    net = qtn.Network(n, inst.edges, g, b)
+    plan = qtn.Plan(net, k=k)
+    x = I.bitstrings(n, 1, 5)[0]
+    s = 1 - 2 * x.astype(np.int64)
+    C = int(sum(s[a] * s[bb] for a, bb in inst.edges))
+    h = 2.0 ** (-n / 2)
+    want = {"gamma0": np.exp(-1j * n * b[0]) * h, "beta0": h * np.exp(-1j * g[0] * C),
+            "beta_pi2": (-1j) ** n * h * np.exp(-1j * g[0] * C)}[which]
+    assert rel(plan.contract_amplitude(x, "fp64"), want) < 1e-10
+    assert rel(plan.contract_amplitude(x, "fp32"), want) < 1e-5
+
+
+def test_edge_cases(gpu):
+    # a single gate (no merge at all), no cuts, a disconnected graph, an
+    # unsupported precision.
+    e = np.array([[0, 1]], np.int32)
+    net = qtn.Network(2, e, [0.37], [1.1])
+    sv = O.statevector(2, e, [0.37], [1.1])
+    plan = qtn.Plan(net, cuts=[])
+    for xi in range(4):
+        x = [(xi >> q) & 1 for q in range(2)]
+        assert rel(plan.contract_amplitude(x, "fp64"), sv[xi]) < 1e-13
+    e2 = np.array([[0, 1], [1, 2], [0, 2], [3, 4], [4, 5], [3, 5]], np.int32)  # two triangles
+    net2 = qtn.Network(6, e2, [0.3, 0.9], [0.4, 1.7])
+    sv2 = O.statevector(6, e2, [0.3, 0.9], [0.4, 1.7])
+    for k in (0, 3):
+        plan2 = qtn.Plan(net2, k=k)
+        for xi in (0, 17, 63):
+            x = [(xi >> q) & 1 for q in range(6)]
+            assert rel(plan2.contract_amplitude(x, "fp64"), sv2[xi]) < 1e-12
+    with pytest.raises(qtn.QTNError) as ei:
+        plan.contract_amplitude([0, 1], "bf16x6")
+    assert ei.value.status == 6
+    with pytest.raises(qtn.QTNError):
+        plan.contract_amplitude([0, 2], "fp64")
+
+
+def test_deterministic(gpu, config80):
+    inst, plan, xs, refs = config80
+    a = device_amplitudes(plan, xs, "fp32")
+    b = device_amplitudes(plan, xs, "fp32")
+    assert np.array_equal(a, b)
+
+
+def test_batch_of_plans(gpu):
+    jobs = []
+    for j, (n, p, k) in enumerate([(20, 1, 4), (24, 2, 6), (20, 1, 4)]):
+        inst = I.qaoa_instance(n, p, 50 + j)
+        net = qtn.Network(n, inst.edges, inst.gamma, inst.beta)
+        jobs.append((inst, qtn.Plan(net, k=k)))
+    plans = [jobs[0][1], jobs[1][1], jobs[2][1], jobs[0][1]]
+    insts = [jobs[0][0], jobs[1][0], jobs[2][0], jobs[0][0]]
+    xs = [I.bitstrings(pl.n, 1, 60 + i)[0] for i, pl in enumerate(plans)]
+    got = qtn.contract_batch(plans, xs, "fp64")
+    for g, inst, pl, x in zip(got, insts, plans, xs):
+        ref = O.tn_amplitude(inst.n, inst.edges, inst.gamma, inst.beta, x).value
+        assert rel(g, ref) < 1e-10

@@ -1,0 +1,236 @@
+"""Host-side logic of the library (no GPU needed): the C ABI loads and
+exports every declared symbol, the network build, the planner (tree
+decomposition conditions of Sec. II.B, exact cost counter), the cut searches
+(greedy; Algorithm 1), and the compiled step programs, emulated on the CPU
+against the oracle slice by slice (Sec. III.A, Eq. 2)."""
+import ctypes
+import itertools
+
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_2010_14962_gb300 import instances as I
+from paper_2010_14962_gb300 import qtn
+
+from . import program_emulator as E
+
+
+def test_library_exports_every_declared_symbol():
+    L = ctypes.CDLL(qtn.LIB_PATH)
+    names = qtn.declared_symbols()
+    assert "qtn_contract_amplitude" in names and "qtn_plan" in names
+    for name in names:
+        assert hasattr(L, name), name
+
+
+def test_network_counts_and_names():
+    for n, p in [(16, 1), (40, 2), (80, 1)]:
+        inst = I.qaoa_instance(n, p, 3)
+        net = qtn.Network(n, inst.edges, inst.gamma, inst.beta)
+        nt, ni = net.info()
+        assert nt == p * len(inst.edges) == p * 3 * n // 2
+        assert ni == n * (3 * p - 1)
+        zz = O.zz_per_qubit(n, inst.edges, p)
+        seen = set()
+        for i in range(ni):
+            q, pos, ta, tb = net.index(i)
+            assert 0 <= pos < zz[q] - 1 and ta < tb
+            seen.add((q, pos))
+        assert len(seen) == ni
+
+
+@pytest.mark.parametrize("edges", [[[0, 0]], [[0, 1], [1, 0]], [[0, 5]], [[0, 1]]])
+def test_network_rejects_bad_graphs(edges):
+    n = 3 if edges != [[0, 1]] else 3  # the last graph leaves qubit 2 without a gate
+    with pytest.raises(qtn.QTNError) as ei:
+        qtn.Network(n, edges, [0.1], [0.2])
+    assert ei.value.status == 1
+
+
+def test_plan_rejects_bad_cuts_and_orders():
+    inst = I.qaoa_instance(12, 1, 1)
+    net = qtn.Network(12, inst.edges, inst.gamma, inst.beta)
+    _, ni = net.info()
+    for cuts in ([0, 0], [ni], [-1]):
+        with pytest.raises(qtn.QTNError):
+            qtn.Plan(net, cuts=cuts)
+    with pytest.raises(qtn.QTNError):
+        qtn.Plan(net, cuts=[0], order=list(range(ni)))  # contains the cut index
+    with pytest.raises(qtn.QTNError):
+        qtn.Plan(net, cuts=[], order=list(range(ni - 1)))  # not every index
+
+
+def bags(desc):
+    T = desc["tensors"]
+    return [sorted(set(T[a]) | set(T[b])) for a, b, _ in desc["merges"]]
+
+
+@pytest.mark.parametrize("n,p,k", [(16, 1, 2), (24, 2, 4), (40, 1, 6)])
+def test_plan_is_a_tree_decomposition(n, p, k):
+    # Sec. II.B: the bags {A u B} of the merges, arranged as the contraction
+    # tree, satisfy conditions (1)-(3) for the graph whose vertices are the
+    # non-cut indices and whose edges join indices of a common gate tensor.
+    inst = I.qaoa_instance(n, p, 5)
+    net = qtn.Network(n, inst.edges, inst.gamma, inst.beta)
+    plan = qtn.Plan(net, k=k)
+    d = plan.describe()
+    B = bags(d)
+    T = d["tensors"]
+    L = d["n_leaves"]
+    cuts = set(d["cuts"])
+    _, ni = net.info()
+    live = [i for i in range(ni) if i not in cuts]
+    # (1) every vertex is in a bag
+    assert set(live) <= set(itertools.chain.from_iterable(B))
+    # (2) every edge is inside a bag: indices of one leaf
+    for t in range(L):
+        pairs = itertools.combinations(T[t], 2)
+        for u, v in pairs:
+            assert any(u in b and v in b for b in B)
+    # (3) the bags holding an index are connected in the contraction tree
+    parent = {}
+    prod = {c: j for j, (_, _, c) in enumerate(d["merges"])}
+    for j, (a, b, c) in enumerate(d["merges"]):
+        for child in (a, b):
+            if child in prod:
+                parent[prod[child]] = j
+    for u in live:
+        holders = [j for j, b in enumerate(B) if u in b]
+        tops = [j for j in holders if parent.get(j) not in holders]
+        assert len(tops) == 1, (u, holders)
+    # width and exact MAC count agree with the counter
+    assert max(len(b) for b in B) == plan.cost()["width"]
+    assert sum(2 ** len(b) for b in B) == plan.cost()["macs_per_slice"]
+
+
+def treewidth_dp(vertices, adj):
+    """Exact treewidth by dynamic programming over vertex subsets."""
+    vs = list(vertices)
+    idx = {v: i for i, v in enumerate(vs)}
+    N = len(vs)
+    nbr = [0] * N
+    for v in vs:
+        for u in adj[v]:
+            nbr[idx[v]] |= 1 << idx[u]
+
+    def q_size(S, v):
+        # vertices outside S u {v} reachable from v through S
+        seen = 1 << v
+        stack = [v]
+        out = 0
+        while stack:
+            w = stack.pop()
+            m = nbr[w] & ~seen
+            while m:
+                b = m & -m
+                m ^= b
+                u = b.bit_length() - 1
+                seen |= b
+                if S >> u & 1:
+                    stack.append(u)
+                else:
+                    out += 1
+        return out
+
+    TW = {0: -1}
+    for size in range(1, N + 1):
+        for combo in itertools.combinations(range(N), size):
+            S = sum(1 << c for c in combo)
+            best = N
+            for v in combo:
+                rest = S & ~(1 << v)
+                best = min(best, max(TW[rest], q_size(rest, v)))
+            TW[S] = best
+    return TW[(1 << N) - 1]
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_min_fill_width_bounds_exact_treewidth(seed):
+    n = 6
+    inst = I.qaoa_instance(n, 1, seed)
+    net = qtn.Network(n, inst.edges, inst.gamma, inst.beta)
+    plan = qtn.Plan(net, cuts=[])
+    d = plan.describe()
+    _, ni = net.info()
+    adj = {i: set() for i in range(ni)}
+    for t in d["tensors"][: d["n_leaves"]]:
+        for u, v in itertools.combinations(t, 2):
+            adj[u].add(v)
+            adj[v].add(u)
+    tw = treewidth_dp(range(ni), adj)
+    assert plan.cost()["width"] - 1 >= tw
+
+
+def test_greedy_cuts_lower_width():
+    n = 40
+    inst = I.qaoa_instance(n, 1, 7)
+    net = qtn.Network(n, inst.edges, inst.gamma, inst.beta)
+    cuts, trace, _ = qtn.search_cuts(net, 8, "greedy")
+    assert len(set(cuts.tolist())) == 8
+    widths = [int(t) for t in trace]
+    assert widths[-1] < qtn.Plan(net, cuts=[]).cost()["width"]
+    assert all(b <= a for a, b in zip(widths, widths[1:]))
+
+
+def test_genetic_search_is_deterministic_and_elitist():
+    # Algorithm 1: the best individual is never crossed or mutated, so the
+    # best fitness per generation never rises; T = 4 runs the body 5 times
+    # (t = 0..4) plus the final evaluation of Step 5.
+    n = 40
+    inst = I.qaoa_instance(n, 1, 8)
+    net = qtn.Network(n, inst.edges, inst.gamma, inst.beta)
+    c1, tr1, ev1 = qtn.search_cuts(net, 6, "ga", seed=3)
+    c2, tr2, ev2 = qtn.search_cuts(net, 6, "ga", seed=3)
+    assert list(c1) == list(c2) and np.array_equal(tr1, tr2)
+    assert len(tr1) == 6 and ev1 == 6 * 11
+    assert all(b <= a + 1e-12 for a, b in zip(tr1, tr1[1:]))
+    greedy, gtr, _ = qtn.search_cuts(net, 6, "greedy")
+    assert tr1[-1] <= gtr[-1] + 1e-12  # seeded with the greedy set
+
+
+def oracle_cuts(plan):
+    return plan.cut_names()
+
+
+@pytest.mark.parametrize("which", ["lane", "block"])
+@pytest.mark.parametrize("n,p,k,seed", [(12, 1, 3, 1), (16, 1, 2, 1), (14, 2, 4, 6)])
+def test_emulated_program_matches_oracle_per_slice(which, n, p, k, seed):
+    inst = I.qaoa_instance(n, p, seed)
+    net = qtn.Network(n, inst.edges, inst.gamma, inst.beta)
+    plan = qtn.Plan(net, k=k)
+    d = plan.describe()
+    x = I.bitstrings(n, 1, seed)[0]
+    ref = O.tn_amplitude(n, inst.edges, inst.gamma, inst.beta, x, cuts=oracle_cuts(plan), per_slice=True)
+    lt = E.leaf_table(d, which, inst.gamma, inst.beta, x)
+    scale = 2.0 ** (-n / 2)
+    got = np.array([E.run_slice(d, which, lt, s) for s in range(1 << k)]) * scale
+    assert np.max(np.abs(got - ref.per_slice)) < 1e-13 * max(1.0, np.max(np.abs(ref.per_slice)))
+    assert abs(got.sum() - ref.value) < 1e-13
+
+
+def test_emulated_program_n80_sampled_slices():
+    n, p = 80, 1
+    inst = I.qaoa_instance(n, p, 3)
+    net = qtn.Network(n, inst.edges, inst.gamma, inst.beta)
+    plan = qtn.Plan(net, k=16)
+    d = plan.describe()
+    x = I.bitstrings(n, 1, 3)[0]
+    lt = E.leaf_table(d, d["executor"], inst.gamma, inst.beta, x)
+    scale = 2.0 ** (-n / 2)
+    for s in (0, 1, 12345, 65535):
+        ref = O.tn_amplitude(n, inst.edges, inst.gamma, inst.beta, x, cuts=plan.cut_names(), slices=(s, s + 1))
+        got = E.run_slice(d, d["executor"], lt, s) * scale
+        assert abs(got - ref.value) < 1e-12 * abs(ref.value) + 1e-30
+
+
+def test_plan_cost_matches_counter_and_cap():
+    inst = I.qaoa_instance(40, 2, 2)
+    net = qtn.Network(40, inst.edges, inst.gamma, inst.beta)
+    plan = qtn.Plan(net, k=10)
+    c = plan.cost()
+    assert c["k"] == 10
+    assert abs(c["log2_flops"] - (10 + np.log2(8 * c["macs_per_slice"]))) < 1e-9
+    with pytest.raises(qtn.QTNError) as ei:
+        qtn.Plan(net, cuts=plan.cuts, max_slice_bytes=1024)
+    assert ei.value.status == 3
