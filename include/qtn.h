@@ -175,11 +175,11 @@ qtn_status qtn_contract_batch(const qtn_plan_t* const* plans, const uint8_t* con
  * plans with every tensor rank <= 5; "block": one slice per thread block). */
 qtn_status qtn_plan_executor(const qtn_plan_t* plan, const char** name);
 
-/* Kernel timing for measurement: when on, contraction calls record CUDA
- * events on the launching stream just before and after the executor kernel
- * (inside the replayed graph as well); qtn_plan_kernel_ms returns the
- * executor's duration in the most recent call once that call's stream has
- * been synchronised.  Switching it changes the recorded graphs. */
+/* Kernel timing for measurement: when on, qtn_contract_amplitudes_device
+ * launches its three kernels directly (no graph replay) and records CUDA
+ * events on the launching stream just before and after the executor kernel;
+ * qtn_plan_kernel_ms returns the executor's duration in the most recent such
+ * call once its stream has been synchronised. */
 qtn_status qtn_plan_set_kernel_timing(const qtn_plan_t* plan, int on);
 qtn_status qtn_plan_kernel_ms(const qtn_plan_t* plan, float* ms);
 

@@ -219,14 +219,19 @@ struct qtn_plan {
     if (st != QTN_OK) return st;
     st = ensure_workspace(nx, sh.blocks_per_x);
     if (st != QTN_OK) return st;
+    if (timing) {  // direct launches with events around the executor
+      cudaError_t le = launch_contraction(dprog, prec == QTN_FP64, d_x, nx, 0, S, buffers(), sh, scale(), d_out,
+                                          nullptr, nullptr, stream, ev0, ev1);
+      if (le != cudaSuccess) return cuda_fail(le, "launch_contraction");
+      return QTN_OK;
+    }
     GraphKey key{d_x, d_out, nx, (int)prec};
     auto it = graphs.find(key);
     if (it == graphs.end()) {
       cudaGraph_t g;
       QTN_CUDA(cudaStreamBeginCapture(capture_stream, cudaStreamCaptureModeThreadLocal));
       cudaError_t le = launch_contraction(dprog, prec == QTN_FP64, d_x, nx, 0, S, buffers(), sh, scale(), d_out,
-                                          nullptr, nullptr, capture_stream, timing ? ev0 : nullptr,
-                                          timing ? ev1 : nullptr);
+                                          nullptr, nullptr, capture_stream);
       cudaError_t ce = cudaStreamEndCapture(capture_stream, &g);
       if (le != cudaSuccess) return cuda_fail(le, "launch_contraction (capture)");
       if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
@@ -393,11 +398,7 @@ qtn_status qtn_plan_set_kernel_timing(const qtn_plan_t* cplan, int on) {
     QTN_CUDA(cudaEventCreate(&plan->ev0));
     QTN_CUDA(cudaEventCreate(&plan->ev1));
   }
-  if ((on != 0) != plan->timing) {
-    for (auto& g : plan->graphs) cudaGraphExecDestroy(g.second);
-    plan->graphs.clear();
-    plan->timing = on != 0;
-  }
+  plan->timing = on != 0;
   return QTN_OK;
 }
 

@@ -167,6 +167,7 @@ std::string compile_program(const Network& net, const Plan& plan_in, bool c_reus
     const Merge& mg = plan.merges[j];
     const Canon& c = canon[j];
     DevStep st{};
+    int64_t a_block = -1;
     st.ma = (uint8_t)c.m.size();
     st.nb = (uint8_t)c.n.size();
     st.kb = (uint8_t)c.k.size();
@@ -176,7 +177,7 @@ std::string compile_program(const Network& net, const Plan& plan_in, bool c_reus
       st.a = (uint16_t)mg.a;
     } else {
       st.a = where[mg.a];
-      to_release.push_back(where[mg.a]);
+      a_block = (int64_t)where[mg.a];
     }
     if (is_leaf(mg.b)) {
       st.flags |= STEP_B_LEAF;
@@ -189,9 +190,11 @@ std::string compile_program(const Network& net, const Plan& plan_in, bool c_reus
     pg.width = std::max(pg.width, (int)(c.m.size() + c.n.size() + c.k.size()));
     pg.max_rank = std::max(pg.max_rank, rc);
     pg.macs_per_slice += std::ldexp(1.0, (int)(c.m.size() + c.n.size() + c.k.size()));
-    if (c_reuses_operands) {
-      for (uint32_t r : to_release) arena.release(r);
-      to_release.clear();
+    // A is read completely before the first store of C; B is streamed while
+    // C is written, so only A's block may be reused by C.
+    if (a_block >= 0) {
+      if (c_reuses_operands) arena.release((uint32_t)a_block);
+      else to_release.push_back((uint32_t)a_block);
     }
     if (mg.c == root) {
       st.flags |= STEP_ROOT;
@@ -211,10 +214,8 @@ std::string compile_program(const Network& net, const Plan& plan_in, bool c_reus
         st.w[b] = (uint16_t)(1u << (it - lay.begin()));
       }
     }
-    if (!c_reuses_operands) {
-      for (uint32_t r : to_release) arena.release(r);
-      to_release.clear();
-    }
+    for (uint32_t r : to_release) arena.release(r);
+    to_release.clear();
     pg.steps.push_back(st);
   }
   pg.arena_elems = std::max<uint32_t>(arena.high, 1);

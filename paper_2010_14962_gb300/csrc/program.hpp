@@ -60,7 +60,7 @@ struct Program {
   std::vector<DevStep> steps;
   uint32_t leaf_elems = 0;           // elements in one leaf table
   uint32_t arena_elems = 0;          // per-slice arena (elements)
-  bool c_reuses_operands = false;    // arena lets C overlap A and B
+  bool c_reuses_operands = false;    // arena lets C overlap A (never B)
   int width = 0;                     // max ma + nb + kb
   int max_rank = 0;                  // max tensor rank in the program
   double macs_per_slice = 0;         // sum 2^(ma+nb+kb)
@@ -72,9 +72,9 @@ struct Program {
 };
 
 // Lowers `plan` (merges over `net`) to a program.  With `c_reuses_operands`
-// the arena lets a merge's result overwrite its operands (for executors that
-// read both operands completely before the first store).  Returns "" or an
-// error.
+// the arena lets a merge's result overwrite its A operand (for executors that
+// read A completely before the first store of C; B may still be read while C
+// is written).  Returns "" or an error.
 std::string compile_program(const Network& net, const Plan& plan, bool c_reuses_operands,
                             Program* out);
 

@@ -74,18 +74,27 @@ def run_slice(desc, which, lt, s):
 
     for st in pg["steps"]:
         ma, nb, kb = st["ma"], st["nb"], st["kb"]
-        A = operand(st["flags"] & 1, st["a"], 1 << (ma + kb))
-        B = operand(st["flags"] & 2, st["b"], 1 << (kb + nb))
-        Am = A.reshape(1 << kb, 1 << ma).T      # A[m + (k << ma)] -> Am[m, k]
-        Bm = B.reshape(1 << nb, 1 << kb).T      # B[k + (n << kb)] -> Bm[k, n]
-        Cm = Am @ Bm                             # C[m, n]
-        if st["flags"] & 4:
-            res = Cm[0, 0]
-            continue
         rc = ma + nb
+        # Same read/write order as the lane executor: A is read whole, then
+        # for each column n the k entries of B are read and the column of C
+        # is stored (so a store that clobbers unread B data shows up here).
+        A = operand(st["flags"] & 1, st["a"], 1 << (ma + kb))
+        Am = A.reshape(1 << kb, 1 << ma).T      # A[m + (k << ma)] -> Am[m, k]
         for n in range(1 << nb):
+            if st["flags"] & 2:
+                L = leaves[st["b"]]
+                off = L["base"]
+                for j, cb in enumerate(L["cut_bit"]):
+                    off += ((s >> cb) & 1) << (L["rank_nc"] + j)
+                col = lt[off + (n << kb): off + ((n + 1) << kb)].copy()
+            else:
+                col = arena[st["b"] + (n << kb): st["b"] + ((n + 1) << kb)].copy()
+            Ccol = Am @ col                      # C[m, n] for this n
+            if st["flags"] & 4:
+                res = Ccol[0]
+                continue
             for m in range(1 << ma):
                 o = m + (n << ma)
                 pos = sum(st["w"][j] for j in range(rc) if (o >> j) & 1)
-                arena[st["c"] + pos] = Cm[m, n]
+                arena[st["c"] + pos] = Ccol[m]
     return res

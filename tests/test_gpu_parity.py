@@ -2,10 +2,15 @@
 
 Tolerances (relative error |a - a*| / |a*| unless stated):
   * complex128 path: 1e-10 (the FP64 form's bound).
-  * complex64 path: 1e-6 for amplitudes whose slice sum does not cancel
-    strongly; every comparison also bounds the absolute error by
-    2e-6 * sum_s |a_s| (FP32 unit roundoff 6e-8 times the depth of the merge
-    chain, ~30, applied to the cancellation-free magnitude).
+  * complex64 path: the slice value is multilinear in the gate tensors, so
+    to first order each rounding to FP32 (u = 2^-24) -- of a gate-tensor
+    entry or of a merge's output -- perturbs it by at most u relative.  All
+    gates share the same rounded cos/sin values, so these errors add
+    coherently: per slice |da_s| <= 2 * G * u * |a_s| with G = #gates
+    (leaves and merges).  The slices of Eq. 2 partly cancel, so the bound on
+    the amplitude is absolute: |a - a*| <= 2 * G * u * sum_s |a_s|, with
+    sum_s |a_s| from the oracle's per-slice values.  Where that sum is not
+    computed, the relative bound stated at the test is used.
 """
 import math
 
@@ -21,8 +26,15 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
+U32 = 2.0 ** -24
+
+
 def rel(a, b):
     return abs(a - b) / abs(b)
+
+
+def fp32_bound(n_gates, per_slice):
+    return 2 * n_gates * U32 * np.sum(np.abs(per_slice))
 
 
 def device_amplitudes(plan, xs, prec):
@@ -82,9 +94,13 @@ def test_per_slice_values(gpu, prec, n, p, k, seed):
     s, c, per = plan.contract_slices(x, 0, 1 << k, prec, per_slice=True)
     scale = 2.0 ** (-n / 2)
     per = per * scale
-    mag = np.max(np.abs(ref.per_slice))
-    tol = 1e-12 if prec == "fp64" else 2e-6
-    assert np.max(np.abs(per - ref.per_slice)) < tol * mag
+    if prec == "fp64":
+        tol = 1e-12
+    else:
+        tol = 2 * p * len(inst.edges) * U32
+    zero = ref.per_slice == 0  # structurally zero slices (a diagonal gate with both wire legs cut)
+    assert np.all(per[zero] == 0)
+    assert np.max(np.abs(per[~zero] - ref.per_slice[~zero]) / np.abs(ref.per_slice[~zero])) < tol
     assert abs((s - c) * scale - ref.value) < tol * np.sum(np.abs(ref.per_slice))
 
 
@@ -115,15 +131,27 @@ def config80():
     return inst, plan, xs, np.array(refs)
 
 
-@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 1e-5)])
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32", 2e-5)])
 def test_n80_eight_bitstrings(gpu, config80, prec, tol):
     # The 80-qubit, 16-cut (65536-slice) workload in the launch configuration
-    # the benchmark times (8 bit strings, one graph).
+    # the benchmark times (8 bit strings, one graph).  complex64: relative
+    # bound 2e-5 (see the module docstring; test_n80_fp32_error_bound checks
+    # the absolute bound on one bit string).
     inst, plan, xs, refs = config80
     got = device_amplitudes(plan, xs, prec)
     errs = np.abs(got - refs) / np.abs(refs)
     print(prec, "max rel err", errs.max())
     assert errs.max() < tol
+
+
+def test_n80_fp32_error_bound(gpu, config80):
+    inst, plan, xs, refs = config80
+    x = xs[0]
+    ref = O.tn_amplitude(80, inst.edges, inst.gamma, inst.beta, x, cuts=plan.cut_names(), per_slice=True, threads=16)
+    got = device_amplitudes(plan, x[None, :], "fp32")[0]
+    l1 = np.sum(np.abs(ref.per_slice))
+    print("n80 cancellation ratio", l1 / abs(ref.value), "fp32 abs err / l1", abs(got - ref.value) / l1)
+    assert abs(got - ref.value) <= fp32_bound(len(inst.edges), ref.per_slice)
 
 
 def test_n80_sampled_slices(gpu, config80):
@@ -169,7 +197,9 @@ def test_closed_forms_n120(gpu, which):
     want = {"gamma0": np.exp(-1j * n * b[0]) * h, "beta0": h * np.exp(-1j * g[0] * C),
             "beta_pi2": (-1j) ** n * h * np.exp(-1j * g[0] * C)}[which]
     assert rel(plan.contract_amplitude(x, "fp64"), want) < 1e-10
-    assert rel(plan.contract_amplitude(x, "fp32"), want) < 1e-5
+    ref = O.tn_amplitude(n, inst.edges, g, b, x, cuts=plan.cut_names(), per_slice=True, threads=16)
+    assert rel(ref.value, want) < 1e-12
+    assert abs(plan.contract_amplitude(x, "fp32") - want) <= fp32_bound(len(inst.edges), ref.per_slice)
 
 
 def test_edge_cases(gpu):
