@@ -152,6 +152,28 @@ qtn_status qtn_contract_amplitude(const qtn_plan_t* plan, const uint8_t* x, qtn_
 qtn_status qtn_contract_amplitudes_device(const qtn_plan_t* plan, const uint8_t* d_x, int nx,
                                           qtn_precision prec, cudaStream_t stream, double* d_out);
 
+/* Allocation-free variant of qtn_contract_amplitudes_device.  The paper has
+ * no counterpart: this entry point exists for callers that cannot let a
+ * library call cudaMalloc -- applications whose framework already holds the
+ * device memory in its own pool, or code running where allocating is not
+ * allowed or would stall.  Same arguments and results as
+ * qtn_contract_amplitudes_device (FP64 and FP32 precisions).
+ *   Memory: a fixed scratch array of 64 MiB inside the library, which every
+ *     GPU that loads the library holds until the process exits.  The plan's
+ *     program, the gate tensors of the nx bit strings and the per-block
+ *     partial sums must fit in it; larger requests fail with
+ *     QTN_ERR_INVALID_ARG (call again with fewer bit strings).  No call makes
+ *     a device allocation or frees device memory.
+ *   Set-up: the first call on each device looks up the array's device
+ *     address with that device current; make that first call before any
+ *     stream capture.
+ *   Sharing: all calls use the same array, so calls that overlap on the GPU
+ *     (on different streams, or from racing host threads) corrupt each
+ *     other; issue them on one stream.
+ *   Launches its kernels directly on `stream` (no graph is recorded). */
+qtn_status qtn_contract_amplitudes_noalloc(const qtn_plan_t* plan, const uint8_t* d_x, int nx,
+                                           qtn_precision prec, cudaStream_t stream, double* d_out);
+
 /* Slices [slice_lo, slice_hi) of one amplitude, e.g. to recompute the slices
  * of a lost worker (Sec. V: fault tolerance at the level of subgraphs).
  *   x         : host, n bytes.

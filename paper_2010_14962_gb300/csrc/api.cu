@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "../../include/qtn.h"
+#include "internal.hpp"
 #include "kernels.cuh"
 #include "network.hpp"
 #include "plan.hpp"
@@ -389,6 +390,32 @@ qtn_status qtn_plan(const qtn_network_t* net, const int32_t* cuts, int k, const 
 }
 
 void qtn_plan_destroy(qtn_plan_t* plan) { delete plan; }
+
+}  // extern "C"
+
+namespace qtn {
+namespace internal {
+
+bool plan_view(const qtn_plan_t* cplan, PlanView* view) {
+  if (!cplan || !view) return false;
+  qtn_plan_t* plan = const_cast<qtn_plan_t*>(cplan);
+  view->program = &plan->program();
+  view->lane = plan->exec == Executor::Lane;
+  view->n = plan->net.n;
+  view->k = (int)plan->plan.cuts.size();
+  view->gamma = plan->net.gamma.data();
+  view->beta = plan->net.beta.data();
+  view->p = plan->net.p;
+  view->mu = &plan->mu;
+  return true;
+}
+
+qtn_status set_error(qtn_status s, const std::string& msg) { return fail(s, msg); }
+
+}  // namespace internal
+}  // namespace qtn
+
+extern "C" {
 
 qtn_status qtn_plan_set_kernel_timing(const qtn_plan_t* cplan, int on) {
   qtn_plan_t* plan = const_cast<qtn_plan_t*>(cplan);

@@ -72,6 +72,7 @@ def lib():
             "qtn_plan_macs_per_slice": [vp, f64p],
             "qtn_contract_amplitude": [vp, u8p, ctypes.c_int, vp, f64p],
             "qtn_contract_amplitudes_device": [vp, vp, ctypes.c_int, ctypes.c_int, vp, vp],
+            "qtn_contract_amplitudes_noalloc": [vp, vp, ctypes.c_int, ctypes.c_int, vp, vp],
             "qtn_contract_slices": [vp, u8p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, vp, f64p, vp],
             "qtn_contract_batch": [P(vp), P(u8p), ctypes.c_int, ctypes.c_int, vp, f64p],
             "qtn_plan_executor": [vp, P(ctypes.c_char_p)],
@@ -264,6 +265,18 @@ class Plan:
         _check(lib().qtn_contract_amplitudes_device(self._h, ctypes.c_void_p(d_x.data_ptr()), nx,
                                                     PRECISIONS[precision], _stream_handle(stream),
                                                     ctypes.c_void_p(d_out.data_ptr())))
+
+    def contract_amplitudes_noalloc(self, d_x, d_out, precision: str = "fp32", stream=None):
+        """Like contract_amplitudes_device, but the library allocates no device
+        memory (a fixed in-library scratch array; see include/qtn.h)."""
+        if not (d_x.is_cuda and d_out.is_cuda) or d_x.dtype.itemsize != 1 or d_out.element_size() != 8:
+            raise ValueError("d_x must be a CUDA uint8 tensor and d_out a CUDA float64 tensor")
+        nx = int(d_x.shape[0])
+        if d_x.numel() != nx * self.n or d_out.numel() != 2 * nx or not d_x.is_contiguous() or not d_out.is_contiguous():
+            raise ValueError("shapes must be (nx, n) and (nx, 2), contiguous")
+        _check(lib().qtn_contract_amplitudes_noalloc(self._h, ctypes.c_void_p(d_x.data_ptr()), nx,
+                                                     PRECISIONS[precision], _stream_handle(stream),
+                                                     ctypes.c_void_p(d_out.data_ptr())))
 
     def contract_slices(self, x, lo: int, hi: int, precision: str = "fp32", per_slice: bool = False, stream=None):
         """Kahan sum (and compensation) of slices [lo, hi), unscaled; optionally
