@@ -165,6 +165,15 @@ def run_ours(args, rank, world, local_rank):
         flush.zero_()
     torch.cuda.synchronize()
 
+    # The executor the autotuner picked (first call above) and the work it
+    # executes per amplitude: 2^(outer classes) items x MACs per item.
+    desc = plan.describe()
+    prec_id = qtn.PRECISIONS[args.precision]
+    tuned = [t for t in desc["tuned"] if t["prec"] == prec_id and t["nx"] == nx][0]
+    prog = desc["programs"][tuned["executor"]]
+    exec_macs_per_amp = (2 ** len(prog["outer_class"])) * prog["macs_per_item"]
+    exec_flops_per_amp = 8 * exec_macs_per_amp
+
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     kernel_ms = []
@@ -232,7 +241,7 @@ def run_ours(args, rank, world, local_rank):
     sm_for_peak = peaks.get("sm_max_mhz", 2070.0)
     peak = alu_peak_tflops(args.precision, sm_for_peak)
     avg_kernel_s = statistics.mean(kernel_ms) / 1e3
-    achieved = flops_per_amp * nx / avg_kernel_s / 1e12
+    achieved = exec_flops_per_amp * nx / avg_kernel_s / 1e12
     out = {
         "metric": METRIC,
         "value": value,
@@ -248,13 +257,18 @@ def run_ours(args, rank, world, local_rank):
         "data": "synthetic: seeded random 3-regular graph, gamma/beta ~ U[0,pi), seeded bit strings",
         "config": {"workload": WORKLOAD["name"], "n": WORKLOAD["n"], "p": WORKLOAD["p"], "cuts": WORKLOAD["k"],
                    "slices_per_amplitude": 2 ** cost["k"], "bitstrings_per_step": nx, "precision": args.precision,
-                   "executor": plan.executor, "plan_width": cost["width"],
-                   "macs_per_slice": cost["macs_per_slice"], "effective_tflops": flops_per_amp * value / 1e12,
+                   "executor": tuned["executor"], "autotune_ms": tuned["ms"], "plan_width": cost["width"],
+                   "cut_classes": max(desc["cut_class"]) + 1 if desc["cut_class"] else 0,
+                   "inner_classes": len(prog["inner_class"]),
+                   "macs_per_slice_unshared": cost["macs_per_slice"],
+                   "executed_macs_per_amplitude": exec_macs_per_amp,
+                   "executed_tflops": exec_flops_per_amp * value / 1e12,
+                   "effective_tflops_per_slice_method": flops_per_amp * value / 1e12,
                    "slices_per_s": value * 2 ** cost["k"], "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"weak: {nx} bit strings per GPU, slices across CTAs/threads"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": profiled_traffic(args.precision),
-                     "kernel": "lane_exec_kernel" if plan.executor == "lane" else "block_exec_kernel",
+                     "kernel": "lane_exec_kernel" if prog["executor"] == "lane" else "block_exec_kernel",
                      "peak_source": ("FP32: 152 SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock of measured peaks)"
                                      % sm_for_peak) if args.precision != "fp64" else "FP64 nominal 1.25 TFLOP/s",
                      "kernel_ms_avg": avg_kernel_s * 1e3},

@@ -147,8 +147,12 @@ qtn_status qtn_contract_amplitude(const qtn_plan_t* plan, const uint8_t* x, qtn_
 /* nx amplitudes of one plan with device-resident data (the throughput path).
  *   d_x   : device, nx * n bytes (row j = bit string j).
  *   d_out : device, nx * 2 doubles (Re, Im per bit string).
- * Asynchronous on `stream`; the first call for a given (d_x, d_out, nx,
- * prec) records a CUDA graph that later calls replay. */
+ * Asynchronous on `stream`, except that the first call for a given (prec,
+ * nx) autotunes: it times every executor the plan compiled (per-class lane
+ * executor, batched executors at two shared-memory budgets) on `stream`,
+ * synchronising it, and keeps the fastest -- make that first call outside any
+ * stream capture.  The first call for a given (d_x, d_out, nx, prec) records
+ * a CUDA graph that later calls replay. */
 qtn_status qtn_contract_amplitudes_device(const qtn_plan_t* plan, const uint8_t* d_x, int nx,
                                           qtn_precision prec, cudaStream_t stream, double* d_out);
 

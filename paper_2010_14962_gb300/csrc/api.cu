@@ -68,18 +68,29 @@ bool precision_supported(qtn_precision p) { return p == QTN_FP64 || p == QTN_FP3
 
 }  // namespace
 
+// One compiled program of a plan and its device copy.
+struct ProgSlot {
+  std::string name;
+  Program prog;
+  Executor exec = Executor::Block;
+  bool fp64_only = false, fp32_only = false;
+  DeviceProgram dprog;
+  bool uploaded = false;
+  uint64_t items() const { return 1ull << prog.n_outer; }
+};
+
 struct qtn_plan {
   Network net;
   Plan plan;
-  Program lane_prog, block_prog;
-  Executor exec = Executor::Lane;
+  std::vector<ProgSlot> slots;  // [0]: per-slice program (slice ranges); then throughput candidates
   double log2_flops = 0, log2_peak_bytes = 0;
   std::mutex mu;
+  std::map<std::pair<int, int>, int> tuned;                         // (prec, nx) -> slot
+  std::map<std::pair<int, int>, std::vector<double>> tune_ms;       // candidate timings
 
   // Device state, created on first use on the then-current device.
   int device = -1;
   std::vector<void*> dev_allocs;
-  DeviceProgram dprog;
   int cap_nx = 0, cap_blocks = 0;
   void* d_leaf_tables = nullptr;
   Partial* d_partials = nullptr;
@@ -123,8 +134,6 @@ struct qtn_plan {
     cap_nx = cap_blocks = 0;
   }
 
-  const Program& program() const { return exec == Executor::Lane ? lane_prog : block_prog; }
-
   qtn_status ensure_device() {
     int dev = 0;
     QTN_CUDA(cudaGetDevice(&dev));
@@ -132,47 +141,60 @@ struct qtn_plan {
       if (dev != device) return fail(QTN_ERR_INVALID_ARG, "plan was first used on another device");
       return QTN_OK;
     }
-    const Program& pg = program();
+    QTN_CUDA(cudaStreamCreateWithFlags(&capture_stream, cudaStreamNonBlocking));
+    device = dev;
+    return QTN_OK;
+  }
+
+  qtn_status upload(ProgSlot& sl) {
+    if (sl.uploaded) return QTN_OK;
+    const Program& pg = sl.prog;
     DevLeaf* leaves;
     DevStep* steps;
     int32_t* gq;
     int8_t *gl, *gi, *go;
     double *ga, *be;
-    QTN_CUDA(upload(&leaves, pg.leaves));
+    QTN_CUDA(::upload(&leaves, pg.leaves));
     dev_allocs.push_back(leaves);
-    QTN_CUDA(upload(&steps, pg.steps));
+    QTN_CUDA(::upload(&steps, pg.steps));
     dev_allocs.push_back(steps);
-    QTN_CUDA(upload(&gq, pg.gate_q));
+    QTN_CUDA(::upload(&gq, pg.gate_q));
     dev_allocs.push_back(gq);
-    QTN_CUDA(upload(&gl, pg.gate_layer));
+    QTN_CUDA(::upload(&gl, pg.gate_layer));
     dev_allocs.push_back(gl);
-    QTN_CUDA(upload(&gi, pg.gate_in_h));
+    QTN_CUDA(::upload(&gi, pg.gate_in_h));
     dev_allocs.push_back(gi);
-    QTN_CUDA(upload(&go, pg.gate_out_kind));
+    QTN_CUDA(::upload(&go, pg.gate_out_kind));
     dev_allocs.push_back(go);
-    QTN_CUDA(upload(&ga, net.gamma));
+    QTN_CUDA(::upload(&ga, net.gamma));
     dev_allocs.push_back(ga);
-    QTN_CUDA(upload(&be, net.beta));
+    QTN_CUDA(::upload(&be, net.beta));
     dev_allocs.push_back(be);
-    QTN_CUDA(cudaStreamCreateWithFlags(&capture_stream, cudaStreamNonBlocking));
-    dprog.n = pg.n;
-    dprog.p = pg.p;
-    dprog.k = pg.k;
-    dprog.n_leaves = (int)pg.leaves.size();
-    dprog.n_steps = (int)pg.steps.size();
-    dprog.leaf_elems = pg.leaf_elems;
-    dprog.arena_elems = pg.arena_elems;
-    dprog.exec = exec;
-    dprog.leaves = leaves;
-    dprog.steps = steps;
-    dprog.gate_q = gq;
-    dprog.gate_layer = gl;
-    dprog.gate_in_h = gi;
-    dprog.gate_out_kind = go;
-    dprog.gamma = ga;
-    dprog.beta = be;
-    device = dev;
+    DeviceProgram& d = sl.dprog;
+    d.n = pg.n;
+    d.p = pg.p;
+    d.k = pg.k;
+    d.n_leaves = (int)pg.leaves.size();
+    d.n_steps = (int)pg.steps.size();
+    d.leaf_elems = pg.leaf_elems;
+    d.arena_elems = pg.arena_elems;
+    d.exec = sl.exec;
+    d.leaves = leaves;
+    d.steps = steps;
+    d.gate_q = gq;
+    d.gate_layer = gl;
+    d.gate_in_h = gi;
+    d.gate_out_kind = go;
+    d.gamma = ga;
+    d.beta = be;
+    sl.uploaded = true;
     return QTN_OK;
+  }
+
+  uint32_t max_leaf_elems() const {
+    uint32_t m = 1;
+    for (const ProgSlot& s : slots) m = std::max(m, s.prog.leaf_elems);
+    return m;
   }
 
   qtn_status ensure_workspace(int nx, int blocks) {
@@ -181,12 +203,13 @@ struct qtn_plan {
     graphs.clear();
     int nnx = std::max(nx, cap_nx), nb = std::max(blocks, cap_blocks);
     free_workspace();
-    size_t lt = (size_t)nnx * program().leaf_elems * sizeof(double2);
+    size_t lt = (size_t)nnx * max_leaf_elems() * sizeof(double2);
     QTN_CUDA(cudaMalloc(&d_leaf_tables, std::max<size_t>(lt, 16)));
     QTN_CUDA(cudaMalloc((void**)&d_partials, (size_t)nnx * nb * sizeof(Partial)));
     QTN_CUDA(cudaMalloc((void**)&d_err, sizeof(int)));
     QTN_CUDA(cudaMemset(d_err, 0, sizeof(int)));
     QTN_CUDA(cudaMalloc((void**)&d_x_stage, (size_t)nnx * net.n));
+    QTN_CUDA(cudaMemset(d_x_stage, 0, (size_t)nnx * net.n));
     QTN_CUDA(cudaMalloc((void**)&d_out_stage, (size_t)nnx * sizeof(double2)));
     QTN_CUDA(cudaMalloc((void**)&d_raw_stage, (size_t)nnx * sizeof(Partial)));
     QTN_CUDA(cudaMallocHost((void**)&h_x_pinned, (size_t)nnx * net.n));
@@ -198,12 +221,6 @@ struct qtn_plan {
 
   double scale() const { return std::pow(2.0, -0.5 * net.n); }
 
-  qtn_status shape_for(qtn_precision prec, int nx, uint64_t slices, ExecShape* sh) {
-    if (!exec_shape(dprog, prec == QTN_FP64 ? 16 : 8, nx, slices, sh))
-      return fail(QTN_ERR_UNSUPPORTED, "the plan's per-slice working set does not fit in shared memory");
-    return QTN_OK;
-  }
-
   LaunchBuffers buffers() const {
     LaunchBuffers b;
     b.leaf_tables = d_leaf_tables;
@@ -212,17 +229,84 @@ struct qtn_plan {
     return b;
   }
 
-  // Enqueue the graph for (d_x, d_out, nx, prec) on `stream`.
+  // Grid of slot `si` for nx bit strings (uploads the slot on first use).
+  qtn_status prepare(int si, qtn_precision prec, int nx, uint64_t items, ExecShape* sh) {
+    qtn_status st = upload(slots[si]);
+    if (st != QTN_OK) return st;
+    if (!exec_shape(slots[si].dprog, prec == QTN_FP64 ? 16 : 8, nx, items, sh))
+      return fail(QTN_ERR_UNSUPPORTED, "the plan's per-item working set does not fit in shared memory");
+    return ensure_workspace(nx, sh->blocks_per_x);
+  }
+
+  bool eligible(int si, qtn_precision prec) const {
+    const ProgSlot& s = slots[si];
+    if (prec == QTN_FP64 && s.fp32_only) return false;
+    if (prec == QTN_FP32 && s.fp64_only) return false;
+    return true;
+  }
+
+  // Autotuner: times every eligible throughput candidate for (prec, nx) on
+  // the workspace (bit strings all zero) and keeps the fastest.  Runs on the
+  // caller's stream (after its earlier work) and synchronises it.
+  qtn_status tune(qtn_precision prec, int nx, cudaStream_t stream, int* out_slot) {
+    auto key = std::make_pair((int)prec, nx);
+    auto it = tuned.find(key);
+    if (it != tuned.end()) {
+      *out_slot = it->second;
+      return QTN_OK;
+    }
+    QTN_CUDA(cudaStreamSynchronize(stream));
+    cudaEvent_t a, b;
+    QTN_CUDA(cudaEventCreate(&a));
+    QTN_CUDA(cudaEventCreate(&b));
+    int best = -1;
+    float best_ms = 0;
+    std::vector<double> times(slots.size(), -1.0);
+    for (int si = 1; si < (int)slots.size(); ++si) {
+      if (!eligible(si, prec)) continue;
+      ExecShape sh;
+      if (prepare(si, prec, nx, slots[si].items(), &sh) != QTN_OK) continue;
+      float ms_min = 1e30f;
+      for (int rep = 0; rep < 4; ++rep) {
+        QTN_CUDA(cudaEventRecord(a, stream));
+        cudaError_t le = launch_contraction(slots[si].dprog, prec == QTN_FP64, d_x_stage, nx, 0, slots[si].items(),
+                                            buffers(), sh, scale(), d_out_stage, nullptr, nullptr, stream);
+        if (le != cudaSuccess) return cuda_fail(le, "launch_contraction (tuning)");
+        QTN_CUDA(cudaEventRecord(b, stream));
+        QTN_CUDA(cudaEventSynchronize(b));
+        float ms = 0;
+        QTN_CUDA(cudaEventElapsedTime(&ms, a, b));
+        if (rep > 0) ms_min = std::min(ms_min, ms);
+      }
+      times[si] = ms_min;
+      if (best < 0 || ms_min < best_ms) {
+        best = si;
+        best_ms = ms_min;
+      }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (best < 0) return fail(QTN_ERR_UNSUPPORTED, "no executor fits this plan on chip");
+    tuned[key] = best;
+    tune_ms[key] = times;
+    *out_slot = best;
+    return QTN_OK;
+  }
+
+  // Enqueue the contraction of nx bit strings at d_x on `stream`: the tuned
+  // executor, replayed from a CUDA graph (or launched directly with kernel
+  // timing on).
   qtn_status run_graph(const uint8_t* d_x, int nx, qtn_precision prec, double2* d_out, cudaStream_t stream) {
-    const uint64_t S = 1ull << plan.cuts.size();
+    int si = 0;
+    qtn_status st = tune(prec, nx, stream, &si);
+    if (st != QTN_OK) return st;
+    const uint64_t S = slots[si].items();
     ExecShape sh;
-    qtn_status st = shape_for(prec, nx, S, &sh);
+    st = prepare(si, prec, nx, S, &sh);
     if (st != QTN_OK) return st;
-    st = ensure_workspace(nx, sh.blocks_per_x);
-    if (st != QTN_OK) return st;
-    if (timing) {  // direct launches with events around the executor
-      cudaError_t le = launch_contraction(dprog, prec == QTN_FP64, d_x, nx, 0, S, buffers(), sh, scale(), d_out,
-                                          nullptr, nullptr, stream, ev0, ev1);
+    if (timing) {
+      cudaError_t le = launch_contraction(slots[si].dprog, prec == QTN_FP64, d_x, nx, 0, S, buffers(), sh, scale(),
+                                          d_out, nullptr, nullptr, stream, ev0, ev1);
       if (le != cudaSuccess) return cuda_fail(le, "launch_contraction");
       return QTN_OK;
     }
@@ -231,8 +315,8 @@ struct qtn_plan {
     if (it == graphs.end()) {
       cudaGraph_t g;
       QTN_CUDA(cudaStreamBeginCapture(capture_stream, cudaStreamCaptureModeThreadLocal));
-      cudaError_t le = launch_contraction(dprog, prec == QTN_FP64, d_x, nx, 0, S, buffers(), sh, scale(), d_out,
-                                          nullptr, nullptr, capture_stream);
+      cudaError_t le = launch_contraction(slots[si].dprog, prec == QTN_FP64, d_x, nx, 0, S, buffers(), sh, scale(),
+                                          d_out, nullptr, nullptr, capture_stream);
       cudaError_t ce = cudaStreamEndCapture(capture_stream, &g);
       if (le != cudaSuccess) return cuda_fail(le, "launch_contraction (capture)");
       if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
@@ -372,13 +456,62 @@ qtn_status qtn_plan(const qtn_network_t* net, const int32_t* cuts, int k, const 
   if (!h) return fail(QTN_ERR_OOM, "host allocation failed");
   h->net = net->net;
   std::string err = make_plan(h->net, cutv, ord, &h->plan);
-  if (err.empty()) err = compile_program(h->net, h->plan, true, &h->lane_prog);
-  if (err.empty()) err = compile_program(h->net, h->plan, false, &h->block_prog);
+  // Slot 0: the per-slice program (exact slice numbering, for slice ranges).
+  Program lane_p, block_p;
+  ProgramOptions lane_o, block_o;
+  lane_o.c_reuses_a = true;
+  if (err.empty()) err = compile_program(h->net, h->plan, lane_o, &lane_p);
+  if (err.empty()) err = compile_program(h->net, h->plan, block_o, &block_p);
   if (!err.empty()) {
     delete h;
     return fail(QTN_ERR_INVALID_ARG, err);
   }
-  h->exec = h->lane_prog.max_rank <= kLaneMaxRank ? Executor::Lane : Executor::Block;
+  const bool lane_ok = lane_p.max_rank <= kLaneMaxRank;
+  {
+    ProgSlot s0;
+    s0.name = lane_ok ? "lane" : "block";
+    s0.exec = lane_ok ? Executor::Lane : Executor::Block;
+    s0.prog = lane_ok ? lane_p : block_p;
+    h->slots.push_back(std::move(s0));
+  }
+  // Throughput candidates: slices enumerated over cut classes (structurally
+  // zero slices skipped); lane executor, and batched block executors whose
+  // inner classes are chosen for a small and a large shared-memory budget.
+  int ncls = 0;
+  std::vector<int> cls = cut_classes(h->net, h->plan.cuts, &ncls);
+  if (lane_ok) {
+    ProgramOptions o;
+    o.c_reuses_a = true;
+    o.cut_class = cls;
+    ProgSlot sl;
+    sl.name = "lane/classes";
+    sl.exec = Executor::Lane;
+    if (compile_program(h->net, h->plan, o, &sl.prog).empty()) h->slots.push_back(std::move(sl));
+  }
+  struct Budget {
+    const char* name;
+    uint32_t elems;
+    bool fp64;
+  } budgets[] = {{"batched/fp32/48KiB", 6 * 1024, false},
+                 {"batched/fp32/192KiB", 24 * 1024, false},
+                 {"batched/fp64/48KiB", 3 * 1024, true},
+                 {"batched/fp64/192KiB", 12 * 1024, true}};
+  for (const Budget& bd : budgets) {
+    ProgramOptions o = choose_batched(h->net, h->plan, bd.elems, 64);
+    ProgSlot sl;
+    sl.name = bd.name;
+    sl.exec = Executor::Block;
+    sl.fp64_only = bd.fp64;
+    sl.fp32_only = !bd.fp64;
+    if (!compile_program(h->net, h->plan, o, &sl.prog).empty()) continue;
+    if (sl.prog.arena_elems + sl.prog.leaf_elems > bd.elems) continue;
+    h->slots.push_back(std::move(sl));
+  }
+  if (h->slots.size() == 1) {  // nothing else fits: the per-slice program
+    ProgSlot sl = h->slots[0];
+    sl.name += "/slices";
+    h->slots.push_back(std::move(sl));
+  }
   h->log2_flops = h->plan.log2_flops_total();
   h->log2_peak_bytes = std::log2(h->plan.peak_elems * 8.0);
   if (opts.max_slice_bytes > 0 && h->plan.peak_elems * 8.0 > opts.max_slice_bytes) {
@@ -399,8 +532,8 @@ namespace internal {
 bool plan_view(const qtn_plan_t* cplan, PlanView* view) {
   if (!cplan || !view) return false;
   qtn_plan_t* plan = const_cast<qtn_plan_t*>(cplan);
-  view->program = &plan->program();
-  view->lane = plan->exec == Executor::Lane;
+  view->program = &plan->slots[0].prog;
+  view->lane = plan->slots[0].exec == Executor::Lane;
   view->n = plan->net.n;
   view->k = (int)plan->plan.cuts.size();
   view->gamma = plan->net.gamma.data();
@@ -497,7 +630,7 @@ qtn_status qtn_plan_macs_per_slice(const qtn_plan_t* plan, double* macs) {
 
 qtn_status qtn_plan_executor(const qtn_plan_t* plan, const char** name) {
   if (!plan || !name) return fail(QTN_ERR_INVALID_ARG, "NULL argument");
-  *name = plan->exec == Executor::Lane ? "lane" : "block";
+  *name = plan->slots[0].name.c_str();
   return QTN_OK;
 }
 
@@ -523,9 +656,10 @@ qtn_status qtn_contract_amplitude(const qtn_plan_t* cplan, const uint8_t* x, qtn
   st = plan->ensure_device();
   if (st != QTN_OK) return st;
   ExecShape sh;
-  st = plan->shape_for(prec, 1, 1ull << plan->plan.cuts.size(), &sh);
+  int si = 0;
+  st = plan->tune(prec, 1, stream, &si);
   if (st != QTN_OK) return st;
-  st = plan->ensure_workspace(1, sh.blocks_per_x);
+  st = plan->prepare(si, prec, 1, plan->slots[si].items(), &sh);
   if (st != QTN_OK) return st;
   std::memcpy(plan->h_x_pinned, x, plan->net.n);
   QTN_CUDA(cudaMemcpyAsync(plan->d_x_stage, plan->h_x_pinned, plan->net.n, cudaMemcpyHostToDevice, stream));
@@ -557,13 +691,11 @@ qtn_status qtn_contract_slices(const qtn_plan_t* cplan, const uint8_t* x, uint64
     return QTN_OK;
   }
   ExecShape sh;
-  st = plan->shape_for(prec, 1, slice_hi - slice_lo, &sh);
-  if (st != QTN_OK) return st;
-  st = plan->ensure_workspace(1, sh.blocks_per_x);
+  st = plan->prepare(0, prec, 1, slice_hi - slice_lo, &sh);
   if (st != QTN_OK) return st;
   std::memcpy(plan->h_x_pinned, x, plan->net.n);
   QTN_CUDA(cudaMemcpyAsync(plan->d_x_stage, plan->h_x_pinned, plan->net.n, cudaMemcpyHostToDevice, stream));
-  cudaError_t le = launch_contraction(plan->dprog, prec == QTN_FP64, plan->d_x_stage, 1, slice_lo, slice_hi,
+  cudaError_t le = launch_contraction(plan->slots[0].dprog, prec == QTN_FP64, plan->d_x_stage, 1, slice_lo, slice_hi,
                                       plan->buffers(), sh, 1.0, nullptr, plan->d_raw_stage,
                                       reinterpret_cast<double2*>(d_slices), stream);
   if (le != cudaSuccess) return cuda_fail(le, "launch_contraction");
@@ -593,9 +725,10 @@ qtn_status qtn_contract_batch(const qtn_plan_t* const* plans, const uint8_t* con
     if (st != QTN_OK) return st;
     int nx = (int)jobs.size();
     ExecShape sh;
-    st = plan->shape_for(prec, nx, 1ull << plan->plan.cuts.size(), &sh);
+    int si = 0;
+    st = plan->tune(prec, nx, stream, &si);
     if (st != QTN_OK) return st;
-    st = plan->ensure_workspace(nx, sh.blocks_per_x);
+    st = plan->prepare(si, prec, nx, plan->slots[si].items(), &sh);
     if (st != QTN_OK) return st;
     for (int i = 0; i < nx; ++i) std::memcpy(plan->h_x_pinned + (size_t)i * plan->net.n, xs[jobs[i]], plan->net.n);
     QTN_CUDA(cudaMemcpyAsync(plan->d_x_stage, plan->h_x_pinned, (size_t)nx * plan->net.n, cudaMemcpyHostToDevice,
@@ -633,38 +766,70 @@ qtn_status qtn_plan_describe(const qtn_plan_t* plan, char* buf, size_t cap, size
     json_ints(o, P.tensors[i].data(), P.tensors[i].size());
   }
   o << "],\"width\":" << P.width << ",\"max_rank\":" << P.max_rank << ",\"macs\":" << P.macs
-    << ",\"peak_elems\":" << P.peak_elems << ",\"executor\":\"" << (plan->exec == Executor::Lane ? "lane" : "block")
-    << "\",\"programs\":{";
-  for (int which = 0; which < 2; ++which) {
-    const Program& pg = which == 0 ? plan->lane_prog : plan->block_prog;
-    o << (which ? "," : "") << "\"" << (which == 0 ? "lane" : "block") << "\":{\"leaf_elems\":" << pg.leaf_elems
+    << ",\"peak_elems\":" << P.peak_elems << ",\"executor\":\"" << plan->slots[0].name << "\",\"programs\":{";
+  for (size_t which = 0; which < plan->slots.size(); ++which) {
+    const Program& pg = plan->slots[which].prog;
+    o << (which ? "," : "") << "\"" << plan->slots[which].name << "\":{\"leaf_elems\":" << pg.leaf_elems
       << ",\"arena_elems\":" << pg.arena_elems << ",\"width\":" << pg.width << ",\"max_rank\":" << pg.max_rank
-      << ",\"macs_per_slice\":" << pg.macs_per_slice << ",\"leaves\":[";
+      << ",\"macs_per_item\":" << pg.macs_per_item << ",\"n_classes\":" << pg.n_classes
+      << ",\"executor\":\"" << (plan->slots[which].exec == Executor::Lane ? "lane" : "block") << "\",\"outer_class\":";
+    json_ints(o, pg.outer_class.data(), pg.outer_class.size());
+    o << ",\"inner_class\":";
+    json_ints(o, pg.inner_class.data(), pg.inner_class.size());
+    o << ",\"root_class\":";
+    json_ints(o, pg.root_class.data(), pg.root_class.size());
+    o << ",\"leaves\":[";
     for (size_t i = 0; i < pg.leaves.size(); ++i) {
       const DevLeaf& L = pg.leaves[i];
       int cb[kMaxLeafCuts], sb[8];
       for (int j = 0; j < L.ncut; ++j) cb[j] = L.cut_bit[j];
-      for (int j = 0; j < L.rank_nc + L.ncut; ++j) sb[j] = L.slot_of_bit[j];
+      for (int j = 0; j < L.rank_nc + L.ncut; ++j) sb[j] = L.slot_mask[j];
       o << (i ? "," : "") << "{\"base\":" << L.base << ",\"rank_nc\":" << (int)L.rank_nc << ",\"gate\":" << L.gate
         << ",\"cut_bit\":";
       json_ints(o, cb, L.ncut);
-      o << ",\"slot_of_bit\":";
+      o << ",\"slot_mask\":";
       json_ints(o, sb, L.rank_nc + L.ncut);
       o << "}";
     }
     o << "],\"steps\":[";
     for (size_t i = 0; i < pg.steps.size(); ++i) {
-      const DevStep& s = pg.steps[i];
+      const DevStep& st = pg.steps[i];
       int w[kMaxRank];
-      for (int j = 0; j < s.ma + s.nb; ++j) w[j] = s.w[j];
-      o << (i ? "," : "") << "{\"ma\":" << (int)s.ma << ",\"nb\":" << (int)s.nb << ",\"kb\":" << (int)s.kb
-        << ",\"flags\":" << (int)s.flags << ",\"a\":" << s.a << ",\"b\":" << s.b << ",\"c\":" << s.c << ",\"w\":";
-      json_ints(o, w, s.ma + s.nb);
+      const int rc = st.ma + st.nb + st.bb;
+      for (int j = 0; j < rc; ++j) w[j] = st.w[j];
+      o << (i ? "," : "") << "{\"ma\":" << (int)st.ma << ",\"nb\":" << (int)st.nb << ",\"kb\":" << (int)st.kb
+        << ",\"bb\":" << (int)st.bb << ",\"flags\":" << (int)st.flags << ",\"a\":" << st.a << ",\"b\":" << st.b
+        << ",\"c\":" << st.c << ",\"w\":";
+      json_ints(o, w, rc);
       o << "}";
     }
     o << "]}";
   }
-  o << "},\"gates\":[";
+  o << "},\"cut_class\":";
+  {
+    int nc = 0;
+    std::vector<int> cls = cut_classes(plan->net, P.cuts, &nc);
+    json_ints(o, cls.data(), cls.size());
+  }
+  o << ",\"tuned\":[";
+  {
+    bool first = true;
+    for (const auto& [key, slot] : plan->tuned) {
+      o << (first ? "" : ",") << "{\"prec\":" << key.first << ",\"nx\":" << key.second << ",\"executor\":\""
+        << plan->slots[slot].name << "\",\"ms\":{";
+      const auto& t = plan->tune_ms.at(key);
+      bool f2 = true;
+      for (size_t i = 0; i < t.size(); ++i)
+        if (t[i] >= 0) {
+          o << (f2 ? "" : ",") << "\"" << plan->slots[i].name << "\":" << t[i];
+          f2 = false;
+        }
+      o << "}}";
+      first = false;
+    }
+  }
+  o << "]";
+  o << ",\"gates\":[";
   for (size_t g = 0; g < plan->net.gates.size(); ++g) {
     const Gate& G = plan->net.gates[g];
     o << (g ? "," : "") << "{\"layer\":" << G.layer << ",\"q\":[" << G.q[0] << "," << G.q[1] << "],\"in_h\":["

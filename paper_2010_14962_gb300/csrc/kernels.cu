@@ -11,9 +11,11 @@
 //                       intermediates in a private column of shared memory
 //                       and every merge (Eq. 1) is a fully unrolled
 //                       register-resident product specialised on its shape.
-//   block_exec_kernel   one slice per thread block, for programs with larger
-//                       tensors; threads split the output elements of each
-//                       merge.
+//   block_exec_kernel   one work item per thread block: a slice, or (batched
+//                       programs) a sub-cube of slices whose inner cut classes
+//                       are carried as batch bits, so each merge runs once per
+//                       distinct value of the bits it depends on; threads
+//                       split the output elements of each merge.
 //   finalize_kernel     fixed-order compensated FP64 sum of the per-block
 //                       partial sums over slices (Eq. 2) and the 2^{-n/2}
 //                       normalisation of the unnormalised H|0> = (1, 1).
@@ -119,7 +121,9 @@ __global__ void leaf_build_kernel(const DevLeaf* __restrict__ leaves, const int3
       const int g = L.gate;
       const int l = gate_layer[g];
       int v[4] = {-1, -1, -1, -1};
-      for (int b = 0; b < r; ++b) v[L.slot_of_bit[b]] = (e >> b) & 1;
+      for (int b = 0; b < r; ++b)
+        for (int sl = 0; sl < 4; ++sl)
+          if ((L.slot_mask[b] >> sl) & 1) v[sl] = (e >> b) & 1;
       double sg, cg, sb, cb;
       sincos(gamma[l], &sg, &cg);
       sincos(beta[l], &sb, &cb);
@@ -305,6 +309,12 @@ __global__ void __launch_bounds__(128) lane_exec_kernel(ExecParams P, int* err) 
 
 // ------------------------------------------------------------ block exec --
 
+// One work item per thread block at a time: an item is one slice (per-slice
+// programs) or one assignment of the outer slice classes (batched programs,
+// whose tensors carry the inner classes as batch bits: every merge then runs
+// once per distinct value of the inner bits it depends on, and the root holds
+// the scalars of all slices of the item).  Threads split the output elements
+// of each merge; a barrier separates merges.
 template <class V>
 __global__ void __launch_bounds__(256) block_exec_kernel(ExecParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -314,6 +324,7 @@ __global__ void __launch_bounds__(256) block_exec_kernel(ExecParams P) {
   DevLeaf* s_leaves = reinterpret_cast<DevLeaf*>(smem + lay.leaves);
   V* s_lt = reinterpret_cast<V*>(smem + lay.table);
   V* s_arena = reinterpret_cast<V*>(smem + lay.arena);
+  Partial* s_red = reinterpret_cast<Partial*>(smem + lay.red);
   const int xi = blockIdx.x / P.blocks_per_x;
   const int bx = blockIdx.x % P.blocks_per_x;
   copy_words(s_steps, P.steps, (size_t)P.n_steps * sizeof(DevStep));
@@ -326,55 +337,81 @@ __global__ void __launch_bounds__(256) block_exec_kernel(ExecParams P) {
   const uint64_t S = P.slice_hi - P.slice_lo;
   for (uint64_t i = bx; i < S; i += P.blocks_per_x) {
     const uint64_t s = P.slice_lo + i;
-    V res = CplxOps<V>::zero();
     for (int j = 0; j < P.n_steps; ++j) {
       const DevStep& st = s_steps[j];
       const V* A = (st.flags & STEP_A_LEAF) ? s_lt + leaf_offset(s_leaves[st.a], s) : s_arena + st.a;
       const V* B = (st.flags & STEP_B_LEAF) ? s_lt + leaf_offset(s_leaves[st.b], s) : s_arena + st.b;
-      const int ma = st.ma, kb = st.kb, rc = st.ma + st.nb;
-      const uint32_t NC = 1u << rc, K = 1u << kb, mmask = (1u << ma) - 1u;
+      const int ma = st.ma, nb = st.nb, kb = st.kb, rc = st.ma + st.nb + st.bb;
+      const uint32_t NC = 1u << rc, K = 1u << kb;
+      const uint32_t mmask = (1u << ma) - 1u, nmask = (1u << nb) - 1u;
+      const bool root = st.flags & STEP_ROOT;
       for (uint32_t o = threadIdx.x; o < NC; o += T) {
-        const uint32_t m = o & mmask, n = o >> ma;
-        const V* ap = A + m;
-        const V* bp = B + (n << kb);
+        const uint32_t m = o & mmask, n = (o >> ma) & nmask, b = o >> (ma + nb);
+        const V* ap = A + m + (b << (ma + kb));
+        const V* bp = B + (n << kb) + (b << (kb + nb));
         V acc = CplxOps<V>::zero();
         for (uint32_t k = 0; k < K; ++k) CplxOps<V>::fma(acc, ap[k << ma], bp[k]);
-        if (st.flags & STEP_ROOT) {
-          res = acc;
+        if (root) {
+          kahan_add(sr, cr, (double)acc.x);
+          kahan_add(si, ci, (double)acc.y);
+          if (P.slices && NC == 1) P.slices[(size_t)xi * S + i] = make_double2((double)acc.x, (double)acc.y);
         } else {
           uint32_t pos = 0;
-          for (int b = 0; b < rc; ++b)
-            if ((o >> b) & 1u) pos += st.w[b];
+          for (int bit = 0; bit < rc; ++bit)
+            if ((o >> bit) & 1u) pos += st.w[bit];
           s_arena[st.c + pos] = acc;
         }
       }
       __syncthreads();
     }
-    if (threadIdx.x == 0) {
-      kahan_add(sr, cr, (double)res.x);
-      kahan_add(si, ci, (double)res.y);
-      if (P.slices) P.slices[(size_t)xi * S + i] = make_double2((double)res.x, (double)res.y);
-    }
   }
-  if (threadIdx.x == 0) P.partials[(size_t)xi * P.blocks_per_x + bx] = Partial::make(sr, si, cr, ci);
+  s_red[threadIdx.x] = Partial::make(sr, si, cr, ci);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, b = 0, ca = 0, cb = 0;
+    for (int t = 0; t < T; ++t) {
+      const Partial v = s_red[t];
+      kahan_add(a, ca, v.re);
+      kahan_add(a, ca, -v.cre);
+      kahan_add(b, cb, v.im);
+      kahan_add(b, cb, -v.cim);
+    }
+    P.partials[(size_t)xi * P.blocks_per_x + bx] = Partial::make(a, b, ca, cb);
+  }
 }
 
 // -------------------------------------------------------------- finalize --
 
-__global__ void finalize_kernel(const Partial* __restrict__ partials, int blocks, int nx, double scale,
-                                double2* __restrict__ out, Partial* __restrict__ raw) {
-  const int xi = blockIdx.x * blockDim.x + threadIdx.x;
-  if (xi >= nx) return;
+// One block per bit string: thread t adds partials t, t + T, ... in order
+// (compensated), then the per-thread sums are added in thread order.  The
+// grouping depends only on the block count, so the result is deterministic.
+__global__ void __launch_bounds__(128) finalize_kernel(const Partial* __restrict__ partials, int blocks,
+                                                       double scale, double2* __restrict__ out,
+                                                       Partial* __restrict__ raw) {
+  __shared__ Partial red[128];
+  const int xi = blockIdx.x;
   double a = 0, b = 0, ca = 0, cb = 0;
-  for (int t = 0; t < blocks; ++t) {  // fixed order: deterministic result
+  for (int t = threadIdx.x; t < blocks; t += blockDim.x) {
     const Partial v = partials[(size_t)xi * blocks + t];
     kahan_add(a, ca, v.re);
     kahan_add(a, ca, -v.cre);
     kahan_add(b, cb, v.im);
     kahan_add(b, cb, -v.cim);
   }
-  if (out) out[xi] = make_double2((a - ca) * scale, (b - cb) * scale);
-  if (raw) raw[xi] = Partial::make(a, b, ca, cb);
+  red[threadIdx.x] = Partial::make(a, b, ca, cb);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    a = b = ca = cb = 0;
+    for (int t = 0; t < (int)blockDim.x; ++t) {
+      const Partial v = red[t];
+      kahan_add(a, ca, v.re);
+      kahan_add(a, ca, -v.cre);
+      kahan_add(b, cb, v.im);
+      kahan_add(b, cb, -v.cim);
+    }
+    if (out) out[xi] = make_double2((a - ca) * scale, (b - cb) * scale);
+    if (raw) raw[xi] = Partial::make(a, b, ca, cb);
+  }
 }
 
 int g_num_sms = 0;
@@ -489,7 +526,7 @@ cudaError_t launch_contraction(const DeviceProgram& prog, bool fp64, const uint8
     e = cudaEventRecord(ev1, stream);
     if (e != cudaSuccess) return e;
   }
-  finalize_kernel<<<(nx + 127) / 128, 128, 0, stream>>>(buf.partials, shape.blocks_per_x, nx, scale, d_out, d_raw);
+  finalize_kernel<<<nx, 128, 0, stream>>>(buf.partials, shape.blocks_per_x, scale, d_out, d_raw);
   return cudaGetLastError();
 }
 

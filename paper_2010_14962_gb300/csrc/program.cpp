@@ -4,19 +4,32 @@
 #include <cmath>
 #include <functional>
 #include <map>
+#include <numeric>
 
 namespace qtn {
 
 namespace {
 
-std::vector<int> set_and(const std::vector<int>& a, const std::vector<int>& b) {
-  std::vector<int> r;
+using Set = std::vector<int>;  // sorted ids: real index i < I, inner class c as I + c
+
+Set set_and(const Set& a, const Set& b) {
+  Set r;
   std::set_intersection(a.begin(), a.end(), b.begin(), b.end(), std::back_inserter(r));
   return r;
 }
-std::vector<int> set_minus(const std::vector<int>& a, const std::vector<int>& b) {
-  std::vector<int> r;
+Set set_minus(const Set& a, const Set& b) {
+  Set r;
   std::set_difference(a.begin(), a.end(), b.begin(), b.end(), std::back_inserter(r));
+  return r;
+}
+Set set_or(const Set& a, const Set& b) {
+  Set r;
+  std::set_union(a.begin(), a.end(), b.begin(), b.end(), std::back_inserter(r));
+  return r;
+}
+Set concat(const Set& a, const Set& b) {
+  Set r = a;
+  r.insert(r.end(), b.begin(), b.end());
   return r;
 }
 
@@ -37,38 +50,124 @@ struct Arena {
   void release(uint32_t off) { used.erase(off); }
 };
 
+int find_root(std::vector<int>& parent, int x) {
+  while (parent[x] != x) x = parent[x] = parent[parent[x]];
+  return x;
+}
+
 }  // namespace
 
-std::string compile_program(const Network& net, const Plan& plan_in, bool c_reuses_operands,
-                            Program* out) {
+std::vector<int> cut_classes(const Network& net, const std::vector<int>& cuts, int* n_classes) {
+  const int k = (int)cuts.size();
+  std::vector<int> cut_no(net.indices.size(), -1);
+  for (int j = 0; j < k; ++j) cut_no[cuts[j]] = j;
+  std::vector<int> parent(k);
+  std::iota(parent.begin(), parent.end(), 0);
+  for (const Gate& g : net.gates)
+    for (int w = 0; w < 2; ++w) {
+      if (g.out_kind[w] != OUT_PLAIN || g.leg[w] < 0 || g.leg[2 + w] < 0) continue;
+      int a = cut_no[g.leg[w]], b = cut_no[g.leg[2 + w]];
+      if (a >= 0 && b >= 0) parent[find_root(parent, a)] = find_root(parent, b);
+    }
+  std::map<int, int> id;
+  std::vector<int> cls(k);
+  for (int j = 0; j < k; ++j) {
+    int r = find_root(parent, j);
+    auto it = id.find(r);
+    if (it == id.end()) it = id.emplace(r, (int)id.size()).first;
+    cls[j] = it->second;
+  }
+  *n_classes = (int)id.size();
+  return cls;
+}
+
+std::string compile_program(const Network& net, const Plan& plan_in, const ProgramOptions& opt, Program* out) {
   Plan plan = plan_in;
   const int L = plan.n_leaves;
+  const int I = (int)net.indices.size();
+  const int K = (int)plan.cuts.size();
   Program pg;
   pg.n = net.n;
   pg.p = net.p;
-  pg.k = (int)plan.cuts.size();
+  pg.k = K;
+
+  // Classes and their outer / inner positions.
+  std::vector<int> cls = opt.cut_class;
+  if (cls.empty()) {
+    cls.resize(K);
+    std::iota(cls.begin(), cls.end(), 0);
+  }
+  if ((int)cls.size() != K) return "cut_class must have one entry per cut";
+  pg.n_classes = K ? *std::max_element(cls.begin(), cls.end()) + 1 : 0;
+  std::vector<int> cls_pos(pg.n_classes, -1);
+  std::vector<char> is_inner(pg.n_classes, 0);
+  for (int c = 0; c < pg.n_classes; ++c) is_inner[c] = c < (int)opt.inner.size() && opt.inner[c];
+  for (int c = 0; c < pg.n_classes; ++c) {
+    if (is_inner[c]) {
+      cls_pos[c] = (int)pg.inner_class.size();
+      pg.inner_class.push_back(c);
+    } else {
+      cls_pos[c] = (int)pg.outer_class.size();
+      pg.outer_class.push_back(c);
+    }
+  }
+  pg.n_inner = (int)pg.inner_class.size();
+  pg.n_outer = (int)pg.outer_class.size();
+  if (pg.n_outer > 62) return "too many outer slice classes";
+  std::vector<int> cut_no(I, -1);
+  for (int j = 0; j < K; ++j) cut_no[plan.cuts[j]] = j;
 
   // A network of one tensor has no merge: multiply it by a constant 1.
   bool unit_leaf = false;
   if (plan.merges.empty()) {
     unit_leaf = true;
-    plan.tensors.insert(plan.tensors.begin() + L, std::vector<int>{});
-    // shift intermediate ids (there are none) and add the merge
+    plan.tensors.insert(plan.tensors.begin() + L, Set{});
     plan.merges.push_back({0, L, L + 1});
-    plan.tensors.push_back(plan.tensors[0]);  // rank of leaf 0 must be 0 here
+    plan.tensors.push_back(plan.tensors[0]);
     if (!plan.tensors[0].empty()) return "single-tensor network must be closed";
   }
   const int n_leaves = L + (unit_leaf ? 1 : 0);
   const int T = (int)plan.tensors.size();
   auto is_leaf = [&](int t) { return t < n_leaves; };
+  auto leaf_gate = [&](int t) -> const Gate* { return (unit_leaf && t == L) ? nullptr : &net.gates[t]; };
 
-  // Contraction tree.
+  // Full index set of every tensor: real open indices + inner classes below it.
+  std::vector<Set> full(T);
+  for (int t = 0; t < n_leaves; ++t) {
+    Set f = plan.tensors[t];
+    if (const Gate* g = leaf_gate(t))
+      for (int s = 0; s < 4; ++s)
+        if (g->leg[s] >= 0 && cut_no[g->leg[s]] >= 0 && is_inner[cls[cut_no[g->leg[s]]]])
+          f.push_back(I + cls[cut_no[g->leg[s]]]);
+    std::sort(f.begin(), f.end());
+    f.erase(std::unique(f.begin(), f.end()), f.end());
+    full[t] = f;
+  }
+  struct Canon {
+    Set m, n, k, b;
+  };
+  std::vector<Canon> canon(plan.merges.size());
+  for (size_t j = 0; j < plan.merges.size(); ++j) {
+    const Merge& mg = plan.merges[j];
+    const Set& A = full[mg.a];
+    const Set& B = full[mg.b];
+    Canon& c = canon[j];
+    Set shared = set_and(A, B);
+    for (int x : shared) (x < I ? c.k : c.b).push_back(x);
+    c.m = set_minus(A, B);
+    c.n = set_minus(B, A);
+    Set vC = set_or(set_minus(A, c.k), set_minus(B, c.k));
+    full[mg.c] = vC;
+    if ((int)(c.m.size() + c.k.size() + c.b.size()) > kMaxRank ||
+        (int)(c.n.size() + c.k.size() + c.b.size()) > kMaxRank || (int)vC.size() > kMaxRank)
+      return "a tensor of rank > 16 is beyond the on-chip executors";
+  }
+
+  // Contraction tree, DFS order visiting the needier child first.
   std::vector<int> producer(T, -1);
   for (size_t j = 0; j < plan.merges.size(); ++j) producer[plan.merges[j].c] = (int)j;
   const int root = plan.merges.back().c;
-  auto elems = [&](int t) -> double { return is_leaf(t) ? 0.0 : std::ldexp(1.0, (int)plan.tensors[t].size()); };
-
-  // Peak arena need of each subtree, visiting the needier child first.
+  auto elems = [&](int t) -> double { return is_leaf(t) ? 0.0 : std::ldexp(1.0, (int)full[t].size()); };
   std::vector<double> need(T, 0.0);
   std::vector<char> first_is_a(T, 1);
   for (const Merge& m : plan.merges) {
@@ -78,7 +177,7 @@ std::string compile_program(const Network& net, const Plan& plan_in, bool c_reus
     first_is_a[m.c] = ab <= ba;
     need[m.c] = std::min(ab, ba);
   }
-  std::vector<int> order;  // merge ids in execution order
+  std::vector<int> order;
   std::function<void(int)> visit = [&](int t) {
     if (producer[t] < 0) return;
     const Merge& m = plan.merges[producer[t]];
@@ -94,63 +193,56 @@ std::string compile_program(const Network& net, const Plan& plan_in, bool c_reus
   visit(root);
   if (order.size() != plan.merges.size()) return "contraction tree is not connected to its root";
 
-  // Canonical lists per merge, and the storage layout of every operand.
-  struct Canon {
-    std::vector<int> m, n, k;
-  };
-  std::vector<Canon> canon(plan.merges.size());
-  std::vector<std::vector<int>> layout(T);
+  // Storage layout of each operand: its consumer's canonical order.
+  std::vector<Set> layout(T);
   for (size_t j = 0; j < plan.merges.size(); ++j) {
     const Merge& mg = plan.merges[j];
-    const auto& A = plan.tensors[mg.a];
-    const auto& B = plan.tensors[mg.b];
-    Canon& c = canon[j];
-    c.k = set_and(A, B);
-    c.m = set_minus(A, B);
-    c.n = set_minus(B, A);
-    if (c.m.size() + c.k.size() > 16 || c.n.size() + c.k.size() > 16 || c.m.size() + c.n.size() > 16)
-      return "a tensor of rank > 16 is beyond the on-chip executors";
-    layout[mg.a] = c.m;
-    layout[mg.a].insert(layout[mg.a].end(), c.k.begin(), c.k.end());
-    layout[mg.b] = c.k;
-    layout[mg.b].insert(layout[mg.b].end(), c.n.begin(), c.n.end());
+    const Canon& c = canon[j];
+    layout[mg.a] = concat(concat(c.m, c.k), c.b);
+    layout[mg.b] = concat(concat(c.k, c.n), c.b);
   }
 
-  // Leaves: [open legs in consumer order | cut legs by cut number].
-  std::vector<int> cut_no(net.indices.size(), -1);
-  for (size_t j = 0; j < plan.cuts.size(); ++j) cut_no[plan.cuts[j]] = (int)j;
+  // Leaves: [consumer layout | outer classes of the cut legs].
   pg.leaves.resize(n_leaves);
   uint32_t leaf_off = 0;
   for (int t = 0; t < n_leaves; ++t) {
     DevLeaf lf{};
     lf.base = leaf_off;
-    for (int b = 0; b < 8; ++b) lf.slot_of_bit[b] = -1;
-    if (unit_leaf && t == L) {
+    const Gate* g = leaf_gate(t);
+    if (!g) {
       lf.gate = -1;
-      lf.rank_nc = 0;
-      lf.ncut = 0;
     } else {
-      const Gate& g = net.gates[t];
       lf.gate = (int16_t)t;
-      const auto& lay = layout[t];
-      lf.rank_nc = (uint8_t)lay.size();
       int pos = 0;
-      for (int ix : lay) {
-        int slot = -1;
-        for (int s = 0; s < 4; ++s)
-          if (g.leg[s] == ix) slot = s;
-        if (slot < 0) return "leaf layout refers to an index the gate does not carry";
-        lf.slot_of_bit[pos++] = (int8_t)slot;
+      auto slots_of = [&](int id) -> uint8_t {
+        uint8_t mask = 0;
+        for (int s = 0; s < 4; ++s) {
+          int ix = g->leg[s];
+          if (ix < 0) continue;
+          if (id < I ? ix == id : (cut_no[ix] >= 0 && cls[cut_no[ix]] == id - I)) mask |= (uint8_t)(1u << s);
+        }
+        return mask;
+      };
+      for (int id : layout[t]) {
+        uint8_t mask = slots_of(id);
+        if (!mask) return "leaf layout refers to an index the gate does not carry";
+        lf.slot_mask[pos++] = mask;
       }
-      std::vector<std::pair<int, int>> cuts_here;  // (cut number, slot)
-      for (int s = 0; s < 4; ++s)
-        if (g.leg[s] >= 0 && cut_no[g.leg[s]] >= 0) cuts_here.push_back({cut_no[g.leg[s]], s});
-      std::sort(cuts_here.begin(), cuts_here.end());
-      if ((int)cuts_here.size() > kMaxLeafCuts) return "too many cut legs on one gate";
-      lf.ncut = (uint8_t)cuts_here.size();
-      for (size_t j = 0; j < cuts_here.size(); ++j) {
-        lf.cut_bit[j] = (uint8_t)cuts_here[j].first;
-        lf.slot_of_bit[pos++] = (int8_t)cuts_here[j].second;
+      lf.rank_nc = (uint8_t)pos;
+      std::vector<std::pair<int, int>> outer;  // (outer position, class)
+      for (int s = 0; s < 4; ++s) {
+        int ix = g->leg[s];
+        if (ix < 0 || cut_no[ix] < 0) continue;
+        int c = cls[cut_no[ix]];
+        if (!is_inner[c]) outer.push_back({cls_pos[c], c});
+      }
+      std::sort(outer.begin(), outer.end());
+      outer.erase(std::unique(outer.begin(), outer.end()), outer.end());
+      if ((int)outer.size() > kMaxLeafCuts || pos + (int)outer.size() > 8) return "too many cut legs on one gate";
+      lf.ncut = (uint8_t)outer.size();
+      for (size_t j = 0; j < outer.size(); ++j) {
+        lf.cut_bit[j] = (uint8_t)outer[j].first;
+        lf.slot_mask[pos++] = slots_of(I + outer[j].second);
       }
     }
     pg.max_rank = std::max(pg.max_rank, (int)lf.rank_nc);
@@ -160,54 +252,55 @@ std::string compile_program(const Network& net, const Plan& plan_in, bool c_reus
   pg.leaf_elems = leaf_off;
 
   Arena arena;
-  pg.c_reuses_operands = c_reuses_operands;
-  std::vector<uint32_t> to_release;
   std::vector<uint32_t> where(T, 0);
   for (int j : order) {
     const Merge& mg = plan.merges[j];
     const Canon& c = canon[j];
     DevStep st{};
-    int64_t a_block = -1;
     st.ma = (uint8_t)c.m.size();
     st.nb = (uint8_t)c.n.size();
     st.kb = (uint8_t)c.k.size();
-    st.flags = 0;
+    st.bb = (uint8_t)c.b.size();
+    std::vector<uint32_t> to_release;
+    int64_t a_block = -1;
     if (is_leaf(mg.a)) {
       st.flags |= STEP_A_LEAF;
-      st.a = (uint16_t)mg.a;
+      st.a = (uint32_t)mg.a;
     } else {
       st.a = where[mg.a];
-      a_block = (int64_t)where[mg.a];
+      a_block = where[mg.a];
     }
     if (is_leaf(mg.b)) {
       st.flags |= STEP_B_LEAF;
-      st.b = (uint16_t)mg.b;
+      st.b = (uint32_t)mg.b;
     } else {
       st.b = where[mg.b];
       to_release.push_back(where[mg.b]);
     }
-    int rc = (int)(c.m.size() + c.n.size());
-    pg.width = std::max(pg.width, (int)(c.m.size() + c.n.size() + c.k.size()));
+    const int rc = (int)(c.m.size() + c.n.size() + c.b.size());
+    const int wd = rc + (int)c.k.size();
+    pg.width = std::max(pg.width, wd);
     pg.max_rank = std::max(pg.max_rank, rc);
-    pg.macs_per_slice += std::ldexp(1.0, (int)(c.m.size() + c.n.size() + c.k.size()));
-    // A is read completely before the first store of C; B is streamed while
+    pg.macs_per_item += std::ldexp(1.0, wd);
+    // A is read completely before the first store of C; B may be read while
     // C is written, so only A's block may be reused by C.
     if (a_block >= 0) {
-      if (c_reuses_operands) arena.release((uint32_t)a_block);
+      if (opt.c_reuses_a) arena.release((uint32_t)a_block);
       else to_release.push_back((uint32_t)a_block);
     }
     if (mg.c == root) {
       st.flags |= STEP_ROOT;
       st.c = 0;
+      for (int id : concat(concat(c.m, c.n), c.b)) {
+        if (id < I) return "the root keeps a real index open";
+        pg.root_class.push_back(id - I);
+      }
     } else {
       uint32_t off = arena.alloc(1u << rc);
       where[mg.c] = off;
       st.c = off;
-      // canonical C bit b is index (b < |m| ? m[b] : n[b - |m|]); its storage
-      // bit is its position in C's consumer layout.
-      std::vector<int> canon_ix = c.m;
-      canon_ix.insert(canon_ix.end(), c.n.begin(), c.n.end());
-      const auto& lay = layout[mg.c];
+      const Set canon_ix = concat(concat(c.m, c.n), c.b);
+      const Set& lay = layout[mg.c];
       for (int b = 0; b < rc; ++b) {
         auto it = std::find(lay.begin(), lay.end(), canon_ix[b]);
         if (it == lay.end()) return "consumer layout misses an index";
@@ -215,7 +308,6 @@ std::string compile_program(const Network& net, const Plan& plan_in, bool c_reus
       }
     }
     for (uint32_t r : to_release) arena.release(r);
-    to_release.clear();
     pg.steps.push_back(st);
   }
   pg.arena_elems = std::max<uint32_t>(arena.high, 1);
@@ -234,6 +326,42 @@ std::string compile_program(const Network& net, const Plan& plan_in, bool c_reus
   }
   *out = std::move(pg);
   return "";
+}
+
+ProgramOptions choose_batched(const Network& net, const Plan& plan, uint32_t smem_elems, uint64_t min_items) {
+  ProgramOptions opt;
+  int nc = 0;
+  opt.cut_class = cut_classes(net, plan.cuts, &nc);
+  opt.inner.assign(nc, 0);
+  auto per_slice = [&](const ProgramOptions& o, Program* pg) -> double {
+    if (!compile_program(net, plan, o, pg).empty()) return -1.0;
+    if (pg->arena_elems + pg->leaf_elems > smem_elems) return -1.0;
+    return pg->macs_per_item / std::ldexp(1.0, pg->n_inner);
+  };
+  Program cur;
+  double best = per_slice(opt, &cur);
+  int n_inner = 0;
+  while (true) {
+    if (std::ldexp(1.0, nc - n_inner - 1) < (double)min_items) break;
+    int pick = -1;
+    double pick_cost = best;
+    for (int c = 0; c < nc; ++c) {
+      if (opt.inner[c]) continue;
+      ProgramOptions trial = opt;
+      trial.inner[c] = 1;
+      Program pg;
+      double v = per_slice(trial, &pg);
+      if (v >= 0 && v < pick_cost * 0.97) {
+        pick_cost = v;
+        pick = c;
+      }
+    }
+    if (pick < 0) break;
+    opt.inner[pick] = 1;
+    best = pick_cost;
+    ++n_inner;
+  }
+  return opt;
 }
 
 }  // namespace qtn

@@ -1,18 +1,29 @@
 // Step program: a contraction plan lowered to the flat form the device
-// kernels interpret.
+// executors interpret.
 //
-// Every pairwise merge C = A * B (Eq. 1) is executed in a canonical form:
-//   A stored as [m | k], B as [k | n], C computed as [m | n],
-// where m = A's free indices, n = B's free indices, k = shared (summed)
-// indices; bit 0 is the fastest.  Each tensor is stored in the canonical
-// order of the merge that consumes it, so operand loads are contiguous and
-// only the producer's store is permuted (per-merge bit weights).
+// Every pairwise merge C = A * B (Eq. 1) is executed in a canonical form
+//   A stored as [m | k | b], B as [k | n | b], C computed as [m | n | b],
+// where k = indices shared by A and B (summed), b = batch bits shared by A
+// and B (kept), m = the rest of A, n = the rest of B; bit 0 is the fastest.
+// Each tensor is stored in the canonical order of the merge that consumes
+// it, so operand loads are contiguous and only the producer's store is
+// permuted (per-merge bit weights).
 //
-// Leaves (gate tensors) live in a per-amplitude leaf table built on the device
-// in FP64 and rounded to the working precision.  A leaf's cut legs are its
-// highest bits, so the sub-block of slice s (Sec. III.A: the cut edges fixed
-// to the bits of s) is the contiguous block at offset
-//   sum_j bit(s, cut_bit_j) << (rank_nc + j).
+// Slices (Sec. III.A, Eq. 2).  The k cut indices are grouped into classes:
+// two cuts that are the input and output segment of one wire through a
+// diagonal ZZ gate can only take equal values in a non-zero slice, so they
+// form one class and the other slices (exactly zero) are never enumerated
+// by the batched executor.  Classes are either "outer" (fixed per work item:
+// the leaf sub-block is selected by an offset) or "inner" (carried as an
+// open batch index through the merges of one work item, so each merge runs
+// once per distinct value of the inner bits it depends on; the root then
+// holds one scalar per inner assignment, i.e. per slice).  With no inner
+// class and one class per cut this is the plain per-slice contraction.
+//
+// Leaves (gate tensors) live in a per-bit-string leaf table built on the
+// device in FP64 and rounded to the working precision.  A leaf's outer-class
+// bits are its highest bits, so the sub-block of a work item is the
+// contiguous block at offset sum_j bit(item, cut_bit_j) << (rank_nc + j).
 #pragma once
 #include <cstdint>
 #include <string>
@@ -24,46 +35,56 @@
 namespace qtn {
 
 constexpr int kMaxLeafCuts = 4;
+constexpr int kMaxRank = 16;
 
 // Leaf table entry; also carries what the leaf-build kernel needs.
 struct DevLeaf {
   uint32_t base;       // element offset in the leaf table
-  uint8_t rank_nc;     // legs kept open (low bits)
-  uint8_t ncut;        // cut legs (high bits), <= kMaxLeafCuts
-  uint8_t cut_bit[kMaxLeafCuts];  // slice bit fixing each cut leg
+  uint8_t rank_nc;     // layout bits read by the consumer (low bits)
+  uint8_t ncut;        // outer-class bits (high bits), <= kMaxLeafCuts
+  uint8_t cut_bit[kMaxLeafCuts];  // item bit fixing each high bit
   int16_t gate;        // gate id (-1: the constant scalar 1)
-  int8_t slot_of_bit[8];           // gate leg slot (0..3) at each layout bit
+  uint8_t slot_mask[8];           // gate leg slots (bit s = slot s) of each layout bit
 };
+static_assert(sizeof(DevLeaf) == 20, "DevLeaf layout");
 
 enum StepFlags : uint8_t {
   STEP_A_LEAF = 1,
   STEP_B_LEAF = 2,
-  STEP_ROOT = 4,  // C is the slice's scalar result
+  STEP_ROOT = 4,  // C is the work item's result: summed, not stored
 };
 
-constexpr int kMaxRank = 16;
-
-// One merge.  The canonical C element o = m + (n << ma) is stored at arena
-// offset c + sum_b bit(o, b) * w[b] (w: bit weights of C's storage layout).
+// One merge.  The canonical C element o = m + (n << ma) + (b << (ma + nb))
+// is stored at arena offset c + sum_i bit(o, i) * w[i].
 struct DevStep {
-  uint8_t ma, nb, kb;  // log2 sizes of m, n, k
-  uint8_t flags;
-  uint32_t a, b;       // leaf id or arena element offset
-  uint32_t c;          // arena element offset of C
+  uint8_t ma, nb, kb, bb;  // log2 sizes of m, n, k, b
+  uint8_t flags, pad0, pad1, pad2;
+  uint32_t a, b;           // leaf id or arena element offset
+  uint32_t c;              // arena element offset of C
   uint16_t w[kMaxRank];
 };
-static_assert(sizeof(DevStep) == 48, "DevStep layout");
+static_assert(sizeof(DevStep) == 52, "DevStep layout");
+
+struct ProgramOptions {
+  bool c_reuses_a = false;        // C may overwrite A's arena block
+  std::vector<int> cut_class;     // class of each cut (size k); empty = one class per cut
+  std::vector<char> inner;        // per class: carried as a batch index
+};
 
 struct Program {
   int n = 0, p = 0, k = 0;
+  int n_classes = 0;                 // slice classes (non-zero slices = 2^n_classes)
+  int n_outer = 0, n_inner = 0;      // outer / inner classes
+  std::vector<int> outer_class;      // outer bit position -> class
+  std::vector<int> inner_class;      // inner bit position -> class
+  std::vector<int> root_class;       // class of each canonical bit of the root's output
   std::vector<DevLeaf> leaves;
   std::vector<DevStep> steps;
   uint32_t leaf_elems = 0;           // elements in one leaf table
-  uint32_t arena_elems = 0;          // per-slice arena (elements)
-  bool c_reuses_operands = false;    // arena lets C overlap A (never B)
-  int width = 0;                     // max ma + nb + kb
-  int max_rank = 0;                  // max tensor rank in the program
-  double macs_per_slice = 0;         // sum 2^(ma+nb+kb)
+  uint32_t arena_elems = 0;          // per-item arena (elements)
+  int width = 0;                     // max ma + nb + kb + bb
+  int max_rank = 0;                  // max tensor rank (with batch bits)
+  double macs_per_item = 0;          // sum 2^(ma+nb+kb+bb)
   // Gate data for the leaf-build kernel.
   std::vector<int32_t> gate_q;       // 2 per gate
   std::vector<int8_t> gate_layer;
@@ -71,11 +92,18 @@ struct Program {
   std::vector<int8_t> gate_out_kind; // 2 per gate
 };
 
-// Lowers `plan` (merges over `net`) to a program.  With `c_reuses_operands`
-// the arena lets a merge's result overwrite its A operand (for executors that
-// read A completely before the first store of C; B may still be read while C
-// is written).  Returns "" or an error.
-std::string compile_program(const Network& net, const Plan& plan, bool c_reuses_operands,
-                            Program* out);
+// Lowers `plan` (merges over `net`) to a program.  Returns "" or an error.
+std::string compile_program(const Network& net, const Plan& plan, const ProgramOptions& opt, Program* out);
+
+// Classes of the plan's cuts: cuts that are the in and out segment of one
+// wire through a ZZ gate whose out leg is plain (a diagonal delta) must take
+// equal values in every non-zero slice.  Returns the class of each cut and
+// sets *n_classes.
+std::vector<int> cut_classes(const Network& net, const std::vector<int>& cuts, int* n_classes);
+
+// Chooses inner classes greedily (largest MAC saving first) while the
+// program's arena + leaf table fit `smem_elems` elements and at least
+// `min_items` work items remain per bit string.
+ProgramOptions choose_batched(const Network& net, const Plan& plan, uint32_t smem_elems, uint64_t min_items);
 
 }  // namespace qtn

@@ -1,9 +1,10 @@
 """Test-only CPU emulation of a compiled step program (complex128).
 
 Reads the JSON of ``qtn_plan_describe`` and runs the same program the device
-executors run -- leaf tables, canonical [m|k] x [k|n] merges, permuted
-stores, sliced leaf sub-blocks -- so the host-side compiler (layouts, bit
-weights, arena offsets, leaf layouts) can be checked against the oracle
+executors run -- leaf tables, canonical [m|k|b] x [k|n|b] merges, permuted
+stores, leaf sub-blocks selected by the outer slice classes, batch bits for
+the inner classes -- so the host-side compiler (layouts, bit weights, arena
+offsets, leaf layouts, cut classes) can be checked against the oracle
 without a GPU.  The gate-tensor values are written here from the circuit
 definition (ZZ phase exp(-i g s0 s1), RX(2b) = [[cos b, -i sin b],
 [-i sin b, cos b]], H|0> = (1, 1)), independently of the CUDA leaf kernel.
@@ -39,62 +40,104 @@ def gate_entry(gate, gamma, beta, x, v):
     return total
 
 
-def leaf_table(desc, which, gamma, beta, x):
-    pg = desc["programs"][which]
-    lt = np.zeros(max(pg["leaf_elems"], 1), dtype=complex)
-    for L in pg["leaves"]:
+def leaf_table(desc, prog, gamma, beta, x):
+    lt = np.zeros(max(prog["leaf_elems"], 1), dtype=complex)
+    for L in prog["leaves"]:
         r = L["rank_nc"] + len(L["cut_bit"])
         for e in range(1 << r):
             if L["gate"] < 0:
                 val = 1.0
             else:
                 v = [-1] * 4
-                for bit, slot in enumerate(L["slot_of_bit"]):
-                    v[slot] = (e >> bit) & 1
+                for bit, mask in enumerate(L["slot_mask"]):
+                    for sl in range(4):
+                        if (mask >> sl) & 1:
+                            v[sl] = (e >> bit) & 1
                 val = gate_entry(desc["gates"][L["gate"]], gamma, beta, x, v)
             lt[L["base"] + e] = val
     return lt
 
 
-def run_slice(desc, which, lt, s):
-    """Unnormalised scalar of slice s."""
-    pg = desc["programs"][which]
-    leaves = pg["leaves"]
-    arena = np.zeros(max(pg["arena_elems"], 1) + 64, dtype=complex)
-    res = None
+def run_item(prog, lt, item):
+    """Root outputs of one work item (a slice, or an outer-class assignment
+    whose root holds one scalar per inner assignment), unnormalised."""
+    leaves = prog["leaves"]
+    lane = prog["executor"] == "lane"
+    arena = np.zeros(max(prog["arena_elems"], 1) + 64, dtype=complex)
 
-    def operand(is_leaf, ref, size):
-        if is_leaf:
-            L = leaves[ref]
-            off = L["base"]
-            for j, cb in enumerate(L["cut_bit"]):
-                off += ((s >> cb) & 1) << (L["rank_nc"] + j)
-            return lt[off:off + size].copy()
-        return arena[ref:ref + size].copy()
+    def leaf_off(ref):
+        L = leaves[ref]
+        off = L["base"]
+        for j, cb in enumerate(L["cut_bit"]):
+            off += ((item >> cb) & 1) << (L["rank_nc"] + j)
+        return off
 
-    for st in pg["steps"]:
-        ma, nb, kb = st["ma"], st["nb"], st["kb"]
-        rc = ma + nb
-        # Same read/write order as the lane executor: A is read whole, then
-        # for each column n the k entries of B are read and the column of C
-        # is stored (so a store that clobbers unread B data shows up here).
-        A = operand(st["flags"] & 1, st["a"], 1 << (ma + kb))
-        Am = A.reshape(1 << kb, 1 << ma).T      # A[m + (k << ma)] -> Am[m, k]
-        for n in range(1 << nb):
-            if st["flags"] & 2:
-                L = leaves[st["b"]]
-                off = L["base"]
-                for j, cb in enumerate(L["cut_bit"]):
-                    off += ((s >> cb) & 1) << (L["rank_nc"] + j)
-                col = lt[off + (n << kb): off + ((n + 1) << kb)].copy()
+    root = None
+    for st in prog["steps"]:
+        ma, nb, kb, bb = st["ma"], st["nb"], st["kb"], st["bb"]
+        rc = ma + nb + bb
+        na, nbe = 1 << (ma + kb + bb), 1 << (kb + nb + bb)
+        src_a = lt if st["flags"] & 1 else arena
+        src_b = lt if st["flags"] & 2 else arena
+        a0 = leaf_off(st["a"]) if st["flags"] & 1 else st["a"]
+        b0 = leaf_off(st["b"]) if st["flags"] & 2 else st["b"]
+        A = src_a[a0:a0 + na].copy()
+        out = np.zeros(1 << rc, dtype=complex)
+        is_root = st["flags"] & 4
+
+        def store(o, v):
+            if is_root:
+                out[o] = v
             else:
-                col = arena[st["b"] + (n << kb): st["b"] + ((n + 1) << kb)].copy()
-            Ccol = Am @ col                      # C[m, n] for this n
-            if st["flags"] & 4:
-                res = Ccol[0]
-                continue
-            for m in range(1 << ma):
-                o = m + (n << ma)
                 pos = sum(st["w"][j] for j in range(rc) if (o >> j) & 1)
-                arena[st["c"] + pos] = Ccol[m]
-    return res
+                arena[st["c"] + pos] = v
+
+        if lane:
+            # The lane executor reads A whole, then per column n reads B's
+            # column and stores C's column (so a store that clobbers unread
+            # B data shows up here).
+            assert bb == 0
+            Am = A.reshape(1 << kb, 1 << ma).T
+            for n in range(1 << nb):
+                col = src_b[b0 + (n << kb): b0 + ((n + 1) << kb)].copy()
+                Ccol = Am @ col
+                for m in range(1 << ma):
+                    store(m + (n << ma), Ccol[m])
+        else:
+            B = src_b[b0:b0 + nbe].copy()
+            Ab = A.reshape(1 << bb, 1 << kb, 1 << ma)     # [b, k, m]
+            Bb = B.reshape(1 << bb, 1 << nb, 1 << kb)     # [b, n, k]
+            C = np.einsum("bkm,bnk->bnm", Ab, Bb)          # [b, n, m]
+            for o in range(1 << rc):
+                m, n, bch = o & ((1 << ma) - 1), (o >> ma) & ((1 << nb) - 1), o >> (ma + nb)
+                store(o, C[bch, n, m])
+        if is_root:
+            root = out
+    return root
+
+
+def slice_of(prog, cut_class, item, o):
+    """Slice id (cut j <- bit j) of root output o of work item `item`."""
+    cls_val = {}
+    for pos, c in enumerate(prog["outer_class"]):
+        cls_val[c] = (item >> pos) & 1
+    for bit, c in enumerate(prog["root_class"]):
+        cls_val[c] = (o >> bit) & 1
+    s = 0
+    for j, c in enumerate(cut_class):
+        s |= cls_val[c] << j
+    return s
+
+
+def run_program(desc, name, gamma, beta, x):
+    """{slice id: unnormalised value} over the slices the program enumerates."""
+    prog = desc["programs"][name]
+    lt = leaf_table(desc, prog, gamma, beta, x)
+    trivial = list(range(len(desc["cuts"])))
+    cut_class = trivial if name == desc["executor"] else desc["cut_class"]
+    vals = {}
+    for item in range(1 << len(prog["outer_class"])):
+        out = run_item(prog, lt, item)
+        for o, v in enumerate(out):
+            vals[slice_of(prog, cut_class, item, o)] = v
+    return vals

@@ -193,20 +193,30 @@ def oracle_cuts(plan):
     return plan.cut_names()
 
 
-@pytest.mark.parametrize("which", ["lane", "block"])
-@pytest.mark.parametrize("n,p,k,seed", [(12, 1, 3, 1), (16, 1, 2, 1), (14, 2, 4, 6)])
-def test_emulated_program_matches_oracle_per_slice(which, n, p, k, seed):
+@pytest.mark.parametrize("n,p,k,seed", [(12, 1, 3, 1), (16, 1, 2, 1), (14, 2, 4, 6), (24, 1, 8, 2), (40, 2, 6, 2)])
+def test_emulated_programs_match_oracle_per_slice(n, p, k, seed):
+    # Every compiled program of the plan (the per-slice one and the
+    # throughput ones: cut classes, batched inner classes) reproduces the
+    # oracle's slice values; slices a program skips are exactly zero.
     inst = I.qaoa_instance(n, p, seed)
     net = qtn.Network(n, inst.edges, inst.gamma, inst.beta)
     plan = qtn.Plan(net, k=k)
     d = plan.describe()
     x = I.bitstrings(n, 1, seed)[0]
-    ref = O.tn_amplitude(n, inst.edges, inst.gamma, inst.beta, x, cuts=oracle_cuts(plan), per_slice=True)
-    lt = E.leaf_table(d, which, inst.gamma, inst.beta, x)
+    ref = O.tn_amplitude(n, inst.edges, inst.gamma, inst.beta, x, cuts=plan.cut_names(), per_slice=True,
+                         threads=4)
     scale = 2.0 ** (-n / 2)
-    got = np.array([E.run_slice(d, which, lt, s) for s in range(1 << k)]) * scale
-    assert np.max(np.abs(got - ref.per_slice)) < 1e-13 * max(1.0, np.max(np.abs(ref.per_slice)))
-    assert abs(got.sum() - ref.value) < 1e-13
+    mag = np.max(np.abs(ref.per_slice))
+    for name in d["programs"]:
+        vals = E.run_program(d, name, inst.gamma, inst.beta, x)
+        got = np.zeros(1 << k, dtype=complex)
+        for s_id, v in vals.items():
+            got[s_id] = v * scale
+        assert np.max(np.abs(got - ref.per_slice)) < 1e-13 * mag, name
+        skipped = np.ones(1 << k, bool)
+        skipped[list(vals)] = False
+        assert np.all(ref.per_slice[skipped] == 0), name
+        assert abs(got.sum() - ref.value) < 1e-13 * np.sum(np.abs(ref.per_slice)), name
 
 
 def test_emulated_program_n80_sampled_slices():
@@ -216,12 +226,28 @@ def test_emulated_program_n80_sampled_slices():
     plan = qtn.Plan(net, k=16)
     d = plan.describe()
     x = I.bitstrings(n, 1, 3)[0]
-    lt = E.leaf_table(d, d["executor"], inst.gamma, inst.beta, x)
+    prog = d["programs"][d["executor"]]
+    lt = E.leaf_table(d, prog, inst.gamma, inst.beta, x)
     scale = 2.0 ** (-n / 2)
     for s in (0, 1, 12345, 65535):
         ref = O.tn_amplitude(n, inst.edges, inst.gamma, inst.beta, x, cuts=plan.cut_names(), slices=(s, s + 1))
-        got = E.run_slice(d, d["executor"], lt, s) * scale
+        got = E.run_item(prog, lt, s)[0] * scale
         assert abs(got - ref.value) < 1e-12 * abs(ref.value) + 1e-30
+
+
+def test_cut_classes_and_batched_programs_n80():
+    # The 16 greedy cuts of the n = 80 workload contain one diagonal pair:
+    # 15 classes, so half of the 65536 slices are never enumerated; the
+    # batched program carries some classes as batch bits.
+    inst = I.qaoa_instance(80, 1, 3)
+    net = qtn.Network(80, inst.edges, inst.gamma, inst.beta)
+    d = qtn.Plan(net, k=16).describe()
+    assert max(d["cut_class"]) + 1 == 15
+    batched = [v for k, v in d["programs"].items() if k.startswith("batched")]
+    assert batched and all(len(v["inner_class"]) >= 1 for v in batched)
+    per_slice = d["programs"][d["executor"]]["macs_per_item"]
+    for v in batched:
+        assert v["macs_per_item"] / 2 ** len(v["inner_class"]) < per_slice
 
 
 def test_plan_cost_matches_counter_and_cap():
