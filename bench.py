@@ -157,6 +157,9 @@ def run_ours(args, rank, world, local_rank):
     d_out = torch.zeros((nx, 2), dtype=torch.float64, device="cuda")
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")  # > 129 MB L2
 
+    if args.executor:
+        plan.select_executor(args.executor, args.precision, nx)
+
     def step():
         plan.contract_amplitudes_device(d_x, d_out, args.precision, stream)
 
@@ -349,6 +352,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--executor", default=None, help="force an executor (default: autotuned)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -201,6 +201,12 @@ qtn_status qtn_contract_batch(const qtn_plan_t* const* plans, const uint8_t* con
  * plans with every tensor rank <= 5; "block": one slice per thread block). */
 qtn_status qtn_plan_executor(const qtn_plan_t* plan, const char** name);
 
+/* Overrides the autotuner: contraction calls of (prec, nx) use the executor
+ * called `name` (one of the names in qtn_plan_describe's "programs", other
+ * than the per-slice program).  Fails with QTN_ERR_INVALID_ARG for an unknown
+ * name or one compiled for the other precision. */
+qtn_status qtn_plan_select_executor(const qtn_plan_t* plan, qtn_precision prec, int nx, const char* name);
+
 /* Kernel timing for measurement: when on, qtn_contract_amplitudes_device
  * launches its three kernels directly (no graph replay) and records CUDA
  * events on the launching stream just before and after the executor kernel;

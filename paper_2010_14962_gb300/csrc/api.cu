@@ -158,6 +158,9 @@ struct qtn_plan {
     dev_allocs.push_back(leaves);
     QTN_CUDA(::upload(&steps, pg.steps));
     dev_allocs.push_back(steps);
+    DevStep* pro;
+    QTN_CUDA(::upload(&pro, pg.prologue));
+    dev_allocs.push_back(pro);
     QTN_CUDA(::upload(&gq, pg.gate_q));
     dev_allocs.push_back(gq);
     QTN_CUDA(::upload(&gl, pg.gate_layer));
@@ -181,6 +184,9 @@ struct qtn_plan {
     d.exec = sl.exec;
     d.leaves = leaves;
     d.steps = steps;
+    d.pro_steps = pro;
+    d.n_pro_steps = (int)pg.prologue.size();
+    d.pro_arena_elems = pg.pro_arena_elems;
     d.gate_q = gq;
     d.gate_layer = gl;
     d.gate_in_h = gi;
@@ -492,15 +498,21 @@ qtn_status qtn_plan(const qtn_network_t* net, const int32_t* cuts, int k, const 
     const char* name;
     uint32_t elems;
     bool fp64;
-  } budgets[] = {{"batched/fp32/48KiB", 6 * 1024, false},
-                 {"batched/fp32/192KiB", 24 * 1024, false},
-                 {"batched/fp64/48KiB", 3 * 1024, true},
-                 {"batched/fp64/192KiB", 12 * 1024, true}};
+    bool warp;
+  } budgets[] = {{"batched-warp/fp32/8KiB", 1024, false, true},
+                 {"batched-warp/fp32/24KiB", 3 * 1024, false, true},
+                 {"batched/fp32/48KiB", 6 * 1024, false, false},
+                 {"batched/fp32/192KiB", 24 * 1024, false, false},
+                 {"batched-warp/fp64/8KiB", 512, true, true},
+                 {"batched-warp/fp64/24KiB", 1536, true, true},
+                 {"batched/fp64/48KiB", 3 * 1024, true, false},
+                 {"batched/fp64/192KiB", 12 * 1024, true, false}};
   for (const Budget& bd : budgets) {
+    // Arena budget per item; warp executors run 8 items per block.
     ProgramOptions o = choose_batched(h->net, h->plan, bd.elems, 64);
     ProgSlot sl;
     sl.name = bd.name;
-    sl.exec = Executor::Block;
+    sl.exec = bd.warp ? Executor::Warp : Executor::Block;
     sl.fp64_only = bd.fp64;
     sl.fp32_only = !bd.fp64;
     if (!compile_program(h->net, h->plan, o, &sl.prog).empty()) continue;
@@ -549,6 +561,23 @@ qtn_status set_error(qtn_status s, const std::string& msg) { return fail(s, msg)
 }  // namespace qtn
 
 extern "C" {
+
+qtn_status qtn_plan_select_executor(const qtn_plan_t* cplan, qtn_precision prec, int nx, const char* name) {
+  qtn_plan_t* plan = const_cast<qtn_plan_t*>(cplan);
+  if (!plan || !name || nx <= 0) return fail(QTN_ERR_INVALID_ARG, "bad argument");
+  std::lock_guard<std::mutex> lk(plan->mu);
+  for (int si = 1; si < (int)plan->slots.size(); ++si)
+    if (plan->slots[si].name == name) {
+      if (!plan->eligible(si, prec)) return fail(QTN_ERR_INVALID_ARG, "executor not available for this precision");
+      auto key = std::make_pair((int)prec, nx);
+      plan->tuned[key] = si;
+      plan->tune_ms[key] = std::vector<double>(plan->slots.size(), -1.0);
+      for (auto& g : plan->graphs) cudaGraphExecDestroy(g.second);
+      plan->graphs.clear();
+      return QTN_OK;
+    }
+  return fail(QTN_ERR_INVALID_ARG, std::string("no executor named ") + name);
+}
 
 qtn_status qtn_plan_set_kernel_timing(const qtn_plan_t* cplan, int on) {
   qtn_plan_t* plan = const_cast<qtn_plan_t*>(cplan);
@@ -772,7 +801,9 @@ qtn_status qtn_plan_describe(const qtn_plan_t* plan, char* buf, size_t cap, size
     o << (which ? "," : "") << "\"" << plan->slots[which].name << "\":{\"leaf_elems\":" << pg.leaf_elems
       << ",\"arena_elems\":" << pg.arena_elems << ",\"width\":" << pg.width << ",\"max_rank\":" << pg.max_rank
       << ",\"macs_per_item\":" << pg.macs_per_item << ",\"n_classes\":" << pg.n_classes
-      << ",\"executor\":\"" << (plan->slots[which].exec == Executor::Lane ? "lane" : "block") << "\",\"outer_class\":";
+      << ",\"executor\":\""
+      << (plan->slots[which].exec == Executor::Lane ? "lane" : plan->slots[which].exec == Executor::Warp ? "warp" : "block")
+      << "\",\"outer_class\":";
     json_ints(o, pg.outer_class.data(), pg.outer_class.size());
     o << ",\"inner_class\":";
     json_ints(o, pg.inner_class.data(), pg.inner_class.size());
@@ -791,9 +822,12 @@ qtn_status qtn_plan_describe(const qtn_plan_t* plan, char* buf, size_t cap, size
       json_ints(o, sb, L.rank_nc + L.ncut);
       o << "}";
     }
-    o << "],\"steps\":[";
-    for (size_t i = 0; i < pg.steps.size(); ++i) {
-      const DevStep& st = pg.steps[i];
+    o << "],\"pro_arena_elems\":" << pg.pro_arena_elems << ",\"macs_prologue\":" << pg.macs_prologue;
+    for (int pass = 0; pass < 2; ++pass) {
+    const std::vector<DevStep>& steps = pass ? pg.steps : pg.prologue;
+    o << (pass ? ",\"steps\":[" : ",\"prologue\":[");
+    for (size_t i = 0; i < steps.size(); ++i) {
+      const DevStep& st = steps[i];
       int w[kMaxRank];
       const int rc = st.ma + st.nb + st.bb;
       for (int j = 0; j < rc; ++j) w[j] = st.w[j];
@@ -803,7 +837,9 @@ qtn_status qtn_plan_describe(const qtn_plan_t* plan, char* buf, size_t cap, size
       json_ints(o, w, rc);
       o << "}";
     }
-    o << "]}";
+    o << "]";
+    }
+    o << "}";
   }
   o << "},\"cut_class\":";
   {

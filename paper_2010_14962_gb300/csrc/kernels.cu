@@ -114,6 +114,7 @@ __global__ void leaf_build_kernel(const DevLeaf* __restrict__ leaves, const int3
                                   uint32_t leaf_elems, int n_leaves, V* __restrict__ out) {
   const DevLeaf L = leaves[blockIdx.x % n_leaves];
   const int xi = blockIdx.x / n_leaves;
+  if (L.gate == -2) return;  // pseudo-leaf: written by the prologue kernel
   const int r = L.rank_nc + L.ncut;
   for (int e = threadIdx.x; e < (1 << r); e += blockDim.x) {
     double re = 1.0, im = 0.0;
@@ -309,21 +310,80 @@ __global__ void __launch_bounds__(128) lane_exec_kernel(ExecParams P, int* err) 
 
 // ------------------------------------------------------------ block exec --
 
-// One work item per thread block at a time: an item is one slice (per-slice
-// programs) or one assignment of the outer slice classes (batched programs,
-// whose tensors carry the inner classes as batch bits: every merge then runs
-// once per distinct value of the inner bits it depends on, and the root holds
-// the scalars of all slices of the item).  Threads split the output elements
-// of each merge; a barrier separates merges.
+// One merge executed by a group of G threads (G = 32: one warp; G = block
+// size), thread t of the group: outputs o = t, t + G, ... of the canonical
+// C[m, n, b] = sum_k A[m + (k << ma) + (b << (ma+kb))] * B[k + (n << kb) +
+// (b << (kb+nb))].  Results are stored at c + pos(o) (bit weights w), or,
+// for the root, added to the thread's compensated sum.
+template <class V, int K>
+__device__ __forceinline__ void group_merge_k(const DevStep& st, const V* __restrict__ A, const V* __restrict__ B,
+                                              V* __restrict__ C, uint32_t t, uint32_t G, uint32_t pos_t,
+                                              int log2G, bool root, double& sr, double& cr, double& si,
+                                              double& ci, double2* slice_out) {
+  const int ma = st.ma, nb = st.nb, kb = st.kb, rc = st.ma + st.nb + st.bb;
+  const uint32_t NC = 1u << rc;
+  const uint32_t mmask = (1u << ma) - 1u, nmask = (1u << nb) - 1u;
+  for (uint32_t o = t; o < NC; o += G) {
+    const uint32_t m = o & mmask, n = (o >> ma) & nmask, b = o >> (ma + nb);
+    const V* ap = A + m + (b << (ma + kb));
+    const V* bp = B + (n << kb) + (b << (kb + nb));
+    V acc = CplxOps<V>::zero();
+    if (K > 0) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) CplxOps<V>::fma(acc, ap[k << ma], bp[k]);
+    } else {
+      for (uint32_t k = 0; k < (1u << kb); ++k) CplxOps<V>::fma(acc, ap[k << ma], bp[k]);
+    }
+    if (root) {
+      kahan_add(sr, cr, (double)acc.x);
+      kahan_add(si, ci, (double)acc.y);
+      if (slice_out && NC == 1) *slice_out = make_double2((double)acc.x, (double)acc.y);
+    } else {
+      uint32_t pos = pos_t;
+      for (uint32_t hi = o >> log2G; hi; hi &= hi - 1u) pos += st.w[log2G + __ffs(hi) - 1];
+      C[pos] = acc;
+    }
+  }
+}
+
 template <class V>
+__device__ __forceinline__ void group_merge(const DevStep& st, const V* A, const V* B, V* C, uint32_t t,
+                                            uint32_t G, int log2G, double& sr, double& cr, double& si, double& ci,
+                                            double2* slice_out) {
+  const bool root = st.flags & STEP_ROOT;
+  const int rc = st.ma + st.nb + st.bb;
+  if (t >= (1u << rc)) return;  // no output of this merge for the thread
+  // Store offset of the thread's own low bits, shared by all its outputs.
+  uint32_t pos_t = 0;
+  if (!root)
+    for (int bit = 0; bit < log2G && bit < rc; ++bit)
+      if ((t >> bit) & 1u) pos_t += st.w[bit];
+  switch (st.kb) {
+    case 0: group_merge_k<V, 1>(st, A, B, C, t, G, pos_t, log2G, root, sr, cr, si, ci, slice_out); break;
+    case 1: group_merge_k<V, 2>(st, A, B, C, t, G, pos_t, log2G, root, sr, cr, si, ci, slice_out); break;
+    case 2: group_merge_k<V, 4>(st, A, B, C, t, G, pos_t, log2G, root, sr, cr, si, ci, slice_out); break;
+    case 3: group_merge_k<V, 8>(st, A, B, C, t, G, pos_t, log2G, root, sr, cr, si, ci, slice_out); break;
+    case 4: group_merge_k<V, 16>(st, A, B, C, t, G, pos_t, log2G, root, sr, cr, si, ci, slice_out); break;
+    default: group_merge_k<V, 0>(st, A, B, C, t, G, pos_t, log2G, root, sr, cr, si, ci, slice_out); break;
+  }
+}
+
+// Work items: a slice (per-slice programs) or one assignment of the outer
+// slice classes (batched programs, whose tensors carry the inner classes as
+// batch bits: every merge then runs once per distinct value of the inner
+// bits it depends on, and the root holds the scalars of all slices of the
+// item).  WARP_ITEMS: every warp contracts its own items in its own arena
+// (barriers are warp barriers); otherwise the whole block works on one item.
+template <class V, bool WARP_ITEMS>
 __global__ void __launch_bounds__(256) block_exec_kernel(ExecParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int T = blockDim.x;
-  const SmemLayout lay = smem_layout(P.n_steps, P.n_leaves, P.leaf_elems, P.arena_elems, (int)sizeof(V), T, false);
+  const int groups = WARP_ITEMS ? T / 32 : 1;
+  const SmemLayout lay =
+      smem_layout(P.n_steps, P.n_leaves, P.leaf_elems, P.arena_elems * groups, (int)sizeof(V), T, false);
   DevStep* s_steps = reinterpret_cast<DevStep*>(smem);
   DevLeaf* s_leaves = reinterpret_cast<DevLeaf*>(smem + lay.leaves);
   V* s_lt = reinterpret_cast<V*>(smem + lay.table);
-  V* s_arena = reinterpret_cast<V*>(smem + lay.arena);
   Partial* s_red = reinterpret_cast<Partial*>(smem + lay.red);
   const int xi = blockIdx.x / P.blocks_per_x;
   const int bx = blockIdx.x % P.blocks_per_x;
@@ -333,50 +393,74 @@ __global__ void __launch_bounds__(256) block_exec_kernel(ExecParams P) {
              (size_t)P.leaf_elems * sizeof(V));
   __syncthreads();
 
+  const uint32_t G = WARP_ITEMS ? 32u : (uint32_t)T;
+  const int log2G = 31 - __clz((int)G);
+  const int grp = WARP_ITEMS ? threadIdx.x / 32 : 0;
+  const uint32_t t = threadIdx.x % G;
+  V* s_arena = reinterpret_cast<V*>(smem + lay.arena) + (size_t)grp * P.arena_elems;
   double sr = 0.0, si = 0.0, cr = 0.0, ci = 0.0;
   const uint64_t S = P.slice_hi - P.slice_lo;
-  for (uint64_t i = bx; i < S; i += P.blocks_per_x) {
+  const uint64_t stride = (uint64_t)P.blocks_per_x * groups;
+  for (uint64_t i = (uint64_t)bx * groups + grp; i < S; i += stride) {
     const uint64_t s = P.slice_lo + i;
+    double2* slice_out = P.slices ? P.slices + (size_t)xi * S + i : nullptr;
     for (int j = 0; j < P.n_steps; ++j) {
       const DevStep& st = s_steps[j];
-      const V* A = (st.flags & STEP_A_LEAF) ? s_lt + leaf_offset(s_leaves[st.a], s) : s_arena + st.a;
-      const V* B = (st.flags & STEP_B_LEAF) ? s_lt + leaf_offset(s_leaves[st.b], s) : s_arena + st.b;
-      const int ma = st.ma, nb = st.nb, kb = st.kb, rc = st.ma + st.nb + st.bb;
-      const uint32_t NC = 1u << rc, K = 1u << kb;
-      const uint32_t mmask = (1u << ma) - 1u, nmask = (1u << nb) - 1u;
-      const bool root = st.flags & STEP_ROOT;
-      for (uint32_t o = threadIdx.x; o < NC; o += T) {
-        const uint32_t m = o & mmask, n = (o >> ma) & nmask, b = o >> (ma + nb);
-        const V* ap = A + m + (b << (ma + kb));
-        const V* bp = B + (n << kb) + (b << (kb + nb));
-        V acc = CplxOps<V>::zero();
-        for (uint32_t k = 0; k < K; ++k) CplxOps<V>::fma(acc, ap[k << ma], bp[k]);
-        if (root) {
-          kahan_add(sr, cr, (double)acc.x);
-          kahan_add(si, ci, (double)acc.y);
-          if (P.slices && NC == 1) P.slices[(size_t)xi * S + i] = make_double2((double)acc.x, (double)acc.y);
-        } else {
-          uint32_t pos = 0;
-          for (int bit = 0; bit < rc; ++bit)
-            if ((o >> bit) & 1u) pos += st.w[bit];
-          s_arena[st.c + pos] = acc;
-        }
+      if (t < (1u << (st.ma + st.nb + st.bb))) {
+        const V* A = (st.flags & STEP_A_LEAF) ? s_lt + leaf_offset(s_leaves[st.a], s) : s_arena + st.a;
+        const V* B = (st.flags & STEP_B_LEAF) ? s_lt + leaf_offset(s_leaves[st.b], s) : s_arena + st.b;
+        group_merge<V>(st, A, B, s_arena + st.c, t, G, log2G, sr, cr, si, ci, slice_out);
       }
-      __syncthreads();
+      if (WARP_ITEMS) __syncwarp();
+      else __syncthreads();
     }
   }
   s_red[threadIdx.x] = Partial::make(sr, si, cr, ci);
   __syncthreads();
   if (threadIdx.x == 0) {
     double a = 0, b = 0, ca = 0, cb = 0;
-    for (int t = 0; t < T; ++t) {
-      const Partial v = s_red[t];
+    for (int tt = 0; tt < T; ++tt) {
+      const Partial v = s_red[tt];
       kahan_add(a, ca, v.re);
       kahan_add(a, ca, -v.cre);
       kahan_add(b, cb, v.im);
       kahan_add(b, cb, -v.cim);
     }
     P.partials[(size_t)xi * P.blocks_per_x + bx] = Partial::make(a, b, ca, cb);
+  }
+}
+
+// -------------------------------------------------------------- prologue --
+
+// Hoisted merges (no outer slice class below them): run once per bit string
+// (one block each); exported results become pseudo-leaves of the leaf table.
+template <class V>
+__global__ void __launch_bounds__(256) prologue_kernel(const DevStep* __restrict__ steps, int n_steps,
+                                                       const DevLeaf* __restrict__ leaves, int n_leaves,
+                                                       void* leaf_tables, uint32_t leaf_elems, uint32_t arena_elems) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int T = blockDim.x;
+  const SmemLayout lay = smem_layout(n_steps, n_leaves, leaf_elems, arena_elems, (int)sizeof(V), T, false);
+  DevStep* s_steps = reinterpret_cast<DevStep*>(smem);
+  DevLeaf* s_leaves = reinterpret_cast<DevLeaf*>(smem + lay.leaves);
+  V* s_lt = reinterpret_cast<V*>(smem + lay.table);
+  V* s_arena = reinterpret_cast<V*>(smem + lay.arena);
+  V* g_lt = static_cast<V*>(leaf_tables) + (size_t)blockIdx.x * leaf_elems;
+  copy_words(s_steps, steps, (size_t)n_steps * sizeof(DevStep));
+  copy_words(s_leaves, leaves, (size_t)n_leaves * sizeof(DevLeaf));
+  copy_words(s_lt, g_lt, (size_t)leaf_elems * sizeof(V));
+  __syncthreads();
+  const int log2G = 31 - __clz(T);
+  double sr = 0, si = 0, cr = 0, ci = 0;
+  for (int j = 0; j < n_steps; ++j) {
+    const DevStep& st = s_steps[j];
+    if (threadIdx.x < (1u << (st.ma + st.nb + st.bb))) {
+      const V* A = (st.flags & STEP_A_LEAF) ? s_lt + s_leaves[st.a].base : s_arena + st.a;
+      const V* B = (st.flags & STEP_B_LEAF) ? s_lt + s_leaves[st.b].base : s_arena + st.b;
+      V* C = (st.flags & STEP_EXPORT) ? g_lt + s_leaves[st.c].base : s_arena + st.c;
+      group_merge<V>(st, A, B, C, threadIdx.x, T, log2G, sr, cr, si, ci, nullptr);
+    }
+    __syncthreads();
   }
 }
 
@@ -418,54 +502,81 @@ int g_num_sms = 0;
 
 }  // namespace
 
+namespace {
+template <class K>
+bool shape_for_kernel(K kernel, int threads, size_t smem, int* occ) {
+  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return false;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kernel, threads, smem) == cudaSuccess && *occ >= 1;
+}
+}  // namespace
+
 bool exec_shape(const DeviceProgram& prog, int elem_bytes, int nx, uint64_t slices_per_x, ExecShape* out) {
+  int dev = 0;
+  cudaGetDevice(&dev);
   if (g_num_sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (g_num_sms <= 0) g_num_sms = 1;
   }
   int max_optin = 0;
-  {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  }
+  cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   ExecShape sh;
-  const bool lane = prog.exec == Executor::Lane;
-  sh.threads = lane ? 128 : 256;
-  SmemLayout L = smem_layout(prog.n_steps, prog.n_leaves, prog.leaf_elems, prog.arena_elems, elem_bytes,
-                             sh.threads, lane);
-  if (lane && L.total > (size_t)max_optin) {
-    sh.threads = 64;
-    L = smem_layout(prog.n_steps, prog.n_leaves, prog.leaf_elems, prog.arena_elems, elem_bytes, sh.threads, lane);
-  }
-  if (L.total > (size_t)max_optin) return false;
-  sh.smem = L.total;
-  int occ = 1;
-  cudaError_t e;
-  if (lane) {
-    if (elem_bytes == 8) {
-      cudaFuncSetAttribute(lane_exec_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lane_exec_kernel<float2>, sh.threads, sh.smem);
-    } else {
-      cudaFuncSetAttribute(lane_exec_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, lane_exec_kernel<double2>, sh.threads, sh.smem);
+  const bool fp64 = elem_bytes == 16;
+  int occ = 0;
+  uint64_t per_block_items = 1;
+  if (prog.exec == Executor::Lane) {
+    sh.threads = 128;
+    SmemLayout L = smem_layout(prog.n_steps, prog.n_leaves, prog.leaf_elems, prog.arena_elems, elem_bytes,
+                               sh.threads, true);
+    if (L.total > (size_t)max_optin) {
+      sh.threads = 64;
+      L = smem_layout(prog.n_steps, prog.n_leaves, prog.leaf_elems, prog.arena_elems, elem_bytes, sh.threads, true);
     }
+    if (L.total > (size_t)max_optin) return false;
+    sh.smem = L.total;
+    bool ok = fp64 ? shape_for_kernel(lane_exec_kernel<double2>, sh.threads, sh.smem, &occ)
+                   : shape_for_kernel(lane_exec_kernel<float2>, sh.threads, sh.smem, &occ);
+    if (!ok) return false;
+    per_block_items = (uint64_t)sh.threads;
+  } else if (prog.exec == Executor::Warp) {
+    sh.threads = 256;
+    SmemLayout L;
+    for (;;) {
+      L = smem_layout(prog.n_steps, prog.n_leaves, prog.leaf_elems, prog.arena_elems * (sh.threads / 32),
+                      elem_bytes, sh.threads, false);
+      if (L.total <= (size_t)max_optin || sh.threads == 32) break;
+      sh.threads /= 2;
+    }
+    if (L.total > (size_t)max_optin) return false;
+    sh.smem = L.total;
+    bool ok = fp64 ? shape_for_kernel(block_exec_kernel<double2, true>, sh.threads, sh.smem, &occ)
+                   : shape_for_kernel(block_exec_kernel<float2, true>, sh.threads, sh.smem, &occ);
+    if (!ok) return false;
+    per_block_items = (uint64_t)(sh.threads / 32);
   } else {
-    if (elem_bytes == 8) {
-      cudaFuncSetAttribute(block_exec_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, block_exec_kernel<float2>, sh.threads, sh.smem);
-    } else {
-      cudaFuncSetAttribute(block_exec_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, block_exec_kernel<double2>, sh.threads, sh.smem);
-    }
+    sh.threads = 256;
+    SmemLayout L = smem_layout(prog.n_steps, prog.n_leaves, prog.leaf_elems, prog.arena_elems, elem_bytes,
+                               sh.threads, false);
+    if (L.total > (size_t)max_optin) return false;
+    sh.smem = L.total;
+    bool ok = fp64 ? shape_for_kernel(block_exec_kernel<double2, false>, sh.threads, sh.smem, &occ)
+                   : shape_for_kernel(block_exec_kernel<float2, false>, sh.threads, sh.smem, &occ);
+    if (!ok) return false;
   }
-  if (e != cudaSuccess || occ < 1) return false;
+  if (prog.n_pro_steps > 0) {
+    const SmemLayout PL = smem_layout(prog.n_pro_steps, prog.n_leaves, prog.leaf_elems, prog.pro_arena_elems,
+                                      elem_bytes, 256, false);
+    if (PL.total > (size_t)max_optin) return false;
+    sh.pro_smem = PL.total;
+    cudaError_t pe = fp64 ? cudaFuncSetAttribute(prologue_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)PL.total)
+                          : cudaFuncSetAttribute(prologue_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)PL.total);
+    if (pe != cudaSuccess) return false;
+  }
   const uint64_t total_blocks = (uint64_t)g_num_sms * (uint64_t)occ;
   uint64_t per_x = total_blocks / (uint64_t)(nx > 0 ? nx : 1);
   if (per_x < 1) per_x = 1;
-  const uint64_t units = lane ? (slices_per_x + sh.threads - 1) / sh.threads : slices_per_x;
+  const uint64_t units = (slices_per_x + per_block_items - 1) / per_block_items;
   if (per_x > units) per_x = units;
   if (per_x < 1) per_x = 1;
   sh.blocks_per_x = (int)per_x;
@@ -491,6 +602,18 @@ cudaError_t launch_contraction(const DeviceProgram& prog, bool fp64, const uint8
                                                          static_cast<float2*>(buf.leaf_tables));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (prog.n_pro_steps > 0) {
+    if (fp64)
+      prologue_kernel<double2><<<nx, 256, shape.pro_smem, stream>>>(prog.pro_steps, prog.n_pro_steps, prog.leaves,
+                                                                   prog.n_leaves, buf.leaf_tables, prog.leaf_elems,
+                                                                   prog.pro_arena_elems);
+    else
+      prologue_kernel<float2><<<nx, 256, shape.pro_smem, stream>>>(prog.pro_steps, prog.n_pro_steps, prog.leaves,
+                                                                  prog.n_leaves, buf.leaf_tables, prog.leaf_elems,
+                                                                  prog.pro_arena_elems);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   ExecParams P;
   P.steps = prog.steps;
   P.leaves = prog.leaves;
@@ -514,11 +637,16 @@ cudaError_t launch_contraction(const DeviceProgram& prog, bool fp64, const uint8
       lane_exec_kernel<double2><<<grid, shape.threads, shape.smem, stream>>>(P, buf.err);
     else
       lane_exec_kernel<float2><<<grid, shape.threads, shape.smem, stream>>>(P, buf.err);
+  } else if (prog.exec == Executor::Warp) {
+    if (fp64)
+      block_exec_kernel<double2, true><<<grid, shape.threads, shape.smem, stream>>>(P);
+    else
+      block_exec_kernel<float2, true><<<grid, shape.threads, shape.smem, stream>>>(P);
   } else {
     if (fp64)
-      block_exec_kernel<double2><<<grid, shape.threads, shape.smem, stream>>>(P);
+      block_exec_kernel<double2, false><<<grid, shape.threads, shape.smem, stream>>>(P);
     else
-      block_exec_kernel<float2><<<grid, shape.threads, shape.smem, stream>>>(P);
+      block_exec_kernel<float2, false><<<grid, shape.threads, shape.smem, stream>>>(P);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;

@@ -9,7 +9,7 @@
 
 namespace qtn {
 
-enum class Executor : int { Lane = 0, Block = 1 };
+enum class Executor : int { Lane = 0, Block = 1, Warp = 2 };
 
 // Compensated (Kahan) partial sum of complex slice results: the running sums
 // (re, im) and their compensations (cre, cim).
@@ -27,6 +27,9 @@ struct DeviceProgram {
   Executor exec = Executor::Lane;
   const DevLeaf* leaves = nullptr;
   const DevStep* steps = nullptr;
+  const DevStep* pro_steps = nullptr;  // hoisted merges, once per bit string
+  int n_pro_steps = 0;
+  uint32_t pro_arena_elems = 0;
   const int32_t* gate_q = nullptr;
   const int8_t* gate_layer = nullptr;
   const int8_t* gate_in_h = nullptr;
@@ -50,6 +53,7 @@ struct ExecShape {
   int threads = 0;
   int blocks_per_x = 0;
   size_t smem = 0;
+  size_t pro_smem = 0;  // prologue kernel (one block of 256 threads per bit string)
 };
 bool exec_shape(const DeviceProgram& prog, int elem_bytes, int nx, uint64_t slices_per_x, ExecShape* out);
 

@@ -90,6 +90,8 @@ extern "C" qtn_status qtn_contract_amplitudes_noalloc(const qtn_plan_t* plan, co
   dp.n_steps = (int)pg.steps.size();
   dp.leaf_elems = pg.leaf_elems;
   dp.arena_elems = pg.arena_elems;
+  dp.n_pro_steps = (int)pg.prologue.size();
+  dp.pro_arena_elems = pg.pro_arena_elems;
   dp.exec = pv.lane ? Executor::Lane : Executor::Block;
   ExecShape sh;
   if (!exec_shape(dp, (int)elem, nx, S, &sh))
@@ -104,6 +106,7 @@ extern "C" qtn_status qtn_contract_amplitudes_noalloc(const qtn_plan_t* plan, co
   };
   const size_t o_leaves = take(bytes_of(pg.leaves));
   const size_t o_steps = take(bytes_of(pg.steps));
+  const size_t o_pro = take(bytes_of(pg.prologue));
   const size_t o_gq = take(bytes_of(pg.gate_q));
   const size_t o_gl = take(bytes_of(pg.gate_layer));
   const size_t o_gi = take(bytes_of(pg.gate_in_h));
@@ -129,6 +132,7 @@ extern "C" qtn_status qtn_contract_amplitudes_noalloc(const qtn_plan_t* plan, co
     size_t bytes;
   } pieces[] = {{o_leaves, pg.leaves.data(), bytes_of(pg.leaves)},
                 {o_steps, pg.steps.data(), bytes_of(pg.steps)},
+                {o_pro, pg.prologue.data(), bytes_of(pg.prologue)},
                 {o_gq, pg.gate_q.data(), bytes_of(pg.gate_q)},
                 {o_gl, pg.gate_layer.data(), bytes_of(pg.gate_layer)},
                 {o_gi, pg.gate_in_h.data(), bytes_of(pg.gate_in_h)},
@@ -148,6 +152,7 @@ extern "C" qtn_status qtn_contract_amplitudes_noalloc(const qtn_plan_t* plan, co
 
   dp.leaves = reinterpret_cast<const DevLeaf*>(base + o_leaves);
   dp.steps = reinterpret_cast<const DevStep*>(base + o_steps);
+  dp.pro_steps = reinterpret_cast<const DevStep*>(base + o_pro);
   dp.gate_q = reinterpret_cast<const int32_t*>(base + o_gq);
   dp.gate_layer = reinterpret_cast<const int8_t*>(base + o_gl);
   dp.gate_in_h = reinterpret_cast<const int8_t*>(base + o_gi);

@@ -249,68 +249,111 @@ std::string compile_program(const Network& net, const Plan& plan_in, const Progr
     leaf_off += 1u << (lf.rank_nc + lf.ncut);
     pg.leaves[t] = lf;
   }
+
+  // Hoisting: merges reached by no outer-class cut leg.
+  std::vector<char> dep_outer(T, 0), pro(plan.merges.size(), 0), exported(T, 0);
+  for (int t = 0; t < n_leaves; ++t) dep_outer[t] = pg.leaves[t].ncut > 0;
+  for (const Merge& m : plan.merges) dep_outer[m.c] = dep_outer[m.a] || dep_outer[m.b];
+  const bool hoist = opt.hoist && pg.n_outer > 0;
+  std::vector<int> consumer(T, -1);
+  for (size_t j = 0; j < plan.merges.size(); ++j) {
+    consumer[plan.merges[j].a] = (int)j;
+    consumer[plan.merges[j].b] = (int)j;
+    if (hoist && !dep_outer[plan.merges[j].c]) pro[j] = 1;
+  }
+  std::vector<int> leaf_id(T, -1);  // leaves and pseudo-leaves
+  for (int t = 0; t < n_leaves; ++t) leaf_id[t] = t;
+  for (size_t j = 0; j < plan.merges.size(); ++j) {
+    const int c = plan.merges[j].c;
+    if (pro[j] && consumer[c] >= 0 && !pro[consumer[c]]) {
+      exported[c] = 1;
+      DevLeaf lf{};
+      lf.base = leaf_off;
+      lf.gate = -2;
+      lf.rank_nc = (uint8_t)layout[c].size();
+      lf.ncut = 0;
+      leaf_off += 1u << lf.rank_nc;
+      leaf_id[c] = (int)pg.leaves.size();
+      pg.leaves.push_back(lf);
+    }
+  }
   pg.leaf_elems = leaf_off;
 
-  Arena arena;
   std::vector<uint32_t> where(T, 0);
-  for (int j : order) {
-    const Merge& mg = plan.merges[j];
-    const Canon& c = canon[j];
-    DevStep st{};
-    st.ma = (uint8_t)c.m.size();
-    st.nb = (uint8_t)c.n.size();
-    st.kb = (uint8_t)c.k.size();
-    st.bb = (uint8_t)c.b.size();
-    std::vector<uint32_t> to_release;
-    int64_t a_block = -1;
-    if (is_leaf(mg.a)) {
-      st.flags |= STEP_A_LEAF;
-      st.a = (uint32_t)mg.a;
-    } else {
-      st.a = where[mg.a];
-      a_block = where[mg.a];
-    }
-    if (is_leaf(mg.b)) {
-      st.flags |= STEP_B_LEAF;
-      st.b = (uint32_t)mg.b;
-    } else {
-      st.b = where[mg.b];
-      to_release.push_back(where[mg.b]);
-    }
-    const int rc = (int)(c.m.size() + c.n.size() + c.b.size());
-    const int wd = rc + (int)c.k.size();
-    pg.width = std::max(pg.width, wd);
-    pg.max_rank = std::max(pg.max_rank, rc);
-    pg.macs_per_item += std::ldexp(1.0, wd);
-    // A is read completely before the first store of C; B may be read while
-    // C is written, so only A's block may be reused by C.
-    if (a_block >= 0) {
-      if (opt.c_reuses_a) arena.release((uint32_t)a_block);
-      else to_release.push_back((uint32_t)a_block);
-    }
-    if (mg.c == root) {
-      st.flags |= STEP_ROOT;
-      st.c = 0;
-      for (int id : concat(concat(c.m, c.n), c.b)) {
-        if (id < I) return "the root keeps a real index open";
-        pg.root_class.push_back(id - I);
+  auto emit = [&](bool prologue_pass, bool c_reuses_a, std::vector<DevStep>* out, uint32_t* arena_high,
+                  double* macs) -> std::string {
+    Arena arena;
+    for (int j : order) {
+      if ((bool)pro[j] != prologue_pass) continue;
+      const Merge& mg = plan.merges[j];
+      const Canon& c = canon[j];
+      DevStep st{};
+      st.ma = (uint8_t)c.m.size();
+      st.nb = (uint8_t)c.n.size();
+      st.kb = (uint8_t)c.k.size();
+      st.bb = (uint8_t)c.b.size();
+      std::vector<uint32_t> to_release;
+      int64_t a_block = -1;
+      auto as_leaf = [&](int t) { return is_leaf(t) || (!prologue_pass && exported[t]); };
+      if (as_leaf(mg.a)) {
+        st.flags |= STEP_A_LEAF;
+        st.a = (uint32_t)leaf_id[mg.a];
+      } else {
+        st.a = where[mg.a];
+        a_block = where[mg.a];
       }
-    } else {
-      uint32_t off = arena.alloc(1u << rc);
-      where[mg.c] = off;
-      st.c = off;
+      if (as_leaf(mg.b)) {
+        st.flags |= STEP_B_LEAF;
+        st.b = (uint32_t)leaf_id[mg.b];
+      } else {
+        st.b = where[mg.b];
+        to_release.push_back(where[mg.b]);
+      }
+      const int rc = (int)(c.m.size() + c.n.size() + c.b.size());
+      const int wd = rc + (int)c.k.size();
+      pg.width = std::max(pg.width, wd);
+      pg.max_rank = std::max(pg.max_rank, rc);
+      *macs += std::ldexp(1.0, wd);
+      // A is read completely before the first store of C; B may be read
+      // while C is written, so only A's block may be reused by C.
+      if (a_block >= 0) {
+        if (c_reuses_a) arena.release((uint32_t)a_block);
+        else to_release.push_back((uint32_t)a_block);
+      }
       const Set canon_ix = concat(concat(c.m, c.n), c.b);
-      const Set& lay = layout[mg.c];
-      for (int b = 0; b < rc; ++b) {
-        auto it = std::find(lay.begin(), lay.end(), canon_ix[b]);
-        if (it == lay.end()) return "consumer layout misses an index";
-        st.w[b] = (uint16_t)(1u << (it - lay.begin()));
+      if (mg.c == root) {
+        st.flags |= STEP_ROOT;
+        st.c = 0;
+        for (int id : canon_ix) {
+          if (id < I) return "the root keeps a real index open";
+          pg.root_class.push_back(id - I);
+        }
+      } else {
+        if (prologue_pass && exported[mg.c]) {
+          st.flags |= STEP_EXPORT;
+          st.c = (uint32_t)leaf_id[mg.c];
+        } else {
+          uint32_t off = arena.alloc(1u << rc);
+          where[mg.c] = off;
+          st.c = off;
+        }
+        const Set& lay = layout[mg.c];
+        for (int b = 0; b < rc; ++b) {
+          auto it = std::find(lay.begin(), lay.end(), canon_ix[b]);
+          if (it == lay.end()) return "consumer layout misses an index";
+          st.w[b] = (uint16_t)(1u << (it - lay.begin()));
+        }
       }
+      for (uint32_t r : to_release) arena.release(r);
+      out->push_back(st);
     }
-    for (uint32_t r : to_release) arena.release(r);
-    pg.steps.push_back(st);
-  }
-  pg.arena_elems = std::max<uint32_t>(arena.high, 1);
+    *arena_high = std::max<uint32_t>(arena.high, 1);
+    return "";
+  };
+  std::string err = emit(true, false, &pg.prologue, &pg.pro_arena_elems, &pg.macs_prologue);
+  if (err.empty()) err = emit(false, opt.c_reuses_a, &pg.steps, &pg.arena_elems, &pg.macs_per_item);
+  if (!err.empty()) return err;
+  if (pg.prologue.empty()) pg.pro_arena_elems = 0;
 
   pg.gate_q.resize(2 * net.gates.size());
   pg.gate_layer.resize(net.gates.size());

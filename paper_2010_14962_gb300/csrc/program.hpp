@@ -24,6 +24,12 @@
 // device in FP64 and rounded to the working precision.  A leaf's outer-class
 // bits are its highest bits, so the sub-block of a work item is the
 // contiguous block at offset sum_j bit(item, cut_bit_j) << (rank_nc + j).
+//
+// Hoisting: a merge whose subtree holds no leaf with an outer-class cut leg
+// has the same value in every work item.  Such merges form the prologue,
+// run once per bit string; the ones consumed by per-item merges write their
+// result into the leaf table as "pseudo-leaves" (gate -2), which the item
+// steps read like leaves.
 #pragma once
 #include <cstdint>
 #include <string>
@@ -51,7 +57,8 @@ static_assert(sizeof(DevLeaf) == 20, "DevLeaf layout");
 enum StepFlags : uint8_t {
   STEP_A_LEAF = 1,
   STEP_B_LEAF = 2,
-  STEP_ROOT = 4,  // C is the work item's result: summed, not stored
+  STEP_ROOT = 4,    // C is the work item's result: summed, not stored
+  STEP_EXPORT = 8,  // prologue step: C is written to the leaf table as leaf `c`
 };
 
 // One merge.  The canonical C element o = m + (n << ma) + (b << (ma + nb))
@@ -67,6 +74,7 @@ static_assert(sizeof(DevStep) == 52, "DevStep layout");
 
 struct ProgramOptions {
   bool c_reuses_a = false;        // C may overwrite A's arena block
+  bool hoist = true;              // run outer-class-invariant merges once per bit string
   std::vector<int> cut_class;     // class of each cut (size k); empty = one class per cut
   std::vector<char> inner;        // per class: carried as a batch index
 };
@@ -79,7 +87,10 @@ struct Program {
   std::vector<int> inner_class;      // inner bit position -> class
   std::vector<int> root_class;       // class of each canonical bit of the root's output
   std::vector<DevLeaf> leaves;
-  std::vector<DevStep> steps;
+  std::vector<DevStep> steps;        // per work item
+  std::vector<DevStep> prologue;     // once per bit string: merges that no outer class reaches
+  uint32_t pro_arena_elems = 0;      // prologue arena (elements)
+  double macs_prologue = 0;          // per bit string
   uint32_t leaf_elems = 0;           // elements in one leaf table
   uint32_t arena_elems = 0;          // per-item arena (elements)
   int width = 0;                     // max ma + nb + kb + bb

@@ -78,6 +78,7 @@ def lib():
             "qtn_plan_executor": [vp, P(ctypes.c_char_p)],
             "qtn_plan_describe": [vp, ctypes.c_char_p, ctypes.c_size_t, P(ctypes.c_size_t)],
             "qtn_plan_set_kernel_timing": [vp, ctypes.c_int],
+            "qtn_plan_select_executor": [vp, ctypes.c_int, ctypes.c_int, ctypes.c_char_p],
             "qtn_plan_kernel_ms": [vp, P(ctypes.c_float)],
             "qtn_search_cuts": [vp, P(_PlanOpts), i32p, f64p, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int)],
             "qtn_status_string": [ctypes.c_int],
@@ -231,6 +232,10 @@ class Plan:
         buf = ctypes.create_string_buffer(need.value)
         _check(lib().qtn_plan_describe(self._h, buf, need.value, ctypes.byref(need)))
         return json.loads(buf.value.decode())
+
+    def select_executor(self, name: str, precision: str = "fp32", nx: int = 1):
+        """Override the autotuner for (precision, nx)."""
+        _check(lib().qtn_plan_select_executor(self._h, PRECISIONS[precision], int(nx), name.encode()))
 
     def set_kernel_timing(self, on: bool = True):
         _check(lib().qtn_plan_set_kernel_timing(self._h, int(bool(on))))

@@ -43,6 +43,8 @@ def gate_entry(gate, gamma, beta, x, v):
 def leaf_table(desc, prog, gamma, beta, x):
     lt = np.zeros(max(prog["leaf_elems"], 1), dtype=complex)
     for L in prog["leaves"]:
+        if L["gate"] == -2:  # pseudo-leaf: written by the prologue
+            continue
         r = L["rank_nc"] + len(L["cut_bit"])
         for e in range(1 << r):
             if L["gate"] < 0:
@@ -56,6 +58,26 @@ def leaf_table(desc, prog, gamma, beta, x):
                 val = gate_entry(desc["gates"][L["gate"]], gamma, beta, x, v)
             lt[L["base"] + e] = val
     return lt
+
+
+def run_prologue(prog, lt):
+    """Hoisted merges, once per bit string; exported results become
+    pseudo-leaves of the leaf table (in place)."""
+    leaves = prog["leaves"]
+    arena = np.zeros(max(prog["pro_arena_elems"], 1) + 64, dtype=complex)
+    for st in prog["prologue"]:
+        ma, nb, kb, bb = st["ma"], st["nb"], st["kb"], st["bb"]
+        rc = ma + nb + bb
+        A = (lt[leaves[st["a"]]["base"]:] if st["flags"] & 1 else arena[st["a"]:])[: 1 << (ma + kb + bb)].copy()
+        B = (lt[leaves[st["b"]]["base"]:] if st["flags"] & 2 else arena[st["b"]:])[: 1 << (kb + nb + bb)].copy()
+        C = np.einsum("bkm,bnk->bnm", A.reshape(1 << bb, 1 << kb, 1 << ma), B.reshape(1 << bb, 1 << nb, 1 << kb))
+        for o in range(1 << rc):
+            m, n, bch = o & ((1 << ma) - 1), (o >> ma) & ((1 << nb) - 1), o >> (ma + nb)
+            pos = sum(st["w"][j] for j in range(rc) if (o >> j) & 1)
+            if st["flags"] & 8:
+                lt[leaves[st["c"]]["base"] + pos] = C[bch, n, m]
+            else:
+                arena[st["c"] + pos] = C[bch, n, m]
 
 
 def run_item(prog, lt, item):
@@ -133,6 +155,7 @@ def run_program(desc, name, gamma, beta, x):
     """{slice id: unnormalised value} over the slices the program enumerates."""
     prog = desc["programs"][name]
     lt = leaf_table(desc, prog, gamma, beta, x)
+    run_prologue(prog, lt)
     trivial = list(range(len(desc["cuts"])))
     cut_class = trivial if name == desc["executor"] else desc["cut_class"]
     vals = {}

@@ -228,6 +228,7 @@ def test_emulated_program_n80_sampled_slices():
     x = I.bitstrings(n, 1, 3)[0]
     prog = d["programs"][d["executor"]]
     lt = E.leaf_table(d, prog, inst.gamma, inst.beta, x)
+    E.run_prologue(prog, lt)
     scale = 2.0 ** (-n / 2)
     for s in (0, 1, 12345, 65535):
         ref = O.tn_amplitude(n, inst.edges, inst.gamma, inst.beta, x, cuts=plan.cut_names(), slices=(s, s + 1))
