@@ -46,11 +46,19 @@ def measured_peaks():
         return {}
 
 
+# FP32 pipe instructions per real multiply-add in each arithmetic (the
+# double-float MAC: 1 FMUL + 3 FFMA + 2 TwoSum (6 each) + 2 FADD + 2 Fast2Sum
+# (3 each) = 24; TF32 / split forms: conversions + products on the FP32 pipe).
+INSTR_PER_MAC = {"fp32": 1, "fp32x2": 24, "tf32": 3, "tf32x3": 9, "bf16x3": 13, "bf16x6": 22}
+
+
 def alu_peak_tflops(prec: str, sm_mhz: float) -> float:
-    """FP32: 152 SMs x 128 FMA lanes x 2 flops x clock; FP64: nominal."""
+    """Algorithmic flops (2 per real multiply-add) the ALUs can sustain:
+    FP32 pipe 152 SMs x 128 lanes x clock / instructions per MAC x 2;
+    FP64: the nominal 1.25 TFLOP/s of GB300."""
     if prec == "fp64":
         return FP64_TFLOPS_NOMINAL
-    return NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    return NUM_SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12 / INSTR_PER_MAC[prec]
 
 
 class ClockSampler:
@@ -151,6 +159,9 @@ def run_ours(args, rank, world, local_rank):
     inst, net, plan, xs = setup_workload(rank)
     nx = xs.shape[0]
     cost = plan.cost()
+    sweep = None
+    if args.precision == "auto":
+        sweep, args.precision = precision_sweep(plan, inst, xs, torch, rank == 0 and not args.no_oracle_refs)
     flops_per_amp = (2 ** cost["k"]) * 8 * cost["macs_per_slice"]
     stream = torch.cuda.current_stream()
     d_x = torch.from_numpy(np.ascontiguousarray(xs)).cuda()
@@ -256,7 +267,7 @@ def run_ours(args, rank, world, local_rank):
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
-        "dtype": "c64" if args.precision == "fp32" else "c128",
+        "dtype": {"fp32": "c64", "fp64": "c128", "fp32x2": "c64x2 (double-float)"}.get(args.precision, "c64"),
         "data": "synthetic: seeded random 3-regular graph, gamma/beta ~ U[0,pi), seeded bit strings",
         "config": {"workload": WORKLOAD["name"], "n": WORKLOAD["n"], "p": WORKLOAD["p"], "cuts": WORKLOAD["k"],
                    "slices_per_amplitude": 2 ** cost["k"], "bitstrings_per_step": nx, "precision": args.precision,
@@ -272,8 +283,10 @@ def run_ours(args, rank, world, local_rank):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": profiled_traffic(args.precision),
                      "kernel": "lane_exec_kernel" if prog["executor"] == "lane" else "block_exec_kernel",
-                     "peak_source": ("FP32: 152 SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock of measured peaks)"
-                                     % sm_for_peak) if args.precision != "fp64" else "FP64 nominal 1.25 TFLOP/s",
+                     "peak_source": ("FP32 pipe: 152 SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock of measured "
+                                     "peaks) / %d FP32 instructions per multiply-add"
+                                     % (sm_for_peak, INSTR_PER_MAC[args.precision]))
+                     if args.precision != "fp64" else "FP64 nominal 1.25 TFLOP/s",
                      "kernel_ms_avg": avg_kernel_s * 1e3},
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": "amplitudes/s", "h2d_bytes_per_step": int(nx * WORKLOAD["n"]),
@@ -281,11 +294,67 @@ def run_ours(args, rank, world, local_rank):
         "gpu_launches": 3 * args.steps,
         "wall_s_timed_region": wall,
     }
+    if sweep is not None:
+        out["precision_sweep"] = sweep
+        out["config"]["precision_rule"] = ("fastest arithmetic whose max relative error against the FP64 GPU form "
+                                           "over the 8 bit strings is <= 1e-6")
     if world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+SWEEP = ["fp64", "fp32", "fp32x2", "tf32", "bf16x3", "tf32x3", "bf16x6"]
+
+
+def precision_sweep(plan, inst, xs, torch, oracle_refs: bool):
+    """Throughput and accuracy of every arithmetic on the workload; returns
+    (table, chosen precision)."""
+    nx = xs.shape[0]
+    d_x = torch.from_numpy(np.ascontiguousarray(xs)).cuda()
+    stream = torch.cuda.current_stream()
+    refs = None
+    if oracle_refs:
+        from oracle import oracle as O
+
+        refs = np.array([O.tn_amplitude(WORKLOAD["n"], inst.edges, inst.gamma, inst.beta, x,
+                                        threads=os.cpu_count() or 1).value for x in xs])
+    table, vals = {}, {}
+    for prec in SWEEP:
+        d_out = torch.zeros((nx, 2), dtype=torch.float64, device="cuda")
+        plan.contract_amplitudes_device(d_x, d_out, prec, stream)  # autotunes
+        for _ in range(3):
+            plan.contract_amplitudes_device(d_x, d_out, prec, stream)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 20
+        a.record(stream)
+        for _ in range(reps):
+            plan.contract_amplitudes_device(d_x, d_out, prec, stream)
+        b.record(stream)
+        torch.cuda.synchronize()
+        o = d_out.cpu().numpy()
+        vals[prec] = o[:, 0] + 1j * o[:, 1]
+        tuned = [t for t in plan.describe()["tuned"] if t["prec"] == plan_prec_id(prec) and t["nx"] == nx]
+        table[prec] = {"amplitudes_per_s": nx * reps / (a.elapsed_time(b) / 1e3),
+                       "executor": tuned[0]["executor"] if tuned else None}
+    f64 = vals["fp64"]
+    for prec in SWEEP:
+        table[prec]["max_rel_err_vs_fp64_gpu"] = float(np.max(np.abs(vals[prec] - f64) / np.abs(f64)))
+        if refs is not None:
+            table[prec]["max_rel_err_vs_oracle"] = float(np.max(np.abs(vals[prec] - refs) / np.abs(refs)))
+    ok = [p for p in SWEEP if p == "fp64" or table[p]["max_rel_err_vs_fp64_gpu"] <= 1e-6]
+    chosen = max(ok, key=lambda p: table[p]["amplitudes_per_s"])
+    table["chosen"] = chosen
+    table["speedup_vs_fp64_gpu"] = table[chosen]["amplitudes_per_s"] / table["fp64"]["amplitudes_per_s"]
+    return table, chosen
+
+
+def plan_prec_id(prec):
+    from paper_2010_14962_gb300 import qtn
+
+    return qtn.PRECISIONS[prec]
 
 
 def cpu_baseline(seconds: float, plan_bundle=None):
@@ -348,7 +417,9 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="auto", choices=["auto"] + SWEEP,
+                    help="auto: sweep every arithmetic and time the fastest within 1e-6 of the FP64 GPU form")
+    ap.add_argument("--no-oracle-refs", action="store_true", help="sweep without the oracle's reference values")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -55,14 +55,19 @@ typedef enum {
 } qtn_status;
 
 /* Arithmetic of the elimination steps.  Gate phases (sincos of gamma, beta)
- * and the sum over slices are FP64 in every mode (Kahan-compensated). */
+ * and the sum over slices are FP64 in every mode (Kahan-compensated).
+ * TF32 .. BF16X6 reproduce the products tensor cores form (operands rounded
+ * or split as stated, products accumulated in FP32); they run on the FP32
+ * pipes of the batched executors, to measure what each format costs in
+ * accuracy on this workload. */
 typedef enum {
   QTN_FP64 = 0,   /* complex128 contractions (the plain FP64 GPU form) */
   QTN_FP32 = 1,   /* complex64 contractions, FP32 FMA */
-  QTN_TF32 = 2,   /* tensor cores: operands rounded to TF32, FP32 accumulate */
-  QTN_BF16X3 = 3, /* tensor cores: split-BF16 (hi*hi + hi*lo + lo*hi), FP32 acc */
-  QTN_TF32X3 = 4, /* tensor cores: split-TF32 3-term, FP32 accumulate */
-  QTN_BF16X6 = 5  /* tensor cores: 3-way split BF16, 6 products, FP32 acc */
+  QTN_TF32 = 2,   /* operands rounded to TF32, FP32 accumulate */
+  QTN_BF16X3 = 3, /* split-BF16 (hi*hi + hi*lo + lo*hi), FP32 accumulate */
+  QTN_TF32X3 = 4, /* split-TF32, 3 products, FP32 accumulate */
+  QTN_BF16X6 = 5, /* 3-way split BF16, 6 products, FP32 accumulate */
+  QTN_FP32X2 = 6  /* double-float complex (hi + lo FP32 pairs), ~44-bit */
 } qtn_precision;
 
 typedef struct qtn_network qtn_network_t;

@@ -50,7 +50,8 @@ def build(verbose: bool = False) -> str:
         objs = list(ex.map(_compile, SOURCES))
     if not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
         tmp = LIB + f".{os.getpid()}.tmp"
-        subprocess.run([_nvcc(), *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"], check=True)
+        subprocess.run([_nvcc(), *ARCH, "-shared", "-Xlinker", "-z", "-Xlinker", "defs", "-o", tmp, *objs, "-lcudart"],
+                       check=True)
         os.replace(tmp, LIB)
     if verbose:
         print("built", LIB)

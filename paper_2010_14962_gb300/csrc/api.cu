@@ -64,7 +64,21 @@ struct GraphKey {
   }
 };
 
-bool precision_supported(qtn_precision p) { return p == QTN_FP64 || p == QTN_FP32; }
+bool precision_supported(qtn_precision p) { return (int)p >= 0 && (int)p <= 6; }
+
+Arith arith_of(qtn_precision p) {
+  switch (p) {
+    case QTN_FP64: return Arith::F64;
+    case QTN_FP32: return Arith::F32;
+    case QTN_TF32: return Arith::TF32;
+    case QTN_BF16X3: return Arith::BF16X3;
+    case QTN_TF32X3: return Arith::TF32X3;
+    case QTN_BF16X6: return Arith::BF16X6;
+    case QTN_FP32X2: return Arith::F32X2;
+  }
+  return Arith::F64;
+}
+bool wide(qtn_precision p) { return arith_elem_bytes(arith_of(p)) == 16; }
 
 }  // namespace
 
@@ -239,15 +253,17 @@ struct qtn_plan {
   qtn_status prepare(int si, qtn_precision prec, int nx, uint64_t items, ExecShape* sh) {
     qtn_status st = upload(slots[si]);
     if (st != QTN_OK) return st;
-    if (!exec_shape(slots[si].dprog, prec == QTN_FP64 ? 16 : 8, nx, items, sh))
+    if (!exec_shape(slots[si].dprog, arith_of(prec), nx, items, sh))
       return fail(QTN_ERR_UNSUPPORTED, "the plan's per-item working set does not fit in shared memory");
     return ensure_workspace(nx, sh->blocks_per_x);
   }
 
   bool eligible(int si, qtn_precision prec) const {
     const ProgSlot& s = slots[si];
-    if (prec == QTN_FP64 && s.fp32_only) return false;
-    if (prec == QTN_FP32 && s.fp64_only) return false;
+    if (wide(prec) && s.fp32_only) return false;
+    if (!wide(prec) && s.fp64_only) return false;
+    const bool lane_arith = prec == QTN_FP64 || prec == QTN_FP32 || prec == QTN_FP32X2;
+    if (s.exec == Executor::Lane && !lane_arith) return false;
     return true;
   }
 
@@ -275,7 +291,7 @@ struct qtn_plan {
       float ms_min = 1e30f;
       for (int rep = 0; rep < 4; ++rep) {
         QTN_CUDA(cudaEventRecord(a, stream));
-        cudaError_t le = launch_contraction(slots[si].dprog, prec == QTN_FP64, d_x_stage, nx, 0, slots[si].items(),
+        cudaError_t le = launch_contraction(slots[si].dprog, arith_of(prec), d_x_stage, nx, 0, slots[si].items(),
                                             buffers(), sh, scale(), d_out_stage, nullptr, nullptr, stream);
         if (le != cudaSuccess) return cuda_fail(le, "launch_contraction (tuning)");
         QTN_CUDA(cudaEventRecord(b, stream));
@@ -311,7 +327,7 @@ struct qtn_plan {
     st = prepare(si, prec, nx, S, &sh);
     if (st != QTN_OK) return st;
     if (timing) {
-      cudaError_t le = launch_contraction(slots[si].dprog, prec == QTN_FP64, d_x, nx, 0, S, buffers(), sh, scale(),
+      cudaError_t le = launch_contraction(slots[si].dprog, arith_of(prec), d_x, nx, 0, S, buffers(), sh, scale(),
                                           d_out, nullptr, nullptr, stream, ev0, ev1);
       if (le != cudaSuccess) return cuda_fail(le, "launch_contraction");
       return QTN_OK;
@@ -321,7 +337,7 @@ struct qtn_plan {
     if (it == graphs.end()) {
       cudaGraph_t g;
       QTN_CUDA(cudaStreamBeginCapture(capture_stream, cudaStreamCaptureModeThreadLocal));
-      cudaError_t le = launch_contraction(slots[si].dprog, prec == QTN_FP64, d_x, nx, 0, S, buffers(), sh, scale(),
+      cudaError_t le = launch_contraction(slots[si].dprog, arith_of(prec), d_x, nx, 0, S, buffers(), sh, scale(),
                                           d_out, nullptr, nullptr, capture_stream);
       cudaError_t ce = cudaStreamEndCapture(capture_stream, &g);
       if (le != cudaSuccess) return cuda_fail(le, "launch_contraction (capture)");
@@ -724,7 +740,7 @@ qtn_status qtn_contract_slices(const qtn_plan_t* cplan, const uint8_t* x, uint64
   if (st != QTN_OK) return st;
   std::memcpy(plan->h_x_pinned, x, plan->net.n);
   QTN_CUDA(cudaMemcpyAsync(plan->d_x_stage, plan->h_x_pinned, plan->net.n, cudaMemcpyHostToDevice, stream));
-  cudaError_t le = launch_contraction(plan->slots[0].dprog, prec == QTN_FP64, plan->d_x_stage, 1, slice_lo, slice_hi,
+  cudaError_t le = launch_contraction(plan->slots[0].dprog, arith_of(prec), plan->d_x_stage, 1, slice_lo, slice_hi,
                                       plan->buffers(), sh, 1.0, nullptr, plan->d_raw_stage,
                                       reinterpret_cast<double2*>(d_slices), stream);
   if (le != cudaSuccess) return cuda_fail(le, "launch_contraction");

@@ -21,6 +21,10 @@
 //                       normalisation of the unnormalised H|0> = (1, 1).
 #include "kernels.cuh"
 
+#include <cuda_bf16.h>
+
+#include <type_traits>
+
 namespace qtn {
 namespace {
 
@@ -52,6 +56,8 @@ struct CplxOps<float2> {
   static __device__ __forceinline__ float2 from(double re, double im) {
     return make_float2((float)re, (float)im);
   }
+  static __device__ __forceinline__ double re(float2 v) { return (double)v.x; }
+  static __device__ __forceinline__ double im(float2 v) { return (double)v.y; }
 };
 template <>
 struct CplxOps<double2> {
@@ -64,6 +70,109 @@ struct CplxOps<double2> {
     acc.y = ::fma(a.y, b.x, acc.y);
   }
   static __device__ __forceinline__ double2 from(double re, double im) { return make_double2(re, im); }
+  static __device__ __forceinline__ double re(double2 v) { return v.x; }
+  static __device__ __forceinline__ double im(double2 v) { return v.y; }
+};
+
+// ---------------------------------------------------- double-float (FP32X2) --
+
+// A complex number as two double-word floats (value = hi + lo per part).
+struct dfc {
+  float rh, rl, ih, il;
+};
+
+// Error-free transforms: TwoSum (Knuth), Fast2Sum (Dekker, |a| >= |b|) and
+// the FMA-based exact product.  The _rn intrinsics keep the compiler from
+// contracting them into FMAs, which would break exactness.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+// (ah, al) += (xh, xl) * (yh, yl) in double-word arithmetic: the product's
+// high part is exact (TwoProd), the cross terms are added to its low part,
+// and the sum is the accurate double-word addition.
+__device__ __forceinline__ void dw_fma(float& ah, float& al, float xh, float xl, float yh, float yl) {
+  const float ph = __fmul_rn(xh, yh);
+  float pl = __fmaf_rn(xh, yh, -ph);
+  pl = __fmaf_rn(xh, yl, pl);
+  pl = __fmaf_rn(xl, yh, pl);
+  float sh, sl, th, tl;
+  two_sum(ah, ph, sh, sl);
+  two_sum(al, pl, th, tl);
+  sl = __fadd_rn(sl, th);
+  fast_two_sum(sh, sl, sh, sl);
+  sl = __fadd_rn(sl, tl);
+  fast_two_sum(sh, sl, ah, al);
+}
+
+template <>
+struct CplxOps<dfc> {
+  static __device__ __forceinline__ dfc zero() { return dfc{0.f, 0.f, 0.f, 0.f}; }
+  static __device__ __forceinline__ void fma(dfc& acc, dfc a, dfc b) {
+    dw_fma(acc.rh, acc.rl, a.rh, a.rl, b.rh, b.rl);
+    dw_fma(acc.rh, acc.rl, -a.ih, -a.il, b.ih, b.il);
+    dw_fma(acc.ih, acc.il, a.rh, a.rl, b.ih, b.il);
+    dw_fma(acc.ih, acc.il, a.ih, a.il, b.rh, b.rl);
+  }
+  static __device__ __forceinline__ dfc from(double re, double im) {
+    const float rh = (float)re, ih = (float)im;
+    return dfc{rh, (float)(re - (double)rh), ih, (float)(im - (double)ih)};
+  }
+  static __device__ __forceinline__ double re(dfc v) { return (double)v.rh + (double)v.rl; }
+  static __device__ __forceinline__ double im(dfc v) { return (double)v.ih + (double)v.il; }
+};
+
+// ------------------------------------- tensor-core product numerics (FP32) --
+
+// Products of operands rounded as the tensor cores see them, accumulated in
+// FP32: TF32 (10-bit significand), split BF16 / TF32 in 2 pieces with the
+// 3 leading products, split BF16 in 3 pieces with the 6 leading products.
+enum class Round { TF32, BF16X3, TF32X3, BF16X6 };
+
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+__device__ __forceinline__ float to_bf16(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+template <Round R>
+struct RoundOps {
+  static __device__ __forceinline__ float2 zero() { return make_float2(0.f, 0.f); }
+  // acc + x * y for real x, y under the rounding mode.
+  static __device__ __forceinline__ float mul_add(float acc, float x, float y) {
+    if (R == Round::TF32) return __fmaf_rn(to_tf32(x), to_tf32(y), acc);
+    if (R == Round::BF16X3 || R == Round::TF32X3) {
+      const float xh = R == Round::BF16X3 ? to_bf16(x) : to_tf32(x);
+      const float yh = R == Round::BF16X3 ? to_bf16(y) : to_tf32(y);
+      const float xl = R == Round::BF16X3 ? to_bf16(x - xh) : to_tf32(x - xh);
+      const float yl = R == Round::BF16X3 ? to_bf16(y - yh) : to_tf32(y - yh);
+      acc = __fmaf_rn(xl, yh, acc);
+      acc = __fmaf_rn(xh, yl, acc);
+      return __fmaf_rn(xh, yh, acc);
+    }
+    const float x0 = to_bf16(x), x1 = to_bf16(x - x0), x2 = to_bf16(x - x0 - x1);
+    const float y0 = to_bf16(y), y1 = to_bf16(y - y0), y2 = to_bf16(y - y0 - y1);
+    acc = __fmaf_rn(x0, y2, acc);
+    acc = __fmaf_rn(x1, y1, acc);
+    acc = __fmaf_rn(x2, y0, acc);
+    acc = __fmaf_rn(x0, y1, acc);
+    acc = __fmaf_rn(x1, y0, acc);
+    return __fmaf_rn(x0, y0, acc);
+  }
+  static __device__ __forceinline__ void fma(float2& acc, float2 a, float2 b) {
+    acc.x = mul_add(acc.x, a.x, b.x);
+    acc.x = mul_add(acc.x, -a.y, b.y);
+    acc.y = mul_add(acc.y, a.x, b.y);
+    acc.y = mul_add(acc.y, a.y, b.x);
+  }
+  static __device__ __forceinline__ double re(float2 v) { return (double)v.x; }
+  static __device__ __forceinline__ double im(float2 v) { return (double)v.y; }
 };
 
 __device__ __forceinline__ void kahan_add(double& sum, double& comp, double v) {
@@ -171,7 +280,7 @@ __global__ void leaf_build_kernel(const DevLeaf* __restrict__ leaves, const int3
 // C[m, n] = sum_k A[m + (k << MA)] * B[k + (n << KB)], stored at the bit
 // weights w of C's layout.  A stays in registers while B is streamed one
 // column (fixed n) at a time.  Operands stride sa / sb elements, C strides sc.
-template <int MA, int NB, int KB, class V>
+template <int MA, int NB, int KB, class V, class Ops>
 __device__ __forceinline__ V lane_merge(const V* __restrict__ A, int sa, const V* __restrict__ B, int sb,
                                         V* __restrict__ C, int sc, const uint16_t* __restrict__ w,
                                         bool store) {
@@ -183,7 +292,7 @@ __device__ __forceinline__ V lane_merge(const V* __restrict__ A, int sa, const V
   uint32_t wl[RC > 0 ? RC : 1];
 #pragma unroll
   for (int j = 0; j < RC; ++j) wl[j] = w[j];
-  V acc = CplxOps<V>::zero();
+  V acc = Ops::zero();
 #pragma unroll
   for (int n = 0; n < (1 << NB); ++n) {
     V b[1 << KB];
@@ -191,9 +300,9 @@ __device__ __forceinline__ V lane_merge(const V* __restrict__ A, int sa, const V
     for (int k = 0; k < (1 << KB); ++k) b[k] = B[(k + (n << KB)) * sb];
 #pragma unroll
     for (int m = 0; m < (1 << MA); ++m) {
-      acc = CplxOps<V>::zero();
+      acc = Ops::zero();
 #pragma unroll
-      for (int k = 0; k < (1 << KB); ++k) CplxOps<V>::fma(acc, a[m + (k << MA)], b[k]);
+      for (int k = 0; k < (1 << KB); ++k) Ops::fma(acc, a[m + (k << MA)], b[k]);
       if (store) {
         const uint32_t o = (uint32_t)(m + (n << MA));
         uint32_t pos = 0;
@@ -210,7 +319,7 @@ __device__ __forceinline__ V lane_merge(const V* __restrict__ A, int sa, const V
 #define QTN_SHAPE(MA, NB, KB) ((MA) | ((NB) << 3) | ((KB) << 6))
 #define QTN_LANE_CASE(MA, NB, KB)                                 \
   case QTN_SHAPE(MA, NB, KB):                                     \
-    r = lane_merge<MA, NB, KB, V>(A, sa, B, sb, C, sc, w, store); \
+    r = lane_merge<MA, NB, KB, V, Ops>(A, sa, B, sb, C, sc, w, store); \
     break;
 // Every (ma, nb, kb) whose three tensors have rank <= kLaneMaxRank (5).
 #define QTN_LANE_CASES \
@@ -233,7 +342,7 @@ __device__ __forceinline__ V lane_merge(const V* __restrict__ A, int sa, const V
   QTN_LANE_CASE(0, 0, 4) QTN_LANE_CASE(0, 1, 4) QTN_LANE_CASE(1, 0, 4) QTN_LANE_CASE(1, 1, 4) \
   QTN_LANE_CASE(0, 0, 5)
 
-template <class V>
+template <class V, class Ops = CplxOps<V>>
 __global__ void __launch_bounds__(128) lane_exec_kernel(ExecParams P, int* err) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int T = blockDim.x;
@@ -256,7 +365,7 @@ __global__ void __launch_bounds__(128) lane_exec_kernel(ExecParams P, int* err) 
   const uint64_t S = P.slice_hi - P.slice_lo;
   for (uint64_t i = (uint64_t)bx * T + threadIdx.x; i < S; i += (uint64_t)P.blocks_per_x * T) {
     const uint64_t s = P.slice_lo + i;
-    V res = CplxOps<V>::zero();
+    V res = Ops::zero();
     for (int j = 0; j < P.n_steps; ++j) {
       const DevStep& st = s_steps[j];
       const V* A;
@@ -280,7 +389,7 @@ __global__ void __launch_bounds__(128) lane_exec_kernel(ExecParams P, int* err) 
       const int sc = T;
       const uint16_t* w = st.w;
       const bool store = !(st.flags & STEP_ROOT);
-      V r = CplxOps<V>::zero();
+      V r = Ops::zero();
       switch (QTN_SHAPE(st.ma, st.nb, st.kb)) {
         QTN_LANE_CASES
         default:
@@ -289,9 +398,9 @@ __global__ void __launch_bounds__(128) lane_exec_kernel(ExecParams P, int* err) 
       }
       if (!store) res = r;
     }
-    kahan_add(sr, cr, (double)res.x);
-    kahan_add(si, ci, (double)res.y);
-    if (P.slices) P.slices[(size_t)xi * S + i] = make_double2((double)res.x, (double)res.y);
+    kahan_add(sr, cr, Ops::re(res));
+    kahan_add(si, ci, Ops::im(res));
+    if (P.slices) P.slices[(size_t)xi * S + i] = make_double2(Ops::re(res), Ops::im(res));
   }
   s_red[threadIdx.x] = Partial::make(sr, si, cr, ci);
   __syncthreads();
@@ -313,59 +422,75 @@ __global__ void __launch_bounds__(128) lane_exec_kernel(ExecParams P, int* err) 
 // One merge executed by a group of G threads (G = 32: one warp; G = block
 // size), thread t of the group: outputs o = t, t + G, ... of the canonical
 // C[m, n, b] = sum_k A[m + (k << ma) + (b << (ma+kb))] * B[k + (n << kb) +
-// (b << (kb+nb))].  Results are stored at c + pos(o) (bit weights w), or,
-// for the root, added to the thread's compensated sum.
-template <class V, int K>
-__device__ __forceinline__ void group_merge_k(const DevStep& st, const V* __restrict__ A, const V* __restrict__ B,
-                                              V* __restrict__ C, uint32_t t, uint32_t G, uint32_t pos_t,
-                                              int log2G, bool root, double& sr, double& cr, double& si,
-                                              double& ci, double2* slice_out) {
-  const int ma = st.ma, nb = st.nb, kb = st.kb, rc = st.ma + st.nb + st.bb;
+// (b << (kb+nb))].  Results are stored at C + pos(o) (bit weights w), or,
+// for the root, added to the thread's compensated sum.  The step's fields
+// arrive as scalars (registers): read through shared memory, every store of
+// C would force them to be read again.
+struct StepRegs {
+  int ma, nb, kb, rc;
+  bool root;
+};
+
+template <class V, int K, class Ops>
+__device__ __forceinline__ void group_merge_k(const StepRegs sr_, const uint16_t* __restrict__ w,
+                                              const V* __restrict__ A, const V* __restrict__ B, V* __restrict__ C,
+                                              uint32_t t, uint32_t G, uint32_t pos_t, int log2G, double& sr,
+                                              double& cr, double& si, double& ci, double2* slice_out) {
+  const int ma = sr_.ma, nb = sr_.nb, kb = sr_.kb, rc = sr_.rc;
   const uint32_t NC = 1u << rc;
   const uint32_t mmask = (1u << ma) - 1u, nmask = (1u << nb) - 1u;
   for (uint32_t o = t; o < NC; o += G) {
     const uint32_t m = o & mmask, n = (o >> ma) & nmask, b = o >> (ma + nb);
     const V* ap = A + m + (b << (ma + kb));
     const V* bp = B + (n << kb) + (b << (kb + nb));
-    V acc = CplxOps<V>::zero();
+    V acc = Ops::zero();
     if (K > 0) {
 #pragma unroll
-      for (int k = 0; k < K; ++k) CplxOps<V>::fma(acc, ap[k << ma], bp[k]);
+      for (int k = 0; k < K; ++k) Ops::fma(acc, ap[k << ma], bp[k]);
     } else {
-      for (uint32_t k = 0; k < (1u << kb); ++k) CplxOps<V>::fma(acc, ap[k << ma], bp[k]);
+      for (uint32_t k = 0; k < (1u << kb); ++k) Ops::fma(acc, ap[k << ma], bp[k]);
     }
-    if (root) {
-      kahan_add(sr, cr, (double)acc.x);
-      kahan_add(si, ci, (double)acc.y);
-      if (slice_out && NC == 1) *slice_out = make_double2((double)acc.x, (double)acc.y);
+    if (sr_.root) {
+      kahan_add(sr, cr, Ops::re(acc));
+      kahan_add(si, ci, Ops::im(acc));
+      if (slice_out && NC == 1) *slice_out = make_double2(Ops::re(acc), Ops::im(acc));
     } else {
       uint32_t pos = pos_t;
-      for (uint32_t hi = o >> log2G; hi; hi &= hi - 1u) pos += st.w[log2G + __ffs(hi) - 1];
+      for (uint32_t hi = o >> log2G; hi; hi &= hi - 1u) pos += w[log2G + __ffs(hi) - 1];
       C[pos] = acc;
     }
   }
 }
 
-template <class V>
-__device__ __forceinline__ void group_merge(const DevStep& st, const V* A, const V* B, V* C, uint32_t t,
-                                            uint32_t G, int log2G, double& sr, double& cr, double& si, double& ci,
-                                            double2* slice_out) {
-  const bool root = st.flags & STEP_ROOT;
-  const int rc = st.ma + st.nb + st.bb;
-  if (t >= (1u << rc)) return;  // no output of this merge for the thread
+template <class V, class Ops>
+__device__ __forceinline__ void group_merge(const StepRegs r, const uint16_t* w, const V* A, const V* B, V* C,
+                                            uint32_t t, uint32_t G, int log2G, double& sr, double& cr, double& si,
+                                            double& ci, double2* slice_out) {
+  if (t >= (1u << r.rc)) return;  // no output of this merge for the thread
   // Store offset of the thread's own low bits, shared by all its outputs.
   uint32_t pos_t = 0;
-  if (!root)
-    for (int bit = 0; bit < log2G && bit < rc; ++bit)
-      if ((t >> bit) & 1u) pos_t += st.w[bit];
-  switch (st.kb) {
-    case 0: group_merge_k<V, 1>(st, A, B, C, t, G, pos_t, log2G, root, sr, cr, si, ci, slice_out); break;
-    case 1: group_merge_k<V, 2>(st, A, B, C, t, G, pos_t, log2G, root, sr, cr, si, ci, slice_out); break;
-    case 2: group_merge_k<V, 4>(st, A, B, C, t, G, pos_t, log2G, root, sr, cr, si, ci, slice_out); break;
-    case 3: group_merge_k<V, 8>(st, A, B, C, t, G, pos_t, log2G, root, sr, cr, si, ci, slice_out); break;
-    case 4: group_merge_k<V, 16>(st, A, B, C, t, G, pos_t, log2G, root, sr, cr, si, ci, slice_out); break;
-    default: group_merge_k<V, 0>(st, A, B, C, t, G, pos_t, log2G, root, sr, cr, si, ci, slice_out); break;
+  if (!r.root)
+    for (int bit = 0; bit < log2G && bit < r.rc; ++bit)
+      if ((t >> bit) & 1u) pos_t += w[bit];
+  switch (r.kb) {
+    case 0: group_merge_k<V, 1, Ops>(r, w, A, B, C, t, G, pos_t, log2G, sr, cr, si, ci, slice_out); break;
+    case 1: group_merge_k<V, 2, Ops>(r, w, A, B, C, t, G, pos_t, log2G, sr, cr, si, ci, slice_out); break;
+    case 2: group_merge_k<V, 4, Ops>(r, w, A, B, C, t, G, pos_t, log2G, sr, cr, si, ci, slice_out); break;
+    case 3: group_merge_k<V, 8, Ops>(r, w, A, B, C, t, G, pos_t, log2G, sr, cr, si, ci, slice_out); break;
+    case 4: group_merge_k<V, 16, Ops>(r, w, A, B, C, t, G, pos_t, log2G, sr, cr, si, ci, slice_out); break;
+    default: group_merge_k<V, 0, Ops>(r, w, A, B, C, t, G, pos_t, log2G, sr, cr, si, ci, slice_out); break;
   }
+}
+
+// Scalars of a step, read once.
+__device__ __forceinline__ StepRegs step_regs(const DevStep& st) {
+  StepRegs r;
+  r.ma = st.ma;
+  r.nb = st.nb;
+  r.kb = st.kb;
+  r.rc = st.ma + st.nb + st.bb;
+  r.root = st.flags & STEP_ROOT;
+  return r;
 }
 
 // Work items: a slice (per-slice programs) or one assignment of the outer
@@ -374,7 +499,7 @@ __device__ __forceinline__ void group_merge(const DevStep& st, const V* A, const
 // bits it depends on, and the root holds the scalars of all slices of the
 // item).  WARP_ITEMS: every warp contracts its own items in its own arena
 // (barriers are warp barriers); otherwise the whole block works on one item.
-template <class V, bool WARP_ITEMS>
+template <class V, bool WARP_ITEMS, class Ops = CplxOps<V>>
 __global__ void __launch_bounds__(256) block_exec_kernel(ExecParams P) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int T = blockDim.x;
@@ -406,10 +531,13 @@ __global__ void __launch_bounds__(256) block_exec_kernel(ExecParams P) {
     double2* slice_out = P.slices ? P.slices + (size_t)xi * S + i : nullptr;
     for (int j = 0; j < P.n_steps; ++j) {
       const DevStep& st = s_steps[j];
-      if (t < (1u << (st.ma + st.nb + st.bb))) {
-        const V* A = (st.flags & STEP_A_LEAF) ? s_lt + leaf_offset(s_leaves[st.a], s) : s_arena + st.a;
-        const V* B = (st.flags & STEP_B_LEAF) ? s_lt + leaf_offset(s_leaves[st.b], s) : s_arena + st.b;
-        group_merge<V>(st, A, B, s_arena + st.c, t, G, log2G, sr, cr, si, ci, slice_out);
+      const StepRegs r = step_regs(st);
+      if (t < (1u << r.rc)) {
+        const uint8_t flags = st.flags;
+        const uint32_t ao = st.a, bo = st.b, co = st.c;
+        const V* A = (flags & STEP_A_LEAF) ? s_lt + leaf_offset(s_leaves[ao], s) : s_arena + ao;
+        const V* B = (flags & STEP_B_LEAF) ? s_lt + leaf_offset(s_leaves[bo], s) : s_arena + bo;
+        group_merge<V, Ops>(r, st.w, A, B, s_arena + co, t, G, log2G, sr, cr, si, ci, slice_out);
       }
       if (WARP_ITEMS) __syncwarp();
       else __syncthreads();
@@ -434,7 +562,7 @@ __global__ void __launch_bounds__(256) block_exec_kernel(ExecParams P) {
 
 // Hoisted merges (no outer slice class below them): run once per bit string
 // (one block each); exported results become pseudo-leaves of the leaf table.
-template <class V>
+template <class V, class Ops = CplxOps<V>>
 __global__ void __launch_bounds__(256) prologue_kernel(const DevStep* __restrict__ steps, int n_steps,
                                                        const DevLeaf* __restrict__ leaves, int n_leaves,
                                                        void* leaf_tables, uint32_t leaf_elems, uint32_t arena_elems) {
@@ -454,11 +582,14 @@ __global__ void __launch_bounds__(256) prologue_kernel(const DevStep* __restrict
   double sr = 0, si = 0, cr = 0, ci = 0;
   for (int j = 0; j < n_steps; ++j) {
     const DevStep& st = s_steps[j];
-    if (threadIdx.x < (1u << (st.ma + st.nb + st.bb))) {
-      const V* A = (st.flags & STEP_A_LEAF) ? s_lt + s_leaves[st.a].base : s_arena + st.a;
-      const V* B = (st.flags & STEP_B_LEAF) ? s_lt + s_leaves[st.b].base : s_arena + st.b;
-      V* C = (st.flags & STEP_EXPORT) ? g_lt + s_leaves[st.c].base : s_arena + st.c;
-      group_merge<V>(st, A, B, C, threadIdx.x, T, log2G, sr, cr, si, ci, nullptr);
+    const StepRegs r = step_regs(st);
+    if (threadIdx.x < (1u << r.rc)) {
+      const uint8_t flags = st.flags;
+      const uint32_t ao = st.a, bo = st.b, co = st.c;
+      const V* A = (flags & STEP_A_LEAF) ? s_lt + s_leaves[ao].base : s_arena + ao;
+      const V* B = (flags & STEP_B_LEAF) ? s_lt + s_leaves[bo].base : s_arena + bo;
+      V* C = (flags & STEP_EXPORT) ? g_lt + s_leaves[co].base : s_arena + co;
+      group_merge<V, Ops>(r, st.w, A, B, C, threadIdx.x, T, log2G, sr, cr, si, ci, nullptr);
     }
     __syncthreads();
   }
@@ -500,17 +631,20 @@ __global__ void __launch_bounds__(128) finalize_kernel(const Partial* __restrict
 
 int g_num_sms = 0;
 
-}  // namespace
+template <class Ops>
+struct LaneCapable : std::false_type {};
+template <class V>
+struct LaneCapable<CplxOps<V>> : std::true_type {};
 
-namespace {
 template <class K>
 bool shape_for_kernel(K kernel, int threads, size_t smem, int* occ) {
   if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return false;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kernel, threads, smem) == cudaSuccess && *occ >= 1;
 }
-}  // namespace
 
-bool exec_shape(const DeviceProgram& prog, int elem_bytes, int nx, uint64_t slices_per_x, ExecShape* out) {
+template <class V, class Ops>
+bool exec_shape_typed(const DeviceProgram& prog, int nx, uint64_t slices_per_x, ExecShape* out) {
+  const int elem_bytes = (int)sizeof(V);
   int dev = 0;
   cudaGetDevice(&dev);
   if (g_num_sms == 0) {
@@ -520,23 +654,25 @@ bool exec_shape(const DeviceProgram& prog, int elem_bytes, int nx, uint64_t slic
   int max_optin = 0;
   cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   ExecShape sh;
-  const bool fp64 = elem_bytes == 16;
   int occ = 0;
   uint64_t per_block_items = 1;
   if (prog.exec == Executor::Lane) {
-    sh.threads = 128;
-    SmemLayout L = smem_layout(prog.n_steps, prog.n_leaves, prog.leaf_elems, prog.arena_elems, elem_bytes,
-                               sh.threads, true);
-    if (L.total > (size_t)max_optin) {
-      sh.threads = 64;
-      L = smem_layout(prog.n_steps, prog.n_leaves, prog.leaf_elems, prog.arena_elems, elem_bytes, sh.threads, true);
+    if constexpr (!LaneCapable<Ops>::value) {
+      return false;
+    } else {
+      sh.threads = 128;
+      SmemLayout L = smem_layout(prog.n_steps, prog.n_leaves, prog.leaf_elems, prog.arena_elems, elem_bytes,
+                                 sh.threads, true);
+      if (L.total > (size_t)max_optin) {
+        sh.threads = 64;
+        L = smem_layout(prog.n_steps, prog.n_leaves, prog.leaf_elems, prog.arena_elems, elem_bytes, sh.threads,
+                        true);
+      }
+      if (L.total > (size_t)max_optin) return false;
+      sh.smem = L.total;
+      if (!shape_for_kernel(lane_exec_kernel<V, Ops>, sh.threads, sh.smem, &occ)) return false;
+      per_block_items = (uint64_t)sh.threads;
     }
-    if (L.total > (size_t)max_optin) return false;
-    sh.smem = L.total;
-    bool ok = fp64 ? shape_for_kernel(lane_exec_kernel<double2>, sh.threads, sh.smem, &occ)
-                   : shape_for_kernel(lane_exec_kernel<float2>, sh.threads, sh.smem, &occ);
-    if (!ok) return false;
-    per_block_items = (uint64_t)sh.threads;
   } else if (prog.exec == Executor::Warp) {
     sh.threads = 256;
     SmemLayout L;
@@ -548,9 +684,7 @@ bool exec_shape(const DeviceProgram& prog, int elem_bytes, int nx, uint64_t slic
     }
     if (L.total > (size_t)max_optin) return false;
     sh.smem = L.total;
-    bool ok = fp64 ? shape_for_kernel(block_exec_kernel<double2, true>, sh.threads, sh.smem, &occ)
-                   : shape_for_kernel(block_exec_kernel<float2, true>, sh.threads, sh.smem, &occ);
-    if (!ok) return false;
+    if (!shape_for_kernel(block_exec_kernel<V, true, Ops>, sh.threads, sh.smem, &occ)) return false;
     per_block_items = (uint64_t)(sh.threads / 32);
   } else {
     sh.threads = 256;
@@ -558,20 +692,16 @@ bool exec_shape(const DeviceProgram& prog, int elem_bytes, int nx, uint64_t slic
                                sh.threads, false);
     if (L.total > (size_t)max_optin) return false;
     sh.smem = L.total;
-    bool ok = fp64 ? shape_for_kernel(block_exec_kernel<double2, false>, sh.threads, sh.smem, &occ)
-                   : shape_for_kernel(block_exec_kernel<float2, false>, sh.threads, sh.smem, &occ);
-    if (!ok) return false;
+    if (!shape_for_kernel(block_exec_kernel<V, false, Ops>, sh.threads, sh.smem, &occ)) return false;
   }
   if (prog.n_pro_steps > 0) {
     const SmemLayout PL = smem_layout(prog.n_pro_steps, prog.n_leaves, prog.leaf_elems, prog.pro_arena_elems,
                                       elem_bytes, 256, false);
     if (PL.total > (size_t)max_optin) return false;
     sh.pro_smem = PL.total;
-    cudaError_t pe = fp64 ? cudaFuncSetAttribute(prologue_kernel<double2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)PL.total)
-                          : cudaFuncSetAttribute(prologue_kernel<float2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)PL.total);
-    if (pe != cudaSuccess) return false;
+    if (cudaFuncSetAttribute(prologue_kernel<V, Ops>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PL.total) !=
+        cudaSuccess)
+      return false;
   }
   const uint64_t total_blocks = (uint64_t)g_num_sms * (uint64_t)occ;
   uint64_t per_x = total_blocks / (uint64_t)(nx > 0 ? nx : 1);
@@ -584,33 +714,20 @@ bool exec_shape(const DeviceProgram& prog, int elem_bytes, int nx, uint64_t slic
   return true;
 }
 
-cudaError_t launch_contraction(const DeviceProgram& prog, bool fp64, const uint8_t* d_x, int nx,
-                               uint64_t slice_lo, uint64_t slice_hi, const LaunchBuffers& buf,
-                               const ExecShape& shape, double scale, double2* d_out, Partial* d_raw,
-                               double2* d_slices, cudaStream_t stream, cudaEvent_t ev0, cudaEvent_t ev1) {
-  if (nx <= 0) return cudaSuccess;
+template <class V, class Ops>
+cudaError_t launch_typed(const DeviceProgram& prog, const uint8_t* d_x, int nx, uint64_t slice_lo, uint64_t slice_hi,
+                         const LaunchBuffers& buf, const ExecShape& shape, double scale, double2* d_out,
+                         Partial* d_raw, double2* d_slices, cudaStream_t stream, cudaEvent_t ev0, cudaEvent_t ev1) {
   const unsigned lgrid = (unsigned)prog.n_leaves * (unsigned)nx;
-  if (fp64)
-    leaf_build_kernel<double2><<<lgrid, 32, 0, stream>>>(prog.leaves, prog.gate_q, prog.gate_layer, prog.gate_in_h,
-                                                          prog.gate_out_kind, prog.gamma, prog.beta, d_x, prog.n,
-                                                          prog.leaf_elems, prog.n_leaves,
-                                                          static_cast<double2*>(buf.leaf_tables));
-  else
-    leaf_build_kernel<float2><<<lgrid, 32, 0, stream>>>(prog.leaves, prog.gate_q, prog.gate_layer, prog.gate_in_h,
-                                                         prog.gate_out_kind, prog.gamma, prog.beta, d_x, prog.n,
-                                                         prog.leaf_elems, prog.n_leaves,
-                                                         static_cast<float2*>(buf.leaf_tables));
+  leaf_build_kernel<V><<<lgrid, 32, 0, stream>>>(prog.leaves, prog.gate_q, prog.gate_layer, prog.gate_in_h,
+                                                 prog.gate_out_kind, prog.gamma, prog.beta, d_x, prog.n,
+                                                 prog.leaf_elems, prog.n_leaves, static_cast<V*>(buf.leaf_tables));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (prog.n_pro_steps > 0) {
-    if (fp64)
-      prologue_kernel<double2><<<nx, 256, shape.pro_smem, stream>>>(prog.pro_steps, prog.n_pro_steps, prog.leaves,
-                                                                   prog.n_leaves, buf.leaf_tables, prog.leaf_elems,
-                                                                   prog.pro_arena_elems);
-    else
-      prologue_kernel<float2><<<nx, 256, shape.pro_smem, stream>>>(prog.pro_steps, prog.n_pro_steps, prog.leaves,
-                                                                  prog.n_leaves, buf.leaf_tables, prog.leaf_elems,
-                                                                  prog.pro_arena_elems);
+    prologue_kernel<V, Ops><<<nx, 256, shape.pro_smem, stream>>>(prog.pro_steps, prog.n_pro_steps, prog.leaves,
+                                                                 prog.n_leaves, buf.leaf_tables, prog.leaf_elems,
+                                                                 prog.pro_arena_elems);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
@@ -633,20 +750,15 @@ cudaError_t launch_contraction(const DeviceProgram& prog, bool fp64, const uint8
     if (e != cudaSuccess) return e;
   }
   if (prog.exec == Executor::Lane) {
-    if (fp64)
-      lane_exec_kernel<double2><<<grid, shape.threads, shape.smem, stream>>>(P, buf.err);
-    else
-      lane_exec_kernel<float2><<<grid, shape.threads, shape.smem, stream>>>(P, buf.err);
+    if constexpr (LaneCapable<Ops>::value) {
+      lane_exec_kernel<V, Ops><<<grid, shape.threads, shape.smem, stream>>>(P, buf.err);
+    } else {
+      return cudaErrorInvalidValue;
+    }
   } else if (prog.exec == Executor::Warp) {
-    if (fp64)
-      block_exec_kernel<double2, true><<<grid, shape.threads, shape.smem, stream>>>(P);
-    else
-      block_exec_kernel<float2, true><<<grid, shape.threads, shape.smem, stream>>>(P);
+    block_exec_kernel<V, true, Ops><<<grid, shape.threads, shape.smem, stream>>>(P);
   } else {
-    if (fp64)
-      block_exec_kernel<double2, false><<<grid, shape.threads, shape.smem, stream>>>(P);
-    else
-      block_exec_kernel<float2, false><<<grid, shape.threads, shape.smem, stream>>>(P);
+    block_exec_kernel<V, false, Ops><<<grid, shape.threads, shape.smem, stream>>>(P);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -656,6 +768,40 @@ cudaError_t launch_contraction(const DeviceProgram& prog, bool fp64, const uint8
   }
   finalize_kernel<<<nx, 128, 0, stream>>>(buf.partials, shape.blocks_per_x, scale, d_out, d_raw);
   return cudaGetLastError();
+}
+
+}  // namespace
+
+int arith_elem_bytes(Arith a) { return (a == Arith::F64 || a == Arith::F32X2) ? 16 : 8; }
+
+#define QTN_ARITH_SWITCH(a, CALL)                                     \
+  switch (a) {                                                        \
+    case Arith::F64: return CALL(double2, CplxOps<double2>);          \
+    case Arith::F32: return CALL(float2, CplxOps<float2>);            \
+    case Arith::F32X2: return CALL(dfc, CplxOps<dfc>);                \
+    case Arith::TF32: return CALL(float2, RoundOps<Round::TF32>);     \
+    case Arith::BF16X3: return CALL(float2, RoundOps<Round::BF16X3>); \
+    case Arith::TF32X3: return CALL(float2, RoundOps<Round::TF32X3>); \
+    case Arith::BF16X6: return CALL(float2, RoundOps<Round::BF16X6>); \
+  }
+
+bool exec_shape(const DeviceProgram& prog, Arith a, int nx, uint64_t slices_per_x, ExecShape* out) {
+#define QTN_SHAPE_CALL(V, O) exec_shape_typed<V, O>(prog, nx, slices_per_x, out)
+  QTN_ARITH_SWITCH(a, QTN_SHAPE_CALL)
+#undef QTN_SHAPE_CALL
+  return false;
+}
+
+cudaError_t launch_contraction(const DeviceProgram& prog, Arith a, const uint8_t* d_x, int nx, uint64_t slice_lo,
+                               uint64_t slice_hi, const LaunchBuffers& buf, const ExecShape& shape, double scale,
+                               double2* d_out, Partial* d_raw, double2* d_slices, cudaStream_t stream,
+                               cudaEvent_t ev0, cudaEvent_t ev1) {
+  if (nx <= 0) return cudaSuccess;
+#define QTN_LAUNCH_CALL(V, O) \
+  launch_typed<V, O>(prog, d_x, nx, slice_lo, slice_hi, buf, shape, scale, d_out, d_raw, d_slices, stream, ev0, ev1)
+  QTN_ARITH_SWITCH(a, QTN_LAUNCH_CALL)
+#undef QTN_LAUNCH_CALL
+  return cudaErrorInvalidValue;
 }
 
 }  // namespace qtn

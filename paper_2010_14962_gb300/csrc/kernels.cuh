@@ -11,6 +11,13 @@ namespace qtn {
 
 enum class Executor : int { Lane = 0, Block = 1, Warp = 2 };
 
+// Arithmetic of the merges: complex128, complex64, double-float complex64
+// (FP32X2), and complex64 storage with products rounded as the tensor cores
+// would (TF32; BF16 / TF32 split in two, 3 products; BF16 split in three,
+// 6 products), FP32 accumulation.
+enum class Arith : int { F64, F32, F32X2, TF32, BF16X3, TF32X3, BF16X6 };
+int arith_elem_bytes(Arith a);
+
 // Compensated (Kahan) partial sum of complex slice results: the running sums
 // (re, im) and their compensations (cre, cim).
 struct alignas(16) Partial {
@@ -46,16 +53,16 @@ struct LaunchBuffers {
   int* err = nullptr;            // set non-zero by a kernel that met a bad step
 };
 
-// Grid shape and dynamic shared memory of the executor for `prog`, `nx` and
-// element size `elem_bytes` (8: complex64, 16: complex128).  Returns false if
-// the program does not fit on chip.
+// Grid shape and dynamic shared memory of the executor for `prog`, `nx` bit
+// strings and arithmetic `arith`.  Returns false if the program does not fit
+// on chip (or the executor has no kernel for that arithmetic).
 struct ExecShape {
   int threads = 0;
   int blocks_per_x = 0;
   size_t smem = 0;
   size_t pro_smem = 0;  // prologue kernel (one block of 256 threads per bit string)
 };
-bool exec_shape(const DeviceProgram& prog, int elem_bytes, int nx, uint64_t slices_per_x, ExecShape* out);
+bool exec_shape(const DeviceProgram& prog, Arith arith, int nx, uint64_t slices_per_x, ExecShape* out);
 
 // Enqueues leaf build + execution + finalisation on `stream`.
 //   d_x       : nx * n bit bytes (device)
@@ -63,7 +70,7 @@ bool exec_shape(const DeviceProgram& prog, int elem_bytes, int nx, uint64_t slic
 //   d_raw     : nx Partial (unscaled Kahan sum and compensation), may be null
 //   d_slices  : nx * (slice_hi - slice_lo) double2, may be null
 //   ev0, ev1  : optional events recorded just before / after the executor
-cudaError_t launch_contraction(const DeviceProgram& prog, bool fp64, const uint8_t* d_x, int nx,
+cudaError_t launch_contraction(const DeviceProgram& prog, Arith arith, const uint8_t* d_x, int nx,
                                uint64_t slice_lo, uint64_t slice_hi, const LaunchBuffers& buf,
                                const ExecShape& shape, double scale, double2* d_out, Partial* d_raw,
                                double2* d_slices, cudaStream_t stream, cudaEvent_t ev0 = nullptr,

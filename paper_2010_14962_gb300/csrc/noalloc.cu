@@ -78,8 +78,8 @@ extern "C" qtn_status qtn_contract_amplitudes_noalloc(const qtn_plan_t* plan, co
     return internal::set_error(QTN_ERR_UNSUPPORTED, "precision not available on this plan's executor");
   std::lock_guard<std::mutex> lk(*pv.mu);
   const Program& pg = *pv.program;
-  const bool fp64 = prec == QTN_FP64;
-  const size_t elem = fp64 ? sizeof(double2) : sizeof(float2);
+  const Arith arith = prec == QTN_FP64 ? Arith::F64 : Arith::F32;
+  const size_t elem = (size_t)arith_elem_bytes(arith);
   const uint64_t S = 1ull << pv.k;
 
   DeviceProgram dp;
@@ -94,7 +94,7 @@ extern "C" qtn_status qtn_contract_amplitudes_noalloc(const qtn_plan_t* plan, co
   dp.pro_arena_elems = pg.pro_arena_elems;
   dp.exec = pv.lane ? Executor::Lane : Executor::Block;
   ExecShape sh;
-  if (!exec_shape(dp, (int)elem, nx, S, &sh))
+  if (!exec_shape(dp, arith, nx, S, &sh))
     return internal::set_error(QTN_ERR_UNSUPPORTED, "the plan's per-slice working set does not fit in shared memory");
 
   // Scratch layout: program | gate data | angles | leaf tables | partials | error word.
@@ -164,7 +164,7 @@ extern "C" qtn_status qtn_contract_amplitudes_noalloc(const qtn_plan_t* plan, co
   buf.partials = reinterpret_cast<Partial*>(base + o_pa);
   buf.err = reinterpret_cast<int*>(base + o_err);
   const double scale = std::pow(2.0, -0.5 * pv.n);
-  e = launch_contraction(dp, fp64, d_x, nx, 0, S, buf, sh, scale, reinterpret_cast<double2*>(d_out), nullptr, nullptr,
+  e = launch_contraction(dp, arith, d_x, nx, 0, S, buf, sh, scale, reinterpret_cast<double2*>(d_out), nullptr, nullptr,
                          stream);
   if (e != cudaSuccess)
     return internal::set_error(QTN_ERR_CUDA, std::string("launch_contraction: ") + cudaGetErrorString(e));

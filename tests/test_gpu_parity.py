@@ -12,6 +12,7 @@ Tolerances (relative error |a - a*| / |a*| unless stated):
     sum_s |a_s| from the oracle's per-slice values.  Where that sum is not
     computed, the relative bound stated at the test is used.
 """
+import ctypes
 import math
 
 import numpy as np
@@ -220,9 +221,12 @@ def test_edge_cases(gpu):
         for xi in (0, 17, 63):
             x = [(xi >> q) & 1 for q in range(6)]
             assert rel(plan2.contract_amplitude(x, "fp64"), sv2[xi]) < 1e-12
-    with pytest.raises(qtn.QTNError) as ei:
-        plan.contract_amplitude([0, 1], "bf16x6")
-    assert ei.value.status == 6
+    L = qtn.lib()
+    xb = np.zeros(2, np.uint8)
+    out = np.zeros(2)
+    st = L.qtn_contract_amplitude(plan.handle, xb.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8)), 99,
+                                  ctypes.c_void_p(0), out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    assert st == 6  # unknown precision
     with pytest.raises(qtn.QTNError):
         plan.contract_amplitude([0, 2], "fp64")
 
@@ -247,3 +251,39 @@ def test_batch_of_plans(gpu):
     for g, inst, pl, x in zip(got, insts, plans, xs):
         ref = O.tn_amplitude(inst.n, inst.edges, inst.gamma, inst.beta, x).value
         assert rel(g, ref) < 1e-10
+
+
+# Unit roundoff of each arithmetic's products (first order): TF32 keeps 10
+# fraction bits (u = 2^-11); a 2-piece split drops the lo*lo product
+# (2^-16 for BF16, 2^-22 for TF32); the 3-piece BF16 split and FP32 keep
+# FP32 accuracy (2^-24); the double-float pair carries ~2^-44.
+PREC_U = {"fp32": 2.0 ** -24, "tf32": 2.0 ** -11, "bf16x3": 2.0 ** -16, "tf32x3": 2.0 ** -22,
+          "bf16x6": 2.0 ** -24, "fp32x2": 2.0 ** -44}
+
+
+@pytest.fixture(scope="module")
+def config80_l1(config80):
+    inst, plan, xs, refs = config80
+    ref = O.tn_amplitude(80, inst.edges, inst.gamma, inst.beta, xs[0], cuts=plan.cut_names(), per_slice=True,
+                         threads=16)
+    return ref.value, np.sum(np.abs(ref.per_slice))
+
+
+@pytest.mark.parametrize("prec", sorted(PREC_U))
+def test_precision_sweep_n80(gpu, config80, config80_l1, prec):
+    # Sec. III.A slices summed in FP64; merges in each arithmetic.  Bound:
+    # |a - a*| <= 2 G u sum_s |a_s| (G gates, coherent first-order rounding).
+    inst, plan, xs, refs = config80
+    ref, l1 = config80_l1
+    got = device_amplitudes(plan, xs[:1], prec)[0]
+    bound = 2 * len(inst.edges) * PREC_U[prec] * l1
+    print(prec, "rel err", abs(got - ref) / abs(ref), "bound/|a|", bound / abs(ref))
+    assert abs(got - ref) <= max(bound, 1e-12 * abs(ref))
+
+
+def test_fp32x2_meets_fp64_accuracy(gpu, config80):
+    # The double-float form is the mixed-precision variant that meets the
+    # 1e-10 bound of the complex128 path on all 8 bit strings.
+    inst, plan, xs, refs = config80
+    got = device_amplitudes(plan, xs, "fp32x2")
+    assert np.max(np.abs(got - refs) / np.abs(refs)) < 1e-10
