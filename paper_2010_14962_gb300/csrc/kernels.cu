@@ -531,8 +531,12 @@ __global__ void __launch_bounds__(256) block_exec_kernel(ExecParams P) {
     double2* slice_out = P.slices ? P.slices + (size_t)xi * S + i : nullptr;
     for (int j = 0; j < P.n_steps; ++j) {
       const DevStep& st = s_steps[j];
-      const StepRegs r = step_regs(st);
-      if (t < (1u << r.rc)) {
+      // One 32-bit read (ma | nb | kb | bb) decides whether this thread has an
+      // output; most merges of an item are small, so most warps skip here.
+      const uint32_t hdr = *reinterpret_cast<const uint32_t*>(&st);
+      const int rc_h = (int)((hdr & 0xffu) + ((hdr >> 8) & 0xffu) + (hdr >> 24));
+      if (t < (1u << rc_h)) {
+        const StepRegs r = step_regs(st);
         const uint8_t flags = st.flags;
         const uint32_t ao = st.a, bo = st.b, co = st.c;
         const V* A = (flags & STEP_A_LEAF) ? s_lt + leaf_offset(s_leaves[ao], s) : s_arena + ao;

@@ -62,7 +62,8 @@ enum StepFlags : uint8_t {
 };
 
 // One merge.  The canonical C element o = m + (n << ma) + (b << (ma + nb))
-// is stored at arena offset c + sum_i bit(o, i) * w[i].
+// is stored at arena offset c + sum_i bit(o, i) * w[i].  The first four
+// bytes (ma, nb, kb, bb) are read by the executors as one 32-bit word.
 struct DevStep {
   uint8_t ma, nb, kb, bb;  // log2 sizes of m, n, k, b
   uint8_t flags, pad0, pad1, pad2;
