@@ -95,8 +95,10 @@ qtn_status qtn_network_index(const qtn_network_t* net, int index, int* qubit, in
 
 /* Cut-set search used when qtn_plan gets cuts == NULL. */
 typedef enum {
-  QTN_SEARCH_GREEDY = 0, /* cut the index that most lowers the width, k times */
-  QTN_SEARCH_GA = 1      /* Algorithm 1 (Sec. III.B), seeded with the greedy set */
+  QTN_SEARCH_GREEDY = 0,  /* cut the index that most lowers the width, k times */
+  QTN_SEARCH_GA = 1,      /* Algorithm 1 (Sec. III.B), seeded with the greedy set;
+                             fitness = width, then total flops */
+  QTN_SEARCH_GA_FLOPS = 2 /* Algorithm 1 with total log2 flops as the fitness */
 } qtn_search;
 
 typedef struct {
@@ -106,9 +108,14 @@ typedef struct {
   int ga_T;          /* GA maximum iteration counter (default 4) */
   int ga_N;          /* GA population size (default 11) */
   double max_slice_bytes; /* 0 = no cap; else largest per-slice working set */
+  int ga_seed_greedy;     /* GA: start from the greedy set plus random sets
+                             (default 1) or from random sets only (0) */
+  double time_budget_s;   /* GA: stop after the generation that exceeds it
+                             (0 = run all T + 1 generations) */
 } qtn_plan_opts;
 
-/* Fills `opts` with the defaults (greedy search, k = 0, T = 4, N = 11). */
+/* Fills `opts` with the defaults (greedy search, k = 0, T = 4, N = 11,
+ * greedy seed, no time budget). */
 void qtn_plan_opts_default(qtn_plan_opts* opts);
 
 /* Plans the sliced contraction (Sec. III.A) of `net`.
@@ -219,6 +226,64 @@ qtn_status qtn_plan_select_executor(const qtn_plan_t* plan, qtn_precision prec, 
  * call once its stream has been synchronised. */
 qtn_status qtn_plan_set_kernel_timing(const qtn_plan_t* plan, int on);
 qtn_status qtn_plan_kernel_ms(const qtn_plan_t* plan, float* ms);
+
+/* ------------------------------------------------ learned cost surrogate --
+ * A small MLP predicts the exact counter's log2 total flops and log2 peak
+ * bytes of cutting a set of indices (min-fill plan) from cheap features, so a
+ * genetic cut search (Algorithm 1, Sec. III.B) can rank far more candidates;
+ * the exact counter still judges the candidates the search keeps.  Training
+ * and inference run on the device (FP32, the library's own kernels). */
+typedef struct qtn_mlp qtn_mlp_t;
+#define QTN_SURROGATE_FEATURES 48
+#define QTN_SURROGATE_TARGETS 2
+
+/* Features of cutting `cuts` (k index ids) out of `net` (host, 48 floats):
+ * sizes, the cut pattern, the gate graph left after cutting and the bag
+ * sizes of a min-degree elimination. */
+qtn_status qtn_surrogate_features(const qtn_network_t* net, const int32_t* cuts, int k, float* out);
+/* The exact labels of the same (host, 2 floats): log2 total flops and log2
+ * peak bytes of the min-fill plan. */
+qtn_status qtn_surrogate_labels(const qtn_network_t* net, const int32_t* cuts, int k, float* out);
+
+/* `count` labelled samples (host X: count x 48, Y: count x 2 = exact log2
+ * flops, log2 peak bytes) on random connected 3-regular graphs with even
+ * n in [n_lo, n_hi], p in [p_lo, p_hi], k in [k_lo, k_hi]; sample i depends
+ * only on (seed, i); `threads` host threads. */
+qtn_status qtn_surrogate_dataset(int count, int n_lo, int n_hi, int p_lo, int p_hi, int k_lo, int k_hi,
+                                 uint64_t seed, int threads, float* X, float* Y);
+
+/* An MLP in -> hidden -> hidden -> out (ReLU), He-initialised from `seed`. */
+qtn_status qtn_mlp_create(int in, int hidden, int out, uint64_t seed, qtn_mlp_t** mlp);
+void qtn_mlp_destroy(qtn_mlp_t* mlp);
+qtn_status qtn_mlp_num_params(const qtn_mlp_t* mlp, size_t* n);
+/* Parameters (host, num_params floats: W1 b1 W2 b2 W3 b3, row-major W[out][in])
+ * read (set = 0) or written (set = 1). */
+qtn_status qtn_mlp_params(qtn_mlp_t* mlp, float* params, int set);
+/* Input / target normalisation (mean, std per column) read or written. */
+qtn_status qtn_mlp_normalisation(qtn_mlp_t* mlp, float* x_mean, float* x_std, float* y_mean, float* y_std,
+                                 int set);
+/* Gradients (host, num_params floats) of mean((Y_pred - Y)^2) over the n x out
+ * normalised outputs for raw rows X (n x in), Y (n x out); *loss (optional)
+ * receives that mean.  No parameter changes. */
+qtn_status qtn_mlp_gradients(qtn_mlp_t* mlp, const float* X, const float* Y, int n, float* grads, float* loss);
+/* Trains with Adam (lr, betas 0.9/0.999) on mini-batches of `batch` shuffled
+ * rows for `epochs` epochs; the normalisation is set from X, Y.  epoch_loss
+ * (optional, host, epochs floats) receives the mean loss of each epoch. */
+qtn_status qtn_mlp_fit(qtn_mlp_t* mlp, const float* X, const float* Y, int n, int epochs, int batch, float lr,
+                       uint64_t seed, float* epoch_loss);
+/* Predictions (host Y: n x out) for raw feature rows (host X: n x in). */
+qtn_status qtn_mlp_predict(qtn_mlp_t* mlp, const float* X, int n, float* Y);
+
+/* Surrogate-guided genetic cut search for k cuts: population N (seeded with
+ * the greedy set if seed_greedy, else random), generations t = 0..T ranked by the surrogate's predicted
+ * log2 flops; each generation the `top` best are evaluated exactly and the
+ * best exact set is kept.  Writes the best set by the exact counter (k
+ * entries), its exact log2 total flops, the numbers of exact and surrogate
+ * evaluations, and the best exact value per generation (trace). */
+qtn_status qtn_search_cuts_surrogate(const qtn_network_t* net, int k, qtn_mlp_t* mlp, int T, int N, int top,
+                                     uint64_t seed, int seed_greedy, int32_t* cuts, double* best_log2_flops,
+                                     int* exact_evals, int* surrogate_evals, double* trace, int trace_cap,
+                                     int* trace_len);
 
 /* Introspection: a JSON description of the plan (cuts, elimination order,
  * merges, tensor index sets, both executors' step programs, gate legs), for

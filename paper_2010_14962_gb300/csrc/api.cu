@@ -441,6 +441,8 @@ void qtn_plan_opts_default(qtn_plan_opts* o) {
   o->ga_T = 4;
   o->ga_N = 11;
   o->max_slice_bytes = 0;
+  o->ga_seed_greedy = 1;
+  o->time_budget_s = 0;
 }
 
 qtn_status qtn_plan(const qtn_network_t* net, const int32_t* cuts, int k, const int32_t* order, int order_len,
@@ -457,14 +459,19 @@ qtn_status qtn_plan(const qtn_network_t* net, const int32_t* cuts, int k, const 
   } else {
     if (opts.k < 0 || opts.k > (int)net->net.indices.size()) return fail(QTN_ERR_INVALID_ARG, "opts.k out of range");
     cutv = greedy_cuts(net->net, opts.k);
-    if (opts.search == QTN_SEARCH_GA && opts.k > 0) {
+    if ((opts.search == QTN_SEARCH_GA || opts.search == QTN_SEARCH_GA_FLOPS) && opts.k > 0) {
       GAOptions ga;
       ga.T = opts.ga_T;
       ga.N = opts.ga_N;
       ga.seed = opts.seed;
-      GAResult r = genetic_cuts(net->net, opts.k, ga, {cutv}, default_fitness, nullptr);
+      ga.time_budget_s = opts.time_budget_s;
+      std::vector<std::vector<int>> seeds;
+      if (opts.ga_seed_greedy) seeds.push_back(cutv);
+      GAResult r = genetic_cuts(net->net, opts.k, ga, seeds,
+                                opts.search == QTN_SEARCH_GA ? default_fitness : flops_fitness, nullptr);
       cutv = r.best;
-    } else if (opts.search != QTN_SEARCH_GREEDY && opts.search != QTN_SEARCH_GA) {
+    } else if (opts.search != QTN_SEARCH_GREEDY && opts.search != QTN_SEARCH_GA &&
+               opts.search != QTN_SEARCH_GA_FLOPS) {
       return fail(QTN_ERR_INVALID_ARG, "unknown search");
     }
   }
@@ -573,6 +580,8 @@ bool plan_view(const qtn_plan_t* cplan, PlanView* view) {
 
 qtn_status set_error(qtn_status s, const std::string& msg) { return fail(s, msg); }
 
+const Network* network_of(const qtn_network_t* net) { return net ? &net->net : nullptr; }
+
 }  // namespace internal
 }  // namespace qtn
 
@@ -629,14 +638,16 @@ qtn_status qtn_search_cuts(const qtn_network_t* net, const qtn_plan_opts* opts, 
       tr.push_back(default_fitness(net->net, cur, nullptr));
     }
     best = cur;
-  } else if (opts->search == QTN_SEARCH_GA) {
+  } else if (opts->search == QTN_SEARCH_GA || opts->search == QTN_SEARCH_GA_FLOPS) {
     GAOptions ga;
     ga.T = opts->ga_T;
     ga.N = opts->ga_N;
     ga.seed = opts->seed;
+    ga.time_budget_s = opts->time_budget_s;
     std::vector<std::vector<int>> seeds;
-    if (opts->k > 0) seeds.push_back(greedy_cuts(net->net, opts->k));
-    GAResult r = genetic_cuts(net->net, opts->k, ga, seeds, default_fitness, nullptr);
+    if (opts->k > 0 && opts->ga_seed_greedy) seeds.push_back(greedy_cuts(net->net, opts->k));
+    GAResult r = genetic_cuts(net->net, opts->k, ga, seeds,
+                              opts->search == QTN_SEARCH_GA ? default_fitness : flops_fitness, nullptr);
     best = r.best;
     tr = r.best_fitness_per_generation;
     evals = r.evaluations;

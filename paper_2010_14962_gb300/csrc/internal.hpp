@@ -24,6 +24,9 @@ struct PlanView {
 // Fills `view` for `plan`; returns false if plan is NULL.
 bool plan_view(const qtn_plan_t* plan, PlanView* view);
 
+// The host network behind a handle.
+const Network* network_of(const qtn_network_t* net);
+
 // Sets the calling thread's qtn_last_error() text and returns `s`.
 qtn_status set_error(qtn_status s, const std::string& msg);
 

@@ -182,6 +182,31 @@ __device__ __forceinline__ void kahan_add(double& sum, double& comp, double v) {
   sum = t;
 }
 
+// Sum of two compensated partials (value = sum - compensation): the sums are
+// added with TwoSum and the rounding error joins the compensations.
+__device__ __forceinline__ double two_sum_d(double a, double b, double& err) {
+  const double s = a + b;
+  const double bb = s - a;
+  err = (a - (s - bb)) + (b - bb);
+  return s;
+}
+__device__ __forceinline__ Partial combine(const Partial& x, const Partial& y) {
+  double er, ei;
+  const double sr = two_sum_d(x.re, y.re, er);
+  const double si = two_sum_d(x.im, y.im, ei);
+  return Partial::make(sr, si, x.cre + y.cre - er, x.cim + y.cim - ei);
+}
+
+// Fixed-order pairwise reduction of `n` partials in shared memory (n a power
+// of two, all threads of the block call it); the result is in red[0].
+__device__ __forceinline__ void tree_reduce(Partial* red, int n) {
+  for (int w = n / 2; w > 0; w >>= 1) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < w; t += blockDim.x) red[t] = combine(red[t], red[t + w]);
+  }
+  __syncthreads();
+}
+
 // Offset of slice s's sub-block inside a leaf: cut legs are the high bits.
 __device__ __forceinline__ uint32_t leaf_offset(const DevLeaf& L, uint64_t s) {
   uint32_t off = L.base;
@@ -403,18 +428,8 @@ __global__ void __launch_bounds__(128) lane_exec_kernel(ExecParams P, int* err) 
     if (P.slices) P.slices[(size_t)xi * S + i] = make_double2(Ops::re(res), Ops::im(res));
   }
   s_red[threadIdx.x] = Partial::make(sr, si, cr, ci);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = 0, b = 0, ca = 0, cb = 0;
-    for (int t = 0; t < T; ++t) {
-      const Partial v = s_red[t];
-      kahan_add(a, ca, v.re);
-      kahan_add(a, ca, -v.cre);
-      kahan_add(b, cb, v.im);
-      kahan_add(b, cb, -v.cim);
-    }
-    P.partials[(size_t)xi * P.blocks_per_x + bx] = Partial::make(a, b, ca, cb);
-  }
+  tree_reduce(s_red, T);
+  if (threadIdx.x == 0) P.partials[(size_t)xi * P.blocks_per_x + bx] = s_red[0];
 }
 
 // ------------------------------------------------------------ block exec --
@@ -548,18 +563,8 @@ __global__ void __launch_bounds__(256) block_exec_kernel(ExecParams P) {
     }
   }
   s_red[threadIdx.x] = Partial::make(sr, si, cr, ci);
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double a = 0, b = 0, ca = 0, cb = 0;
-    for (int tt = 0; tt < T; ++tt) {
-      const Partial v = s_red[tt];
-      kahan_add(a, ca, v.re);
-      kahan_add(a, ca, -v.cre);
-      kahan_add(b, cb, v.im);
-      kahan_add(b, cb, -v.cim);
-    }
-    P.partials[(size_t)xi * P.blocks_per_x + bx] = Partial::make(a, b, ca, cb);
-  }
+  tree_reduce(s_red, T);
+  if (threadIdx.x == 0) P.partials[(size_t)xi * P.blocks_per_x + bx] = s_red[0];
 }
 
 // -------------------------------------------------------------- prologue --
@@ -602,8 +607,9 @@ __global__ void __launch_bounds__(256) prologue_kernel(const DevStep* __restrict
 // -------------------------------------------------------------- finalize --
 
 // One block per bit string: thread t adds partials t, t + T, ... in order
-// (compensated), then the per-thread sums are added in thread order.  The
-// grouping depends only on the block count, so the result is deterministic.
+// (compensated), then the per-thread partials are combined by a fixed
+// pairwise tree.  The grouping depends only on the block count, so the result
+// is deterministic.
 __global__ void __launch_bounds__(128) finalize_kernel(const Partial* __restrict__ partials, int blocks,
                                                        double scale, double2* __restrict__ out,
                                                        Partial* __restrict__ raw) {
@@ -618,18 +624,11 @@ __global__ void __launch_bounds__(128) finalize_kernel(const Partial* __restrict
     kahan_add(b, cb, -v.cim);
   }
   red[threadIdx.x] = Partial::make(a, b, ca, cb);
-  __syncthreads();
+  tree_reduce(red, 128);
   if (threadIdx.x == 0) {
-    a = b = ca = cb = 0;
-    for (int t = 0; t < (int)blockDim.x; ++t) {
-      const Partial v = red[t];
-      kahan_add(a, ca, v.re);
-      kahan_add(a, ca, -v.cre);
-      kahan_add(b, cb, v.im);
-      kahan_add(b, cb, -v.cim);
-    }
-    if (out) out[xi] = make_double2((a - ca) * scale, (b - cb) * scale);
-    if (raw) raw[xi] = Partial::make(a, b, ca, cb);
+    const Partial v = red[0];
+    if (out) out[xi] = make_double2((v.re - v.cre) * scale, (v.im - v.cim) * scale);
+    if (raw) raw[xi] = v;
   }
 }
 

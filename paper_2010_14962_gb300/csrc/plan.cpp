@@ -1,6 +1,7 @@
 #include "plan.hpp"
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <limits>
@@ -37,8 +38,12 @@ namespace {
 // order, merging the two tensors that hold the eliminated index.  Fills
 // `plan` (when non-null) with the merge list and tensor index sets, and
 // always fills `cost`.
+// With `min_degree` the index whose merged bag is smallest is taken (no fill
+// computation: a cheap estimate); `bag_sizes` (optional) receives |A u B| of
+// every merge.
 std::string eliminate(const Network& net, const std::vector<char>& is_cut,
-                      const std::vector<int>* given_order, Plan* plan, Cost* cost) {
+                      const std::vector<int>* given_order, Plan* plan, Cost* cost, bool min_degree = false,
+                      std::vector<int>* bag_sizes = nullptr) {
   const int I = (int)net.indices.size();
   const int L = (int)net.gates.size();
   const int W = (I + 63) / 64;
@@ -93,6 +98,7 @@ std::string eliminate(const Network& net, const std::vector<char>& is_cut,
     }
     int c = (int)T.size();
     int rc = C.count();
+    if (bag_sizes) bag_sizes->push_back(u_size);
     width = std::max(width, u_size);
     max_rank = std::max(max_rank, rc);
     macs += std::ldexp(1.0, u_size);
@@ -127,6 +133,19 @@ std::string eliminate(const Network& net, const std::vector<char>& is_cut,
       while (order_pos < given_order->size() && !alive_i[(*given_order)[order_pos]]) order_pos++;
       if (order_pos == given_order->size()) return "order does not cover every non-cut index";
       best = (*given_order)[order_pos++];
+    } else if (min_degree) {
+      int best_size = 1 << 30;
+      for (int e = 0; e < I; ++e) {
+        if (!alive_i[e]) continue;
+        const Bits& A = T[where[e][0]];
+        const Bits& B = T[where[e][1]];
+        int size = 0;
+        for (int j = 0; j < W; ++j) size += __builtin_popcountll(A.w[j] | B.w[j]);
+        if (size < best_size) {
+          best_size = size;
+          best = e;
+        }
+      }
     } else {
       long best_fill = std::numeric_limits<long>::max();
       int best_size = 0;
@@ -226,6 +245,19 @@ std::string make_plan(const Network& net, const std::vector<int>& cuts,
   return "";
 }
 
+Cost min_degree_cost(const Network& net, const std::vector<int>& cuts, std::vector<int>* bag_sizes) {
+  std::vector<char> is_cut;
+  Cost c{};
+  c.k = (int)cuts.size();
+  if (!check_cuts(net, cuts, &is_cut).empty()) {
+    c.width = 1 << 20;
+    c.macs = std::numeric_limits<double>::infinity();
+    return c;
+  }
+  eliminate(net, is_cut, nullptr, nullptr, &c, true, bag_sizes);
+  return c;
+}
+
 Cost plan_cost(const Network& net, const std::vector<int>& cuts) {
   std::vector<char> is_cut;
   Cost c{};
@@ -287,6 +319,10 @@ double default_fitness(const Network& net, const std::vector<int>& cuts, void*) 
   Cost c = plan_cost(net, cuts);
   // Width first (the paper's tree width), then total log2 flops (< 128).
   return (double)c.width + c.log2_flops_total() / 128.0;
+}
+
+double flops_fitness(const Network& net, const std::vector<int>& cuts, void*) {
+  return plan_cost(net, cuts).log2_flops_total();
 }
 
 namespace {
@@ -357,6 +393,7 @@ GAResult genetic_cuts(const Network& net, int M, const GAOptions& opt,
   };
   const int tail = M / 2;
   int t = 0;
+  const auto t_start = std::chrono::steady_clock::now();
   do {
     evaluate_and_sort();                                // Step 1
     for (int i = 1; i + 1 < N; i += 2) {                // Step 2
@@ -370,6 +407,9 @@ GAResult genetic_cuts(const Network& net, int M, const GAOptions& opt,
       P[who][pos] = draw_absent(rng, I, P[who]);
     }
     ++t;                                                // Step 4
+    if (opt.time_budget_s > 0 &&
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count() > opt.time_budget_s)
+      break;
   } while (t <= opt.T);
   evaluate_and_sort();                                  // Step 5
   res.best = P[0];

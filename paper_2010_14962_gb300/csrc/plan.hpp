@@ -70,6 +70,10 @@ struct Cost {
 };
 Cost plan_cost(const Network& net, const std::vector<int>& cuts);
 
+// Cheap estimate of the same: elimination by smallest merged bag (min
+// degree, no fill computation); `bag_sizes` (optional) gets |A u B| per merge.
+Cost min_degree_cost(const Network& net, const std::vector<int>& cuts, std::vector<int>* bag_sizes);
+
 // Greedy cut search: k times, cut the index (taken from the widest bags of
 // the current min-fill order) that gives the smallest (width, total flops).
 std::vector<int> greedy_cuts(const Network& net, int k,
@@ -81,6 +85,7 @@ struct GAOptions {
   int T = 4;          // maximum iteration counter (loop runs until t > T)
   int N = 11;         // population size
   uint64_t seed = 1;
+  double time_budget_s = 0;  // stop after the generation that exceeds it (0: none)
 };
 struct GAResult {
   std::vector<int> best;
@@ -89,6 +94,7 @@ struct GAResult {
 };
 using FitnessFn = double (*)(const Network&, const std::vector<int>&, void*);
 double default_fitness(const Network& net, const std::vector<int>& cuts, void*);
+double flops_fitness(const Network& net, const std::vector<int>& cuts, void*);  // log2 total flops
 GAResult genetic_cuts(const Network& net, int M, const GAOptions& opt,
                       const std::vector<std::vector<int>>& seeds,
                       FitnessFn fitness, void* ctx);

@@ -21,7 +21,9 @@ LIB_PATH = os.path.join(_HERE, "_build", "libqtn.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "qtn.h")
 
 PRECISIONS = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16x3": 3, "tf32x3": 4, "bf16x6": 5, "fp32x2": 6}
-SEARCHES = {"greedy": 0, "ga": 1}
+SEARCHES = {"greedy": 0, "ga": 1, "ga_flops": 2}
+SURROGATE_FEATURES = 48
+SURROGATE_TARGETS = 2
 
 
 class QTNError(RuntimeError):
@@ -32,7 +34,8 @@ class QTNError(RuntimeError):
 
 class _PlanOpts(ctypes.Structure):
     _fields_ = [("search", ctypes.c_int), ("k", ctypes.c_int), ("seed", ctypes.c_uint64), ("ga_T", ctypes.c_int),
-                ("ga_N", ctypes.c_int), ("max_slice_bytes", ctypes.c_double)]
+                ("ga_N", ctypes.c_int), ("max_slice_bytes", ctypes.c_double), ("ga_seed_greedy", ctypes.c_int),
+                ("time_budget_s", ctypes.c_double)]
 
 
 _lock = threading.Lock()
@@ -81,6 +84,23 @@ def lib():
             "qtn_plan_select_executor": [vp, ctypes.c_int, ctypes.c_int, ctypes.c_char_p],
             "qtn_plan_kernel_ms": [vp, P(ctypes.c_float)],
             "qtn_search_cuts": [vp, P(_PlanOpts), i32p, f64p, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int)],
+            "qtn_surrogate_features": [vp, i32p, ctypes.c_int, P(ctypes.c_float)],
+            "qtn_surrogate_labels": [vp, i32p, ctypes.c_int, P(ctypes.c_float)],
+            "qtn_surrogate_dataset": [ctypes.c_int] * 7 + [ctypes.c_uint64, ctypes.c_int, P(ctypes.c_float),
+                                                           P(ctypes.c_float)],
+            "qtn_mlp_create": [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_uint64, P(vp)],
+            "qtn_mlp_destroy": [vp],
+            "qtn_mlp_num_params": [vp, P(ctypes.c_size_t)],
+            "qtn_mlp_params": [vp, P(ctypes.c_float), ctypes.c_int],
+            "qtn_mlp_normalisation": [vp] + [P(ctypes.c_float)] * 4 + [ctypes.c_int],
+            "qtn_mlp_gradients": [vp, P(ctypes.c_float), P(ctypes.c_float), ctypes.c_int, P(ctypes.c_float),
+                                  P(ctypes.c_float)],
+            "qtn_mlp_fit": [vp, P(ctypes.c_float), P(ctypes.c_float), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                            ctypes.c_float, ctypes.c_uint64, P(ctypes.c_float)],
+            "qtn_mlp_predict": [vp, P(ctypes.c_float), ctypes.c_int, P(ctypes.c_float)],
+            "qtn_search_cuts_surrogate": [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_uint64, ctypes.c_int, i32p, f64p, P(ctypes.c_int),
+                                          P(ctypes.c_int), f64p, ctypes.c_int, P(ctypes.c_int)],
             "qtn_status_string": [ctypes.c_int],
             "qtn_last_error": [],
         }
@@ -91,6 +111,7 @@ def lib():
         L.qtn_plan_opts_default.restype = None
         L.qtn_network_destroy.restype = None
         L.qtn_plan_destroy.restype = None
+        L.qtn_mlp_destroy.restype = None
         L.qtn_status_string.restype = ctypes.c_char_p
         L.qtn_last_error.restype = ctypes.c_char_p
         _lib = L
@@ -158,11 +179,14 @@ class Network:
         return q.value, p.value, a.value, b.value
 
 
-def search_cuts(network: Network, k: int, search: str = "greedy", seed: int = 1, ga_T: int = 4, ga_N: int = 11):
+def search_cuts(network: Network, k: int, search: str = "greedy", seed: int = 1, ga_T: int = 4, ga_N: int = 11,
+                seed_greedy: bool = True, time_budget_s: float = 0.0):
     """qtn_search_cuts: (cuts, fitness trace, fitness evaluations)."""
     opts = _PlanOpts()
     lib().qtn_plan_opts_default(ctypes.byref(opts))
     opts.search, opts.k, opts.seed, opts.ga_T, opts.ga_N = SEARCHES[search], int(k), int(seed), int(ga_T), int(ga_N)
+    opts.ga_seed_greedy = int(bool(seed_greedy))
+    opts.time_budget_s = float(time_budget_s)
     cuts = np.zeros(max(k, 1), dtype=np.int32)
     trace = np.zeros(256)
     tl, ev = ctypes.c_int(), ctypes.c_int()
@@ -317,3 +341,104 @@ def contract_batch(plans, xs, precision: str = "fp32", stream=None) -> np.ndarra
     _check(lib().qtn_contract_batch(hp, xp, n, PRECISIONS[precision], _stream_handle(stream),
                                     _ptr(out, ctypes.c_double)))
     return out[0:2 * n:2] + 1j * out[1:2 * n:2]
+
+
+# ------------------------------------------------------- learned surrogate --
+
+def _f32(a, shape=None):
+    a = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    return a if shape is None else a.reshape(shape)
+
+
+def surrogate_features(network: Network, cuts) -> np.ndarray:
+    c = np.ascontiguousarray(np.asarray(cuts, dtype=np.int32))
+    out = np.zeros(SURROGATE_FEATURES, dtype=np.float32)
+    _check(lib().qtn_surrogate_features(network.handle, _ptr(c, ctypes.c_int32), len(c), _ptr(out, ctypes.c_float)))
+    return out
+
+
+def surrogate_labels(network: Network, cuts) -> np.ndarray:
+    c = np.ascontiguousarray(np.asarray(cuts, dtype=np.int32))
+    out = np.zeros(SURROGATE_TARGETS, dtype=np.float32)
+    _check(lib().qtn_surrogate_labels(network.handle, _ptr(c, ctypes.c_int32), len(c), _ptr(out, ctypes.c_float)))
+    return out
+
+
+def surrogate_dataset(count, n_lo, n_hi, p_lo, p_hi, k_lo, k_hi, seed=0, threads=8):
+    """(X, Y): features and exact labels of `count` random (graph, cut set) samples."""
+    X = np.zeros((count, SURROGATE_FEATURES), dtype=np.float32)
+    Y = np.zeros((count, SURROGATE_TARGETS), dtype=np.float32)
+    _check(lib().qtn_surrogate_dataset(count, n_lo, n_hi, p_lo, p_hi, k_lo, k_hi, ctypes.c_uint64(seed), threads,
+                                       _ptr(X, ctypes.c_float), _ptr(Y, ctypes.c_float)))
+    return X, Y
+
+
+class MLP:
+    """The cost surrogate (qtn_mlp_*): trained and evaluated on the device."""
+
+    def __init__(self, n_in=SURROGATE_FEATURES, hidden=256, n_out=SURROGATE_TARGETS, seed=0):
+        h = ctypes.c_void_p()
+        _check(lib().qtn_mlp_create(n_in, hidden, n_out, ctypes.c_uint64(seed), ctypes.byref(h)))
+        self._h = h
+        self.n_in, self.hidden, self.n_out = n_in, hidden, n_out
+        n = ctypes.c_size_t()
+        _check(lib().qtn_mlp_num_params(h, ctypes.byref(n)))
+        self.num_params = n.value
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.qtn_mlp_destroy(self._h)
+            self._h = None
+
+    @property
+    def handle(self):
+        return self._h
+
+    def params(self) -> np.ndarray:
+        out = np.zeros(self.num_params, dtype=np.float32)
+        _check(lib().qtn_mlp_params(self._h, _ptr(out, ctypes.c_float), 0))
+        return out
+
+    def set_params(self, p):
+        p = _f32(p)
+        assert p.size == self.num_params
+        _check(lib().qtn_mlp_params(self._h, _ptr(p, ctypes.c_float), 1))
+
+    def set_normalisation(self, x_mean, x_std, y_mean, y_std):
+        a, b, c, d = _f32(x_mean), _f32(x_std), _f32(y_mean), _f32(y_std)
+        _check(lib().qtn_mlp_normalisation(self._h, _ptr(a, ctypes.c_float), _ptr(b, ctypes.c_float),
+                                           _ptr(c, ctypes.c_float), _ptr(d, ctypes.c_float), 1))
+
+    def gradients(self, X, Y):
+        X, Y = _f32(X), _f32(Y)
+        g = np.zeros(self.num_params, dtype=np.float32)
+        loss = ctypes.c_float()
+        _check(lib().qtn_mlp_gradients(self._h, _ptr(X, ctypes.c_float), _ptr(Y, ctypes.c_float), X.shape[0],
+                                       _ptr(g, ctypes.c_float), ctypes.byref(loss)))
+        return g, float(loss.value)
+
+    def fit(self, X, Y, epochs=20, batch=256, lr=1e-3, seed=0):
+        X, Y = _f32(X), _f32(Y)
+        losses = np.zeros(max(epochs, 1), dtype=np.float32)
+        _check(lib().qtn_mlp_fit(self._h, _ptr(X, ctypes.c_float), _ptr(Y, ctypes.c_float), X.shape[0], epochs,
+                                 batch, ctypes.c_float(lr), ctypes.c_uint64(seed), _ptr(losses, ctypes.c_float)))
+        return losses[:epochs]
+
+    def predict(self, X) -> np.ndarray:
+        X = _f32(X)
+        Y = np.zeros((X.shape[0], self.n_out), dtype=np.float32)
+        _check(lib().qtn_mlp_predict(self._h, _ptr(X, ctypes.c_float), X.shape[0], _ptr(Y, ctypes.c_float)))
+        return Y
+
+
+def search_cuts_surrogate(network: Network, k: int, mlp: MLP, T=8, N=256, top=4, seed=0, seed_greedy=True):
+    """(cuts, best exact log2 flops, exact evaluations, surrogate evaluations, trace)."""
+    cuts = np.zeros(k, dtype=np.int32)
+    best = ctypes.c_double()
+    ne, ns, tl = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    trace = np.zeros(256)
+    _check(lib().qtn_search_cuts_surrogate(network.handle, k, mlp.handle, T, N, top, ctypes.c_uint64(seed),
+                                           int(bool(seed_greedy)), _ptr(cuts, ctypes.c_int32), ctypes.byref(best), ctypes.byref(ne),
+                                           ctypes.byref(ns), _ptr(trace, ctypes.c_double), len(trace),
+                                           ctypes.byref(tl)))
+    return cuts, best.value, ne.value, ns.value, trace[: tl.value]

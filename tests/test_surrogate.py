@@ -1,0 +1,150 @@
+"""Learned cost surrogate (the benchmark spec's learned part): features, labelled data
+from the exact counter, the MLP's device kernels against a CPU float64
+reference (itself pinned by finite differences), training, and the
+surrogate-guided cut search against the search without it."""
+import ctypes
+import time
+
+import numpy as np
+import pytest
+
+from oracle import mlp_reference as R
+from paper_2010_14962_gb300 import instances as I
+from paper_2010_14962_gb300 import qtn
+
+F, O = qtn.SURROGATE_FEATURES, qtn.SURROGATE_TARGETS
+
+
+def test_reference_gradient_matches_finite_differences():
+    rng = np.random.default_rng(0)
+    n_in, hidden, n_out = 5, 7, 2
+    size = hidden * n_in + hidden + hidden * hidden + hidden + n_out * hidden + n_out
+    p = rng.normal(size=size) * 0.5
+    X = rng.normal(size=(6, n_in))
+    T = rng.normal(size=(6, n_out))
+    _, g = R.loss_and_grad(p, X, T, n_in, hidden, n_out)
+    h = 1e-6
+    for i in rng.choice(size, 25, replace=False):
+        e = np.zeros(size)
+        e[i] = h
+        fd = (R.loss_and_grad(p + e, X, T, n_in, hidden, n_out)[0] - R.loss_and_grad(p - e, X, T, n_in, hidden,
+                                                                                     n_out)[0]) / (2 * h)
+        assert abs(fd - g[i]) < 1e-7 * max(1.0, abs(g[i]))
+
+
+def test_features_and_labels():
+    inst = I.qaoa_instance(40, 1, 3)
+    net = qtn.Network(40, inst.edges, inst.gamma, inst.beta)
+    plan = qtn.Plan(net, k=6)
+    f1 = qtn.surrogate_features(net, plan.cuts)
+    f2 = qtn.surrogate_features(net, plan.cuts)
+    assert f1.shape == (F,) and np.array_equal(f1, f2) and np.all(np.isfinite(f1))
+    assert f1[-1] == 1.0 and abs(f1[2] - 6 / 32) < 1e-7
+    X, Y = qtn.surrogate_dataset(64, 30, 60, 1, 1, 2, 10, seed=5, threads=4)
+    X2, Y2 = qtn.surrogate_dataset(64, 30, 60, 1, 1, 2, 10, seed=5, threads=2)
+    assert np.array_equal(X, X2) and np.array_equal(Y, Y2)  # sample i depends only on (seed, i)
+    assert np.all(np.isfinite(X)) and np.all(Y[:, 0] > 0)
+
+
+def test_labels_are_the_exact_counter():
+    # A dataset label is the plan cost of the same cut set (min-fill).
+    inst = I.qaoa_instance(50, 1, 8)
+    net = qtn.Network(50, inst.edges, inst.gamma, inst.beta)
+    rng = np.random.default_rng(1)
+    _, ni = net.info()
+    for _ in range(3):
+        cuts = rng.choice(ni, 7, replace=False)
+        c = qtn.Plan(net, cuts=cuts).cost()
+        lab = qtn.surrogate_labels(net, cuts)
+        assert abs(lab[0] - c["log2_flops"]) < 1e-4
+        assert abs(lab[1] - c["log2_peak_bytes"]) < 1e-4
+
+
+@pytest.mark.gpu
+def test_device_gradients_match_reference(gpu):
+    m = qtn.MLP(F, 32, O, seed=3)
+    rng = np.random.default_rng(2)
+    p = (rng.normal(size=m.num_params) * 0.2).astype(np.float32)
+    m.set_params(p)
+    m.set_normalisation(np.zeros(F), np.ones(F), np.zeros(O), np.ones(O))
+    X = rng.normal(size=(70, F)).astype(np.float32)
+    T = rng.normal(size=(70, O)).astype(np.float32)
+    g, loss = m.gradients(X, T)
+    ref_loss, ref_g = R.loss_and_grad(p.astype(np.float64), X, T, F, 32, O)
+    assert abs(loss - ref_loss) < 1e-4 * abs(ref_loss)
+    assert np.max(np.abs(g - ref_g)) < 1e-4 * max(1e-3, np.max(np.abs(ref_g)))
+    Y = m.predict(X)
+    ref_Y, _ = R.forward(p.astype(np.float64), X, F, 32, O)
+    assert np.max(np.abs(Y - ref_Y)) < 1e-4 * np.max(np.abs(ref_Y))
+
+
+@pytest.fixture(scope="module")
+def trained(gpu):
+    X, Y = qtn.surrogate_dataset(6000, 40, 120, 1, 1, 8, 24, seed=11, threads=16)
+    m = qtn.MLP(F, 256, O, seed=1)
+    losses = m.fit(X[:5000], Y[:5000], epochs=60, batch=256, lr=1e-3, seed=2)
+    return m, losses, X[5000:], Y[5000:]
+
+
+@pytest.mark.gpu
+def test_training_learns_the_counter(trained):
+    m, losses, Xv, Yv = trained
+    assert losses[-1] < 0.2 * losses[0]
+    P = m.predict(Xv)
+    err = np.abs(P[:, 0] - Yv[:, 0])
+    rank = lambda v: np.argsort(np.argsort(v))
+    rho = np.corrcoef(rank(P[:, 0]), rank(Yv[:, 0]))[0, 1]
+    print("held-out log2 flops: mean abs err", err.mean(), "spearman", rho)
+    assert rho > 0.9 and err.mean() < 1.0
+
+
+@pytest.mark.gpu
+def test_surrogate_search_gain(trained):
+    # What the network adds to Algorithm 1: both searches start from random
+    # populations (as Algorithm 1 does) and get the same wall-clock budget on
+    # n = 120, k = 22; the exact counter judges both results.
+    m = trained[0]
+    rows = []
+    for seed in (5, 6, 7):
+        inst = I.qaoa_instance(120, 1, seed)
+        net = qtn.Network(120, inst.edges, inst.gamma, inst.beta)
+        k = 22
+        t0 = time.perf_counter()
+        cuts_s, best_s, n_exact, n_sur, trace = qtn.search_cuts_surrogate(net, k, m, T=10, N=256, top=4, seed=seed,
+                                                                          seed_greedy=False)
+        budget = time.perf_counter() - t0
+        assert abs(qtn.surrogate_labels(net, cuts_s)[0] - best_s) < 1e-3
+        assert all(b <= a + 1e-9 for a, b in zip(trace, trace[1:]))  # elitism by the exact counter
+        cuts_e, _, n_ga = qtn.search_cuts(net, k, "ga_flops", seed=seed, ga_T=10 ** 6, ga_N=11, seed_greedy=False,
+                                          time_budget_s=budget)
+        best_e = float(qtn.surrogate_labels(net, cuts_e)[0])
+        rows.append((best_e, best_s))
+        print(f"seed {seed}: exact-counter GA {best_e:.2f} ({n_ga} evaluations) vs surrogate GA {best_s:.2f} "
+              f"({n_sur} surrogate + {n_exact} exact evaluations) in {budget:.2f} s")
+    gain = np.mean([e - s_ for e, s_ in rows])
+    print("mean gain (log2 flops):", gain)
+    assert gain > 0
+
+
+@pytest.mark.gpu
+def test_learned_planner_n120(trained):
+    # n = 120, 22 cuts: the surrogate-guided plan and the exact-counter plan
+    # (greedy) contracted in the double-float form; the two slicings give the
+    # same amplitude, and both fit far inside a 150 GB memory cap.
+    m = trained[0]
+    inst = I.qaoa_instance(120, 1, 5)
+    net = qtn.Network(120, inst.edges, inst.gamma, inst.beta)
+    cuts_s, best_s, *_ = qtn.search_cuts_surrogate(net, 22, m, T=6, N=256, top=4, seed=1, seed_greedy=True)
+    plan_s = qtn.Plan(net, cuts=cuts_s, max_slice_bytes=150e9)
+    plan_e = qtn.Plan(net, k=22, max_slice_bytes=150e9)
+    x = I.bitstrings(120, 1, 5)[0]
+    times, vals = [], []
+    for plan in (plan_s, plan_e):
+        plan.contract_amplitude(x, "fp32x2")  # autotune + warm up
+        t0 = time.perf_counter()
+        vals.append(plan.contract_amplitude(x, "fp32x2"))
+        times.append(time.perf_counter() - t0)
+    print("surrogate plan log2 flops", plan_s.cost()["log2_flops"], "time", times[0],
+          "| exact-counter plan", plan_e.cost()["log2_flops"], "time", times[1])
+    assert plan_s.cost()["log2_flops"] <= plan_e.cost()["log2_flops"] + 1e-9
+    assert abs(vals[0] - vals[1]) < 1e-10 * abs(vals[1])
