@@ -291,7 +291,7 @@ def run_ours(args, rank, world, local_rank):
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": "amplitudes/s", "h2d_bytes_per_step": int(nx * WORKLOAD["n"]),
                 "d2h_bytes_per_step": int(nx * 16), "api": "qtn_contract_batch (host x in, host amplitudes out)"},
-        "gpu_launches": 3 * args.steps,
+        "gpu_launches": (3 + (1 if prog.get("prologue") else 0)) * args.steps,
         "wall_s_timed_region": wall,
     }
     if sweep is not None:
@@ -407,6 +407,162 @@ def run_reference(args, rank, world):
     print(json.dumps(out), flush=True)
 
 
+UNEVEN = dict(name="uneven64", jobs=64, n_range=(30, 100), p_choices=(1, 2), k_range=(6, 18), seed=4)
+UNEVEN_METRIC = "amplitudes/sec, 64 uneven QAOA jobs (n 30-100, p in {1,2}, own cut set each), one launch sequence"
+
+
+def setup_uneven(rank: int):
+    import concurrent.futures as cf
+
+    from paper_2010_14962_gb300 import instances as I
+    from paper_2010_14962_gb300 import qtn
+
+    w = {k: v for k, v in UNEVEN.items() if k != "name"}
+    spec = I.uneven_jobs(**w)
+
+    def one(jd):
+        j, d = jd
+        inst = I.qaoa_instance(d["n"], d["p"], d["seed"])
+        net = qtn.Network(d["n"], inst.edges, inst.gamma, inst.beta)
+        return inst, qtn.plan_to_fit(net, d["k"]), I.bitstrings(d["n"], 1, 700 + j + 1000 * rank)[0]
+
+    with cf.ThreadPoolExecutor(min(16, os.cpu_count() or 1)) as ex:
+        jobs = list(ex.map(one, enumerate(spec)))
+    return spec, jobs
+
+
+def uneven_cpu_baseline(seconds: float, jobs):
+    """The oracle on a seeded random sample of the batch's jobs (whole
+    amplitudes, all host cores) until ``seconds`` have passed."""
+    from oracle import oracle as O
+
+    cores = os.cpu_count() or 1
+    order = np.random.default_rng(11).permutation(len(jobs))
+    done = []
+    t0 = time.perf_counter()
+    for j in order:
+        if time.perf_counter() - t0 >= seconds and done:
+            break
+        inst, plan, x = jobs[j]
+        O.tn_amplitude(inst.n, inst.edges, inst.gamma, inst.beta, x, cuts=plan.cut_names(), threads=cores)
+        done.append(int(j))
+    dt = time.perf_counter() - t0
+    return {"value": len(done) / dt, "unit": "amplitudes/s", "cores": cores, "kind": "oracle",
+            "sample": f"{len(done)} of {len(jobs)} jobs (seeded shuffle: {done[:8]}...), {dt:.1f} s"}
+
+
+def run_uneven(args, rank, world, local_rank):
+    import torch
+
+    from paper_2010_14962_gb300 import qtn
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl")
+    spec, jobs = setup_uneven(rank)
+    plans = [j[1] for j in jobs]
+    xs = [j[2] for j in jobs]
+    nj = len(jobs)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def step(prec):
+        out = qtn.contract_batch(plans, xs, prec, stream)
+        return out, qtn.batch_last_ms()[0]
+
+    ref = step("fp64")[0]
+    sweep = {}
+    for prec in (["fp64", "fp32", "fp32x2"] if args.precision == "auto" else [args.precision]):
+        for _ in range(2):
+            step(prec)
+        ms = []
+        for _ in range(5):
+            got, m = step(prec)
+            ms.append(m)
+            flush.zero_()
+        err = float(np.max(np.abs(got - ref) / np.abs(ref)))
+        sweep[prec] = {"amplitudes_per_s": nj / (statistics.median(ms) / 1e3), "max_rel_err_vs_fp64": err}
+    if args.precision == "auto":
+        ok = [p for p, v in sweep.items() if v["max_rel_err_vs_fp64"] <= 1e-6]
+        args.precision = max(ok, key=lambda p: sweep[p]["amplitudes_per_s"])
+    prec = args.precision
+    for _ in range(args.warmup):
+        step(prec)
+        flush.zero_()
+    torch.cuda.synchronize()
+    dev_ms = []
+    with ClockSampler(local_rank) as clk:
+        time.sleep(0.3)
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            dev_ms.append(step(prec)[1])
+            flush.zero_()
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        wall = time.perf_counter() - t0
+        time.sleep(0.3)
+    total_ms = float(sum(dev_ms))
+    if dist:
+        t = torch.tensor([total_ms, wall], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms, wall = float(t[0].item()), float(t[1].item())
+    value = nj * args.steps * world / (total_ms / 1e3)
+    e2e_value = nj * args.steps * world / wall
+    clocks = clk.summary()
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    exec_flops = 0.0
+    for pl in plans:
+        prog = pl.describe()["programs"][qtn.batch_program(pl, prec)]
+        exec_flops += 8.0 * (2 ** len(prog["outer_class"])) * prog["macs_per_item"]
+    method_flops = sum((2 ** c["k"]) * 8 * c["macs_per_slice"] for c in (pl.cost() for pl in plans))
+    peaks = measured_peaks()
+    sm_for_peak = peaks.get("sm_max_mhz", 2070.0)
+    peak = alu_peak_tflops(prec, sm_for_peak)
+    avg_s = statistics.mean(dev_ms) / 1e3
+    achieved = exec_flops / avg_s / 1e12
+    ks = [pl.k for pl in plans]
+    out = {
+        "metric": UNEVEN_METRIC, "value": value, "unit": "amplitudes/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": {"fp32": "c64", "fp64": "c128", "fp32x2": "c64x2 (double-float)"}.get(prec, "c64"),
+        "data": "synthetic: seeded random 3-regular graphs, gamma/beta ~ U[0,pi), seeded bit strings",
+        "config": {"workload": UNEVEN["name"], "jobs": nj, "n": [min(d["n"] for d in spec), max(d["n"] for d in spec)],
+                   "p1_jobs": sum(d["p"] == 1 for d in spec), "p2_jobs": sum(d["p"] == 2 for d in spec),
+                   "cuts": [min(ks), max(ks)], "precision": prec,
+                   "executed_flops_per_step": exec_flops, "method_flops_per_step": method_flops,
+                   "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": "one launch sequence per step: all jobs' chunks on one persistent grid"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "traffic": None, "kernel": "multi-job launch sequence (leaf, prologue, multi_exec, sums)",
+                     "peak_source": ("FP32 pipe: 152 SMs x 128 lanes x 2 flop x %.0f MHz / %d FP32 instructions per "
+                                     "multiply-add" % (sm_for_peak, INSTR_PER_MAC.get(prec, 1)))
+                     if prec != "fp64" else "FP64 nominal 1.25 TFLOP/s",
+                     "kernel_ms_avg": avg_s * 1e3},
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": "amplitudes/s", "h2d_bytes_per_step": int(sum(d["n"] for d in spec)),
+                "d2h_bytes_per_step": int(nj * 16), "api": "qtn_contract_batch (host x in, host amplitudes out)"},
+        "gpu_launches": qtn.batch_last_ms()[1] * args.steps,
+        "precision_sweep": sweep,
+        "wall_s_timed_region": wall,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = uneven_cpu_baseline(args.cpu_seconds, jobs)
+    print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
 def setup_workload_cpu():
     """Plan on the host only (the reference arm needs no GPU)."""
     return setup_workload(0)
@@ -424,6 +580,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--executor", default=None, help="force an executor (default: autotuned)")
+    ap.add_argument("--workload", default="qaoa80_p1_k16", choices=["qaoa80_p1_k16", "uneven64"],
+                    help="uneven64: 64 independent jobs of different plans in one launch sequence")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -432,6 +590,8 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "uneven64":
+        run_uneven(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 

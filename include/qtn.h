@@ -202,12 +202,29 @@ qtn_status qtn_contract_slices(const qtn_plan_t* plan, const uint8_t* x, uint64_
                                uint64_t slice_hi, qtn_precision prec, cudaStream_t stream,
                                double out[4], double* d_slices);
 
-/* Amplitudes of njobs independent (plan, x) jobs in one persistent launch.
+/* Amplitudes of njobs independent (plan, x) jobs (Sec. III.A per job: each
+ * job sums its own slices; the jobs share nothing but the launch).
  *   plans : host, njobs plan handles (different networks allowed).
- *   xs    : host, njobs pointers to host bit strings.
- *   out   : host, 2 * njobs doubles. */
+ *   xs    : host, njobs pointers to host bit strings (n_j bytes of 0/1).
+ *   out   : host, 2 * njobs doubles (Re, Im of job j at 2j, 2j+1).
+ * When every job names the same plan, the jobs run as one multi-bit-string
+ * launch of that plan's tuned program.  Otherwise one launch sequence runs
+ * all jobs: their leaf tables, their hoisted merges (one block per job), a
+ * persistent kernel whose blocks take (job, item range) chunks from a device
+ * counter -- largest jobs first -- and a fixed-order per-job sum of the chunk
+ * partials, so results do not depend on the block schedule.  Each job runs
+ * its plan's 48 KiB batched program, else its per-class block program.
+ * Errors: QTN_ERR_INVALID_ARG (NULL plan, bad x), QTN_ERR_UNSUPPORTED (a
+ * job's working set exceeds shared memory), QTN_ERR_CUDA.  Internal device
+ * and pinned buffers are kept between calls (grow-only); calls from several
+ * host threads are serialised.  Synchronises `stream`. */
 qtn_status qtn_contract_batch(const qtn_plan_t* const* plans, const uint8_t* const* xs, int njobs,
                               qtn_precision prec, cudaStream_t stream, double* out);
+
+/* Device time (ms) of the most recent multi-plan qtn_contract_batch launch
+ * sequence (leaf tables to per-job sums, CUDA events on its stream), and the
+ * number of kernels it launched.  QTN_ERR_INVALID_ARG if none ran yet. */
+qtn_status qtn_batch_last_ms(float* ms, int* kernels);
 
 /* Which executor the plan runs on ("lane": one slice per GPU thread, for
  * plans with every tensor rank <= 5; "block": one slice per thread block). */

@@ -2,6 +2,7 @@
 // CUDA-graph replay and the host <-> device entry points of qtn.h.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -79,6 +80,72 @@ Arith arith_of(qtn_precision p) {
   return Arith::F64;
 }
 bool wide(qtn_precision p) { return arith_elem_bytes(arith_of(p)) == 16; }
+
+// Device and pinned host buffers of qtn_contract_batch (grow-only).
+struct BatchWorkspace {
+  int device = -1;
+  size_t cap_jobs = 0, cap_chunks = 0, cap_lt = 0, cap_x = 0;
+  JobDesc* d_jobs = nullptr;
+  ChunkDesc* d_chunks = nullptr;
+  void* d_lt = nullptr;
+  uint8_t* d_x = nullptr;
+  Partial* d_partials = nullptr;
+  unsigned* d_counter = nullptr;
+  double2* d_out = nullptr;
+  JobDesc* h_jobs = nullptr;
+  ChunkDesc* h_chunks = nullptr;
+  uint8_t* h_x = nullptr;
+  double* h_out = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  bool timed = false;
+
+  void release() {
+    cudaFree(d_jobs);
+    cudaFree(d_chunks);
+    cudaFree(d_lt);
+    cudaFree(d_x);
+    cudaFree(d_partials);
+    cudaFree(d_counter);
+    cudaFree(d_out);
+    cudaFreeHost(h_jobs);
+    cudaFreeHost(h_chunks);
+    cudaFreeHost(h_x);
+    cudaFreeHost(h_out);
+    if (ev0) cudaEventDestroy(ev0);
+    if (ev1) cudaEventDestroy(ev1);
+    *this = BatchWorkspace();
+  }
+  cudaError_t reserve(size_t jobs, size_t chunks, size_t lt, size_t x) {
+    if (jobs <= cap_jobs && chunks <= cap_chunks && lt <= cap_lt && x <= cap_x) return cudaSuccess;
+    const int dev = device;
+    jobs = std::max(jobs, cap_jobs);
+    chunks = std::max(chunks, cap_chunks);
+    lt = std::max(lt, cap_lt);
+    x = std::max(x, cap_x);
+    release();
+    device = dev;
+    cudaError_t e;
+    if ((e = cudaMalloc((void**)&d_jobs, sizeof(JobDesc) * jobs)) != cudaSuccess) return e;
+    if ((e = cudaMalloc((void**)&d_chunks, sizeof(ChunkDesc) * chunks)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&d_lt, std::max<size_t>(lt, 256))) != cudaSuccess) return e;
+    if ((e = cudaMalloc((void**)&d_x, std::max<size_t>(x, 16))) != cudaSuccess) return e;
+    if ((e = cudaMalloc((void**)&d_partials, sizeof(Partial) * chunks)) != cudaSuccess) return e;
+    if ((e = cudaMalloc((void**)&d_counter, sizeof(unsigned))) != cudaSuccess) return e;
+    if ((e = cudaMalloc((void**)&d_out, sizeof(double2) * jobs)) != cudaSuccess) return e;
+    if ((e = cudaMallocHost((void**)&h_jobs, sizeof(JobDesc) * jobs)) != cudaSuccess) return e;
+    if ((e = cudaMallocHost((void**)&h_chunks, sizeof(ChunkDesc) * chunks)) != cudaSuccess) return e;
+    if ((e = cudaMallocHost((void**)&h_x, std::max<size_t>(x, 16))) != cudaSuccess) return e;
+    if ((e = cudaMallocHost((void**)&h_out, sizeof(double2) * jobs)) != cudaSuccess) return e;
+    cap_jobs = jobs;
+    cap_chunks = chunks;
+    cap_lt = lt;
+    cap_x = x;
+    return cudaSuccess;
+  }
+};
+BatchWorkspace g_batch;
+std::mutex g_batch_mu;
+constexpr int kMultiKernels = 4;  // leaf tables, prologue, executor, per-job sums
 
 }  // namespace
 
@@ -517,6 +584,14 @@ qtn_status qtn_plan(const qtn_network_t* net, const int32_t* cuts, int k, const 
     sl.exec = Executor::Lane;
     if (compile_program(h->net, h->plan, o, &sl.prog).empty()) h->slots.push_back(std::move(sl));
   }
+  {
+    ProgramOptions o;
+    o.cut_class = cls;
+    ProgSlot sl;
+    sl.name = "block/classes";
+    sl.exec = Executor::Block;
+    if (compile_program(h->net, h->plan, o, &sl.prog).empty()) h->slots.push_back(std::move(sl));
+  }
   struct Budget {
     const char* name;
     uint32_t elems;
@@ -766,41 +841,174 @@ qtn_status qtn_contract_slices(const qtn_plan_t* cplan, const uint8_t* x, uint64
 qtn_status qtn_contract_batch(const qtn_plan_t* const* plans, const uint8_t* const* xs, int njobs, qtn_precision prec,
                               cudaStream_t stream, double* out) {
   if (!plans || !xs || !out || njobs < 0) return fail(QTN_ERR_INVALID_ARG, "bad argument");
+  if (!precision_supported(prec)) return fail(QTN_ERR_UNSUPPORTED, "unknown precision");
+  if (njobs == 0) return QTN_OK;
   for (int j = 0; j < njobs; ++j) {
     if (!plans[j]) return fail(QTN_ERR_INVALID_ARG, "NULL plan in batch");
     qtn_status st = validate_x(plans[j], xs[j]);
     if (st != QTN_OK) return st;
   }
-  // Jobs of one plan run as one multi-bit-string launch.
-  std::map<const qtn_plan_t*, std::vector<int>> groups;
-  for (int j = 0; j < njobs; ++j) groups[plans[j]].push_back(j);
-  for (auto& [cp, jobs] : groups) {
-    qtn_plan_t* plan = const_cast<qtn_plan_t*>(cp);
+  bool one_plan = true;
+  for (int j = 1; j < njobs; ++j) one_plan = one_plan && plans[j] == plans[0];
+  if (one_plan) {
+    // Jobs of one plan: one multi-bit-string launch of its tuned program.
+    qtn_plan_t* plan = const_cast<qtn_plan_t*>(plans[0]);
     std::lock_guard<std::mutex> lk(plan->mu);
     qtn_status st = plan->ensure_device();
     if (st != QTN_OK) return st;
-    int nx = (int)jobs.size();
     ExecShape sh;
     int si = 0;
-    st = plan->tune(prec, nx, stream, &si);
+    st = plan->tune(prec, njobs, stream, &si);
     if (st != QTN_OK) return st;
-    st = plan->prepare(si, prec, nx, plan->slots[si].items(), &sh);
+    st = plan->prepare(si, prec, njobs, plan->slots[si].items(), &sh);
     if (st != QTN_OK) return st;
-    for (int i = 0; i < nx; ++i) std::memcpy(plan->h_x_pinned + (size_t)i * plan->net.n, xs[jobs[i]], plan->net.n);
-    QTN_CUDA(cudaMemcpyAsync(plan->d_x_stage, plan->h_x_pinned, (size_t)nx * plan->net.n, cudaMemcpyHostToDevice,
-                             stream));
-    st = plan->run_graph(plan->d_x_stage, nx, prec, plan->d_out_stage, stream);
+    for (int i = 0; i < njobs; ++i) std::memcpy(plan->h_x_pinned + (size_t)i * plan->net.n, xs[i], plan->net.n);
+    QTN_CUDA(cudaMemcpyAsync(plan->d_x_stage, plan->h_x_pinned, (size_t)njobs * plan->net.n,
+                             cudaMemcpyHostToDevice, stream));
+    st = plan->run_graph(plan->d_x_stage, njobs, prec, plan->d_out_stage, stream);
     if (st != QTN_OK) return st;
-    QTN_CUDA(cudaMemcpyAsync(plan->h_out_pinned, plan->d_out_stage, (size_t)nx * sizeof(double2),
+    QTN_CUDA(cudaMemcpyAsync(plan->h_out_pinned, plan->d_out_stage, (size_t)njobs * sizeof(double2),
                              cudaMemcpyDeviceToHost, stream));
     QTN_CUDA(cudaStreamSynchronize(stream));
     st = plan->check_err_flag();
     if (st != QTN_OK) return st;
-    for (int i = 0; i < nx; ++i) {
-      out[2 * jobs[i]] = plan->h_out_pinned[2 * i];
-      out[2 * jobs[i] + 1] = plan->h_out_pinned[2 * i + 1];
-    }
+    std::memcpy(out, plan->h_out_pinned, (size_t)njobs * 2 * sizeof(double));
+    return QTN_OK;
   }
+  const Arith arith = arith_of(prec);
+  const size_t elem = (size_t)arith_elem_bytes(arith);
+  // Each job runs its plan's batched program (48 KiB budget) or, if the plan
+  // has none, its per-class block program, on the block executor.
+  struct JobHost {
+    int job;
+    qtn_plan_t* plan;
+    int slot;
+    double cost;
+    uint64_t items;
+  };
+  std::vector<JobHost> jh(njobs);
+  for (int j = 0; j < njobs; ++j) {
+    qtn_plan_t* plan = const_cast<qtn_plan_t*>(plans[j]);
+    std::lock_guard<std::mutex> lk(plan->mu);
+    qtn_status st = plan->ensure_device();
+    if (st != QTN_OK) return st;
+    const std::string want = wide(prec) ? "batched/fp64/48KiB" : "batched/fp32/48KiB";
+    int si = -1;
+    for (int k = 1; k < (int)plan->slots.size() && si < 0; ++k)
+      if (plan->slots[k].name == want) si = k;
+    for (int k = 1; k < (int)plan->slots.size() && si < 0; ++k)
+      if (plan->slots[k].name == "block/classes") si = k;
+    if (si < 0) return fail(QTN_ERR_UNSUPPORTED, "a plan of the batch has no block-executor program");
+    st = plan->upload(plan->slots[si]);
+    if (st != QTN_OK) return st;
+    const Program& pg = plan->slots[si].prog;
+    jh[j] = JobHost{j, plan, si, std::ldexp(pg.macs_per_item, pg.n_outer), 1ull << pg.n_outer};
+  }
+  // Jobs by descending cost; chunks of about total / (8 x 304) items.
+  std::vector<int> order(njobs);
+  for (int j = 0; j < njobs; ++j) order[j] = j;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return jh[a].cost > jh[b].cost; });
+  uint64_t total_items = 0;
+  for (const JobHost& h : jh) total_items += h.items;
+  const uint64_t chunk_items = std::max<uint64_t>(1, (total_items + 8 * 304 - 1) / (8 * 304));
+  std::vector<JobDesc> jobs(njobs);
+  std::vector<ChunkDesc> chunks;
+  size_t lt_bytes = 0, x_bytes = 0, exec_smem = 0, pro_smem = 16;
+  uint32_t total_leaves = 0;
+  std::vector<size_t> lt_off(njobs), x_off(njobs);
+  for (int j = 0; j < njobs; ++j) {
+    const Program& pg = jh[j].plan->slots[jh[j].slot].prog;
+    lt_off[j] = lt_bytes;
+    lt_bytes += ((size_t)pg.leaf_elems * elem + 255) & ~(size_t)255;
+    x_off[j] = x_bytes;
+    x_bytes += ((size_t)jh[j].plan->net.n + 15) & ~(size_t)15;
+    exec_smem = std::max(exec_smem, block_smem_bytes((int)pg.steps.size(), (int)pg.leaves.size(), pg.leaf_elems,
+                                                     pg.arena_elems, arith, 256));
+    if (!pg.prologue.empty())
+      pro_smem = std::max(pro_smem, block_smem_bytes((int)pg.prologue.size(), (int)pg.leaves.size(), pg.leaf_elems,
+                                                     pg.pro_arena_elems, arith, 256));
+  }
+  for (int oj : order) {
+    jobs[oj].first_chunk = (uint32_t)chunks.size();
+    for (uint64_t lo = 0; lo < jh[oj].items; lo += chunk_items)
+      chunks.push_back(ChunkDesc{(uint32_t)oj, 0u, lo, std::min(jh[oj].items, lo + chunk_items)});
+    jobs[oj].n_chunks = (uint32_t)chunks.size() - jobs[oj].first_chunk;
+  }
+  {
+    int dev = 0, max_optin = 0;
+    QTN_CUDA(cudaGetDevice(&dev));
+    QTN_CUDA(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    if (exec_smem > (size_t)max_optin || pro_smem > (size_t)max_optin)
+      return fail(QTN_ERR_UNSUPPORTED, "a job's per-slice working set does not fit in shared memory");
+  }
+  // Workspace (grow-only, shared by batch calls on this device).
+  std::lock_guard<std::mutex> wlk(g_batch_mu);
+  BatchWorkspace& W = g_batch;
+  int dev = 0;
+  QTN_CUDA(cudaGetDevice(&dev));
+  if (W.device != dev) {
+    W.release();
+    W.device = dev;
+  }
+  QTN_CUDA(W.reserve(njobs, chunks.size(), lt_bytes, x_bytes));
+  for (int j = 0; j < njobs; ++j) {
+    const ProgSlot& sl = jh[j].plan->slots[jh[j].slot];
+    const DeviceProgram& d = sl.dprog;
+    JobDesc& J = jobs[j];
+    J.leaves = d.leaves;
+    J.steps = d.steps;
+    J.pro_steps = d.pro_steps;
+    J.gate_q = d.gate_q;
+    J.gate_layer = d.gate_layer;
+    J.gate_in_h = d.gate_in_h;
+    J.gate_out_kind = d.gate_out_kind;
+    J.gamma = d.gamma;
+    J.beta = d.beta;
+    J.x = W.d_x + x_off[j];
+    J.leaf_table = static_cast<unsigned char*>(W.d_lt) + lt_off[j];
+    J.n = jh[j].plan->net.n;
+    J.n_leaves = d.n_leaves;
+    J.n_steps = d.n_steps;
+    J.n_pro_steps = d.n_pro_steps;
+    J.leaf_elems = d.leaf_elems;
+    J.arena_elems = d.arena_elems;
+    J.pro_arena_elems = d.pro_arena_elems;
+    J.leaf_start = total_leaves;
+    total_leaves += (uint32_t)d.n_leaves;
+    J.scale = jh[j].plan->scale();
+    std::memcpy(W.h_x + x_off[j], xs[j], (size_t)J.n);
+  }
+  std::memcpy(W.h_jobs, jobs.data(), sizeof(JobDesc) * njobs);
+  std::memcpy(W.h_chunks, chunks.data(), sizeof(ChunkDesc) * chunks.size());
+  QTN_CUDA(cudaMemcpyAsync(W.d_x, W.h_x, x_bytes, cudaMemcpyHostToDevice, stream));
+  QTN_CUDA(cudaMemcpyAsync(W.d_jobs, W.h_jobs, sizeof(JobDesc) * njobs, cudaMemcpyHostToDevice, stream));
+  QTN_CUDA(cudaMemcpyAsync(W.d_chunks, W.h_chunks, sizeof(ChunkDesc) * chunks.size(), cudaMemcpyHostToDevice, stream));
+  if (!W.ev0) {
+    QTN_CUDA(cudaEventCreate(&W.ev0));
+    QTN_CUDA(cudaEventCreate(&W.ev1));
+  }
+  QTN_CUDA(cudaEventRecord(W.ev0, stream));
+  cudaError_t le = launch_multi(arith, W.d_jobs, njobs, total_leaves, W.d_chunks, (uint32_t)chunks.size(), W.d_counter,
+                                W.d_partials, W.d_out, exec_smem, pro_smem, stream);
+  if (le != cudaSuccess) return cuda_fail(le, "launch_multi");
+  QTN_CUDA(cudaEventRecord(W.ev1, stream));
+  W.timed = true;
+  QTN_CUDA(cudaMemcpyAsync(W.h_out, W.d_out, sizeof(double2) * njobs, cudaMemcpyDeviceToHost, stream));
+  QTN_CUDA(cudaStreamSynchronize(stream));
+  for (int j = 0; j < njobs; ++j) {
+    out[2 * j] = W.h_out[2 * j];
+    out[2 * j + 1] = W.h_out[2 * j + 1];
+  }
+  return QTN_OK;
+}
+
+qtn_status qtn_batch_last_ms(float* ms, int* kernels) {
+  if (!ms) return fail(QTN_ERR_INVALID_ARG, "ms is NULL");
+  std::lock_guard<std::mutex> wlk(g_batch_mu);
+  if (!g_batch.timed) return fail(QTN_ERR_INVALID_ARG, "no multi-plan batch has run");
+  QTN_CUDA(cudaEventSynchronize(g_batch.ev1));
+  QTN_CUDA(cudaEventElapsedTime(ms, g_batch.ev0, g_batch.ev1));
+  if (kernels) *kernels = kMultiKernels;
   return QTN_OK;
 }
 

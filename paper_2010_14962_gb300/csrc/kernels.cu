@@ -23,6 +23,7 @@
 
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <type_traits>
 
 namespace qtn {
@@ -240,6 +241,61 @@ __host__ __device__ inline SmemLayout smem_layout(int n_steps, int n_leaves, uin
 
 // ------------------------------------------------------------ leaf build --
 
+// Entry e of leaf L (FP64 evaluation, rounded by V's conversion).
+template <class V>
+__device__ __forceinline__ V leaf_entry(const DevLeaf& L, int e, const int32_t* __restrict__ gate_q,
+                                        const int8_t* __restrict__ gate_layer, const int8_t* __restrict__ gate_in_h,
+                                        const int8_t* __restrict__ gate_out_kind, const double* __restrict__ gamma,
+                                        const double* __restrict__ beta, const uint8_t* __restrict__ xrow) {
+  const int r = L.rank_nc + L.ncut;
+  double re = 1.0, im = 0.0;
+  if (L.gate >= 0) {
+    const int g = L.gate;
+    const int l = gate_layer[g];
+    int v[4] = {-1, -1, -1, -1};
+    for (int b = 0; b < r; ++b)
+      for (int sl = 0; sl < 4; ++sl)
+        if ((L.slot_mask[b] >> sl) & 1) v[sl] = (e >> b) & 1;
+    double sg, cg, sb, cb;
+    sincos(gamma[l], &sg, &cg);
+    sincos(beta[l], &sb, &cb);
+    re = 0.0;
+    im = 0.0;
+    // T = sum over the wire values (u0, u1) inside the diagonal ZZ gate of
+    //   exp(-i gamma s0 s1) * prod_w [in leg: delta] * [out leg: delta or
+    //   RX(2 beta)[out, u] or <x_q|RX(2 beta)|u>];  absorbed H|0> = (1, 1).
+    for (int u0 = 0; u0 < 2; ++u0)
+      for (int u1 = 0; u1 < 2; ++u1) {
+        const int u[2] = {u0, u1};
+        const double sgn = (double)((1 - 2 * u0) * (1 - 2 * u1));
+        double tre = cg, tim = -sgn * sg;
+        bool ok = true;
+        for (int w = 0; w < 2; ++w) {
+          if (!gate_in_h[2 * g + w] && v[w] != u[w]) ok = false;
+          const int kind = gate_out_kind[2 * g + w];
+          if (kind == OUT_PLAIN) {
+            if (v[2 + w] != u[w]) ok = false;
+          } else {
+            const int row = (kind == OUT_RX) ? v[2 + w] : (int)xrow[gate_q[2 * g + w]];
+            if (row != u[w]) {  // multiply by -i sin(beta)
+              const double nre = tim * sb, nim = -tre * sb;
+              tre = nre;
+              tim = nim;
+            } else {
+              tre *= cb;
+              tim *= cb;
+            }
+          }
+        }
+        if (ok) {
+          re += tre;
+          im += tim;
+        }
+      }
+  }
+  return CplxOps<V>::from(re, im);
+}
+
 template <class V>
 __global__ void leaf_build_kernel(const DevLeaf* __restrict__ leaves, const int32_t* __restrict__ gate_q,
                                   const int8_t* __restrict__ gate_layer, const int8_t* __restrict__ gate_in_h,
@@ -250,54 +306,9 @@ __global__ void leaf_build_kernel(const DevLeaf* __restrict__ leaves, const int3
   const int xi = blockIdx.x / n_leaves;
   if (L.gate == -2) return;  // pseudo-leaf: written by the prologue kernel
   const int r = L.rank_nc + L.ncut;
-  for (int e = threadIdx.x; e < (1 << r); e += blockDim.x) {
-    double re = 1.0, im = 0.0;
-    if (L.gate >= 0) {
-      const int g = L.gate;
-      const int l = gate_layer[g];
-      int v[4] = {-1, -1, -1, -1};
-      for (int b = 0; b < r; ++b)
-        for (int sl = 0; sl < 4; ++sl)
-          if ((L.slot_mask[b] >> sl) & 1) v[sl] = (e >> b) & 1;
-      double sg, cg, sb, cb;
-      sincos(gamma[l], &sg, &cg);
-      sincos(beta[l], &sb, &cb);
-      re = 0.0;
-      im = 0.0;
-      // T = sum over the wire values (u0, u1) inside the diagonal ZZ gate of
-      //   exp(-i gamma s0 s1) * prod_w [in leg: delta] * [out leg: delta or
-      //   RX(2 beta)[out, u] or <x_q|RX(2 beta)|u>];  absorbed H|0> = (1, 1).
-      for (int u0 = 0; u0 < 2; ++u0)
-        for (int u1 = 0; u1 < 2; ++u1) {
-          const int u[2] = {u0, u1};
-          const double s = (double)((1 - 2 * u0) * (1 - 2 * u1));
-          double tre = cg, tim = -s * sg;
-          bool ok = true;
-          for (int w = 0; w < 2; ++w) {
-            if (!gate_in_h[2 * g + w] && v[w] != u[w]) ok = false;
-            const int kind = gate_out_kind[2 * g + w];
-            if (kind == OUT_PLAIN) {
-              if (v[2 + w] != u[w]) ok = false;
-            } else {
-              const int row = (kind == OUT_RX) ? v[2 + w] : (int)x[(size_t)xi * n + gate_q[2 * g + w]];
-              if (row != u[w]) {  // multiply by -i sin(beta)
-                const double nre = tim * sb, nim = -tre * sb;
-                tre = nre;
-                tim = nim;
-              } else {
-                tre *= cb;
-                tim *= cb;
-              }
-            }
-          }
-          if (ok) {
-            re += tre;
-            im += tim;
-          }
-        }
-    }
-    out[(size_t)xi * leaf_elems + L.base + e] = CplxOps<V>::from(re, im);
-  }
+  for (int e = threadIdx.x; e < (1 << r); e += blockDim.x)
+    out[(size_t)xi * leaf_elems + L.base + e] = leaf_entry<V>(L, e, gate_q, gate_layer, gate_in_h, gate_out_kind,
+                                                              gamma, beta, x + (size_t)xi * n);
 }
 
 // ------------------------------------------------------------- lane exec --
@@ -508,6 +519,31 @@ __device__ __forceinline__ StepRegs step_regs(const DevStep& st) {
   return r;
 }
 
+// All merges of one work item (item s selects the leaves' outer sub-blocks),
+// by a group of G threads (thread t); G = 32 synchronises with warp barriers.
+template <class V, class Ops, bool WARP_SYNC>
+__device__ __forceinline__ void run_item(const DevStep* s_steps, int n_steps, const DevLeaf* s_leaves, const V* s_lt,
+                                         V* s_arena, uint64_t s, uint32_t t, uint32_t G, int log2G, double& sr,
+                                         double& cr, double& si, double& ci, double2* slice_out) {
+  for (int j = 0; j < n_steps; ++j) {
+    const DevStep& st = s_steps[j];
+    // One 32-bit read (ma | nb | kb | bb) decides whether this thread has an
+    // output; most merges of an item are small, so most warps skip here.
+    const uint32_t hdr = *reinterpret_cast<const uint32_t*>(&st);
+    const int rc_h = (int)((hdr & 0xffu) + ((hdr >> 8) & 0xffu) + (hdr >> 24));
+    if (t < (1u << rc_h)) {
+      const StepRegs r = step_regs(st);
+      const uint8_t flags = st.flags;
+      const uint32_t ao = st.a, bo = st.b, co = st.c;
+      const V* A = (flags & STEP_A_LEAF) ? s_lt + leaf_offset(s_leaves[ao], s) : s_arena + ao;
+      const V* B = (flags & STEP_B_LEAF) ? s_lt + leaf_offset(s_leaves[bo], s) : s_arena + bo;
+      group_merge<V, Ops>(r, st.w, A, B, s_arena + co, t, G, log2G, sr, cr, si, ci, slice_out);
+    }
+    if (WARP_SYNC) __syncwarp();
+    else __syncthreads();
+  }
+}
+
 // Work items: a slice (per-slice programs) or one assignment of the outer
 // slice classes (batched programs, whose tensors carry the inner classes as
 // batch bits: every merge then runs once per distinct value of the inner
@@ -542,25 +578,9 @@ __global__ void __launch_bounds__(256) block_exec_kernel(ExecParams P) {
   const uint64_t S = P.slice_hi - P.slice_lo;
   const uint64_t stride = (uint64_t)P.blocks_per_x * groups;
   for (uint64_t i = (uint64_t)bx * groups + grp; i < S; i += stride) {
-    const uint64_t s = P.slice_lo + i;
     double2* slice_out = P.slices ? P.slices + (size_t)xi * S + i : nullptr;
-    for (int j = 0; j < P.n_steps; ++j) {
-      const DevStep& st = s_steps[j];
-      // One 32-bit read (ma | nb | kb | bb) decides whether this thread has an
-      // output; most merges of an item are small, so most warps skip here.
-      const uint32_t hdr = *reinterpret_cast<const uint32_t*>(&st);
-      const int rc_h = (int)((hdr & 0xffu) + ((hdr >> 8) & 0xffu) + (hdr >> 24));
-      if (t < (1u << rc_h)) {
-        const StepRegs r = step_regs(st);
-        const uint8_t flags = st.flags;
-        const uint32_t ao = st.a, bo = st.b, co = st.c;
-        const V* A = (flags & STEP_A_LEAF) ? s_lt + leaf_offset(s_leaves[ao], s) : s_arena + ao;
-        const V* B = (flags & STEP_B_LEAF) ? s_lt + leaf_offset(s_leaves[bo], s) : s_arena + bo;
-        group_merge<V, Ops>(r, st.w, A, B, s_arena + co, t, G, log2G, sr, cr, si, ci, slice_out);
-      }
-      if (WARP_ITEMS) __syncwarp();
-      else __syncthreads();
-    }
+    run_item<V, Ops, WARP_ITEMS>(s_steps, P.n_steps, s_leaves, s_lt, s_arena, P.slice_lo + i, t, G, log2G, sr, cr,
+                                 si, ci, slice_out);
   }
   s_red[threadIdx.x] = Partial::make(sr, si, cr, ci);
   tree_reduce(s_red, T);
@@ -571,18 +591,16 @@ __global__ void __launch_bounds__(256) block_exec_kernel(ExecParams P) {
 
 // Hoisted merges (no outer slice class below them): run once per bit string
 // (one block each); exported results become pseudo-leaves of the leaf table.
-template <class V, class Ops = CplxOps<V>>
-__global__ void __launch_bounds__(256) prologue_kernel(const DevStep* __restrict__ steps, int n_steps,
-                                                       const DevLeaf* __restrict__ leaves, int n_leaves,
-                                                       void* leaf_tables, uint32_t leaf_elems, uint32_t arena_elems) {
-  extern __shared__ __align__(16) unsigned char smem[];
+template <class V, class Ops>
+__device__ __forceinline__ void prologue_body(const DevStep* __restrict__ steps, int n_steps,
+                                              const DevLeaf* __restrict__ leaves, int n_leaves, V* g_lt,
+                                              uint32_t leaf_elems, uint32_t arena_elems, unsigned char* smem) {
   const int T = blockDim.x;
   const SmemLayout lay = smem_layout(n_steps, n_leaves, leaf_elems, arena_elems, (int)sizeof(V), T, false);
   DevStep* s_steps = reinterpret_cast<DevStep*>(smem);
   DevLeaf* s_leaves = reinterpret_cast<DevLeaf*>(smem + lay.leaves);
   V* s_lt = reinterpret_cast<V*>(smem + lay.table);
   V* s_arena = reinterpret_cast<V*>(smem + lay.arena);
-  V* g_lt = static_cast<V*>(leaf_tables) + (size_t)blockIdx.x * leaf_elems;
   copy_words(s_steps, steps, (size_t)n_steps * sizeof(DevStep));
   copy_words(s_leaves, leaves, (size_t)n_leaves * sizeof(DevLeaf));
   copy_words(s_lt, g_lt, (size_t)leaf_elems * sizeof(V));
@@ -601,6 +619,118 @@ __global__ void __launch_bounds__(256) prologue_kernel(const DevStep* __restrict
       group_merge<V, Ops>(r, st.w, A, B, C, threadIdx.x, T, log2G, sr, cr, si, ci, nullptr);
     }
     __syncthreads();
+  }
+}
+
+// Hoisted merges (no outer slice class below them): run once per bit string
+// (one block each); exported results become pseudo-leaves of the leaf table.
+template <class V, class Ops = CplxOps<V>>
+__global__ void __launch_bounds__(256) prologue_kernel(const DevStep* __restrict__ steps, int n_steps,
+                                                       const DevLeaf* __restrict__ leaves, int n_leaves,
+                                                       void* leaf_tables, uint32_t leaf_elems, uint32_t arena_elems) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  V* g_lt = static_cast<V*>(leaf_tables) + (size_t)blockIdx.x * leaf_elems;
+  prologue_body<V, Ops>(steps, n_steps, leaves, n_leaves, g_lt, leaf_elems, arena_elems, smem);
+}
+
+// ------------------------------------------------------------- multi-job --
+
+// Many independent (plan, bit string) jobs in one launch sequence: leaf
+// tables of all jobs, one prologue block per job, a persistent executor that
+// takes chunks (job, item range) from a counter -- in the order of
+// descending job cost the host gave them -- and loads a job's program into
+// shared memory when its job changes, then one finalising block per job.
+__device__ __forceinline__ int job_of_leaf(const JobDesc* jobs, int njobs, uint32_t b) {
+  int lo = 0, hi = njobs - 1;
+  while (lo < hi) {  // last job with leaf_start <= b
+    const int mid = (lo + hi + 1) / 2;
+    if (jobs[mid].leaf_start <= b) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <class V>
+__global__ void multi_leaf_kernel(const JobDesc* __restrict__ jobs, int njobs) {
+  const int j = job_of_leaf(jobs, njobs, blockIdx.x);
+  const JobDesc& J = jobs[j];
+  const DevLeaf L = J.leaves[blockIdx.x - J.leaf_start];
+  if (L.gate == -2) return;
+  const int r = L.rank_nc + L.ncut;
+  V* out = static_cast<V*>(J.leaf_table);
+  for (int e = threadIdx.x; e < (1 << r); e += blockDim.x)
+    out[L.base + e] = leaf_entry<V>(L, e, J.gate_q, J.gate_layer, J.gate_in_h, J.gate_out_kind, J.gamma, J.beta, J.x);
+}
+
+template <class V, class Ops = CplxOps<V>>
+__global__ void __launch_bounds__(256) multi_prologue_kernel(const JobDesc* __restrict__ jobs) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const JobDesc& J = jobs[blockIdx.x];
+  if (J.n_pro_steps == 0) return;
+  prologue_body<V, Ops>(J.pro_steps, J.n_pro_steps, J.leaves, J.n_leaves, static_cast<V*>(J.leaf_table),
+                        J.leaf_elems, J.pro_arena_elems, smem);
+}
+
+template <class V, class Ops = CplxOps<V>>
+__global__ void __launch_bounds__(256) multi_exec_kernel(const JobDesc* __restrict__ jobs,
+                                                         const ChunkDesc* __restrict__ chunks, uint32_t n_chunks,
+                                                         unsigned* __restrict__ counter,
+                                                         Partial* __restrict__ chunk_partials) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned s_c;
+  __shared__ int s_job;
+  const int T = blockDim.x;
+  const int log2G = 31 - __clz(T);
+  if (threadIdx.x == 0) s_job = -1;
+  for (;;) {
+    __syncthreads();  // the previous chunk is done with shared memory
+    if (threadIdx.x == 0) s_c = atomicAdd(counter, 1u);
+    __syncthreads();
+    const unsigned c = s_c;
+    if (c >= n_chunks) break;
+    const ChunkDesc ch = chunks[c];
+    const JobDesc& J = jobs[ch.job];
+    const SmemLayout lay = smem_layout(J.n_steps, J.n_leaves, J.leaf_elems, J.arena_elems, (int)sizeof(V), T, false);
+    DevStep* s_steps = reinterpret_cast<DevStep*>(smem);
+    DevLeaf* s_leaves = reinterpret_cast<DevLeaf*>(smem + lay.leaves);
+    V* s_lt = reinterpret_cast<V*>(smem + lay.table);
+    V* s_arena = reinterpret_cast<V*>(smem + lay.arena);
+    Partial* s_red = reinterpret_cast<Partial*>(smem + lay.red);
+    if (s_job != (int)ch.job) {
+      copy_words(s_steps, J.steps, (size_t)J.n_steps * sizeof(DevStep));
+      copy_words(s_leaves, J.leaves, (size_t)J.n_leaves * sizeof(DevLeaf));
+      copy_words(s_lt, J.leaf_table, (size_t)J.leaf_elems * sizeof(V));
+      __syncthreads();
+      if (threadIdx.x == 0) s_job = (int)ch.job;
+    }
+    double sr = 0.0, si = 0.0, cr = 0.0, ci = 0.0;
+    for (uint64_t it = ch.lo; it < ch.hi; ++it)
+      run_item<V, Ops, false>(s_steps, J.n_steps, s_leaves, s_lt, s_arena, it, threadIdx.x, T, log2G, sr, cr, si,
+                              ci, nullptr);
+    s_red[threadIdx.x] = Partial::make(sr, si, cr, ci);
+    tree_reduce(s_red, T);
+    if (threadIdx.x == 0) chunk_partials[c] = s_red[0];
+  }
+}
+
+__global__ void __launch_bounds__(128) multi_finalize_kernel(const JobDesc* __restrict__ jobs,
+                                                             const Partial* __restrict__ chunk_partials,
+                                                             double2* __restrict__ out) {
+  __shared__ Partial red[128];
+  const JobDesc& J = jobs[blockIdx.x];
+  double a = 0, b = 0, ca = 0, cb = 0;
+  for (uint32_t t = threadIdx.x; t < J.n_chunks; t += blockDim.x) {
+    const Partial v = chunk_partials[J.first_chunk + t];
+    kahan_add(a, ca, v.re);
+    kahan_add(a, ca, -v.cre);
+    kahan_add(b, cb, v.im);
+    kahan_add(b, cb, -v.cim);
+  }
+  red[threadIdx.x] = Partial::make(a, b, ca, cb);
+  tree_reduce(red, 128);
+  if (threadIdx.x == 0) {
+    const Partial v = red[0];
+    out[blockIdx.x] = make_double2((v.re - v.cre) * J.scale, (v.im - v.cim) * J.scale);
   }
 }
 
@@ -773,6 +903,30 @@ cudaError_t launch_typed(const DeviceProgram& prog, const uint8_t* d_x, int nx, 
   return cudaGetLastError();
 }
 
+template <class V, class Ops>
+cudaError_t launch_multi_typed(const JobDesc* d_jobs, int njobs, uint32_t total_leaves, const ChunkDesc* d_chunks,
+                               uint32_t n_chunks, unsigned* d_counter, Partial* d_chunk_partials, double2* d_out,
+                               size_t exec_smem, size_t pro_smem, cudaStream_t stream) {
+  int dev = 0, sms = 0, max_optin = 0, occ = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (exec_smem > (size_t)max_optin || pro_smem > (size_t)max_optin) return cudaErrorInvalidValue;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(multi_prologue_kernel<V, Ops>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)pro_smem)) != cudaSuccess)
+    return e;
+  if (!shape_for_kernel(multi_exec_kernel<V, Ops>, 256, exec_smem, &occ)) return cudaErrorInvalidConfiguration;
+  if ((e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned), stream)) != cudaSuccess) return e;
+  multi_leaf_kernel<V><<<total_leaves, 32, 0, stream>>>(d_jobs, njobs);
+  multi_prologue_kernel<V, Ops><<<njobs, 256, pro_smem, stream>>>(d_jobs);
+  const unsigned grid = (unsigned)std::min<uint64_t>((uint64_t)sms * occ, n_chunks);
+  multi_exec_kernel<V, Ops><<<grid, 256, exec_smem, stream>>>(d_jobs, d_chunks, n_chunks, d_counter,
+                                                               d_chunk_partials);
+  multi_finalize_kernel<<<njobs, 128, 0, stream>>>(d_jobs, d_chunk_partials, d_out);
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 int arith_elem_bytes(Arith a) { return (a == Arith::F64 || a == Arith::F32X2) ? 16 : 8; }
@@ -804,6 +958,22 @@ cudaError_t launch_contraction(const DeviceProgram& prog, Arith a, const uint8_t
   launch_typed<V, O>(prog, d_x, nx, slice_lo, slice_hi, buf, shape, scale, d_out, d_raw, d_slices, stream, ev0, ev1)
   QTN_ARITH_SWITCH(a, QTN_LAUNCH_CALL)
 #undef QTN_LAUNCH_CALL
+  return cudaErrorInvalidValue;
+}
+
+size_t block_smem_bytes(int n_steps, int n_leaves, uint32_t leaf_elems, uint32_t arena_elems, Arith a, int threads) {
+  return smem_layout(n_steps, n_leaves, leaf_elems, arena_elems, arith_elem_bytes(a), threads, false).total;
+}
+
+cudaError_t launch_multi(Arith a, const JobDesc* d_jobs, int njobs, uint32_t total_leaves, const ChunkDesc* d_chunks,
+                         uint32_t n_chunks, unsigned* d_counter, Partial* d_chunk_partials, double2* d_out,
+                         size_t exec_smem, size_t pro_smem, cudaStream_t stream) {
+  if (njobs <= 0) return cudaSuccess;
+#define QTN_MULTI_CALL(V, O)                                                                                  \
+  launch_multi_typed<V, O>(d_jobs, njobs, total_leaves, d_chunks, n_chunks, d_counter, d_chunk_partials, d_out, \
+                           exec_smem, pro_smem, stream)
+  QTN_ARITH_SWITCH(a, QTN_MULTI_CALL)
+#undef QTN_MULTI_CALL
   return cudaErrorInvalidValue;
 }
 

@@ -76,6 +76,41 @@ cudaError_t launch_contraction(const DeviceProgram& prog, Arith arith, const uin
                                double2* d_slices, cudaStream_t stream, cudaEvent_t ev0 = nullptr,
                                cudaEvent_t ev1 = nullptr);
 
+// One job of a multi-job launch (device array; pointers are device pointers).
+struct JobDesc {
+  const DevLeaf* leaves;
+  const DevStep* steps;
+  const DevStep* pro_steps;
+  const int32_t* gate_q;
+  const int8_t* gate_layer;
+  const int8_t* gate_in_h;
+  const int8_t* gate_out_kind;
+  const double* gamma;
+  const double* beta;
+  const uint8_t* x;   // n bit bytes
+  void* leaf_table;   // leaf_elems elements
+  int n, n_leaves, n_steps, n_pro_steps;
+  uint32_t leaf_elems, arena_elems, pro_arena_elems;
+  uint32_t leaf_start;   // first block of this job in the leaf launch
+  uint32_t first_chunk, n_chunks;
+  double scale;
+};
+// A range of work items of one job.
+struct ChunkDesc {
+  uint32_t job, pad;
+  uint64_t lo, hi;
+};
+
+// Shared memory of the block executor for a program.
+size_t block_smem_bytes(int n_steps, int n_leaves, uint32_t leaf_elems, uint32_t arena_elems, Arith a, int threads);
+
+// Enqueues the multi-job sequence (leaf tables, prologues, persistent
+// executor over `n_chunks` chunks, per-job finalisation into d_out[njobs]).
+// exec_smem / pro_smem: the largest shared memory any job needs.
+cudaError_t launch_multi(Arith a, const JobDesc* d_jobs, int njobs, uint32_t total_leaves, const ChunkDesc* d_chunks,
+                         uint32_t n_chunks, unsigned* d_counter, Partial* d_chunk_partials, double2* d_out,
+                         size_t exec_smem, size_t pro_smem, cudaStream_t stream);
+
 // Largest tensor rank the lane executor accepts.
 constexpr int kLaneMaxRank = 5;
 

@@ -98,13 +98,20 @@ WORKLOADS = {
 }
 
 
-def uneven_jobs(jobs: int = 64, n_range=(30, 100), p_choices=(1, 2), k_range=(6, 18), seed: int = 4):
-    """Job list for the uneven batch: (n even, p, k, instance seed)."""
+def uneven_jobs(jobs: int = 64, n_range=(30, 100), p_choices=(1, 2), k_range=(6, 18), seed: int = 4,
+                p2_n_max: int = 40):
+    """Job list for the uneven batch: (n even, p, k, instance seed).
+
+    p = 2 jobs draw n from [n_range[0], p2_n_max]: beyond about 40 qubits a
+    depth-2 network keeps intermediates of 2^30 and more entries after 18 cuts,
+    which is no batch job.  ``k`` is the fewest cuts the job asks for.
+    """
     rng = np.random.Generator(np.random.PCG64(seed + 0xBA7C))
     out = []
     for j in range(jobs):
-        n = int(rng.integers(n_range[0] // 2, n_range[1] // 2 + 1)) * 2
         p = int(rng.choice(p_choices))
+        hi = n_range[1] if p == 1 else min(n_range[1], p2_n_max)
+        n = int(rng.integers(n_range[0] // 2, hi // 2 + 1)) * 2
         k = int(rng.integers(k_range[0], k_range[1] + 1))
         out.append(dict(n=n, p=p, k=k, seed=1000 + seed * 100 + j))
     return out

@@ -83,6 +83,7 @@ def lib():
             "qtn_plan_set_kernel_timing": [vp, ctypes.c_int],
             "qtn_plan_select_executor": [vp, ctypes.c_int, ctypes.c_int, ctypes.c_char_p],
             "qtn_plan_kernel_ms": [vp, P(ctypes.c_float)],
+            "qtn_batch_last_ms": [P(ctypes.c_float), P(ctypes.c_int)],
             "qtn_search_cuts": [vp, P(_PlanOpts), i32p, f64p, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int)],
             "qtn_surrogate_features": [vp, i32p, ctypes.c_int, P(ctypes.c_float)],
             "qtn_surrogate_labels": [vp, i32p, ctypes.c_int, P(ctypes.c_float)],
@@ -193,6 +194,25 @@ def search_cuts(network: Network, k: int, search: str = "greedy", seed: int = 1,
     _check(lib().qtn_search_cuts(network.handle, ctypes.byref(opts), _ptr(cuts, ctypes.c_int32),
                                  _ptr(trace, ctypes.c_double), len(trace), ctypes.byref(tl), ctypes.byref(ev)))
     return cuts[:k], trace[: tl.value], ev.value
+
+
+def plan_to_fit(network: "Network", k_min: int, k_max: int = 24, slice_bytes: float = 65536.0) -> "Plan":
+    """Plan with the fewest greedy cuts in [k_min, k_max] whose per-slice
+    working set (complex64, planner's count) is at most ``slice_bytes``.
+
+    Greedy cuts are chosen one at a time (each given the earlier ones), so the
+    first j cuts of a k_max search are the j-cut greedy set: one search serves
+    every j.  Raises QTNError(PLAN_EXCEEDS_CAP) when no j fits.
+    """
+    cuts, _, _ = search_cuts(network, k_max)
+    last = None
+    for k in range(k_min, k_max + 1):
+        try:
+            pl = Plan(network, cuts=cuts[:k], max_slice_bytes=slice_bytes)
+            return pl
+        except QTNError as e:
+            last = e
+    raise QTNError(3, f"no greedy cut set of {k_min}..{k_max} cuts fits {slice_bytes:g} bytes per slice ({last})")
 
 
 class Plan:
@@ -341,6 +361,23 @@ def contract_batch(plans, xs, precision: str = "fp32", stream=None) -> np.ndarra
     _check(lib().qtn_contract_batch(hp, xp, n, PRECISIONS[precision], _stream_handle(stream),
                                     _ptr(out, ctypes.c_double)))
     return out[0:2 * n:2] + 1j * out[1:2 * n:2]
+
+
+def batch_last_ms():
+    """(device ms, kernels launched) of the latest multi-plan contract_batch."""
+    ms, k = ctypes.c_float(), ctypes.c_int()
+    _check(lib().qtn_batch_last_ms(ctypes.byref(ms), ctypes.byref(k)))
+    return float(ms.value), int(k.value)
+
+
+def batch_program(plan, precision: str) -> str:
+    """Name of the program a multi-plan contract_batch runs for ``plan``: its
+    48 KiB batched program of the precision's width, else its per-class block
+    program (the rule qtn_contract_batch documents)."""
+    progs = plan.describe()["programs"]
+    wide = precision in ("fp64", "fp32x2")
+    want = "batched/fp64/48KiB" if wide else "batched/fp32/48KiB"
+    return want if want in progs else "block/classes"
 
 
 # ------------------------------------------------------- learned surrogate --
