@@ -1047,14 +1047,17 @@ qtn_status qtn_plan_describe(const qtn_plan_t* plan, char* buf, size_t cap, size
     o << ",\"leaves\":[";
     for (size_t i = 0; i < pg.leaves.size(); ++i) {
       const DevLeaf& L = pg.leaves[i];
+      // A hoisted result (gate -2) has no gate legs: its rank may exceed the
+      // eight slot masks of a gate leaf.
       int cb[kMaxLeafCuts], sb[8];
+      const int n_sb = L.gate == -2 ? 0 : std::min(8, L.rank_nc + L.ncut);
       for (int j = 0; j < L.ncut; ++j) cb[j] = L.cut_bit[j];
-      for (int j = 0; j < L.rank_nc + L.ncut; ++j) sb[j] = L.slot_mask[j];
+      for (int j = 0; j < n_sb; ++j) sb[j] = L.slot_mask[j];
       o << (i ? "," : "") << "{\"base\":" << L.base << ",\"rank_nc\":" << (int)L.rank_nc << ",\"gate\":" << L.gate
         << ",\"cut_bit\":";
       json_ints(o, cb, L.ncut);
       o << ",\"slot_mask\":";
-      json_ints(o, sb, L.rank_nc + L.ncut);
+      json_ints(o, sb, n_sb);
       o << "}";
     }
     o << "],\"pro_arena_elems\":" << pg.pro_arena_elems << ",\"macs_prologue\":" << pg.macs_prologue;
