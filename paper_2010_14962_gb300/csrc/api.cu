@@ -254,7 +254,18 @@ struct qtn_plan {
     dev_allocs.push_back(ga);
     QTN_CUDA(::upload(&be, net.beta));
     dev_allocs.push_back(be);
+    DevLevel* lvls = nullptr;
+    uint32_t* ost = nullptr;
+    if (!pg.levels.empty()) {
+      QTN_CUDA(::upload(&lvls, pg.levels));
+      dev_allocs.push_back(lvls);
+      QTN_CUDA(::upload(&ost, pg.out_start));
+      dev_allocs.push_back(ost);
+    }
     DeviceProgram& d = sl.dprog;
+    d.levels = lvls;
+    d.out_start = ost;
+    d.n_levels = (int)pg.levels.size();
     d.n = pg.n;
     d.p = pg.p;
     d.k = pg.k;
@@ -616,6 +627,24 @@ qtn_status qtn_plan(const qtn_network_t* net, const int32_t* cuts, int k, const 
     if (!compile_program(h->net, h->plan, o, &sl.prog).empty()) continue;
     if (sl.prog.arena_elems + sl.prog.leaf_elems > bd.elems) continue;
     h->slots.push_back(std::move(sl));
+    // The same inner classes, level-ordered: the level executor packs as
+    // many items of this budget into a block as shared memory holds.
+    ProgSlot lv;
+    lv.name = std::string("level") + std::strchr(bd.name, '/');
+    lv.exec = Executor::Level;
+    lv.fp64_only = bd.fp64;
+    lv.fp32_only = !bd.fp64;
+    o.levels = true;
+    if (compile_program(h->net, h->plan, o, &lv.prog).empty()) h->slots.push_back(std::move(lv));
+  }
+  {
+    ProgramOptions o;
+    o.cut_class = cls;
+    o.levels = true;
+    ProgSlot sl;
+    sl.name = "level/classes";
+    sl.exec = Executor::Level;
+    if (compile_program(h->net, h->plan, o, &sl.prog).empty()) h->slots.push_back(std::move(sl));
   }
   if (h->slots.size() == 1) {  // nothing else fits: the per-slice program
     ProgSlot sl = h->slots[0];
@@ -1037,7 +1066,10 @@ qtn_status qtn_plan_describe(const qtn_plan_t* plan, char* buf, size_t cap, size
       << ",\"arena_elems\":" << pg.arena_elems << ",\"width\":" << pg.width << ",\"max_rank\":" << pg.max_rank
       << ",\"macs_per_item\":" << pg.macs_per_item << ",\"n_classes\":" << pg.n_classes
       << ",\"executor\":\""
-      << (plan->slots[which].exec == Executor::Lane ? "lane" : plan->slots[which].exec == Executor::Warp ? "warp" : "block")
+      << (plan->slots[which].exec == Executor::Lane    ? "lane"
+          : plan->slots[which].exec == Executor::Warp  ? "warp"
+          : plan->slots[which].exec == Executor::Level ? "level"
+                                                       : "block")
       << "\",\"outer_class\":";
     json_ints(o, pg.outer_class.data(), pg.outer_class.size());
     o << ",\"inner_class\":";
@@ -1061,6 +1093,13 @@ qtn_status qtn_plan_describe(const qtn_plan_t* plan, char* buf, size_t cap, size
       o << "}";
     }
     o << "],\"pro_arena_elems\":" << pg.pro_arena_elems << ",\"macs_prologue\":" << pg.macs_prologue;
+    o << ",\"levels\":[";
+    for (size_t i = 0; i < pg.levels.size(); ++i)
+      o << (i ? "," : "") << "[" << pg.levels[i].first << "," << pg.levels[i].count << "," << pg.levels[i].outputs
+        << "]";
+    o << "],\"out_start\":[";
+    for (size_t i = 0; i < pg.out_start.size(); ++i) o << (i ? "," : "") << pg.out_start[i];
+    o << "]";
     for (int pass = 0; pass < 2; ++pass) {
     const std::vector<DevStep>& steps = pass ? pg.steps : pg.prologue;
     o << (pass ? ",\"steps\":[" : ",\"prologue\":[");

@@ -587,6 +587,132 @@ __global__ void __launch_bounds__(256) block_exec_kernel(ExecParams P) {
   if (threadIdx.x == 0) P.partials[(size_t)xi * P.blocks_per_x + bx] = s_red[0];
 }
 
+// ------------------------------------------------------------ level exec --
+
+// Shared memory of the level executor: steps, per-step output starts, level
+// table, leaves, leaf table, `items` arenas of `stride` elements, partials.
+struct LevelLayout {
+  size_t out_start, levels, leaves, table, arena, red, total;
+};
+__host__ __device__ inline LevelLayout level_layout(int n_steps, int n_levels, int n_leaves, uint32_t leaf_elems,
+                                                    uint32_t stride, int items, int elem_bytes, int threads) {
+  LevelLayout L;
+  L.out_start = align16((size_t)n_steps * sizeof(DevStep));
+  L.levels = L.out_start + align16((size_t)n_steps * sizeof(uint32_t));
+  L.leaves = L.levels + align16((size_t)n_levels * sizeof(DevLevel));
+  L.table = L.leaves + align16((size_t)n_leaves * sizeof(DevLeaf));
+  L.arena = L.table + align16((size_t)leaf_elems * elem_bytes);
+  L.red = L.arena + align16((size_t)stride * items * elem_bytes);
+  L.total = L.red + (size_t)threads * sizeof(Partial);
+  return L;
+}
+
+struct LevelParams {
+  const DevLevel* levels;
+  const uint32_t* out_start;
+  int n_levels;
+  int log2_items;
+  uint32_t arena_stride;
+};
+
+// Output o of step st for one item: C[pos(o)] = sum_k A[..k..] B[..k..]
+// (canonical form of the step), or the root's value added to the sums.
+template <class V, int K, class Ops>
+__device__ __forceinline__ void level_output(const DevStep& st, uint32_t o, const V* __restrict__ A,
+                                             const V* __restrict__ B, V* __restrict__ C, double& sr, double& cr,
+                                             double& si, double& ci) {
+  const int ma = st.ma, nb = st.nb, kb = st.kb;
+  const uint32_t m = o & ((1u << ma) - 1u), n = (o >> ma) & ((1u << nb) - 1u), b = o >> (ma + nb);
+  const V* ap = A + m + (b << (ma + kb));
+  const V* bp = B + (n << kb) + (b << (kb + nb));
+  V acc = Ops::zero();
+  if (K > 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) Ops::fma(acc, ap[k << ma], bp[k]);
+  } else {
+    for (uint32_t k = 0; k < (1u << kb); ++k) Ops::fma(acc, ap[k << ma], bp[k]);
+  }
+  if (st.flags & STEP_ROOT) {
+    kahan_add(sr, cr, Ops::re(acc));
+    kahan_add(si, ci, Ops::im(acc));
+  } else {
+    uint32_t pos = 0;
+    for (uint32_t x = o; x; x &= x - 1u) pos += st.w[__ffs(x) - 1];
+    C[pos] = acc;
+  }
+}
+
+// Level executor: a block takes 2^log2_items consecutive work items at a
+// time.  For each level the outputs of all its merges, for all those items,
+// form one flat range (item index fastest) that the threads stride over;
+// one barrier ends the level.  Item arenas are `arena_stride` elements apart
+// (an odd stride, so the items of one warp hit different banks).
+template <class V, class Ops = CplxOps<V>>
+__global__ void __launch_bounds__(256) level_exec_kernel(ExecParams P, LevelParams LP) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int T = blockDim.x;
+  const uint32_t log2I = (uint32_t)LP.log2_items;
+  const uint32_t I = 1u << log2I;
+  const LevelLayout lay = level_layout(P.n_steps, LP.n_levels, P.n_leaves, P.leaf_elems, LP.arena_stride, (int)I,
+                                       (int)sizeof(V), T);
+  DevStep* s_steps = reinterpret_cast<DevStep*>(smem);
+  uint32_t* s_out = reinterpret_cast<uint32_t*>(smem + lay.out_start);
+  DevLevel* s_levels = reinterpret_cast<DevLevel*>(smem + lay.levels);
+  DevLeaf* s_leaves = reinterpret_cast<DevLeaf*>(smem + lay.leaves);
+  V* s_lt = reinterpret_cast<V*>(smem + lay.table);
+  V* s_arena = reinterpret_cast<V*>(smem + lay.arena);
+  Partial* s_red = reinterpret_cast<Partial*>(smem + lay.red);
+  const int xi = blockIdx.x / P.blocks_per_x;
+  const int bx = blockIdx.x % P.blocks_per_x;
+  copy_words(s_steps, P.steps, (size_t)P.n_steps * sizeof(DevStep));
+  copy_words(s_out, LP.out_start, (size_t)P.n_steps * sizeof(uint32_t));
+  copy_words(s_levels, LP.levels, (size_t)LP.n_levels * sizeof(DevLevel));
+  copy_words(s_leaves, P.leaves, (size_t)P.n_leaves * sizeof(DevLeaf));
+  copy_words(s_lt, static_cast<const V*>(P.leaf_tables) + (size_t)xi * P.leaf_elems,
+             (size_t)P.leaf_elems * sizeof(V));
+  __syncthreads();
+
+  double sr = 0.0, si = 0.0, cr = 0.0, ci = 0.0;
+  const uint64_t S = P.slice_hi - P.slice_lo;
+  for (uint64_t i0 = (uint64_t)bx * I; i0 < S; i0 += (uint64_t)P.blocks_per_x * I) {
+    const uint32_t nI = (uint32_t)((S - i0) < I ? (S - i0) : I);
+    for (int l = 0; l < LP.n_levels; ++l) {
+      const DevLevel lv = s_levels[l];
+      const uint32_t total = lv.outputs << log2I;
+      int j = lv.first;
+      uint32_t jbeg = s_out[j];
+      uint32_t jend = jbeg + (1u << (s_steps[j].ma + s_steps[j].nb + s_steps[j].bb));
+      for (uint32_t f = threadIdx.x; f < total; f += T) {
+        const uint32_t item = f & (I - 1u), of = f >> log2I;
+        while (of >= jend) {  // steps of the level in order; of < lv.outputs
+          ++j;
+          jbeg = s_out[j];
+          jend = jbeg + (1u << (s_steps[j].ma + s_steps[j].nb + s_steps[j].bb));
+        }
+        if (item >= nI) continue;
+        const DevStep& st = s_steps[j];
+        const uint64_t s = P.slice_lo + i0 + item;
+        V* arena = s_arena + (size_t)item * LP.arena_stride;
+        const V* A = (st.flags & STEP_A_LEAF) ? s_lt + leaf_offset(s_leaves[st.a], s) : arena + st.a;
+        const V* B = (st.flags & STEP_B_LEAF) ? s_lt + leaf_offset(s_leaves[st.b], s) : arena + st.b;
+        V* C = arena + st.c;
+        const uint32_t o = of - jbeg;
+        switch (st.kb) {
+          case 0: level_output<V, 1, Ops>(st, o, A, B, C, sr, cr, si, ci); break;
+          case 1: level_output<V, 2, Ops>(st, o, A, B, C, sr, cr, si, ci); break;
+          case 2: level_output<V, 4, Ops>(st, o, A, B, C, sr, cr, si, ci); break;
+          case 3: level_output<V, 8, Ops>(st, o, A, B, C, sr, cr, si, ci); break;
+          default: level_output<V, 0, Ops>(st, o, A, B, C, sr, cr, si, ci); break;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  s_red[threadIdx.x] = Partial::make(sr, si, cr, ci);
+  tree_reduce(s_red, T);
+  if (threadIdx.x == 0) P.partials[(size_t)xi * P.blocks_per_x + bx] = s_red[0];
+}
+
 // -------------------------------------------------------------- prologue --
 
 // Hoisted merges (no outer slice class below them): run once per bit string
@@ -819,6 +945,22 @@ bool exec_shape_typed(const DeviceProgram& prog, int nx, uint64_t slices_per_x, 
     sh.smem = L.total;
     if (!shape_for_kernel(block_exec_kernel<V, true, Ops>, sh.threads, sh.smem, &occ)) return false;
     per_block_items = (uint64_t)(sh.threads / 32);
+  } else if (prog.exec == Executor::Level) {
+    // The most items (power of two, <= 32) whose arenas fit on chip.
+    sh.threads = 256;
+    sh.arena_stride = prog.arena_elems | 1u;
+    int lg = 5;
+    LevelLayout L;
+    for (;; --lg) {
+      L = level_layout(prog.n_steps, prog.n_levels, prog.n_leaves, prog.leaf_elems, sh.arena_stride, 1 << lg,
+                       elem_bytes, sh.threads);
+      if (L.total <= (size_t)max_optin || lg == 0) break;
+    }
+    if (L.total > (size_t)max_optin) return false;
+    sh.log2_items = lg;
+    sh.smem = L.total;
+    if (!shape_for_kernel(level_exec_kernel<V, Ops>, sh.threads, sh.smem, &occ)) return false;
+    per_block_items = 1ull << lg;
   } else {
     sh.threads = 256;
     SmemLayout L = smem_layout(prog.n_steps, prog.n_leaves, prog.leaf_elems, prog.arena_elems, elem_bytes,
@@ -890,6 +1032,9 @@ cudaError_t launch_typed(const DeviceProgram& prog, const uint8_t* d_x, int nx, 
     }
   } else if (prog.exec == Executor::Warp) {
     block_exec_kernel<V, true, Ops><<<grid, shape.threads, shape.smem, stream>>>(P);
+  } else if (prog.exec == Executor::Level) {
+    const LevelParams LP{prog.levels, prog.out_start, prog.n_levels, shape.log2_items, shape.arena_stride};
+    level_exec_kernel<V, Ops><<<grid, shape.threads, shape.smem, stream>>>(P, LP);
   } else {
     block_exec_kernel<V, false, Ops><<<grid, shape.threads, shape.smem, stream>>>(P);
   }

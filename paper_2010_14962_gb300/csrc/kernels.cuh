@@ -9,7 +9,10 @@
 
 namespace qtn {
 
-enum class Executor : int { Lane = 0, Block = 1, Warp = 2 };
+// Lane: one work item per thread; Block: one item per block, a barrier per
+// merge; Warp: one item per warp; Level: 2^log2_items items per block, all
+// merges of one tree level (of all those items) at once, a barrier per level.
+enum class Executor : int { Lane = 0, Block = 1, Warp = 2, Level = 3 };
 
 // Arithmetic of the merges: complex128, complex64, double-float complex64
 // (FP32X2), and complex64 storage with products rounded as the tensor cores
@@ -43,6 +46,10 @@ struct DeviceProgram {
   const int8_t* gate_out_kind = nullptr;
   const double* gamma = nullptr;
   const double* beta = nullptr;
+  // Level executor only.
+  const DevLevel* levels = nullptr;
+  const uint32_t* out_start = nullptr;
+  int n_levels = 0;
 };
 
 // One launch sequence: leaf tables for nx bit strings, the slice range
@@ -59,6 +66,8 @@ struct LaunchBuffers {
 struct ExecShape {
   int threads = 0;
   int blocks_per_x = 0;
+  int log2_items = 0;          // Level executor: items per block = 2^log2_items
+  uint32_t arena_stride = 0;   // Level executor: elements between item arenas
   size_t smem = 0;
   size_t pro_smem = 0;  // prologue kernel (one block of 256 threads per bit string)
 };

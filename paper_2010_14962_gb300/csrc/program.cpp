@@ -279,11 +279,32 @@ std::string compile_program(const Network& net, const Plan& plan_in, const Progr
   }
   pg.leaf_elems = leaf_off;
 
+  // Item steps by level (stable: DFS order within a level).
+  std::vector<int> item_order;
+  for (int j : order)
+    if (!pro[j]) item_order.push_back(j);
+  std::vector<int> level_of(plan.merges.size(), 0);
+  if (opt.levels) {
+    std::vector<int> lev_t(T, 0);  // leaves and hoisted results: level 0
+    for (int j : item_order) {
+      const Merge& mg = plan.merges[j];
+      auto lv = [&](int t) { return (is_leaf(t) || exported[t]) ? 0 : lev_t[t]; };
+      lev_t[mg.c] = 1 + std::max(lv(mg.a), lv(mg.b));
+      level_of[j] = lev_t[mg.c];
+    }
+    std::stable_sort(item_order.begin(), item_order.end(),
+                     [&](int x, int y) { return level_of[x] < level_of[y]; });
+  }
+
   std::vector<uint32_t> where(T, 0);
   auto emit = [&](bool prologue_pass, bool c_reuses_a, std::vector<DevStep>* out, uint32_t* arena_high,
                   double* macs) -> std::string {
     Arena arena;
-    for (int j : order) {
+    const bool by_level = opt.levels && !prologue_pass;
+    std::vector<uint32_t> level_release;  // inputs freed when their level ends
+    const std::vector<int>& seq = prologue_pass ? order : item_order;
+    for (size_t si = 0; si < seq.size(); ++si) {
+      const int j = seq[si];
       if ((bool)pro[j] != prologue_pass) continue;
       const Merge& mg = plan.merges[j];
       const Canon& c = canon[j];
@@ -315,9 +336,10 @@ std::string compile_program(const Network& net, const Plan& plan_in, const Progr
       pg.max_rank = std::max(pg.max_rank, rc);
       *macs += std::ldexp(1.0, wd);
       // A is read completely before the first store of C; B may be read
-      // while C is written, so only A's block may be reused by C.
+      // while C is written, so only A's block may be reused by C.  Within a
+      // level nothing is reused: its merges run at the same time.
       if (a_block >= 0) {
-        if (c_reuses_a) arena.release((uint32_t)a_block);
+        if (c_reuses_a && !by_level) arena.release((uint32_t)a_block);
         else to_release.push_back((uint32_t)a_block);
       }
       const Set canon_ix = concat(concat(c.m, c.n), c.b);
@@ -344,7 +366,16 @@ std::string compile_program(const Network& net, const Plan& plan_in, const Progr
           st.w[b] = (uint16_t)(1u << (it - lay.begin()));
         }
       }
-      for (uint32_t r : to_release) arena.release(r);
+      if (by_level) {
+        level_release.insert(level_release.end(), to_release.begin(), to_release.end());
+        const bool level_ends = si + 1 == seq.size() || level_of[seq[si + 1]] != level_of[j];
+        if (level_ends) {
+          for (uint32_t r : level_release) arena.release(r);
+          level_release.clear();
+        }
+      } else {
+        for (uint32_t r : to_release) arena.release(r);
+      }
       out->push_back(st);
     }
     *arena_high = std::max<uint32_t>(arena.high, 1);
@@ -354,6 +385,23 @@ std::string compile_program(const Network& net, const Plan& plan_in, const Progr
   if (err.empty()) err = emit(false, opt.c_reuses_a, &pg.steps, &pg.arena_elems, &pg.macs_per_item);
   if (!err.empty()) return err;
   if (pg.prologue.empty()) pg.pro_arena_elems = 0;
+  if (opt.levels) {
+    pg.out_start.assign(pg.steps.size(), 0);
+    for (size_t i = 0; i < pg.steps.size(); ++i) {
+      const DevStep& st = pg.steps[i];
+      const uint32_t size = 1u << (st.ma + st.nb + st.bb);
+      if (i == 0 || level_of[item_order[i]] != level_of[item_order[i - 1]]) {
+        if (pg.levels.size() >= 0xffff) return "too many levels";
+        pg.levels.push_back(DevLevel{(uint16_t)i, 0, 0});
+      }
+      DevLevel& lv = pg.levels.back();
+      // Executors index (output, item) pairs of a level in 32 bits, <= 32 items.
+      if ((uint64_t)lv.outputs + size > (1ull << 26)) return "level too large";
+      pg.out_start[i] = lv.outputs;
+      lv.outputs += size;
+      ++lv.count;
+    }
+  }
 
   pg.gate_q.resize(2 * net.gates.size());
   pg.gate_layer.resize(net.gates.size());

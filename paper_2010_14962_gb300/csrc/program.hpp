@@ -30,6 +30,13 @@
 // run once per bit string; the ones consumed by per-item merges write their
 // result into the leaf table as "pseudo-leaves" (gate -2), which the item
 // steps read like leaves.
+//
+// Levels (optional): the item steps are ordered by their depth in the
+// contraction tree (a merge's level is one more than the deepest merge that
+// produces one of its operands).  Merges of one level are independent, so
+// an executor can run all of them at once, with one barrier per level
+// instead of one per merge; the arena is then allocated per level (a
+// level's results never overlap the tensors it reads).
 #pragma once
 #include <cstdint>
 #include <string>
@@ -73,7 +80,16 @@ struct DevStep {
 };
 static_assert(sizeof(DevStep) == 52, "DevStep layout");
 
+// One level of a level-ordered program: steps [first, first + count), whose
+// outputs (2^rc each, in step order) form one flat range of `outputs`.
+struct DevLevel {
+  uint16_t first, count;
+  uint32_t outputs;
+};
+static_assert(sizeof(DevLevel) == 8, "DevLevel layout");
+
 struct ProgramOptions {
+  bool levels = false;            // order item steps by tree level (see above)
   bool c_reuses_a = false;        // C may overwrite A's arena block
   bool hoist = true;              // run outer-class-invariant merges once per bit string
   std::vector<int> cut_class;     // class of each cut (size k); empty = one class per cut
@@ -89,6 +105,8 @@ struct Program {
   std::vector<int> root_class;       // class of each canonical bit of the root's output
   std::vector<DevLeaf> leaves;
   std::vector<DevStep> steps;        // per work item
+  std::vector<DevLevel> levels;      // level-ordered programs only
+  std::vector<uint32_t> out_start;   // per step: first output in its level's range
   std::vector<DevStep> prologue;     // once per bit string: merges that no outer class reaches
   uint32_t pro_arena_elems = 0;      // prologue arena (elements)
   double macs_prologue = 0;          // per bit string

@@ -287,3 +287,45 @@ def test_fp32x2_meets_fp64_accuracy(gpu, config80):
     inst, plan, xs, refs = config80
     got = device_amplitudes(plan, xs, "fp32x2")
     assert np.max(np.abs(got - refs) / np.abs(refs)) < 1e-10
+
+
+def _executor_precisions(name):
+    if "/fp64/" in name:
+        return ["fp64", "fp32x2"]
+    if "/fp32/" in name:
+        return ["fp32"]
+    if name.startswith("lane"):
+        return ["fp64", "fp32"]
+    return ["fp64", "fp32x2", "fp32"]
+
+
+@pytest.mark.parametrize("n,p,k,seed,nx", [(16, 1, 2, 1, 3), (40, 2, 10, 2, 2), (80, 1, 16, 3, 1)])
+def test_every_executor_matches_oracle(gpu, n, p, k, seed, nx):
+    # Every compiled program on its executor (lane, block, warp, level), forced
+    # through qtn_plan_select_executor, in every arithmetic it is compiled for.
+    inst = I.qaoa_instance(n, p, seed)
+    net = qtn.Network(n, inst.edges, inst.gamma, inst.beta)
+    plan = qtn.Plan(net, k=k)
+    xs = I.bitstrings(n, nx, seed + 40)
+    refs, l1s = [], []
+    for x in xs:
+        r = O.tn_amplitude(n, inst.edges, inst.gamma, inst.beta, x, cuts=plan.cut_names(), per_slice=True,
+                           threads=16)
+        refs.append(r.value)
+        l1s.append(np.sum(np.abs(r.per_slice)))
+    d = plan.describe()
+    checked = []
+    for name in d["programs"]:
+        if name == d["executor"]:
+            continue  # the per-slice program: slice ranges, tested by the slice tests
+        for prec in _executor_precisions(name):
+            plan.select_executor(name, prec, nx)
+            got = device_amplitudes(plan, xs, prec)
+            for g, r, l1 in zip(got, refs, l1s):
+                if prec == "fp32":
+                    assert abs(g - r) <= fp32_bound(len(inst.edges) * p, [l1]), (name, prec)
+                else:
+                    assert abs(g - r) <= 1e-10 * abs(r), (name, prec, abs(g - r) / abs(r))
+            checked.append((name, prec))
+    print(len(checked), "program/arithmetic pairs")
+    assert any(nm.startswith("level") for nm, _ in checked)

@@ -219,6 +219,47 @@ def test_emulated_programs_match_oracle_per_slice(n, p, k, seed):
         assert abs(got.sum() - ref.value) < 1e-13 * np.sum(np.abs(ref.per_slice)), name
 
 
+@pytest.mark.parametrize("n,p,k,seed", [(16, 1, 2, 1), (40, 2, 10, 2), (80, 1, 16, 3)])
+def test_level_programs_are_race_free(n, p, k, seed):
+    # Level-ordered programs: the merges of a level run at the same time, so
+    # within a level no result may overlap another result or any operand the
+    # level reads; the level table must tile the steps and their outputs.
+    inst = I.qaoa_instance(n, p, seed)
+    net = qtn.Network(n, inst.edges, inst.gamma, inst.beta)
+    d = qtn.Plan(net, k=k).describe()
+    level_progs = {k_: v for k_, v in d["programs"].items() if v["executor"] == "level"}
+    assert "level/classes" in level_progs
+    for name, prog in level_progs.items():
+        steps, levels, out_start = prog["steps"], prog["levels"], prog["out_start"]
+        assert levels and levels[0][0] == 0 and len(out_start) == len(steps), name
+        nxt = 0
+        for li, (first, count, outputs) in enumerate(levels):
+            assert first == nxt and count >= 1, name
+            nxt = first + count
+            acc = 0
+            reads, writes = [], []
+            for j in range(first, first + count):
+                st = steps[j]
+                ma, nb, kb, bb = st["ma"], st["nb"], st["kb"], st["bb"]
+                assert out_start[j] == acc, name
+                acc += 1 << (ma + nb + bb)
+                if not st["flags"] & 1:
+                    reads.append((st["a"], st["a"] + (1 << (ma + kb + bb))))
+                if not st["flags"] & 2:
+                    reads.append((st["b"], st["b"] + (1 << (kb + nb + bb))))
+                if st["flags"] & 4:
+                    assert li == len(levels) - 1 and count == 1, name  # the root ends the program alone
+                else:
+                    writes.append((st["c"], st["c"] + (1 << (ma + nb + bb))))
+            assert acc == outputs, name
+            for lo, hi in reads + writes:
+                assert 0 <= lo < hi <= prog["arena_elems"], name
+            for i, (lo, hi) in enumerate(writes):
+                for lo2, hi2 in writes[i + 1:] + reads:
+                    assert hi <= lo2 or hi2 <= lo, (name, li)
+        assert nxt == len(steps), name
+
+
 def test_emulated_program_n80_sampled_slices():
     n, p = 80, 1
     inst = I.qaoa_instance(n, p, 3)
