@@ -282,7 +282,8 @@ def run_ours(args, rank, world, local_rank):
                    "parallelism": f"weak: {nx} bit strings per GPU, slices across CTAs/threads"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": profiled_traffic(args.precision),
-                     "kernel": "lane_exec_kernel" if prog["executor"] == "lane" else "block_exec_kernel",
+                     "kernel": {"lane": "lane_exec_kernel", "level": "level_exec_kernel"}.get(prog["executor"],
+                                                                                            "block_exec_kernel"),
                      "peak_source": ("FP32 pipe: 152 SMs x 128 lanes x 2 flop x %.0f MHz (max SM clock of measured "
                                      "peaks) / %d FP32 instructions per multiply-add"
                                      % (sm_for_peak, INSTR_PER_MAC[args.precision]))

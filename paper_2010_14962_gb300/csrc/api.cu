@@ -155,6 +155,7 @@ struct ProgSlot {
   Program prog;
   Executor exec = Executor::Block;
   bool fp64_only = false, fp32_only = false;
+  int threads = 256;  // level executor: threads per block
   DeviceProgram dprog;
   bool uploaded = false;
   uint64_t items() const { return 1ull << prog.n_outer; }
@@ -266,6 +267,7 @@ struct qtn_plan {
     d.levels = lvls;
     d.out_start = ost;
     d.n_levels = (int)pg.levels.size();
+    d.block_threads = sl.threads;
     d.n = pg.n;
     d.p = pg.p;
     d.k = pg.k;
@@ -635,7 +637,13 @@ qtn_status qtn_plan(const qtn_network_t* net, const int32_t* cuts, int k, const 
     lv.fp64_only = bd.fp64;
     lv.fp32_only = !bd.fp64;
     o.levels = true;
-    if (compile_program(h->net, h->plan, o, &lv.prog).empty()) h->slots.push_back(std::move(lv));
+    if (compile_program(h->net, h->plan, o, &lv.prog).empty()) {
+      ProgSlot wide_lv = lv;  // the same program on 1024 threads
+      wide_lv.name += "/t1024";
+      wide_lv.threads = 1024;
+      h->slots.push_back(std::move(lv));
+      h->slots.push_back(std::move(wide_lv));
+    }
   }
   {
     ProgramOptions o;
@@ -644,7 +652,13 @@ qtn_status qtn_plan(const qtn_network_t* net, const int32_t* cuts, int k, const 
     ProgSlot sl;
     sl.name = "level/classes";
     sl.exec = Executor::Level;
-    if (compile_program(h->net, h->plan, o, &sl.prog).empty()) h->slots.push_back(std::move(sl));
+    if (compile_program(h->net, h->plan, o, &sl.prog).empty()) {
+      ProgSlot wide_sl = sl;
+      wide_sl.name += "/t1024";
+      wide_sl.threads = 1024;
+      h->slots.push_back(std::move(sl));
+      h->slots.push_back(std::move(wide_sl));
+    }
   }
   if (h->slots.size() == 1) {  // nothing else fits: the per-slice program
     ProgSlot sl = h->slots[0];

@@ -590,7 +590,8 @@ __global__ void __launch_bounds__(256) block_exec_kernel(ExecParams P) {
 // ------------------------------------------------------------ level exec --
 
 // Shared memory of the level executor: steps, per-step output starts, level
-// table, leaves, leaf table, `items` arenas of `stride` elements, partials.
+// table, leaves, leaf table, then `items` arenas of `stride` elements, which
+// the per-thread partials overlay once the last level is done.
 struct LevelLayout {
   size_t out_start, levels, leaves, table, arena, red, total;
 };
@@ -602,8 +603,9 @@ __host__ __device__ inline LevelLayout level_layout(int n_steps, int n_levels, i
   L.leaves = L.levels + align16((size_t)n_levels * sizeof(DevLevel));
   L.table = L.leaves + align16((size_t)n_leaves * sizeof(DevLeaf));
   L.arena = L.table + align16((size_t)leaf_elems * elem_bytes);
-  L.red = L.arena + align16((size_t)stride * items * elem_bytes);
-  L.total = L.red + (size_t)threads * sizeof(Partial);
+  L.red = L.arena;
+  const size_t arena_bytes = (size_t)stride * items * elem_bytes, red_bytes = (size_t)threads * sizeof(Partial);
+  L.total = L.arena + align16(arena_bytes > red_bytes ? arena_bytes : red_bytes);
   return L;
 }
 
@@ -648,7 +650,7 @@ __device__ __forceinline__ void level_output(const DevStep& st, uint32_t o, cons
 // one barrier ends the level.  Item arenas are `arena_stride` elements apart
 // (an odd stride, so the items of one warp hit different banks).
 template <class V, class Ops = CplxOps<V>>
-__global__ void __launch_bounds__(256) level_exec_kernel(ExecParams P, LevelParams LP) {
+__global__ void __launch_bounds__(1024) level_exec_kernel(ExecParams P, LevelParams LP) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int T = blockDim.x;
   const uint32_t log2I = (uint32_t)LP.log2_items;
@@ -705,7 +707,7 @@ __global__ void __launch_bounds__(256) level_exec_kernel(ExecParams P, LevelPara
           default: level_output<V, 0, Ops>(st, o, A, B, C, sr, cr, si, ci); break;
         }
       }
-      __syncthreads();
+      __syncthreads();  // also orders the last level's arena reads before s_red's stores
     }
   }
   s_red[threadIdx.x] = Partial::make(sr, si, cr, ci);
@@ -947,7 +949,7 @@ bool exec_shape_typed(const DeviceProgram& prog, int nx, uint64_t slices_per_x, 
     per_block_items = (uint64_t)(sh.threads / 32);
   } else if (prog.exec == Executor::Level) {
     // The most items (power of two, <= 32) whose arenas fit on chip.
-    sh.threads = 256;
+    sh.threads = prog.block_threads;
     sh.arena_stride = prog.arena_elems | 1u;
     int lg = 5;
     LevelLayout L;

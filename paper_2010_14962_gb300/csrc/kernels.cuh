@@ -50,6 +50,7 @@ struct DeviceProgram {
   const DevLevel* levels = nullptr;
   const uint32_t* out_start = nullptr;
   int n_levels = 0;
+  int block_threads = 256;  // threads per block (256 or 1024)
 };
 
 // One launch sequence: leaf tables for nx bit strings, the slice range

@@ -320,12 +320,17 @@ def test_every_executor_matches_oracle(gpu, n, p, k, seed, nx):
             continue  # the per-slice program: slice ranges, tested by the slice tests
         for prec in _executor_precisions(name):
             plan.select_executor(name, prec, nx)
-            got = device_amplitudes(plan, xs, prec)
+            try:
+                got = device_amplitudes(plan, xs, prec)
+            except qtn.QTNError as e:  # a program whose working set exceeds shared memory at this width
+                assert e.status == 6 and "shared memory" in str(e), (name, prec, str(e))
+                continue
             for g, r, l1 in zip(got, refs, l1s):
                 if prec == "fp32":
                     assert abs(g - r) <= fp32_bound(len(inst.edges) * p, [l1]), (name, prec)
                 else:
                     assert abs(g - r) <= 1e-10 * abs(r), (name, prec, abs(g - r) / abs(r))
             checked.append((name, prec))
-    print(len(checked), "program/arithmetic pairs")
+    print(len(checked), "program/arithmetic pairs:", checked)
     assert any(nm.startswith("level") for nm, _ in checked)
+    assert {pr for _, pr in checked} >= {"fp64", "fp32x2", "fp32"}
