@@ -47,9 +47,11 @@ def measured_peaks():
 
 
 # FP32 pipe instructions per real multiply-add in each arithmetic (the
-# double-float MAC: 1 FMUL + 3 FFMA + 2 TwoSum (6 each) + 2 FADD + 2 Fast2Sum
-# (3 each) = 24; TF32 / split forms: conversions + products on the FP32 pipe).
-INSTR_PER_MAC = {"fp32": 1, "fp32x2": 24, "tf32": 3, "tf32x3": 9, "bf16x3": 13, "bf16x6": 22}
+# double-float MAC with lazy normalisation: 1 FMUL + 3 FFMA for the product,
+# one TwoSum (6) into the high word, 2 FADD into the low word = 12, plus one
+# TwoSum per part and output; TF32 / split forms: conversions + products on
+# the FP32 pipe).
+INSTR_PER_MAC = {"fp32": 1, "fp32x2": 12, "tf32": 3, "tf32x3": 9, "bf16x3": 13, "bf16x6": 22}
 
 
 def alu_peak_tflops(prec: str, sm_mhz: float) -> float:

@@ -54,6 +54,12 @@ struct CplxOps<float2> {
     acc.y = fmaf(a.x, b.y, acc.y);
     acc.y = fmaf(a.y, b.x, acc.y);
   }
+  static __device__ __forceinline__ float2 mul(float2 a, float2 b) {
+    float2 r = zero();
+    fma(r, a, b);
+    return r;
+  }
+  static __device__ __forceinline__ void finish(float2&) {}
   static __device__ __forceinline__ float2 from(double re, double im) {
     return make_float2((float)re, (float)im);
   }
@@ -70,6 +76,12 @@ struct CplxOps<double2> {
     acc.y = ::fma(a.x, b.y, acc.y);
     acc.y = ::fma(a.y, b.x, acc.y);
   }
+  static __device__ __forceinline__ double2 mul(double2 a, double2 b) {
+    double2 r = zero();
+    fma(r, a, b);
+    return r;
+  }
+  static __device__ __forceinline__ void finish(double2&) {}
   static __device__ __forceinline__ double2 from(double re, double im) { return make_double2(re, im); }
   static __device__ __forceinline__ double re(double2 v) { return v.x; }
   static __device__ __forceinline__ double im(double2 v) { return v.y; }
@@ -94,31 +106,50 @@ __device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& 
   s = __fadd_rn(a, b);
   e = __fsub_rn(b, __fsub_rn(s, a));
 }
-// (ah, al) += (xh, xl) * (yh, yl) in double-word arithmetic: the product's
-// high part is exact (TwoProd), the cross terms are added to its low part,
-// and the sum is the accurate double-word addition.
-__device__ __forceinline__ void dw_fma(float& ah, float& al, float xh, float xl, float yh, float yl) {
-  const float ph = __fmul_rn(xh, yh);
-  float pl = __fmaf_rn(xh, yh, -ph);
+// Double-word product (xh + xl)(yh + yl) as ph + pl: ph = fl(xh yh), and pl
+// = its exact rounding error (FMA) plus the cross terms (the xl yl term is
+// below the format's precision).
+__device__ __forceinline__ void dw_prod(float xh, float xl, float yh, float yl, float& ph, float& pl) {
+  ph = __fmul_rn(xh, yh);
+  pl = __fmaf_rn(xh, yh, -ph);
   pl = __fmaf_rn(xh, yl, pl);
   pl = __fmaf_rn(xl, yh, pl);
-  float sh, sl, th, tl;
-  two_sum(ah, ph, sh, sl);
-  two_sum(al, pl, th, tl);
-  sl = __fadd_rn(sl, th);
-  fast_two_sum(sh, sl, sh, sl);
-  sl = __fadd_rn(sl, tl);
-  fast_two_sum(sh, sl, ah, al);
+}
+// (ah, al) += x * y with lazy normalisation: ah takes the TwoSum of the
+// product's high part, al collects that sum's exact error and the product's
+// low part in plain FP32 (a second-order quantity, so its own roundings stay
+// below the double-word precision); finish() renormalises once per output
+// instead of once per product.
+__device__ __forceinline__ void dw_fma_lazy(float& ah, float& al, float xh, float xl, float yh, float yl) {
+  float ph, pl, sh, e;
+  dw_prod(xh, xl, yh, yl, ph, pl);
+  two_sum(ah, ph, sh, e);
+  ah = sh;
+  al = __fadd_rn(al, __fadd_rn(e, pl));
 }
 
 template <>
 struct CplxOps<dfc> {
   static __device__ __forceinline__ dfc zero() { return dfc{0.f, 0.f, 0.f, 0.f}; }
   static __device__ __forceinline__ void fma(dfc& acc, dfc a, dfc b) {
-    dw_fma(acc.rh, acc.rl, a.rh, a.rl, b.rh, b.rl);
-    dw_fma(acc.rh, acc.rl, -a.ih, -a.il, b.ih, b.il);
-    dw_fma(acc.ih, acc.il, a.rh, a.rl, b.ih, b.il);
-    dw_fma(acc.ih, acc.il, a.ih, a.il, b.rh, b.rl);
+    dw_fma_lazy(acc.rh, acc.rl, a.rh, a.rl, b.rh, b.rl);
+    dw_fma_lazy(acc.rh, acc.rl, -a.ih, -a.il, b.ih, b.il);
+    dw_fma_lazy(acc.ih, acc.il, a.rh, a.rl, b.ih, b.il);
+    dw_fma_lazy(acc.ih, acc.il, a.ih, a.il, b.rh, b.rl);
+  }
+  // a * b: the first product of each part needs no sum.
+  static __device__ __forceinline__ dfc mul(dfc a, dfc b) {
+    dfc r;
+    dw_prod(a.rh, a.rl, b.rh, b.rl, r.rh, r.rl);
+    dw_fma_lazy(r.rh, r.rl, -a.ih, -a.il, b.ih, b.il);
+    dw_prod(a.rh, a.rl, b.ih, b.il, r.ih, r.il);
+    dw_fma_lazy(r.ih, r.il, a.ih, a.il, b.rh, b.rl);
+    return r;
+  }
+  // Renormalise each part to a double word (|lo| <= ulp(hi) / 2).
+  static __device__ __forceinline__ void finish(dfc& v) {
+    two_sum(v.rh, v.rl, v.rh, v.rl);
+    two_sum(v.ih, v.il, v.ih, v.il);
   }
   static __device__ __forceinline__ dfc from(double re, double im) {
     const float rh = (float)re, ih = (float)im;
@@ -172,6 +203,12 @@ struct RoundOps {
     acc.y = mul_add(acc.y, a.x, b.y);
     acc.y = mul_add(acc.y, a.y, b.x);
   }
+  static __device__ __forceinline__ float2 mul(float2 a, float2 b) {
+    float2 r = zero();
+    fma(r, a, b);
+    return r;
+  }
+  static __device__ __forceinline__ void finish(float2&) {}
   static __device__ __forceinline__ double re(float2 v) { return (double)v.x; }
   static __device__ __forceinline__ double im(float2 v) { return (double)v.y; }
 };
@@ -336,9 +373,10 @@ __device__ __forceinline__ V lane_merge(const V* __restrict__ A, int sa, const V
     for (int k = 0; k < (1 << KB); ++k) b[k] = B[(k + (n << KB)) * sb];
 #pragma unroll
     for (int m = 0; m < (1 << MA); ++m) {
-      acc = Ops::zero();
+      acc = Ops::mul(a[m], b[0]);
 #pragma unroll
-      for (int k = 0; k < (1 << KB); ++k) Ops::fma(acc, a[m + (k << MA)], b[k]);
+      for (int k = 1; k < (1 << KB); ++k) Ops::fma(acc, a[m + (k << MA)], b[k]);
+      Ops::finish(acc);
       if (store) {
         const uint32_t o = (uint32_t)(m + (n << MA));
         uint32_t pos = 0;
@@ -469,13 +507,14 @@ __device__ __forceinline__ void group_merge_k(const StepRegs sr_, const uint16_t
     const uint32_t m = o & mmask, n = (o >> ma) & nmask, b = o >> (ma + nb);
     const V* ap = A + m + (b << (ma + kb));
     const V* bp = B + (n << kb) + (b << (kb + nb));
-    V acc = Ops::zero();
+    V acc = Ops::mul(ap[0], bp[0]);
     if (K > 0) {
 #pragma unroll
-      for (int k = 0; k < K; ++k) Ops::fma(acc, ap[k << ma], bp[k]);
+      for (int k = 1; k < K; ++k) Ops::fma(acc, ap[k << ma], bp[k]);
     } else {
-      for (uint32_t k = 0; k < (1u << kb); ++k) Ops::fma(acc, ap[k << ma], bp[k]);
+      for (uint32_t k = 1; k < (1u << kb); ++k) Ops::fma(acc, ap[k << ma], bp[k]);
     }
+    Ops::finish(acc);
     if (sr_.root) {
       kahan_add(sr, cr, Ops::re(acc));
       kahan_add(si, ci, Ops::im(acc));
@@ -627,13 +666,14 @@ __device__ __forceinline__ void level_output(const DevStep& st, uint32_t o, cons
   const uint32_t m = o & ((1u << ma) - 1u), n = (o >> ma) & ((1u << nb) - 1u), b = o >> (ma + nb);
   const V* ap = A + m + (b << (ma + kb));
   const V* bp = B + (n << kb) + (b << (kb + nb));
-  V acc = Ops::zero();
+  V acc = Ops::mul(ap[0], bp[0]);
   if (K > 0) {
 #pragma unroll
-    for (int k = 0; k < K; ++k) Ops::fma(acc, ap[k << ma], bp[k]);
+    for (int k = 1; k < K; ++k) Ops::fma(acc, ap[k << ma], bp[k]);
   } else {
-    for (uint32_t k = 0; k < (1u << kb); ++k) Ops::fma(acc, ap[k << ma], bp[k]);
+    for (uint32_t k = 1; k < (1u << kb); ++k) Ops::fma(acc, ap[k << ma], bp[k]);
   }
+  Ops::finish(acc);
   if (st.flags & STEP_ROOT) {
     kahan_add(sr, cr, Ops::re(acc));
     kahan_add(si, ci, Ops::im(acc));
