@@ -1109,7 +1109,7 @@ qtn_status qtn_plan_describe(const qtn_plan_t* plan, char* buf, size_t cap, size
     o << "],\"pro_arena_elems\":" << pg.pro_arena_elems << ",\"macs_prologue\":" << pg.macs_prologue;
     o << ",\"levels\":[";
     for (size_t i = 0; i < pg.levels.size(); ++i)
-      o << (i ? "," : "") << "[" << pg.levels[i].first << "," << pg.levels[i].count << "," << pg.levels[i].outputs
+      o << (i ? "," : "") << "[" << pg.levels[i].first << "," << pg.levels[i].count << "," << pg.levels[i].units
         << "]";
     o << "],\"out_start\":[";
     for (size_t i = 0; i < pg.out_start.size(); ++i) o << (i ? "," : "") << pg.out_start[i];

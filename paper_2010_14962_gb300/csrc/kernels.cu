@@ -656,36 +656,50 @@ struct LevelParams {
   uint32_t arena_stride;
 };
 
-// Output o of step st for one item: C[pos(o)] = sum_k A[..k..] B[..k..]
-// (canonical form of the step), or the root's value added to the sums.
+// One unit of step st for one item: outputs o0 .. o0 + u - 1 (u = 4, or
+// 2^rc if smaller), C[pos(o)] = sum_k A[..k..] B[..k..] in the step's
+// canonical form, or the root's values added to the sums.  o0 is a multiple
+// of u, so pos(o0 + r) = pos(o0) + the weights of r's two low bits.
 template <class V, int K, class Ops>
-__device__ __forceinline__ void level_output(const DevStep& st, uint32_t o, const V* __restrict__ A,
-                                             const V* __restrict__ B, V* __restrict__ C, double& sr, double& cr,
-                                             double& si, double& ci) {
+__device__ __forceinline__ void level_unit(const DevStep& st, uint32_t o0, uint32_t u, const V* __restrict__ A,
+                                           const V* __restrict__ B, V* __restrict__ C, double& sr, double& cr,
+                                           double& si, double& ci) {
   const int ma = st.ma, nb = st.nb, kb = st.kb;
-  const uint32_t m = o & ((1u << ma) - 1u), n = (o >> ma) & ((1u << nb) - 1u), b = o >> (ma + nb);
-  const V* ap = A + m + (b << (ma + kb));
-  const V* bp = B + (n << kb) + (b << (kb + nb));
-  V acc = Ops::mul(ap[0], bp[0]);
-  if (K > 0) {
-#pragma unroll
-    for (int k = 1; k < K; ++k) Ops::fma(acc, ap[k << ma], bp[k]);
-  } else {
-    for (uint32_t k = 1; k < (1u << kb); ++k) Ops::fma(acc, ap[k << ma], bp[k]);
+  const bool root = st.flags & STEP_ROOT;
+  uint32_t pos0 = 0, w0 = 0, w1 = 0;
+  if (!root) {
+    for (uint32_t x = o0; x; x &= x - 1u) pos0 += st.w[__ffs(x) - 1];
+    w0 = st.w[0];
+    w1 = st.w[1];
   }
-  Ops::finish(acc);
-  if (st.flags & STEP_ROOT) {
-    kahan_add(sr, cr, Ops::re(acc));
-    kahan_add(si, ci, Ops::im(acc));
-  } else {
-    uint32_t pos = 0;
-    for (uint32_t x = o; x; x &= x - 1u) pos += st.w[__ffs(x) - 1];
-    C[pos] = acc;
+  const uint32_t mmask = (1u << ma) - 1u, nmask = (1u << nb) - 1u;
+#pragma unroll
+  for (uint32_t r = 0; r < (uint32_t)kLevelUnit; ++r) {
+    if (r < u) {
+      const uint32_t o = o0 + r;
+      const uint32_t m = o & mmask, n = (o >> ma) & nmask, b = o >> (ma + nb);
+      const V* ap = A + m + (b << (ma + kb));
+      const V* bp = B + (n << kb) + (b << (kb + nb));
+      V acc = Ops::mul(ap[0], bp[0]);
+      if (K > 0) {
+#pragma unroll
+        for (int k = 1; k < K; ++k) Ops::fma(acc, ap[k << ma], bp[k]);
+      } else {
+        for (uint32_t k = 1; k < (1u << kb); ++k) Ops::fma(acc, ap[k << ma], bp[k]);
+      }
+      Ops::finish(acc);
+      if (root) {
+        kahan_add(sr, cr, Ops::re(acc));
+        kahan_add(si, ci, Ops::im(acc));
+      } else {
+        C[pos0 + ((r & 1u) ? w0 : 0u) + ((r & 2u) ? w1 : 0u)] = acc;
+      }
+    }
   }
 }
 
 // Level executor: a block takes 2^log2_items consecutive work items at a
-// time.  For each level the outputs of all its merges, for all those items,
+// time.  For each level the units of all its merges, for all those items,
 // form one flat range (item index fastest) that the threads stride over;
 // one barrier ends the level.  Item arenas are `arena_stride` elements apart
 // (an odd stride, so the items of one warp hit different banks).
@@ -714,22 +728,26 @@ __global__ void __launch_bounds__(1024) level_exec_kernel(ExecParams P, LevelPar
              (size_t)P.leaf_elems * sizeof(V));
   __syncthreads();
 
+  auto units_of = [&](int j) -> uint32_t {
+    const int rc = s_steps[j].ma + s_steps[j].nb + s_steps[j].bb;
+    return 1u << (rc > kLevelUnitLog2 ? rc - kLevelUnitLog2 : 0);
+  };
   double sr = 0.0, si = 0.0, cr = 0.0, ci = 0.0;
   const uint64_t S = P.slice_hi - P.slice_lo;
   for (uint64_t i0 = (uint64_t)bx * I; i0 < S; i0 += (uint64_t)P.blocks_per_x * I) {
     const uint32_t nI = (uint32_t)((S - i0) < I ? (S - i0) : I);
     for (int l = 0; l < LP.n_levels; ++l) {
       const DevLevel lv = s_levels[l];
-      const uint32_t total = lv.outputs << log2I;
+      const uint32_t total = lv.units << log2I;
       int j = lv.first;
       uint32_t jbeg = s_out[j];
-      uint32_t jend = jbeg + (1u << (s_steps[j].ma + s_steps[j].nb + s_steps[j].bb));
+      uint32_t jend = jbeg + units_of(j);
       for (uint32_t f = threadIdx.x; f < total; f += T) {
-        const uint32_t item = f & (I - 1u), of = f >> log2I;
-        while (of >= jend) {  // steps of the level in order; of < lv.outputs
+        const uint32_t item = f & (I - 1u), uf = f >> log2I;
+        while (uf >= jend) {  // steps of the level in order; uf < lv.units
           ++j;
           jbeg = s_out[j];
-          jend = jbeg + (1u << (s_steps[j].ma + s_steps[j].nb + s_steps[j].bb));
+          jend = jbeg + units_of(j);
         }
         if (item >= nI) continue;
         const DevStep& st = s_steps[j];
@@ -738,13 +756,16 @@ __global__ void __launch_bounds__(1024) level_exec_kernel(ExecParams P, LevelPar
         const V* A = (st.flags & STEP_A_LEAF) ? s_lt + leaf_offset(s_leaves[st.a], s) : arena + st.a;
         const V* B = (st.flags & STEP_B_LEAF) ? s_lt + leaf_offset(s_leaves[st.b], s) : arena + st.b;
         V* C = arena + st.c;
-        const uint32_t o = of - jbeg;
+        const int rc = st.ma + st.nb + st.bb;
+        const uint32_t ulog = rc < kLevelUnitLog2 ? (uint32_t)rc : (uint32_t)kLevelUnitLog2;
+        const uint32_t o0 = (uf - jbeg) << ulog;
+        const uint32_t u = 1u << ulog;
         switch (st.kb) {
-          case 0: level_output<V, 1, Ops>(st, o, A, B, C, sr, cr, si, ci); break;
-          case 1: level_output<V, 2, Ops>(st, o, A, B, C, sr, cr, si, ci); break;
-          case 2: level_output<V, 4, Ops>(st, o, A, B, C, sr, cr, si, ci); break;
-          case 3: level_output<V, 8, Ops>(st, o, A, B, C, sr, cr, si, ci); break;
-          default: level_output<V, 0, Ops>(st, o, A, B, C, sr, cr, si, ci); break;
+          case 0: level_unit<V, 1, Ops>(st, o0, u, A, B, C, sr, cr, si, ci); break;
+          case 1: level_unit<V, 2, Ops>(st, o0, u, A, B, C, sr, cr, si, ci); break;
+          case 2: level_unit<V, 4, Ops>(st, o0, u, A, B, C, sr, cr, si, ci); break;
+          case 3: level_unit<V, 8, Ops>(st, o0, u, A, B, C, sr, cr, si, ci); break;
+          default: level_unit<V, 0, Ops>(st, o0, u, A, B, C, sr, cr, si, ci); break;
         }
       }
       __syncthreads();  // also orders the last level's arena reads before s_red's stores

@@ -389,16 +389,17 @@ std::string compile_program(const Network& net, const Plan& plan_in, const Progr
     pg.out_start.assign(pg.steps.size(), 0);
     for (size_t i = 0; i < pg.steps.size(); ++i) {
       const DevStep& st = pg.steps[i];
-      const uint32_t size = 1u << (st.ma + st.nb + st.bb);
+      const int rc = st.ma + st.nb + st.bb;
+      const uint32_t units = 1u << std::max(0, rc - kLevelUnitLog2);
       if (i == 0 || level_of[item_order[i]] != level_of[item_order[i - 1]]) {
         if (pg.levels.size() >= 0xffff) return "too many levels";
         pg.levels.push_back(DevLevel{(uint16_t)i, 0, 0});
       }
       DevLevel& lv = pg.levels.back();
-      // Executors index (output, item) pairs of a level in 32 bits, <= 32 items.
-      if ((uint64_t)lv.outputs + size > (1ull << 26)) return "level too large";
-      pg.out_start[i] = lv.outputs;
-      lv.outputs += size;
+      // Executors index (unit, item) pairs of a level in 32 bits, <= 32 items.
+      if ((uint64_t)lv.units + units > (1ull << 26)) return "level too large";
+      pg.out_start[i] = lv.units;
+      lv.units += units;
       ++lv.count;
     }
   }

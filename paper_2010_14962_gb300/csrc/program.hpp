@@ -81,10 +81,14 @@ struct DevStep {
 static_assert(sizeof(DevStep) == 52, "DevStep layout");
 
 // One level of a level-ordered program: steps [first, first + count), whose
-// outputs (2^rc each, in step order) form one flat range of `outputs`.
+// output units (in step order) form one flat range of `units`.  A unit is
+// kLevelUnit consecutive outputs of a step (all of them if it has fewer), so
+// a step of rank rc has max(1, 2^rc / kLevelUnit) units.
+constexpr int kLevelUnitLog2 = 2;
+constexpr int kLevelUnit = 1 << kLevelUnitLog2;
 struct DevLevel {
   uint16_t first, count;
-  uint32_t outputs;
+  uint32_t units;
 };
 static_assert(sizeof(DevLevel) == 8, "DevLevel layout");
 
@@ -106,7 +110,7 @@ struct Program {
   std::vector<DevLeaf> leaves;
   std::vector<DevStep> steps;        // per work item
   std::vector<DevLevel> levels;      // level-ordered programs only
-  std::vector<uint32_t> out_start;   // per step: first output in its level's range
+  std::vector<uint32_t> out_start;   // per step: first unit in its level's range
   std::vector<DevStep> prologue;     // once per bit string: merges that no outer class reaches
   uint32_t pro_arena_elems = 0;      // prologue arena (elements)
   double macs_prologue = 0;          // per bit string
