@@ -1109,8 +1109,8 @@ qtn_status qtn_plan_describe(const qtn_plan_t* plan, char* buf, size_t cap, size
     o << "],\"pro_arena_elems\":" << pg.pro_arena_elems << ",\"macs_prologue\":" << pg.macs_prologue;
     o << ",\"levels\":[";
     for (size_t i = 0; i < pg.levels.size(); ++i)
-      o << (i ? "," : "") << "[" << pg.levels[i].first << "," << pg.levels[i].count << "," << pg.levels[i].units
-        << "]";
+      o << (i ? "," : "") << "[" << pg.levels[i].first << "," << pg.levels[i].count << "," << pg.levels[i].units[0]
+        << "," << pg.levels[i].units[1] << "]";
     o << "],\"out_start\":[";
     for (size_t i = 0; i < pg.out_start.size(); ++i) o << (i ? "," : "") << pg.out_start[i];
     o << "]";

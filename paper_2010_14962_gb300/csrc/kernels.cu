@@ -638,7 +638,7 @@ __host__ __device__ inline LevelLayout level_layout(int n_steps, int n_levels, i
                                                     uint32_t stride, int items, int elem_bytes, int threads) {
   LevelLayout L;
   L.out_start = align16((size_t)n_steps * sizeof(DevStep));
-  L.levels = L.out_start + align16((size_t)n_steps * sizeof(uint32_t));
+  L.levels = L.out_start + align16((size_t)n_steps * 2 * sizeof(uint32_t));
   L.leaves = L.levels + align16((size_t)n_levels * sizeof(DevLevel));
   L.table = L.leaves + align16((size_t)n_leaves * sizeof(DevLeaf));
   L.arena = L.table + align16((size_t)leaf_elems * elem_bytes);
@@ -656,11 +656,11 @@ struct LevelParams {
   uint32_t arena_stride;
 };
 
-// One unit of step st for one item: outputs o0 .. o0 + u - 1 (u = 4, or
-// 2^rc if smaller), C[pos(o)] = sum_k A[..k..] B[..k..] in the step's
-// canonical form, or the root's values added to the sums.  o0 is a multiple
-// of u, so pos(o0 + r) = pos(o0) + the weights of r's two low bits.
-template <class V, int K, class Ops>
+// One unit of step st for one item: outputs o0 .. o0 + u - 1 (u <= UNIT),
+// C[pos(o)] = sum_k A[..k..] B[..k..] in the step's canonical form, or the
+// root's values added to the sums.  o0 is a multiple of u, so pos(o0 + r) =
+// pos(o0) + the weights of r's low bits.
+template <class V, int K, class Ops, int UNIT>
 __device__ __forceinline__ void level_unit(const DevStep& st, uint32_t o0, uint32_t u, const V* __restrict__ A,
                                            const V* __restrict__ B, V* __restrict__ C, double& sr, double& cr,
                                            double& si, double& ci) {
@@ -674,7 +674,7 @@ __device__ __forceinline__ void level_unit(const DevStep& st, uint32_t o0, uint3
   }
   const uint32_t mmask = (1u << ma) - 1u, nmask = (1u << nb) - 1u;
 #pragma unroll
-  for (uint32_t r = 0; r < (uint32_t)kLevelUnit; ++r) {
+  for (uint32_t r = 0; r < (uint32_t)UNIT; ++r) {
     if (r < u) {
       const uint32_t o = o0 + r;
       const uint32_t m = o & mmask, n = (o >> ma) & nmask, b = o >> (ma + nb);
@@ -702,9 +702,14 @@ __device__ __forceinline__ void level_unit(const DevStep& st, uint32_t o0, uint3
 // time.  For each level the units of all its merges, for all those items,
 // form one flat range (item index fastest) that the threads stride over;
 // one barrier ends the level.  Item arenas are `arena_stride` elements apart
-// (an odd stride, so the items of one warp hit different banks).
+// (an odd stride, so the items of one warp hit different banks).  Units: four
+// outputs per thread for complex64 (amortises a merge's decode over cheap
+// arithmetic), one for the 16-byte types (their arithmetic dominates, and a
+// level keeps four times more threads busy).
 template <class V, class Ops = CplxOps<V>>
 __global__ void __launch_bounds__(1024) level_exec_kernel(ExecParams P, LevelParams LP) {
+  constexpr int UL = sizeof(V) == 16 ? 0 : kLevelUnitLog2;  // log2 outputs per unit
+  constexpr int US = UL ? 1 : 0;                            // which unit table
   extern __shared__ __align__(16) unsigned char smem[];
   const int T = blockDim.x;
   const uint32_t log2I = (uint32_t)LP.log2_items;
@@ -721,7 +726,7 @@ __global__ void __launch_bounds__(1024) level_exec_kernel(ExecParams P, LevelPar
   const int xi = blockIdx.x / P.blocks_per_x;
   const int bx = blockIdx.x % P.blocks_per_x;
   copy_words(s_steps, P.steps, (size_t)P.n_steps * sizeof(DevStep));
-  copy_words(s_out, LP.out_start, (size_t)P.n_steps * sizeof(uint32_t));
+  copy_words(s_out, LP.out_start, (size_t)P.n_steps * 2 * sizeof(uint32_t));
   copy_words(s_levels, LP.levels, (size_t)LP.n_levels * sizeof(DevLevel));
   copy_words(s_leaves, P.leaves, (size_t)P.n_leaves * sizeof(DevLeaf));
   copy_words(s_lt, static_cast<const V*>(P.leaf_tables) + (size_t)xi * P.leaf_elems,
@@ -730,7 +735,7 @@ __global__ void __launch_bounds__(1024) level_exec_kernel(ExecParams P, LevelPar
 
   auto units_of = [&](int j) -> uint32_t {
     const int rc = s_steps[j].ma + s_steps[j].nb + s_steps[j].bb;
-    return 1u << (rc > kLevelUnitLog2 ? rc - kLevelUnitLog2 : 0);
+    return 1u << (rc > UL ? rc - UL : 0);
   };
   double sr = 0.0, si = 0.0, cr = 0.0, ci = 0.0;
   const uint64_t S = P.slice_hi - P.slice_lo;
@@ -738,15 +743,15 @@ __global__ void __launch_bounds__(1024) level_exec_kernel(ExecParams P, LevelPar
     const uint32_t nI = (uint32_t)((S - i0) < I ? (S - i0) : I);
     for (int l = 0; l < LP.n_levels; ++l) {
       const DevLevel lv = s_levels[l];
-      const uint32_t total = lv.units << log2I;
+      const uint32_t total = lv.units[US] << log2I;
       int j = lv.first;
-      uint32_t jbeg = s_out[j];
+      uint32_t jbeg = s_out[2 * j + US];
       uint32_t jend = jbeg + units_of(j);
       for (uint32_t f = threadIdx.x; f < total; f += T) {
         const uint32_t item = f & (I - 1u), uf = f >> log2I;
         while (uf >= jend) {  // steps of the level in order; uf < lv.units
           ++j;
-          jbeg = s_out[j];
+          jbeg = s_out[2 * j + US];
           jend = jbeg + units_of(j);
         }
         if (item >= nI) continue;
@@ -757,15 +762,15 @@ __global__ void __launch_bounds__(1024) level_exec_kernel(ExecParams P, LevelPar
         const V* B = (st.flags & STEP_B_LEAF) ? s_lt + leaf_offset(s_leaves[st.b], s) : arena + st.b;
         V* C = arena + st.c;
         const int rc = st.ma + st.nb + st.bb;
-        const uint32_t ulog = rc < kLevelUnitLog2 ? (uint32_t)rc : (uint32_t)kLevelUnitLog2;
+        const uint32_t ulog = rc < UL ? (uint32_t)rc : (uint32_t)UL;
         const uint32_t o0 = (uf - jbeg) << ulog;
         const uint32_t u = 1u << ulog;
         switch (st.kb) {
-          case 0: level_unit<V, 1, Ops>(st, o0, u, A, B, C, sr, cr, si, ci); break;
-          case 1: level_unit<V, 2, Ops>(st, o0, u, A, B, C, sr, cr, si, ci); break;
-          case 2: level_unit<V, 4, Ops>(st, o0, u, A, B, C, sr, cr, si, ci); break;
-          case 3: level_unit<V, 8, Ops>(st, o0, u, A, B, C, sr, cr, si, ci); break;
-          default: level_unit<V, 0, Ops>(st, o0, u, A, B, C, sr, cr, si, ci); break;
+          case 0: level_unit<V, 1, Ops, 1 << UL>(st, o0, u, A, B, C, sr, cr, si, ci); break;
+          case 1: level_unit<V, 2, Ops, 1 << UL>(st, o0, u, A, B, C, sr, cr, si, ci); break;
+          case 2: level_unit<V, 4, Ops, 1 << UL>(st, o0, u, A, B, C, sr, cr, si, ci); break;
+          case 3: level_unit<V, 8, Ops, 1 << UL>(st, o0, u, A, B, C, sr, cr, si, ci); break;
+          default: level_unit<V, 0, Ops, 1 << UL>(st, o0, u, A, B, C, sr, cr, si, ci); break;
         }
       }
       __syncthreads();  // also orders the last level's arena reads before s_red's stores

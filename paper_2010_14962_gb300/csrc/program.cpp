@@ -386,20 +386,22 @@ std::string compile_program(const Network& net, const Plan& plan_in, const Progr
   if (!err.empty()) return err;
   if (pg.prologue.empty()) pg.pro_arena_elems = 0;
   if (opt.levels) {
-    pg.out_start.assign(pg.steps.size(), 0);
+    pg.out_start.assign(2 * pg.steps.size(), 0);
     for (size_t i = 0; i < pg.steps.size(); ++i) {
       const DevStep& st = pg.steps[i];
       const int rc = st.ma + st.nb + st.bb;
-      const uint32_t units = 1u << std::max(0, rc - kLevelUnitLog2);
       if (i == 0 || level_of[item_order[i]] != level_of[item_order[i - 1]]) {
         if (pg.levels.size() >= 0xffff) return "too many levels";
-        pg.levels.push_back(DevLevel{(uint16_t)i, 0, 0});
+        pg.levels.push_back(DevLevel{(uint16_t)i, 0, {0, 0}});
       }
       DevLevel& lv = pg.levels.back();
-      // Executors index (unit, item) pairs of a level in 32 bits, <= 32 items.
-      if ((uint64_t)lv.units + units > (1ull << 26)) return "level too large";
-      pg.out_start[i] = lv.units;
-      lv.units += units;
+      for (int u = 0; u < 2; ++u) {
+        const uint32_t units = 1u << std::max(0, rc - (u ? kLevelUnitLog2 : 0));
+        // Executors index (unit, item) pairs of a level in 32 bits, <= 32 items.
+        if ((uint64_t)lv.units[u] + units > (1ull << 26)) return "level too large";
+        pg.out_start[2 * i + u] = lv.units[u];
+        lv.units[u] += units;
+      }
       ++lv.count;
     }
   }

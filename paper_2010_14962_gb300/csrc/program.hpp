@@ -81,16 +81,17 @@ struct DevStep {
 static_assert(sizeof(DevStep) == 52, "DevStep layout");
 
 // One level of a level-ordered program: steps [first, first + count), whose
-// output units (in step order) form one flat range of `units`.  A unit is
-// kLevelUnit consecutive outputs of a step (all of them if it has fewer), so
-// a step of rank rc has max(1, 2^rc / kLevelUnit) units.
+// output units (in step order) form one flat range.  A unit is 2^u
+// consecutive outputs of a step (all of them if it has fewer), so a step of
+// rank rc has 2^max(0, rc - u) units; tables are kept for u = 0 (one output
+// per unit) and u = 2 (four).
 constexpr int kLevelUnitLog2 = 2;
 constexpr int kLevelUnit = 1 << kLevelUnitLog2;
 struct DevLevel {
   uint16_t first, count;
-  uint32_t units;
+  uint32_t units[2];  // [0]: single outputs, [1]: units of kLevelUnit
 };
-static_assert(sizeof(DevLevel) == 8, "DevLevel layout");
+static_assert(sizeof(DevLevel) == 12, "DevLevel layout");
 
 struct ProgramOptions {
   bool levels = false;            // order item steps by tree level (see above)
@@ -110,7 +111,7 @@ struct Program {
   std::vector<DevLeaf> leaves;
   std::vector<DevStep> steps;        // per work item
   std::vector<DevLevel> levels;      // level-ordered programs only
-  std::vector<uint32_t> out_start;   // per step: first unit in its level's range
+  std::vector<uint32_t> out_start;   // per step: first unit in its level's range, 2 per step (as DevLevel::units)
   std::vector<DevStep> prologue;     // once per bit string: merges that no outer class reaches
   uint32_t pro_arena_elems = 0;      // prologue arena (elements)
   double macs_prologue = 0;          // per bit string

@@ -231,17 +231,18 @@ def test_level_programs_are_race_free(n, p, k, seed):
     assert "level/classes" in level_progs
     for name, prog in level_progs.items():
         steps, levels, out_start = prog["steps"], prog["levels"], prog["out_start"]
-        assert levels and levels[0][0] == 0 and len(out_start) == len(steps), name
+        assert levels and levels[0][0] == 0 and len(out_start) == 2 * len(steps), name
         nxt = 0
-        for li, (first, count, units) in enumerate(levels):
+        for li, (first, count, units1, units) in enumerate(levels):
             assert first == nxt and count >= 1, name
             nxt = first + count
-            acc = 0
+            acc = acc1 = 0
             reads, writes = [], []
             for j in range(first, first + count):
                 st = steps[j]
                 ma, nb, kb, bb = st["ma"], st["nb"], st["kb"], st["bb"]
-                assert out_start[j] == acc, name
+                assert out_start[2 * j] == acc1 and out_start[2 * j + 1] == acc, name
+                acc1 += 1 << (ma + nb + bb)
                 acc += 1 << max(0, ma + nb + bb - 2)  # units of 4 outputs (all, if fewer)
                 if not st["flags"] & 1:
                     reads.append((st["a"], st["a"] + (1 << (ma + kb + bb))))
@@ -251,7 +252,7 @@ def test_level_programs_are_race_free(n, p, k, seed):
                     assert li == len(levels) - 1 and count == 1, name  # the root ends the program alone
                 else:
                     writes.append((st["c"], st["c"] + (1 << (ma + nb + bb))))
-            assert acc == units, name
+            assert acc == units and acc1 == units1, name
             for lo, hi in reads + writes:
                 assert 0 <= lo < hi <= prog["arena_elems"], name
             for i, (lo, hi) in enumerate(writes):
