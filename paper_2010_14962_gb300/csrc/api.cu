@@ -155,7 +155,8 @@ struct ProgSlot {
   Program prog;
   Executor exec = Executor::Block;
   bool fp64_only = false, fp32_only = false;
-  int threads = 256;  // level executor: threads per block
+  int threads = 256;      // level executor: threads per block
+  int blocks_per_sm = 1;  // level executor: blocks sharing an SM's shared memory
   DeviceProgram dprog;
   bool uploaded = false;
   uint64_t items() const { return 1ull << prog.n_outer; }
@@ -268,6 +269,7 @@ struct qtn_plan {
     d.out_start = ost;
     d.n_levels = (int)pg.levels.size();
     d.block_threads = sl.threads;
+    d.blocks_per_sm = sl.blocks_per_sm;
     d.n = pg.n;
     d.p = pg.p;
     d.k = pg.k;
@@ -613,10 +615,12 @@ qtn_status qtn_plan(const qtn_network_t* net, const int32_t* cuts, int k, const 
   } budgets[] = {{"batched-warp/fp32/8KiB", 1024, false, true},
                  {"batched-warp/fp32/24KiB", 3 * 1024, false, true},
                  {"batched/fp32/48KiB", 6 * 1024, false, false},
+                 {"batched/fp32/96KiB", 12 * 1024, false, false},
                  {"batched/fp32/192KiB", 24 * 1024, false, false},
                  {"batched-warp/fp64/8KiB", 512, true, true},
                  {"batched-warp/fp64/24KiB", 1536, true, true},
                  {"batched/fp64/48KiB", 3 * 1024, true, false},
+                 {"batched/fp64/96KiB", 6 * 1024, true, false},
                  {"batched/fp64/192KiB", 12 * 1024, true, false}};
   for (const Budget& bd : budgets) {
     // Arena budget per item; warp executors run 8 items per block.
@@ -638,9 +642,15 @@ qtn_status qtn_plan(const qtn_network_t* net, const int32_t* cuts, int k, const 
     lv.fp32_only = !bd.fp64;
     o.levels = true;
     if (compile_program(h->net, h->plan, o, &lv.prog).empty()) {
-      ProgSlot wide_lv = lv;  // the same program on 1024 threads
+      // Two shapes: 512 threads with two blocks per SM (a block's barrier
+      // waits overlap the other's work), or one block of 1024 threads with
+      // twice the shared memory for items.
+      lv.threads = 512;
+      lv.blocks_per_sm = 2;
+      ProgSlot wide_lv = lv;
       wide_lv.name += "/t1024";
       wide_lv.threads = 1024;
+      wide_lv.blocks_per_sm = 1;
       h->slots.push_back(std::move(lv));
       h->slots.push_back(std::move(wide_lv));
     }
@@ -653,9 +663,12 @@ qtn_status qtn_plan(const qtn_network_t* net, const int32_t* cuts, int k, const 
     sl.name = "level/classes";
     sl.exec = Executor::Level;
     if (compile_program(h->net, h->plan, o, &sl.prog).empty()) {
+      sl.threads = 512;
+      sl.blocks_per_sm = 2;
       ProgSlot wide_sl = sl;
       wide_sl.name += "/t1024";
       wide_sl.threads = 1024;
+      wide_sl.blocks_per_sm = 1;
       h->slots.push_back(std::move(sl));
       h->slots.push_back(std::move(wide_sl));
     }

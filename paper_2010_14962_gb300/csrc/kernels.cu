@@ -1014,17 +1014,22 @@ bool exec_shape_typed(const DeviceProgram& prog, int nx, uint64_t slices_per_x, 
     if (!shape_for_kernel(block_exec_kernel<V, true, Ops>, sh.threads, sh.smem, &occ)) return false;
     per_block_items = (uint64_t)(sh.threads / 32);
   } else if (prog.exec == Executor::Level) {
-    // The most items (power of two, <= 32) whose arenas fit on chip.
+    // The most items (power of two, <= 32) whose arenas fit in the block's
+    // share of the SM's shared memory (1 KiB per block is the system's).
     sh.threads = prog.block_threads;
     sh.arena_stride = prog.arena_elems | 1u;
+    int per_sm = 0;
+    cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    const int bps = prog.blocks_per_sm > 1 ? prog.blocks_per_sm : 1;
+    const size_t cap = std::min<size_t>((size_t)max_optin, (size_t)per_sm / bps - 1024);
     int lg = 5;
     LevelLayout L;
     for (;; --lg) {
       L = level_layout(prog.n_steps, prog.n_levels, prog.n_leaves, prog.leaf_elems, sh.arena_stride, 1 << lg,
                        elem_bytes, sh.threads);
-      if (L.total <= (size_t)max_optin || lg == 0) break;
+      if (L.total <= cap || lg == 0) break;
     }
-    if (L.total > (size_t)max_optin) return false;
+    if (L.total > cap) return false;
     sh.log2_items = lg;
     sh.smem = L.total;
     if (!shape_for_kernel(level_exec_kernel<V, Ops>, sh.threads, sh.smem, &occ)) return false;

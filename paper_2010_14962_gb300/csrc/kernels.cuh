@@ -50,7 +50,8 @@ struct DeviceProgram {
   const DevLevel* levels = nullptr;
   const uint32_t* out_start = nullptr;
   int n_levels = 0;
-  int block_threads = 256;  // threads per block (256 or 1024)
+  int block_threads = 256;  // threads per block (512 or 1024)
+  int blocks_per_sm = 1;    // shared memory is sized for this many blocks per SM
 };
 
 // One launch sequence: leaf tables for nx bit strings, the slice range
