@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <initializer_list>
 #include <map>
 #include <mutex>
 #include <new>
@@ -933,32 +934,69 @@ qtn_status qtn_contract_batch(const qtn_plan_t* const* plans, const uint8_t* con
   }
   const Arith arith = arith_of(prec);
   const size_t elem = (size_t)arith_elem_bytes(arith);
-  // Each job runs its plan's batched program (48 KiB budget) or, if the plan
-  // has none, its per-class block program, on the block executor.
+  // Each job runs its plan's level program of the 48 KiB budget (else its
+  // per-class level program) on the multi-job level executor, with as many
+  // items per block as fit; if some job has no level program that fits, all
+  // jobs run their batched (else per-class) block programs instead.
   struct JobHost {
     int job;
     qtn_plan_t* plan;
     int slot;
     double cost;
     uint64_t items;
+    int log2_items;
+  };
+  int max_optin = 0;
+  {
+    int dev = 0;
+    QTN_CUDA(cudaGetDevice(&dev));
+    QTN_CUDA(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  }
+  auto find_slot = [](const qtn_plan_t* plan, std::initializer_list<const char*> names) {
+    for (const char* nm : names)
+      for (int k = 1; k < (int)plan->slots.size(); ++k)
+        if (plan->slots[k].name == nm) return k;
+    return -1;
   };
   std::vector<JobHost> jh(njobs);
+  bool level = true;
+  for (int j = 0; j < njobs && level; ++j) {
+    const qtn_plan_t* plan = plans[j];
+    const int si = find_slot(plan, {wide(prec) ? "level/fp64/48KiB" : "level/fp32/48KiB", "level/classes"});
+    if (si < 0) {
+      level = false;
+      break;
+    }
+    const Program& pg = plan->slots[si].prog;
+    int lg = 5;
+    for (; lg >= 0; --lg)
+      if (level_smem_bytes((int)pg.steps.size(), (int)pg.levels.size(), (int)pg.leaves.size(), pg.leaf_elems,
+                           pg.arena_elems | 1u, 1 << lg, arith, kMultiLevelThreads) <= (size_t)max_optin)
+        break;
+    if (lg < 0) {
+      level = false;
+      break;
+    }
+    jh[j] = JobHost{j, const_cast<qtn_plan_t*>(plan), si, std::ldexp(pg.macs_per_item, pg.n_outer),
+                    1ull << pg.n_outer, lg};
+  }
+  if (!level) {
+    for (int j = 0; j < njobs; ++j) {
+      const qtn_plan_t* plan = plans[j];
+      const int si = find_slot(plan, {wide(prec) ? "batched/fp64/48KiB" : "batched/fp32/48KiB", "block/classes"});
+      if (si < 0) return fail(QTN_ERR_UNSUPPORTED, "a plan of the batch has no block-executor program");
+      const Program& pg = plan->slots[si].prog;
+      jh[j] = JobHost{j, const_cast<qtn_plan_t*>(plan), si, std::ldexp(pg.macs_per_item, pg.n_outer),
+                      1ull << pg.n_outer, 0};
+    }
+  }
   for (int j = 0; j < njobs; ++j) {
-    qtn_plan_t* plan = const_cast<qtn_plan_t*>(plans[j]);
+    qtn_plan_t* plan = jh[j].plan;
     std::lock_guard<std::mutex> lk(plan->mu);
     qtn_status st = plan->ensure_device();
     if (st != QTN_OK) return st;
-    const std::string want = wide(prec) ? "batched/fp64/48KiB" : "batched/fp32/48KiB";
-    int si = -1;
-    for (int k = 1; k < (int)plan->slots.size() && si < 0; ++k)
-      if (plan->slots[k].name == want) si = k;
-    for (int k = 1; k < (int)plan->slots.size() && si < 0; ++k)
-      if (plan->slots[k].name == "block/classes") si = k;
-    if (si < 0) return fail(QTN_ERR_UNSUPPORTED, "a plan of the batch has no block-executor program");
-    st = plan->upload(plan->slots[si]);
+    st = plan->upload(plan->slots[jh[j].slot]);
     if (st != QTN_OK) return st;
-    const Program& pg = plan->slots[si].prog;
-    jh[j] = JobHost{j, plan, si, std::ldexp(pg.macs_per_item, pg.n_outer), 1ull << pg.n_outer};
   }
   // Jobs by descending cost; chunks of about total / (8 x 304) items.
   std::vector<int> order(njobs);
@@ -978,16 +1016,22 @@ qtn_status qtn_contract_batch(const qtn_plan_t* const* plans, const uint8_t* con
     lt_bytes += ((size_t)pg.leaf_elems * elem + 255) & ~(size_t)255;
     x_off[j] = x_bytes;
     x_bytes += ((size_t)jh[j].plan->net.n + 15) & ~(size_t)15;
-    exec_smem = std::max(exec_smem, block_smem_bytes((int)pg.steps.size(), (int)pg.leaves.size(), pg.leaf_elems,
-                                                     pg.arena_elems, arith, 256));
+    exec_smem = std::max(exec_smem, level ? level_smem_bytes((int)pg.steps.size(), (int)pg.levels.size(),
+                                                             (int)pg.leaves.size(), pg.leaf_elems,
+                                                             pg.arena_elems | 1u, 1 << jh[j].log2_items, arith,
+                                                             kMultiLevelThreads)
+                                          : block_smem_bytes((int)pg.steps.size(), (int)pg.leaves.size(),
+                                                             pg.leaf_elems, pg.arena_elems, arith, 256));
     if (!pg.prologue.empty())
       pro_smem = std::max(pro_smem, block_smem_bytes((int)pg.prologue.size(), (int)pg.leaves.size(), pg.leaf_elems,
                                                      pg.pro_arena_elems, arith, 256));
   }
   for (int oj : order) {
     jobs[oj].first_chunk = (uint32_t)chunks.size();
-    for (uint64_t lo = 0; lo < jh[oj].items; lo += chunk_items)
-      chunks.push_back(ChunkDesc{(uint32_t)oj, 0u, lo, std::min(jh[oj].items, lo + chunk_items)});
+    const uint64_t I = 1ull << jh[oj].log2_items;
+    const uint64_t step = (chunk_items + I - 1) / I * I;  // whole item groups per chunk
+    for (uint64_t lo = 0; lo < jh[oj].items; lo += step)
+      chunks.push_back(ChunkDesc{(uint32_t)oj, 0u, lo, std::min(jh[oj].items, lo + step)});
     jobs[oj].n_chunks = (uint32_t)chunks.size() - jobs[oj].first_chunk;
   }
   {
@@ -1032,6 +1076,11 @@ qtn_status qtn_contract_batch(const qtn_plan_t* const* plans, const uint8_t* con
     J.leaf_start = total_leaves;
     total_leaves += (uint32_t)d.n_leaves;
     J.scale = jh[j].plan->scale();
+    J.levels = d.levels;
+    J.out_start = d.out_start;
+    J.n_levels = d.n_levels;
+    J.log2_items = jh[j].log2_items;
+    J.arena_stride = d.arena_elems | 1u;
     std::memcpy(W.h_x + x_off[j], xs[j], (size_t)J.n);
   }
   std::memcpy(W.h_jobs, jobs.data(), sizeof(JobDesc) * njobs);
@@ -1045,7 +1094,7 @@ qtn_status qtn_contract_batch(const qtn_plan_t* const* plans, const uint8_t* con
   }
   QTN_CUDA(cudaEventRecord(W.ev0, stream));
   cudaError_t le = launch_multi(arith, W.d_jobs, njobs, total_leaves, W.d_chunks, (uint32_t)chunks.size(), W.d_counter,
-                                W.d_partials, W.d_out, exec_smem, pro_smem, stream);
+                                W.d_partials, W.d_out, exec_smem, pro_smem, level, stream);
   if (le != cudaSuccess) return cuda_fail(le, "launch_multi");
   QTN_CUDA(cudaEventRecord(W.ev1, stream));
   W.timed = true;

@@ -698,18 +698,69 @@ __device__ __forceinline__ void level_unit(const DevStep& st, uint32_t o0, uint3
   }
 }
 
-// Level executor: a block takes 2^log2_items consecutive work items at a
-// time.  For each level the units of all its merges, for all those items,
-// form one flat range (item index fastest) that the threads stride over;
-// one barrier ends the level.  Item arenas are `arena_stride` elements apart
-// (an odd stride, so the items of one warp hit different banks).  Units: four
-// outputs per thread for complex64 (amortises a merge's decode over cheap
-// arithmetic), one for the 16-byte types (their arithmetic dominates, and a
-// level keeps four times more threads busy).
-template <class V, class Ops = CplxOps<V>>
-__global__ void __launch_bounds__(1024) level_exec_kernel(ExecParams P, LevelParams LP) {
+// Units per step for the level executor's unit size 2^UL.
+template <int UL>
+__device__ __forceinline__ uint32_t level_units(const DevStep& st) {
+  const int rc = st.ma + st.nb + st.bb;
+  return 1u << (rc > UL ? rc - UL : 0);
+}
+
+// All levels of one group of nI <= 2^log2I consecutive work items (global
+// index s0 + item).  For each level the units of all its merges, for all
+// those items, form one flat range (item index fastest) that the threads
+// stride over; one barrier ends the level.  Item arenas are `stride`
+// elements apart (an odd stride, so the items of one warp hit different
+// banks).  Units: four outputs per thread for complex64 (amortises a merge's
+// decode over cheap arithmetic), one for the 16-byte types (their arithmetic
+// dominates, and a level keeps four times more threads busy).
+template <class V, class Ops>
+__device__ __forceinline__ void level_run(const DevStep* s_steps, const uint32_t* s_out, const DevLevel* s_levels,
+                                          int n_levels, const DevLeaf* s_leaves, const V* s_lt, V* s_arena,
+                                          uint32_t stride, uint32_t log2I, uint64_t s0, uint32_t nI, double& sr,
+                                          double& cr, double& si, double& ci) {
   constexpr int UL = sizeof(V) == 16 ? 0 : kLevelUnitLog2;  // log2 outputs per unit
   constexpr int US = UL ? 1 : 0;                            // which unit table
+  const uint32_t I = 1u << log2I;
+  for (int l = 0; l < n_levels; ++l) {
+    const DevLevel lv = s_levels[l];
+    const uint32_t total = lv.units[US] << log2I;
+    int j = lv.first;
+    uint32_t jbeg = s_out[2 * j + US];
+    uint32_t jend = jbeg + level_units<UL>(s_steps[j]);
+    for (uint32_t f = threadIdx.x; f < total; f += blockDim.x) {
+      const uint32_t item = f & (I - 1u), uf = f >> log2I;
+      while (uf >= jend) {  // steps of the level in order; uf < lv.units
+        ++j;
+        jbeg = s_out[2 * j + US];
+        jend = jbeg + level_units<UL>(s_steps[j]);
+      }
+      if (item >= nI) continue;
+      const DevStep& st = s_steps[j];
+      const uint64_t s = s0 + item;
+      V* arena = s_arena + (size_t)item * stride;
+      const V* A = (st.flags & STEP_A_LEAF) ? s_lt + leaf_offset(s_leaves[st.a], s) : arena + st.a;
+      const V* B = (st.flags & STEP_B_LEAF) ? s_lt + leaf_offset(s_leaves[st.b], s) : arena + st.b;
+      V* C = arena + st.c;
+      const int rc = st.ma + st.nb + st.bb;
+      const uint32_t ulog = rc < UL ? (uint32_t)rc : (uint32_t)UL;
+      const uint32_t o0 = (uf - jbeg) << ulog;
+      const uint32_t u = 1u << ulog;
+      switch (st.kb) {
+        case 0: level_unit<V, 1, Ops, 1 << UL>(st, o0, u, A, B, C, sr, cr, si, ci); break;
+        case 1: level_unit<V, 2, Ops, 1 << UL>(st, o0, u, A, B, C, sr, cr, si, ci); break;
+        case 2: level_unit<V, 4, Ops, 1 << UL>(st, o0, u, A, B, C, sr, cr, si, ci); break;
+        case 3: level_unit<V, 8, Ops, 1 << UL>(st, o0, u, A, B, C, sr, cr, si, ci); break;
+        default: level_unit<V, 0, Ops, 1 << UL>(st, o0, u, A, B, C, sr, cr, si, ci); break;
+      }
+    }
+    __syncthreads();  // also orders the last level's arena reads before later reuse of the arena
+  }
+}
+
+// Level executor: a block takes 2^log2_items consecutive work items at a
+// time and runs them level by level (level_run).
+template <class V, class Ops = CplxOps<V>>
+__global__ void __launch_bounds__(1024) level_exec_kernel(ExecParams P, LevelParams LP) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int T = blockDim.x;
   const uint32_t log2I = (uint32_t)LP.log2_items;
@@ -733,50 +784,14 @@ __global__ void __launch_bounds__(1024) level_exec_kernel(ExecParams P, LevelPar
              (size_t)P.leaf_elems * sizeof(V));
   __syncthreads();
 
-  auto units_of = [&](int j) -> uint32_t {
-    const int rc = s_steps[j].ma + s_steps[j].nb + s_steps[j].bb;
-    return 1u << (rc > UL ? rc - UL : 0);
-  };
   double sr = 0.0, si = 0.0, cr = 0.0, ci = 0.0;
   const uint64_t S = P.slice_hi - P.slice_lo;
   for (uint64_t i0 = (uint64_t)bx * I; i0 < S; i0 += (uint64_t)P.blocks_per_x * I) {
     const uint32_t nI = (uint32_t)((S - i0) < I ? (S - i0) : I);
-    for (int l = 0; l < LP.n_levels; ++l) {
-      const DevLevel lv = s_levels[l];
-      const uint32_t total = lv.units[US] << log2I;
-      int j = lv.first;
-      uint32_t jbeg = s_out[2 * j + US];
-      uint32_t jend = jbeg + units_of(j);
-      for (uint32_t f = threadIdx.x; f < total; f += T) {
-        const uint32_t item = f & (I - 1u), uf = f >> log2I;
-        while (uf >= jend) {  // steps of the level in order; uf < lv.units
-          ++j;
-          jbeg = s_out[2 * j + US];
-          jend = jbeg + units_of(j);
-        }
-        if (item >= nI) continue;
-        const DevStep& st = s_steps[j];
-        const uint64_t s = P.slice_lo + i0 + item;
-        V* arena = s_arena + (size_t)item * LP.arena_stride;
-        const V* A = (st.flags & STEP_A_LEAF) ? s_lt + leaf_offset(s_leaves[st.a], s) : arena + st.a;
-        const V* B = (st.flags & STEP_B_LEAF) ? s_lt + leaf_offset(s_leaves[st.b], s) : arena + st.b;
-        V* C = arena + st.c;
-        const int rc = st.ma + st.nb + st.bb;
-        const uint32_t ulog = rc < UL ? (uint32_t)rc : (uint32_t)UL;
-        const uint32_t o0 = (uf - jbeg) << ulog;
-        const uint32_t u = 1u << ulog;
-        switch (st.kb) {
-          case 0: level_unit<V, 1, Ops, 1 << UL>(st, o0, u, A, B, C, sr, cr, si, ci); break;
-          case 1: level_unit<V, 2, Ops, 1 << UL>(st, o0, u, A, B, C, sr, cr, si, ci); break;
-          case 2: level_unit<V, 4, Ops, 1 << UL>(st, o0, u, A, B, C, sr, cr, si, ci); break;
-          case 3: level_unit<V, 8, Ops, 1 << UL>(st, o0, u, A, B, C, sr, cr, si, ci); break;
-          default: level_unit<V, 0, Ops, 1 << UL>(st, o0, u, A, B, C, sr, cr, si, ci); break;
-        }
-      }
-      __syncthreads();  // also orders the last level's arena reads before s_red's stores
-    }
+    level_run<V, Ops>(s_steps, s_out, s_levels, LP.n_levels, s_leaves, s_lt, s_arena, LP.arena_stride, log2I,
+                      P.slice_lo + i0, nI, sr, cr, si, ci);
   }
-  s_red[threadIdx.x] = Partial::make(sr, si, cr, ci);
+  s_red[threadIdx.x] = Partial::make(sr, si, cr, ci);  // overlays the arenas: every level is done
   tree_reduce(s_red, T);
   if (threadIdx.x == 0) P.partials[(size_t)xi * P.blocks_per_x + bx] = s_red[0];
 }
@@ -902,6 +917,60 @@ __global__ void __launch_bounds__(256) multi_exec_kernel(const JobDesc* __restri
       run_item<V, Ops, false>(s_steps, J.n_steps, s_leaves, s_lt, s_arena, it, threadIdx.x, T, log2G, sr, cr, si,
                               ci, nullptr);
     s_red[threadIdx.x] = Partial::make(sr, si, cr, ci);
+    tree_reduce(s_red, T);
+    if (threadIdx.x == 0) chunk_partials[c] = s_red[0];
+  }
+}
+
+// The multi-job executor on level programs: chunks are (job, item range)
+// with the range a multiple of the job's items per block (the last one may
+// be short); the job's program, level table and leaf table are loaded into
+// shared memory when the job changes.
+template <class V, class Ops = CplxOps<V>>
+__global__ void __launch_bounds__(1024) multi_level_kernel(const JobDesc* __restrict__ jobs,
+                                                           const ChunkDesc* __restrict__ chunks, uint32_t n_chunks,
+                                                           unsigned* __restrict__ counter,
+                                                           Partial* __restrict__ chunk_partials) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ unsigned s_c;
+  __shared__ int s_job;
+  const int T = blockDim.x;
+  if (threadIdx.x == 0) s_job = -1;
+  for (;;) {
+    __syncthreads();  // the previous chunk is done with shared memory
+    if (threadIdx.x == 0) s_c = atomicAdd(counter, 1u);
+    __syncthreads();
+    const unsigned c = s_c;
+    if (c >= n_chunks) break;
+    const ChunkDesc ch = chunks[c];
+    const JobDesc& J = jobs[ch.job];
+    const uint32_t log2I = (uint32_t)J.log2_items;
+    const uint32_t I = 1u << log2I;
+    const LevelLayout lay = level_layout(J.n_steps, J.n_levels, J.n_leaves, J.leaf_elems, J.arena_stride, (int)I,
+                                         (int)sizeof(V), T);
+    DevStep* s_steps = reinterpret_cast<DevStep*>(smem);
+    uint32_t* s_out = reinterpret_cast<uint32_t*>(smem + lay.out_start);
+    DevLevel* s_levels = reinterpret_cast<DevLevel*>(smem + lay.levels);
+    DevLeaf* s_leaves = reinterpret_cast<DevLeaf*>(smem + lay.leaves);
+    V* s_lt = reinterpret_cast<V*>(smem + lay.table);
+    V* s_arena = reinterpret_cast<V*>(smem + lay.arena);
+    Partial* s_red = reinterpret_cast<Partial*>(smem + lay.red);
+    if (s_job != (int)ch.job) {
+      copy_words(s_steps, J.steps, (size_t)J.n_steps * sizeof(DevStep));
+      copy_words(s_out, J.out_start, (size_t)J.n_steps * 2 * sizeof(uint32_t));
+      copy_words(s_levels, J.levels, (size_t)J.n_levels * sizeof(DevLevel));
+      copy_words(s_leaves, J.leaves, (size_t)J.n_leaves * sizeof(DevLeaf));
+      copy_words(s_lt, J.leaf_table, (size_t)J.leaf_elems * sizeof(V));
+      __syncthreads();
+      if (threadIdx.x == 0) s_job = (int)ch.job;
+    }
+    double sr = 0.0, si = 0.0, cr = 0.0, ci = 0.0;
+    for (uint64_t i0 = ch.lo; i0 < ch.hi; i0 += I) {
+      const uint32_t nI = (uint32_t)((ch.hi - i0) < I ? (ch.hi - i0) : I);
+      level_run<V, Ops>(s_steps, s_out, s_levels, J.n_levels, s_leaves, s_lt, s_arena, J.arena_stride, log2I, i0,
+                        nI, sr, cr, si, ci);
+    }
+    s_red[threadIdx.x] = Partial::make(sr, si, cr, ci);  // overlays the arenas
     tree_reduce(s_red, T);
     if (threadIdx.x == 0) chunk_partials[c] = s_red[0];
   }
@@ -1124,7 +1193,7 @@ cudaError_t launch_typed(const DeviceProgram& prog, const uint8_t* d_x, int nx, 
 template <class V, class Ops>
 cudaError_t launch_multi_typed(const JobDesc* d_jobs, int njobs, uint32_t total_leaves, const ChunkDesc* d_chunks,
                                uint32_t n_chunks, unsigned* d_counter, Partial* d_chunk_partials, double2* d_out,
-                               size_t exec_smem, size_t pro_smem, cudaStream_t stream) {
+                               size_t exec_smem, size_t pro_smem, bool level, cudaStream_t stream) {
   int dev = 0, sms = 0, max_optin = 0, occ = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1134,13 +1203,20 @@ cudaError_t launch_multi_typed(const JobDesc* d_jobs, int njobs, uint32_t total_
   if ((e = cudaFuncSetAttribute(multi_prologue_kernel<V, Ops>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)pro_smem)) != cudaSuccess)
     return e;
-  if (!shape_for_kernel(multi_exec_kernel<V, Ops>, 256, exec_smem, &occ)) return cudaErrorInvalidConfiguration;
+  const int threads = level ? kMultiLevelThreads : 256;
+  if (level ? !shape_for_kernel(multi_level_kernel<V, Ops>, threads, exec_smem, &occ)
+            : !shape_for_kernel(multi_exec_kernel<V, Ops>, threads, exec_smem, &occ))
+    return cudaErrorInvalidConfiguration;
   if ((e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned), stream)) != cudaSuccess) return e;
   multi_leaf_kernel<V><<<total_leaves, 32, 0, stream>>>(d_jobs, njobs);
   multi_prologue_kernel<V, Ops><<<njobs, 256, pro_smem, stream>>>(d_jobs);
   const unsigned grid = (unsigned)std::min<uint64_t>((uint64_t)sms * occ, n_chunks);
-  multi_exec_kernel<V, Ops><<<grid, 256, exec_smem, stream>>>(d_jobs, d_chunks, n_chunks, d_counter,
-                                                               d_chunk_partials);
+  if (level)
+    multi_level_kernel<V, Ops><<<grid, threads, exec_smem, stream>>>(d_jobs, d_chunks, n_chunks, d_counter,
+                                                                     d_chunk_partials);
+  else
+    multi_exec_kernel<V, Ops><<<grid, threads, exec_smem, stream>>>(d_jobs, d_chunks, n_chunks, d_counter,
+                                                                    d_chunk_partials);
   multi_finalize_kernel<<<njobs, 128, 0, stream>>>(d_jobs, d_chunk_partials, d_out);
   return cudaGetLastError();
 }
@@ -1183,13 +1259,19 @@ size_t block_smem_bytes(int n_steps, int n_leaves, uint32_t leaf_elems, uint32_t
   return smem_layout(n_steps, n_leaves, leaf_elems, arena_elems, arith_elem_bytes(a), threads, false).total;
 }
 
+size_t level_smem_bytes(int n_steps, int n_levels, int n_leaves, uint32_t leaf_elems, uint32_t arena_stride,
+                        int items, Arith a, int threads) {
+  return level_layout(n_steps, n_levels, n_leaves, leaf_elems, arena_stride, items, arith_elem_bytes(a), threads)
+      .total;
+}
+
 cudaError_t launch_multi(Arith a, const JobDesc* d_jobs, int njobs, uint32_t total_leaves, const ChunkDesc* d_chunks,
                          uint32_t n_chunks, unsigned* d_counter, Partial* d_chunk_partials, double2* d_out,
-                         size_t exec_smem, size_t pro_smem, cudaStream_t stream) {
+                         size_t exec_smem, size_t pro_smem, bool level, cudaStream_t stream) {
   if (njobs <= 0) return cudaSuccess;
 #define QTN_MULTI_CALL(V, O)                                                                                  \
   launch_multi_typed<V, O>(d_jobs, njobs, total_leaves, d_chunks, n_chunks, d_counter, d_chunk_partials, d_out, \
-                           exec_smem, pro_smem, stream)
+                           exec_smem, pro_smem, level, stream)
   QTN_ARITH_SWITCH(a, QTN_MULTI_CALL)
 #undef QTN_MULTI_CALL
   return cudaErrorInvalidValue;

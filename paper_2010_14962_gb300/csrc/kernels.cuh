@@ -105,6 +105,12 @@ struct JobDesc {
   uint32_t leaf_start;   // first block of this job in the leaf launch
   uint32_t first_chunk, n_chunks;
   double scale;
+  // Level programs (multi_level_kernel) only.
+  const DevLevel* levels;
+  const uint32_t* out_start;
+  int n_levels;
+  int log2_items;          // items per block = 2^log2_items; chunks are multiples of it
+  uint32_t arena_stride;   // elements between item arenas
 };
 // A range of work items of one job.
 struct ChunkDesc {
@@ -114,13 +120,20 @@ struct ChunkDesc {
 
 // Shared memory of the block executor for a program.
 size_t block_smem_bytes(int n_steps, int n_leaves, uint32_t leaf_elems, uint32_t arena_elems, Arith a, int threads);
+// Shared memory of the level executor for a program and `items` items per block.
+size_t level_smem_bytes(int n_steps, int n_levels, int n_leaves, uint32_t leaf_elems, uint32_t arena_stride,
+                        int items, Arith a, int threads);
+// Threads per block of the multi-job level executor.
+constexpr int kMultiLevelThreads = 1024;
 
 // Enqueues the multi-job sequence (leaf tables, prologues, persistent
 // executor over `n_chunks` chunks, per-job finalisation into d_out[njobs]).
-// exec_smem / pro_smem: the largest shared memory any job needs.
+// exec_smem / pro_smem: the largest shared memory any job needs.  `level`:
+// every job carries a level program (multi_level_kernel, 1024 threads);
+// otherwise block programs (multi_exec_kernel, 256 threads).
 cudaError_t launch_multi(Arith a, const JobDesc* d_jobs, int njobs, uint32_t total_leaves, const ChunkDesc* d_chunks,
                          uint32_t n_chunks, unsigned* d_counter, Partial* d_chunk_partials, double2* d_out,
-                         size_t exec_smem, size_t pro_smem, cudaStream_t stream);
+                         size_t exec_smem, size_t pro_smem, bool level, cudaStream_t stream);
 
 // Largest tensor rank the lane executor accepts.
 constexpr int kLaneMaxRank = 5;

@@ -372,12 +372,15 @@ def batch_last_ms():
 
 def batch_program(plan, precision: str) -> str:
     """Name of the program a multi-plan contract_batch runs for ``plan``: its
-    48 KiB batched program of the precision's width, else its per-class block
-    program (the rule qtn_contract_batch documents)."""
+    48 KiB level program of the precision's width, else its per-class level
+    program (the rule qtn_contract_batch documents, when every job's level
+    program fits in shared memory)."""
     progs = plan.describe()["programs"]
-    wide = precision in ("fp64", "fp32x2")
-    want = "batched/fp64/48KiB" if wide else "batched/fp32/48KiB"
-    return want if want in progs else "block/classes"
+    width = "fp64" if precision in ("fp64", "fp32x2") else "fp32"
+    for name in (f"level/{width}/48KiB", "level/classes", f"batched/{width}/48KiB", "block/classes"):
+        if name in progs:
+            return name
+    raise QTNError(6, "the plan has no program for a batch")
 
 
 # ------------------------------------------------------- learned surrogate --
