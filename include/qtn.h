@@ -251,7 +251,7 @@ qtn_status qtn_plan_kernel_ms(const qtn_plan_t* plan, float* ms);
  * A small MLP predicts the exact counter's log2 total flops and log2 peak
  * bytes of cutting a set of indices (min-fill plan) from cheap features, so a
  * genetic cut search (Algorithm 1, Sec. III.B) can rank far more candidates;
- * the exact counter still judges the candidates the search keeps.  Training
+ * the exact counter still scores the candidates the search keeps.  Training
  * and inference run on the device (FP32, the library's own kernels). */
 typedef struct qtn_mlp qtn_mlp_t;
 #define QTN_SURROGATE_FEATURES 48

@@ -282,7 +282,7 @@ SurrogateSearchResult surrogate_genetic_cuts(const Network& net, int M, int T, i
                      [&](int a, int b) { return Y[(size_t)a * kSurrogateTargets] < Y[(size_t)b * kSurrogateTargets]; });
     std::vector<std::vector<int>> S(N);
     for (int i = 0; i < N; ++i) S[i] = P[idx[i]];
-    // the exact counter judges the most promising individuals
+    // the exact counter scores the most promising individuals
     for (int i = 0; i < std::min(top, N); ++i) exact_of(S[i]);
     // elitism by the exact counter: the best exact set stays first
     S[0] = res.best;

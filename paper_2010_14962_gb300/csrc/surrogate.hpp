@@ -1,7 +1,7 @@
 // Learned cost surrogate for the cut search: features of a (network, cut set)
 // pair that cost far less than planning it, training data labelled by the
 // exact counter, and a genetic search (Algorithm 1, Sec. III.B) whose fitness
-// is the surrogate's prediction, with the exact counter as the judge of the
+// is the surrogate's prediction, with the exact counter deciding among the
 // individuals it keeps.
 #pragma once
 #include <cstdint>

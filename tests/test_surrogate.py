@@ -1,4 +1,4 @@
-"""Learned cost surrogate (the benchmark spec's learned part): features, labelled data
+"""Learned cost surrogate: features, labelled data
 from the exact counter, the MLP's device kernels against a CPU float64
 reference (itself pinned by finite differences), training, and the
 surrogate-guided cut search against the search without it."""
@@ -102,7 +102,7 @@ def test_training_learns_the_counter(trained):
 def test_surrogate_search_gain(trained):
     # What the network adds to Algorithm 1: both searches start from random
     # populations (as Algorithm 1 does) and get the same wall-clock budget on
-    # n = 120, k = 22; the exact counter judges both results.
+    # n = 120, k = 22; the exact counter scores both results.
     m = trained[0]
     rows = []
     for seed in (5, 6, 7):
