@@ -190,6 +190,23 @@ qtn_status qtn_contract_amplitudes_device(const qtn_plan_t* plan, const uint8_t*
 qtn_status qtn_contract_amplitudes_noalloc(const qtn_plan_t* plan, const uint8_t* d_x, int nx,
                                            qtn_precision prec, cudaStream_t stream, double* d_out);
 
+/* Amplitudes of nx (bit string, angle set) pairs of the plan's graph: the
+ * gate tensors depend on gamma and beta (Sec. II.A) but the network's
+ * topology, cut set and elimination order (Sec. II.B, III.A) do not, so one
+ * plan serves a whole QAOA parameter scan.  Same launch as
+ * qtn_contract_amplitudes_device, with the leaf tables of bit string i built
+ * from angle set i.
+ *   d_x     : device, nx * n bytes (0/1).
+ *   d_gamma : device, nx * p doubles (angle set i at i * p).
+ *   d_beta  : device, nx * p doubles.
+ *   d_out   : device, 2 * nx doubles (scaled amplitudes).
+ * Asynchronous on `stream`; the CUDA graph is cached per (d_x, d_gamma,
+ * d_beta, d_out, nx, prec), so buffers reused across calls replay it.
+ * QTN_ERR_INVALID_ARG for NULL buffers or nx <= 0. */
+qtn_status qtn_contract_sweep_device(const qtn_plan_t* plan, const uint8_t* d_x, const double* d_gamma,
+                                     const double* d_beta, int nx, qtn_precision prec, cudaStream_t stream,
+                                     double* d_out);
+
 /* Slices [slice_lo, slice_hi) of one amplitude, e.g. to recompute the slices
  * of a lost worker (Sec. V: fault tolerance at the level of subgraphs).
  *   x         : host, n bytes.

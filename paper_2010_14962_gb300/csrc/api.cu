@@ -61,8 +61,10 @@ struct GraphKey {
   const void* out;
   int nx;
   int prec;
+  const void* gamma;  // per-bit-string angles (sweeps), or null
+  const void* beta;
   bool operator<(const GraphKey& o) const {
-    return std::tie(x, out, nx, prec) < std::tie(o.x, o.out, o.nx, o.prec);
+    return std::tie(x, out, nx, prec, gamma, beta) < std::tie(o.x, o.out, o.nx, o.prec, o.gamma, o.beta);
   }
 };
 
@@ -401,7 +403,8 @@ struct qtn_plan {
   // Enqueue the contraction of nx bit strings at d_x on `stream`: the tuned
   // executor, replayed from a CUDA graph (or launched directly with kernel
   // timing on).
-  qtn_status run_graph(const uint8_t* d_x, int nx, qtn_precision prec, double2* d_out, cudaStream_t stream) {
+  qtn_status run_graph(const uint8_t* d_x, int nx, qtn_precision prec, double2* d_out, cudaStream_t stream,
+                       const double* d_gamma = nullptr, const double* d_beta = nullptr) {
     int si = 0;
     qtn_status st = tune(prec, nx, stream, &si);
     if (st != QTN_OK) return st;
@@ -411,17 +414,18 @@ struct qtn_plan {
     if (st != QTN_OK) return st;
     if (timing) {
       cudaError_t le = launch_contraction(slots[si].dprog, arith_of(prec), d_x, nx, 0, S, buffers(), sh, scale(),
-                                          d_out, nullptr, nullptr, stream, ev0, ev1);
+                                          d_out, nullptr, nullptr, stream, ev0, ev1, d_gamma, d_beta);
       if (le != cudaSuccess) return cuda_fail(le, "launch_contraction");
       return QTN_OK;
     }
-    GraphKey key{d_x, d_out, nx, (int)prec};
+    GraphKey key{d_x, d_out, nx, (int)prec, d_gamma, d_beta};
     auto it = graphs.find(key);
     if (it == graphs.end()) {
       cudaGraph_t g;
       QTN_CUDA(cudaStreamBeginCapture(capture_stream, cudaStreamCaptureModeThreadLocal));
       cudaError_t le = launch_contraction(slots[si].dprog, arith_of(prec), d_x, nx, 0, S, buffers(), sh, scale(),
-                                          d_out, nullptr, nullptr, capture_stream);
+                                          d_out, nullptr, nullptr, capture_stream, nullptr, nullptr, d_gamma,
+                                          d_beta);
       cudaError_t ce = cudaStreamEndCapture(capture_stream, &g);
       if (le != cudaSuccess) return cuda_fail(le, "launch_contraction (capture)");
       if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
@@ -831,6 +835,18 @@ qtn_status qtn_contract_amplitudes_device(const qtn_plan_t* cplan, const uint8_t
   qtn_status st = plan->ensure_device();
   if (st != QTN_OK) return st;
   return plan->run_graph(d_x, nx, prec, reinterpret_cast<double2*>(d_out), stream);
+}
+
+qtn_status qtn_contract_sweep_device(const qtn_plan_t* cplan, const uint8_t* d_x, const double* d_gamma,
+                                     const double* d_beta, int nx, qtn_precision prec, cudaStream_t stream,
+                                     double* d_out) {
+  qtn_plan_t* plan = const_cast<qtn_plan_t*>(cplan);
+  if (!plan || !d_x || !d_gamma || !d_beta || !d_out || nx <= 0) return fail(QTN_ERR_INVALID_ARG, "bad argument");
+  if (!precision_supported(prec)) return fail(QTN_ERR_UNSUPPORTED, "precision not available on this plan's executor");
+  std::lock_guard<std::mutex> lk(plan->mu);
+  qtn_status st = plan->ensure_device();
+  if (st != QTN_OK) return st;
+  return plan->run_graph(d_x, nx, prec, reinterpret_cast<double2*>(d_out), stream, d_gamma, d_beta);
 }
 
 qtn_status qtn_contract_amplitude(const qtn_plan_t* cplan, const uint8_t* x, qtn_precision prec, cudaStream_t stream,

@@ -333,19 +333,23 @@ __device__ __forceinline__ V leaf_entry(const DevLeaf& L, int e, const int32_t* 
   return CplxOps<V>::from(re, im);
 }
 
+// Leaf tables of nx bit strings; bit string xi uses angles gamma / beta +
+// xi * angle_stride (0: one angle set for all).
 template <class V>
 __global__ void leaf_build_kernel(const DevLeaf* __restrict__ leaves, const int32_t* __restrict__ gate_q,
                                   const int8_t* __restrict__ gate_layer, const int8_t* __restrict__ gate_in_h,
                                   const int8_t* __restrict__ gate_out_kind, const double* __restrict__ gamma,
-                                  const double* __restrict__ beta, const uint8_t* __restrict__ x, int n,
-                                  uint32_t leaf_elems, int n_leaves, V* __restrict__ out) {
+                                  const double* __restrict__ beta, int angle_stride, const uint8_t* __restrict__ x,
+                                  int n, uint32_t leaf_elems, int n_leaves, V* __restrict__ out) {
   const DevLeaf L = leaves[blockIdx.x % n_leaves];
   const int xi = blockIdx.x / n_leaves;
   if (L.gate == -2) return;  // pseudo-leaf: written by the prologue kernel
   const int r = L.rank_nc + L.ncut;
+  const double* g = gamma + (size_t)xi * angle_stride;
+  const double* b = beta + (size_t)xi * angle_stride;
   for (int e = threadIdx.x; e < (1 << r); e += blockDim.x)
     out[(size_t)xi * leaf_elems + L.base + e] = leaf_entry<V>(L, e, gate_q, gate_layer, gate_in_h, gate_out_kind,
-                                                              gamma, beta, x + (size_t)xi * n);
+                                                              g, b, x + (size_t)xi * n);
 }
 
 // ------------------------------------------------------------- lane exec --
@@ -1134,10 +1138,13 @@ bool exec_shape_typed(const DeviceProgram& prog, int nx, uint64_t slices_per_x, 
 template <class V, class Ops>
 cudaError_t launch_typed(const DeviceProgram& prog, const uint8_t* d_x, int nx, uint64_t slice_lo, uint64_t slice_hi,
                          const LaunchBuffers& buf, const ExecShape& shape, double scale, double2* d_out,
-                         Partial* d_raw, double2* d_slices, cudaStream_t stream, cudaEvent_t ev0, cudaEvent_t ev1) {
+                         Partial* d_raw, double2* d_slices, cudaStream_t stream, cudaEvent_t ev0, cudaEvent_t ev1,
+                         const double* d_gamma, const double* d_beta) {
   const unsigned lgrid = (unsigned)prog.n_leaves * (unsigned)nx;
+  const bool sweep = d_gamma != nullptr;
   leaf_build_kernel<V><<<lgrid, 32, 0, stream>>>(prog.leaves, prog.gate_q, prog.gate_layer, prog.gate_in_h,
-                                                 prog.gate_out_kind, prog.gamma, prog.beta, d_x, prog.n,
+                                                 prog.gate_out_kind, sweep ? d_gamma : prog.gamma,
+                                                 sweep ? d_beta : prog.beta, sweep ? prog.p : 0, d_x, prog.n,
                                                  prog.leaf_elems, prog.n_leaves, static_cast<V*>(buf.leaf_tables));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -1246,10 +1253,12 @@ bool exec_shape(const DeviceProgram& prog, Arith a, int nx, uint64_t slices_per_
 cudaError_t launch_contraction(const DeviceProgram& prog, Arith a, const uint8_t* d_x, int nx, uint64_t slice_lo,
                                uint64_t slice_hi, const LaunchBuffers& buf, const ExecShape& shape, double scale,
                                double2* d_out, Partial* d_raw, double2* d_slices, cudaStream_t stream,
-                               cudaEvent_t ev0, cudaEvent_t ev1) {
+                               cudaEvent_t ev0, cudaEvent_t ev1, const double* d_gamma, const double* d_beta) {
   if (nx <= 0) return cudaSuccess;
-#define QTN_LAUNCH_CALL(V, O) \
-  launch_typed<V, O>(prog, d_x, nx, slice_lo, slice_hi, buf, shape, scale, d_out, d_raw, d_slices, stream, ev0, ev1)
+  if ((d_gamma == nullptr) != (d_beta == nullptr)) return cudaErrorInvalidValue;
+#define QTN_LAUNCH_CALL(V, O)                                                                                   \
+  launch_typed<V, O>(prog, d_x, nx, slice_lo, slice_hi, buf, shape, scale, d_out, d_raw, d_slices, stream, ev0, ev1, \
+                     d_gamma, d_beta)
   QTN_ARITH_SWITCH(a, QTN_LAUNCH_CALL)
 #undef QTN_LAUNCH_CALL
   return cudaErrorInvalidValue;

@@ -81,11 +81,14 @@ bool exec_shape(const DeviceProgram& prog, Arith arith, int nx, uint64_t slices_
 //   d_raw     : nx Partial (unscaled Kahan sum and compensation), may be null
 //   d_slices  : nx * (slice_hi - slice_lo) double2, may be null
 //   ev0, ev1  : optional events recorded just before / after the executor
+//   d_gamma, d_beta : optional nx * p angles (device), one set per bit
+//               string; null: the program's angles for all
 cudaError_t launch_contraction(const DeviceProgram& prog, Arith arith, const uint8_t* d_x, int nx,
                                uint64_t slice_lo, uint64_t slice_hi, const LaunchBuffers& buf,
                                const ExecShape& shape, double scale, double2* d_out, Partial* d_raw,
                                double2* d_slices, cudaStream_t stream, cudaEvent_t ev0 = nullptr,
-                               cudaEvent_t ev1 = nullptr);
+                               cudaEvent_t ev1 = nullptr, const double* d_gamma = nullptr,
+                               const double* d_beta = nullptr);
 
 // One job of a multi-job launch (device array; pointers are device pointers).
 struct JobDesc {

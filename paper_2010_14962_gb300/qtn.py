@@ -77,6 +77,7 @@ def lib():
             "qtn_contract_amplitudes_device": [vp, vp, ctypes.c_int, ctypes.c_int, vp, vp],
             "qtn_contract_amplitudes_noalloc": [vp, vp, ctypes.c_int, ctypes.c_int, vp, vp],
             "qtn_contract_slices": [vp, u8p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, vp, f64p, vp],
+            "qtn_contract_sweep_device": [vp, vp, vp, vp, ctypes.c_int, ctypes.c_int, vp, vp],
             "qtn_contract_batch": [P(vp), P(u8p), ctypes.c_int, ctypes.c_int, vp, f64p],
             "qtn_plan_executor": [vp, P(ctypes.c_char_p)],
             "qtn_plan_describe": [vp, ctypes.c_char_p, ctypes.c_size_t, P(ctypes.c_size_t)],
@@ -314,6 +315,23 @@ class Plan:
         _check(lib().qtn_contract_amplitudes_device(self._h, ctypes.c_void_p(d_x.data_ptr()), nx,
                                                     PRECISIONS[precision], _stream_handle(stream),
                                                     ctypes.c_void_p(d_out.data_ptr())))
+
+    def contract_sweep_device(self, d_x, d_gamma, d_beta, d_out, precision: str = "fp32", stream=None):
+        """Amplitudes of (bit string i, angles i): d_x CUDA uint8 (nx, n);
+        d_gamma, d_beta CUDA float64 (nx, p); d_out CUDA float64 (nx, 2)."""
+        for t in (d_x, d_gamma, d_beta, d_out):
+            if not t.is_cuda or not t.is_contiguous():
+                raise ValueError("every buffer must be a contiguous CUDA tensor")
+        nx = int(d_x.shape[0])
+        p = self.network.p
+        if (d_x.dtype.itemsize != 1 or d_x.numel() != nx * self.n or d_gamma.element_size() != 8
+                or d_beta.element_size() != 8 or d_gamma.numel() != nx * p or d_beta.numel() != nx * p
+                or d_out.element_size() != 8 or d_out.numel() != 2 * nx):
+            raise ValueError("shapes must be (nx, n) uint8, (nx, p) float64 twice and (nx, 2) float64")
+        _check(lib().qtn_contract_sweep_device(self._h, ctypes.c_void_p(d_x.data_ptr()),
+                                               ctypes.c_void_p(d_gamma.data_ptr()),
+                                               ctypes.c_void_p(d_beta.data_ptr()), nx, PRECISIONS[precision],
+                                               _stream_handle(stream), ctypes.c_void_p(d_out.data_ptr())))
 
     def contract_amplitudes_noalloc(self, d_x, d_out, precision: str = "fp32", stream=None):
         """Like contract_amplitudes_device, but the library allocates no device

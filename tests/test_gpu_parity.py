@@ -334,3 +334,47 @@ def test_every_executor_matches_oracle(gpu, n, p, k, seed, nx):
     print(len(checked), "program/arithmetic pairs:", checked)
     assert any(nm.startswith("level") for nm, _ in checked)
     assert {pr for _, pr in checked} >= {"fp64", "fp32x2", "fp32"}
+
+
+def _sweep(plan, xs, G, B, prec):
+    d_x = torch.from_numpy(np.ascontiguousarray(xs.astype(np.uint8))).cuda()
+    d_g = torch.from_numpy(np.ascontiguousarray(G)).cuda()
+    d_b = torch.from_numpy(np.ascontiguousarray(B)).cuda()
+    d_out = torch.zeros((xs.shape[0], 2), dtype=torch.float64, device="cuda")
+    plan.contract_sweep_device(d_x, d_g, d_b, d_out, prec)
+    torch.cuda.synchronize()
+    o = d_out.cpu().numpy()
+    return o[:, 0] + 1j * o[:, 1]
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32x2", 1e-10)])
+def test_parameter_sweep_matches_statevector(gpu, prec, tol):
+    # One plan serves a QAOA parameter scan (Sec. II.A: only the gate tensors
+    # depend on gamma, beta): every (bit string, angle set) pair against the
+    # state vector of its own angles.
+    n, p, nx = 16, 2, 6
+    inst = I.qaoa_instance(n, p, 21)
+    net = qtn.Network(n, inst.edges, inst.gamma, inst.beta)
+    plan = qtn.Plan(net, k=3)
+    rng = np.random.default_rng(4)
+    G, B = rng.uniform(0, np.pi, (nx, p)), rng.uniform(0, np.pi, (nx, p))
+    xs = I.bitstrings(n, nx, 21)
+    got = _sweep(plan, xs, G, B, prec)
+    for i in range(nx):
+        sv = O.statevector(n, inst.edges, G[i], B[i])
+        assert rel(got[i], sv[O.bits_to_int(xs[i])]) < tol, i
+
+
+def test_parameter_sweep_n80_and_shared_angles(gpu, config80):
+    # n = 80 sweep against the oracle (FP64 form), and a sweep whose angle sets
+    # all equal the network's reproduces the fixed-angle launch bit for bit.
+    inst, plan, xs, refs = config80
+    rng = np.random.default_rng(9)
+    G, B = rng.uniform(0, np.pi, (3, 1)), rng.uniform(0, np.pi, (3, 1))
+    got = _sweep(plan, xs[:3], G, B, "fp64")
+    for i in range(3):
+        ref = O.tn_amplitude(80, inst.edges, G[i], B[i], xs[i], cuts=plan.cut_names(), threads=16).value
+        assert rel(got[i], ref) < 1e-10, i
+    same = _sweep(plan, xs, np.tile(inst.gamma, (8, 1)), np.tile(inst.beta, (8, 1)), "fp64")
+    fixed = device_amplitudes(plan, xs, "fp64")
+    assert np.array_equal(same, fixed)
