@@ -82,6 +82,17 @@ typedef struct qtn_plan qtn_plan_t;
  * tensors and sum_q (p*deg(q) - 1) indices (Sec. II.A, Fig. 1). */
 qtn_status qtn_build_network(int n, int p, const int32_t* edges, int m, const double* gamma,
                              const double* beta, qtn_network_t** out);
+
+/* The density form of an amplitude network (Sec. II.A: vertices are the
+ * gates' superoperators G (x) conj(G), every edge has dimension 4).  An edge
+ * of dimension 4 is a pair of binary indices: ket index i and bra index
+ * i + I (I = the amplitude network's index count), with the same endpoints.
+ * Cutting both indices of an edge fixes it to one of 4 values, so m cut
+ * edges give 4^m slices (Sec. III.A).  Plans of this network contract
+ * <x| rho |x> = |a(x)|^2 (returned as a complex value with zero imaginary
+ * part up to rounding).  *out is a new handle owned by the caller.
+ * QTN_ERR_INVALID_ARG if `amplitude` is NULL or already in density form. */
+qtn_status qtn_network_density(const qtn_network_t* amplitude, qtn_network_t** out);
 void qtn_network_destroy(qtn_network_t* net);
 
 /* Counts of tensors and indices.  Index ids 0..n_indices-1 are stable. */

@@ -273,6 +273,7 @@ struct qtn_plan {
     d.n_levels = (int)pg.levels.size();
     d.block_threads = sl.threads;
     d.blocks_per_sm = sl.blocks_per_sm;
+    d.density = pg.density ? 1 : 0;
     d.n = pg.n;
     d.p = pg.p;
     d.k = pg.k;
@@ -324,7 +325,9 @@ struct qtn_plan {
     return QTN_OK;
   }
 
-  double scale() const { return std::pow(2.0, -0.5 * net.n); }
+  // 2^{-n/2} per unnormalised H|0> = (1, 1) on each ket wire; the density
+  // form has the bra wires too.
+  double scale() const { return std::pow(2.0, (net.density ? -1.0 : -0.5) * net.n); }
 
   LaunchBuffers buffers() const {
     LaunchBuffers b;
@@ -495,6 +498,17 @@ qtn_status qtn_build_network(int n, int p, const int32_t* edges, int m, const do
     delete h;
     return fail(QTN_ERR_INVALID_ARG, err);
   }
+  *out = h;
+  return QTN_OK;
+}
+
+qtn_status qtn_network_density(const qtn_network_t* amplitude, qtn_network_t** out) {
+  if (!amplitude || !out) return fail(QTN_ERR_INVALID_ARG, "NULL argument");
+  *out = nullptr;
+  if (amplitude->net.density) return fail(QTN_ERR_INVALID_ARG, "the network is already in density form");
+  qtn_network_t* h = new (std::nothrow) qtn_network_t;
+  if (!h) return fail(QTN_ERR_OOM, "host allocation failed");
+  h->net = density_network(amplitude->net);
   *out = h;
   return QTN_OK;
 }
@@ -1097,6 +1111,7 @@ qtn_status qtn_contract_batch(const qtn_plan_t* const* plans, const uint8_t* con
     J.n_levels = d.n_levels;
     J.log2_items = jh[j].log2_items;
     J.arena_stride = d.arena_elems | 1u;
+    J.density = d.density;
     std::memcpy(W.h_x + x_off[j], xs[j], (size_t)J.n);
   }
   std::memcpy(W.h_jobs, jobs.data(), sizeof(JobDesc) * njobs);
@@ -1138,7 +1153,8 @@ qtn_status qtn_plan_describe(const qtn_plan_t* plan, char* buf, size_t cap, size
   std::ostringstream o;
   o.precision(17);
   const Plan& P = plan->plan;
-  o << "{\"n\":" << plan->net.n << ",\"p\":" << plan->net.p << ",\"n_leaves\":" << P.n_leaves << ",\"cuts\":";
+  o << "{\"n\":" << plan->net.n << ",\"p\":" << plan->net.p << ",\"density\":" << (plan->net.density ? "true" : "false")
+    << ",\"n_leaves\":" << P.n_leaves << ",\"cuts\":";
   json_ints(o, P.cuts.data(), P.cuts.size());
   o << ",\"order\":";
   json_ints(o, P.order.data(), P.order.size());
@@ -1239,8 +1255,9 @@ qtn_status qtn_plan_describe(const qtn_plan_t* plan, char* buf, size_t cap, size
     const Gate& G = plan->net.gates[g];
     o << (g ? "," : "") << "{\"layer\":" << G.layer << ",\"q\":[" << G.q[0] << "," << G.q[1] << "],\"in_h\":["
       << (int)G.in_h[0] << "," << (int)G.in_h[1] << "],\"out_kind\":[" << (int)G.out_kind[0] << ","
-      << (int)G.out_kind[1] << "],\"leg\":[" << G.leg[0] << "," << G.leg[1] << "," << G.leg[2] << "," << G.leg[3]
-      << "]}";
+      << (int)G.out_kind[1] << "],\"leg\":[";
+    for (int s = 0; s < (plan->net.density ? kMaxLegs : 4); ++s) o << (s ? "," : "") << G.leg[s];
+    o << "]}";
   }
   o << "]}";
   std::string s = o.str();

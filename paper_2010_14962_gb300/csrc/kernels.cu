@@ -278,57 +278,78 @@ __host__ __device__ inline SmemLayout smem_layout(int n_steps, int n_leaves, uin
 
 // ------------------------------------------------------------ leaf build --
 
-// Entry e of leaf L (FP64 evaluation, rounded by V's conversion).
+// Value of ZZ gate g (with its absorbed H|0>, RX and <x| pieces) at leg
+// values v[0..3] (in q0, in q1, out q0, out q1; -1 on absorbed legs).
+__device__ __forceinline__ void gate_value(int g, const int* v, const int32_t* __restrict__ gate_q,
+                                           const int8_t* __restrict__ gate_layer,
+                                           const int8_t* __restrict__ gate_in_h,
+                                           const int8_t* __restrict__ gate_out_kind, const double* __restrict__ gamma,
+                                           const double* __restrict__ beta, const uint8_t* __restrict__ xrow,
+                                           double& re, double& im) {
+  const int l = gate_layer[g];
+  double sg, cg, sb, cb;
+  sincos(gamma[l], &sg, &cg);
+  sincos(beta[l], &sb, &cb);
+  re = 0.0;
+  im = 0.0;
+  // T = sum over the wire values (u0, u1) inside the diagonal ZZ gate of
+  //   exp(-i gamma s0 s1) * prod_w [in leg: delta] * [out leg: delta or
+  //   RX(2 beta)[out, u] or <x_q|RX(2 beta)|u>];  absorbed H|0> = (1, 1).
+  for (int u0 = 0; u0 < 2; ++u0)
+    for (int u1 = 0; u1 < 2; ++u1) {
+      const int u[2] = {u0, u1};
+      const double sgn = (double)((1 - 2 * u0) * (1 - 2 * u1));
+      double tre = cg, tim = -sgn * sg;
+      bool ok = true;
+      for (int w = 0; w < 2; ++w) {
+        if (!gate_in_h[2 * g + w] && v[w] != u[w]) ok = false;
+        const int kind = gate_out_kind[2 * g + w];
+        if (kind == OUT_PLAIN) {
+          if (v[2 + w] != u[w]) ok = false;
+        } else {
+          const int row = (kind == OUT_RX) ? v[2 + w] : (int)xrow[gate_q[2 * g + w]];
+          if (row != u[w]) {  // multiply by -i sin(beta)
+            const double nre = tim * sb, nim = -tre * sb;
+            tre = nre;
+            tim = nim;
+          } else {
+            tre *= cb;
+            tim *= cb;
+          }
+        }
+      }
+      if (ok) {
+        re += tre;
+        im += tim;
+      }
+    }
+}
+
+// Entry e of leaf L (FP64 evaluation, rounded by V's conversion).  In the
+// density form (Sec. II.A, dimension-4 edges) the leaf is the superoperator
+// G (x) conj(G): slots 0..3 carry the ket bits, slots 4..7 the bra bits.
 template <class V>
 __device__ __forceinline__ V leaf_entry(const DevLeaf& L, int e, const int32_t* __restrict__ gate_q,
                                         const int8_t* __restrict__ gate_layer, const int8_t* __restrict__ gate_in_h,
                                         const int8_t* __restrict__ gate_out_kind, const double* __restrict__ gamma,
-                                        const double* __restrict__ beta, const uint8_t* __restrict__ xrow) {
+                                        const double* __restrict__ beta, const uint8_t* __restrict__ xrow,
+                                        bool density) {
   const int r = L.rank_nc + L.ncut;
   double re = 1.0, im = 0.0;
   if (L.gate >= 0) {
     const int g = L.gate;
-    const int l = gate_layer[g];
-    int v[4] = {-1, -1, -1, -1};
+    int v[8] = {-1, -1, -1, -1, -1, -1, -1, -1};
     for (int b = 0; b < r; ++b)
-      for (int sl = 0; sl < 4; ++sl)
+      for (int sl = 0; sl < 8; ++sl)
         if ((L.slot_mask[b] >> sl) & 1) v[sl] = (e >> b) & 1;
-    double sg, cg, sb, cb;
-    sincos(gamma[l], &sg, &cg);
-    sincos(beta[l], &sb, &cb);
-    re = 0.0;
-    im = 0.0;
-    // T = sum over the wire values (u0, u1) inside the diagonal ZZ gate of
-    //   exp(-i gamma s0 s1) * prod_w [in leg: delta] * [out leg: delta or
-    //   RX(2 beta)[out, u] or <x_q|RX(2 beta)|u>];  absorbed H|0> = (1, 1).
-    for (int u0 = 0; u0 < 2; ++u0)
-      for (int u1 = 0; u1 < 2; ++u1) {
-        const int u[2] = {u0, u1};
-        const double sgn = (double)((1 - 2 * u0) * (1 - 2 * u1));
-        double tre = cg, tim = -sgn * sg;
-        bool ok = true;
-        for (int w = 0; w < 2; ++w) {
-          if (!gate_in_h[2 * g + w] && v[w] != u[w]) ok = false;
-          const int kind = gate_out_kind[2 * g + w];
-          if (kind == OUT_PLAIN) {
-            if (v[2 + w] != u[w]) ok = false;
-          } else {
-            const int row = (kind == OUT_RX) ? v[2 + w] : (int)xrow[gate_q[2 * g + w]];
-            if (row != u[w]) {  // multiply by -i sin(beta)
-              const double nre = tim * sb, nim = -tre * sb;
-              tre = nre;
-              tim = nim;
-            } else {
-              tre *= cb;
-              tim *= cb;
-            }
-          }
-        }
-        if (ok) {
-          re += tre;
-          im += tim;
-        }
-      }
+    gate_value(g, v, gate_q, gate_layer, gate_in_h, gate_out_kind, gamma, beta, xrow, re, im);
+    if (density) {
+      double bre, bim;
+      gate_value(g, v + 4, gate_q, gate_layer, gate_in_h, gate_out_kind, gamma, beta, xrow, bre, bim);
+      const double pre = re * bre + im * bim, pim = im * bre - re * bim;  // (re + i im) * conj(bre + i bim)
+      re = pre;
+      im = pim;
+    }
   }
   return CplxOps<V>::from(re, im);
 }
@@ -340,7 +361,7 @@ __global__ void leaf_build_kernel(const DevLeaf* __restrict__ leaves, const int3
                                   const int8_t* __restrict__ gate_layer, const int8_t* __restrict__ gate_in_h,
                                   const int8_t* __restrict__ gate_out_kind, const double* __restrict__ gamma,
                                   const double* __restrict__ beta, int angle_stride, const uint8_t* __restrict__ x,
-                                  int n, uint32_t leaf_elems, int n_leaves, V* __restrict__ out) {
+                                  int n, uint32_t leaf_elems, int n_leaves, bool density, V* __restrict__ out) {
   const DevLeaf L = leaves[blockIdx.x % n_leaves];
   const int xi = blockIdx.x / n_leaves;
   if (L.gate == -2) return;  // pseudo-leaf: written by the prologue kernel
@@ -349,7 +370,7 @@ __global__ void leaf_build_kernel(const DevLeaf* __restrict__ leaves, const int3
   const double* b = beta + (size_t)xi * angle_stride;
   for (int e = threadIdx.x; e < (1 << r); e += blockDim.x)
     out[(size_t)xi * leaf_elems + L.base + e] = leaf_entry<V>(L, e, gate_q, gate_layer, gate_in_h, gate_out_kind,
-                                                              g, b, x + (size_t)xi * n);
+                                                              g, b, x + (size_t)xi * n, density);
 }
 
 // ------------------------------------------------------------- lane exec --
@@ -872,7 +893,8 @@ __global__ void multi_leaf_kernel(const JobDesc* __restrict__ jobs, int njobs) {
   const int r = L.rank_nc + L.ncut;
   V* out = static_cast<V*>(J.leaf_table);
   for (int e = threadIdx.x; e < (1 << r); e += blockDim.x)
-    out[L.base + e] = leaf_entry<V>(L, e, J.gate_q, J.gate_layer, J.gate_in_h, J.gate_out_kind, J.gamma, J.beta, J.x);
+    out[L.base + e] = leaf_entry<V>(L, e, J.gate_q, J.gate_layer, J.gate_in_h, J.gate_out_kind, J.gamma, J.beta, J.x,
+                                    J.density != 0);
 }
 
 template <class V, class Ops = CplxOps<V>>
@@ -1145,7 +1167,8 @@ cudaError_t launch_typed(const DeviceProgram& prog, const uint8_t* d_x, int nx, 
   leaf_build_kernel<V><<<lgrid, 32, 0, stream>>>(prog.leaves, prog.gate_q, prog.gate_layer, prog.gate_in_h,
                                                  prog.gate_out_kind, sweep ? d_gamma : prog.gamma,
                                                  sweep ? d_beta : prog.beta, sweep ? prog.p : 0, d_x, prog.n,
-                                                 prog.leaf_elems, prog.n_leaves, static_cast<V*>(buf.leaf_tables));
+                                                 prog.leaf_elems, prog.n_leaves, prog.density != 0,
+                                                 static_cast<V*>(buf.leaf_tables));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (prog.n_pro_steps > 0) {

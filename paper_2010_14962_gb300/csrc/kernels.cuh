@@ -46,6 +46,7 @@ struct DeviceProgram {
   const int8_t* gate_out_kind = nullptr;
   const double* gamma = nullptr;
   const double* beta = nullptr;
+  int density = 0;  // leaves are G (x) conj(G) (density form)
   // Level executor only.
   const DevLevel* levels = nullptr;
   const uint32_t* out_start = nullptr;
@@ -114,6 +115,7 @@ struct JobDesc {
   int n_levels;
   int log2_items;          // items per block = 2^log2_items; chunks are multiples of it
   uint32_t arena_stride;   // elements between item arenas
+  int density;             // leaves are G (x) conj(G) (density form)
 };
 // A range of work items of one job.
 struct ChunkDesc {

@@ -57,6 +57,8 @@ std::string build_network(int n, int p, const int32_t* edges, int m,
         int q = e[w];
         g.leg[w] = -1;
         g.leg[2 + w] = -1;
+        g.leg[4 + w] = -1;
+        g.leg[6 + w] = -1;
         g.out_kind[w] = OUT_PLAIN;
         if (open_gate[q] < 0) {
           g.in_h[w] = 1;
@@ -94,9 +96,24 @@ std::string build_network(int n, int p, const int32_t* edges, int m,
 std::vector<std::vector<int>> leaf_index_lists(const Network& net) {
   std::vector<std::vector<int>> r(net.gates.size());
   for (size_t g = 0; g < net.gates.size(); ++g)
-    for (int s = 0; s < 4; ++s)
+    for (int s = 0; s < kMaxLegs; ++s)
       if (net.gates[g].leg[s] >= 0) r[g].push_back(net.gates[g].leg[s]);
   return r;
+}
+
+Network density_network(const Network& a) {
+  Network d = a;
+  d.density = true;
+  const int I = (int)a.indices.size();
+  for (int i = 0; i < I; ++i) {
+    Index bra = a.indices[i];
+    bra.slot[0] += 4;
+    bra.slot[1] += 4;
+    d.indices.push_back(bra);
+  }
+  for (Gate& g : d.gates)
+    for (int s = 0; s < 4; ++s) g.leg[4 + s] = g.leg[s] >= 0 ? g.leg[s] + I : -1;
+  return d;
 }
 
 }  // namespace qtn

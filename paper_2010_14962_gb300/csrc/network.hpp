@@ -25,10 +25,14 @@ enum OutKind : int8_t {
 // One ZZ(gamma_l) gate on qubits (q[0], q[1]).  Leg slots are
 // 0 = in q0, 1 = in q1, 2 = out q0, 3 = out q1.  A slot holds the id of the
 // index (wire segment) it connects to, or -1 if the wire end was absorbed.
+// In the density form (Sec. II.A with dimension-4 edges) the vertex is the
+// gate's superoperator G (x) conj(G): slots 4..7 are the bra copies of
+// slots 0..3 (each dimension-4 edge is a ket bit and a bra bit).
+constexpr int kMaxLegs = 8;
 struct Gate {
   int layer;
   int q[2];
-  int leg[4];
+  int leg[kMaxLegs];
   int8_t in_h[2];    // 1 if H|0> (unnormalised [1,1]) is absorbed on the in leg
   int8_t out_kind[2];
 };
@@ -48,11 +52,18 @@ struct Network {
   std::vector<double> gamma, beta;
   std::vector<Gate> gates;
   std::vector<Index> indices;
+  // Density form: indices [I/2, I) are the bra copies of [0, I/2); the
+  // network's scalar is <x| rho |x> = |a(x)|^2 (times 2^-n unnormalised).
+  bool density = false;
 };
 
 // Builds the network; returns an empty string on success, else a message.
 std::string build_network(int n, int p, const int32_t* edges, int m,
                           const double* gamma, const double* beta, Network* out);
+
+// The density form of an amplitude network: same vertices, every edge of
+// dimension 4 (ket bit i, bra bit i + I).
+Network density_network(const Network& amplitude);
 
 // Index sets of every leaf (gate) tensor, in leg-slot order, absorbed legs
 // dropped.

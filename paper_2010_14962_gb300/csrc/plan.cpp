@@ -51,7 +51,7 @@ std::string eliminate(const Network& net, const std::vector<char>& is_cut,
   T.reserve(2 * L);
   for (int g = 0; g < L; ++g) {
     Bits b(I);
-    for (int s = 0; s < 4; ++s) {
+    for (int s = 0; s < kMaxLegs; ++s) {
       int e = net.gates[g].leg[s];
       if (e >= 0 && !is_cut[e]) b.set(e);
     }

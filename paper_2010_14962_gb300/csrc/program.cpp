@@ -63,12 +63,15 @@ std::vector<int> cut_classes(const Network& net, const std::vector<int>& cuts, i
   for (int j = 0; j < k; ++j) cut_no[cuts[j]] = j;
   std::vector<int> parent(k);
   std::iota(parent.begin(), parent.end(), 0);
+  // The in and out segment of a wire through a diagonal gate (ket slots w,
+  // 2 + w; in the density form also the bra slots 4 + w, 6 + w).
   for (const Gate& g : net.gates)
-    for (int w = 0; w < 2; ++w) {
-      if (g.out_kind[w] != OUT_PLAIN || g.leg[w] < 0 || g.leg[2 + w] < 0) continue;
-      int a = cut_no[g.leg[w]], b = cut_no[g.leg[2 + w]];
-      if (a >= 0 && b >= 0) parent[find_root(parent, a)] = find_root(parent, b);
-    }
+    for (int d = 0; d < (net.density ? 8 : 4); d += 4)
+      for (int w = 0; w < 2; ++w) {
+        if (g.out_kind[w] != OUT_PLAIN || g.leg[d + w] < 0 || g.leg[d + 2 + w] < 0) continue;
+        int a = cut_no[g.leg[d + w]], b = cut_no[g.leg[d + 2 + w]];
+        if (a >= 0 && b >= 0) parent[find_root(parent, a)] = find_root(parent, b);
+      }
   std::map<int, int> id;
   std::vector<int> cls(k);
   for (int j = 0; j < k; ++j) {
@@ -90,6 +93,7 @@ std::string compile_program(const Network& net, const Plan& plan_in, const Progr
   pg.n = net.n;
   pg.p = net.p;
   pg.k = K;
+  pg.density = net.density;
 
   // Classes and their outer / inner positions.
   std::vector<int> cls = opt.cut_class;
@@ -136,7 +140,7 @@ std::string compile_program(const Network& net, const Plan& plan_in, const Progr
   for (int t = 0; t < n_leaves; ++t) {
     Set f = plan.tensors[t];
     if (const Gate* g = leaf_gate(t))
-      for (int s = 0; s < 4; ++s)
+      for (int s = 0; s < kMaxLegs; ++s)
         if (g->leg[s] >= 0 && cut_no[g->leg[s]] >= 0 && is_inner[cls[cut_no[g->leg[s]]]])
           f.push_back(I + cls[cut_no[g->leg[s]]]);
     std::sort(f.begin(), f.end());
@@ -216,7 +220,7 @@ std::string compile_program(const Network& net, const Plan& plan_in, const Progr
       int pos = 0;
       auto slots_of = [&](int id) -> uint8_t {
         uint8_t mask = 0;
-        for (int s = 0; s < 4; ++s) {
+        for (int s = 0; s < kMaxLegs; ++s) {
           int ix = g->leg[s];
           if (ix < 0) continue;
           if (id < I ? ix == id : (cut_no[ix] >= 0 && cls[cut_no[ix]] == id - I)) mask |= (uint8_t)(1u << s);
@@ -230,7 +234,7 @@ std::string compile_program(const Network& net, const Plan& plan_in, const Progr
       }
       lf.rank_nc = (uint8_t)pos;
       std::vector<std::pair<int, int>> outer;  // (outer position, class)
-      for (int s = 0; s < 4; ++s) {
+      for (int s = 0; s < kMaxLegs; ++s) {
         int ix = g->leg[s];
         if (ix < 0 || cut_no[ix] < 0) continue;
         int c = cls[cut_no[ix]];

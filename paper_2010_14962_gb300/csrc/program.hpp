@@ -103,6 +103,7 @@ struct ProgramOptions {
 
 struct Program {
   int n = 0, p = 0, k = 0;
+  bool density = false;              // leaves are G (x) conj(G)
   int n_classes = 0;                 // slice classes (non-zero slices = 2^n_classes)
   int n_outer = 0, n_inner = 0;      // outer / inner classes
   std::vector<int> outer_class;      // outer bit position -> class

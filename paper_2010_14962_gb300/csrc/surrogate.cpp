@@ -115,7 +115,7 @@ void surrogate_features(const Network& net, const std::vector<int>& cuts, float*
   f[5] = ncls / 32.f;
   std::vector<int> per_gate(L, 0), deg_after(L, 0);
   for (int g = 0; g < L; ++g)
-    for (int s = 0; s < 4; ++s) {
+    for (int s = 0; s < kMaxLegs; ++s) {
       int ix = net.gates[g].leg[s];
       if (ix < 0) continue;
       if (is_cut[ix]) per_gate[g]++;

@@ -64,6 +64,7 @@ def lib():
         sig = {
             "qtn_build_network": [ctypes.c_int, ctypes.c_int, i32p, ctypes.c_int, f64p, f64p, P(vp)],
             "qtn_network_destroy": [vp],
+            "qtn_network_density": [vp, P(vp)],
             "qtn_network_info": [vp, P(ctypes.c_int), P(ctypes.c_int)],
             "qtn_network_index": [vp, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int),
                                   P(ctypes.c_int)],
@@ -159,6 +160,17 @@ class Network:
                                        _ptr(b, ctypes.c_double), ctypes.byref(h)))
         self._h = h
 
+    def density(self) -> "Network":
+        """qtn_network_density: the dimension-4 (density) form of this network."""
+        h = ctypes.c_void_p()
+        _check(lib().qtn_network_density(self._h, ctypes.byref(h)))
+        d = Network.__new__(Network)
+        d.n, d.p, d._h = self.n, self.p, h
+        d.is_density = True
+        return d
+
+    is_density = False
+
     def __del__(self):
         if getattr(self, "_h", None) and _lib is not None:
             _lib.qtn_network_destroy(self._h)
@@ -214,6 +226,15 @@ def plan_to_fit(network: "Network", k_min: int, k_max: int = 24, slice_bytes: fl
         except QTNError as e:
             last = e
     raise QTNError(3, f"no greedy cut set of {k_min}..{k_max} cuts fits {slice_bytes:g} bytes per slice ({last})")
+
+
+def density_plan(amplitude_plan: "Plan", density_net: "Network", **kw) -> "Plan":
+    """Plan of the density form that cuts the same edges as ``amplitude_plan``:
+    each cut edge is both its ket index c and its bra index c + I, so k cut
+    edges give 4^k slices (ket cut bits first, then the bra bits)."""
+    _, n_idx = amplitude_plan.network.info()
+    c = [int(x) for x in amplitude_plan.cuts]
+    return Plan(density_net, cuts=c + [x + n_idx for x in c], **kw)
 
 
 class Plan:

@@ -40,6 +40,15 @@ def gate_entry(gate, gamma, beta, x, v):
     return total
 
 
+def leaf_value(desc, gate, gamma, beta, x, v):
+    """A leaf's entry: the gate at ket legs v[0..3]; in the density form
+    (dimension-4 edges) times the conjugate gate at the bra legs v[4..7]."""
+    val = gate_entry(gate, gamma, beta, x, v[:4])
+    if desc.get("density"):
+        val *= np.conj(gate_entry(gate, gamma, beta, x, v[4:]))
+    return val
+
+
 def leaf_table(desc, prog, gamma, beta, x):
     lt = np.zeros(max(prog["leaf_elems"], 1), dtype=complex)
     for L in prog["leaves"]:
@@ -50,12 +59,12 @@ def leaf_table(desc, prog, gamma, beta, x):
             if L["gate"] < 0:
                 val = 1.0
             else:
-                v = [-1] * 4
+                v = [-1] * 8
                 for bit, mask in enumerate(L["slot_mask"]):
-                    for sl in range(4):
+                    for sl in range(8):
                         if (mask >> sl) & 1:
                             v[sl] = (e >> bit) & 1
-                val = gate_entry(desc["gates"][L["gate"]], gamma, beta, x, v)
+                val = leaf_value(desc, desc["gates"][L["gate"]], gamma, beta, x, v)
             lt[L["base"] + e] = val
     return lt
 

@@ -378,3 +378,35 @@ def test_parameter_sweep_n80_and_shared_angles(gpu, config80):
     same = _sweep(plan, xs, np.tile(inst.gamma, (8, 1)), np.tile(inst.beta, (8, 1)), "fp64")
     fixed = device_amplitudes(plan, xs, "fp64")
     assert np.array_equal(same, fixed)
+
+
+@pytest.mark.parametrize("n,p,k,seed", [(16, 1, 2, 1), (14, 2, 3, 4)])
+def test_density_form_every_executor(gpu, n, p, k, seed):
+    # The density form (dimension-4 edges, 4^k slices) on every executor:
+    # <x| rho |x> = |a(x)|^2 from the state vector.
+    inst = I.qaoa_instance(n, p, seed)
+    net = qtn.Network(n, inst.edges, inst.gamma, inst.beta)
+    plan = qtn.Plan(net, k=k)
+    dplan = qtn.density_plan(plan, net.density())
+    sv = O.statevector(n, inst.edges, inst.gamma, inst.beta)
+    xs = I.bitstrings(n, 2, seed + 7)
+    probs = np.array([abs(sv[O.bits_to_int(x)]) ** 2 for x in xs])
+    d = dplan.describe()
+    checked = 0
+    for name in d["programs"]:
+        if name == d["executor"]:
+            continue
+        for prec in _executor_precisions(name):
+            if prec == "fp32":
+                continue
+            dplan.select_executor(name, prec, 2)
+            try:
+                got = device_amplitudes(dplan, xs, prec)
+            except qtn.QTNError as e:
+                assert e.status == 6 and "shared memory" in str(e), (name, prec, str(e))
+                continue
+            assert np.max(np.abs(got - probs) / probs) < 1e-10, (name, prec)
+            checked += 1
+    for x, pr in zip(xs, probs):  # host entry point, per-slice program
+        assert abs(dplan.contract_amplitude(x, "fp64") - pr) < 1e-10 * pr
+    assert checked >= 4

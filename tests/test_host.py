@@ -219,6 +219,40 @@ def test_emulated_programs_match_oracle_per_slice(n, p, k, seed):
         assert abs(got.sum() - ref.value) < 1e-13 * np.sum(np.abs(ref.per_slice)), name
 
 
+@pytest.mark.parametrize("n,p,k,seed", [(10, 1, 2, 1), (12, 2, 3, 4)])
+def test_density_form_slices_are_ket_bra_products(n, p, k, seed):
+    # The density form (Sec. II.A, dimension-4 edges): cutting k edges gives
+    # 4^k slices (Sec. III.A); slice (s, t) -- ket cut bits s, bra cut bits
+    # t -- is a_s * conj(a_t) with a_s the amplitude network's slice s, so
+    # the sum is |a|^2.  Every compiled program of the density plan, emulated.
+    inst = I.qaoa_instance(n, p, seed)
+    net = qtn.Network(n, inst.edges, inst.gamma, inst.beta)
+    plan = qtn.Plan(net, k=k)
+    dnet = net.density()
+    _, ni = net.info()
+    _, dni = dnet.info()
+    assert dni == 2 * ni
+    dplan = qtn.density_plan(plan, dnet)
+    assert dplan.cost()["k"] == 2 * k
+    d = dplan.describe()
+    assert d["density"] is True
+    x = I.bitstrings(n, 1, seed)[0]
+    ref = O.tn_amplitude(n, inst.edges, inst.gamma, inst.beta, x, cuts=plan.cut_names(), per_slice=True)
+    a_s = ref.per_slice  # scaled by 2^{-n/2}
+    want = np.array([a_s[i % (1 << k)] * np.conj(a_s[i >> k]) for i in range(1 << 2 * k)])
+    sv = O.statevector(n, inst.edges, inst.gamma, inst.beta)
+    prob = abs(sv[O.bits_to_int(x)]) ** 2
+    assert abs(want.sum() - prob) < 1e-12 * prob
+    scale = 2.0 ** (-n)
+    for name in d["programs"]:
+        vals = E.run_program(d, name, inst.gamma, inst.beta, x)
+        got = np.zeros(1 << 2 * k, dtype=complex)
+        for s_id, v in vals.items():
+            got[s_id] = v * scale
+        assert np.max(np.abs(got - want)) < 1e-13 * np.max(np.abs(want)), name
+        assert abs(got.sum() - prob) < 1e-12 * prob, name
+
+
 @pytest.mark.parametrize("n,p,k,seed", [(16, 1, 2, 1), (40, 2, 10, 2), (80, 1, 16, 3)])
 def test_level_programs_are_race_free(n, p, k, seed):
     # Level-ordered programs: the merges of a level run at the same time, so
