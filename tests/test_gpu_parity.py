@@ -380,7 +380,7 @@ def test_parameter_sweep_n80_and_shared_angles(gpu, config80):
     assert np.array_equal(same, fixed)
 
 
-@pytest.mark.parametrize("n,p,k,seed", [(16, 1, 2, 1), (14, 2, 3, 4)])
+@pytest.mark.parametrize("n,p,k,seed", [(16, 1, 2, 1), (12, 2, 6, 4)])
 def test_density_form_every_executor(gpu, n, p, k, seed):
     # The density form (dimension-4 edges, 4^k slices) on every executor:
     # <x| rho |x> = |a(x)|^2 from the state vector.
