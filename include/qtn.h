@@ -83,6 +83,22 @@ typedef struct qtn_plan qtn_plan_t;
 qtn_status qtn_build_network(int n, int p, const int32_t* edges, int m, const double* gamma,
                              const double* beta, qtn_network_t** out);
 
+/* The graphical-model form of the same circuit (the undirected graphical
+ * model in which diagonal gates share indices): the ZZ gates of a layer are
+ * diagonal, so a qubit keeps one basis value z_q^(l) from one mixer to the
+ * next.  Indices are these n * p variables (index (l - 1) * n + q is
+ * z_q^(l)); tensors are the p * m ZZ factors exp(-i gamma_l s_i s_j) (rank
+ * 2) and the p * n mixer factors <z_q^(l+1)| RX(2 beta_l) |z_q^(l)> (rank 2;
+ * rank 1 in the last layer, whose row is x_q).  An index is held by every
+ * factor of its layer on that qubit, so eliminating it merges all of them.
+ * Its width is much smaller than the gate network's; plans, slices (Sec.
+ * III.A: a cut fixes one variable in every factor that holds it) and all
+ * contraction entry points work on it unchanged and give the same amplitude.
+ * Arguments and errors as qtn_build_network; qtn_network_index reports
+ * (qubit, pos = l - 1) and two of the index's holders. */
+qtn_status qtn_build_network_gm(int n, int p, const int32_t* edges, int m, const double* gamma,
+                                const double* beta, qtn_network_t** out);
+
 /* The density form of an amplitude network (Sec. II.A: vertices are the
  * gates' superoperators G (x) conj(G), every edge has dimension 4).  An edge
  * of dimension 4 is a pair of binary indices: ket index i and bra index
@@ -91,7 +107,8 @@ qtn_status qtn_build_network(int n, int p, const int32_t* edges, int m, const do
  * edges give 4^m slices (Sec. III.A).  Plans of this network contract
  * <x| rho |x> = |a(x)|^2 (returned as a complex value with zero imaginary
  * part up to rounding).  *out is a new handle owned by the caller.
- * QTN_ERR_INVALID_ARG if `amplitude` is NULL or already in density form. */
+ * QTN_ERR_INVALID_ARG if `amplitude` is NULL or already in density form;
+ * QTN_ERR_UNSUPPORTED for a graphical-model network. */
 qtn_status qtn_network_density(const qtn_network_t* amplitude, qtn_network_t** out);
 void qtn_network_destroy(qtn_network_t* net);
 

@@ -255,6 +255,9 @@ struct qtn_plan {
     dev_allocs.push_back(gi);
     QTN_CUDA(::upload(&go, pg.gate_out_kind));
     dev_allocs.push_back(go);
+    int8_t* gk;
+    QTN_CUDA(::upload(&gk, pg.gate_kind));
+    dev_allocs.push_back(gk);
     QTN_CUDA(::upload(&ga, net.gamma));
     dev_allocs.push_back(ga);
     QTN_CUDA(::upload(&be, net.beta));
@@ -291,6 +294,7 @@ struct qtn_plan {
     d.gate_layer = gl;
     d.gate_in_h = gi;
     d.gate_out_kind = go;
+    d.gate_kind = gk;
     d.gamma = ga;
     d.beta = be;
     sl.uploaded = true;
@@ -502,10 +506,26 @@ qtn_status qtn_build_network(int n, int p, const int32_t* edges, int m, const do
   return QTN_OK;
 }
 
+qtn_status qtn_build_network_gm(int n, int p, const int32_t* edges, int m, const double* gamma, const double* beta,
+                                qtn_network_t** out) {
+  if (!out) return fail(QTN_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  qtn_network_t* h = new (std::nothrow) qtn_network_t;
+  if (!h) return fail(QTN_ERR_OOM, "host allocation failed");
+  std::string err = build_gm_network(n, p, edges, m, gamma, beta, &h->net);
+  if (!err.empty()) {
+    delete h;
+    return fail(QTN_ERR_INVALID_ARG, err);
+  }
+  *out = h;
+  return QTN_OK;
+}
+
 qtn_status qtn_network_density(const qtn_network_t* amplitude, qtn_network_t** out) {
   if (!amplitude || !out) return fail(QTN_ERR_INVALID_ARG, "NULL argument");
   *out = nullptr;
   if (amplitude->net.density) return fail(QTN_ERR_INVALID_ARG, "the network is already in density form");
+  if (amplitude->net.gm) return fail(QTN_ERR_UNSUPPORTED, "the density form is built from the gate network");
   qtn_network_t* h = new (std::nothrow) qtn_network_t;
   if (!h) return fail(QTN_ERR_OOM, "host allocation failed");
   h->net = density_network(amplitude->net);
@@ -596,7 +616,16 @@ qtn_status qtn_plan(const qtn_network_t* net, const int32_t* cuts, int k, const 
     delete h;
     return fail(QTN_ERR_INVALID_ARG, err);
   }
-  const bool lane_ok = lane_p.max_rank <= kLaneMaxRank;
+  // The lane executor's register merges have no batch bits (a graphical-model
+  // plan keeps indices shared by three or more tensors as batch bits).
+  auto no_batch_bits = [](const Program& pg) {
+    for (const DevStep& st : pg.steps)
+      if (st.bb) return false;
+    for (const DevStep& st : pg.prologue)
+      if (st.bb) return false;
+    return true;
+  };
+  const bool lane_ok = lane_p.max_rank <= kLaneMaxRank && no_batch_bits(lane_p);
   {
     ProgSlot s0;
     s0.name = lane_ok ? "lane" : "block";
@@ -616,7 +645,8 @@ qtn_status qtn_plan(const qtn_network_t* net, const int32_t* cuts, int k, const 
     ProgSlot sl;
     sl.name = "lane/classes";
     sl.exec = Executor::Lane;
-    if (compile_program(h->net, h->plan, o, &sl.prog).empty()) h->slots.push_back(std::move(sl));
+    if (compile_program(h->net, h->plan, o, &sl.prog).empty() && no_batch_bits(sl.prog))
+      h->slots.push_back(std::move(sl));
   }
   {
     ProgramOptions o;
@@ -1092,6 +1122,7 @@ qtn_status qtn_contract_batch(const qtn_plan_t* const* plans, const uint8_t* con
     J.gate_layer = d.gate_layer;
     J.gate_in_h = d.gate_in_h;
     J.gate_out_kind = d.gate_out_kind;
+    J.gate_kind = d.gate_kind;
     J.gamma = d.gamma;
     J.beta = d.beta;
     J.x = W.d_x + x_off[j];
@@ -1154,6 +1185,7 @@ qtn_status qtn_plan_describe(const qtn_plan_t* plan, char* buf, size_t cap, size
   o.precision(17);
   const Plan& P = plan->plan;
   o << "{\"n\":" << plan->net.n << ",\"p\":" << plan->net.p << ",\"density\":" << (plan->net.density ? "true" : "false")
+    << ",\"gm\":" << (plan->net.gm ? "true" : "false")
     << ",\"n_leaves\":" << P.n_leaves << ",\"cuts\":";
   json_ints(o, P.cuts.data(), P.cuts.size());
   o << ",\"order\":";
@@ -1253,7 +1285,8 @@ qtn_status qtn_plan_describe(const qtn_plan_t* plan, char* buf, size_t cap, size
   o << ",\"gates\":[";
   for (size_t g = 0; g < plan->net.gates.size(); ++g) {
     const Gate& G = plan->net.gates[g];
-    o << (g ? "," : "") << "{\"layer\":" << G.layer << ",\"q\":[" << G.q[0] << "," << G.q[1] << "],\"in_h\":["
+    o << (g ? "," : "") << "{\"kind\":" << (int)G.kind << ",\"layer\":" << G.layer << ",\"q\":[" << G.q[0] << ","
+      << G.q[1] << "],\"in_h\":["
       << (int)G.in_h[0] << "," << (int)G.in_h[1] << "],\"out_kind\":[" << (int)G.out_kind[0] << ","
       << (int)G.out_kind[1] << "],\"leg\":[";
     for (int s = 0; s < (plan->net.density ? kMaxLegs : 4); ++s) o << (s ? "," : "") << G.leg[s];

@@ -328,12 +328,41 @@ __device__ __forceinline__ void gate_value(int g, const int* v, const int32_t* _
 // Entry e of leaf L (FP64 evaluation, rounded by V's conversion).  In the
 // density form (Sec. II.A, dimension-4 edges) the leaf is the superoperator
 // G (x) conj(G): slots 0..3 carry the ket bits, slots 4..7 the bra bits.
+// Value of a graphical-model factor at leg values v[0], v[1]: the ZZ phase
+// exp(-i gamma_l s_0 s_1) (s = 1 - 2 z), or the mixer entry
+// <z_out| RX(2 beta_l) |z_in> = cos beta_l or -i sin beta_l, with z_out =
+// x_q on the last layer (leg 1 absent).
+__device__ __forceinline__ void gm_factor_value(int g, int kind, const int* v, const int32_t* __restrict__ gate_q,
+                                                const int8_t* __restrict__ gate_layer,
+                                                const double* __restrict__ gamma, const double* __restrict__ beta,
+                                                const uint8_t* __restrict__ xrow, double& re, double& im) {
+  const int l = gate_layer[g];
+  if (kind == GATE_GM_ZZ) {
+    double sg, cg;
+    sincos(gamma[l], &sg, &cg);
+    const double sgn = (double)((1 - 2 * v[0]) * (1 - 2 * v[1]));
+    re = cg;
+    im = -sgn * sg;
+  } else {
+    double sb, cb;
+    sincos(beta[l], &sb, &cb);
+    const int out = v[1] >= 0 ? v[1] : (int)xrow[gate_q[2 * g]];
+    if (out == v[0]) {
+      re = cb;
+      im = 0.0;
+    } else {
+      re = 0.0;
+      im = -sb;
+    }
+  }
+}
+
 template <class V>
 __device__ __forceinline__ V leaf_entry(const DevLeaf& L, int e, const int32_t* __restrict__ gate_q,
                                         const int8_t* __restrict__ gate_layer, const int8_t* __restrict__ gate_in_h,
-                                        const int8_t* __restrict__ gate_out_kind, const double* __restrict__ gamma,
-                                        const double* __restrict__ beta, const uint8_t* __restrict__ xrow,
-                                        bool density) {
+                                        const int8_t* __restrict__ gate_out_kind, const int8_t* __restrict__ gate_kind,
+                                        const double* __restrict__ gamma, const double* __restrict__ beta,
+                                        const uint8_t* __restrict__ xrow, bool density) {
   const int r = L.rank_nc + L.ncut;
   double re = 1.0, im = 0.0;
   if (L.gate >= 0) {
@@ -342,6 +371,11 @@ __device__ __forceinline__ V leaf_entry(const DevLeaf& L, int e, const int32_t* 
     for (int b = 0; b < r; ++b)
       for (int sl = 0; sl < 8; ++sl)
         if ((L.slot_mask[b] >> sl) & 1) v[sl] = (e >> b) & 1;
+    const int kind = gate_kind[g];
+    if (kind != GATE_ZZ) {
+      gm_factor_value(g, kind, v, gate_q, gate_layer, gamma, beta, xrow, re, im);
+      return CplxOps<V>::from(re, im);
+    }
     gate_value(g, v, gate_q, gate_layer, gate_in_h, gate_out_kind, gamma, beta, xrow, re, im);
     if (density) {
       double bre, bim;
@@ -359,7 +393,8 @@ __device__ __forceinline__ V leaf_entry(const DevLeaf& L, int e, const int32_t* 
 template <class V>
 __global__ void leaf_build_kernel(const DevLeaf* __restrict__ leaves, const int32_t* __restrict__ gate_q,
                                   const int8_t* __restrict__ gate_layer, const int8_t* __restrict__ gate_in_h,
-                                  const int8_t* __restrict__ gate_out_kind, const double* __restrict__ gamma,
+                                  const int8_t* __restrict__ gate_out_kind, const int8_t* __restrict__ gate_kind,
+                                  const double* __restrict__ gamma,
                                   const double* __restrict__ beta, int angle_stride, const uint8_t* __restrict__ x,
                                   int n, uint32_t leaf_elems, int n_leaves, bool density, V* __restrict__ out) {
   const DevLeaf L = leaves[blockIdx.x % n_leaves];
@@ -370,7 +405,7 @@ __global__ void leaf_build_kernel(const DevLeaf* __restrict__ leaves, const int3
   const double* b = beta + (size_t)xi * angle_stride;
   for (int e = threadIdx.x; e < (1 << r); e += blockDim.x)
     out[(size_t)xi * leaf_elems + L.base + e] = leaf_entry<V>(L, e, gate_q, gate_layer, gate_in_h, gate_out_kind,
-                                                              g, b, x + (size_t)xi * n, density);
+                                                              gate_kind, g, b, x + (size_t)xi * n, density);
 }
 
 // ------------------------------------------------------------- lane exec --
@@ -893,8 +928,8 @@ __global__ void multi_leaf_kernel(const JobDesc* __restrict__ jobs, int njobs) {
   const int r = L.rank_nc + L.ncut;
   V* out = static_cast<V*>(J.leaf_table);
   for (int e = threadIdx.x; e < (1 << r); e += blockDim.x)
-    out[L.base + e] = leaf_entry<V>(L, e, J.gate_q, J.gate_layer, J.gate_in_h, J.gate_out_kind, J.gamma, J.beta, J.x,
-                                    J.density != 0);
+    out[L.base + e] = leaf_entry<V>(L, e, J.gate_q, J.gate_layer, J.gate_in_h, J.gate_out_kind, J.gate_kind,
+                                    J.gamma, J.beta, J.x, J.density != 0);
 }
 
 template <class V, class Ops = CplxOps<V>>
@@ -1165,7 +1200,7 @@ cudaError_t launch_typed(const DeviceProgram& prog, const uint8_t* d_x, int nx, 
   const unsigned lgrid = (unsigned)prog.n_leaves * (unsigned)nx;
   const bool sweep = d_gamma != nullptr;
   leaf_build_kernel<V><<<lgrid, 32, 0, stream>>>(prog.leaves, prog.gate_q, prog.gate_layer, prog.gate_in_h,
-                                                 prog.gate_out_kind, sweep ? d_gamma : prog.gamma,
+                                                 prog.gate_out_kind, prog.gate_kind, sweep ? d_gamma : prog.gamma,
                                                  sweep ? d_beta : prog.beta, sweep ? prog.p : 0, d_x, prog.n,
                                                  prog.leaf_elems, prog.n_leaves, prog.density != 0,
                                                  static_cast<V*>(buf.leaf_tables));

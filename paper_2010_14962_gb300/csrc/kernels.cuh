@@ -47,6 +47,7 @@ struct DeviceProgram {
   const double* gamma = nullptr;
   const double* beta = nullptr;
   int density = 0;  // leaves are G (x) conj(G) (density form)
+  const int8_t* gate_kind = nullptr;  // GateKind per gate
   // Level executor only.
   const DevLevel* levels = nullptr;
   const uint32_t* out_start = nullptr;
@@ -100,6 +101,7 @@ struct JobDesc {
   const int8_t* gate_layer;
   const int8_t* gate_in_h;
   const int8_t* gate_out_kind;
+  const int8_t* gate_kind;
   const double* gamma;
   const double* beta;
   const uint8_t* x;   // n bit bytes

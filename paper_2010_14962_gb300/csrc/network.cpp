@@ -116,4 +116,63 @@ Network density_network(const Network& a) {
   return d;
 }
 
+std::string build_gm_network(int n, int p, const int32_t* edges, int m, const double* gamma, const double* beta,
+                             Network* out) {
+  Network base;
+  std::string err = build_network(n, p, edges, m, gamma, beta, &base);  // validation, edge order
+  if (!err.empty()) return err;
+  Network net;
+  net.n = n;
+  net.p = p;
+  net.gm = true;
+  net.edges = base.edges;
+  net.gamma = base.gamma;
+  net.beta = base.beta;
+  auto var = [&](int l, int q) { return l * n + q; };  // z_q^(l + 1)
+  for (int l = 0; l < p; ++l)
+    for (const auto& e : net.edges) {
+      Gate g{};
+      g.kind = GATE_GM_ZZ;
+      g.layer = l;
+      g.q[0] = e[0];
+      g.q[1] = e[1];
+      for (int s = 0; s < kMaxLegs; ++s) g.leg[s] = -1;
+      g.leg[0] = var(l, e[0]);
+      g.leg[1] = var(l, e[1]);
+      net.gates.push_back(g);
+    }
+  for (int l = 0; l < p; ++l)
+    for (int q = 0; q < n; ++q) {
+      Gate g{};
+      g.kind = GATE_GM_RX;
+      g.layer = l;
+      g.q[0] = g.q[1] = q;
+      for (int s = 0; s < kMaxLegs; ++s) g.leg[s] = -1;
+      g.leg[0] = var(l, q);
+      g.leg[1] = l + 1 < p ? var(l + 1, q) : -1;
+      net.gates.push_back(g);
+    }
+  net.indices.resize((size_t)n * p);
+  for (int i = 0; i < n * p; ++i) {
+    Index& ix = net.indices[i];
+    ix.qubit = i % n;
+    ix.pos = i / n;
+    ix.tensor[0] = ix.tensor[1] = -1;
+    ix.slot[0] = ix.slot[1] = -1;
+  }
+  for (int g = 0; g < (int)net.gates.size(); ++g)
+    for (int s = 0; s < 2; ++s) {
+      const int e = net.gates[g].leg[s];
+      if (e < 0) continue;
+      Index& ix = net.indices[e];
+      const int h = ix.tensor[0] < 0 ? 0 : ix.tensor[1] < 0 ? 1 : -1;
+      if (h >= 0) {
+        ix.tensor[h] = g;
+        ix.slot[h] = s;
+      }
+    }
+  *out = std::move(net);
+  return "";
+}
+
 }  // namespace qtn

@@ -29,16 +29,28 @@ enum OutKind : int8_t {
 // gate's superoperator G (x) conj(G): slots 4..7 are the bra copies of
 // slots 0..3 (each dimension-4 edge is a ket bit and a bra bit).
 constexpr int kMaxLegs = 8;
+
+// Vertex kinds.  GATE_ZZ: a ZZ gate with its absorbed pieces, legs as above.
+// The graphical-model form shares one index among all diagonal gates that
+// act on a qubit between two mixers (the basis value z_q^(l) of qubit q in
+// layer l): GATE_GM_ZZ is the factor exp(-i gamma_l s_i s_j) on legs 0, 1 =
+// z_i^(l), z_j^(l); GATE_GM_RX is <z_q^(l+1)| RX(2 beta_l) |z_q^(l)> on legs
+// 0 = z_q^(l), 1 = z_q^(l+1) (-1 in the last layer: the row is x_q).
+enum GateKind : int8_t { GATE_ZZ = 0, GATE_GM_ZZ = 1, GATE_GM_RX = 2 };
+
 struct Gate {
   int layer;
   int q[2];
   int leg[kMaxLegs];
   int8_t in_h[2];    // 1 if H|0> (unnormalised [1,1]) is absorbed on the in leg
   int8_t out_kind[2];
+  int8_t kind = GATE_ZZ;
 };
 
 // A wire segment between two consecutive ZZ gates on qubit `qubit`; it is the
 // segment that follows the `pos`-th ZZ gate (0-based) acting on that qubit.
+// In the graphical-model form: the variable z_qubit^(pos + 1), held by every
+// factor of its layer on that qubit (tensor / slot: the first two holders).
 struct Index {
   int tensor[2];  // gate ids of the endpoints (tensor[0] is the earlier gate)
   int slot[2];    // leg slots on those gates
@@ -55,6 +67,8 @@ struct Network {
   // Density form: indices [I/2, I) are the bra copies of [0, I/2); the
   // network's scalar is <x| rho |x> = |a(x)|^2 (times 2^-n unnormalised).
   bool density = false;
+  // Graphical-model form: an index may be held by more than two tensors.
+  bool gm = false;
 };
 
 // Builds the network; returns an empty string on success, else a message.
@@ -64,6 +78,13 @@ std::string build_network(int n, int p, const int32_t* edges, int m,
 // The density form of an amplitude network: same vertices, every edge of
 // dimension 4 (ket bit i, bra bit i + I).
 Network density_network(const Network& amplitude);
+
+// The graphical-model form of the same circuit: n * p variables z_q^(l)
+// (index (l - 1) * n + q), p * m ZZ factors (layer-major, edge order) then
+// p * n mixer factors (layer-major, qubit order).  Same validation and the
+// same amplitude as build_network.
+std::string build_gm_network(int n, int p, const int32_t* edges, int m, const double* gamma, const double* beta,
+                             Network* out);
 
 // Index sets of every leaf (gate) tensor, in leg-slot order, absorbed legs
 // dropped.

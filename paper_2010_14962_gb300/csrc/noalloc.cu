@@ -93,6 +93,7 @@ extern "C" qtn_status qtn_contract_amplitudes_noalloc(const qtn_plan_t* plan, co
   dp.n_pro_steps = (int)pg.prologue.size();
   dp.pro_arena_elems = pg.pro_arena_elems;
   dp.exec = pv.lane ? Executor::Lane : Executor::Block;
+  dp.density = pg.density ? 1 : 0;
   ExecShape sh;
   if (!exec_shape(dp, arith, nx, S, &sh))
     return internal::set_error(QTN_ERR_UNSUPPORTED, "the plan's per-slice working set does not fit in shared memory");
@@ -111,6 +112,7 @@ extern "C" qtn_status qtn_contract_amplitudes_noalloc(const qtn_plan_t* plan, co
   const size_t o_gl = take(bytes_of(pg.gate_layer));
   const size_t o_gi = take(bytes_of(pg.gate_in_h));
   const size_t o_go = take(bytes_of(pg.gate_out_kind));
+  const size_t o_gk = take(bytes_of(pg.gate_kind));
   const size_t o_ga = take(sizeof(double) * pv.p);
   const size_t o_be = take(sizeof(double) * pv.p);
   const size_t o_lt = take((size_t)nx * pg.leaf_elems * elem);
@@ -137,6 +139,7 @@ extern "C" qtn_status qtn_contract_amplitudes_noalloc(const qtn_plan_t* plan, co
                 {o_gl, pg.gate_layer.data(), bytes_of(pg.gate_layer)},
                 {o_gi, pg.gate_in_h.data(), bytes_of(pg.gate_in_h)},
                 {o_go, pg.gate_out_kind.data(), bytes_of(pg.gate_out_kind)},
+                {o_gk, pg.gate_kind.data(), bytes_of(pg.gate_kind)},
                 {o_ga, pv.gamma, sizeof(double) * pv.p},
                 {o_be, pv.beta, sizeof(double) * pv.p}};
   for (const Piece& pc : pieces) {
@@ -157,13 +160,14 @@ extern "C" qtn_status qtn_contract_amplitudes_noalloc(const qtn_plan_t* plan, co
   dp.gate_layer = reinterpret_cast<const int8_t*>(base + o_gl);
   dp.gate_in_h = reinterpret_cast<const int8_t*>(base + o_gi);
   dp.gate_out_kind = reinterpret_cast<const int8_t*>(base + o_go);
+  dp.gate_kind = reinterpret_cast<const int8_t*>(base + o_gk);
   dp.gamma = reinterpret_cast<const double*>(base + o_ga);
   dp.beta = reinterpret_cast<const double*>(base + o_be);
   LaunchBuffers buf;
   buf.leaf_tables = base + o_lt;
   buf.partials = reinterpret_cast<Partial*>(base + o_pa);
   buf.err = reinterpret_cast<int*>(base + o_err);
-  const double scale = std::pow(2.0, -0.5 * pv.n);
+  const double scale = std::pow(2.0, (pg.density ? -1.0 : -0.5) * pv.n);
   e = launch_contraction(dp, arith, d_x, nx, 0, S, buf, sh, scale, reinterpret_cast<double2*>(d_out), nullptr, nullptr,
                          stream);
   if (e != cudaSuccess)

@@ -41,9 +41,14 @@ namespace {
 // With `min_degree` the index whose merged bag is smallest is taken (no fill
 // computation: a cheap estimate); `bag_sizes` (optional) receives |A u B| of
 // every merge.
+std::string eliminate_hyper(const Network& net, const std::vector<char>& is_cut,
+                            const std::vector<int>* given_order, Plan* plan, Cost* cost, bool min_degree,
+                            std::vector<int>* bag_sizes);
+
 std::string eliminate(const Network& net, const std::vector<char>& is_cut,
                       const std::vector<int>* given_order, Plan* plan, Cost* cost, bool min_degree = false,
                       std::vector<int>* bag_sizes = nullptr) {
+  if (net.gm) return eliminate_hyper(net, is_cut, given_order, plan, cost, min_degree, bag_sizes);
   const int I = (int)net.indices.size();
   const int L = (int)net.gates.size();
   const int W = (I + 63) / 64;
@@ -181,6 +186,160 @@ std::string eliminate(const Network& net, const std::vector<char>& is_cut,
   }
   // Every remaining live tensor is a scalar (one per connected component,
   // plus leaves whose legs were all cut): multiply them together.
+  std::vector<int> rest;
+  for (int t = 0; t < (int)T.size(); ++t)
+    if (alive_t[t]) rest.push_back(t);
+  int acc = rest[0];
+  for (size_t i = 1; i < rest.size(); ++i) acc = merge(acc, rest[i]);
+
+  if (cost) {
+    cost->width = width;
+    cost->max_rank = max_rank;
+    cost->macs = macs;
+    cost->peak_elems = peak;
+  }
+  if (plan) {
+    plan->n_indices = I;
+    plan->n_leaves = L;
+    plan->tensors.resize(T.size());
+    for (size_t t = 0; t < T.size(); ++t) plan->tensors[t] = T[t].list();
+    plan->width = width;
+    plan->max_rank = max_rank;
+    plan->macs = macs;
+    plan->peak_elems = peak;
+  }
+  return "";
+}
+
+// The same elimination when an index may be held by more than two tensors
+// (graphical-model form: a variable shared by the diagonal gates of its
+// layer).  Eliminating index e merges all tensors that hold it, two at a
+// time (lowest ids first); a merge sums every index no other live tensor
+// holds, so e is summed by the last merge.  Min-fill counts the pairs of
+// e's neighbours that are not yet adjacent.
+std::string eliminate_hyper(const Network& net, const std::vector<char>& is_cut,
+                            const std::vector<int>* given_order, Plan* plan, Cost* cost, bool min_degree,
+                            std::vector<int>* bag_sizes) {
+  const int I = (int)net.indices.size();
+  const int L = (int)net.gates.size();
+  const int W = (I + 63) / 64;
+  std::vector<Bits> T;
+  T.reserve(3 * L);
+  std::vector<std::vector<int>> hold(I);
+  for (int g = 0; g < L; ++g) {
+    Bits b(I);
+    for (int s = 0; s < kMaxLegs; ++s) {
+      const int e = net.gates[g].leg[s];
+      if (e >= 0 && !is_cut[e] && !b.get(e)) {
+        b.set(e);
+        hold[e].push_back(g);
+      }
+    }
+    T.push_back(std::move(b));
+  }
+  std::vector<char> alive_i(I, 0);
+  int n_alive = 0;
+  for (int e = 0; e < I; ++e)
+    if (!is_cut[e]) {
+      if (hold[e].size() < 2) return "an index is held by fewer than two tensors";
+      alive_i[e] = 1;
+      n_alive++;
+    }
+  std::vector<int> rank(L);
+  for (int g = 0; g < L; ++g) rank[g] = T[g].count();
+  std::vector<Bits> adj(I, Bits(I));
+  for (int g = 0; g < L; ++g)
+    for (int u : T[g].list())
+      for (int j = 0; j < W; ++j) adj[u].w[j] |= T[g].w[j];
+  std::vector<char> alive_t(L, 1);
+  int width = 0, max_rank = 0;
+  double macs = 0, live = 0, peak = 0;
+  for (int g = 0; g < L; ++g) {
+    live += std::ldexp(1.0, rank[g]);
+    max_rank = std::max(max_rank, rank[g]);
+  }
+  peak = live;
+  if (plan) {
+    plan->merges.clear();
+    plan->order.clear();
+  }
+
+  auto merge = [&](int t1, int t2) {
+    Bits C(I);
+    int u_size = 0;
+    for (int j = 0; j < W; ++j) {
+      C.w[j] = T[t1].w[j] | T[t2].w[j];
+      u_size += __builtin_popcountll(C.w[j]);
+    }
+    const int c = (int)T.size();
+    for (int u : C.list()) {
+      std::vector<int>& h = hold[u];
+      h.erase(std::remove_if(h.begin(), h.end(), [&](int t) { return t == t1 || t == t2; }), h.end());
+      if (h.empty()) {  // only the merged tensor holds u: summed here
+        C.clear(u);
+        alive_i[u] = 0;
+        n_alive--;
+      } else {
+        h.push_back(c);
+      }
+    }
+    const int rc = C.count();
+    if (bag_sizes) bag_sizes->push_back(u_size);
+    width = std::max(width, u_size);
+    max_rank = std::max(max_rank, rc);
+    macs += std::ldexp(1.0, u_size);
+    live += std::ldexp(1.0, rc);
+    peak = std::max(peak, live);
+    live -= std::ldexp(1.0, rank[t1]) + std::ldexp(1.0, rank[t2]);
+    for (int u : C.list())
+      for (int j = 0; j < W; ++j) adj[u].w[j] |= C.w[j];
+    alive_t[t1] = alive_t[t2] = 0;
+    alive_t.push_back(1);
+    rank.push_back(rc);
+    T.push_back(std::move(C));
+    if (plan) plan->merges.push_back({t1, t2, c});
+    return c;
+  };
+
+  size_t order_pos = 0;
+  Bits nb(I);
+  while (n_alive > 0) {
+    int best = -1;
+    if (given_order) {
+      while (order_pos < given_order->size() && !alive_i[(*given_order)[order_pos]]) order_pos++;
+      if (order_pos == given_order->size()) return "order does not cover every non-cut index";
+      best = (*given_order)[order_pos++];
+    } else {
+      long best_fill = std::numeric_limits<long>::max();
+      int best_size = 1 << 30;
+      for (int e = 0; e < I; ++e) {
+        if (!alive_i[e]) continue;
+        for (int j = 0; j < W; ++j) nb.w[j] = 0;
+        for (int t : hold[e])
+          for (int j = 0; j < W; ++j) nb.w[j] |= T[t].w[j];
+        const int size = nb.count();
+        long fill = 0;
+        if (!min_degree) {
+          nb.clear(e);
+          for (int u : nb.list()) {
+            for (int j = 0; j < W; ++j) fill += __builtin_popcountll(nb.w[j] & ~adj[u].w[j]);
+            if (fill / 2 > best_fill) break;
+          }
+          fill /= 2;
+        }
+        if (fill < best_fill || (fill == best_fill && size < best_size)) {
+          best_fill = fill;
+          best_size = size;
+          best = e;
+        }
+      }
+    }
+    if (plan) plan->order.push_back(best);
+    std::vector<int> h = hold[best];
+    std::sort(h.begin(), h.end());
+    int acc = h[0];
+    for (size_t i = 1; i < h.size(); ++i) acc = merge(acc, h[i]);
+  }
   std::vector<int> rest;
   for (int t = 0; t < (int)T.size(); ++t)
     if (alive_t[t]) rest.push_back(t);

@@ -66,7 +66,7 @@ std::vector<int> cut_classes(const Network& net, const std::vector<int>& cuts, i
   // The in and out segment of a wire through a diagonal gate (ket slots w,
   // 2 + w; in the density form also the bra slots 4 + w, 6 + w).
   for (const Gate& g : net.gates)
-    for (int d = 0; d < (net.density ? 8 : 4); d += 4)
+    for (int d = 0; d < (g.kind != GATE_ZZ ? 0 : net.density ? 8 : 4); d += 4)
       for (int w = 0; w < 2; ++w) {
         if (g.out_kind[w] != OUT_PLAIN || g.leg[d + w] < 0 || g.leg[d + 2 + w] < 0) continue;
         int a = cut_no[g.leg[d + w]], b = cut_no[g.leg[d + 2 + w]];
@@ -156,8 +156,12 @@ std::string compile_program(const Network& net, const Plan& plan_in, const Progr
     const Set& A = full[mg.a];
     const Set& B = full[mg.b];
     Canon& c = canon[j];
+    // Shared real indices are summed unless the result keeps them (an index
+    // held by a third tensor, graphical-model form): those are batch bits.
     Set shared = set_and(A, B);
-    for (int x : shared) (x < I ? c.k : c.b).push_back(x);
+    const Set& kept = plan.tensors[mg.c];
+    for (int x : shared)
+      (x < I && !std::binary_search(kept.begin(), kept.end(), x) ? c.k : c.b).push_back(x);
     c.m = set_minus(A, B);
     c.n = set_minus(B, A);
     Set vC = set_or(set_minus(A, c.k), set_minus(B, c.k));
@@ -414,6 +418,7 @@ std::string compile_program(const Network& net, const Plan& plan_in, const Progr
   pg.gate_layer.resize(net.gates.size());
   pg.gate_in_h.resize(2 * net.gates.size());
   pg.gate_out_kind.resize(2 * net.gates.size());
+  pg.gate_kind.resize(net.gates.size());
   for (size_t g = 0; g < net.gates.size(); ++g) {
     for (int w = 0; w < 2; ++w) {
       pg.gate_q[2 * g + w] = net.gates[g].q[w];
@@ -421,6 +426,7 @@ std::string compile_program(const Network& net, const Plan& plan_in, const Progr
       pg.gate_out_kind[2 * g + w] = net.gates[g].out_kind[w];
     }
     pg.gate_layer[g] = (int8_t)net.gates[g].layer;
+    pg.gate_kind[g] = net.gates[g].kind;
   }
   *out = std::move(pg);
   return "";

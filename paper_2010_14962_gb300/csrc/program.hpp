@@ -126,6 +126,7 @@ struct Program {
   std::vector<int8_t> gate_layer;
   std::vector<int8_t> gate_in_h;     // 2 per gate
   std::vector<int8_t> gate_out_kind; // 2 per gate
+  std::vector<int8_t> gate_kind;     // GateKind per gate
 };
 
 // Lowers `plan` (merges over `net`) to a program.  Returns "" or an error.

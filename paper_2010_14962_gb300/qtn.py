@@ -65,6 +65,7 @@ def lib():
             "qtn_build_network": [ctypes.c_int, ctypes.c_int, i32p, ctypes.c_int, f64p, f64p, P(vp)],
             "qtn_network_destroy": [vp],
             "qtn_network_density": [vp, P(vp)],
+            "qtn_build_network_gm": [ctypes.c_int, ctypes.c_int, i32p, ctypes.c_int, f64p, f64p, P(vp)],
             "qtn_network_info": [vp, P(ctypes.c_int), P(ctypes.c_int)],
             "qtn_network_index": [vp, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int),
                                   P(ctypes.c_int)],
@@ -148,16 +149,23 @@ def _stream_handle(stream):
 class Network:
     """qtn_build_network: the ZZ-gate tensor network of a p-layer QAOA circuit."""
 
-    def __init__(self, n: int, edges, gamma, beta):
+    def __init__(self, n: int, edges, gamma, beta, form: str = "gates"):
+        """form: "gates" (ZZ gates as vertices, wire segments as indices) or
+        "gm" (graphical model: one index per qubit and layer, shared by the
+        diagonal gates; qtn_build_network_gm)."""
         e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
         g = np.ascontiguousarray(np.atleast_1d(np.asarray(gamma, dtype=np.float64)))
         b = np.ascontiguousarray(np.atleast_1d(np.asarray(beta, dtype=np.float64)))
         if g.shape != b.shape:
             raise ValueError("gamma and beta need the same length p")
+        if form not in ("gates", "gm"):
+            raise ValueError("form must be 'gates' or 'gm'")
         self.n, self.p = int(n), int(g.size)
+        self.form = form
+        build = lib().qtn_build_network if form == "gates" else lib().qtn_build_network_gm
         h = ctypes.c_void_p()
-        _check(lib().qtn_build_network(self.n, self.p, _ptr(e, ctypes.c_int32), len(e), _ptr(g, ctypes.c_double),
-                                       _ptr(b, ctypes.c_double), ctypes.byref(h)))
+        _check(build(self.n, self.p, _ptr(e, ctypes.c_int32), len(e), _ptr(g, ctypes.c_double),
+                     _ptr(b, ctypes.c_double), ctypes.byref(h)))
         self._h = h
 
     def density(self) -> "Network":
@@ -165,7 +173,7 @@ class Network:
         h = ctypes.c_void_p()
         _check(lib().qtn_network_density(self._h, ctypes.byref(h)))
         d = Network.__new__(Network)
-        d.n, d.p, d._h = self.n, self.p, h
+        d.n, d.p, d._h, d.form = self.n, self.p, h, self.form
         d.is_density = True
         return d
 

@@ -40,9 +40,22 @@ def gate_entry(gate, gamma, beta, x, v):
     return total
 
 
+def gm_factor_entry(gate, gamma, beta, x, v):
+    """Graphical-model factors: the ZZ phase exp(-i g s0 s1) on z_i, z_j, or
+    <z_out|RX(2b)|z_in> with z_out = x_q in the last layer."""
+    l = gate["layer"]
+    if gate["kind"] == 1:
+        s = (1 - 2 * v[0]) * (1 - 2 * v[1])
+        return complex(math.cos(gamma[l]), -s * math.sin(gamma[l]))
+    out = v[1] if v[1] >= 0 else int(x[gate["q"][0]])
+    return math.cos(beta[l]) if out == v[0] else -1j * math.sin(beta[l])
+
+
 def leaf_value(desc, gate, gamma, beta, x, v):
     """A leaf's entry: the gate at ket legs v[0..3]; in the density form
     (dimension-4 edges) times the conjugate gate at the bra legs v[4..7]."""
+    if gate.get("kind", 0) != 0:
+        return gm_factor_entry(gate, gamma, beta, x, v)
     val = gate_entry(gate, gamma, beta, x, v[:4])
     if desc.get("density"):
         val *= np.conj(gate_entry(gate, gamma, beta, x, v[4:]))

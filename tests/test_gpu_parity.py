@@ -410,3 +410,46 @@ def test_density_form_every_executor(gpu, n, p, k, seed):
     for x, pr in zip(xs, probs):  # host entry point, per-slice program
         assert abs(dplan.contract_amplitude(x, "fp64") - pr) < 1e-10 * pr
     assert checked >= 4
+
+
+@pytest.mark.parametrize("n,p,k,seed,nx", [(16, 1, 2, 1, 3), (40, 2, 8, 2, 2)])
+def test_graphical_model_every_executor(gpu, n, p, k, seed, nx):
+    # Graphical-model form (one index per qubit and layer, shared by the
+    # diagonal gates) on every executor: the same amplitudes as the oracle.
+    # complex64: relative bound 1e-4 (its per-slice sums are not computed).
+    inst = I.qaoa_instance(n, p, seed)
+    net = qtn.Network(n, inst.edges, inst.gamma, inst.beta, form="gm")
+    plan = qtn.Plan(net, k=k)
+    gates = qtn.Plan(qtn.Network(n, inst.edges, inst.gamma, inst.beta), k=10 if n >= 40 else k)
+    xs = I.bitstrings(n, nx, seed + 40)
+    refs = [O.tn_amplitude(n, inst.edges, inst.gamma, inst.beta, x, cuts=gates.cut_names(), threads=16).value
+            for x in xs]
+    d = plan.describe()
+    checked = set()
+    for name in d["programs"]:
+        if name == d["executor"]:
+            continue
+        for prec in _executor_precisions(name):
+            plan.select_executor(name, prec, nx)
+            try:
+                got = device_amplitudes(plan, xs, prec)
+            except qtn.QTNError as e:
+                assert e.status == 6 and "shared memory" in str(e), (name, prec, str(e))
+                continue
+            tol = 1e-4 if prec == "fp32" else 1e-10
+            for g, r in zip(got, refs):
+                assert rel(g, r) < tol, (name, prec, rel(g, r))
+            checked.add((name, prec))
+    for x, r in zip(xs, refs):  # per-slice program through the host entry point
+        assert rel(plan.contract_amplitude(x, "fp64"), r) < 1e-10
+    assert any(nm.startswith("level") for nm, _ in checked)
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-10), ("fp32x2", 1e-10)])
+def test_graphical_model_n80(gpu, config80, prec, tol):
+    # The n = 80 workload in graphical-model form (8 cuts): the benchmark's
+    # eight amplitudes.
+    inst, plan, xs, refs = config80
+    gm = qtn.Plan(qtn.Network(80, inst.edges, inst.gamma, inst.beta, form="gm"), k=8)
+    got = device_amplitudes(gm, xs, prec)
+    assert np.max(np.abs(got - refs) / np.abs(refs)) < tol

@@ -337,3 +337,67 @@ def test_plan_cost_matches_counter_and_cap():
     with pytest.raises(qtn.QTNError) as ei:
         qtn.Plan(net, cuts=plan.cuts, max_slice_bytes=1024)
     assert ei.value.status == 3
+
+
+def _gm_restricted_path_sum(n, edges, gamma, beta, x, fixed):
+    """Brute force over z (p = 1): 2^{-n/2} sum_z prod_E exp(-i g s_i s_j)
+    prod_q <x_q|RX(2b)|z_q>, with the variables in `fixed` held."""
+    g, b = gamma[0], beta[0]
+    total = 0j
+    for z in range(1 << n):
+        if any(((z >> q) & 1) != v for q, v in fixed.items()):
+            continue
+        s = [1 - 2 * ((z >> q) & 1) for q in range(n)]
+        ph = sum(s[i] * s[j] for i, j in edges)
+        t = np.exp(-1j * g * ph)
+        for q in range(n):
+            t *= np.cos(b) if ((z >> q) & 1) == int(x[q]) else -1j * np.sin(b)
+        total += t
+    return total * 2.0 ** (-n / 2)
+
+
+def test_graphical_model_slices_brute_force():
+    # Graphical-model form (diagonal gates share one index per qubit and
+    # layer): a slice fixes the cut variables; its value is the path sum
+    # restricted to them (brute force), and the slices add up to a(x).
+    n, p, k = 8, 1, 3
+    inst = I.qaoa_instance(n, p, 2)
+    net = qtn.Network(n, inst.edges, inst.gamma, inst.beta, form="gm")
+    plan = qtn.Plan(net, k=k)
+    d = plan.describe()
+    assert d["gm"] is True and len(d["cuts"]) == k
+    x = I.bitstrings(n, 1, 2)[0]
+    cut_q = [net.index(int(c))[0] for c in d["cuts"]]
+    want = np.array([_gm_restricted_path_sum(n, inst.edges, inst.gamma, inst.beta, x,
+                                             {q: (s >> j) & 1 for j, q in enumerate(cut_q)})
+                     for s in range(1 << k)])
+    sv = O.statevector(n, inst.edges, inst.gamma, inst.beta)
+    assert abs(want.sum() - sv[O.bits_to_int(x)]) < 1e-12
+    scale = 2.0 ** (-n / 2)
+    for name in d["programs"]:
+        vals = E.run_program(d, name, inst.gamma, inst.beta, x)
+        got = np.zeros(1 << k, dtype=complex)
+        for s_id, v in vals.items():
+            got[s_id] = v * scale
+        assert np.max(np.abs(got - want)) < 1e-13, name
+
+
+@pytest.mark.parametrize("n,p,k,seed", [(12, 2, 4, 6), (16, 1, 2, 1), (40, 2, 8, 2)])
+def test_graphical_model_programs_match_oracle(n, p, k, seed):
+    # Every compiled program of a graphical-model plan (hyperedge merges keep
+    # a shared index as a batch bit until its last holder) gives the
+    # oracle's amplitude; its width is below the gate network's.
+    inst = I.qaoa_instance(n, p, seed)
+    gm = qtn.Network(n, inst.edges, inst.gamma, inst.beta, form="gm")
+    gates = qtn.Network(n, inst.edges, inst.gamma, inst.beta)
+    plan = qtn.Plan(gm, k=k)
+    gplan = qtn.Plan(gates, k=max(k, 10) if p == 2 and n >= 40 else k)
+    assert plan.cost()["width"] < gplan.cost()["width"] or plan.cost()["log2_flops"] < gplan.cost()["log2_flops"]
+    x = I.bitstrings(n, 1, seed)[0]
+    ref = O.tn_amplitude(n, inst.edges, inst.gamma, inst.beta, x, cuts=gplan.cut_names(), threads=8).value
+    d = plan.describe()
+    scale = 2.0 ** (-n / 2)
+    for name in d["programs"]:
+        vals = E.run_program(d, name, inst.gamma, inst.beta, x)
+        got = sum(vals.values()) * scale
+        assert abs(got - ref) < 1e-12 * abs(ref), name
