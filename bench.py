@@ -135,13 +135,13 @@ def profiled_traffic(prec: str):
     return e.get("dram_bytes_per_launch")
 
 
-def setup_workload(rank: int):
+def setup_workload(rank: int, form: str = "gates"):
     from paper_2010_14962_gb300 import instances as I
     from paper_2010_14962_gb300 import qtn
 
     w = WORKLOAD
     inst = I.qaoa_instance(w["n"], w["p"], w["seed"])
-    net = qtn.Network(w["n"], inst.edges, inst.gamma, inst.beta)
+    net = qtn.Network(w["n"], inst.edges, inst.gamma, inst.beta, form=form)
     plan = qtn.Plan(net, k=w["k"])
     xs = I.bitstrings(w["n"], w["bitstrings"], w["seed"] + 1000 * rank)
     return inst, net, plan, xs
@@ -158,7 +158,7 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as dist
 
         dist.init_process_group("nccl")
-    inst, net, plan, xs = setup_workload(rank)
+    inst, net, plan, xs = setup_workload(rank, args.form)
     nx = xs.shape[0]
     cost = plan.cost()
     sweep = None
@@ -366,6 +366,10 @@ def cpu_baseline(seconds: float, plan_bundle=None):
     from oracle import oracle as O
 
     inst, net, plan, xs = plan_bundle or setup_workload(0)
+    if WORKLOAD.get("form") == "gm":  # the oracle slices the gate network: its own 16-cut plan
+        from paper_2010_14962_gb300 import qtn
+
+        plan = qtn.Plan(qtn.Network(WORKLOAD["n"], inst.edges, inst.gamma, inst.beta), k=16)
     cuts = plan.cut_names()
     cores = os.cpu_count() or 1
     S = 2 ** len(cuts)
@@ -597,9 +601,16 @@ def main():
     ap.add_argument("--executor", default=None, help="force an executor (default: autotuned)")
     ap.add_argument("--workload", default="qaoa80_p1_k16", choices=["qaoa80_p1_k16", "uneven64"],
                     help="uneven64: 64 independent jobs of different plans in one launch sequence")
+    ap.add_argument("--form", default="gates", choices=["gates", "gm"],
+                    help="network form of the n=80 workload: the paper's gate network (16 cuts) or the "
+                         "graphical model with shared diagonal-gate indices (8 cuts)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.form == "gm":
+        global METRIC
+        WORKLOAD.update(name="qaoa80_p1_gm_k8", k=8, form="gm")
+        METRIC = "amplitudes/sec, n=80 QAOA p=1, graphical-model network, 8 cut variables (256 slices)"
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
     local_rank = int(os.environ.get("LOCAL_RANK", 0))
