@@ -262,18 +262,27 @@ struct qtn_plan {
     dev_allocs.push_back(ga);
     QTN_CUDA(::upload(&be, net.beta));
     dev_allocs.push_back(be);
-    DevLevel* lvls = nullptr;
-    uint32_t* ost = nullptr;
+    DevLevel *lvls = nullptr, *plvls = nullptr;
+    uint32_t *ost = nullptr, *post = nullptr;
     if (!pg.levels.empty()) {
       QTN_CUDA(::upload(&lvls, pg.levels));
       dev_allocs.push_back(lvls);
       QTN_CUDA(::upload(&ost, pg.out_start));
       dev_allocs.push_back(ost);
     }
+    if (!pg.pro_levels.empty()) {
+      QTN_CUDA(::upload(&plvls, pg.pro_levels));
+      dev_allocs.push_back(plvls);
+      QTN_CUDA(::upload(&post, pg.pro_out_start));
+      dev_allocs.push_back(post);
+    }
     DeviceProgram& d = sl.dprog;
     d.levels = lvls;
     d.out_start = ost;
     d.n_levels = (int)pg.levels.size();
+    d.pro_levels = plvls;
+    d.pro_out_start = post;
+    d.n_pro_levels = (int)pg.pro_levels.size();
     d.block_threads = sl.threads;
     d.blocks_per_sm = sl.blocks_per_sm;
     d.density = pg.density ? 1 : 0;
@@ -1083,8 +1092,12 @@ qtn_status qtn_contract_batch(const qtn_plan_t* const* plans, const uint8_t* con
                                           : block_smem_bytes((int)pg.steps.size(), (int)pg.leaves.size(),
                                                              pg.leaf_elems, pg.arena_elems, arith, 256));
     if (!pg.prologue.empty())
-      pro_smem = std::max(pro_smem, block_smem_bytes((int)pg.prologue.size(), (int)pg.leaves.size(), pg.leaf_elems,
-                                                     pg.pro_arena_elems, arith, 256));
+      pro_smem = std::max(pro_smem, level && !pg.pro_levels.empty()
+                                        ? level_smem_bytes((int)pg.prologue.size(), (int)pg.pro_levels.size(),
+                                                           (int)pg.leaves.size(), pg.leaf_elems,
+                                                           pg.pro_arena_elems | 1u, 1, arith, kMultiLevelThreads)
+                                        : block_smem_bytes((int)pg.prologue.size(), (int)pg.leaves.size(),
+                                                           pg.leaf_elems, pg.pro_arena_elems, arith, 256));
   }
   for (int oj : order) {
     jobs[oj].first_chunk = (uint32_t)chunks.size();
@@ -1140,6 +1153,9 @@ qtn_status qtn_contract_batch(const qtn_plan_t* const* plans, const uint8_t* con
     J.levels = d.levels;
     J.out_start = d.out_start;
     J.n_levels = d.n_levels;
+    J.pro_levels = level ? d.pro_levels : nullptr;
+    J.pro_out_start = level ? d.pro_out_start : nullptr;
+    J.n_pro_levels = level ? d.n_pro_levels : 0;
     J.log2_items = jh[j].log2_items;
     J.arena_stride = d.arena_elems | 1u;
     J.density = d.density;

@@ -761,8 +761,30 @@ __device__ __forceinline__ void level_unit(const DevStep& st, uint32_t o0, uint3
 // Units per step for the level executor's unit size 2^UL.
 template <int UL>
 __device__ __forceinline__ uint32_t level_units(const DevStep& st) {
-  const int rc = st.ma + st.nb + st.bb;
+  const int rc = st.ma + st.nb + st.bb + ((st.flags & STEP_ROOT) ? st.kb : 0);
   return 1u << (rc > UL ? rc - UL : 0);
+}
+
+// The root of one item, split over its summed index too: entries e = (o, k)
+// (k fastest) for e in [e0, e0 + u); each product A[m, k, b] B[k, n, b] is
+// added to the compensated sums (the root's outputs are only summed).
+template <class V, class Ops, int UNIT>
+__device__ __forceinline__ void level_root_unit(const DevStep& st, uint32_t e0, uint32_t u, const V* __restrict__ A,
+                                                const V* __restrict__ B, double& sr, double& cr, double& si,
+                                                double& ci) {
+  const int ma = st.ma, nb = st.nb, kb = st.kb;
+#pragma unroll
+  for (uint32_t r = 0; r < (uint32_t)UNIT; ++r) {
+    if (r < u) {
+      const uint32_t e = e0 + r;
+      const uint32_t k = e & ((1u << kb) - 1u), o = e >> kb;
+      const uint32_t m = o & ((1u << ma) - 1u), n = (o >> ma) & ((1u << nb) - 1u), b = o >> (ma + nb);
+      V prod = Ops::mul(A[m + (k << ma) + (b << (ma + kb))], B[k + (n << kb) + (b << (kb + nb))]);
+      Ops::finish(prod);
+      kahan_add(sr, cr, Ops::re(prod));
+      kahan_add(si, ci, Ops::im(prod));
+    }
+  }
 }
 
 // All levels of one group of nI <= 2^log2I consecutive work items (global
@@ -777,7 +799,7 @@ template <class V, class Ops>
 __device__ __forceinline__ void level_run(const DevStep* s_steps, const uint32_t* s_out, const DevLevel* s_levels,
                                           int n_levels, const DevLeaf* s_leaves, const V* s_lt, V* s_arena,
                                           uint32_t stride, uint32_t log2I, uint64_t s0, uint32_t nI, double& sr,
-                                          double& cr, double& si, double& ci) {
+                                          double& cr, double& si, double& ci, V* g_lt = nullptr) {
   constexpr int UL = sizeof(V) == 16 ? 0 : kLevelUnitLog2;  // log2 outputs per unit
   constexpr int US = UL ? 1 : 0;                            // which unit table
   const uint32_t I = 1u << log2I;
@@ -800,11 +822,17 @@ __device__ __forceinline__ void level_run(const DevStep* s_steps, const uint32_t
       V* arena = s_arena + (size_t)item * stride;
       const V* A = (st.flags & STEP_A_LEAF) ? s_lt + leaf_offset(s_leaves[st.a], s) : arena + st.a;
       const V* B = (st.flags & STEP_B_LEAF) ? s_lt + leaf_offset(s_leaves[st.b], s) : arena + st.b;
-      V* C = arena + st.c;
-      const int rc = st.ma + st.nb + st.bb;
+      // Prologue steps may export their result into the (global) leaf table.
+      V* C = (st.flags & STEP_EXPORT) ? g_lt + s_leaves[st.c].base : arena + st.c;
+      const bool root = st.flags & STEP_ROOT;
+      const int rc = st.ma + st.nb + st.bb + (root ? st.kb : 0);
       const uint32_t ulog = rc < UL ? (uint32_t)rc : (uint32_t)UL;
       const uint32_t o0 = (uf - jbeg) << ulog;
       const uint32_t u = 1u << ulog;
+      if (root) {
+        level_root_unit<V, Ops, 1 << UL>(st, o0, u, A, B, sr, cr, si, ci);
+        continue;
+      }
       switch (st.kb) {
         case 0: level_unit<V, 1, Ops, 1 << UL>(st, o0, u, A, B, C, sr, cr, si, ci); break;
         case 1: level_unit<V, 2, Ops, 1 << UL>(st, o0, u, A, B, C, sr, cr, si, ci); break;
@@ -854,6 +882,47 @@ __global__ void __launch_bounds__(1024) level_exec_kernel(ExecParams P, LevelPar
   s_red[threadIdx.x] = Partial::make(sr, si, cr, ci);  // overlays the arenas: every level is done
   tree_reduce(s_red, T);
   if (threadIdx.x == 0) P.partials[(size_t)xi * P.blocks_per_x + bx] = s_red[0];
+}
+
+// Hoisted merges of a level-ordered program: one block of up to 1024
+// threads per bit string, one barrier per level; exported results go to the
+// bit string's leaf table in global memory.
+template <class V, class Ops>
+__device__ __forceinline__ void prologue_level_body(const DevStep* __restrict__ steps, int n_steps,
+                                                    const uint32_t* __restrict__ out_start,
+                                                    const DevLevel* __restrict__ levels, int n_levels,
+                                                    const DevLeaf* __restrict__ leaves, int n_leaves, V* g_lt,
+                                                    uint32_t leaf_elems, uint32_t arena_elems, unsigned char* smem) {
+  const LevelLayout lay = level_layout(n_steps, n_levels, n_leaves, leaf_elems, arena_elems | 1u, 1, (int)sizeof(V),
+                                       blockDim.x);
+  DevStep* s_steps = reinterpret_cast<DevStep*>(smem);
+  uint32_t* s_out = reinterpret_cast<uint32_t*>(smem + lay.out_start);
+  DevLevel* s_levels = reinterpret_cast<DevLevel*>(smem + lay.levels);
+  DevLeaf* s_leaves = reinterpret_cast<DevLeaf*>(smem + lay.leaves);
+  V* s_lt = reinterpret_cast<V*>(smem + lay.table);
+  V* s_arena = reinterpret_cast<V*>(smem + lay.arena);
+  copy_words(s_steps, steps, (size_t)n_steps * sizeof(DevStep));
+  copy_words(s_out, out_start, (size_t)n_steps * 2 * sizeof(uint32_t));
+  copy_words(s_levels, levels, (size_t)n_levels * sizeof(DevLevel));
+  copy_words(s_leaves, leaves, (size_t)n_leaves * sizeof(DevLeaf));
+  copy_words(s_lt, g_lt, (size_t)leaf_elems * sizeof(V));
+  __syncthreads();
+  double sr = 0, si = 0, cr = 0, ci = 0;  // no root among hoisted merges
+  level_run<V, Ops>(s_steps, s_out, s_levels, n_levels, s_leaves, s_lt, s_arena, arena_elems | 1u, 0, 0, 1, sr, cr,
+                    si, ci, g_lt);
+}
+
+template <class V, class Ops = CplxOps<V>>
+__global__ void __launch_bounds__(1024) prologue_level_kernel(const DevStep* __restrict__ steps, int n_steps,
+                                                              const uint32_t* __restrict__ out_start,
+                                                              const DevLevel* __restrict__ levels, int n_levels,
+                                                              const DevLeaf* __restrict__ leaves, int n_leaves,
+                                                              void* leaf_tables, uint32_t leaf_elems,
+                                                              uint32_t arena_elems) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  V* g_lt = static_cast<V*>(leaf_tables) + (size_t)blockIdx.x * leaf_elems;
+  prologue_level_body<V, Ops>(steps, n_steps, out_start, levels, n_levels, leaves, n_leaves, g_lt, leaf_elems,
+                              arena_elems, smem);
 }
 
 // -------------------------------------------------------------- prologue --
@@ -933,12 +1002,16 @@ __global__ void multi_leaf_kernel(const JobDesc* __restrict__ jobs, int njobs) {
 }
 
 template <class V, class Ops = CplxOps<V>>
-__global__ void __launch_bounds__(256) multi_prologue_kernel(const JobDesc* __restrict__ jobs) {
+__global__ void __launch_bounds__(1024) multi_prologue_kernel(const JobDesc* __restrict__ jobs) {
   extern __shared__ __align__(16) unsigned char smem[];
   const JobDesc& J = jobs[blockIdx.x];
   if (J.n_pro_steps == 0) return;
-  prologue_body<V, Ops>(J.pro_steps, J.n_pro_steps, J.leaves, J.n_leaves, static_cast<V*>(J.leaf_table),
-                        J.leaf_elems, J.pro_arena_elems, smem);
+  if (J.n_pro_levels > 0)
+    prologue_level_body<V, Ops>(J.pro_steps, J.n_pro_steps, J.pro_out_start, J.pro_levels, J.n_pro_levels, J.leaves,
+                                J.n_leaves, static_cast<V*>(J.leaf_table), J.leaf_elems, J.pro_arena_elems, smem);
+  else
+    prologue_body<V, Ops>(J.pro_steps, J.n_pro_steps, J.leaves, J.n_leaves, static_cast<V*>(J.leaf_table),
+                          J.leaf_elems, J.pro_arena_elems, smem);
 }
 
 template <class V, class Ops = CplxOps<V>>
@@ -1172,7 +1245,15 @@ bool exec_shape_typed(const DeviceProgram& prog, int nx, uint64_t slices_per_x, 
     sh.smem = L.total;
     if (!shape_for_kernel(block_exec_kernel<V, false, Ops>, sh.threads, sh.smem, &occ)) return false;
   }
-  if (prog.n_pro_steps > 0) {
+  if (prog.n_pro_steps > 0 && prog.n_pro_levels > 0) {
+    const LevelLayout PL = level_layout(prog.n_pro_steps, prog.n_pro_levels, prog.n_leaves, prog.leaf_elems,
+                                        prog.pro_arena_elems | 1u, 1, elem_bytes, kLevelPrologueThreads);
+    if (PL.total > (size_t)max_optin) return false;
+    sh.pro_smem = PL.total;
+    if (cudaFuncSetAttribute(prologue_level_kernel<V, Ops>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)PL.total) != cudaSuccess)
+      return false;
+  } else if (prog.n_pro_steps > 0) {
     const SmemLayout PL = smem_layout(prog.n_pro_steps, prog.n_leaves, prog.leaf_elems, prog.pro_arena_elems,
                                       elem_bytes, 256, false);
     if (PL.total > (size_t)max_optin) return false;
@@ -1206,7 +1287,13 @@ cudaError_t launch_typed(const DeviceProgram& prog, const uint8_t* d_x, int nx, 
                                                  static_cast<V*>(buf.leaf_tables));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if (prog.n_pro_steps > 0) {
+  if (prog.n_pro_steps > 0 && prog.n_pro_levels > 0) {
+    prologue_level_kernel<V, Ops><<<nx, kLevelPrologueThreads, shape.pro_smem, stream>>>(
+        prog.pro_steps, prog.n_pro_steps, prog.pro_out_start, prog.pro_levels, prog.n_pro_levels, prog.leaves,
+        prog.n_leaves, buf.leaf_tables, prog.leaf_elems, prog.pro_arena_elems);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  } else if (prog.n_pro_steps > 0) {
     prologue_kernel<V, Ops><<<nx, 256, shape.pro_smem, stream>>>(prog.pro_steps, prog.n_pro_steps, prog.leaves,
                                                                  prog.n_leaves, buf.leaf_tables, prog.leaf_elems,
                                                                  prog.pro_arena_elems);
@@ -1274,7 +1361,7 @@ cudaError_t launch_multi_typed(const JobDesc* d_jobs, int njobs, uint32_t total_
     return cudaErrorInvalidConfiguration;
   if ((e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned), stream)) != cudaSuccess) return e;
   multi_leaf_kernel<V><<<total_leaves, 32, 0, stream>>>(d_jobs, njobs);
-  multi_prologue_kernel<V, Ops><<<njobs, 256, pro_smem, stream>>>(d_jobs);
+  multi_prologue_kernel<V, Ops><<<njobs, level ? kMultiLevelThreads : 256, pro_smem, stream>>>(d_jobs);
   const unsigned grid = (unsigned)std::min<uint64_t>((uint64_t)sms * occ, n_chunks);
   if (level)
     multi_level_kernel<V, Ops><<<grid, threads, exec_smem, stream>>>(d_jobs, d_chunks, n_chunks, d_counter,

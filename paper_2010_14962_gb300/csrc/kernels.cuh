@@ -52,6 +52,9 @@ struct DeviceProgram {
   const DevLevel* levels = nullptr;
   const uint32_t* out_start = nullptr;
   int n_levels = 0;
+  const DevLevel* pro_levels = nullptr;  // level-ordered prologue (1024-thread blocks)
+  const uint32_t* pro_out_start = nullptr;
+  int n_pro_levels = 0;
   int block_threads = 256;  // threads per block (512 or 1024)
   int blocks_per_sm = 1;    // shared memory is sized for this many blocks per SM
 };
@@ -115,6 +118,9 @@ struct JobDesc {
   const DevLevel* levels;
   const uint32_t* out_start;
   int n_levels;
+  const DevLevel* pro_levels;
+  const uint32_t* pro_out_start;
+  int n_pro_levels;
   int log2_items;          // items per block = 2^log2_items; chunks are multiples of it
   uint32_t arena_stride;   // elements between item arenas
   int density;             // leaves are G (x) conj(G) (density form)
@@ -130,8 +136,9 @@ size_t block_smem_bytes(int n_steps, int n_leaves, uint32_t leaf_elems, uint32_t
 // Shared memory of the level executor for a program and `items` items per block.
 size_t level_smem_bytes(int n_steps, int n_levels, int n_leaves, uint32_t leaf_elems, uint32_t arena_stride,
                         int items, Arith a, int threads);
-// Threads per block of the multi-job level executor.
+// Threads per block of the multi-job level executor and of level prologues.
 constexpr int kMultiLevelThreads = 1024;
+constexpr int kLevelPrologueThreads = 1024;
 
 // Enqueues the multi-job sequence (leaf tables, prologues, persistent
 // executor over `n_chunks` chunks, per-job finalisation into d_out[njobs]).

@@ -287,30 +287,32 @@ std::string compile_program(const Network& net, const Plan& plan_in, const Progr
   }
   pg.leaf_elems = leaf_off;
 
-  // Item steps by level (stable: DFS order within a level).
-  std::vector<int> item_order;
-  for (int j : order)
-    if (!pro[j]) item_order.push_back(j);
+  // Item steps and prologue steps by level (stable: DFS order within a
+  // level).  For the items, leaves and hoisted results are level 0.
+  std::vector<int> item_order, pro_order;
+  for (int j : order) (pro[j] ? pro_order : item_order).push_back(j);
   std::vector<int> level_of(plan.merges.size(), 0);
   if (opt.levels) {
-    std::vector<int> lev_t(T, 0);  // leaves and hoisted results: level 0
-    for (int j : item_order) {
-      const Merge& mg = plan.merges[j];
-      auto lv = [&](int t) { return (is_leaf(t) || exported[t]) ? 0 : lev_t[t]; };
-      lev_t[mg.c] = 1 + std::max(lv(mg.a), lv(mg.b));
-      level_of[j] = lev_t[mg.c];
+    std::vector<int> lev_t(T, 0);
+    for (const std::vector<int>* seq : {&pro_order, &item_order}) {
+      for (int j : *seq) {
+        const Merge& mg = plan.merges[j];
+        auto lv = [&](int t) { return (is_leaf(t) || (!pro[j] && exported[t])) ? 0 : lev_t[t]; };
+        lev_t[mg.c] = 1 + std::max(lv(mg.a), lv(mg.b));
+        level_of[j] = lev_t[mg.c];
+      }
     }
-    std::stable_sort(item_order.begin(), item_order.end(),
-                     [&](int x, int y) { return level_of[x] < level_of[y]; });
+    for (std::vector<int>* seq : {&pro_order, &item_order})
+      std::stable_sort(seq->begin(), seq->end(), [&](int x, int y) { return level_of[x] < level_of[y]; });
   }
 
   std::vector<uint32_t> where(T, 0);
   auto emit = [&](bool prologue_pass, bool c_reuses_a, std::vector<DevStep>* out, uint32_t* arena_high,
                   double* macs) -> std::string {
     Arena arena;
-    const bool by_level = opt.levels && !prologue_pass;
+    const bool by_level = opt.levels;
     std::vector<uint32_t> level_release;  // inputs freed when their level ends
-    const std::vector<int>& seq = prologue_pass ? order : item_order;
+    const std::vector<int>& seq = prologue_pass ? pro_order : item_order;
     for (size_t si = 0; si < seq.size(); ++si) {
       const int j = seq[si];
       if ((bool)pro[j] != prologue_pass) continue;
@@ -394,24 +396,33 @@ std::string compile_program(const Network& net, const Plan& plan_in, const Progr
   if (!err.empty()) return err;
   if (pg.prologue.empty()) pg.pro_arena_elems = 0;
   if (opt.levels) {
-    pg.out_start.assign(2 * pg.steps.size(), 0);
-    for (size_t i = 0; i < pg.steps.size(); ++i) {
-      const DevStep& st = pg.steps[i];
-      const int rc = st.ma + st.nb + st.bb;
-      if (i == 0 || level_of[item_order[i]] != level_of[item_order[i - 1]]) {
-        if (pg.levels.size() >= 0xffff) return "too many levels";
-        pg.levels.push_back(DevLevel{(uint16_t)i, 0, {0, 0}});
+    auto tables = [&](const std::vector<DevStep>& steps, const std::vector<int>& seq, std::vector<DevLevel>* levels,
+                      std::vector<uint32_t>* out_start) -> std::string {
+      out_start->assign(2 * steps.size(), 0);
+      for (size_t i = 0; i < steps.size(); ++i) {
+        const DevStep& st = steps[i];
+        // The root's outputs are summed, not stored, so its (output, k) pairs
+        // are independent: it is split over k as well.
+        const int rc = st.ma + st.nb + st.bb + ((st.flags & STEP_ROOT) ? st.kb : 0);
+        if (i == 0 || level_of[seq[i]] != level_of[seq[i - 1]]) {
+          if (levels->size() >= 0xffff) return "too many levels";
+          levels->push_back(DevLevel{(uint16_t)i, 0, {0, 0}});
+        }
+        DevLevel& lv = levels->back();
+        for (int u = 0; u < 2; ++u) {
+          const uint32_t units = 1u << std::max(0, rc - (u ? kLevelUnitLog2 : 0));
+          // Executors index (unit, item) pairs of a level in 32 bits, <= 32 items.
+          if ((uint64_t)lv.units[u] + units > (1ull << 26)) return "level too large";
+          (*out_start)[2 * i + u] = lv.units[u];
+          lv.units[u] += units;
+        }
+        ++lv.count;
       }
-      DevLevel& lv = pg.levels.back();
-      for (int u = 0; u < 2; ++u) {
-        const uint32_t units = 1u << std::max(0, rc - (u ? kLevelUnitLog2 : 0));
-        // Executors index (unit, item) pairs of a level in 32 bits, <= 32 items.
-        if ((uint64_t)lv.units[u] + units > (1ull << 26)) return "level too large";
-        pg.out_start[2 * i + u] = lv.units[u];
-        lv.units[u] += units;
-      }
-      ++lv.count;
-    }
+      return "";
+    };
+    err = tables(pg.steps, item_order, &pg.levels, &pg.out_start);
+    if (err.empty()) err = tables(pg.prologue, pro_order, &pg.pro_levels, &pg.pro_out_start);
+    if (!err.empty()) return err;
   }
 
   pg.gate_q.resize(2 * net.gates.size());

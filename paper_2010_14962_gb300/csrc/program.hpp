@@ -84,7 +84,8 @@ static_assert(sizeof(DevStep) == 52, "DevStep layout");
 // output units (in step order) form one flat range.  A unit is 2^u
 // consecutive outputs of a step (all of them if it has fewer), so a step of
 // rank rc has 2^max(0, rc - u) units; tables are kept for u = 0 (one output
-// per unit) and u = 2 (four).
+// per unit) and u = 2 (four).  The root step counts rc + kb: its outputs are
+// summed, so every (output, summed index) product is a unit entry of its own.
 constexpr int kLevelUnitLog2 = 2;
 constexpr int kLevelUnit = 1 << kLevelUnitLog2;
 struct DevLevel {
@@ -113,6 +114,8 @@ struct Program {
   std::vector<DevStep> steps;        // per work item
   std::vector<DevLevel> levels;      // level-ordered programs only
   std::vector<uint32_t> out_start;   // per step: first unit in its level's range, 2 per step (as DevLevel::units)
+  std::vector<DevLevel> pro_levels;  // the same for the prologue
+  std::vector<uint32_t> pro_out_start;
   std::vector<DevStep> prologue;     // once per bit string: merges that no outer class reaches
   uint32_t pro_arena_elems = 0;      // prologue arena (elements)
   double macs_prologue = 0;          // per bit string
