@@ -759,30 +759,40 @@ __device__ __forceinline__ void level_unit(const DevStep& st, uint32_t o0, uint3
 }
 
 // Units per step for the level executor's unit size 2^UL.
+__device__ __forceinline__ int root_split(const DevStep& st) {
+  return (st.flags & STEP_ROOT) ? (st.kb < kRootSplitLog2 ? st.kb : kRootSplitLog2) : 0;
+}
+
 template <int UL>
 __device__ __forceinline__ uint32_t level_units(const DevStep& st) {
-  const int rc = st.ma + st.nb + st.bb + ((st.flags & STEP_ROOT) ? st.kb : 0);
+  const int rc = st.ma + st.nb + st.bb + root_split(st);
   return 1u << (rc > UL ? rc - UL : 0);
 }
 
-// The root of one item, split over its summed index too: entries e = (o, k)
-// (k fastest) for e in [e0, e0 + u); each product A[m, k, b] B[k, n, b] is
-// added to the compensated sums (the root's outputs are only summed).
+// The root of one item, its sum over k split into 2^ks parts: entries
+// e = (o, part) (part fastest) for e in [e0, e0 + u); each part's partial
+// sum over its k range is added to the compensated sums (the root's outputs
+// are only summed).
 template <class V, class Ops, int UNIT>
-__device__ __forceinline__ void level_root_unit(const DevStep& st, uint32_t e0, uint32_t u, const V* __restrict__ A,
-                                                const V* __restrict__ B, double& sr, double& cr, double& si,
-                                                double& ci) {
+__device__ __forceinline__ void level_root_unit(const DevStep& st, int ks, uint32_t e0, uint32_t u,
+                                                const V* __restrict__ A, const V* __restrict__ B, double& sr,
+                                                double& cr, double& si, double& ci) {
   const int ma = st.ma, nb = st.nb, kb = st.kb;
+  const uint32_t kpart = 1u << (kb - ks);
 #pragma unroll
   for (uint32_t r = 0; r < (uint32_t)UNIT; ++r) {
     if (r < u) {
       const uint32_t e = e0 + r;
-      const uint32_t k = e & ((1u << kb) - 1u), o = e >> kb;
+      const uint32_t part = e & ((1u << ks) - 1u), o = e >> ks;
       const uint32_t m = o & ((1u << ma) - 1u), n = (o >> ma) & ((1u << nb) - 1u), b = o >> (ma + nb);
-      V prod = Ops::mul(A[m + (k << ma) + (b << (ma + kb))], B[k + (n << kb) + (b << (kb + nb))]);
-      Ops::finish(prod);
-      kahan_add(sr, cr, Ops::re(prod));
-      kahan_add(si, ci, Ops::im(prod));
+      const uint32_t k0 = part * kpart;
+      const V* ap = A + m + (k0 << ma) + (b << (ma + kb));
+      const V* bp = B + k0 + (n << kb) + (b << (kb + nb));
+      V acc = Ops::mul(ap[0], bp[0]);
+      for (uint32_t k = 1; k < kpart; ++k) Ops::fma(acc, ap[k << ma], bp[k]);
+      Ops::finish(acc);
+      kahan_add(sr, cr, Ops::re(acc));
+      kahan_add(si, ci, Ops::im(acc));
     }
   }
 }
@@ -825,12 +835,13 @@ __device__ __forceinline__ void level_run(const DevStep* s_steps, const uint32_t
       // Prologue steps may export their result into the (global) leaf table.
       V* C = (st.flags & STEP_EXPORT) ? g_lt + s_leaves[st.c].base : arena + st.c;
       const bool root = st.flags & STEP_ROOT;
-      const int rc = st.ma + st.nb + st.bb + (root ? st.kb : 0);
+      const int ks = root_split(st);
+      const int rc = st.ma + st.nb + st.bb + ks;
       const uint32_t ulog = rc < UL ? (uint32_t)rc : (uint32_t)UL;
       const uint32_t o0 = (uf - jbeg) << ulog;
       const uint32_t u = 1u << ulog;
       if (root) {
-        level_root_unit<V, Ops, 1 << UL>(st, o0, u, A, B, sr, cr, si, ci);
+        level_root_unit<V, Ops, 1 << UL>(st, ks, o0, u, A, B, sr, cr, si, ci);
         continue;
       }
       switch (st.kb) {

@@ -401,9 +401,8 @@ std::string compile_program(const Network& net, const Plan& plan_in, const Progr
       out_start->assign(2 * steps.size(), 0);
       for (size_t i = 0; i < steps.size(); ++i) {
         const DevStep& st = steps[i];
-        // The root's outputs are summed, not stored, so its (output, k) pairs
-        // are independent: it is split over k as well.
-        const int rc = st.ma + st.nb + st.bb + ((st.flags & STEP_ROOT) ? st.kb : 0);
+        // The root's outputs are summed, not stored: its sum over k is split.
+        const int rc = st.ma + st.nb + st.bb + ((st.flags & STEP_ROOT) ? std::min<int>(st.kb, kRootSplitLog2) : 0);
         if (i == 0 || level_of[seq[i]] != level_of[seq[i - 1]]) {
           if (levels->size() >= 0xffff) return "too many levels";
           levels->push_back(DevLevel{(uint16_t)i, 0, {0, 0}});
