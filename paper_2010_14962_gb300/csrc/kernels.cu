@@ -765,7 +765,7 @@ __device__ __forceinline__ int root_split(const DevStep& st) {
 
 template <int UL>
 __device__ __forceinline__ uint32_t level_units(const DevStep& st) {
-  const int rc = st.ma + st.nb + st.bb + root_split(st);
+  const int rc = st.ma + st.nb + st.bb + (UL ? root_split(st) : 0);
   return 1u << (rc > UL ? rc - UL : 0);
 }
 
@@ -835,7 +835,7 @@ __device__ __forceinline__ void level_run(const DevStep* s_steps, const uint32_t
       // Prologue steps may export their result into the (global) leaf table.
       V* C = (st.flags & STEP_EXPORT) ? g_lt + s_leaves[st.c].base : arena + st.c;
       const bool root = st.flags & STEP_ROOT;
-      const int ks = root_split(st);
+      const int ks = UL ? root_split(st) : 0;  // split roots in the four-output table only
       const int rc = st.ma + st.nb + st.bb + ks;
       const uint32_t ulog = rc < UL ? (uint32_t)rc : (uint32_t)UL;
       const uint32_t o0 = (uf - jbeg) << ulog;

@@ -401,15 +401,17 @@ std::string compile_program(const Network& net, const Plan& plan_in, const Progr
       out_start->assign(2 * steps.size(), 0);
       for (size_t i = 0; i < steps.size(); ++i) {
         const DevStep& st = steps[i];
-        // The root's outputs are summed, not stored: its sum over k is split.
-        const int rc = st.ma + st.nb + st.bb + ((st.flags & STEP_ROOT) ? std::min<int>(st.kb, kRootSplitLog2) : 0);
+        const int rc = st.ma + st.nb + st.bb;
+        // Four-output table: the root's outputs are summed, not stored, so
+        // its sum over k is split too.
+        const int split = (st.flags & STEP_ROOT) ? std::min<int>(st.kb, kRootSplitLog2) : 0;
         if (i == 0 || level_of[seq[i]] != level_of[seq[i - 1]]) {
           if (levels->size() >= 0xffff) return "too many levels";
           levels->push_back(DevLevel{(uint16_t)i, 0, {0, 0}});
         }
         DevLevel& lv = levels->back();
         for (int u = 0; u < 2; ++u) {
-          const uint32_t units = 1u << std::max(0, rc - (u ? kLevelUnitLog2 : 0));
+          const uint32_t units = 1u << std::max(0, rc + (u ? split - kLevelUnitLog2 : 0));
           // Executors index (unit, item) pairs of a level in 32 bits, <= 32 items.
           if ((uint64_t)lv.units[u] + units > (1ull << 26)) return "level too large";
           (*out_start)[2 * i + u] = lv.units[u];

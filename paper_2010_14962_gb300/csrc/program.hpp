@@ -84,9 +84,11 @@ static_assert(sizeof(DevStep) == 52, "DevStep layout");
 // output units (in step order) form one flat range.  A unit is 2^u
 // consecutive outputs of a step (all of them if it has fewer), so a step of
 // rank rc has 2^max(0, rc - u) units; tables are kept for u = 0 (one output
-// per unit) and u = 2 (four).  The root step counts rc + min(kb, 2): its
-// outputs are summed, not stored, so its sum over k is split into up to four
-// independent parts (entries of their own).
+// per unit) and u = 2 (four).  In the four-output table the root step
+// counts rc + min(kb, 2): its outputs are summed, not stored, so its sum over
+// k is split into up to four independent parts (entries of their own; the
+// 16-byte types, whose table is the first, keep one compensated FP64 add per
+// output).
 constexpr int kLevelUnitLog2 = 2;
 constexpr int kRootSplitLog2 = 2;
 constexpr int kLevelUnit = 1 << kLevelUnitLog2;

@@ -276,9 +276,10 @@ def test_level_programs_are_race_free(n, p, k, seed):
                 st = steps[j]
                 ma, nb, kb, bb = st["ma"], st["nb"], st["kb"], st["bb"]
                 assert out_start[2 * j] == acc1 and out_start[2 * j + 1] == acc, name
-                rc = ma + nb + bb + (min(kb, 2) if st["flags"] & 4 else 0)  # the root's k sum in <= 4 parts
+                rc = ma + nb + bb
+                split = min(kb, 2) if st["flags"] & 4 else 0  # four-output table: root k sum in <= 4 parts
                 acc1 += 1 << rc
-                acc += 1 << max(0, rc - 2)  # units of 4 outputs (all, if fewer)
+                acc += 1 << max(0, rc + split - 2)  # units of 4 outputs (all, if fewer)
                 if not st["flags"] & 1:
                     reads.append((st["a"], st["a"] + (1 << (ma + kb + bb))))
                 if not st["flags"] & 2:
