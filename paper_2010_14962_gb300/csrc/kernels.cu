@@ -692,7 +692,7 @@ __global__ void __launch_bounds__(256) block_exec_kernel(ExecParams P) {
 // table, leaves, leaf table, then `items` arenas of `stride` elements, which
 // the per-thread partials overlay once the last level is done.
 struct LevelLayout {
-  size_t out_start, levels, leaves, table, arena, red, total;
+  size_t out_start, levels, leaves, loff, table, arena, red, total;
 };
 __host__ __device__ inline LevelLayout level_layout(int n_steps, int n_levels, int n_leaves, uint32_t leaf_elems,
                                                     uint32_t stride, int items, int elem_bytes, int threads) {
@@ -700,7 +700,8 @@ __host__ __device__ inline LevelLayout level_layout(int n_steps, int n_levels, i
   L.out_start = align16((size_t)n_steps * sizeof(DevStep));
   L.levels = L.out_start + align16((size_t)n_steps * 2 * sizeof(uint32_t));
   L.leaves = L.levels + align16((size_t)n_levels * sizeof(DevLevel));
-  L.table = L.leaves + align16((size_t)n_leaves * sizeof(DevLeaf));
+  L.loff = L.leaves + align16((size_t)n_leaves * sizeof(DevLeaf));  // per item: every leaf's sub-block offset
+  L.table = L.loff + align16((size_t)n_leaves * items * sizeof(uint32_t));
   L.arena = L.table + align16((size_t)leaf_elems * elem_bytes);
   L.red = L.arena;
   const size_t arena_bytes = (size_t)stride * items * elem_bytes, red_bytes = (size_t)threads * sizeof(Partial);
@@ -716,22 +717,27 @@ struct LevelParams {
   uint32_t arena_stride;
 };
 
-// One unit of step st for one item: outputs o0 .. o0 + u - 1 (u <= UNIT),
-// C[pos(o)] = sum_k A[..k..] B[..k..] in the step's canonical form, or the
-// root's values added to the sums.  o0 is a multiple of u, so pos(o0 + r) =
-// pos(o0) + the weights of r's low bits.
+// A merge's fields, decoded once into registers while a thread stays on it.
+struct LStep {
+  uint32_t beg, end;  // its units in the level's flat range
+  uint32_t a, b, c;
+  int ma, nb, kb, ks;
+  uint32_t ulog;      // log2 entries per unit
+  uint8_t flags;
+  const uint16_t* w;  // store bit weights (shared memory)
+};
+
+// One unit of a (non-root) merge for one item: outputs o0 .. o0 + u - 1
+// (u <= UNIT), C[pos(o)] = sum_k A[..k..] B[..k..] in the merge's canonical
+// form.  o0 is a multiple of u, so pos(o0 + r) = pos(o0) + the weights of
+// r's low bits.
 template <class V, int K, class Ops, int UNIT>
-__device__ __forceinline__ void level_unit(const DevStep& st, uint32_t o0, uint32_t u, const V* __restrict__ A,
-                                           const V* __restrict__ B, V* __restrict__ C, double& sr, double& cr,
-                                           double& si, double& ci) {
-  const int ma = st.ma, nb = st.nb, kb = st.kb;
-  const bool root = st.flags & STEP_ROOT;
-  uint32_t pos0 = 0, w0 = 0, w1 = 0;
-  if (!root) {
-    for (uint32_t x = o0; x; x &= x - 1u) pos0 += st.w[__ffs(x) - 1];
-    w0 = st.w[0];
-    w1 = st.w[1];
-  }
+__device__ __forceinline__ void level_unit(const LStep& q, uint32_t o0, uint32_t u, const V* __restrict__ A,
+                                           const V* __restrict__ B, V* __restrict__ C) {
+  const int ma = q.ma, nb = q.nb, kb = q.kb;
+  uint32_t pos0 = 0;
+  for (uint32_t x = o0; x; x &= x - 1u) pos0 += q.w[__ffs(x) - 1];
+  const uint32_t w0 = UNIT > 1 ? q.w[0] : 0u, w1 = UNIT > 2 ? q.w[1] : 0u;
   const uint32_t mmask = (1u << ma) - 1u, nmask = (1u << nb) - 1u;
 #pragma unroll
   for (uint32_t r = 0; r < (uint32_t)UNIT; ++r) {
@@ -748,12 +754,7 @@ __device__ __forceinline__ void level_unit(const DevStep& st, uint32_t o0, uint3
         for (uint32_t k = 1; k < (1u << kb); ++k) Ops::fma(acc, ap[k << ma], bp[k]);
       }
       Ops::finish(acc);
-      if (root) {
-        kahan_add(sr, cr, Ops::re(acc));
-        kahan_add(si, ci, Ops::im(acc));
-      } else {
-        C[pos0 + ((r & 1u) ? w0 : 0u) + ((r & 2u) ? w1 : 0u)] = acc;
-      }
+      C[pos0 + ((r & 1u) ? w0 : 0u) + ((r & 2u) ? w1 : 0u)] = acc;
     }
   }
 }
@@ -774,10 +775,10 @@ __device__ __forceinline__ uint32_t level_units(const DevStep& st) {
 // sum over its k range is added to the compensated sums (the root's outputs
 // are only summed).
 template <class V, class Ops, int UNIT>
-__device__ __forceinline__ void level_root_unit(const DevStep& st, int ks, uint32_t e0, uint32_t u,
-                                                const V* __restrict__ A, const V* __restrict__ B, double& sr,
-                                                double& cr, double& si, double& ci) {
-  const int ma = st.ma, nb = st.nb, kb = st.kb;
+__device__ __forceinline__ void level_root_unit(const LStep& q, uint32_t e0, uint32_t u, const V* __restrict__ A,
+                                                const V* __restrict__ B, double& sr, double& cr, double& si,
+                                                double& ci) {
+  const int ma = q.ma, nb = q.nb, kb = q.kb, ks = q.ks;
   const uint32_t kpart = 1u << (kb - ks);
 #pragma unroll
   for (uint32_t r = 0; r < (uint32_t)UNIT; ++r) {
@@ -807,49 +808,62 @@ __device__ __forceinline__ void level_root_unit(const DevStep& st, int ks, uint3
 // dominates, and a level keeps four times more threads busy).
 template <class V, class Ops>
 __device__ __forceinline__ void level_run(const DevStep* s_steps, const uint32_t* s_out, const DevLevel* s_levels,
-                                          int n_levels, const DevLeaf* s_leaves, const V* s_lt, V* s_arena,
-                                          uint32_t stride, uint32_t log2I, uint64_t s0, uint32_t nI, double& sr,
-                                          double& cr, double& si, double& ci, V* g_lt = nullptr) {
+                                          int n_levels, const DevLeaf* s_leaves, int n_leaves, uint32_t* s_loff,
+                                          const V* s_lt, V* s_arena, uint32_t stride, uint32_t log2I, uint64_t s0,
+                                          uint32_t nI, double& sr, double& cr, double& si, double& ci,
+                                          V* g_lt = nullptr) {
   constexpr int UL = sizeof(V) == 16 ? 0 : kLevelUnitLog2;  // log2 outputs per unit
   constexpr int US = UL ? 1 : 0;                            // which unit table
   const uint32_t I = 1u << log2I;
+  // Sub-block offset of every leaf for every item of the group.
+  for (uint32_t it = 0; it < nI; ++it)
+    for (int l = threadIdx.x; l < n_leaves; l += blockDim.x)
+      s_loff[it * n_leaves + l] = leaf_offset(s_leaves[l], s0 + it);
+  __syncthreads();
+  auto decode = [&](int j, LStep& q) {
+    const DevStep& st = s_steps[j];
+    q.ma = st.ma;
+    q.nb = st.nb;
+    q.kb = st.kb;
+    q.flags = st.flags;
+    q.a = st.a;
+    q.b = st.b;
+    q.c = (st.flags & STEP_EXPORT) ? s_leaves[st.c].base : st.c;
+    q.w = st.w;
+    q.ks = UL ? root_split(st) : 0;  // split roots in the four-output table only
+    const int rc = st.ma + st.nb + st.bb + q.ks;
+    q.ulog = rc < UL ? (uint32_t)rc : (uint32_t)UL;
+    q.beg = s_out[2 * j + US];
+    q.end = q.beg + (1u << (rc - (int)q.ulog));
+  };
   for (int l = 0; l < n_levels; ++l) {
     const DevLevel lv = s_levels[l];
     const uint32_t total = lv.units[US] << log2I;
     int j = lv.first;
-    uint32_t jbeg = s_out[2 * j + US];
-    uint32_t jend = jbeg + level_units<UL>(s_steps[j]);
+    LStep q;
+    decode(j, q);
     for (uint32_t f = threadIdx.x; f < total; f += blockDim.x) {
       const uint32_t item = f & (I - 1u), uf = f >> log2I;
-      while (uf >= jend) {  // steps of the level in order; uf < lv.units
-        ++j;
-        jbeg = s_out[2 * j + US];
-        jend = jbeg + level_units<UL>(s_steps[j]);
-      }
+      while (uf >= q.end) decode(++j, q);  // steps of the level in order; uf < its units
       if (item >= nI) continue;
-      const DevStep& st = s_steps[j];
-      const uint64_t s = s0 + item;
       V* arena = s_arena + (size_t)item * stride;
-      const V* A = (st.flags & STEP_A_LEAF) ? s_lt + leaf_offset(s_leaves[st.a], s) : arena + st.a;
-      const V* B = (st.flags & STEP_B_LEAF) ? s_lt + leaf_offset(s_leaves[st.b], s) : arena + st.b;
-      // Prologue steps may export their result into the (global) leaf table.
-      V* C = (st.flags & STEP_EXPORT) ? g_lt + s_leaves[st.c].base : arena + st.c;
-      const bool root = st.flags & STEP_ROOT;
-      const int ks = UL ? root_split(st) : 0;  // split roots in the four-output table only
-      const int rc = st.ma + st.nb + st.bb + ks;
-      const uint32_t ulog = rc < UL ? (uint32_t)rc : (uint32_t)UL;
-      const uint32_t o0 = (uf - jbeg) << ulog;
-      const uint32_t u = 1u << ulog;
-      if (root) {
-        level_root_unit<V, Ops, 1 << UL>(st, ks, o0, u, A, B, sr, cr, si, ci);
+      const uint32_t* loff = s_loff + item * n_leaves;
+      const V* A = (q.flags & STEP_A_LEAF) ? s_lt + loff[q.a] : arena + q.a;
+      const V* B = (q.flags & STEP_B_LEAF) ? s_lt + loff[q.b] : arena + q.b;
+      const uint32_t u = 1u << q.ulog;
+      const uint32_t o0 = (uf - q.beg) << q.ulog;
+      if (q.flags & STEP_ROOT) {
+        level_root_unit<V, Ops, 1 << UL>(q, o0, u, A, B, sr, cr, si, ci);
         continue;
       }
-      switch (st.kb) {
-        case 0: level_unit<V, 1, Ops, 1 << UL>(st, o0, u, A, B, C, sr, cr, si, ci); break;
-        case 1: level_unit<V, 2, Ops, 1 << UL>(st, o0, u, A, B, C, sr, cr, si, ci); break;
-        case 2: level_unit<V, 4, Ops, 1 << UL>(st, o0, u, A, B, C, sr, cr, si, ci); break;
-        case 3: level_unit<V, 8, Ops, 1 << UL>(st, o0, u, A, B, C, sr, cr, si, ci); break;
-        default: level_unit<V, 0, Ops, 1 << UL>(st, o0, u, A, B, C, sr, cr, si, ci); break;
+      // Prologue steps may export their result into the (global) leaf table.
+      V* C = (q.flags & STEP_EXPORT) ? g_lt + q.c : arena + q.c;
+      switch (q.kb) {
+        case 0: level_unit<V, 1, Ops, 1 << UL>(q, o0, u, A, B, C); break;
+        case 1: level_unit<V, 2, Ops, 1 << UL>(q, o0, u, A, B, C); break;
+        case 2: level_unit<V, 4, Ops, 1 << UL>(q, o0, u, A, B, C); break;
+        case 3: level_unit<V, 8, Ops, 1 << UL>(q, o0, u, A, B, C); break;
+        default: level_unit<V, 0, Ops, 1 << UL>(q, o0, u, A, B, C); break;
       }
     }
     __syncthreads();  // also orders the last level's arena reads before later reuse of the arena
@@ -873,6 +887,7 @@ __global__ void __launch_bounds__(1024) level_exec_kernel(ExecParams P, LevelPar
   V* s_lt = reinterpret_cast<V*>(smem + lay.table);
   V* s_arena = reinterpret_cast<V*>(smem + lay.arena);
   Partial* s_red = reinterpret_cast<Partial*>(smem + lay.red);
+  uint32_t* s_loff = reinterpret_cast<uint32_t*>(smem + lay.loff);
   const int xi = blockIdx.x / P.blocks_per_x;
   const int bx = blockIdx.x % P.blocks_per_x;
   copy_words(s_steps, P.steps, (size_t)P.n_steps * sizeof(DevStep));
@@ -887,8 +902,8 @@ __global__ void __launch_bounds__(1024) level_exec_kernel(ExecParams P, LevelPar
   const uint64_t S = P.slice_hi - P.slice_lo;
   for (uint64_t i0 = (uint64_t)bx * I; i0 < S; i0 += (uint64_t)P.blocks_per_x * I) {
     const uint32_t nI = (uint32_t)((S - i0) < I ? (S - i0) : I);
-    level_run<V, Ops>(s_steps, s_out, s_levels, LP.n_levels, s_leaves, s_lt, s_arena, LP.arena_stride, log2I,
-                      P.slice_lo + i0, nI, sr, cr, si, ci);
+    level_run<V, Ops>(s_steps, s_out, s_levels, LP.n_levels, s_leaves, P.n_leaves, s_loff, s_lt, s_arena,
+                      LP.arena_stride, log2I, P.slice_lo + i0, nI, sr, cr, si, ci);
   }
   s_red[threadIdx.x] = Partial::make(sr, si, cr, ci);  // overlays the arenas: every level is done
   tree_reduce(s_red, T);
@@ -912,6 +927,7 @@ __device__ __forceinline__ void prologue_level_body(const DevStep* __restrict__ 
   DevLeaf* s_leaves = reinterpret_cast<DevLeaf*>(smem + lay.leaves);
   V* s_lt = reinterpret_cast<V*>(smem + lay.table);
   V* s_arena = reinterpret_cast<V*>(smem + lay.arena);
+  uint32_t* s_loff = reinterpret_cast<uint32_t*>(smem + lay.loff);
   copy_words(s_steps, steps, (size_t)n_steps * sizeof(DevStep));
   copy_words(s_out, out_start, (size_t)n_steps * 2 * sizeof(uint32_t));
   copy_words(s_levels, levels, (size_t)n_levels * sizeof(DevLevel));
@@ -919,8 +935,8 @@ __device__ __forceinline__ void prologue_level_body(const DevStep* __restrict__ 
   copy_words(s_lt, g_lt, (size_t)leaf_elems * sizeof(V));
   __syncthreads();
   double sr = 0, si = 0, cr = 0, ci = 0;  // no root among hoisted merges
-  level_run<V, Ops>(s_steps, s_out, s_levels, n_levels, s_leaves, s_lt, s_arena, arena_elems | 1u, 0, 0, 1, sr, cr,
-                    si, ci, g_lt);
+  level_run<V, Ops>(s_steps, s_out, s_levels, n_levels, s_leaves, n_leaves, s_loff, s_lt, s_arena, arena_elems | 1u, 0,
+                    0, 1, sr, cr, si, ci, g_lt);
 }
 
 template <class V, class Ops = CplxOps<V>>
@@ -1013,16 +1029,22 @@ __global__ void multi_leaf_kernel(const JobDesc* __restrict__ jobs, int njobs) {
 }
 
 template <class V, class Ops = CplxOps<V>>
-__global__ void __launch_bounds__(1024) multi_prologue_kernel(const JobDesc* __restrict__ jobs) {
+__global__ void __launch_bounds__(256) multi_prologue_kernel(const JobDesc* __restrict__ jobs) {
   extern __shared__ __align__(16) unsigned char smem[];
   const JobDesc& J = jobs[blockIdx.x];
   if (J.n_pro_steps == 0) return;
-  if (J.n_pro_levels > 0)
-    prologue_level_body<V, Ops>(J.pro_steps, J.n_pro_steps, J.pro_out_start, J.pro_levels, J.n_pro_levels, J.leaves,
-                                J.n_leaves, static_cast<V*>(J.leaf_table), J.leaf_elems, J.pro_arena_elems, smem);
-  else
-    prologue_body<V, Ops>(J.pro_steps, J.n_pro_steps, J.leaves, J.n_leaves, static_cast<V*>(J.leaf_table),
-                          J.leaf_elems, J.pro_arena_elems, smem);
+  prologue_body<V, Ops>(J.pro_steps, J.n_pro_steps, J.leaves, J.n_leaves, static_cast<V*>(J.leaf_table),
+                        J.leaf_elems, J.pro_arena_elems, smem);
+}
+
+// The same for level programs (level-ordered prologues, 1024 threads).
+template <class V, class Ops = CplxOps<V>>
+__global__ void __launch_bounds__(1024) multi_prologue_level_kernel(const JobDesc* __restrict__ jobs) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const JobDesc& J = jobs[blockIdx.x];
+  if (J.n_pro_steps == 0) return;
+  prologue_level_body<V, Ops>(J.pro_steps, J.n_pro_steps, J.pro_out_start, J.pro_levels, J.n_pro_levels, J.leaves,
+                              J.n_leaves, static_cast<V*>(J.leaf_table), J.leaf_elems, J.pro_arena_elems, smem);
 }
 
 template <class V, class Ops = CplxOps<V>>
@@ -1100,6 +1122,7 @@ __global__ void __launch_bounds__(1024) multi_level_kernel(const JobDesc* __rest
     V* s_lt = reinterpret_cast<V*>(smem + lay.table);
     V* s_arena = reinterpret_cast<V*>(smem + lay.arena);
     Partial* s_red = reinterpret_cast<Partial*>(smem + lay.red);
+    uint32_t* s_loff = reinterpret_cast<uint32_t*>(smem + lay.loff);
     if (s_job != (int)ch.job) {
       copy_words(s_steps, J.steps, (size_t)J.n_steps * sizeof(DevStep));
       copy_words(s_out, J.out_start, (size_t)J.n_steps * 2 * sizeof(uint32_t));
@@ -1112,8 +1135,8 @@ __global__ void __launch_bounds__(1024) multi_level_kernel(const JobDesc* __rest
     double sr = 0.0, si = 0.0, cr = 0.0, ci = 0.0;
     for (uint64_t i0 = ch.lo; i0 < ch.hi; i0 += I) {
       const uint32_t nI = (uint32_t)((ch.hi - i0) < I ? (ch.hi - i0) : I);
-      level_run<V, Ops>(s_steps, s_out, s_levels, J.n_levels, s_leaves, s_lt, s_arena, J.arena_stride, log2I, i0,
-                        nI, sr, cr, si, ci);
+      level_run<V, Ops>(s_steps, s_out, s_levels, J.n_levels, s_leaves, J.n_leaves, s_loff, s_lt, s_arena,
+                        J.arena_stride, log2I, i0, nI, sr, cr, si, ci);
     }
     s_red[threadIdx.x] = Partial::make(sr, si, cr, ci);  // overlays the arenas
     tree_reduce(s_red, T);
@@ -1366,13 +1389,19 @@ cudaError_t launch_multi_typed(const JobDesc* d_jobs, int njobs, uint32_t total_
   if ((e = cudaFuncSetAttribute(multi_prologue_kernel<V, Ops>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)pro_smem)) != cudaSuccess)
     return e;
+  if ((e = cudaFuncSetAttribute(multi_prologue_level_kernel<V, Ops>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)pro_smem)) != cudaSuccess)
+    return e;
   const int threads = level ? kMultiLevelThreads : 256;
   if (level ? !shape_for_kernel(multi_level_kernel<V, Ops>, threads, exec_smem, &occ)
             : !shape_for_kernel(multi_exec_kernel<V, Ops>, threads, exec_smem, &occ))
     return cudaErrorInvalidConfiguration;
   if ((e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned), stream)) != cudaSuccess) return e;
   multi_leaf_kernel<V><<<total_leaves, 32, 0, stream>>>(d_jobs, njobs);
-  multi_prologue_kernel<V, Ops><<<njobs, level ? kMultiLevelThreads : 256, pro_smem, stream>>>(d_jobs);
+  if (level)
+    multi_prologue_level_kernel<V, Ops><<<njobs, kMultiLevelThreads, pro_smem, stream>>>(d_jobs);
+  else
+    multi_prologue_kernel<V, Ops><<<njobs, 256, pro_smem, stream>>>(d_jobs);
   const unsigned grid = (unsigned)std::min<uint64_t>((uint64_t)sms * occ, n_chunks);
   if (level)
     multi_level_kernel<V, Ops><<<grid, threads, exec_smem, stream>>>(d_jobs, d_chunks, n_chunks, d_counter,
