@@ -692,7 +692,7 @@ __global__ void __launch_bounds__(256) block_exec_kernel(ExecParams P) {
 // table, leaves, leaf table, then `items` arenas of `stride` elements, which
 // the per-thread partials overlay once the last level is done.
 struct LevelLayout {
-  size_t out_start, levels, leaves, loff, table, arena, red, total;
+  size_t out_start, levels, leaves, table, arena, red, total;
 };
 __host__ __device__ inline LevelLayout level_layout(int n_steps, int n_levels, int n_leaves, uint32_t leaf_elems,
                                                     uint32_t stride, int items, int elem_bytes, int threads) {
@@ -700,8 +700,7 @@ __host__ __device__ inline LevelLayout level_layout(int n_steps, int n_levels, i
   L.out_start = align16((size_t)n_steps * sizeof(DevStep));
   L.levels = L.out_start + align16((size_t)n_steps * 2 * sizeof(uint32_t));
   L.leaves = L.levels + align16((size_t)n_levels * sizeof(DevLevel));
-  L.loff = L.leaves + align16((size_t)n_leaves * sizeof(DevLeaf));  // per item: every leaf's sub-block offset
-  L.table = L.loff + align16((size_t)n_leaves * items * sizeof(uint32_t));
+  L.table = L.leaves + align16((size_t)n_leaves * sizeof(DevLeaf));
   L.arena = L.table + align16((size_t)leaf_elems * elem_bytes);
   L.red = L.arena;
   const size_t arena_bytes = (size_t)stride * items * elem_bytes, red_bytes = (size_t)threads * sizeof(Partial);
@@ -808,18 +807,13 @@ __device__ __forceinline__ void level_root_unit(const LStep& q, uint32_t e0, uin
 // dominates, and a level keeps four times more threads busy).
 template <class V, class Ops>
 __device__ __forceinline__ void level_run(const DevStep* s_steps, const uint32_t* s_out, const DevLevel* s_levels,
-                                          int n_levels, const DevLeaf* s_leaves, int n_leaves, uint32_t* s_loff,
-                                          const V* s_lt, V* s_arena, uint32_t stride, uint32_t log2I, uint64_t s0,
+                                          int n_levels, const DevLeaf* s_leaves, const V* s_lt, V* s_arena,
+                                          uint32_t stride, uint32_t log2I, uint64_t s0,
                                           uint32_t nI, double& sr, double& cr, double& si, double& ci,
                                           V* g_lt = nullptr) {
   constexpr int UL = sizeof(V) == 16 ? 0 : kLevelUnitLog2;  // log2 outputs per unit
   constexpr int US = UL ? 1 : 0;                            // which unit table
   const uint32_t I = 1u << log2I;
-  // Sub-block offset of every leaf for every item of the group.
-  for (uint32_t it = 0; it < nI; ++it)
-    for (int l = threadIdx.x; l < n_leaves; l += blockDim.x)
-      s_loff[it * n_leaves + l] = leaf_offset(s_leaves[l], s0 + it);
-  __syncthreads();
   auto decode = [&](int j, LStep& q) {
     const DevStep& st = s_steps[j];
     q.ma = st.ma;
@@ -847,9 +841,8 @@ __device__ __forceinline__ void level_run(const DevStep* s_steps, const uint32_t
       while (uf >= q.end) decode(++j, q);  // steps of the level in order; uf < its units
       if (item >= nI) continue;
       V* arena = s_arena + (size_t)item * stride;
-      const uint32_t* loff = s_loff + item * n_leaves;
-      const V* A = (q.flags & STEP_A_LEAF) ? s_lt + loff[q.a] : arena + q.a;
-      const V* B = (q.flags & STEP_B_LEAF) ? s_lt + loff[q.b] : arena + q.b;
+      const V* A = (q.flags & STEP_A_LEAF) ? s_lt + leaf_offset(s_leaves[q.a], s0 + item) : arena + q.a;
+      const V* B = (q.flags & STEP_B_LEAF) ? s_lt + leaf_offset(s_leaves[q.b], s0 + item) : arena + q.b;
       const uint32_t u = 1u << q.ulog;
       const uint32_t o0 = (uf - q.beg) << q.ulog;
       if (q.flags & STEP_ROOT) {
@@ -887,7 +880,6 @@ __global__ void __launch_bounds__(1024) level_exec_kernel(ExecParams P, LevelPar
   V* s_lt = reinterpret_cast<V*>(smem + lay.table);
   V* s_arena = reinterpret_cast<V*>(smem + lay.arena);
   Partial* s_red = reinterpret_cast<Partial*>(smem + lay.red);
-  uint32_t* s_loff = reinterpret_cast<uint32_t*>(smem + lay.loff);
   const int xi = blockIdx.x / P.blocks_per_x;
   const int bx = blockIdx.x % P.blocks_per_x;
   copy_words(s_steps, P.steps, (size_t)P.n_steps * sizeof(DevStep));
@@ -902,8 +894,8 @@ __global__ void __launch_bounds__(1024) level_exec_kernel(ExecParams P, LevelPar
   const uint64_t S = P.slice_hi - P.slice_lo;
   for (uint64_t i0 = (uint64_t)bx * I; i0 < S; i0 += (uint64_t)P.blocks_per_x * I) {
     const uint32_t nI = (uint32_t)((S - i0) < I ? (S - i0) : I);
-    level_run<V, Ops>(s_steps, s_out, s_levels, LP.n_levels, s_leaves, P.n_leaves, s_loff, s_lt, s_arena,
-                      LP.arena_stride, log2I, P.slice_lo + i0, nI, sr, cr, si, ci);
+    level_run<V, Ops>(s_steps, s_out, s_levels, LP.n_levels, s_leaves, s_lt, s_arena, LP.arena_stride, log2I,
+                      P.slice_lo + i0, nI, sr, cr, si, ci);
   }
   s_red[threadIdx.x] = Partial::make(sr, si, cr, ci);  // overlays the arenas: every level is done
   tree_reduce(s_red, T);
@@ -927,7 +919,6 @@ __device__ __forceinline__ void prologue_level_body(const DevStep* __restrict__ 
   DevLeaf* s_leaves = reinterpret_cast<DevLeaf*>(smem + lay.leaves);
   V* s_lt = reinterpret_cast<V*>(smem + lay.table);
   V* s_arena = reinterpret_cast<V*>(smem + lay.arena);
-  uint32_t* s_loff = reinterpret_cast<uint32_t*>(smem + lay.loff);
   copy_words(s_steps, steps, (size_t)n_steps * sizeof(DevStep));
   copy_words(s_out, out_start, (size_t)n_steps * 2 * sizeof(uint32_t));
   copy_words(s_levels, levels, (size_t)n_levels * sizeof(DevLevel));
@@ -935,8 +926,8 @@ __device__ __forceinline__ void prologue_level_body(const DevStep* __restrict__ 
   copy_words(s_lt, g_lt, (size_t)leaf_elems * sizeof(V));
   __syncthreads();
   double sr = 0, si = 0, cr = 0, ci = 0;  // no root among hoisted merges
-  level_run<V, Ops>(s_steps, s_out, s_levels, n_levels, s_leaves, n_leaves, s_loff, s_lt, s_arena, arena_elems | 1u, 0,
-                    0, 1, sr, cr, si, ci, g_lt);
+  level_run<V, Ops>(s_steps, s_out, s_levels, n_levels, s_leaves, s_lt, s_arena, arena_elems | 1u, 0, 0, 1, sr, cr,
+                    si, ci, g_lt);
 }
 
 template <class V, class Ops = CplxOps<V>>
@@ -1122,7 +1113,6 @@ __global__ void __launch_bounds__(1024) multi_level_kernel(const JobDesc* __rest
     V* s_lt = reinterpret_cast<V*>(smem + lay.table);
     V* s_arena = reinterpret_cast<V*>(smem + lay.arena);
     Partial* s_red = reinterpret_cast<Partial*>(smem + lay.red);
-    uint32_t* s_loff = reinterpret_cast<uint32_t*>(smem + lay.loff);
     if (s_job != (int)ch.job) {
       copy_words(s_steps, J.steps, (size_t)J.n_steps * sizeof(DevStep));
       copy_words(s_out, J.out_start, (size_t)J.n_steps * 2 * sizeof(uint32_t));
@@ -1135,8 +1125,8 @@ __global__ void __launch_bounds__(1024) multi_level_kernel(const JobDesc* __rest
     double sr = 0.0, si = 0.0, cr = 0.0, ci = 0.0;
     for (uint64_t i0 = ch.lo; i0 < ch.hi; i0 += I) {
       const uint32_t nI = (uint32_t)((ch.hi - i0) < I ? (ch.hi - i0) : I);
-      level_run<V, Ops>(s_steps, s_out, s_levels, J.n_levels, s_leaves, J.n_leaves, s_loff, s_lt, s_arena,
-                        J.arena_stride, log2I, i0, nI, sr, cr, si, ci);
+      level_run<V, Ops>(s_steps, s_out, s_levels, J.n_levels, s_leaves, s_lt, s_arena, J.arena_stride, log2I, i0,
+                        nI, sr, cr, si, ci);
     }
     s_red[threadIdx.x] = Partial::make(sr, si, cr, ci);  // overlays the arenas
     tree_reduce(s_red, T);
