@@ -276,6 +276,15 @@ struct qtn_plan {
       QTN_CUDA(::upload(&post, pg.pro_out_start));
       dev_allocs.push_back(post);
     }
+    uint16_t *nib = nullptr, *pnib = nullptr;
+    if (!pg.pos_nib.empty()) {
+      QTN_CUDA(::upload(&nib, pg.pos_nib));
+      dev_allocs.push_back(nib);
+    }
+    if (!pg.pro_pos_nib.empty()) {
+      QTN_CUDA(::upload(&pnib, pg.pro_pos_nib));
+      dev_allocs.push_back(pnib);
+    }
     DeviceProgram& d = sl.dprog;
     d.levels = lvls;
     d.out_start = ost;
@@ -283,6 +292,8 @@ struct qtn_plan {
     d.pro_levels = plvls;
     d.pro_out_start = post;
     d.n_pro_levels = (int)pg.pro_levels.size();
+    d.pos_nib = nib;
+    d.pro_pos_nib = pnib;
     d.block_threads = sl.threads;
     d.blocks_per_sm = sl.blocks_per_sm;
     d.density = pg.density ? 1 : 0;
@@ -1156,6 +1167,8 @@ qtn_status qtn_contract_batch(const qtn_plan_t* const* plans, const uint8_t* con
     J.pro_levels = level ? d.pro_levels : nullptr;
     J.pro_out_start = level ? d.pro_out_start : nullptr;
     J.n_pro_levels = level ? d.n_pro_levels : 0;
+    J.pos_nib = d.pos_nib;
+    J.pro_pos_nib = d.pro_pos_nib;
     J.log2_items = jh[j].log2_items;
     J.arena_stride = d.arena_elems | 1u;
     J.density = d.density;

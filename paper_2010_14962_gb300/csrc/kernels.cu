@@ -692,13 +692,14 @@ __global__ void __launch_bounds__(256) block_exec_kernel(ExecParams P) {
 // table, leaves, leaf table, then `items` arenas of `stride` elements, which
 // the per-thread partials overlay once the last level is done.
 struct LevelLayout {
-  size_t out_start, levels, leaves, table, arena, red, total;
+  size_t out_start, nib, levels, leaves, table, arena, red, total;
 };
 __host__ __device__ inline LevelLayout level_layout(int n_steps, int n_levels, int n_leaves, uint32_t leaf_elems,
                                                     uint32_t stride, int items, int elem_bytes, int threads) {
   LevelLayout L;
   L.out_start = align16((size_t)n_steps * sizeof(DevStep));
-  L.levels = L.out_start + align16((size_t)n_steps * 2 * sizeof(uint32_t));
+  L.nib = L.out_start + align16((size_t)n_steps * 2 * sizeof(uint32_t));
+  L.levels = L.nib + align16((size_t)n_steps * kPosNibEntries * sizeof(uint16_t));
   L.leaves = L.levels + align16((size_t)n_levels * sizeof(DevLevel));
   L.table = L.leaves + align16((size_t)n_leaves * sizeof(DevLeaf));
   L.arena = L.table + align16((size_t)leaf_elems * elem_bytes);
@@ -711,6 +712,7 @@ __host__ __device__ inline LevelLayout level_layout(int n_steps, int n_levels, i
 struct LevelParams {
   const DevLevel* levels;
   const uint32_t* out_start;
+  const uint16_t* pos_nib;
   int n_levels;
   int log2_items;
   uint32_t arena_stride;
@@ -722,8 +724,9 @@ struct LStep {
   uint32_t a, b, c;
   int ma, nb, kb, ks;
   uint32_t ulog;      // log2 entries per unit
+  int groups;         // nibbles of an output index
   uint8_t flags;
-  const uint16_t* w;  // store bit weights (shared memory)
+  const uint16_t* nib;  // store offsets by nibble (shared memory)
 };
 
 // One unit of a (non-root) merge for one item: outputs o0 .. o0 + u - 1
@@ -735,8 +738,8 @@ __device__ __forceinline__ void level_unit(const LStep& q, uint32_t o0, uint32_t
                                            const V* __restrict__ B, V* __restrict__ C) {
   const int ma = q.ma, nb = q.nb, kb = q.kb;
   uint32_t pos0 = 0;
-  for (uint32_t x = o0; x; x &= x - 1u) pos0 += q.w[__ffs(x) - 1];
-  const uint32_t w0 = UNIT > 1 ? q.w[0] : 0u, w1 = UNIT > 2 ? q.w[1] : 0u;
+  for (int g = 0; g < q.groups; ++g) pos0 += q.nib[16 * g + ((o0 >> (4 * g)) & 15u)];
+  const uint32_t w0 = UNIT > 1 ? q.nib[1] : 0u, w1 = UNIT > 2 ? q.nib[2] : 0u;
   const uint32_t mmask = (1u << ma) - 1u, nmask = (1u << nb) - 1u;
 #pragma unroll
   for (uint32_t r = 0; r < (uint32_t)UNIT; ++r) {
@@ -806,8 +809,9 @@ __device__ __forceinline__ void level_root_unit(const LStep& q, uint32_t e0, uin
 // decode over cheap arithmetic), one for the 16-byte types (their arithmetic
 // dominates, and a level keeps four times more threads busy).
 template <class V, class Ops>
-__device__ __forceinline__ void level_run(const DevStep* s_steps, const uint32_t* s_out, const DevLevel* s_levels,
-                                          int n_levels, const DevLeaf* s_leaves, const V* s_lt, V* s_arena,
+__device__ __forceinline__ void level_run(const DevStep* s_steps, const uint32_t* s_out, const uint16_t* s_nib,
+                                          const DevLevel* s_levels, int n_levels, const DevLeaf* s_leaves,
+                                          const V* s_lt, V* s_arena,
                                           uint32_t stride, uint32_t log2I, uint64_t s0,
                                           uint32_t nI, double& sr, double& cr, double& si, double& ci,
                                           V* g_lt = nullptr) {
@@ -823,7 +827,8 @@ __device__ __forceinline__ void level_run(const DevStep* s_steps, const uint32_t
     q.a = st.a;
     q.b = st.b;
     q.c = (st.flags & STEP_EXPORT) ? s_leaves[st.c].base : st.c;
-    q.w = st.w;
+    q.nib = s_nib + (size_t)j * kPosNibEntries;
+    q.groups = (st.ma + st.nb + st.bb + 3) >> 2;
     q.ks = UL ? root_split(st) : 0;  // split roots in the four-output table only
     const int rc = st.ma + st.nb + st.bb + q.ks;
     q.ulog = rc < UL ? (uint32_t)rc : (uint32_t)UL;
@@ -875,6 +880,7 @@ __global__ void __launch_bounds__(1024) level_exec_kernel(ExecParams P, LevelPar
                                        (int)sizeof(V), T);
   DevStep* s_steps = reinterpret_cast<DevStep*>(smem);
   uint32_t* s_out = reinterpret_cast<uint32_t*>(smem + lay.out_start);
+  uint16_t* s_nib = reinterpret_cast<uint16_t*>(smem + lay.nib);
   DevLevel* s_levels = reinterpret_cast<DevLevel*>(smem + lay.levels);
   DevLeaf* s_leaves = reinterpret_cast<DevLeaf*>(smem + lay.leaves);
   V* s_lt = reinterpret_cast<V*>(smem + lay.table);
@@ -884,6 +890,7 @@ __global__ void __launch_bounds__(1024) level_exec_kernel(ExecParams P, LevelPar
   const int bx = blockIdx.x % P.blocks_per_x;
   copy_words(s_steps, P.steps, (size_t)P.n_steps * sizeof(DevStep));
   copy_words(s_out, LP.out_start, (size_t)P.n_steps * 2 * sizeof(uint32_t));
+  copy_words(s_nib, LP.pos_nib, (size_t)P.n_steps * kPosNibEntries * sizeof(uint16_t));
   copy_words(s_levels, LP.levels, (size_t)LP.n_levels * sizeof(DevLevel));
   copy_words(s_leaves, P.leaves, (size_t)P.n_leaves * sizeof(DevLeaf));
   copy_words(s_lt, static_cast<const V*>(P.leaf_tables) + (size_t)xi * P.leaf_elems,
@@ -894,8 +901,8 @@ __global__ void __launch_bounds__(1024) level_exec_kernel(ExecParams P, LevelPar
   const uint64_t S = P.slice_hi - P.slice_lo;
   for (uint64_t i0 = (uint64_t)bx * I; i0 < S; i0 += (uint64_t)P.blocks_per_x * I) {
     const uint32_t nI = (uint32_t)((S - i0) < I ? (S - i0) : I);
-    level_run<V, Ops>(s_steps, s_out, s_levels, LP.n_levels, s_leaves, s_lt, s_arena, LP.arena_stride, log2I,
-                      P.slice_lo + i0, nI, sr, cr, si, ci);
+    level_run<V, Ops>(s_steps, s_out, s_nib, s_levels, LP.n_levels, s_leaves, s_lt, s_arena, LP.arena_stride,
+                      log2I, P.slice_lo + i0, nI, sr, cr, si, ci);
   }
   s_red[threadIdx.x] = Partial::make(sr, si, cr, ci);  // overlays the arenas: every level is done
   tree_reduce(s_red, T);
@@ -908,6 +915,7 @@ __global__ void __launch_bounds__(1024) level_exec_kernel(ExecParams P, LevelPar
 template <class V, class Ops>
 __device__ __forceinline__ void prologue_level_body(const DevStep* __restrict__ steps, int n_steps,
                                                     const uint32_t* __restrict__ out_start,
+                                                    const uint16_t* __restrict__ pos_nib,
                                                     const DevLevel* __restrict__ levels, int n_levels,
                                                     const DevLeaf* __restrict__ leaves, int n_leaves, V* g_lt,
                                                     uint32_t leaf_elems, uint32_t arena_elems, unsigned char* smem) {
@@ -915,32 +923,35 @@ __device__ __forceinline__ void prologue_level_body(const DevStep* __restrict__ 
                                        blockDim.x);
   DevStep* s_steps = reinterpret_cast<DevStep*>(smem);
   uint32_t* s_out = reinterpret_cast<uint32_t*>(smem + lay.out_start);
+  uint16_t* s_nib = reinterpret_cast<uint16_t*>(smem + lay.nib);
   DevLevel* s_levels = reinterpret_cast<DevLevel*>(smem + lay.levels);
   DevLeaf* s_leaves = reinterpret_cast<DevLeaf*>(smem + lay.leaves);
   V* s_lt = reinterpret_cast<V*>(smem + lay.table);
   V* s_arena = reinterpret_cast<V*>(smem + lay.arena);
   copy_words(s_steps, steps, (size_t)n_steps * sizeof(DevStep));
   copy_words(s_out, out_start, (size_t)n_steps * 2 * sizeof(uint32_t));
+  copy_words(s_nib, pos_nib, (size_t)n_steps * kPosNibEntries * sizeof(uint16_t));
   copy_words(s_levels, levels, (size_t)n_levels * sizeof(DevLevel));
   copy_words(s_leaves, leaves, (size_t)n_leaves * sizeof(DevLeaf));
   copy_words(s_lt, g_lt, (size_t)leaf_elems * sizeof(V));
   __syncthreads();
   double sr = 0, si = 0, cr = 0, ci = 0;  // no root among hoisted merges
-  level_run<V, Ops>(s_steps, s_out, s_levels, n_levels, s_leaves, s_lt, s_arena, arena_elems | 1u, 0, 0, 1, sr, cr,
-                    si, ci, g_lt);
+  level_run<V, Ops>(s_steps, s_out, s_nib, s_levels, n_levels, s_leaves, s_lt, s_arena, arena_elems | 1u, 0, 0, 1, sr,
+                    cr, si, ci, g_lt);
 }
 
 template <class V, class Ops = CplxOps<V>>
 __global__ void __launch_bounds__(1024) prologue_level_kernel(const DevStep* __restrict__ steps, int n_steps,
                                                               const uint32_t* __restrict__ out_start,
+                                                              const uint16_t* __restrict__ pos_nib,
                                                               const DevLevel* __restrict__ levels, int n_levels,
                                                               const DevLeaf* __restrict__ leaves, int n_leaves,
                                                               void* leaf_tables, uint32_t leaf_elems,
                                                               uint32_t arena_elems) {
   extern __shared__ __align__(16) unsigned char smem[];
   V* g_lt = static_cast<V*>(leaf_tables) + (size_t)blockIdx.x * leaf_elems;
-  prologue_level_body<V, Ops>(steps, n_steps, out_start, levels, n_levels, leaves, n_leaves, g_lt, leaf_elems,
-                              arena_elems, smem);
+  prologue_level_body<V, Ops>(steps, n_steps, out_start, pos_nib, levels, n_levels, leaves, n_leaves, g_lt,
+                              leaf_elems, arena_elems, smem);
 }
 
 // -------------------------------------------------------------- prologue --
@@ -1034,8 +1045,9 @@ __global__ void __launch_bounds__(1024) multi_prologue_level_kernel(const JobDes
   extern __shared__ __align__(16) unsigned char smem[];
   const JobDesc& J = jobs[blockIdx.x];
   if (J.n_pro_steps == 0) return;
-  prologue_level_body<V, Ops>(J.pro_steps, J.n_pro_steps, J.pro_out_start, J.pro_levels, J.n_pro_levels, J.leaves,
-                              J.n_leaves, static_cast<V*>(J.leaf_table), J.leaf_elems, J.pro_arena_elems, smem);
+  prologue_level_body<V, Ops>(J.pro_steps, J.n_pro_steps, J.pro_out_start, J.pro_pos_nib, J.pro_levels,
+                              J.n_pro_levels, J.leaves, J.n_leaves, static_cast<V*>(J.leaf_table), J.leaf_elems,
+                              J.pro_arena_elems, smem);
 }
 
 template <class V, class Ops = CplxOps<V>>
@@ -1108,6 +1120,7 @@ __global__ void __launch_bounds__(1024) multi_level_kernel(const JobDesc* __rest
                                          (int)sizeof(V), T);
     DevStep* s_steps = reinterpret_cast<DevStep*>(smem);
     uint32_t* s_out = reinterpret_cast<uint32_t*>(smem + lay.out_start);
+    uint16_t* s_nib = reinterpret_cast<uint16_t*>(smem + lay.nib);
     DevLevel* s_levels = reinterpret_cast<DevLevel*>(smem + lay.levels);
     DevLeaf* s_leaves = reinterpret_cast<DevLeaf*>(smem + lay.leaves);
     V* s_lt = reinterpret_cast<V*>(smem + lay.table);
@@ -1116,6 +1129,7 @@ __global__ void __launch_bounds__(1024) multi_level_kernel(const JobDesc* __rest
     if (s_job != (int)ch.job) {
       copy_words(s_steps, J.steps, (size_t)J.n_steps * sizeof(DevStep));
       copy_words(s_out, J.out_start, (size_t)J.n_steps * 2 * sizeof(uint32_t));
+      copy_words(s_nib, J.pos_nib, (size_t)J.n_steps * kPosNibEntries * sizeof(uint16_t));
       copy_words(s_levels, J.levels, (size_t)J.n_levels * sizeof(DevLevel));
       copy_words(s_leaves, J.leaves, (size_t)J.n_leaves * sizeof(DevLeaf));
       copy_words(s_lt, J.leaf_table, (size_t)J.leaf_elems * sizeof(V));
@@ -1125,8 +1139,8 @@ __global__ void __launch_bounds__(1024) multi_level_kernel(const JobDesc* __rest
     double sr = 0.0, si = 0.0, cr = 0.0, ci = 0.0;
     for (uint64_t i0 = ch.lo; i0 < ch.hi; i0 += I) {
       const uint32_t nI = (uint32_t)((ch.hi - i0) < I ? (ch.hi - i0) : I);
-      level_run<V, Ops>(s_steps, s_out, s_levels, J.n_levels, s_leaves, s_lt, s_arena, J.arena_stride, log2I, i0,
-                        nI, sr, cr, si, ci);
+      level_run<V, Ops>(s_steps, s_out, s_nib, s_levels, J.n_levels, s_leaves, s_lt, s_arena, J.arena_stride,
+                        log2I, i0, nI, sr, cr, si, ci);
     }
     s_red[threadIdx.x] = Partial::make(sr, si, cr, ci);  // overlays the arenas
     tree_reduce(s_red, T);
@@ -1313,7 +1327,8 @@ cudaError_t launch_typed(const DeviceProgram& prog, const uint8_t* d_x, int nx, 
   if (e != cudaSuccess) return e;
   if (prog.n_pro_steps > 0 && prog.n_pro_levels > 0) {
     prologue_level_kernel<V, Ops><<<nx, kLevelPrologueThreads, shape.pro_smem, stream>>>(
-        prog.pro_steps, prog.n_pro_steps, prog.pro_out_start, prog.pro_levels, prog.n_pro_levels, prog.leaves,
+        prog.pro_steps, prog.n_pro_steps, prog.pro_out_start, prog.pro_pos_nib, prog.pro_levels, prog.n_pro_levels,
+        prog.leaves,
         prog.n_leaves, buf.leaf_tables, prog.leaf_elems, prog.pro_arena_elems);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -1351,7 +1366,8 @@ cudaError_t launch_typed(const DeviceProgram& prog, const uint8_t* d_x, int nx, 
   } else if (prog.exec == Executor::Warp) {
     block_exec_kernel<V, true, Ops><<<grid, shape.threads, shape.smem, stream>>>(P);
   } else if (prog.exec == Executor::Level) {
-    const LevelParams LP{prog.levels, prog.out_start, prog.n_levels, shape.log2_items, shape.arena_stride};
+    const LevelParams LP{prog.levels, prog.out_start, prog.pos_nib, prog.n_levels, shape.log2_items,
+                         shape.arena_stride};
     level_exec_kernel<V, Ops><<<grid, shape.threads, shape.smem, stream>>>(P, LP);
   } else {
     block_exec_kernel<V, false, Ops><<<grid, shape.threads, shape.smem, stream>>>(P);

@@ -55,6 +55,8 @@ struct DeviceProgram {
   const DevLevel* pro_levels = nullptr;  // level-ordered prologue (1024-thread blocks)
   const uint32_t* pro_out_start = nullptr;
   int n_pro_levels = 0;
+  const uint16_t* pos_nib = nullptr;      // store offsets by nibble (level programs)
+  const uint16_t* pro_pos_nib = nullptr;
   int block_threads = 256;  // threads per block (512 or 1024)
   int blocks_per_sm = 1;    // shared memory is sized for this many blocks per SM
 };
@@ -121,6 +123,8 @@ struct JobDesc {
   const DevLevel* pro_levels;
   const uint32_t* pro_out_start;
   int n_pro_levels;
+  const uint16_t* pos_nib;
+  const uint16_t* pro_pos_nib;
   int log2_items;          // items per block = 2^log2_items; chunks are multiples of it
   uint32_t arena_stride;   // elements between item arenas
   int density;             // leaves are G (x) conj(G) (density form)

@@ -424,6 +424,23 @@ std::string compile_program(const Network& net, const Plan& plan_in, const Progr
     err = tables(pg.steps, item_order, &pg.levels, &pg.out_start);
     if (err.empty()) err = tables(pg.prologue, pro_order, &pg.pro_levels, &pg.pro_out_start);
     if (!err.empty()) return err;
+    auto nibbles = [](const std::vector<DevStep>& steps, std::vector<uint16_t>* out) {
+      out->assign(steps.size() * kPosNibEntries, 0);
+      for (size_t i = 0; i < steps.size(); ++i) {
+        const DevStep& st = steps[i];
+        const int rc = st.ma + st.nb + st.bb;
+        if (st.flags & STEP_ROOT) continue;
+        for (int g = 0; g < 4; ++g)
+          for (int v = 0; v < 16; ++v) {
+            uint32_t pos = 0;
+            for (int b = 0; b < 4; ++b)
+              if (((v >> b) & 1) && 4 * g + b < rc) pos += st.w[4 * g + b];
+            (*out)[i * kPosNibEntries + 16 * g + v] = (uint16_t)pos;
+          }
+      }
+    };
+    nibbles(pg.steps, &pg.pos_nib);
+    nibbles(pg.prologue, &pg.pro_pos_nib);
   }
 
   pg.gate_q.resize(2 * net.gates.size());

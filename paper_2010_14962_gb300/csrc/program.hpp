@@ -91,6 +91,7 @@ static_assert(sizeof(DevStep) == 52, "DevStep layout");
 // output).
 constexpr int kLevelUnitLog2 = 2;
 constexpr int kRootSplitLog2 = 2;
+constexpr int kPosNibEntries = 64;  // per step: 4 nibbles x 16 values (ranks <= 16)
 constexpr int kLevelUnit = 1 << kLevelUnitLog2;
 struct DevLevel {
   uint16_t first, count;
@@ -120,6 +121,10 @@ struct Program {
   std::vector<uint32_t> out_start;   // per step: first unit in its level's range, 2 per step (as DevLevel::units)
   std::vector<DevLevel> pro_levels;  // the same for the prologue
   std::vector<uint32_t> pro_out_start;
+  // Level-ordered programs: store offsets by nibble, 64 per step: entry
+  // [16 g + v] = the offset of output bits 4g..4g+3 equal to v (sum of the
+  // step's bit weights), so pos(o) = sum_g entry[16 g + nibble_g(o)].
+  std::vector<uint16_t> pos_nib, pro_pos_nib;
   std::vector<DevStep> prologue;     // once per bit string: merges that no outer class reaches
   uint32_t pro_arena_elems = 0;      // prologue arena (elements)
   double macs_prologue = 0;          // per bit string
