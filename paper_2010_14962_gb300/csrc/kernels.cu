@@ -699,7 +699,9 @@ __host__ __device__ inline LevelLayout level_layout(int n_steps, int n_levels, i
   LevelLayout L;
   L.out_start = align16((size_t)n_steps * sizeof(DevStep));
   L.nib = L.out_start + align16((size_t)n_steps * 2 * sizeof(uint32_t));
-  L.levels = L.nib + align16((size_t)n_steps * kPosNibEntries * sizeof(uint16_t));
+  // Nibble tables of store offsets: 16-byte types only (one output per unit;
+  // complex64 units of four compute one offset per four outputs).
+  L.levels = L.nib + (elem_bytes == 16 ? align16((size_t)n_steps * kPosNibEntries * sizeof(uint16_t)) : 0);
   L.leaves = L.levels + align16((size_t)n_levels * sizeof(DevLevel));
   L.table = L.leaves + align16((size_t)n_leaves * sizeof(DevLeaf));
   L.arena = L.table + align16((size_t)leaf_elems * elem_bytes);
@@ -726,7 +728,8 @@ struct LStep {
   uint32_t ulog;      // log2 entries per unit
   int groups;         // nibbles of an output index
   uint8_t flags;
-  const uint16_t* nib;  // store offsets by nibble (shared memory)
+  const uint16_t* nib;  // store offsets by nibble (shared memory; 16-byte types)
+  const uint16_t* w;    // store bit weights (shared memory)
 };
 
 // One unit of a (non-root) merge for one item: outputs o0 .. o0 + u - 1
@@ -738,8 +741,12 @@ __device__ __forceinline__ void level_unit(const LStep& q, uint32_t o0, uint32_t
                                            const V* __restrict__ B, V* __restrict__ C) {
   const int ma = q.ma, nb = q.nb, kb = q.kb;
   uint32_t pos0 = 0;
-  for (int g = 0; g < q.groups; ++g) pos0 += q.nib[16 * g + ((o0 >> (4 * g)) & 15u)];
-  const uint32_t w0 = UNIT > 1 ? q.nib[1] : 0u, w1 = UNIT > 2 ? q.nib[2] : 0u;
+  if (UNIT == 1) {
+    for (int g = 0; g < q.groups; ++g) pos0 += q.nib[16 * g + ((o0 >> (4 * g)) & 15u)];
+  } else {
+    for (uint32_t x = o0; x; x &= x - 1u) pos0 += q.w[__ffs(x) - 1];
+  }
+  const uint32_t w0 = UNIT > 1 ? q.w[0] : 0u, w1 = UNIT > 2 ? q.w[1] : 0u;
   const uint32_t mmask = (1u << ma) - 1u, nmask = (1u << nb) - 1u;
 #pragma unroll
   for (uint32_t r = 0; r < (uint32_t)UNIT; ++r) {
@@ -828,6 +835,7 @@ __device__ __forceinline__ void level_run(const DevStep* s_steps, const uint32_t
     q.b = st.b;
     q.c = (st.flags & STEP_EXPORT) ? s_leaves[st.c].base : st.c;
     q.nib = s_nib + (size_t)j * kPosNibEntries;
+    q.w = st.w;
     q.groups = (st.ma + st.nb + st.bb + 3) >> 2;
     q.ks = UL ? root_split(st) : 0;  // split roots in the four-output table only
     const int rc = st.ma + st.nb + st.bb + q.ks;
@@ -890,7 +898,7 @@ __global__ void __launch_bounds__(1024) level_exec_kernel(ExecParams P, LevelPar
   const int bx = blockIdx.x % P.blocks_per_x;
   copy_words(s_steps, P.steps, (size_t)P.n_steps * sizeof(DevStep));
   copy_words(s_out, LP.out_start, (size_t)P.n_steps * 2 * sizeof(uint32_t));
-  copy_words(s_nib, LP.pos_nib, (size_t)P.n_steps * kPosNibEntries * sizeof(uint16_t));
+  if (sizeof(V) == 16) copy_words(s_nib, LP.pos_nib, (size_t)P.n_steps * kPosNibEntries * sizeof(uint16_t));
   copy_words(s_levels, LP.levels, (size_t)LP.n_levels * sizeof(DevLevel));
   copy_words(s_leaves, P.leaves, (size_t)P.n_leaves * sizeof(DevLeaf));
   copy_words(s_lt, static_cast<const V*>(P.leaf_tables) + (size_t)xi * P.leaf_elems,
@@ -930,7 +938,7 @@ __device__ __forceinline__ void prologue_level_body(const DevStep* __restrict__ 
   V* s_arena = reinterpret_cast<V*>(smem + lay.arena);
   copy_words(s_steps, steps, (size_t)n_steps * sizeof(DevStep));
   copy_words(s_out, out_start, (size_t)n_steps * 2 * sizeof(uint32_t));
-  copy_words(s_nib, pos_nib, (size_t)n_steps * kPosNibEntries * sizeof(uint16_t));
+  if (sizeof(V) == 16) copy_words(s_nib, pos_nib, (size_t)n_steps * kPosNibEntries * sizeof(uint16_t));
   copy_words(s_levels, levels, (size_t)n_levels * sizeof(DevLevel));
   copy_words(s_leaves, leaves, (size_t)n_leaves * sizeof(DevLeaf));
   copy_words(s_lt, g_lt, (size_t)leaf_elems * sizeof(V));
@@ -1129,7 +1137,7 @@ __global__ void __launch_bounds__(1024) multi_level_kernel(const JobDesc* __rest
     if (s_job != (int)ch.job) {
       copy_words(s_steps, J.steps, (size_t)J.n_steps * sizeof(DevStep));
       copy_words(s_out, J.out_start, (size_t)J.n_steps * 2 * sizeof(uint32_t));
-      copy_words(s_nib, J.pos_nib, (size_t)J.n_steps * kPosNibEntries * sizeof(uint16_t));
+      if (sizeof(V) == 16) copy_words(s_nib, J.pos_nib, (size_t)J.n_steps * kPosNibEntries * sizeof(uint16_t));
       copy_words(s_levels, J.levels, (size_t)J.n_levels * sizeof(DevLevel));
       copy_words(s_leaves, J.leaves, (size_t)J.n_leaves * sizeof(DevLeaf));
       copy_words(s_lt, J.leaf_table, (size_t)J.leaf_elems * sizeof(V));
