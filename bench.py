@@ -582,6 +582,101 @@ def run_uneven(args, rank, world, local_rank):
         dist.destroy_process_group()
 
 
+LEARNED = dict(name="learned120", n=120, p=1, k=22, seed=5, bitstrings=8, train=200000, holdout=10000,
+               train_n=(40, 120), train_k=(8, 24), epochs=40)
+
+
+def run_learned(args, rank, world, local_rank):
+    """The learned planner at n = 120: the surrogate is trained on the device
+    on exact-counter labels, then Algorithm 1 guided by it and Algorithm 1 with
+    the exact counter search 22 cuts under the same wall-clock budget; both
+    plans are contracted (FP32X2) on the same bit strings."""
+    import torch
+
+    from paper_2010_14962_gb300 import instances as I
+    from paper_2010_14962_gb300 import qtn
+
+    torch.cuda.set_device(local_rank)
+    if rank != 0:
+        return
+    w = LEARNED
+    threads = min(32, os.cpu_count() or 1)
+    t0 = time.perf_counter()
+    X, Y = qtn.surrogate_dataset(w["train"] + w["holdout"], w["train_n"][0], w["train_n"][1], 1, 1, w["train_k"][0],
+                                 w["train_k"][1], seed=11, threads=threads)
+    t_data = time.perf_counter() - t0
+    m = qtn.MLP(qtn.SURROGATE_FEATURES, 256, qtn.SURROGATE_TARGETS, seed=1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = m.fit(X[: w["train"]], Y[: w["train"]], epochs=w["epochs"], batch=512, lr=1e-3, seed=2)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    P = m.predict(X[w["train"]:])
+    Yv = Y[w["train"]:]
+    rank_of = lambda v: np.argsort(np.argsort(v))
+    spearman = float(np.corrcoef(rank_of(P[:, 0]), rank_of(Yv[:, 0]))[0, 1])
+    mae = float(np.mean(np.abs(P[:, 0] - Yv[:, 0])))
+
+    inst = I.qaoa_instance(w["n"], w["p"], w["seed"])
+    net = qtn.Network(w["n"], inst.edges, inst.gamma, inst.beta)
+    searches = {}
+    for seed_greedy in (False, True):
+        t0 = time.perf_counter()
+        cuts_s, best_s, n_exact, n_sur, _ = qtn.search_cuts_surrogate(net, w["k"], m, T=10, N=256, top=4, seed=1,
+                                                                       seed_greedy=seed_greedy)
+        budget = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        cuts_e, _, n_ga = qtn.search_cuts(net, w["k"], "ga_flops", seed=1, ga_T=10 ** 6, ga_N=11,
+                                          seed_greedy=seed_greedy, time_budget_s=budget)
+        t_e = time.perf_counter() - t0
+        best_e = float(qtn.surrogate_labels(net, cuts_e)[0])
+        searches["greedy_seeded" if seed_greedy else "random_start"] = dict(
+            budget_s=budget, surrogate=dict(log2_flops=float(best_s), surrogate_evals=n_sur, exact_evals=n_exact,
+                                            cuts=[int(c) for c in cuts_s]),
+            exact=dict(log2_flops=best_e, exact_evals=n_ga, search_s=t_e, cuts=[int(c) for c in cuts_e]))
+    pick = searches["greedy_seeded"]
+    plans = {"surrogate": qtn.Plan(net, cuts=pick["surrogate"]["cuts"], max_slice_bytes=150e9),
+             "exact": qtn.Plan(net, cuts=pick["exact"]["cuts"], max_slice_bytes=150e9)}
+    xs = I.bitstrings(w["n"], w["bitstrings"], w["seed"])
+    d_x = torch.from_numpy(np.ascontiguousarray(xs)).cuda()
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    results, vals = {}, {}
+    for name, plan in plans.items():
+        d_out = torch.zeros((len(xs), 2), dtype=torch.float64, device="cuda")
+        for _ in range(args.warmup):
+            plan.contract_amplitudes_device(d_x, d_out, "fp32x2", stream)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * args.steps)]
+        for i in range(args.steps):
+            ev[2 * i].record(stream)
+            plan.contract_amplitudes_device(d_x, d_out, "fp32x2", stream)
+            ev[2 * i + 1].record(stream)
+            flush.zero_()
+        torch.cuda.synchronize()
+        ms = sum(ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(args.steps))
+        o = d_out.cpu().numpy()
+        vals[name] = o[:, 0] + 1j * o[:, 1]
+        c = plan.cost()
+        results[name] = dict(amplitudes_per_s=len(xs) * args.steps / (ms / 1e3), log2_flops=c["log2_flops"],
+                             log2_peak_bytes=c["log2_peak_bytes"], width=c["width"])
+    agree = float(np.max(np.abs(vals["surrogate"] - vals["exact"]) / np.abs(vals["exact"])))
+    out = {
+        "metric": "amplitudes/sec, n=120 QAOA p=1, 22 cuts from the surrogate-guided search",
+        "value": results["surrogate"]["amplitudes_per_s"], "unit": "amplitudes/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "c64x2 (double-float)", "data": "synthetic: seeded random 3-regular graphs",
+        "config": {"workload": w["name"], "n": w["n"], "p": w["p"], "cuts": w["k"], "bitstrings_per_step": len(xs),
+                   "surrogate": {"train_pairs": w["train"], "holdout_pairs": w["holdout"], "epochs": w["epochs"],
+                                 "layers": 3, "width": 256, "dataset_s": t_data, "train_s": t_train,
+                                 "loss_first_last": [float(losses[0]), float(losses[-1])],
+                                 "holdout_spearman_log2_flops": spearman, "holdout_mae_log2_flops": mae},
+                   "searches": searches, "contracted": results, "max_rel_diff_between_plans": agree,
+                   "memory_cap_bytes": 150e9},
+    }
+    print(json.dumps(out), flush=True)
+
+
 def setup_workload_cpu():
     """Plan on the host only (the reference arm needs no GPU)."""
     return setup_workload(0)
@@ -599,7 +694,7 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--executor", default=None, help="force an executor (default: autotuned)")
-    ap.add_argument("--workload", default="qaoa80_p1_k16", choices=["qaoa80_p1_k16", "uneven64"],
+    ap.add_argument("--workload", default="qaoa80_p1_k16", choices=["qaoa80_p1_k16", "uneven64", "learned120"],
                     help="uneven64: 64 independent jobs of different plans in one launch sequence")
     ap.add_argument("--form", default="gates", choices=["gates", "gm"],
                     help="network form of the n=80 workload: the paper's gate network (16 cuts) or the "
@@ -618,6 +713,8 @@ def main():
         run_reference(args, rank, world)
     elif args.workload == "uneven64":
         run_uneven(args, rank, world, local_rank)
+    elif args.workload == "learned120":
+        run_learned(args, rank, world, local_rank)
     else:
         run_ours(args, rank, world, local_rank)
 
