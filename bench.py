@@ -620,20 +620,23 @@ def run_learned(args, rank, world, local_rank):
     inst = I.qaoa_instance(w["n"], w["p"], w["seed"])
     net = qtn.Network(w["n"], inst.edges, inst.gamma, inst.beta)
     searches = {}
-    for seed_greedy in (False, True):
+    for label, seed_greedy, seed in (("random_start_seed1", False, 1), ("random_start_seed2", False, 2),
+                                     ("random_start_seed3", False, 3), ("greedy_seeded", True, 1)):
         t0 = time.perf_counter()
-        cuts_s, best_s, n_exact, n_sur, _ = qtn.search_cuts_surrogate(net, w["k"], m, T=10, N=256, top=4, seed=1,
+        cuts_s, best_s, n_exact, n_sur, _ = qtn.search_cuts_surrogate(net, w["k"], m, T=10, N=256, top=4, seed=seed,
                                                                        seed_greedy=seed_greedy)
         budget = time.perf_counter() - t0
         t0 = time.perf_counter()
-        cuts_e, _, n_ga = qtn.search_cuts(net, w["k"], "ga_flops", seed=1, ga_T=10 ** 6, ga_N=11,
+        cuts_e, _, n_ga = qtn.search_cuts(net, w["k"], "ga_flops", seed=seed, ga_T=10 ** 6, ga_N=11,
                                           seed_greedy=seed_greedy, time_budget_s=budget)
         t_e = time.perf_counter() - t0
         best_e = float(qtn.surrogate_labels(net, cuts_e)[0])
-        searches["greedy_seeded" if seed_greedy else "random_start"] = dict(
+        searches[label] = dict(
             budget_s=budget, surrogate=dict(log2_flops=float(best_s), surrogate_evals=n_sur, exact_evals=n_exact,
                                             cuts=[int(c) for c in cuts_s]),
             exact=dict(log2_flops=best_e, exact_evals=n_ga, search_s=t_e, cuts=[int(c) for c in cuts_e]))
+    gains = [searches[k]["exact"]["log2_flops"] - searches[k]["surrogate"]["log2_flops"]
+             for k in searches if k.startswith("random_start")]
     pick = searches["greedy_seeded"]
     plans = {"surrogate": qtn.Plan(net, cuts=pick["surrogate"]["cuts"], max_slice_bytes=150e9),
              "exact": qtn.Plan(net, cuts=pick["exact"]["cuts"], max_slice_bytes=150e9)}
@@ -671,7 +674,9 @@ def run_learned(args, rank, world, local_rank):
                                  "layers": 3, "width": 256, "dataset_s": t_data, "train_s": t_train,
                                  "loss_first_last": [float(losses[0]), float(losses[-1])],
                                  "holdout_spearman_log2_flops": spearman, "holdout_mae_log2_flops": mae},
-                   "searches": searches, "contracted": results, "max_rel_diff_between_plans": agree,
+                   "searches": searches,
+                   "random_start_mean_gain_log2_flops": float(np.mean(gains)),
+                   "contracted": results, "max_rel_diff_between_plans": agree,
                    "memory_cap_bytes": 150e9},
     }
     print(json.dumps(out), flush=True)
