@@ -343,7 +343,8 @@ struct qtn_plan {
     QTN_CUDA(cudaMalloc((void**)&d_out_stage, (size_t)nnx * sizeof(double2)));
     QTN_CUDA(cudaMalloc((void**)&d_raw_stage, (size_t)nnx * sizeof(Partial)));
     QTN_CUDA(cudaMallocHost((void**)&h_x_pinned, (size_t)nnx * net.n));
-    QTN_CUDA(cudaMallocHost((void**)&h_out_pinned, (size_t)nnx * 4 * sizeof(double)));
+    // Results, then one slot for the executor's error word (read back with them).
+    QTN_CUDA(cudaMallocHost((void**)&h_out_pinned, ((size_t)nnx * 4 + 1) * sizeof(double)));
     cap_nx = nnx;
     cap_blocks = nb;
     return QTN_OK;
@@ -365,10 +366,17 @@ struct qtn_plan {
   qtn_status prepare(int si, qtn_precision prec, int nx, uint64_t items, ExecShape* sh) {
     qtn_status st = upload(slots[si]);
     if (st != QTN_OK) return st;
-    if (!exec_shape(slots[si].dprog, arith_of(prec), nx, items, sh))
-      return fail(QTN_ERR_UNSUPPORTED, "the plan's per-item working set does not fit in shared memory");
+    const auto key = std::make_tuple(si, (int)prec, nx, items);
+    auto it = shapes.find(key);
+    if (it == shapes.end()) {
+      if (!exec_shape(slots[si].dprog, arith_of(prec), nx, items, sh))
+        return fail(QTN_ERR_UNSUPPORTED, "the plan's per-item working set does not fit in shared memory");
+      it = shapes.emplace(key, *sh).first;
+    }
+    *sh = it->second;
     return ensure_workspace(nx, sh->blocks_per_x);
   }
+  std::map<std::tuple<int, int, int, uint64_t>, ExecShape> shapes;  // launch shapes by (slot, prec, nx, items)
 
   bool eligible(int si, qtn_precision prec) const {
     const ProgSlot& s = slots[si];
@@ -466,10 +474,15 @@ struct qtn_plan {
     return QTN_OK;
   }
 
+  int* err_slot() { return reinterpret_cast<int*>(h_out_pinned + (size_t)cap_nx * 4); }
+  // Enqueues the read-back of the executor's error word next to the results.
+  qtn_status read_err_flag(cudaStream_t stream) {
+    QTN_CUDA(cudaMemcpyAsync(err_slot(), d_err, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    return QTN_OK;
+  }
+  // After the stream is synchronised: the word read by read_err_flag.
   qtn_status check_err_flag() {
-    int h = 0;
-    QTN_CUDA(cudaMemcpy(&h, d_err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (h != 0) {
+    if (*err_slot() != 0) {
       cudaMemset(d_err, 0, sizeof(int));
       return fail(QTN_ERR_UNSUPPORTED, "the executor met a merge shape it does not implement");
     }
@@ -934,6 +947,8 @@ qtn_status qtn_contract_amplitude(const qtn_plan_t* cplan, const uint8_t* x, qtn
   st = plan->run_graph(plan->d_x_stage, 1, prec, plan->d_out_stage, stream);
   if (st != QTN_OK) return st;
   QTN_CUDA(cudaMemcpyAsync(plan->h_out_pinned, plan->d_out_stage, sizeof(double2), cudaMemcpyDeviceToHost, stream));
+  st = plan->read_err_flag(stream);
+  if (st != QTN_OK) return st;
   QTN_CUDA(cudaStreamSynchronize(stream));
   st = plan->check_err_flag();
   if (st != QTN_OK) return st;
@@ -968,6 +983,8 @@ qtn_status qtn_contract_slices(const qtn_plan_t* cplan, const uint8_t* x, uint64
                                       reinterpret_cast<double2*>(d_slices), stream);
   if (le != cudaSuccess) return cuda_fail(le, "launch_contraction");
   QTN_CUDA(cudaMemcpyAsync(plan->h_out_pinned, plan->d_raw_stage, sizeof(Partial), cudaMemcpyDeviceToHost, stream));
+  st = plan->read_err_flag(stream);
+  if (st != QTN_OK) return st;
   QTN_CUDA(cudaStreamSynchronize(stream));
   st = plan->check_err_flag();
   if (st != QTN_OK) return st;
@@ -1006,6 +1023,8 @@ qtn_status qtn_contract_batch(const qtn_plan_t* const* plans, const uint8_t* con
     if (st != QTN_OK) return st;
     QTN_CUDA(cudaMemcpyAsync(plan->h_out_pinned, plan->d_out_stage, (size_t)njobs * sizeof(double2),
                              cudaMemcpyDeviceToHost, stream));
+    st = plan->read_err_flag(stream);
+    if (st != QTN_OK) return st;
     QTN_CUDA(cudaStreamSynchronize(stream));
     st = plan->check_err_flag();
     if (st != QTN_OK) return st;

@@ -1212,9 +1212,24 @@ struct LaneCapable : std::false_type {};
 template <class V>
 struct LaneCapable<CplxOps<V>> : std::true_type {};
 
+// Every kernel's dynamic shared memory cap is set to the device's opt-in
+// maximum, not to one launch's size: a cap is global per kernel, and a
+// captured graph of one plan must stay valid after another plan launches the
+// same kernel with less shared memory.
+int max_optin_smem() {
+  int dev = 0, v = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  return v;
+}
+template <class K>
+cudaError_t allow_max_smem(K kernel) {
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin_smem());
+}
+
 template <class K>
 bool shape_for_kernel(K kernel, int threads, size_t smem, int* occ) {
-  if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return false;
+  if (allow_max_smem(kernel) != cudaSuccess) return false;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kernel, threads, smem) == cudaSuccess && *occ >= 1;
 }
 
@@ -1296,17 +1311,13 @@ bool exec_shape_typed(const DeviceProgram& prog, int nx, uint64_t slices_per_x, 
                                         prog.pro_arena_elems | 1u, 1, elem_bytes, kLevelPrologueThreads);
     if (PL.total > (size_t)max_optin) return false;
     sh.pro_smem = PL.total;
-    if (cudaFuncSetAttribute(prologue_level_kernel<V, Ops>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)PL.total) != cudaSuccess)
-      return false;
+    if (allow_max_smem(prologue_level_kernel<V, Ops>) != cudaSuccess) return false;
   } else if (prog.n_pro_steps > 0) {
     const SmemLayout PL = smem_layout(prog.n_pro_steps, prog.n_leaves, prog.leaf_elems, prog.pro_arena_elems,
                                       elem_bytes, 256, false);
     if (PL.total > (size_t)max_optin) return false;
     sh.pro_smem = PL.total;
-    if (cudaFuncSetAttribute(prologue_kernel<V, Ops>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PL.total) !=
-        cudaSuccess)
-      return false;
+    if (allow_max_smem(prologue_kernel<V, Ops>) != cudaSuccess) return false;
   }
   const uint64_t total_blocks = (uint64_t)g_num_sms * (uint64_t)occ;
   uint64_t per_x = total_blocks / (uint64_t)(nx > 0 ? nx : 1);
@@ -1400,12 +1411,8 @@ cudaError_t launch_multi_typed(const JobDesc* d_jobs, int njobs, uint32_t total_
   cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (exec_smem > (size_t)max_optin || pro_smem > (size_t)max_optin) return cudaErrorInvalidValue;
   cudaError_t e;
-  if ((e = cudaFuncSetAttribute(multi_prologue_kernel<V, Ops>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)pro_smem)) != cudaSuccess)
-    return e;
-  if ((e = cudaFuncSetAttribute(multi_prologue_level_kernel<V, Ops>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)pro_smem)) != cudaSuccess)
-    return e;
+  if ((e = allow_max_smem(multi_prologue_kernel<V, Ops>)) != cudaSuccess) return e;
+  if ((e = allow_max_smem(multi_prologue_level_kernel<V, Ops>)) != cudaSuccess) return e;
   const int threads = level ? kMultiLevelThreads : 256;
   if (level ? !shape_for_kernel(multi_level_kernel<V, Ops>, threads, exec_smem, &occ)
             : !shape_for_kernel(multi_exec_kernel<V, Ops>, threads, exec_smem, &occ))
