@@ -1070,7 +1070,7 @@ qtn_status qtn_contract_batch(const qtn_plan_t* const* plans, const uint8_t* con
     int lg = 5;
     for (; lg >= 0; --lg)
       if (level_smem_bytes((int)pg.steps.size(), (int)pg.levels.size(), (int)pg.leaves.size(), pg.leaf_elems,
-                           pg.arena_elems | 1u, 1 << lg, arith, kMultiLevelThreads) <= (size_t)max_optin)
+                           pg.arena_elems | 1u, 1 << lg, arith, kMultiLevelThreads) <= (size_t)max_optin - 64)
         break;
     if (lg < 0) {
       level = false;
@@ -1141,7 +1141,7 @@ qtn_status qtn_contract_batch(const qtn_plan_t* const* plans, const uint8_t* con
     int dev = 0, max_optin = 0;
     QTN_CUDA(cudaGetDevice(&dev));
     QTN_CUDA(cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    if (exec_smem > (size_t)max_optin || pro_smem > (size_t)max_optin)
+    if (exec_smem > (size_t)max_optin - 64 || pro_smem > (size_t)max_optin - 64)  // 64: the kernels' static words
       return fail(QTN_ERR_UNSUPPORTED, "a job's per-slice working set does not fit in shared memory");
   }
   // Workspace (grow-only, shared by batch calls on this device).

@@ -1224,7 +1224,12 @@ int max_optin_smem() {
 }
 template <class K>
 cudaError_t allow_max_smem(K kernel) {
-  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin_smem());
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  // Static and dynamic shared memory together may not exceed the opt-in maximum.
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              max_optin_smem() - (int)fa.sharedSizeBytes);
 }
 
 template <class K>
