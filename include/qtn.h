@@ -258,10 +258,10 @@ qtn_status qtn_contract_slices(const qtn_plan_t* plan, const uint8_t* x, uint64_
  * persistent kernel whose blocks take (job, item range) chunks from a device
  * counter -- largest jobs first -- and a fixed-order per-job sum of the chunk
  * partials, so results do not depend on the block schedule.  Each job runs
- * its plan's level program of the 48 KiB budget, else its per-class level
- * program, with as many items per block as fit (1024 threads); if some job's
- * level program does not fit, every job runs its 48 KiB batched (else
- * per-class) block program instead.
+ * the level program of its plan (of this precision's width) that executes
+ * the fewest multiply-adds and fits in shared memory, with as many items per
+ * block as fit (1024 threads); if some job has none that fits, every job
+ * runs its 48 KiB batched (else per-class) block program instead.
  * Errors: QTN_ERR_INVALID_ARG (NULL plan, bad x), QTN_ERR_UNSUPPORTED (a
  * job's working set exceeds shared memory), QTN_ERR_CUDA.  Internal device
  * and pinned buffers are kept between calls (grow-only); calls from several

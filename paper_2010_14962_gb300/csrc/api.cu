@@ -1060,24 +1060,34 @@ qtn_status qtn_contract_batch(const qtn_plan_t* const* plans, const uint8_t* con
   std::vector<JobHost> jh(njobs);
   bool level = true;
   for (int j = 0; j < njobs && level; ++j) {
+    // The level program of this precision's width (or of either) that does
+    // the least work and fits on chip; as many items per block as fit.
     const qtn_plan_t* plan = plans[j];
-    const int si = find_slot(plan, {wide(prec) ? "level/fp64/48KiB" : "level/fp32/48KiB", "level/classes"});
+    int si = -1, lg_best = -1;
+    double best = 0;
+    for (int k = 1; k < (int)plan->slots.size(); ++k) {
+      const ProgSlot& sl = plan->slots[k];
+      if (sl.exec != Executor::Level || !plan->eligible(k, prec)) continue;
+      const Program& pg = sl.prog;
+      int lg = 5;
+      for (; lg >= 0; --lg)
+        if (level_smem_bytes((int)pg.steps.size(), (int)pg.levels.size(), (int)pg.leaves.size(), pg.leaf_elems,
+                             pg.arena_elems | 1u, 1 << lg, arith, kMultiLevelThreads) <= (size_t)max_optin - 64)
+          break;
+      if (lg < 0) continue;
+      const double work = std::ldexp(pg.macs_per_item, pg.n_outer);
+      if (si < 0 || work < best) {
+        si = k;
+        best = work;
+        lg_best = lg;
+      }
+    }
     if (si < 0) {
       level = false;
       break;
     }
     const Program& pg = plan->slots[si].prog;
-    int lg = 5;
-    for (; lg >= 0; --lg)
-      if (level_smem_bytes((int)pg.steps.size(), (int)pg.levels.size(), (int)pg.leaves.size(), pg.leaf_elems,
-                           pg.arena_elems | 1u, 1 << lg, arith, kMultiLevelThreads) <= (size_t)max_optin - 64)
-        break;
-    if (lg < 0) {
-      level = false;
-      break;
-    }
-    jh[j] = JobHost{j, const_cast<qtn_plan_t*>(plan), si, std::ldexp(pg.macs_per_item, pg.n_outer),
-                    1ull << pg.n_outer, lg};
+    jh[j] = JobHost{j, const_cast<qtn_plan_t*>(plan), si, best, 1ull << pg.n_outer, lg_best};
   }
   if (!level) {
     for (int j = 0; j < njobs; ++j) {

@@ -418,16 +418,23 @@ def batch_last_ms():
 
 
 def batch_program(plan, precision: str) -> str:
-    """Name of the program a multi-plan contract_batch runs for ``plan``: its
-    48 KiB level program of the precision's width, else its per-class level
-    program (the rule qtn_contract_batch documents, when every job's level
-    program fits in shared memory)."""
+    """Name of the program a multi-plan contract_batch runs for ``plan`` (the
+    rule qtn_contract_batch documents): among its level programs of the
+    precision's width, the one with the fewest executed multiply-adds.  (The
+    library also requires it to fit in shared memory, which this host-side
+    helper does not check.)"""
     progs = plan.describe()["programs"]
-    width = "fp64" if precision in ("fp64", "fp32x2") else "fp32"
-    for name in (f"level/{width}/48KiB", "level/classes", f"batched/{width}/48KiB", "block/classes"):
-        if name in progs:
-            return name
-    raise QTNError(6, "the plan has no program for a batch")
+    other = "/fp32/" if precision in ("fp64", "fp32x2") else "/fp64/"
+    best, best_work = None, None
+    for name, pr in progs.items():
+        if pr["executor"] != "level" or other in name:
+            continue
+        work = (2 ** len(pr["outer_class"])) * pr["macs_per_item"]
+        if best is None or work < best_work:
+            best, best_work = name, work
+    if best is None:
+        raise QTNError(6, "the plan has no level program for a batch")
+    return best
 
 
 # ------------------------------------------------------- learned surrogate --
