@@ -689,6 +689,32 @@ qtn_status qtn_plan(const qtn_network_t* net, const int32_t* cuts, int k, const 
     sl.exec = Executor::Block;
     if (compile_program(h->net, h->plan, o, &sl.prog).empty()) h->slots.push_back(std::move(sl));
   }
+  // A level program in two shapes: 512 threads with two blocks per SM (a
+  // block's barrier waits overlap the other's work), or one block of 1024
+  // threads with twice the shared memory for items.  If levels by depth need
+  // more arena than the depth-first program (seq_arena), a memory-bounded
+  // variant ("/fit": depth-first levels within that arena) is added too.
+  auto add_level_slots = [&](ProgSlot lv, ProgramOptions o, uint32_t seq_arena) {
+    for (int bounded = 0; bounded < 2; ++bounded) {
+      ProgSlot v = lv;
+      o.level_budget = bounded ? seq_arena : 0;
+      if (bounded) {
+        const ProgSlot& depth_form = h->slots.back();
+        if (seq_arena == 0 || depth_form.name.rfind(lv.name, 0) != 0 || depth_form.prog.arena_elems <= seq_arena)
+          break;
+        v.name += "/fit";
+      }
+      if (!compile_program(h->net, h->plan, o, &v.prog).empty()) break;
+      v.threads = 512;
+      v.blocks_per_sm = 2;
+      ProgSlot wide_v = v;
+      wide_v.name += "/t1024";
+      wide_v.threads = 1024;
+      wide_v.blocks_per_sm = 1;
+      h->slots.push_back(std::move(v));
+      h->slots.push_back(std::move(wide_v));
+    }
+  };
   struct Budget {
     const char* name;
     uint32_t elems;
@@ -723,19 +749,8 @@ qtn_status qtn_plan(const qtn_network_t* net, const int32_t* cuts, int k, const 
     lv.fp64_only = bd.fp64;
     lv.fp32_only = !bd.fp64;
     o.levels = true;
-    if (compile_program(h->net, h->plan, o, &lv.prog).empty()) {
-      // Two shapes: 512 threads with two blocks per SM (a block's barrier
-      // waits overlap the other's work), or one block of 1024 threads with
-      // twice the shared memory for items.
-      lv.threads = 512;
-      lv.blocks_per_sm = 2;
-      ProgSlot wide_lv = lv;
-      wide_lv.name += "/t1024";
-      wide_lv.threads = 1024;
-      wide_lv.blocks_per_sm = 1;
-      h->slots.push_back(std::move(lv));
-      h->slots.push_back(std::move(wide_lv));
-    }
+    const uint32_t seq_arena = h->slots.back().prog.arena_elems;
+    add_level_slots(std::move(lv), o, seq_arena);
   }
   {
     ProgramOptions o;
@@ -744,16 +759,10 @@ qtn_status qtn_plan(const qtn_network_t* net, const int32_t* cuts, int k, const 
     ProgSlot sl;
     sl.name = "level/classes";
     sl.exec = Executor::Level;
-    if (compile_program(h->net, h->plan, o, &sl.prog).empty()) {
-      sl.threads = 512;
-      sl.blocks_per_sm = 2;
-      ProgSlot wide_sl = sl;
-      wide_sl.name += "/t1024";
-      wide_sl.threads = 1024;
-      wide_sl.blocks_per_sm = 1;
-      h->slots.push_back(std::move(sl));
-      h->slots.push_back(std::move(wide_sl));
-    }
+    uint32_t seq_arena = 0;
+    for (const ProgSlot& x : h->slots)
+      if (x.name == "block/classes") seq_arena = x.prog.arena_elems;
+    add_level_slots(std::move(sl), o, seq_arena);
   }
   if (h->slots.size() == 1) {  // nothing else fits: the per-slice program
     ProgSlot sl = h->slots[0];

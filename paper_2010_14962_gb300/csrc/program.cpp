@@ -302,20 +302,39 @@ std::string compile_program(const Network& net, const Plan& plan_in, const Progr
         level_of[j] = lev_t[mg.c];
       }
     }
-    for (std::vector<int>* seq : {&pro_order, &item_order})
-      std::stable_sort(seq->begin(), seq->end(), [&](int x, int y) { return level_of[x] < level_of[y]; });
+    std::stable_sort(pro_order.begin(), pro_order.end(), [&](int x, int y) { return level_of[x] < level_of[y]; });
+    if (opt.level_budget == 0)
+      std::stable_sort(item_order.begin(), item_order.end(),
+                       [&](int x, int y) { return level_of[x] < level_of[y]; });
   }
+  // Memory-bounded levels of the item steps (depth-first order): the level
+  // of each emitted step, assigned while emitting.
+  std::vector<int> item_level;
 
   std::vector<uint32_t> where(T, 0);
   auto emit = [&](bool prologue_pass, bool c_reuses_a, std::vector<DevStep>* out, uint32_t* arena_high,
                   double* macs) -> std::string {
     Arena arena;
     const bool by_level = opt.levels;
+    const bool bounded = by_level && !prologue_pass && opt.level_budget > 0;
     std::vector<uint32_t> level_release;  // inputs freed when their level ends
+    std::vector<char> in_level(T, 0);     // bounded: produced in the current level
+    std::vector<int> level_members;
+    int cur_level = 0;
+    auto close_level = [&]() {
+      for (uint32_t r : level_release) arena.release(r);
+      level_release.clear();
+      for (int t : level_members) in_level[t] = 0;
+      level_members.clear();
+      ++cur_level;
+    };
     const std::vector<int>& seq = prologue_pass ? pro_order : item_order;
     for (size_t si = 0; si < seq.size(); ++si) {
       const int j = seq[si];
       if ((bool)pro[j] != prologue_pass) continue;
+      if (bounded && !level_members.empty() &&
+          (in_level[plan.merges[j].a] || in_level[plan.merges[j].b]))
+        close_level();  // an operand is produced in this level: the step starts the next
       const Merge& mg = plan.merges[j];
       const Canon& c = canon[j];
       DevStep st{};
@@ -366,6 +385,11 @@ std::string compile_program(const Network& net, const Plan& plan_in, const Progr
           st.c = (uint32_t)leaf_id[mg.c];
         } else {
           uint32_t off = arena.alloc(1u << rc);
+          if (bounded && off + (1u << rc) > opt.level_budget && !level_members.empty()) {
+            arena.release(off);  // over budget: the step starts the next level instead
+            close_level();
+            off = arena.alloc(1u << rc);
+          }
           where[mg.c] = off;
           st.c = off;
         }
@@ -376,7 +400,12 @@ std::string compile_program(const Network& net, const Plan& plan_in, const Progr
           st.w[b] = (uint16_t)(1u << (it - lay.begin()));
         }
       }
-      if (by_level) {
+      if (bounded) {
+        level_release.insert(level_release.end(), to_release.begin(), to_release.end());
+        in_level[mg.c] = 1;
+        level_members.push_back(mg.c);
+        item_level.push_back(cur_level);
+      } else if (by_level) {
         level_release.insert(level_release.end(), to_release.begin(), to_release.end());
         const bool level_ends = si + 1 == seq.size() || level_of[seq[si + 1]] != level_of[j];
         if (level_ends) {
@@ -396,6 +425,11 @@ std::string compile_program(const Network& net, const Plan& plan_in, const Progr
   if (!err.empty()) return err;
   if (pg.prologue.empty()) pg.pro_arena_elems = 0;
   if (opt.levels) {
+    // Level of emitted step i: its depth, or its bounded level.
+    std::vector<int> item_lv(pg.steps.size()), pro_lv(pg.prologue.size());
+    for (size_t i = 0; i < pg.steps.size(); ++i)
+      item_lv[i] = opt.level_budget > 0 ? item_level[i] : level_of[item_order[i]];
+    for (size_t i = 0; i < pg.prologue.size(); ++i) pro_lv[i] = level_of[pro_order[i]];
     auto tables = [&](const std::vector<DevStep>& steps, const std::vector<int>& seq, std::vector<DevLevel>* levels,
                       std::vector<uint32_t>* out_start) -> std::string {
       out_start->assign(2 * steps.size(), 0);
@@ -405,7 +439,7 @@ std::string compile_program(const Network& net, const Plan& plan_in, const Progr
         // Four-output table: the root's outputs are summed, not stored, so
         // its sum over k is split too.
         const int split = (st.flags & STEP_ROOT) ? std::min<int>(st.kb, kRootSplitLog2) : 0;
-        if (i == 0 || level_of[seq[i]] != level_of[seq[i - 1]]) {
+        if (i == 0 || seq[i] != seq[i - 1]) {
           if (levels->size() >= 0xffff) return "too many levels";
           levels->push_back(DevLevel{(uint16_t)i, 0, {0, 0}});
         }
@@ -421,8 +455,8 @@ std::string compile_program(const Network& net, const Plan& plan_in, const Progr
       }
       return "";
     };
-    err = tables(pg.steps, item_order, &pg.levels, &pg.out_start);
-    if (err.empty()) err = tables(pg.prologue, pro_order, &pg.pro_levels, &pg.pro_out_start);
+    err = tables(pg.steps, item_lv, &pg.levels, &pg.out_start);
+    if (err.empty()) err = tables(pg.prologue, pro_lv, &pg.pro_levels, &pg.pro_out_start);
     if (!err.empty()) return err;
     auto nibbles = [](const std::vector<DevStep>& steps, std::vector<uint16_t>* out) {
       out->assign(steps.size() * kPosNibEntries, 0);

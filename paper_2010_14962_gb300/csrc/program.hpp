@@ -101,6 +101,10 @@ static_assert(sizeof(DevLevel) == 12, "DevLevel layout");
 
 struct ProgramOptions {
   bool levels = false;            // order item steps by tree level (see above)
+  // With levels: 0 = levels by depth (fewest barriers); else the item steps
+  // keep their depth-first order and consecutive independent steps share a
+  // level while the arena stays within this many elements (memory-bounded).
+  uint32_t level_budget = 0;
   bool c_reuses_a = false;        // C may overwrite A's arena block
   bool hoist = true;              // run outer-class-invariant merges once per bit string
   std::vector<int> cut_class;     // class of each cut (size k); empty = one class per cut
