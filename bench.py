@@ -418,13 +418,15 @@ UNEVEN = dict(name="uneven64", jobs=64, n_range=(30, 100), p_choices=(1, 2), k_r
 UNEVEN_METRIC = "amplitudes/sec, 64 uneven QAOA jobs (n 30-100, p in {1,2}, own cut set each), one launch sequence"
 
 
-def setup_uneven(rank: int):
+def setup_uneven(rank: int, jobs: int = 0):
     import concurrent.futures as cf
 
     from paper_2010_14962_gb300 import instances as I
     from paper_2010_14962_gb300 import qtn
 
     w = {k: v for k, v in UNEVEN.items() if k != "name"}
+    if jobs:
+        w["jobs"] = jobs
     spec = I.uneven_jobs(**w)
 
     def one(jd):
@@ -481,7 +483,7 @@ def run_uneven(args, rank, world, local_rank):
         import torch.distributed as dist
 
         dist.init_process_group("nccl")
-    spec, jobs = setup_uneven(rank)
+    spec, jobs = setup_uneven(rank, args.jobs)
     plans = [j[1] for j in jobs]
     xs = [j[2] for j in jobs]
     nj = len(jobs)
@@ -556,7 +558,7 @@ def run_uneven(args, rank, world, local_rank):
         "vs_baseline": None,
         "dtype": {"fp32": "c64", "fp64": "c128", "fp32x2": "c64x2 (double-float)"}.get(prec, "c64"),
         "data": "synthetic: seeded random 3-regular graphs, gamma/beta ~ U[0,pi), seeded bit strings",
-        "config": {"workload": UNEVEN["name"], "jobs": nj, "n": [min(d["n"] for d in spec), max(d["n"] for d in spec)],
+        "config": {"workload": UNEVEN["name"] if nj == UNEVEN["jobs"] else f"uneven{nj}", "jobs": nj, "n": [min(d["n"] for d in spec), max(d["n"] for d in spec)],
                    "p1_jobs": sum(d["p"] == 1 for d in spec), "p2_jobs": sum(d["p"] == 2 for d in spec),
                    "cuts": [min(ks), max(ks)], "precision": prec,
                    "executed_flops_per_step": exec_flops, "method_flops_per_step": method_flops,
@@ -701,6 +703,7 @@ def main():
     ap.add_argument("--executor", default=None, help="force an executor (default: autotuned)")
     ap.add_argument("--workload", default="qaoa80_p1_k16", choices=["qaoa80_p1_k16", "uneven64", "learned120"],
                     help="uneven64: 64 independent jobs of different plans in one launch sequence")
+    ap.add_argument("--jobs", type=int, default=0, help="uneven64: take the first N jobs (default all 64)")
     ap.add_argument("--form", default="gates", choices=["gates", "gm"],
                     help="network form of the n=80 workload: the paper's gate network (16 cuts) or the "
                          "graphical model with shared diagonal-gate indices (8 cuts)")
