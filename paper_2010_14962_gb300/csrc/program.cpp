@@ -307,9 +307,60 @@ std::string compile_program(const Network& net, const Plan& plan_in, const Progr
       std::stable_sort(item_order.begin(), item_order.end(),
                        [&](int x, int y) { return level_of[x] < level_of[y]; });
   }
-  // Memory-bounded levels of the item steps (depth-first order): the level
-  // of each emitted step, assigned while emitting.
-  std::vector<int> item_level;
+  // Memory-bounded levels (level_budget > 0): list scheduling along the
+  // depth-first order.  Each level takes, in depth-first order, every step
+  // whose operands are ready (leaves, hoisted results, earlier levels) while
+  // its result still fits in the arena budget (the first ready step always
+  // does); a level's inputs are freed when it ends.  The allocation is
+  // simulated with the same first-fit arena and the same calls as the
+  // emission below, so the emitted program has exactly this arena.
+  std::vector<int> item_level;  // level of each item step, in emission order
+  constexpr size_t kLevelWindow = 12;
+  if (opt.levels && opt.level_budget > 0) {
+    std::vector<int> rem = item_order, bseq;
+    Arena sim;
+    std::vector<uint32_t> at(T, 0);
+    std::vector<char> avail(T, 0), taken(plan.merges.size(), 0);
+    for (int t = 0; t < T; ++t) avail[t] = is_leaf(t) || exported[t];
+    int lev = 0;
+    while (!rem.empty()) {
+      std::vector<uint32_t> rel;
+      std::vector<int> outs, keep;
+      bool took = false;
+      for (size_t q = 0; q < rem.size(); ++q) {
+        const int j = rem[q];
+        const Merge& mg = plan.merges[j];
+        // Look ahead only a few remaining steps: results taken far ahead of
+        // their depth-first turn stay alive long and raise the arena.
+        if (q >= kLevelWindow || !avail[mg.a] || !avail[mg.b]) {
+          keep.push_back(j);
+          continue;
+        }
+        if (mg.c != root) {
+          const Canon& c = canon[j];
+          const uint32_t size = 1u << (c.m.size() + c.n.size() + c.b.size());
+          const uint32_t off = sim.alloc(size);
+          if (took && off + size > opt.level_budget) {
+            sim.release(off);
+            keep.push_back(j);
+            continue;
+          }
+          at[mg.c] = off;
+        }
+        took = true;
+        bseq.push_back(j);
+        item_level.push_back(lev);
+        if (!(is_leaf(mg.a) || exported[mg.a])) rel.push_back(at[mg.a]);
+        if (!(is_leaf(mg.b) || exported[mg.b])) rel.push_back(at[mg.b]);
+        outs.push_back(mg.c);
+      }
+      for (uint32_t r : rel) sim.release(r);
+      for (int t : outs) avail[t] = 1;
+      rem.swap(keep);
+      ++lev;
+    }
+    item_order = bseq;
+  }
 
   std::vector<uint32_t> where(T, 0);
   auto emit = [&](bool prologue_pass, bool c_reuses_a, std::vector<DevStep>* out, uint32_t* arena_high,
@@ -318,23 +369,11 @@ std::string compile_program(const Network& net, const Plan& plan_in, const Progr
     const bool by_level = opt.levels;
     const bool bounded = by_level && !prologue_pass && opt.level_budget > 0;
     std::vector<uint32_t> level_release;  // inputs freed when their level ends
-    std::vector<char> in_level(T, 0);     // bounded: produced in the current level
-    std::vector<int> level_members;
-    int cur_level = 0;
-    auto close_level = [&]() {
-      for (uint32_t r : level_release) arena.release(r);
-      level_release.clear();
-      for (int t : level_members) in_level[t] = 0;
-      level_members.clear();
-      ++cur_level;
-    };
     const std::vector<int>& seq = prologue_pass ? pro_order : item_order;
+    auto level_at = [&](size_t si) { return bounded ? item_level[si] : level_of[seq[si]]; };
     for (size_t si = 0; si < seq.size(); ++si) {
       const int j = seq[si];
       if ((bool)pro[j] != prologue_pass) continue;
-      if (bounded && !level_members.empty() &&
-          (in_level[plan.merges[j].a] || in_level[plan.merges[j].b]))
-        close_level();  // an operand is produced in this level: the step starts the next
       const Merge& mg = plan.merges[j];
       const Canon& c = canon[j];
       DevStep st{};
@@ -385,11 +424,6 @@ std::string compile_program(const Network& net, const Plan& plan_in, const Progr
           st.c = (uint32_t)leaf_id[mg.c];
         } else {
           uint32_t off = arena.alloc(1u << rc);
-          if (bounded && off + (1u << rc) > opt.level_budget && !level_members.empty()) {
-            arena.release(off);  // over budget: the step starts the next level instead
-            close_level();
-            off = arena.alloc(1u << rc);
-          }
           where[mg.c] = off;
           st.c = off;
         }
@@ -400,14 +434,9 @@ std::string compile_program(const Network& net, const Plan& plan_in, const Progr
           st.w[b] = (uint16_t)(1u << (it - lay.begin()));
         }
       }
-      if (bounded) {
+      if (by_level) {
         level_release.insert(level_release.end(), to_release.begin(), to_release.end());
-        in_level[mg.c] = 1;
-        level_members.push_back(mg.c);
-        item_level.push_back(cur_level);
-      } else if (by_level) {
-        level_release.insert(level_release.end(), to_release.begin(), to_release.end());
-        const bool level_ends = si + 1 == seq.size() || level_of[seq[si + 1]] != level_of[j];
+        const bool level_ends = si + 1 == seq.size() || level_at(si + 1) != level_at(si);
         if (level_ends) {
           for (uint32_t r : level_release) arena.release(r);
           level_release.clear();
