@@ -269,6 +269,21 @@ qtn_status qtn_contract_slices(const qtn_plan_t* plan, const uint8_t* x, uint64_
 qtn_status qtn_contract_batch(const qtn_plan_t* const* plans, const uint8_t* const* xs, int njobs,
                               qtn_precision prec, cudaStream_t stream, double* out);
 
+/* Cooperative stop of multi-plan batches (jobs of several plans; Sec. V:
+ * a lost or stalled part of the work is noticed and can be recomputed).  The
+ * persistent executor checks, before each chunk of work, a host-mapped
+ * cancel word and a time budget; nothing on the device waits.  A stopped
+ * call returns QTN_ERR_TIMEOUT and no amplitudes; the library and device stay
+ * usable.
+ *   qtn_batch_cancel         : stops the multi-plan qtn_contract_batch call
+ *                              in progress (from any host thread; a call that
+ *                              starts afterwards is not affected).
+ *   qtn_batch_set_time_limit : ms of executor time each block may use per
+ *                              call (0: no limit, the default); applies to
+ *                              later calls.  QTN_ERR_INVALID_ARG if ms < 0. */
+qtn_status qtn_batch_cancel(void);
+qtn_status qtn_batch_set_time_limit(double ms);
+
 /* Device time (ms) of the most recent multi-plan qtn_contract_batch launch
  * sequence (leaf tables to per-job sums, CUDA events on its stream), and the
  * number of kernels it launched.  QTN_ERR_INVALID_ARG if none ran yet. */

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -101,6 +102,8 @@ struct BatchWorkspace {
   double* h_out = nullptr;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bool timed = false;
+  unsigned* d_status = nullptr;  // set by a stopped executor
+  unsigned* h_status = nullptr;  // pinned read-back
 
   void release() {
     cudaFree(d_jobs);
@@ -116,6 +119,8 @@ struct BatchWorkspace {
     cudaFreeHost(h_out);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
+    cudaFree(d_status);
+    cudaFreeHost(h_status);
     *this = BatchWorkspace();
   }
   cudaError_t reserve(size_t jobs, size_t chunks, size_t lt, size_t x) {
@@ -139,6 +144,8 @@ struct BatchWorkspace {
     if ((e = cudaMallocHost((void**)&h_chunks, sizeof(ChunkDesc) * chunks)) != cudaSuccess) return e;
     if ((e = cudaMallocHost((void**)&h_x, std::max<size_t>(x, 16))) != cudaSuccess) return e;
     if ((e = cudaMallocHost((void**)&h_out, sizeof(double2) * jobs)) != cudaSuccess) return e;
+    if ((e = cudaMalloc((void**)&d_status, sizeof(unsigned))) != cudaSuccess) return e;
+    if ((e = cudaMallocHost((void**)&h_status, sizeof(unsigned))) != cudaSuccess) return e;
     cap_jobs = jobs;
     cap_chunks = chunks;
     cap_lt = lt;
@@ -148,6 +155,11 @@ struct BatchWorkspace {
 };
 BatchWorkspace g_batch;
 std::mutex g_batch_mu;
+// Cooperative stop of multi-plan batches: a host-mapped word the persistent
+// executor polls between chunks (allocated once, never freed, so another
+// host thread may write it at any time), and a time budget per call.
+std::atomic<int*> g_cancel_host{nullptr};
+std::atomic<double> g_batch_limit_ms{0.0};
 constexpr int kMultiKernels = 4;  // leaf tables, prologue, executor, per-job sums
 
 }  // namespace
@@ -1221,18 +1233,48 @@ qtn_status qtn_contract_batch(const qtn_plan_t* const* plans, const uint8_t* con
     QTN_CUDA(cudaEventCreate(&W.ev0));
     QTN_CUDA(cudaEventCreate(&W.ev1));
   }
+  if (!g_cancel_host.load()) {
+    int* hc = nullptr;
+    QTN_CUDA(cudaHostAlloc((void**)&hc, sizeof(int), cudaHostAllocMapped | cudaHostAllocPortable));
+    *hc = 0;
+    int* expected = nullptr;
+    if (!g_cancel_host.compare_exchange_strong(expected, hc)) cudaFreeHost(hc);
+  }
+  int* h_cancel = g_cancel_host.load();
+  *reinterpret_cast<volatile int*>(h_cancel) = 0;
+  int* d_cancel = nullptr;
+  QTN_CUDA(cudaHostGetDevicePointer((void**)&d_cancel, h_cancel, 0));
+  QTN_CUDA(cudaMemsetAsync(W.d_status, 0, sizeof(unsigned), stream));
+  const double limit_ms = g_batch_limit_ms.load();
+  const uint64_t budget_ns = limit_ms > 0 ? (uint64_t)(limit_ms * 1e6) : 0;
   QTN_CUDA(cudaEventRecord(W.ev0, stream));
   cudaError_t le = launch_multi(arith, W.d_jobs, njobs, total_leaves, W.d_chunks, (uint32_t)chunks.size(), W.d_counter,
-                                W.d_partials, W.d_out, exec_smem, pro_smem, level, stream);
+                                W.d_partials, W.d_out, exec_smem, pro_smem, level, d_cancel, W.d_status, budget_ns,
+                                stream);
   if (le != cudaSuccess) return cuda_fail(le, "launch_multi");
   QTN_CUDA(cudaEventRecord(W.ev1, stream));
+  QTN_CUDA(cudaMemcpyAsync(W.h_status, W.d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, stream));
   W.timed = true;
   QTN_CUDA(cudaMemcpyAsync(W.h_out, W.d_out, sizeof(double2) * njobs, cudaMemcpyDeviceToHost, stream));
   QTN_CUDA(cudaStreamSynchronize(stream));
+  if (*W.h_status != 0)
+    return fail(QTN_ERR_TIMEOUT, "the batch was cancelled or exceeded its time limit; no amplitudes were returned");
   for (int j = 0; j < njobs; ++j) {
     out[2 * j] = W.h_out[2 * j];
     out[2 * j + 1] = W.h_out[2 * j + 1];
   }
+  return QTN_OK;
+}
+
+qtn_status qtn_batch_cancel(void) {
+  int* hc = g_cancel_host.load();
+  if (hc) *reinterpret_cast<volatile int*>(hc) = 1;
+  return QTN_OK;
+}
+
+qtn_status qtn_batch_set_time_limit(double ms) {
+  if (!(ms >= 0)) return fail(QTN_ERR_INVALID_ARG, "the time limit must be >= 0");
+  g_batch_limit_ms.store(ms);
   return QTN_OK;
 }
 

@@ -1008,6 +1008,32 @@ __global__ void __launch_bounds__(256) prologue_kernel(const DevStep* __restrict
   prologue_body<V, Ops>(steps, n_steps, leaves, n_leaves, g_lt, leaf_elems, arena_elems, smem);
 }
 
+// ------------------------------------------------------------ abort check --
+
+// Stop conditions of a persistent launch, checked by one thread per block
+// before it takes a chunk (nothing ever waits): a host-mapped cancel word
+// set by another host thread, or a time budget (ns of %globaltimer since the
+// block started; 0 = none).  The first block that stops records it in
+// `status`; every block then stops at its next chunk.
+struct AbortCtl {
+  const volatile int* cancel;
+  unsigned* status;
+  uint64_t budget_ns;
+};
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool should_stop(const AbortCtl& ac, uint64_t t_start) {
+  if (!ac.status) return false;
+  if (*reinterpret_cast<volatile unsigned*>(ac.status) != 0u) return true;
+  bool stop = ac.cancel && *ac.cancel != 0;
+  if (!stop && ac.budget_ns && global_ns() - t_start > ac.budget_ns) stop = true;
+  if (stop) atomicExch(ac.status, 1u);
+  return stop;
+}
+
 // ------------------------------------------------------------- multi-job --
 
 // Many independent (plan, bit string) jobs in one launch sequence: leaf
@@ -1062,16 +1088,17 @@ template <class V, class Ops = CplxOps<V>>
 __global__ void __launch_bounds__(256) multi_exec_kernel(const JobDesc* __restrict__ jobs,
                                                          const ChunkDesc* __restrict__ chunks, uint32_t n_chunks,
                                                          unsigned* __restrict__ counter,
-                                                         Partial* __restrict__ chunk_partials) {
+                                                         Partial* __restrict__ chunk_partials, AbortCtl ac) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned s_c;
   __shared__ int s_job;
   const int T = blockDim.x;
   const int log2G = 31 - __clz(T);
   if (threadIdx.x == 0) s_job = -1;
+  const uint64_t t_start = threadIdx.x == 0 ? global_ns() : 0;
   for (;;) {
     __syncthreads();  // the previous chunk is done with shared memory
-    if (threadIdx.x == 0) s_c = atomicAdd(counter, 1u);
+    if (threadIdx.x == 0) s_c = should_stop(ac, t_start) ? n_chunks : atomicAdd(counter, 1u);
     __syncthreads();
     const unsigned c = s_c;
     if (c >= n_chunks) break;
@@ -1108,15 +1135,16 @@ template <class V, class Ops = CplxOps<V>>
 __global__ void __launch_bounds__(1024) multi_level_kernel(const JobDesc* __restrict__ jobs,
                                                            const ChunkDesc* __restrict__ chunks, uint32_t n_chunks,
                                                            unsigned* __restrict__ counter,
-                                                           Partial* __restrict__ chunk_partials) {
+                                                           Partial* __restrict__ chunk_partials, AbortCtl ac) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ unsigned s_c;
   __shared__ int s_job;
   const int T = blockDim.x;
   if (threadIdx.x == 0) s_job = -1;
+  const uint64_t t_start = threadIdx.x == 0 ? global_ns() : 0;
   for (;;) {
     __syncthreads();  // the previous chunk is done with shared memory
-    if (threadIdx.x == 0) s_c = atomicAdd(counter, 1u);
+    if (threadIdx.x == 0) s_c = should_stop(ac, t_start) ? n_chunks : atomicAdd(counter, 1u);
     __syncthreads();
     const unsigned c = s_c;
     if (c >= n_chunks) break;
@@ -1409,7 +1437,8 @@ cudaError_t launch_typed(const DeviceProgram& prog, const uint8_t* d_x, int nx, 
 template <class V, class Ops>
 cudaError_t launch_multi_typed(const JobDesc* d_jobs, int njobs, uint32_t total_leaves, const ChunkDesc* d_chunks,
                                uint32_t n_chunks, unsigned* d_counter, Partial* d_chunk_partials, double2* d_out,
-                               size_t exec_smem, size_t pro_smem, bool level, cudaStream_t stream) {
+                               size_t exec_smem, size_t pro_smem, bool level, const AbortCtl& ac,
+                               cudaStream_t stream) {
   int dev = 0, sms = 0, max_optin = 0, occ = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1431,10 +1460,10 @@ cudaError_t launch_multi_typed(const JobDesc* d_jobs, int njobs, uint32_t total_
   const unsigned grid = (unsigned)std::min<uint64_t>((uint64_t)sms * occ, n_chunks);
   if (level)
     multi_level_kernel<V, Ops><<<grid, threads, exec_smem, stream>>>(d_jobs, d_chunks, n_chunks, d_counter,
-                                                                     d_chunk_partials);
+                                                                     d_chunk_partials, ac);
   else
     multi_exec_kernel<V, Ops><<<grid, threads, exec_smem, stream>>>(d_jobs, d_chunks, n_chunks, d_counter,
-                                                                    d_chunk_partials);
+                                                                    d_chunk_partials, ac);
   multi_finalize_kernel<<<njobs, 128, 0, stream>>>(d_jobs, d_chunk_partials, d_out);
   return cudaGetLastError();
 }
@@ -1487,11 +1516,13 @@ size_t level_smem_bytes(int n_steps, int n_levels, int n_leaves, uint32_t leaf_e
 
 cudaError_t launch_multi(Arith a, const JobDesc* d_jobs, int njobs, uint32_t total_leaves, const ChunkDesc* d_chunks,
                          uint32_t n_chunks, unsigned* d_counter, Partial* d_chunk_partials, double2* d_out,
-                         size_t exec_smem, size_t pro_smem, bool level, cudaStream_t stream) {
+                         size_t exec_smem, size_t pro_smem, bool level, const volatile int* d_cancel,
+                         unsigned* d_status, uint64_t budget_ns, cudaStream_t stream) {
   if (njobs <= 0) return cudaSuccess;
+  const AbortCtl ac{d_cancel, d_status, budget_ns};
 #define QTN_MULTI_CALL(V, O)                                                                                  \
   launch_multi_typed<V, O>(d_jobs, njobs, total_leaves, d_chunks, n_chunks, d_counter, d_chunk_partials, d_out, \
-                           exec_smem, pro_smem, level, stream)
+                           exec_smem, pro_smem, level, ac, stream)
   QTN_ARITH_SWITCH(a, QTN_MULTI_CALL)
 #undef QTN_MULTI_CALL
   return cudaErrorInvalidValue;

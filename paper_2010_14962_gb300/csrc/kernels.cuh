@@ -148,10 +148,15 @@ constexpr int kLevelPrologueThreads = 1024;
 // executor over `n_chunks` chunks, per-job finalisation into d_out[njobs]).
 // exec_smem / pro_smem: the largest shared memory any job needs.  `level`:
 // every job carries a level program (multi_level_kernel, 1024 threads);
-// otherwise block programs (multi_exec_kernel, 256 threads).
+// otherwise block programs (multi_exec_kernel, 256 threads).  Each block,
+// before it takes a chunk, stops if *d_cancel (host-mapped, may be null) is
+// non-zero or more than budget_ns (0: no limit) have passed since it started;
+// a stop sets *d_status (device, must be 0 at launch) to 1 and the remaining
+// chunks are skipped (the per-job results are then incomplete).
 cudaError_t launch_multi(Arith a, const JobDesc* d_jobs, int njobs, uint32_t total_leaves, const ChunkDesc* d_chunks,
                          uint32_t n_chunks, unsigned* d_counter, Partial* d_chunk_partials, double2* d_out,
-                         size_t exec_smem, size_t pro_smem, bool level, cudaStream_t stream);
+                         size_t exec_smem, size_t pro_smem, bool level, const volatile int* d_cancel,
+                         unsigned* d_status, uint64_t budget_ns, cudaStream_t stream);
 
 // Largest tensor rank the lane executor accepts.
 constexpr int kLaneMaxRank = 5;

@@ -87,6 +87,8 @@ def lib():
             "qtn_plan_select_executor": [vp, ctypes.c_int, ctypes.c_int, ctypes.c_char_p],
             "qtn_plan_kernel_ms": [vp, P(ctypes.c_float)],
             "qtn_batch_last_ms": [P(ctypes.c_float), P(ctypes.c_int)],
+            "qtn_batch_cancel": [],
+            "qtn_batch_set_time_limit": [ctypes.c_double],
             "qtn_search_cuts": [vp, P(_PlanOpts), i32p, f64p, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int)],
             "qtn_surrogate_features": [vp, i32p, ctypes.c_int, P(ctypes.c_float)],
             "qtn_surrogate_labels": [vp, i32p, ctypes.c_int, P(ctypes.c_float)],
@@ -408,6 +410,16 @@ def contract_batch(plans, xs, precision: str = "fp32", stream=None) -> np.ndarra
     _check(lib().qtn_contract_batch(hp, xp, n, PRECISIONS[precision], _stream_handle(stream),
                                     _ptr(out, ctypes.c_double)))
     return out[0:2 * n:2] + 1j * out[1:2 * n:2]
+
+
+def batch_cancel():
+    """Stop the multi-plan contract_batch in progress (any thread)."""
+    _check(lib().qtn_batch_cancel())
+
+
+def batch_set_time_limit(ms: float):
+    """Executor time limit per multi-plan contract_batch call (0: none)."""
+    _check(lib().qtn_batch_set_time_limit(float(ms)))
 
 
 def batch_last_ms():

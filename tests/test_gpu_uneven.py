@@ -130,3 +130,36 @@ def test_uneven64_mixed_precision(gpu, uneven64):
         err = np.abs(got - ref) / np.abs(ref)
         print(prec, "max rel err vs FP64", float(err.max()), "median", float(np.median(err)))
         assert float(err.max()) < tol
+
+
+def test_batch_time_limit_and_cancel(gpu, uneven64):
+    # Cooperative stop of the persistent executor (checked between chunks;
+    # nothing waits on the device): a time limit, and a cancel from another
+    # host thread.  A stopped call reports QTN_ERR_TIMEOUT; later calls work.
+    import threading
+    import time
+
+    spec, jobs = uneven64
+    plans, xs = [j[2] for j in jobs], [j[3] for j in jobs]
+    t0 = time.perf_counter()
+    full = qtn.contract_batch(plans, xs, "fp64")
+    t_full = time.perf_counter() - t0
+    qtn.batch_set_time_limit(0.001)
+    try:
+        with pytest.raises(qtn.QTNError) as e:
+            qtn.contract_batch(plans, xs, "fp64")
+        assert e.value.status == 5
+    finally:
+        qtn.batch_set_time_limit(0)
+    if t_full > 0.1:
+        timer = threading.Timer(t_full / 4, qtn.batch_cancel)
+        timer.start()
+        t0 = time.perf_counter()
+        with pytest.raises(qtn.QTNError) as e:
+            qtn.contract_batch(plans, xs, "fp64")
+        assert e.value.status == 5 and time.perf_counter() - t0 < 0.9 * t_full
+        timer.join()
+    again = qtn.contract_batch(plans, xs, "fp64")
+    assert np.array_equal(again, full)
+    with pytest.raises(qtn.QTNError):
+        qtn.batch_set_time_limit(-1)
