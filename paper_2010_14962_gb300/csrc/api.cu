@@ -16,6 +16,8 @@
 #include <tuple>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/qtn.h"
 #include "internal.hpp"
 #include "kernels.cuh"
@@ -56,6 +58,13 @@ cudaError_t upload(T** dst, const std::vector<T>& v) {
   if (!v.empty()) e = cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
   return e;
 }
+
+// NVTX range for the duration of a scope (visible in Nsight timelines; no
+// cost without a tool attached).
+struct Trace {
+  explicit Trace(const char* name) { nvtxRangePushA(name); }
+  ~Trace() { nvtxRangePop(); }
+};
 
 struct GraphKey {
   const void* x;
@@ -405,6 +414,7 @@ struct qtn_plan {
   qtn_status tune(qtn_precision prec, int nx, cudaStream_t stream, int* out_slot) {
     auto key = std::make_pair((int)prec, nx);
     auto it = tuned.find(key);
+    Trace trace(it == tuned.end() ? "qtn autotune" : "qtn tuned lookup");
     if (it != tuned.end()) {
       *out_slot = it->second;
       return QTN_OK;
@@ -452,6 +462,7 @@ struct qtn_plan {
   // timing on).
   qtn_status run_graph(const uint8_t* d_x, int nx, qtn_precision prec, double2* d_out, cudaStream_t stream,
                        const double* d_gamma = nullptr, const double* d_beta = nullptr) {
+    Trace trace("qtn contraction launch");
     int si = 0;
     qtn_status st = tune(prec, nx, stream, &si);
     if (st != QTN_OK) return st;
@@ -613,6 +624,7 @@ void qtn_plan_opts_default(qtn_plan_opts* o) {
 
 qtn_status qtn_plan(const qtn_network_t* net, const int32_t* cuts, int k, const int32_t* order, int order_len,
                     const qtn_plan_opts* opts_in, qtn_plan_t** out) {
+  Trace trace("qtn_plan");
   if (!net || !out) return fail(QTN_ERR_INVALID_ARG, "net or out is NULL");
   *out = nullptr;
   qtn_plan_opts opts;
@@ -1015,6 +1027,7 @@ qtn_status qtn_contract_slices(const qtn_plan_t* cplan, const uint8_t* x, uint64
 
 qtn_status qtn_contract_batch(const qtn_plan_t* const* plans, const uint8_t* const* xs, int njobs, qtn_precision prec,
                               cudaStream_t stream, double* out) {
+  Trace trace("qtn_contract_batch");
   if (!plans || !xs || !out || njobs < 0) return fail(QTN_ERR_INVALID_ARG, "bad argument");
   if (!precision_supported(prec)) return fail(QTN_ERR_UNSUPPORTED, "unknown precision");
   if (njobs == 0) return QTN_OK;
