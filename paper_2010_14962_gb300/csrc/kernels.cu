@@ -846,12 +846,21 @@ __device__ __forceinline__ void level_run(const DevStep* s_steps, const uint32_t
   for (int l = 0; l < n_levels; ++l) {
     const DevLevel lv = s_levels[l];
     const uint32_t total = lv.units[US] << log2I;
-    int j = lv.first;
     LStep q;
-    decode(j, q);
+    q.beg = q.end = 0;
     for (uint32_t f = threadIdx.x; f < total; f += blockDim.x) {
       const uint32_t item = f & (I - 1u), uf = f >> log2I;
-      while (uf >= q.end) decode(++j, q);  // steps of the level in order; uf < its units
+      if (uf >= q.end || uf < q.beg) {
+        // The level's merge holding unit uf: binary search of the (strictly
+        // increasing) unit starts, then one decode.
+        int lo = lv.first, hi = lv.first + lv.count - 1;
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (s_out[2 * mid + US] <= uf) lo = mid;
+          else hi = mid - 1;
+        }
+        decode(lo, q);
+      }
       if (item >= nI) continue;
       V* arena = s_arena + (size_t)item * stride;
       const V* A = (q.flags & STEP_A_LEAF) ? s_lt + leaf_offset(s_leaves[q.a], s0 + item) : arena + q.a;
