@@ -126,7 +126,10 @@ typedef enum {
   QTN_SEARCH_GREEDY = 0,  /* cut the index that most lowers the width, k times */
   QTN_SEARCH_GA = 1,      /* Algorithm 1 (Sec. III.B), seeded with the greedy set;
                              fitness = width, then total flops */
-  QTN_SEARCH_GA_FLOPS = 2 /* Algorithm 1 with total log2 flops as the fitness */
+  QTN_SEARCH_GA_FLOPS = 2, /* Algorithm 1 with total log2 flops as the fitness */
+  QTN_SEARCH_GA_NONZERO = 3 /* Algorithm 1 with the log2 flops of the slices that are
+                               not structurally zero (cut classes) as the fitness,
+                               width at most the greedy set's */
 } qtn_search;
 
 typedef struct {

@@ -637,7 +637,9 @@ qtn_status qtn_plan(const qtn_network_t* net, const int32_t* cuts, int k, const 
   } else {
     if (opts.k < 0 || opts.k > (int)net->net.indices.size()) return fail(QTN_ERR_INVALID_ARG, "opts.k out of range");
     cutv = greedy_cuts(net->net, opts.k);
-    if ((opts.search == QTN_SEARCH_GA || opts.search == QTN_SEARCH_GA_FLOPS) && opts.k > 0) {
+    const bool ga_search = opts.search == QTN_SEARCH_GA || opts.search == QTN_SEARCH_GA_FLOPS ||
+                           opts.search == QTN_SEARCH_GA_NONZERO;
+    if (ga_search && opts.k > 0) {
       GAOptions ga;
       ga.T = opts.ga_T;
       ga.N = opts.ga_N;
@@ -645,11 +647,14 @@ qtn_status qtn_plan(const qtn_network_t* net, const int32_t* cuts, int k, const 
       ga.time_budget_s = opts.time_budget_s;
       std::vector<std::vector<int>> seeds;
       if (opts.ga_seed_greedy) seeds.push_back(cutv);
+      int width_cap = plan_cost(net->net, cutv).width;
       GAResult r = genetic_cuts(net->net, opts.k, ga, seeds,
-                                opts.search == QTN_SEARCH_GA ? default_fitness : flops_fitness, nullptr);
+                                opts.search == QTN_SEARCH_GA        ? default_fitness
+                                : opts.search == QTN_SEARCH_GA_FLOPS ? flops_fitness
+                                                                     : nonzero_flops_fitness,
+                                &width_cap);
       cutv = r.best;
-    } else if (opts.search != QTN_SEARCH_GREEDY && opts.search != QTN_SEARCH_GA &&
-               opts.search != QTN_SEARCH_GA_FLOPS) {
+    } else if (!ga_search && opts.search != QTN_SEARCH_GREEDY) {
       return fail(QTN_ERR_INVALID_ARG, "unknown search");
     }
   }
@@ -884,16 +889,22 @@ qtn_status qtn_search_cuts(const qtn_network_t* net, const qtn_plan_opts* opts, 
       tr.push_back(default_fitness(net->net, cur, nullptr));
     }
     best = cur;
-  } else if (opts->search == QTN_SEARCH_GA || opts->search == QTN_SEARCH_GA_FLOPS) {
+  } else if (opts->search == QTN_SEARCH_GA || opts->search == QTN_SEARCH_GA_FLOPS ||
+             opts->search == QTN_SEARCH_GA_NONZERO) {
     GAOptions ga;
     ga.T = opts->ga_T;
     ga.N = opts->ga_N;
     ga.seed = opts->seed;
     ga.time_budget_s = opts->time_budget_s;
     std::vector<std::vector<int>> seeds;
-    if (opts->k > 0 && opts->ga_seed_greedy) seeds.push_back(greedy_cuts(net->net, opts->k));
+    const std::vector<int> greedy = opts->k > 0 ? greedy_cuts(net->net, opts->k) : std::vector<int>();
+    if (opts->k > 0 && opts->ga_seed_greedy) seeds.push_back(greedy);
+    int width_cap = plan_cost(net->net, greedy).width;
     GAResult r = genetic_cuts(net->net, opts->k, ga, seeds,
-                              opts->search == QTN_SEARCH_GA ? default_fitness : flops_fitness, nullptr);
+                              opts->search == QTN_SEARCH_GA        ? default_fitness
+                              : opts->search == QTN_SEARCH_GA_FLOPS ? flops_fitness
+                                                                    : nonzero_flops_fitness,
+                              &width_cap);
     best = r.best;
     tr = r.best_fitness_per_generation;
     evals = r.evaluations;

@@ -1,4 +1,5 @@
 #include "plan.hpp"
+#include "program.hpp"
 
 #include <algorithm>
 #include <chrono>
@@ -482,6 +483,17 @@ double default_fitness(const Network& net, const std::vector<int>& cuts, void*) 
 
 double flops_fitness(const Network& net, const std::vector<int>& cuts, void*) {
   return plan_cost(net, cuts).log2_flops_total();
+}
+
+double nonzero_flops_fitness(const Network& net, const std::vector<int>& cuts, void* width_cap) {
+  // Slices of cut classes that disagree are exactly zero and never run:
+  // 2^classes slices of 8 * macs flops each; a width above the cap costs 8
+  // (log2) per extra index.
+  const Cost c = plan_cost(net, cuts);
+  int n_classes = 0;
+  cut_classes(net, cuts, &n_classes);
+  const int cap = width_cap ? *static_cast<const int*>(width_cap) : c.width;
+  return std::log2(8.0 * c.macs) + n_classes + 8.0 * std::max(0, c.width - cap);
 }
 
 namespace {

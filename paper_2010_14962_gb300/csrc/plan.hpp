@@ -95,6 +95,9 @@ struct GAResult {
 using FitnessFn = double (*)(const Network&, const std::vector<int>&, void*);
 double default_fitness(const Network& net, const std::vector<int>& cuts, void*);
 double flops_fitness(const Network& net, const std::vector<int>& cuts, void*);  // log2 total flops
+// log2 flops of the structurally non-zero slices (2^classes x per-slice), plus
+// a penalty for a width above *(const int*)width_cap.
+double nonzero_flops_fitness(const Network& net, const std::vector<int>& cuts, void* width_cap);
 GAResult genetic_cuts(const Network& net, int M, const GAOptions& opt,
                       const std::vector<std::vector<int>>& seeds,
                       FitnessFn fitness, void* ctx);

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "_build", "libqtn.so")
 HEADER = os.path.join(os.path.dirname(_HERE), "include", "qtn.h")
 
 PRECISIONS = {"fp64": 0, "fp32": 1, "tf32": 2, "bf16x3": 3, "tf32x3": 4, "bf16x6": 5, "fp32x2": 6}
-SEARCHES = {"greedy": 0, "ga": 1, "ga_flops": 2}
+SEARCHES = {"greedy": 0, "ga": 1, "ga_flops": 2, "ga_nonzero": 3}
 SURROGATE_FEATURES = 48
 SURROGATE_TARGETS = 2
 

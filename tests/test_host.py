@@ -403,3 +403,22 @@ def test_graphical_model_programs_match_oracle(n, p, k, seed):
         vals = E.run_program(d, name, inst.gamma, inst.beta, x)
         got = sum(vals.values()) * scale
         assert abs(got - ref) < 1e-12 * abs(ref), name
+
+
+def test_nonzero_slice_search():
+    # Algorithm 1 with the flops of the structurally non-zero slices as the
+    # fitness (cut classes, width capped at the greedy set's): seeded with the
+    # greedy set and elitist, so never worse than it on that fitness.
+    inst = I.qaoa_instance(40, 1, 3)
+    net = qtn.Network(40, inst.edges, inst.gamma, inst.beta)
+    greedy = qtn.Plan(net, k=8)
+    cuts, trace, ev = qtn.search_cuts(net, 8, "ga_nonzero", seed=3, ga_T=6, ga_N=11)
+    again, _, _ = qtn.search_cuts(net, 8, "ga_nonzero", seed=3, ga_T=6, ga_N=11)
+    assert np.array_equal(cuts, again) and ev > 0
+    assert all(b <= a + 1e-12 for a, b in zip(trace, trace[1:]))
+
+    def fitness(plan):
+        d, c = plan.describe(), plan.cost()
+        return np.log2(8 * c["macs_per_slice"]) + (max(d["cut_class"]) + 1) + 8 * max(0, c["width"] - greedy.cost()["width"])
+
+    assert fitness(qtn.Plan(net, cuts=cuts)) <= fitness(greedy) + 1e-9
