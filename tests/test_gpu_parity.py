@@ -453,3 +453,25 @@ def test_graphical_model_n80(gpu, config80, prec, tol):
     gm = qtn.Plan(qtn.Network(80, inst.edges, inst.gamma, inst.beta, form="gm"), k=8)
     got = device_amplitudes(gm, xs, prec)
     assert np.max(np.abs(got - refs) / np.abs(refs)) < tol
+
+
+def test_n120_k22_sampled_slices(gpu):
+    # The n = 120, 22-cut workload (4 M slices): slice values over three
+    # sampled ranges against the oracle's own slices (FP64 form).
+    n, p, k = 120, 1, 22
+    inst = I.qaoa_instance(n, p, 5)
+    net = qtn.Network(n, inst.edges, inst.gamma, inst.beta)
+    plan = qtn.Plan(net, k=k)
+    x = I.bitstrings(n, 1, 5)[0]
+    S = 1 << k
+    for lo in (0, S // 2 + 4096, S - 128):
+        hi = lo + 128
+        total, comp, vals = plan.contract_slices(x, lo, hi, "fp64", per_slice=True)
+        ref = O.tn_amplitude(n, inst.edges, inst.gamma, inst.beta, x, cuts=plan.cut_names(), slices=(lo, hi),
+                             per_slice=True, threads=16)
+        scale = 2.0 ** (-n / 2)
+        mag = np.max(np.abs(ref.per_slice))
+        assert mag > 0
+        assert np.max(np.abs(vals * scale - ref.per_slice)) <= 1e-12 * mag, lo
+        assert np.array_equal(vals == 0, ref.per_slice == 0), lo  # structurally zero slices on both sides
+        assert abs((total - comp) * scale - ref.value) <= 1e-12 * np.sum(np.abs(ref.per_slice)), lo
