@@ -265,10 +265,14 @@ qtn_status qtn_contract_slices(const qtn_plan_t* plan, const uint8_t* x, uint64_
  * the fewest multiply-adds and fits in shared memory, with as many items per
  * block as fit (1024 threads); if some job has none that fits, every job
  * runs its 48 KiB batched (else per-class) block program instead.
+ * The multi-plan sequence (uploads, kernels, read-backs) is captured as a
+ * CUDA graph the first time a list of plans is seen (with that precision
+ * and time limit) and replayed afterwards.
  * Errors: QTN_ERR_INVALID_ARG (NULL plan, bad x), QTN_ERR_UNSUPPORTED (a
- * job's working set exceeds shared memory), QTN_ERR_CUDA.  Internal device
- * and pinned buffers are kept between calls (grow-only); calls from several
- * host threads are serialised.  Synchronises `stream`. */
+ * job's working set exceeds shared memory), QTN_ERR_TIMEOUT (stopped, see
+ * qtn_batch_cancel), QTN_ERR_CUDA.  Internal device and pinned buffers are
+ * kept between calls (grow-only); calls from several host threads are
+ * serialised.  Synchronises `stream`. */
 qtn_status qtn_contract_batch(const qtn_plan_t* const* plans, const uint8_t* const* xs, int njobs,
                               qtn_precision prec, cudaStream_t stream, double* out);
 
@@ -288,7 +292,8 @@ qtn_status qtn_batch_cancel(void);
 qtn_status qtn_batch_set_time_limit(double ms);
 
 /* Device time (ms) of the most recent multi-plan qtn_contract_batch launch
- * sequence (leaf tables to per-job sums, CUDA events on its stream), and the
+ * sequence (the replayed graph: bit-string and descriptor uploads, leaf
+ * tables to per-job sums, read-backs; CUDA events on its stream), and the
  * number of kernels it launched.  QTN_ERR_INVALID_ARG if none ran yet. */
 qtn_status qtn_batch_last_ms(float* ms, int* kernels);
 
