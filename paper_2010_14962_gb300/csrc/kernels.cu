@@ -279,17 +279,13 @@ __host__ __device__ inline SmemLayout smem_layout(int n_steps, int n_leaves, uin
 // ------------------------------------------------------------ leaf build --
 
 // Value of ZZ gate g (with its absorbed H|0>, RX and <x| pieces) at leg
-// values v[0..3] (in q0, in q1, out q0, out q1; -1 on absorbed legs).
+// values v[0..3] (in q0, in q1, out q0, out q1; -1 on absorbed legs); t =
+// (cos gamma_l, sin gamma_l, cos beta_l, sin beta_l) of the gate's layer.
 __device__ __forceinline__ void gate_value(int g, const int* v, const int32_t* __restrict__ gate_q,
-                                           const int8_t* __restrict__ gate_layer,
                                            const int8_t* __restrict__ gate_in_h,
-                                           const int8_t* __restrict__ gate_out_kind, const double* __restrict__ gamma,
-                                           const double* __restrict__ beta, const uint8_t* __restrict__ xrow,
-                                           double& re, double& im) {
-  const int l = gate_layer[g];
-  double sg, cg, sb, cb;
-  sincos(gamma[l], &sg, &cg);
-  sincos(beta[l], &sb, &cb);
+                                           const int8_t* __restrict__ gate_out_kind, const double* t,
+                                           const uint8_t* __restrict__ xrow, double& re, double& im) {
+  const double cg = t[0], sg = t[1], cb = t[2], sb = t[3];
   re = 0.0;
   im = 0.0;
   // T = sum over the wire values (u0, u1) inside the diagonal ZZ gate of
@@ -325,44 +321,40 @@ __device__ __forceinline__ void gate_value(int g, const int* v, const int32_t* _
     }
 }
 
-// Entry e of leaf L (FP64 evaluation, rounded by V's conversion).  In the
-// density form (Sec. II.A, dimension-4 edges) the leaf is the superoperator
-// G (x) conj(G): slots 0..3 carry the ket bits, slots 4..7 the bra bits.
 // Value of a graphical-model factor at leg values v[0], v[1]: the ZZ phase
 // exp(-i gamma_l s_0 s_1) (s = 1 - 2 z), or the mixer entry
 // <z_out| RX(2 beta_l) |z_in> = cos beta_l or -i sin beta_l, with z_out =
-// x_q on the last layer (leg 1 absent).
+// x_q on the last layer (leg 1 absent); t as for gate_value.
 __device__ __forceinline__ void gm_factor_value(int g, int kind, const int* v, const int32_t* __restrict__ gate_q,
-                                                const int8_t* __restrict__ gate_layer,
-                                                const double* __restrict__ gamma, const double* __restrict__ beta,
-                                                const uint8_t* __restrict__ xrow, double& re, double& im) {
-  const int l = gate_layer[g];
+                                                const double* t, const uint8_t* __restrict__ xrow, double& re,
+                                                double& im) {
   if (kind == GATE_GM_ZZ) {
-    double sg, cg;
-    sincos(gamma[l], &sg, &cg);
     const double sgn = (double)((1 - 2 * v[0]) * (1 - 2 * v[1]));
-    re = cg;
-    im = -sgn * sg;
+    re = t[0];
+    im = -sgn * t[1];
   } else {
-    double sb, cb;
-    sincos(beta[l], &sb, &cb);
     const int out = v[1] >= 0 ? v[1] : (int)xrow[gate_q[2 * g]];
     if (out == v[0]) {
-      re = cb;
+      re = t[2];
       im = 0.0;
     } else {
       re = 0.0;
-      im = -sb;
+      im = -t[3];
     }
   }
 }
 
+// Entry e of leaf L (FP64 evaluation, rounded by V's conversion); t = the
+// trig values of its gate's layer (cos gamma, sin gamma, cos beta, sin beta).
+// In the density form (Sec. II.A, dimension-4 edges) the leaf is the
+// superoperator G (x) conj(G): slots 0..3 carry the ket bits, slots 4..7 the
+// bra bits.
 template <class V>
-__device__ __forceinline__ V leaf_entry(const DevLeaf& L, int e, const int32_t* __restrict__ gate_q,
-                                        const int8_t* __restrict__ gate_layer, const int8_t* __restrict__ gate_in_h,
-                                        const int8_t* __restrict__ gate_out_kind, const int8_t* __restrict__ gate_kind,
-                                        const double* __restrict__ gamma, const double* __restrict__ beta,
-                                        const uint8_t* __restrict__ xrow, bool density) {
+__device__ __forceinline__ V leaf_entry_trig(const DevLeaf& L, int e, const int32_t* __restrict__ gate_q,
+                                             const int8_t* __restrict__ gate_in_h,
+                                             const int8_t* __restrict__ gate_out_kind,
+                                             const int8_t* __restrict__ gate_kind, const double* t,
+                                             const uint8_t* __restrict__ xrow, bool density) {
   const int r = L.rank_nc + L.ncut;
   double re = 1.0, im = 0.0;
   if (L.gate >= 0) {
@@ -373,19 +365,35 @@ __device__ __forceinline__ V leaf_entry(const DevLeaf& L, int e, const int32_t* 
         if ((L.slot_mask[b] >> sl) & 1) v[sl] = (e >> b) & 1;
     const int kind = gate_kind[g];
     if (kind != GATE_ZZ) {
-      gm_factor_value(g, kind, v, gate_q, gate_layer, gamma, beta, xrow, re, im);
+      gm_factor_value(g, kind, v, gate_q, t, xrow, re, im);
       return CplxOps<V>::from(re, im);
     }
-    gate_value(g, v, gate_q, gate_layer, gate_in_h, gate_out_kind, gamma, beta, xrow, re, im);
+    gate_value(g, v, gate_q, gate_in_h, gate_out_kind, t, xrow, re, im);
     if (density) {
       double bre, bim;
-      gate_value(g, v + 4, gate_q, gate_layer, gate_in_h, gate_out_kind, gamma, beta, xrow, bre, bim);
+      gate_value(g, v + 4, gate_q, gate_in_h, gate_out_kind, t, xrow, bre, bim);
       const double pre = re * bre + im * bim, pim = im * bre - re * bim;  // (re + i im) * conj(bre + i bim)
       re = pre;
       im = pim;
     }
   }
   return CplxOps<V>::from(re, im);
+}
+
+// The same with the layer's trig values computed here.
+template <class V>
+__device__ __forceinline__ V leaf_entry(const DevLeaf& L, int e, const int32_t* __restrict__ gate_q,
+                                        const int8_t* __restrict__ gate_layer, const int8_t* __restrict__ gate_in_h,
+                                        const int8_t* __restrict__ gate_out_kind, const int8_t* __restrict__ gate_kind,
+                                        const double* __restrict__ gamma, const double* __restrict__ beta,
+                                        const uint8_t* __restrict__ xrow, bool density) {
+  double t[4] = {1.0, 0.0, 1.0, 0.0};
+  if (L.gate >= 0) {
+    const int l = gate_layer[L.gate];
+    sincos(gamma[l], &t[1], &t[0]);
+    sincos(beta[l], &t[3], &t[2]);
+  }
+  return leaf_entry_trig<V>(L, e, gate_q, gate_in_h, gate_out_kind, gate_kind, t, xrow, density);
 }
 
 // Leaf tables of nx bit strings; bit string xi uses angles gamma / beta +
@@ -971,6 +979,49 @@ __global__ void __launch_bounds__(1024) prologue_level_kernel(const DevStep* __r
                               leaf_elems, arena_elems, smem);
 }
 
+// Leaf table and hoisted merges of one bit string per block, in one launch:
+// the layers' trig values once per block, every leaf entry (the leaf holding
+// entry i found by binary search on the increasing leaf bases), then the
+// level-ordered prologue on the same table.
+constexpr int kMaxFusedLayers = 16;
+
+template <class V, class Ops = CplxOps<V>>
+__global__ void __launch_bounds__(1024) leaf_prologue_level_kernel(
+    const DevStep* __restrict__ steps, int n_steps, const uint32_t* __restrict__ out_start,
+    const uint16_t* __restrict__ pos_nib, const DevLevel* __restrict__ levels, int n_levels,
+    const DevLeaf* __restrict__ leaves, int n_leaves, void* leaf_tables, uint32_t leaf_elems, uint32_t arena_elems,
+    const int32_t* __restrict__ gate_q, const int8_t* __restrict__ gate_layer, const int8_t* __restrict__ gate_in_h,
+    const int8_t* __restrict__ gate_out_kind, const int8_t* __restrict__ gate_kind, const double* __restrict__ gamma,
+    const double* __restrict__ beta, int angle_stride, int p, const uint8_t* __restrict__ x, int n, bool density) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ double s_trig[4 * kMaxFusedLayers];
+  const int xi = blockIdx.x;
+  V* g_lt = static_cast<V*>(leaf_tables) + (size_t)xi * leaf_elems;
+  const double* ga = gamma + (size_t)xi * angle_stride;
+  const double* be = beta + (size_t)xi * angle_stride;
+  for (int l = threadIdx.x; l < p; l += blockDim.x) {
+    sincos(ga[l], &s_trig[4 * l + 1], &s_trig[4 * l]);
+    sincos(be[l], &s_trig[4 * l + 3], &s_trig[4 * l + 2]);
+  }
+  __syncthreads();
+  const uint8_t* xrow = x + (size_t)xi * n;
+  for (uint32_t i = threadIdx.x; i < leaf_elems; i += blockDim.x) {
+    int lo = 0, hi = n_leaves - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (leaves[mid].base <= i) lo = mid;
+      else hi = mid - 1;
+    }
+    const DevLeaf L = leaves[lo];
+    if (L.gate == -2) continue;  // hoisted result: written by the prologue below
+    const double* t = L.gate >= 0 ? s_trig + 4 * gate_layer[L.gate] : s_trig;
+    g_lt[i] = leaf_entry_trig<V>(L, (int)(i - L.base), gate_q, gate_in_h, gate_out_kind, gate_kind, t, xrow, density);
+  }
+  __syncthreads();  // the block's leaf-table writes are visible to its reads below
+  prologue_level_body<V, Ops>(steps, n_steps, out_start, pos_nib, levels, n_levels, leaves, n_leaves, g_lt,
+                              leaf_elems, arena_elems, smem);
+}
+
 // -------------------------------------------------------------- prologue --
 
 // Hoisted merges (no outer slice class below them): run once per bit string
@@ -1351,9 +1402,10 @@ bool exec_shape_typed(const DeviceProgram& prog, int nx, uint64_t slices_per_x, 
   if (prog.n_pro_steps > 0 && prog.n_pro_levels > 0) {
     const LevelLayout PL = level_layout(prog.n_pro_steps, prog.n_pro_levels, prog.n_leaves, prog.leaf_elems,
                                         prog.pro_arena_elems | 1u, 1, elem_bytes, kLevelPrologueThreads);
-    if (PL.total > (size_t)max_optin) return false;
+    if (PL.total > (size_t)max_optin - 4 * kMaxFusedLayers * sizeof(double)) return false;
     sh.pro_smem = PL.total;
     if (allow_max_smem(prologue_level_kernel<V, Ops>) != cudaSuccess) return false;
+    if (allow_max_smem(leaf_prologue_level_kernel<V, Ops>) != cudaSuccess) return false;
   } else if (prog.n_pro_steps > 0) {
     const SmemLayout PL = smem_layout(prog.n_pro_steps, prog.n_leaves, prog.leaf_elems, prog.pro_arena_elems,
                                       elem_bytes, 256, false);
@@ -1379,21 +1431,34 @@ cudaError_t launch_typed(const DeviceProgram& prog, const uint8_t* d_x, int nx, 
                          const double* d_gamma, const double* d_beta) {
   const unsigned lgrid = (unsigned)prog.n_leaves * (unsigned)nx;
   const bool sweep = d_gamma != nullptr;
-  leaf_build_kernel<V><<<lgrid, 32, 0, stream>>>(prog.leaves, prog.gate_q, prog.gate_layer, prog.gate_in_h,
-                                                 prog.gate_out_kind, prog.gate_kind, sweep ? d_gamma : prog.gamma,
-                                                 sweep ? d_beta : prog.beta, sweep ? prog.p : 0, d_x, prog.n,
-                                                 prog.leaf_elems, prog.n_leaves, prog.density != 0,
-                                                 static_cast<V*>(buf.leaf_tables));
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  if (prog.n_pro_steps > 0 && prog.n_pro_levels > 0) {
+  cudaError_t e;
+  if (prog.n_pro_steps > 0 && prog.n_pro_levels > 0 && prog.p <= kMaxFusedLayers) {
+    // Level programs with hoisted merges: leaf table and prologue in one launch.
+    leaf_prologue_level_kernel<V, Ops><<<nx, kLevelPrologueThreads, shape.pro_smem, stream>>>(
+        prog.pro_steps, prog.n_pro_steps, prog.pro_out_start, prog.pro_pos_nib, prog.pro_levels, prog.n_pro_levels,
+        prog.leaves, prog.n_leaves, buf.leaf_tables, prog.leaf_elems, prog.pro_arena_elems, prog.gate_q,
+        prog.gate_layer, prog.gate_in_h, prog.gate_out_kind, prog.gate_kind, sweep ? d_gamma : prog.gamma,
+        sweep ? d_beta : prog.beta, sweep ? prog.p : 0, prog.p, d_x, prog.n, prog.density != 0);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  } else {
+    leaf_build_kernel<V><<<lgrid, 32, 0, stream>>>(prog.leaves, prog.gate_q, prog.gate_layer, prog.gate_in_h,
+                                                   prog.gate_out_kind, prog.gate_kind, sweep ? d_gamma : prog.gamma,
+                                                   sweep ? d_beta : prog.beta, sweep ? prog.p : 0, d_x, prog.n,
+                                                   prog.leaf_elems, prog.n_leaves, prog.density != 0,
+                                                   static_cast<V*>(buf.leaf_tables));
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  const bool fused = prog.n_pro_steps > 0 && prog.n_pro_levels > 0 && prog.p <= kMaxFusedLayers;
+  if (!fused && prog.n_pro_steps > 0 && prog.n_pro_levels > 0) {
     prologue_level_kernel<V, Ops><<<nx, kLevelPrologueThreads, shape.pro_smem, stream>>>(
         prog.pro_steps, prog.n_pro_steps, prog.pro_out_start, prog.pro_pos_nib, prog.pro_levels, prog.n_pro_levels,
         prog.leaves,
         prog.n_leaves, buf.leaf_tables, prog.leaf_elems, prog.pro_arena_elems);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-  } else if (prog.n_pro_steps > 0) {
+  } else if (!fused && prog.n_pro_steps > 0) {
     prologue_kernel<V, Ops><<<nx, 256, shape.pro_smem, stream>>>(prog.pro_steps, prog.n_pro_steps, prog.leaves,
                                                                  prog.n_leaves, buf.leaf_tables, prog.leaf_elems,
                                                                  prog.pro_arena_elems);
