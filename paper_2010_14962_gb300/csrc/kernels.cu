@@ -405,15 +405,26 @@ __global__ void leaf_build_kernel(const DevLeaf* __restrict__ leaves, const int3
                                   const double* __restrict__ gamma,
                                   const double* __restrict__ beta, int angle_stride, const uint8_t* __restrict__ x,
                                   int n, uint32_t leaf_elems, int n_leaves, bool density, V* __restrict__ out) {
+  __shared__ double s_t[4];  // trig values of the leaf's layer, once per block
   const DevLeaf L = leaves[blockIdx.x % n_leaves];
   const int xi = blockIdx.x / n_leaves;
   if (L.gate == -2) return;  // pseudo-leaf: written by the prologue kernel
   const int r = L.rank_nc + L.ncut;
-  const double* g = gamma + (size_t)xi * angle_stride;
-  const double* b = beta + (size_t)xi * angle_stride;
+  if (threadIdx.x == 0) {
+    s_t[0] = 1.0;
+    s_t[1] = 0.0;
+    s_t[2] = 1.0;
+    s_t[3] = 0.0;
+    if (L.gate >= 0) {
+      const int l = gate_layer[L.gate];
+      sincos(gamma[(size_t)xi * angle_stride + l], &s_t[1], &s_t[0]);
+      sincos(beta[(size_t)xi * angle_stride + l], &s_t[3], &s_t[2]);
+    }
+  }
+  __syncthreads();
   for (int e = threadIdx.x; e < (1 << r); e += blockDim.x)
-    out[(size_t)xi * leaf_elems + L.base + e] = leaf_entry<V>(L, e, gate_q, gate_layer, gate_in_h, gate_out_kind,
-                                                              gate_kind, g, b, x + (size_t)xi * n, density);
+    out[(size_t)xi * leaf_elems + L.base + e] = leaf_entry_trig<V>(L, e, gate_q, gate_in_h, gate_out_kind, gate_kind,
+                                                                   s_t, x + (size_t)xi * n, density);
 }
 
 // ------------------------------------------------------------- lane exec --
@@ -979,49 +990,6 @@ __global__ void __launch_bounds__(1024) prologue_level_kernel(const DevStep* __r
                               leaf_elems, arena_elems, smem);
 }
 
-// Leaf table and hoisted merges of one bit string per block, in one launch:
-// the layers' trig values once per block, every leaf entry (the leaf holding
-// entry i found by binary search on the increasing leaf bases), then the
-// level-ordered prologue on the same table.
-constexpr int kMaxFusedLayers = 16;
-
-template <class V, class Ops = CplxOps<V>>
-__global__ void __launch_bounds__(1024) leaf_prologue_level_kernel(
-    const DevStep* __restrict__ steps, int n_steps, const uint32_t* __restrict__ out_start,
-    const uint16_t* __restrict__ pos_nib, const DevLevel* __restrict__ levels, int n_levels,
-    const DevLeaf* __restrict__ leaves, int n_leaves, void* leaf_tables, uint32_t leaf_elems, uint32_t arena_elems,
-    const int32_t* __restrict__ gate_q, const int8_t* __restrict__ gate_layer, const int8_t* __restrict__ gate_in_h,
-    const int8_t* __restrict__ gate_out_kind, const int8_t* __restrict__ gate_kind, const double* __restrict__ gamma,
-    const double* __restrict__ beta, int angle_stride, int p, const uint8_t* __restrict__ x, int n, bool density) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ double s_trig[4 * kMaxFusedLayers];
-  const int xi = blockIdx.x;
-  V* g_lt = static_cast<V*>(leaf_tables) + (size_t)xi * leaf_elems;
-  const double* ga = gamma + (size_t)xi * angle_stride;
-  const double* be = beta + (size_t)xi * angle_stride;
-  for (int l = threadIdx.x; l < p; l += blockDim.x) {
-    sincos(ga[l], &s_trig[4 * l + 1], &s_trig[4 * l]);
-    sincos(be[l], &s_trig[4 * l + 3], &s_trig[4 * l + 2]);
-  }
-  __syncthreads();
-  const uint8_t* xrow = x + (size_t)xi * n;
-  for (uint32_t i = threadIdx.x; i < leaf_elems; i += blockDim.x) {
-    int lo = 0, hi = n_leaves - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (leaves[mid].base <= i) lo = mid;
-      else hi = mid - 1;
-    }
-    const DevLeaf L = leaves[lo];
-    if (L.gate == -2) continue;  // hoisted result: written by the prologue below
-    const double* t = L.gate >= 0 ? s_trig + 4 * gate_layer[L.gate] : s_trig;
-    g_lt[i] = leaf_entry_trig<V>(L, (int)(i - L.base), gate_q, gate_in_h, gate_out_kind, gate_kind, t, xrow, density);
-  }
-  __syncthreads();  // the block's leaf-table writes are visible to its reads below
-  prologue_level_body<V, Ops>(steps, n_steps, out_start, pos_nib, levels, n_levels, leaves, n_leaves, g_lt,
-                              leaf_elems, arena_elems, smem);
-}
-
 // -------------------------------------------------------------- prologue --
 
 // Hoisted merges (no outer slice class below them): run once per bit string
@@ -1402,10 +1370,9 @@ bool exec_shape_typed(const DeviceProgram& prog, int nx, uint64_t slices_per_x, 
   if (prog.n_pro_steps > 0 && prog.n_pro_levels > 0) {
     const LevelLayout PL = level_layout(prog.n_pro_steps, prog.n_pro_levels, prog.n_leaves, prog.leaf_elems,
                                         prog.pro_arena_elems | 1u, 1, elem_bytes, kLevelPrologueThreads);
-    if (PL.total > (size_t)max_optin - 4 * kMaxFusedLayers * sizeof(double)) return false;
+    if (PL.total > (size_t)max_optin) return false;
     sh.pro_smem = PL.total;
     if (allow_max_smem(prologue_level_kernel<V, Ops>) != cudaSuccess) return false;
-    if (allow_max_smem(leaf_prologue_level_kernel<V, Ops>) != cudaSuccess) return false;
   } else if (prog.n_pro_steps > 0) {
     const SmemLayout PL = smem_layout(prog.n_pro_steps, prog.n_leaves, prog.leaf_elems, prog.pro_arena_elems,
                                       elem_bytes, 256, false);
@@ -1431,34 +1398,21 @@ cudaError_t launch_typed(const DeviceProgram& prog, const uint8_t* d_x, int nx, 
                          const double* d_gamma, const double* d_beta) {
   const unsigned lgrid = (unsigned)prog.n_leaves * (unsigned)nx;
   const bool sweep = d_gamma != nullptr;
-  cudaError_t e;
-  if (prog.n_pro_steps > 0 && prog.n_pro_levels > 0 && prog.p <= kMaxFusedLayers) {
-    // Level programs with hoisted merges: leaf table and prologue in one launch.
-    leaf_prologue_level_kernel<V, Ops><<<nx, kLevelPrologueThreads, shape.pro_smem, stream>>>(
-        prog.pro_steps, prog.n_pro_steps, prog.pro_out_start, prog.pro_pos_nib, prog.pro_levels, prog.n_pro_levels,
-        prog.leaves, prog.n_leaves, buf.leaf_tables, prog.leaf_elems, prog.pro_arena_elems, prog.gate_q,
-        prog.gate_layer, prog.gate_in_h, prog.gate_out_kind, prog.gate_kind, sweep ? d_gamma : prog.gamma,
-        sweep ? d_beta : prog.beta, sweep ? prog.p : 0, prog.p, d_x, prog.n, prog.density != 0);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  } else {
-    leaf_build_kernel<V><<<lgrid, 32, 0, stream>>>(prog.leaves, prog.gate_q, prog.gate_layer, prog.gate_in_h,
-                                                   prog.gate_out_kind, prog.gate_kind, sweep ? d_gamma : prog.gamma,
-                                                   sweep ? d_beta : prog.beta, sweep ? prog.p : 0, d_x, prog.n,
-                                                   prog.leaf_elems, prog.n_leaves, prog.density != 0,
-                                                   static_cast<V*>(buf.leaf_tables));
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-  }
-  const bool fused = prog.n_pro_steps > 0 && prog.n_pro_levels > 0 && prog.p <= kMaxFusedLayers;
-  if (!fused && prog.n_pro_steps > 0 && prog.n_pro_levels > 0) {
+  leaf_build_kernel<V><<<lgrid, 32, 0, stream>>>(prog.leaves, prog.gate_q, prog.gate_layer, prog.gate_in_h,
+                                                 prog.gate_out_kind, prog.gate_kind, sweep ? d_gamma : prog.gamma,
+                                                 sweep ? d_beta : prog.beta, sweep ? prog.p : 0, d_x, prog.n,
+                                                 prog.leaf_elems, prog.n_leaves, prog.density != 0,
+                                                 static_cast<V*>(buf.leaf_tables));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  if (prog.n_pro_steps > 0 && prog.n_pro_levels > 0) {
     prologue_level_kernel<V, Ops><<<nx, kLevelPrologueThreads, shape.pro_smem, stream>>>(
         prog.pro_steps, prog.n_pro_steps, prog.pro_out_start, prog.pro_pos_nib, prog.pro_levels, prog.n_pro_levels,
         prog.leaves,
         prog.n_leaves, buf.leaf_tables, prog.leaf_elems, prog.pro_arena_elems);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-  } else if (!fused && prog.n_pro_steps > 0) {
+  } else if (prog.n_pro_steps > 0) {
     prologue_kernel<V, Ops><<<nx, 256, shape.pro_smem, stream>>>(prog.pro_steps, prog.n_pro_steps, prog.leaves,
                                                                  prog.n_leaves, buf.leaf_tables, prog.leaf_elems,
                                                                  prog.pro_arena_elems);
