@@ -94,17 +94,13 @@ struct dfc {
   float rh, rl, ih, il;
 };
 
-// Error-free transforms: TwoSum (Knuth), Fast2Sum (Dekker, |a| >= |b|) and
-// the FMA-based exact product.  The _rn intrinsics keep the compiler from
-// contracting them into FMAs, which would break exactness.
+// Error-free transform TwoSum (Knuth: s + e = a + b exactly).  The _rn
+// intrinsics keep the compiler from contracting them into FMAs, which would
+// break exactness.
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = __fadd_rn(a, b);
   const float bb = __fsub_rn(s, a);
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
-  e = __fsub_rn(b, __fsub_rn(s, a));
 }
 // Double-word product (xh + xl)(yh + yl) as ph + pl: ph = fl(xh yh), and pl
 // = its exact rounding error (FMA) plus the cross terms (the xl yl term is
