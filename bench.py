@@ -382,8 +382,17 @@ def cpu_baseline(seconds: float, plan_bundle=None):
                        threads=cores)
         done = hi
     dt = time.perf_counter() - t0
+    # One core as well (the paper's single-core comparison), on a shorter sample.
+    one, t1 = 0, time.perf_counter()
+    while time.perf_counter() - t1 < max(1.0, seconds / 4) and one < S:
+        hi = min(S, one + 64)
+        O.tn_amplitude(WORKLOAD["n"], inst.edges, inst.gamma, inst.beta, xs[0], cuts=cuts, slices=(one, hi),
+                       threads=1)
+        one = hi
+    dt1 = time.perf_counter() - t1
     return {"value": (done / S) / dt, "unit": "amplitudes/s", "cores": cores, "kind": "oracle",
-            "sample": f"{done} of {S} slices of one amplitude ({WORKLOAD['name']}), {dt:.1f} s"}
+            "sample": f"{done} of {S} slices of one amplitude ({WORKLOAD['name']}), {dt:.1f} s",
+            "one_core": {"value": (one / S) / dt1, "sample": f"{one} of {S} slices, {dt1:.1f} s"}}
 
 
 def run_reference(args, rank, world):
