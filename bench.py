@@ -232,7 +232,7 @@ def run_ours(args, rank, world, local_rank):
 
     # End to end through the public host API: pinned host x in, host results out.
     plans = [plan] * nx
-    xl = [xs[i] for i in range(nx)]
+    xl = np.ascontiguousarray(xs, dtype=np.uint8)  # one row per bit string
     for _ in range(2):
         qtn.contract_batch(plans, xl, args.precision)
     e2e_steps = max(3, min(args.steps, 50))

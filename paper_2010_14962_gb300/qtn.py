@@ -9,6 +9,7 @@ the library.
 from __future__ import annotations
 
 import ctypes
+import itertools
 import json
 import os
 import re
@@ -80,7 +81,7 @@ def lib():
             "qtn_contract_amplitudes_noalloc": [vp, vp, ctypes.c_int, ctypes.c_int, vp, vp],
             "qtn_contract_slices": [vp, u8p, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, vp, f64p, vp],
             "qtn_contract_sweep_device": [vp, vp, vp, vp, ctypes.c_int, ctypes.c_int, vp, vp],
-            "qtn_contract_batch": [P(vp), P(u8p), ctypes.c_int, ctypes.c_int, vp, f64p],
+            "qtn_contract_batch": [P(vp), vp, ctypes.c_int, ctypes.c_int, vp, vp],
             "qtn_plan_executor": [vp, P(ctypes.c_char_p)],
             "qtn_plan_describe": [vp, ctypes.c_char_p, ctypes.c_size_t, P(ctypes.c_size_t)],
             "qtn_plan_set_kernel_timing": [vp, ctypes.c_int],
@@ -398,18 +399,31 @@ class Plan:
 
 
 def contract_batch(plans, xs, precision: str = "fp32", stream=None) -> np.ndarray:
-    """Amplitudes of independent (plan, x) jobs."""
+    """Amplitudes of independent (plan, x) jobs.  ``xs``: one bit string per
+    job (a sequence), or a 2-D array with one row per job (all of one n)."""
     n = len(plans)
-    arrs = [np.ascontiguousarray(np.asarray(x, dtype=np.uint8).reshape(-1)) for x in xs]
-    for p, a in zip(plans, arrs):
-        if a.size != p.n:
+    if len(xs) != n:
+        raise ValueError("plans and xs must have the same length")
+    # All bit strings in one contiguous host buffer; the row pointers are
+    # addresses in it (cheaper to marshal than one ctypes pointer per array).
+    if isinstance(xs, np.ndarray) and xs.ndim == 2:
+        flat = np.ascontiguousarray(xs, dtype=np.uint8)
+        sizes = [flat.shape[1]] * n
+    else:
+        parts = [np.asarray(x, dtype=np.uint8).reshape(-1) for x in xs]
+        sizes = [a.size for a in parts]
+        flat = np.concatenate(parts) if parts else np.zeros(1, np.uint8)
+    for p, m in zip(plans, sizes):
+        if m != p.n:
             raise ValueError("every x must have its plan's n entries")
+    base = flat.ctypes.data
+    starts = list(itertools.accumulate(sizes[:-1], initial=0))[:n]
+    xp = (ctypes.c_void_p * n)(*[base + o for o in starts])
     hp = (ctypes.c_void_p * n)(*[p.handle for p in plans])
-    xp = (ctypes.POINTER(ctypes.c_uint8) * n)(*[_ptr(a, ctypes.c_uint8) for a in arrs])
-    out = np.zeros(2 * max(n, 1))
+    out = np.empty(2 * max(n, 1))
     _check(lib().qtn_contract_batch(hp, xp, n, PRECISIONS[precision], _stream_handle(stream),
-                                    _ptr(out, ctypes.c_double)))
-    return out[0:2 * n:2] + 1j * out[1:2 * n:2]
+                                    out.ctypes.data))
+    return out.view(np.complex128)[:n]
 
 
 def batch_cancel():

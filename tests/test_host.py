@@ -422,3 +422,17 @@ def test_nonzero_slice_search():
         return np.log2(8 * c["macs_per_slice"]) + (max(d["cut_class"]) + 1) + 8 * max(0, c["width"] - greedy.cost()["width"])
 
     assert fitness(qtn.Plan(net, cuts=cuts)) <= fitness(greedy) + 1e-9
+
+
+def test_contract_batch_checks_bit_strings_before_the_library():
+    # Marshalling of contract_batch: a length mismatch or a bit string of the
+    # wrong size is refused on the host, for the list and the 2-D forms.
+    inst = I.qaoa_instance(16, 1, 1)
+    plan = qtn.Plan(qtn.Network(16, inst.edges, inst.gamma, inst.beta), k=2)
+    xs = I.bitstrings(16, 3, 1)
+    with pytest.raises(ValueError):
+        qtn.contract_batch([plan] * 2, xs, "fp64")
+    with pytest.raises(ValueError):
+        qtn.contract_batch([plan] * 3, xs[:, :15], "fp64")
+    with pytest.raises(ValueError):
+        qtn.contract_batch([plan] * 3, [xs[0], xs[1][:15], xs[2]], "fp64")
