@@ -135,6 +135,25 @@ def profiled_traffic(prec: str):
     return e.get("dram_bytes_per_launch")
 
 
+def step_classes(prog: dict, elem_bytes: int) -> list:
+    """Per merge class (K = 2^kb summed entries) of a program: steps, share of
+    the executed multiply-adds, and flop per byte of shared-memory traffic
+    with every operand and result moved once (the root's outputs are summed,
+    not stored); every class is on chip, so the ALU roof bounds it."""
+    cls = {}
+    for st in prog["steps"]:
+        ma, nb, kb, bb = st["ma"], st["nb"], st["kb"], st["bb"]
+        macs = 2 ** (ma + nb + kb + bb)
+        moved = 2 ** (ma + kb + bb) + 2 ** (kb + nb + bb) + (0 if st["flags"] & 4 else 2 ** (ma + nb + bb))
+        c = cls.setdefault(2 ** kb, [0, 0, 0])
+        c[0] += 1
+        c[1] += macs
+        c[2] += moved * elem_bytes
+    total = sum(c[1] for c in cls.values())
+    return [{"K": k, "steps": c[0], "mac_share": c[1] / total, "flop_per_byte": 8 * c[1] / c[2]}
+            for k, c in sorted(cls.items())]
+
+
 def setup_workload(rank: int, form: str = "gates"):
     from paper_2010_14962_gb300 import instances as I
     from paper_2010_14962_gb300 import qtn
@@ -290,7 +309,9 @@ def run_ours(args, rank, world, local_rank):
                                      "peaks) / %d FP32 instructions per multiply-add"
                                      % (sm_for_peak, INSTR_PER_MAC[args.precision]))
                      if args.precision != "fp64" else "FP64 nominal 1.25 TFLOP/s",
-                     "kernel_ms_avg": avg_kernel_s * 1e3},
+                     "kernel_ms_avg": avg_kernel_s * 1e3,
+                     "step_classes": step_classes(prog, 8 if args.precision in ("fp32", "tf32", "bf16x3", "tf32x3",
+                                                                                "bf16x6") else 16)},
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": "amplitudes/s", "h2d_bytes_per_step": int(nx * WORKLOAD["n"]),
                 "d2h_bytes_per_step": int(nx * 16), "api": "qtn_contract_batch (host x in, host amplitudes out)"},

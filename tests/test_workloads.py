@@ -47,3 +47,22 @@ def test_batch_program_is_least_work_level_program():
         work = lambda pr: (2 ** len(pr["outer_class"])) * pr["macs_per_item"]
         best = min(work(pr) for nm, pr in progs.items() if pr["executor"] == "level" and other not in nm)
         assert work(progs[name]) == best
+
+
+def test_bench_step_classes_cover_the_program():
+    # The benchmark's per-class breakdown: classes partition the steps and the
+    # executed multiply-adds of the program.
+    import os
+    import sys
+
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+
+    inst = I.qaoa_instance(40, 2, 2)
+    plan = qtn.Plan(qtn.Network(40, inst.edges, inst.gamma, inst.beta), k=10)
+    for name, prog in plan.describe()["programs"].items():
+        cls = bench.step_classes(prog, 16)
+        assert sum(c["steps"] for c in cls) == len(prog["steps"]), name
+        assert abs(sum(c["mac_share"] for c in cls) - 1.0) < 1e-12, name
+        macs = sum(c["mac_share"] for c in cls if c["K"] == 1)
+        assert 0.0 <= macs <= 1.0 and all(c["flop_per_byte"] > 0 for c in cls)
