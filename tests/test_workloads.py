@@ -64,5 +64,4 @@ def test_bench_step_classes_cover_the_program():
         cls = bench.step_classes(prog, 16)
         assert sum(c["steps"] for c in cls) == len(prog["steps"]), name
         assert abs(sum(c["mac_share"] for c in cls) - 1.0) < 1e-12, name
-        macs = sum(c["mac_share"] for c in cls if c["K"] == 1)
-        assert 0.0 <= macs <= 1.0 and all(c["flop_per_byte"] > 0 for c in cls)
+        assert all(c["flop_per_byte"] > 0 for c in cls), name
