@@ -10,6 +10,8 @@ a(x) = <x| U_B(beta_p) U_C(gamma_p) ... U_B(beta_1) U_C(gamma_1) H^n |0^n>
 
 * ``statevector``: all 2^n amplitudes (the definition on a state vector).
 * ``pathsum``: one amplitude as an explicit sum over basis paths (tiny n*p).
+* ``choose_cuts``: the oracle's own cut set (greedy on its own min-fill
+  order), so that its timings and reference values need no product plan.
 * ``tn_amplitude``: the paper's method -- circuit as a tensor network with
   gates/inputs/measurements as vertices and wire segments as edges
   (Sec. II.A), cut edges fixed to every value (Sec. III.A, Eq. 2), pairwise
@@ -56,6 +58,8 @@ def _bind(lib):
                               ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int, f64p, f64p,
                               f64p, ctypes.POINTER(ctypes.c_int)]
     lib.oracle_zz_per_qubit.argtypes = [ctypes.c_int, ctypes.c_int, i32p, ctypes.c_int, i32p]
+    lib.oracle_choose_cuts.argtypes = [ctypes.c_int, ctypes.c_int, i32p, ctypes.c_int, ctypes.c_int, i32p, i32p,
+                                       ctypes.POINTER(ctypes.c_int)]
     return lib
 
 
@@ -132,6 +136,22 @@ def zz_per_qubit(n, edges, p, lib=None) -> np.ndarray:
     out = np.zeros(n, dtype=np.int32)
     lib.oracle_zz_per_qubit(n, p, _ptr(e, ctypes.c_int32), len(e), _ptr(out, ctypes.c_int32))
     return out
+
+
+def choose_cuts(n, edges, p, k, lib=None):
+    """The oracle's own k cut segments as (qubit, pos) pairs, and the width
+    they leave: repeatedly cut the segment found in the most widest merges of
+    the current min-fill order (independent of the product's planner)."""
+    lib = lib or _load()
+    e = np.ascontiguousarray(np.asarray(edges, dtype=np.int32).reshape(-1, 2))
+    cq = np.zeros(max(k, 1), dtype=np.int32)
+    cp = np.zeros(max(k, 1), dtype=np.int32)
+    width = ctypes.c_int(0)
+    rc = lib.oracle_choose_cuts(n, int(p), _ptr(e, ctypes.c_int32), len(e), int(k), _ptr(cq, ctypes.c_int32),
+                                _ptr(cp, ctypes.c_int32), ctypes.byref(width))
+    if rc != 0:
+        raise ValueError(f"oracle_choose_cuts failed ({rc})")
+    return [(int(cq[j]), int(cp[j])) for j in range(k)], int(width.value)
 
 
 class TNResult:

@@ -660,3 +660,146 @@ int oracle_zz_per_qubit(int n, int p, const int32_t* edges, int m, int32_t* out)
   }
   return 0;
 }
+
+/* ------------------------------------------------ the oracle's own cuts -- */
+
+/* Largest merged rank |A u B| of the min-fill order (Sec. II.B) of the
+ * network with `cut_labels` removed, replayed on label sets only.  If
+ * `counts` is given, every label of every merge of that largest rank gets
+ * one count there. */
+static int order_width(const Circuit* c, const int* cut_labels, int k, int* counts) {
+  Tensor* ts = sliced_network(c, cut_labels, k, 0);
+  int n_order = 0;
+  int* order = minfill_order(c->n_tensors, ts, c->n_labels, &n_order);
+  int nt = c->n_tensors;
+  int** sets = (int**)malloc(sizeof(int*) * (size_t)nt);
+  int* sz = (int*)malloc(sizeof(int) * (size_t)nt);
+  char* alive = (char*)malloc((size_t)nt);
+  for (int i = 0; i < nt; ++i) {
+    sets[i] = (int*)malloc(sizeof(int) * (size_t)c->n_labels);
+    sz[i] = ts[i].rank;
+    memcpy(sets[i], ts[i].labels, sizeof(int) * (size_t)ts[i].rank);
+    alive[i] = 1;
+    tensor_free(&ts[i]);
+  }
+  free(ts);
+  int* uni = (int*)malloc(sizeof(int) * (size_t)c->n_labels);
+  int width = 0;
+  for (int pass = 0; pass < (counts ? 2 : 1); ++pass) {
+    /* pass 0 finds the width, pass 1 counts the labels of the widest merges */
+    int** ws = (int**)malloc(sizeof(int*) * (size_t)nt);
+    int* wz = (int*)malloc(sizeof(int) * (size_t)nt);
+    char* wa = (char*)malloc((size_t)nt);
+    for (int i = 0; i < nt; ++i) {
+      ws[i] = (int*)malloc(sizeof(int) * (size_t)c->n_labels);
+      memcpy(ws[i], sets[i], sizeof(int) * (size_t)sz[i]);
+      wz[i] = sz[i];
+      wa[i] = alive[i];
+    }
+    for (int s = 0; s < n_order; ++s) {
+      int u = order[s], t1 = -1, t2 = -1;
+      for (int i = 0; i < nt; ++i) {
+        if (!wa[i]) continue;
+        for (int j = 0; j < wz[i]; ++j)
+          if (ws[i][j] == u) {
+            if (t1 < 0) t1 = i;
+            else t2 = i;
+          }
+      }
+      if (t1 < 0 || t2 < 0) continue;
+      int nu = 0;
+      for (int j = 0; j < wz[t1]; ++j) uni[nu++] = ws[t1][j];
+      for (int j = 0; j < wz[t2]; ++j) {
+        int dup = 0;
+        for (int a = 0; a < wz[t1]; ++a) dup |= ws[t1][a] == ws[t2][j];
+        if (!dup) uni[nu++] = ws[t2][j];
+      }
+      if (pass == 0 && nu > width) width = nu;
+      if (pass == 1 && nu == width)
+        for (int j = 0; j < nu; ++j) counts[uni[j]]++;
+      /* merged tensor: labels of the union held by only one of the two */
+      int nr = 0;
+      for (int j = 0; j < nu; ++j) {
+        int in1 = 0, in2 = 0;
+        for (int a = 0; a < wz[t1]; ++a) in1 |= ws[t1][a] == uni[j];
+        for (int a = 0; a < wz[t2]; ++a) in2 |= ws[t2][a] == uni[j];
+        if (!(in1 && in2)) ws[t1][nr++] = uni[j];
+      }
+      wz[t1] = nr;
+      wa[t2] = 0;
+    }
+    for (int i = 0; i < nt; ++i) free(ws[i]);
+    free(ws);
+    free(wz);
+    free(wa);
+  }
+  for (int i = 0; i < nt; ++i) free(sets[i]);
+  free(sets);
+  free(sz);
+  free(alive);
+  free(uni);
+  free(order);
+  return width;
+}
+
+/*
+ * The oracle's own cut set of k wire segments, chosen without the product's
+ * planner (Sec. III.A: cutting edges lowers the width of the subnetworks).
+ * k times: plan the min-fill order of the network with the cuts chosen so
+ * far removed, find its largest merged rank, and cut the candidate segment
+ * that occurs in the most merges of that rank (ties: the lowest label; if
+ * none occurs there, the lowest unused candidate).  Candidates are the
+ * segments oracle_tn can name: those entering a ZZ gate other than the first
+ * one on their qubit.  Writes (cut_qubit[j], cut_pos[j]) in oracle_tn's
+ * naming and, if width_out is given, the width left by all k cuts.
+ * Returns 0 on success, 1 for bad arguments or too few candidates.
+ */
+int oracle_choose_cuts(int n, int p, const int32_t* edges, int m, int k, int32_t* cut_qubit, int32_t* cut_pos,
+                       int* width_out) {
+  if (n < 1 || p < 1 || m < 1 || k < 0) return 1;
+  double* zero = (double*)calloc((size_t)p, sizeof(double));
+  Circuit c;
+  circuit_build(n, p, edges, m, zero, zero, 0, NULL, &c);
+  free(zero);
+  int* cand_q = (int*)malloc(sizeof(int) * (size_t)c.n_labels);
+  int* cand_t = (int*)malloc(sizeof(int) * (size_t)c.n_labels);
+  for (int l = 0; l < c.n_labels; ++l) cand_q[l] = -1;
+  int n_cand = 0;
+  for (int q = 0; q < n; ++q)
+    for (int t = 1; t < c.zz_count[q]; ++t) {
+      int l = c.zz_in_label[q * c.max_zz + t];
+      cand_q[l] = q;
+      cand_t[l] = t - 1;
+      n_cand++;
+    }
+  if (k > n_cand) {
+    free(cand_q);
+    free(cand_t);
+    circuit_free(&c);
+    return 1;
+  }
+  int* cut_labels = (int*)malloc(sizeof(int) * (size_t)(k > 0 ? k : 1));
+  int* counts = (int*)malloc(sizeof(int) * (size_t)c.n_labels);
+  for (int j = 0; j < k; ++j) {
+    for (int l = 0; l < c.n_labels; ++l) counts[l] = 0;
+    order_width(&c, cut_labels, j, counts);
+    int best = -1;
+    for (int l = 0; l < c.n_labels; ++l) {
+      if (cand_q[l] < 0) continue;
+      int used = 0;
+      for (int i = 0; i < j; ++i) used |= cut_labels[i] == l;
+      if (used) continue;
+      if (best < 0 || counts[l] > counts[best]) best = l;
+    }
+    cut_labels[j] = best;
+    cut_qubit[j] = cand_q[best];
+    cut_pos[j] = cand_t[best];
+  }
+  if (width_out) *width_out = order_width(&c, cut_labels, k, NULL);
+  free(counts);
+  free(cut_labels);
+  free(cand_q);
+  free(cand_t);
+  circuit_free(&c);
+  return 0;
+}

@@ -211,3 +211,26 @@ def test_invalid_cut_rejected():
         O.tn_amplitude(8, inst.edges, inst.gamma, inst.beta, x, cuts=[(0, 2)])  # 3 ZZ gates: pos <= 1
     with pytest.raises(ValueError):
         O.tn_amplitude(8, inst.edges, inst.gamma, inst.beta, x, cuts=[(0, 0), (0, 0)])
+
+
+def test_oracle_own_cuts_are_valid_and_exact():
+    # The oracle's own cut chooser (used by the benchmark's CPU arm and for
+    # reference values): k distinct segments that oracle_tn accepts, and the
+    # sliced sum (Eq. 2) over them equals the state vector's amplitude.
+    n, p = 14, 2
+    inst = I.qaoa_instance(n, p, 6)
+    sv = O.statevector(n, inst.edges, inst.gamma, inst.beta)
+    x = I.bitstrings(n, 1, 6)[0]
+    for k in (1, 3, 5):
+        cuts, width = O.choose_cuts(n, inst.edges, p, k)
+        assert len(set(cuts)) == k
+        r = O.tn_amplitude(n, inst.edges, inst.gamma, inst.beta, x, cuts=cuts)
+        assert r.width == width
+        assert abs(r.value - sv[O.bits_to_int(x)]) < 1e-12 * abs(sv[O.bits_to_int(x)])
+
+
+def test_oracle_own_cuts_lower_the_width():
+    # Sec. III.A: cutting edges lowers the width of the subnetworks.
+    inst = I.qaoa_instance(80, 1, 3)
+    widths = [O.choose_cuts(80, inst.edges, 1, k)[1] for k in (0, 4, 8, 16)]
+    assert widths == sorted(widths, reverse=True) and widths[-1] < widths[0] - 8, widths
