@@ -213,7 +213,14 @@ qtn_status qtn_contract_amplitudes_device(const qtn_plan_t* plan, const uint8_t*
  *     a device allocation or frees device memory.
  *   Set-up: the first call on each device looks up the array's device
  *     address with that device current; make that first call before any
- *     stream capture.
+ *     stream capture.  The array's 64 MiB are reserved on a device when the
+ *     library part that holds it is loaded there: with CUDA's default lazy
+ *     module loading that is this first call, so a caller whose framework
+ *     then reserves the rest of the device memory should make its first call
+ *     before that.
+ *   Errors inside the kernels (an executor that meets a merge it cannot run)
+ *     write NaN into that call's d_out; the call itself has already returned
+ *     QTN_OK (nothing here synchronises).
  *   Sharing: all calls use the same array, so calls that overlap on the GPU
  *     (on different streams, or from racing host threads) corrupt each
  *     other; issue them on one stream.
@@ -314,6 +321,16 @@ qtn_status qtn_plan_select_executor(const qtn_plan_t* plan, qtn_precision prec, 
  * call once its stream has been synchronised. */
 qtn_status qtn_plan_set_kernel_timing(const qtn_plan_t* plan, int on);
 qtn_status qtn_plan_kernel_ms(const qtn_plan_t* plan, float* ms);
+
+/* Measured arithmetic peaks of the current device, the denominators of the
+ * executors' roofline fractions (measurement support; the paper has no
+ * counterpart).  A grid of several blocks per SM runs independent FP32 (and
+ * then FP64) fused multiply-add chains; the best of `reps` timed launches
+ * (CUDA events, default stream, synchronous) gives *fp32_tflops and
+ * *fp64_tflops (host), counting a multiply-add as 2 flops.  Takes about
+ * 50 ms per rep on a GB300.  QTN_ERR_INVALID_ARG for null outputs or
+ * reps < 1; QTN_ERR_CUDA if a launch fails. */
+qtn_status qtn_pipe_peaks(int reps, double* fp32_tflops, double* fp64_tflops);
 
 /* ------------------------------------------------ learned cost surrogate --
  * A small MLP predicts the exact counter's log2 total flops and log2 peak

@@ -108,6 +108,7 @@ def lib():
             "qtn_search_cuts_surrogate": [vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                           ctypes.c_uint64, ctypes.c_int, i32p, f64p, P(ctypes.c_int),
                                           P(ctypes.c_int), f64p, ctypes.c_int, P(ctypes.c_int)],
+            "qtn_pipe_peaks": [ctypes.c_int, f64p, f64p],
             "qtn_status_string": [ctypes.c_int],
             "qtn_last_error": [],
         }
@@ -424,6 +425,14 @@ def contract_batch(plans, xs, precision: str = "fp32", stream=None) -> np.ndarra
     _check(lib().qtn_contract_batch(hp, xp, n, PRECISIONS[precision], _stream_handle(stream),
                                     out.ctypes.data))
     return out.view(np.complex128)[:n]
+
+
+def pipe_peaks(reps: int = 3) -> dict:
+    """qtn_pipe_peaks: measured FP32 and FP64 multiply-add peaks (TFLOP/s) of
+    the current device."""
+    f32, f64 = ctypes.c_double(), ctypes.c_double()
+    _check(lib().qtn_pipe_peaks(int(reps), ctypes.byref(f32), ctypes.byref(f64)))
+    return {"fp32_tflops": f32.value, "fp64_tflops": f64.value}
 
 
 def batch_cancel():

@@ -289,6 +289,34 @@ def test_fp32x2_meets_fp64_accuracy(gpu, config80):
     assert np.max(np.abs(got - refs) / np.abs(refs)) < 1e-10
 
 
+@pytest.fixture(scope="module")
+def draws80(config80):
+    # The n = 80 graph and 16-cut plan under four seeded (gamma, beta) draws
+    # (the workload's own first), 8 bit strings each; references from the
+    # oracle with its own 8-cut plan.
+    inst, plan, xs, refs = config80
+    draws = [(inst.gamma, inst.beta)] + [I.angles(1, 7000 + d) for d in range(1, 4)]
+    cuts, _ = O.choose_cuts(80, inst.edges, 1, 8)
+    ref = np.array([O.tn_amplitude(80, inst.edges, g, b, x, cuts=cuts, threads=16).value for g, b in draws for x in xs])
+    G = np.repeat(np.stack([g for g, _ in draws]), len(xs), axis=0)
+    B = np.repeat(np.stack([b for _, b in draws]), len(xs), axis=0)
+    return np.tile(xs, (len(draws), 1)), G, B, ref
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32x2"])
+def test_precision_draws_n80(gpu, config80, draws80, prec):
+    # The precision choice over several angle draws: the complex128 form and
+    # the double-float form stay within 1e-10 of the oracle on every draw and
+    # bit string (element by element); plain FP32 is reported beside them.
+    inst, plan, xs, refs = config80
+    X, G, B, ref = draws80
+    got = _sweep(plan, X, G, B, prec)
+    errs = np.abs(got - ref) / np.abs(ref)
+    f32 = np.abs(_sweep(plan, X, G, B, "fp32") - ref) / np.abs(ref)
+    print(prec, "max rel err per draw", errs.reshape(4, -1).max(axis=1), "fp32:", f32.reshape(4, -1).max(axis=1))
+    assert errs.max() < 1e-10
+
+
 def _executor_precisions(name):
     if "/fp64/" in name:
         return ["fp64", "fp32x2"]
