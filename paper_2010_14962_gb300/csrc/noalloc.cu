@@ -14,7 +14,12 @@
 // host code below asks the runtime for its device address once per device
 // (cudaGetSymbolAddress, with that device current) and passes that address to
 // the kernels.  The first call on a device does this set-up; make that first
-// call before any stream capture.
+// call before any stream capture.  The array belongs to this file's module:
+// the device memory behind it is reserved when that module is loaded on a
+// device, which with CUDA's default lazy module loading is this set-up, i.e.
+// the first call of this entry point on the device.  A caller whose framework
+// later reserves most of the device memory should make that first call before
+// the framework's pool takes it.
 //
 // Every call shares the one array: a call overwrites the previous call's
 // contents, so calls that overlap on the GPU (different streams, or host
@@ -62,6 +67,14 @@ cudaError_t scratch_address(unsigned char** out) {
 template <class T>
 size_t bytes_of(const std::vector<T>& v) {
   return v.size() * sizeof(T);
+}
+
+// The executors set the error word when they meet a merge they cannot run;
+// this path keeps no state between calls, so a set word turns the call's
+// amplitudes into NaN instead of being overwritten by the next call.
+__global__ void mark_failed_kernel(const int* __restrict__ err, double* __restrict__ out, int nx) {
+  if (*err == 0) return;
+  for (int i = threadIdx.x; i < 2 * nx; i += blockDim.x) out[i] = __longlong_as_double(0x7ff8000000000000ll);
 }
 
 }  // namespace
@@ -172,5 +185,9 @@ extern "C" qtn_status qtn_contract_amplitudes_noalloc(const qtn_plan_t* plan, co
                          stream);
   if (e != cudaSuccess)
     return internal::set_error(QTN_ERR_CUDA, std::string("launch_contraction: ") + cudaGetErrorString(e));
+  mark_failed_kernel<<<1, 256, 0, stream>>>(buf.err, d_out, nx);
+  e = cudaGetLastError();
+  if (e != cudaSuccess)
+    return internal::set_error(QTN_ERR_CUDA, std::string("mark_failed_kernel: ") + cudaGetErrorString(e));
   return QTN_OK;
 }
