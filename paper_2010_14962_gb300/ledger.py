@@ -10,6 +10,12 @@ be written to and reloaded from a JSON checkpoint, and the final amplitude
 is the fixed-order (ascending range) compensated sum of the recorded
 partials -- independent of which worker computed what, or when.
 
+`sharded_amplitude` is the data path of one amplitude over several ranks
+(Sec. III.A, Sec. IV.B: only one scalar per subgraph goes back): rank g
+contracts the contiguous slice range [g S / G, (g+1) S / G) and the ranks'
+(sum, compensation) pairs meet in one all-gather (gloo on the CPU, NCCL on
+GPUs), summed in ascending g order on every rank.
+
 `run_ranks` distributes ranges round-robin over the ranks of a
 torch.distributed process group.  Workers publish each finished range in the
 group's key-value store; rank 0 waits for them with a deadline and then
@@ -138,3 +144,55 @@ def run_ranks(ledger: SliceLedger, compute: ComputeFn, rank: int, world: int, st
     if ledger.path:
         ledger.save()
     return ledger.total()
+
+
+def shard_range(n_slices: int, rank: int, world: int) -> Range:
+    """Contiguous slice range of rank `rank` of `world`: [g S / G, (g+1) S / G)."""
+    if world <= 0 or not 0 <= rank < world:
+        raise ValueError("0 <= rank < world required")
+    return (n_slices * rank // world, n_slices * (rank + 1) // world)
+
+
+class ShardsLost(RuntimeError):
+    pass
+
+
+def sharded_amplitude(compute: ComputeFn, n_slices: int, rank: int, world: int, dist, device="cpu",
+                      recover: bool = True):
+    """One amplitude contracted by `world` ranks: this rank computes its
+    contiguous range (compute(lo, hi) -> (sum, comp)), one all_gather of the
+    four doubles (sum.re, sum.im, comp.re, comp.im) per rank, and every rank
+    adds the pairs in ascending rank order (compensated, so the result does
+    not depend on the schedule).  Returns (total, recomputed ranges).
+
+    If the collective fails (a rank died or never joined; the process
+    group's timeout bounds the wait), the surviving rank recomputes every
+    other rank's range itself when `recover` is set (Sec. V: only the lost
+    subgraphs), else raises ShardsLost."""
+    import torch
+
+    mine = shard_range(n_slices, rank, world)
+    s, c = compute(*mine)
+    local = torch.tensor([s.real, s.imag, c.real, c.imag], dtype=torch.float64, device=device)
+    parts = [torch.zeros(4, dtype=torch.float64, device=device) for _ in range(world)]
+    recomputed: List[Range] = []
+    try:
+        dist.all_gather(parts, local)
+        got = [p.cpu().tolist() for p in parts]
+    except Exception as e:  # a lost rank: the collective ended with an error
+        if not recover:
+            raise ShardsLost(str(e)) from e
+        got = []
+        for g in range(world):
+            if g == rank:
+                got.append([s.real, s.imag, c.real, c.imag])
+            else:
+                r = shard_range(n_slices, g, world)
+                recomputed.append(r)
+                sg, cg = compute(*r)
+                got.append([sg.real, sg.imag, cg.real, cg.imag])
+    led = SliceLedger(n_slices, max(1, n_slices))
+    led.ranges = [shard_range(n_slices, g, world) for g in range(world)]
+    for g, (sr, si, cr, ci) in enumerate(got):
+        led.record(led.ranges[g], complex(sr, si), complex(cr, ci), save=False)
+    return led.total(), recomputed
