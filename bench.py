@@ -303,8 +303,9 @@ def run_ours(args, rank, world, local_rank):
                    "parallelism": f"weak: {nx} bit strings per GPU, slices across CTAs/threads"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": profiled_traffic(args.precision),
-                     "kernel": {"lane": "lane_exec_kernel", "level": "level_exec_kernel"}.get(prog["executor"],
-                                                                                            "block_exec_kernel"),
+                     "kernel": {"lane": "lane_exec_kernel", "level": "level_exec_kernel",
+                                "level-jit": "qtn_level_jit (generated for this plan)"}.get(prog["executor"],
+                                                                                             "block_exec_kernel"),
                      "peak_source": ("measured %s FMA peak of this GPU (qtn_pipe_peaks, median SM clock %s MHz)"
                                      % ("FP64" if args.precision == "fp64" else "FP32",
                                         pipe_peaks["clocks"].get("sm_mhz"))),

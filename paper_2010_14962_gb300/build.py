@@ -15,9 +15,10 @@ ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libqtn.so")
 
-SOURCES = ["network.cpp", "plan.cpp", "program.cpp", "surrogate.cpp", "kernels.cu", "api.cu", "noalloc.cu", "mlp.cu", "peaks.cu"]
+SOURCES = ["network.cpp", "plan.cpp", "program.cpp", "surrogate.cpp", "kernels.cu", "api.cu", "noalloc.cu", "mlp.cu",
+           "peaks.cu", "jit.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-COMMON = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"), "-I", CSRC]
+COMMON = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"), "-I", CSRC, "-I", BUILD]
 
 
 def _nvcc() -> str:
@@ -44,14 +45,28 @@ def _compile(src: str) -> str:
     return obj
 
 
+def _write_arith_source():
+    """The shared complex arithmetic (csrc/arith.cuh) as a C++ raw string, for
+    the kernels the library generates and compiles at run time."""
+    with open(os.path.join(CSRC, "arith.cuh")) as f:
+        text = f.read()
+    body = 'R"QTNARITH(' + text + ')QTNARITH"\n'
+    out = os.path.join(BUILD, "arith_src.inc")
+    if not os.path.exists(out) or open(out).read() != body:
+        with open(out + ".tmp", "w") as f:
+            f.write(body)
+        os.replace(out + ".tmp", out)
+
+
 def build(verbose: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
+    _write_arith_source()
     with concurrent.futures.ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(_compile, SOURCES))
     if not os.path.exists(LIB) or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs):
         tmp = LIB + f".{os.getpid()}.tmp"
-        subprocess.run([_nvcc(), *ARCH, "-shared", "-Xlinker", "-z", "-Xlinker", "defs", "-o", tmp, *objs, "-lcudart"],
-                       check=True)
+        subprocess.run([_nvcc(), *ARCH, "-shared", "-Xlinker", "-z", "-Xlinker", "defs", "-o", tmp, *objs, "-lcudart",
+                        "-ldl"], check=True)
         os.replace(tmp, LIB)
     if verbose:
         print("built", LIB)

@@ -20,6 +20,7 @@
 
 #include "../../include/qtn.h"
 #include "internal.hpp"
+#include "jit.hpp"
 #include "kernels.cuh"
 #include "network.hpp"
 #include "plan.hpp"
@@ -196,8 +197,23 @@ struct ProgSlot {
   int blocks_per_sm = 1;  // level executor: blocks sharing an SM's shared memory
   DeviceProgram dprog;
   bool uploaded = false;
+  int jit_arith = -1;     // LevelJit: the arithmetic its generated kernel runs
   uint64_t items() const { return 1ull << prog.n_outer; }
 };
+
+// Suffix of a specialised executor's name for an arithmetic.
+const char* jit_suffix(Arith a) {
+  switch (a) {
+    case Arith::F64: return "/jit-fp64";
+    case Arith::F32: return "/jit-fp32";
+    case Arith::F32X2: return "/jit-fp32x2";
+    default: return nullptr;
+  }
+}
+// Interpreted level executors slower than this (ms per launch) get a
+// specialised variant compiled and timed by the autotuner.
+constexpr float kJitMinMs = 0.05f;
+constexpr int kJitCandidates = 2;
 
 std::atomic<uint64_t> g_plan_uid{0};
 
@@ -417,11 +433,52 @@ struct qtn_plan {
 
   bool eligible(int si, qtn_precision prec) const {
     const ProgSlot& s = slots[si];
+    if (s.exec == Executor::LevelJit) return s.jit_arith == (int)arith_of(prec);
     if (wide(prec) && s.fp32_only) return false;
     if (!wide(prec) && s.fp64_only) return false;
     const bool lane_arith = prec == QTN_FP64 || prec == QTN_FP32 || prec == QTN_FP32X2;
     if (s.exec == Executor::Lane && !lane_arith) return false;
     return true;
+  }
+
+  // The specialised variant of level slot `base` for arithmetic `a` (created,
+  // generated, compiled and uploaded on first use); its index in *out.
+  qtn_status make_jit_slot(int base, Arith a, int* out) {
+    const char* suf = jit_suffix(a);
+    if (!suf || slots[base].exec != Executor::Level)
+      return fail(QTN_ERR_UNSUPPORTED, "no specialised executor for this program and precision");
+    const std::string name = slots[base].name + suf;
+    for (int si = 1; si < (int)slots.size(); ++si)
+      if (slots[si].name == name) {
+        *out = si;
+        return QTN_OK;
+      }
+    std::string why;
+    if (!jit_available(&why)) return fail(QTN_ERR_UNSUPPORTED, "run-time compiler unavailable: " + why);
+    qtn_status st = upload(slots[base]);
+    if (st != QTN_OK) return st;
+    ProgSlot js = slots[base];
+    js.name = name;
+    js.exec = Executor::LevelJit;
+    js.jit_arith = (int)a;
+    JitLevelShape shape;
+    if (!jit_level_shape(js.prog, arith_elem_bytes(a), js.threads, js.blocks_per_sm, &shape))
+      return fail(QTN_ERR_UNSUPPORTED, "the program's items do not fit in shared memory");
+    std::string err;
+    const std::string src = jit_level_source(js.prog, a, shape, &err);
+    if (src.empty()) return fail(QTN_ERR_UNSUPPORTED, "specialised executor: " + err);
+    const void* kernel = nullptr;
+    {
+      Trace trace("qtn jit compile");
+      if (!jit_compile(src, shape.smem, &kernel, &err)) return fail(QTN_ERR_UNSUPPORTED, err);
+    }
+    js.dprog.exec = Executor::LevelJit;
+    js.dprog.jit_kernel = kernel;
+    js.dprog.jit_log2_items = shape.log2_items;
+    js.dprog.jit_smem = shape.smem;
+    slots.push_back(std::move(js));
+    *out = (int)slots.size() - 1;
+    return QTN_OK;
   }
 
   // Autotuner: times every eligible throughput candidate for (prec, nx) on
@@ -462,6 +519,39 @@ struct qtn_plan {
       if (best < 0 || ms_min < best_ms) {
         best = si;
         best_ms = ms_min;
+      }
+    }
+    // The fastest interpreted level executors, if slow enough to matter, also
+    // run as kernels generated for this program (jit.hpp); timed alike.
+    if (best >= 0 && best_ms >= kJitMinMs && jit_suffix(arith_of(prec)) && jit_available(nullptr)) {
+      std::vector<int> lv;
+      for (int si = 1; si < (int)slots.size() && si < (int)times.size(); ++si)
+        if (slots[si].exec == Executor::Level && times[si] >= 0) lv.push_back(si);
+      std::sort(lv.begin(), lv.end(), [&](int x, int y) { return times[x] < times[y]; });
+      if ((int)lv.size() > kJitCandidates) lv.resize(kJitCandidates);
+      for (int base : lv) {
+        int si = -1;
+        if (make_jit_slot(base, arith_of(prec), &si) != QTN_OK) continue;
+        times.resize(slots.size(), -1.0);
+        ExecShape sh;
+        if (prepare(si, prec, nx, slots[si].items(), &sh) != QTN_OK) continue;
+        float ms_min = 1e30f;
+        for (int rep = 0; rep < 4; ++rep) {
+          QTN_CUDA(cudaEventRecord(a, stream));
+          cudaError_t le = launch_contraction(slots[si].dprog, arith_of(prec), d_x_stage, nx, 0, slots[si].items(),
+                                              buffers(), sh, scale(), d_out_stage, nullptr, nullptr, stream);
+          if (le != cudaSuccess) return cuda_fail(le, "launch_contraction (tuning)");
+          QTN_CUDA(cudaEventRecord(b, stream));
+          QTN_CUDA(cudaEventSynchronize(b));
+          float ms = 0;
+          QTN_CUDA(cudaEventElapsedTime(&ms, a, b));
+          if (rep > 0) ms_min = std::min(ms_min, ms);
+        }
+        times[si] = ms_min;
+        if (ms_min < best_ms) {
+          best = si;
+          best_ms = ms_min;
+        }
       }
     }
     cudaEventDestroy(a);
@@ -858,8 +948,23 @@ qtn_status qtn_plan_select_executor(const qtn_plan_t* cplan, qtn_precision prec,
   qtn_plan_t* plan = const_cast<qtn_plan_t*>(cplan);
   if (!plan || !name || nx <= 0) return fail(QTN_ERR_INVALID_ARG, "bad argument");
   std::lock_guard<std::mutex> lk(plan->mu);
+  std::string want = name;
+  // "<level program>/jit": that program's specialised executor for prec.
+  if (want.size() > 4 && want.compare(want.size() - 4, 4, "/jit") == 0) {
+    const std::string base = want.substr(0, want.size() - 4);
+    int bi = -1, si = -1;
+    for (int k = 1; k < (int)plan->slots.size(); ++k)
+      if (plan->slots[k].name == base) bi = k;
+    if (bi < 0) return fail(QTN_ERR_INVALID_ARG, std::string("no executor named ") + base);
+    if (!plan->eligible(bi, prec)) return fail(QTN_ERR_INVALID_ARG, "executor not available for this precision");
+    qtn_status st = plan->ensure_device();
+    if (st != QTN_OK) return st;
+    st = plan->make_jit_slot(bi, arith_of(prec), &si);
+    if (st != QTN_OK) return st;
+    want = plan->slots[si].name;
+  }
   for (int si = 1; si < (int)plan->slots.size(); ++si)
-    if (plan->slots[si].name == name) {
+    if (plan->slots[si].name == want) {
       if (!plan->eligible(si, prec)) return fail(QTN_ERR_INVALID_ARG, "executor not available for this precision");
       auto key = std::make_pair((int)prec, nx);
       plan->tuned[key] = si;
@@ -1386,6 +1491,7 @@ qtn_status qtn_plan_describe(const qtn_plan_t* plan, char* buf, size_t cap, size
       << (plan->slots[which].exec == Executor::Lane    ? "lane"
           : plan->slots[which].exec == Executor::Warp  ? "warp"
           : plan->slots[which].exec == Executor::Level ? "level"
+          : plan->slots[which].exec == Executor::LevelJit ? "level-jit"
                                                        : "block")
       << "\",\"outer_class\":";
     json_ints(o, pg.outer_class.data(), pg.outer_class.size());

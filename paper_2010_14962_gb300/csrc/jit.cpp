@@ -1,0 +1,355 @@
+// Per-plan specialised level executor: source generation, run-time
+// compilation (NVRTC, loaded with dlopen so that the library builds and runs
+// without it) and launch.  The generated kernel computes exactly what
+// level_exec_kernel computes for the same program and launch shape: the same
+// merges (canonical C[m, n, b] = sum_k A[m, k, b] B[k, n, b], Eq. 1) in the
+// same level order with the same units per thread, the same store
+// permutation, the same root split and the same compensated FP64 sums; only
+// the interpretation (merge lookup, field decode, leaf sub-block loops, store
+// offset tables) is resolved when the source is generated.
+#include "jit.hpp"
+
+#include <dlfcn.h>
+#include <nvrtc.h>
+
+#include <algorithm>
+#include <mutex>
+#include <sstream>
+#include <vector>
+
+namespace qtn {
+namespace {
+
+const char* kArithSource =
+#include "arith_src.inc"
+    ;
+
+// ------------------------------------------------------------------ NVRTC --
+
+struct Nvrtc {
+  bool tried = false, ok = false;
+  std::string why;
+  decltype(&nvrtcCreateProgram) create = nullptr;
+  decltype(&nvrtcCompileProgram) compile = nullptr;
+  decltype(&nvrtcGetCUBINSize) cubin_size = nullptr;
+  decltype(&nvrtcGetCUBIN) cubin = nullptr;
+  decltype(&nvrtcGetProgramLogSize) log_size = nullptr;
+  decltype(&nvrtcGetProgramLog) log = nullptr;
+  decltype(&nvrtcDestroyProgram) destroy = nullptr;
+};
+Nvrtc g_nvrtc;
+std::mutex g_nvrtc_mu;
+
+Nvrtc& nvrtc() {
+  std::lock_guard<std::mutex> lk(g_nvrtc_mu);
+  if (g_nvrtc.tried) return g_nvrtc;
+  g_nvrtc.tried = true;
+  void* h = nullptr;
+  for (const char* name : {"libnvrtc.so.13", "libnvrtc.so", "/usr/local/cuda/lib64/libnvrtc.so.13",
+                           "/usr/local/cuda/lib64/libnvrtc.so"}) {
+    h = dlopen(name, RTLD_NOW | RTLD_LOCAL);
+    if (h) break;
+  }
+  if (!h) {
+    g_nvrtc.why = "libnvrtc not found";
+    return g_nvrtc;
+  }
+  auto sym = [&](const char* s) { return dlsym(h, s); };
+  g_nvrtc.create = reinterpret_cast<decltype(&nvrtcCreateProgram)>(sym("nvrtcCreateProgram"));
+  g_nvrtc.compile = reinterpret_cast<decltype(&nvrtcCompileProgram)>(sym("nvrtcCompileProgram"));
+  g_nvrtc.cubin_size = reinterpret_cast<decltype(&nvrtcGetCUBINSize)>(sym("nvrtcGetCUBINSize"));
+  g_nvrtc.cubin = reinterpret_cast<decltype(&nvrtcGetCUBIN)>(sym("nvrtcGetCUBIN"));
+  g_nvrtc.log_size = reinterpret_cast<decltype(&nvrtcGetProgramLogSize)>(sym("nvrtcGetProgramLogSize"));
+  g_nvrtc.log = reinterpret_cast<decltype(&nvrtcGetProgramLog)>(sym("nvrtcGetProgramLog"));
+  g_nvrtc.destroy = reinterpret_cast<decltype(&nvrtcDestroyProgram)>(sym("nvrtcDestroyProgram"));
+  g_nvrtc.ok = g_nvrtc.create && g_nvrtc.compile && g_nvrtc.cubin_size && g_nvrtc.cubin && g_nvrtc.log_size &&
+               g_nvrtc.log && g_nvrtc.destroy;
+  if (!g_nvrtc.ok) g_nvrtc.why = "libnvrtc lacks an entry point";
+  return g_nvrtc;
+}
+
+size_t align16(size_t x) { return (x + 15) & ~size_t(15); }
+
+// --------------------------------------------------------------- codegen --
+
+const char* type_name(Arith a) {
+  switch (a) {
+    case Arith::F64: return "double2";
+    case Arith::F32: return "float2";
+    case Arith::F32X2: return "dfc";
+    default: return nullptr;
+  }
+}
+
+// sum_i bit(o, i) * w[i] for bits lo..rc-1 of `var`, as runs of bits whose
+// weights are consecutive powers of two (each run one shift, mask and add).
+std::string pos_expr(const std::string& var, const uint16_t* w, int lo, int rc) {
+  std::ostringstream e;
+  bool first = true;
+  int i = lo;
+  while (i < rc) {
+    int j = i + 1;
+    const bool pow2 = w[i] != 0 && (w[i] & (w[i] - 1)) == 0;
+    if (pow2)
+      while (j < rc && (uint32_t)w[j] == 2u * w[j - 1]) ++j;
+    const uint32_t mask = (1u << (j - i)) - 1u;
+    e << (first ? "" : " + ") << "(((" << var << " >> " << i << ") & " << mask << "u) * " << w[i] << "u)";
+    first = false;
+    i = j;
+  }
+  return first ? std::string("0u") : e.str();
+}
+
+// Pointer to an operand: leaf (sub-block of the item's outer-class values)
+// or a tensor of the item's arena.
+std::string operand(const Program& pg, bool leaf, uint32_t id) {
+  std::ostringstream e;
+  if (!leaf) {
+    e << "(arena + " << id << "u)";
+    return e.str();
+  }
+  const DevLeaf& L = pg.leaves[id];
+  e << "(s_lt + " << L.base << "u";
+  for (int j = 0; j < L.ncut; ++j)
+    e << " + ((unsigned)((s >> " << (int)L.cut_bit[j] << ") & 1ull) << " << (L.rank_nc + j) << ")";
+  e << ")";
+  return e.str();
+}
+
+// One merge's code for output unit o0 (a multiple of its unit size).
+void emit_merge(std::ostringstream& o, const Program& pg, const DevStep& st, uint32_t beg, int ulog, int ks) {
+  const int ma = st.ma, nb = st.nb, kb = st.kb, bb = st.bb;
+  const int rc = ma + nb + bb;
+  const bool root = st.flags & STEP_ROOT;
+  const uint32_t u = 1u << ulog;
+  o << "      const V* __restrict__ A = " << operand(pg, st.flags & STEP_A_LEAF, st.a) << ";\n";
+  o << "      const V* __restrict__ B = " << operand(pg, st.flags & STEP_B_LEAF, st.b) << ";\n";
+  o << "      const unsigned e0 = (uf - " << beg << "u) << " << ulog << ";\n";
+  if (!root) {
+    o << "      V* __restrict__ C = arena + " << st.c << "u;\n";
+    o << "      const unsigned p0 = " << pos_expr("e0", st.w, ulog, rc) << ";\n";
+  }
+  const uint32_t kpart = 1u << (kb - ks);
+  for (uint32_t r = 0; r < u; ++r) {
+    o << "      {\n";
+    if (root) {
+      o << "        const unsigned e = e0 + " << r << "u;\n";
+      o << "        const unsigned oo = e >> " << ks << ", k0 = (e & " << ((1u << ks) - 1u) << "u) * " << kpart
+        << "u;\n";
+    } else {
+      o << "        const unsigned oo = e0 + " << r << "u, k0 = 0u;\n";
+    }
+    o << "        const unsigned m = oo & " << ((1u << ma) - 1u) << "u, n = (oo >> " << ma << ") & "
+      << ((1u << nb) - 1u) << "u, b = oo >> " << (ma + nb) << ";\n";
+    o << "        const V* __restrict__ ap = A + m + (k0 << " << ma << ") + (b << " << (ma + kb) << ");\n";
+    o << "        const V* __restrict__ bp = B + k0 + (n << " << kb << ") + (b << " << (kb + nb) << ");\n";
+    o << "        V acc = Ops::mul(ap[0], bp[0]);\n";
+    for (uint32_t k = 1; k < kpart; ++k)
+      o << "        Ops::fma(acc, ap[" << (k << ma) << "], bp[" << k << "]);\n";
+    o << "        Ops::finish(acc);\n";
+    if (root) {
+      o << "        kahan_add(sr, cr, Ops::re(acc));\n        kahan_add(si, ci, Ops::im(acc));\n";
+    } else {
+      uint32_t add = 0;
+      for (int bit = 0; bit < ulog; ++bit)
+        if ((r >> bit) & 1u) add += st.w[bit];
+      o << "        C[p0 + " << add << "u] = acc;\n";
+    }
+    o << "      }\n";
+  }
+}
+
+// Binary dispatch over the merges [lo, hi) of a level by unit index uf.
+void emit_dispatch(std::ostringstream& o, const Program& pg, const std::vector<int>& js,
+                   const std::vector<uint32_t>& beg, const std::vector<int>& ulog, const std::vector<int>& ks, int lo,
+                   int hi, int depth) {
+  if (hi - lo == 1) {
+    o << "    {  // merge " << js[lo] << "\n";
+    emit_merge(o, pg, pg.steps[js[lo]], beg[lo], ulog[lo], ks[lo]);
+    o << "    }\n";
+    return;
+  }
+  const int mid = (lo + hi) / 2;
+  o << "    if (uf < " << beg[mid] << "u) {\n";
+  emit_dispatch(o, pg, js, beg, ulog, ks, lo, mid, depth + 1);
+  o << "    } else {\n";
+  emit_dispatch(o, pg, js, beg, ulog, ks, mid, hi, depth + 1);
+  o << "    }\n";
+}
+
+}  // namespace
+
+bool jit_available(std::string* why) {
+  Nvrtc& n = nvrtc();
+  if (!n.ok && why) *why = n.why;
+  return n.ok;
+}
+
+bool jit_level_shape(const Program& pg, int elem_bytes, int threads, int blocks_per_sm, JitLevelShape* out) {
+  int dev = 0, max_optin = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  const int bps = blocks_per_sm > 1 ? blocks_per_sm : 1;
+  const size_t cap = std::min<size_t>((size_t)max_optin, (size_t)per_sm / bps - 1024);
+  JitLevelShape sh;
+  sh.threads = threads;
+  sh.blocks_per_sm = bps;
+  sh.arena_stride = pg.arena_elems | 1u;
+  const size_t table = align16((size_t)pg.leaf_elems * elem_bytes);
+  for (int lg = 5; lg >= 0; --lg) {
+    const size_t arena = (size_t)sh.arena_stride * ((size_t)1 << lg) * elem_bytes;
+    const size_t red = (size_t)threads * 32;  // one Partial per thread, overlaid on the arenas
+    const size_t total = table + align16(std::max(arena, red));
+    if (total <= cap) {
+      sh.log2_items = lg;
+      sh.smem = total;
+      *out = sh;
+      return true;
+    }
+  }
+  return false;
+}
+
+std::string jit_level_source(const Program& pg, Arith a, const JitLevelShape& sh, std::string* err) {
+  const char* vt = type_name(a);
+  if (!vt) {
+    *err = "no specialised executor for this arithmetic";
+    return "";
+  }
+  if (pg.levels.empty()) {
+    *err = "not a level program";
+    return "";
+  }
+  for (const DevStep& st : pg.steps)
+    if (st.flags & STEP_EXPORT) {
+      *err = "item steps export";
+      return "";
+    }
+  const int elem = arith_elem_bytes(a);
+  const int UL = elem == 16 ? 0 : kLevelUnitLog2;
+  const int US = UL ? 1 : 0;
+  const uint32_t I = 1u << sh.log2_items;
+  const size_t table = align16((size_t)pg.leaf_elems * elem);
+  std::ostringstream o;
+  o << "// Generated: specialised level executor (" << pg.steps.size() << " merges, " << pg.levels.size()
+    << " levels).\n";
+  o << "struct __align__(16) Partial {\n  double re, im, cre, cim;\n"
+       "  static __device__ __forceinline__ Partial make(double a, double b, double c, double d) {\n"
+       "    Partial p; p.re = a; p.im = b; p.cre = c; p.cim = d; return p;\n  }\n};\n";
+  o << kArithSource << "\n";
+  o << "typedef " << vt << " V;\ntypedef CplxOps<V> Ops;\n";
+  o << "extern \"C\" __global__ void __launch_bounds__(" << sh.threads << ", " << sh.blocks_per_sm
+    << ") qtn_level_jit(const V* __restrict__ leaf_tables, Partial* __restrict__ partials,\n"
+       "    unsigned long long slice_lo, unsigned long long slice_hi, int blocks_per_x) {\n";
+  o << "  extern __shared__ __align__(16) unsigned char smem[];\n";
+  o << "  V* s_lt = reinterpret_cast<V*>(smem);\n";
+  o << "  V* s_arena = reinterpret_cast<V*>(smem + " << table << ");\n";
+  o << "  Partial* s_red = reinterpret_cast<Partial*>(smem + " << table << ");\n";
+  o << "  const int xi = blockIdx.x / blocks_per_x, bx = blockIdx.x % blocks_per_x;\n";
+  o << "  {\n    const unsigned* src = reinterpret_cast<const unsigned*>(leaf_tables + (size_t)xi * "
+    << pg.leaf_elems << "u);\n    unsigned* dst = reinterpret_cast<unsigned*>(s_lt);\n"
+    << "    for (unsigned i = threadIdx.x; i < " << (size_t)pg.leaf_elems * elem / 4 << "u; i += " << sh.threads
+    << "u) dst[i] = src[i];\n  }\n  __syncthreads();\n";
+  o << "  double sr = 0.0, si = 0.0, cr = 0.0, ci = 0.0;\n";
+  o << "  const unsigned long long S = slice_hi - slice_lo;\n";
+  o << "  for (unsigned long long i0 = (unsigned long long)bx * " << I << "ull; i0 < S; i0 += (unsigned long long)"
+    << "blocks_per_x * " << I << "ull) {\n";
+  o << "    const unsigned nI = (S - i0) < " << I << "ull ? (unsigned)(S - i0) : " << I << "u;\n";
+  o << "    const unsigned long long s0 = slice_lo + i0;\n";
+  for (size_t l = 0; l < pg.levels.size(); ++l) {
+    const DevLevel& lv = pg.levels[l];
+    std::vector<int> js;
+    std::vector<uint32_t> beg;
+    std::vector<int> ulog, ks;
+    for (int j = lv.first; j < lv.first + lv.count; ++j) {
+      const DevStep& st = pg.steps[j];
+      const int k_s = UL ? ((st.flags & STEP_ROOT) ? std::min<int>(st.kb, kRootSplitLog2) : 0) : 0;
+      const int rc = st.ma + st.nb + st.bb + k_s;
+      js.push_back(j);
+      beg.push_back(pg.out_start[2 * j + US]);
+      ulog.push_back(std::min(rc, UL));
+      ks.push_back(k_s);
+    }
+    const uint64_t total = (uint64_t)lv.units[US] << sh.log2_items;
+    o << "    // level " << l << "\n";
+    o << "    for (unsigned f = threadIdx.x; f < " << total << "u; f += " << sh.threads << "u) {\n";
+    o << "      const unsigned item = f & " << (I - 1) << "u, uf = f >> " << sh.log2_items << ";\n";
+    o << "      if (item >= nI) continue;\n";
+    bool leaf_operand = false;
+    for (int j : js) leaf_operand |= (pg.steps[j].flags & (STEP_A_LEAF | STEP_B_LEAF)) != 0;
+    if (leaf_operand) o << "      const unsigned long long s = s0 + item;\n";
+    o << "      V* arena = s_arena + item * " << sh.arena_stride << "u;\n";
+    emit_dispatch(o, pg, js, beg, ulog, ks, 0, (int)js.size(), 0);
+    o << "    }\n    __syncthreads();\n";
+  }
+  o << "  }\n";
+  o << "  s_red[threadIdx.x] = Partial::make(sr, si, cr, ci);\n";
+  o << "  tree_reduce(s_red, " << sh.threads << ");\n";
+  o << "  if (threadIdx.x == 0) partials[(size_t)xi * blocks_per_x + bx] = s_red[0];\n}\n";
+  return o.str();
+}
+
+bool jit_compile(const std::string& src, size_t smem, const void** kernel, std::string* err) {
+  Nvrtc& n = nvrtc();
+  if (!n.ok) {
+    *err = n.why;
+    return false;
+  }
+  int dev = 0, major = 0, minor = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  const std::string arch = "-arch=sm_" + std::to_string(major * 10 + minor) + (major >= 9 ? "a" : "");
+  nvrtcProgram prog;
+  if (n.create(&prog, src.c_str(), "qtn_level_jit.cu", 0, nullptr, nullptr) != NVRTC_SUCCESS) {
+    *err = "nvrtcCreateProgram failed";
+    return false;
+  }
+  const char* opts[] = {arch.c_str(), "-std=c++17", "-default-device"};
+  const nvrtcResult rc = n.compile(prog, 3, opts);
+  if (rc != NVRTC_SUCCESS) {
+    size_t ls = 0;
+    n.log_size(prog, &ls);
+    std::string log(ls, '\0');
+    n.log(prog, &log[0]);
+    *err = "nvrtc: " + log.substr(0, 2000);
+    n.destroy(&prog);
+    return false;
+  }
+  size_t cs = 0;
+  n.cubin_size(prog, &cs);
+  std::vector<char> cubin(cs);
+  n.cubin(prog, cubin.data());
+  n.destroy(&prog);
+  cudaLibrary_t lib;
+  cudaError_t e = cudaLibraryLoadData(&lib, cubin.data(), nullptr, nullptr, 0, nullptr, nullptr, 0);
+  if (e != cudaSuccess) {
+    *err = std::string("cudaLibraryLoadData: ") + cudaGetErrorString(e);
+    return false;
+  }
+  cudaKernel_t k;
+  e = cudaLibraryGetKernel(&k, lib, "qtn_level_jit");
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(reinterpret_cast<const void*>(k), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+  if (e != cudaSuccess) {
+    *err = std::string("loading the specialised kernel: ") + cudaGetErrorString(e);
+    return false;
+  }
+  *kernel = reinterpret_cast<const void*>(k);  // the library stays loaded for the process
+  return true;
+}
+
+cudaError_t jit_level_launch(const void* kernel, const JitLevelShape& sh, int nx, int blocks_per_x,
+                             const void* leaf_tables, Partial* partials, uint64_t slice_lo, uint64_t slice_hi,
+                             cudaStream_t stream) {
+  const void* lt = leaf_tables;
+  unsigned long long lo = slice_lo, hi = slice_hi;
+  int bpx = blocks_per_x;
+  void* args[] = {const_cast<void*>(static_cast<const void*>(&lt)), &partials, &lo, &hi, &bpx};
+  return cudaLaunchKernel(kernel, dim3((unsigned)blocks_per_x * (unsigned)nx), dim3((unsigned)sh.threads), args,
+                          sh.smem, stream);
+}
+
+}  // namespace qtn

@@ -23,6 +23,8 @@
 
 #include <cuda_bf16.h>
 
+#include "jit.hpp"
+
 #include <algorithm>
 #include <type_traits>
 
@@ -42,118 +44,7 @@ struct ExecParams {
   int blocks_per_x;  // blocks per bit string; blockIdx.x = xi * blocks_per_x + b
 };
 
-template <class V>
-struct CplxOps;
-template <>
-struct CplxOps<float2> {
-  using R = float;
-  static __device__ __forceinline__ float2 zero() { return make_float2(0.f, 0.f); }
-  static __device__ __forceinline__ void fma(float2& acc, float2 a, float2 b) {
-    acc.x = fmaf(a.x, b.x, acc.x);
-    acc.x = fmaf(-a.y, b.y, acc.x);
-    acc.y = fmaf(a.x, b.y, acc.y);
-    acc.y = fmaf(a.y, b.x, acc.y);
-  }
-  static __device__ __forceinline__ float2 mul(float2 a, float2 b) {
-    float2 r = zero();
-    fma(r, a, b);
-    return r;
-  }
-  static __device__ __forceinline__ void finish(float2&) {}
-  static __device__ __forceinline__ float2 from(double re, double im) {
-    return make_float2((float)re, (float)im);
-  }
-  static __device__ __forceinline__ double re(float2 v) { return (double)v.x; }
-  static __device__ __forceinline__ double im(float2 v) { return (double)v.y; }
-};
-template <>
-struct CplxOps<double2> {
-  using R = double;
-  static __device__ __forceinline__ double2 zero() { return make_double2(0.0, 0.0); }
-  static __device__ __forceinline__ void fma(double2& acc, double2 a, double2 b) {
-    acc.x = ::fma(a.x, b.x, acc.x);
-    acc.x = ::fma(-a.y, b.y, acc.x);
-    acc.y = ::fma(a.x, b.y, acc.y);
-    acc.y = ::fma(a.y, b.x, acc.y);
-  }
-  static __device__ __forceinline__ double2 mul(double2 a, double2 b) {
-    double2 r = zero();
-    fma(r, a, b);
-    return r;
-  }
-  static __device__ __forceinline__ void finish(double2&) {}
-  static __device__ __forceinline__ double2 from(double re, double im) { return make_double2(re, im); }
-  static __device__ __forceinline__ double re(double2 v) { return v.x; }
-  static __device__ __forceinline__ double im(double2 v) { return v.y; }
-};
-
-// ---------------------------------------------------- double-float (FP32X2) --
-
-// A complex number as two double-word floats (value = hi + lo per part).
-struct dfc {
-  float rh, rl, ih, il;
-};
-
-// Error-free transform TwoSum (Knuth: s + e = a + b exactly).  The _rn
-// intrinsics keep the compiler from contracting them into FMAs, which would
-// break exactness.
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
-  const float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-// Double-word product (xh + xl)(yh + yl) as ph + pl: ph = fl(xh yh), and pl
-// = its exact rounding error (FMA) plus the cross terms (the xl yl term is
-// below the format's precision).
-__device__ __forceinline__ void dw_prod(float xh, float xl, float yh, float yl, float& ph, float& pl) {
-  ph = __fmul_rn(xh, yh);
-  pl = __fmaf_rn(xh, yh, -ph);
-  pl = __fmaf_rn(xh, yl, pl);
-  pl = __fmaf_rn(xl, yh, pl);
-}
-// (ah, al) += x * y with lazy normalisation: ah takes the TwoSum of the
-// product's high part, al collects that sum's exact error and the product's
-// low part in plain FP32 (a second-order quantity, so its own roundings stay
-// below the double-word precision); finish() renormalises once per output
-// instead of once per product.
-__device__ __forceinline__ void dw_fma_lazy(float& ah, float& al, float xh, float xl, float yh, float yl) {
-  float ph, pl, sh, e;
-  dw_prod(xh, xl, yh, yl, ph, pl);
-  two_sum(ah, ph, sh, e);
-  ah = sh;
-  al = __fadd_rn(al, __fadd_rn(e, pl));
-}
-
-template <>
-struct CplxOps<dfc> {
-  static __device__ __forceinline__ dfc zero() { return dfc{0.f, 0.f, 0.f, 0.f}; }
-  static __device__ __forceinline__ void fma(dfc& acc, dfc a, dfc b) {
-    dw_fma_lazy(acc.rh, acc.rl, a.rh, a.rl, b.rh, b.rl);
-    dw_fma_lazy(acc.rh, acc.rl, -a.ih, -a.il, b.ih, b.il);
-    dw_fma_lazy(acc.ih, acc.il, a.rh, a.rl, b.ih, b.il);
-    dw_fma_lazy(acc.ih, acc.il, a.ih, a.il, b.rh, b.rl);
-  }
-  // a * b: the first product of each part needs no sum.
-  static __device__ __forceinline__ dfc mul(dfc a, dfc b) {
-    dfc r;
-    dw_prod(a.rh, a.rl, b.rh, b.rl, r.rh, r.rl);
-    dw_fma_lazy(r.rh, r.rl, -a.ih, -a.il, b.ih, b.il);
-    dw_prod(a.rh, a.rl, b.ih, b.il, r.ih, r.il);
-    dw_fma_lazy(r.ih, r.il, a.ih, a.il, b.rh, b.rl);
-    return r;
-  }
-  // Renormalise each part to a double word (|lo| <= ulp(hi) / 2).
-  static __device__ __forceinline__ void finish(dfc& v) {
-    two_sum(v.rh, v.rl, v.rh, v.rl);
-    two_sum(v.ih, v.il, v.ih, v.il);
-  }
-  static __device__ __forceinline__ dfc from(double re, double im) {
-    const float rh = (float)re, ih = (float)im;
-    return dfc{rh, (float)(re - (double)rh), ih, (float)(im - (double)ih)};
-  }
-  static __device__ __forceinline__ double re(dfc v) { return (double)v.rh + (double)v.rl; }
-  static __device__ __forceinline__ double im(dfc v) { return (double)v.ih + (double)v.il; }
-};
+#include "arith.cuh"
 
 // ------------------------------------- tensor-core product numerics (FP32) --
 
@@ -208,38 +99,6 @@ struct RoundOps {
   static __device__ __forceinline__ double re(float2 v) { return (double)v.x; }
   static __device__ __forceinline__ double im(float2 v) { return (double)v.y; }
 };
-
-__device__ __forceinline__ void kahan_add(double& sum, double& comp, double v) {
-  double y = v - comp;
-  double t = sum + y;
-  comp = (t - sum) - y;
-  sum = t;
-}
-
-// Sum of two compensated partials (value = sum - compensation): the sums are
-// added with TwoSum and the rounding error joins the compensations.
-__device__ __forceinline__ double two_sum_d(double a, double b, double& err) {
-  const double s = a + b;
-  const double bb = s - a;
-  err = (a - (s - bb)) + (b - bb);
-  return s;
-}
-__device__ __forceinline__ Partial combine(const Partial& x, const Partial& y) {
-  double er, ei;
-  const double sr = two_sum_d(x.re, y.re, er);
-  const double si = two_sum_d(x.im, y.im, ei);
-  return Partial::make(sr, si, x.cre + y.cre - er, x.cim + y.cim - ei);
-}
-
-// Fixed-order pairwise reduction of `n` partials in shared memory (n a power
-// of two, all threads of the block call it); the result is in red[0].
-__device__ __forceinline__ void tree_reduce(Partial* red, int n) {
-  for (int w = n / 2; w > 0; w >>= 1) {
-    __syncthreads();
-    for (int t = threadIdx.x; t < w; t += blockDim.x) red[t] = combine(red[t], red[t + w]);
-  }
-  __syncthreads();
-}
 
 // Offset of slice s's sub-block inside a leaf: cut legs are the high bits.
 __device__ __forceinline__ uint32_t leaf_offset(const DevLeaf& L, uint64_t s) {
@@ -1334,6 +1193,15 @@ bool exec_shape_typed(const DeviceProgram& prog, int nx, uint64_t slices_per_x, 
     sh.smem = L.total;
     if (!shape_for_kernel(block_exec_kernel<V, true, Ops>, sh.threads, sh.smem, &occ)) return false;
     per_block_items = (uint64_t)(sh.threads / 32);
+  } else if (prog.exec == Executor::LevelJit) {
+    // Shape fixed when the kernel was generated (jit_level_shape).
+    if (!prog.jit_kernel) return false;
+    sh.threads = prog.block_threads;
+    sh.arena_stride = prog.arena_elems | 1u;
+    sh.log2_items = prog.jit_log2_items;
+    sh.smem = prog.jit_smem;
+    occ = prog.blocks_per_sm > 1 ? prog.blocks_per_sm : 1;
+    per_block_items = 1ull << sh.log2_items;
   } else if (prog.exec == Executor::Level) {
     // The most items (power of two, <= 32) whose arenas fit in the block's
     // share of the SM's shared memory (1 KiB per block is the system's).
@@ -1441,6 +1309,16 @@ cudaError_t launch_typed(const DeviceProgram& prog, const uint8_t* d_x, int nx, 
     }
   } else if (prog.exec == Executor::Warp) {
     block_exec_kernel<V, true, Ops><<<grid, shape.threads, shape.smem, stream>>>(P);
+  } else if (prog.exec == Executor::LevelJit) {
+    JitLevelShape js;
+    js.threads = shape.threads;
+    js.blocks_per_sm = prog.blocks_per_sm;
+    js.log2_items = shape.log2_items;
+    js.arena_stride = shape.arena_stride;
+    js.smem = shape.smem;
+    e = jit_level_launch(prog.jit_kernel, js, nx, shape.blocks_per_x, buf.leaf_tables, buf.partials, slice_lo,
+                         slice_hi, stream);
+    if (e != cudaSuccess) return e;
   } else if (prog.exec == Executor::Level) {
     const LevelParams LP{prog.levels, prog.out_start, prog.pos_nib, prog.n_levels, shape.log2_items,
                          shape.arena_stride};

@@ -11,8 +11,10 @@ namespace qtn {
 
 // Lane: one work item per thread; Block: one item per block, a barrier per
 // merge; Warp: one item per warp; Level: 2^log2_items items per block, all
-// merges of one tree level (of all those items) at once, a barrier per level.
-enum class Executor : int { Lane = 0, Block = 1, Warp = 2, Level = 3 };
+// merges of one tree level (of all those items) at once, a barrier per level;
+// LevelJit: the same as Level, run by a kernel generated for the program
+// (jit.hpp) instead of the interpreter.
+enum class Executor : int { Lane = 0, Block = 1, Warp = 2, Level = 3, LevelJit = 4 };
 
 // Arithmetic of the merges: complex128, complex64, double-float complex64
 // (FP32X2), and complex64 storage with products rounded as the tensor cores
@@ -59,6 +61,10 @@ struct DeviceProgram {
   const uint16_t* pro_pos_nib = nullptr;
   int block_threads = 256;  // threads per block (512 or 1024)
   int blocks_per_sm = 1;    // shared memory is sized for this many blocks per SM
+  // LevelJit only: the generated kernel (for one arithmetic) and its shape.
+  const void* jit_kernel = nullptr;
+  int jit_log2_items = 0;
+  size_t jit_smem = 0;
 };
 
 // One launch sequence: leaf tables for nx bit strings, the slice range

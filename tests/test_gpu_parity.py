@@ -317,7 +317,50 @@ def test_precision_draws_n80(gpu, config80, draws80, prec):
     assert errs.max() < 1e-10
 
 
+@pytest.mark.parametrize("base,prec", [("level/fp64/192KiB/t1024", "fp32x2"), ("level/fp64/192KiB/t1024", "fp64"),
+                                       ("level/fp32/48KiB", "fp32")])
+def test_specialised_level_executor_n80(gpu, config80, base, prec):
+    # The kernel generated for this plan's level program (merges as straight
+    # code) against the oracle on the benchmark's 8 bit strings, and against
+    # the interpreted level executor of the same program.
+    inst, plan, xs, refs = config80
+    plan.select_executor(base, prec, len(xs))
+    interp = device_amplitudes(plan, xs, prec)
+    plan.select_executor(base + "/jit", prec, len(xs))
+    got = device_amplitudes(plan, xs, prec)
+    assert plan.describe()["programs"][base + "/jit-" + prec]["executor"] == "level-jit"
+    tol = 2e-5 if prec == "fp32" else 1e-10
+    assert np.max(np.abs(got - refs) / np.abs(refs)) < tol
+    assert np.max(np.abs(got - interp) / np.abs(interp)) < (1e-5 if prec == "fp32" else 1e-12)
+
+
+@pytest.mark.parametrize("n,p,k,seed", [(40, 2, 10, 2), (30, 1, 8, 5)])
+def test_specialised_level_executor_small(gpu, n, p, k, seed):
+    # Generated kernels of every level program of smaller plans (ragged item
+    # counts, several levels per merge shape) against the oracle.
+    inst = I.qaoa_instance(n, p, seed)
+    plan = qtn.Plan(qtn.Network(n, inst.edges, inst.gamma, inst.beta), k=k)
+    xs = I.bitstrings(n, 3, seed)
+    refs = [O.tn_amplitude(n, inst.edges, inst.gamma, inst.beta, x, cuts=plan.cut_names(), threads=8).value
+            for x in xs]
+    names = [nm for nm, pr in plan.describe()["programs"].items() if pr["executor"] == "level"]
+    checked = 0
+    for nm in names:
+        for prec in _executor_precisions(nm):
+            try:
+                plan.select_executor(nm + "/jit", prec, len(xs))
+            except qtn.QTNError:
+                continue
+            got = device_amplitudes(plan, xs, prec)
+            tol = 2e-5 if prec == "fp32" else 1e-10
+            assert np.max(np.abs(got - refs) / np.abs(refs)) < tol, (nm, prec)
+            checked += 1
+    assert checked >= 3
+
+
 def _executor_precisions(name):
+    if "/jit-" in name:  # a generated kernel runs the one arithmetic it was made for
+        return [name.rsplit("/jit-", 1)[1]]
     if "/fp64/" in name:
         return ["fp64", "fp32x2"]
     if "/fp32/" in name:
