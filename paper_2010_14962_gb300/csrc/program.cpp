@@ -35,10 +35,10 @@ Set concat(const Set& a, const Set& b) {
 
 // First-fit allocator over a linear arena of elements.
 struct Arena {
-  std::map<uint32_t, uint32_t> used;  // offset -> size
-  uint32_t high = 0;
-  uint32_t alloc(uint32_t size) {
-    uint32_t at = 0;
+  std::map<uint64_t, uint64_t> used;  // offset -> size
+  uint64_t high = 0;
+  uint64_t alloc(uint64_t size) {
+    uint64_t at = 0;
     for (const auto& [off, sz] : used) {
       if (off >= at + size) break;
       at = std::max(at, off + sz);
@@ -47,7 +47,7 @@ struct Arena {
     high = std::max(high, at + size);
     return at;
   }
-  void release(uint32_t off) { used.erase(off); }
+  void release(uint64_t off) { used.erase(off); }
 };
 
 int find_root(std::vector<int>& parent, int x) {
@@ -166,9 +166,11 @@ std::string compile_program(const Network& net, const Plan& plan_in, const Progr
     c.n = set_minus(B, A);
     Set vC = set_or(set_minus(A, c.k), set_minus(B, c.k));
     full[mg.c] = vC;
-    if ((int)(c.m.size() + c.k.size() + c.b.size()) > kMaxRank ||
-        (int)(c.n.size() + c.k.size() + c.b.size()) > kMaxRank || (int)vC.size() > kMaxRank)
-      return "a tensor of rank > 16 is beyond the on-chip executors";
+    const int max_rank = opt.wide ? kWideMaxRank : kMaxRank;
+    if ((int)(c.m.size() + c.k.size() + c.b.size()) > max_rank ||
+        (int)(c.n.size() + c.k.size() + c.b.size()) > max_rank || (int)vC.size() > max_rank)
+      return opt.wide ? "a tensor of rank > 34 is beyond the wide executor"
+                      : "a tensor of rank > 16 is beyond the on-chip executors";
   }
 
   // Contraction tree, DFS order visiting the needier child first.
@@ -280,6 +282,7 @@ std::string compile_program(const Network& net, const Plan& plan_in, const Progr
       lf.gate = -2;
       lf.rank_nc = (uint8_t)layout[c].size();
       lf.ncut = 0;
+      if ((uint64_t)leaf_off + (1ull << lf.rank_nc) > 0xffffffffull) return "leaf table beyond 2^32 elements";
       leaf_off += 1u << lf.rank_nc;
       leaf_id[c] = (int)pg.leaves.size();
       pg.leaves.push_back(lf);
@@ -319,12 +322,12 @@ std::string compile_program(const Network& net, const Plan& plan_in, const Progr
   if (opt.levels && opt.level_budget > 0) {
     std::vector<int> rem = item_order, bseq;
     Arena sim;
-    std::vector<uint32_t> at(T, 0);
+    std::vector<uint64_t> at(T, 0);
     std::vector<char> avail(T, 0), taken(plan.merges.size(), 0);
     for (int t = 0; t < T; ++t) avail[t] = is_leaf(t) || exported[t];
     int lev = 0;
     while (!rem.empty()) {
-      std::vector<uint32_t> rel;
+      std::vector<uint64_t> rel;
       std::vector<int> outs, keep;
       bool took = false;
       for (size_t q = 0; q < rem.size(); ++q) {
@@ -338,8 +341,8 @@ std::string compile_program(const Network& net, const Plan& plan_in, const Progr
         }
         if (mg.c != root) {
           const Canon& c = canon[j];
-          const uint32_t size = 1u << (c.m.size() + c.n.size() + c.b.size());
-          const uint32_t off = sim.alloc(size);
+          const uint64_t size = 1ull << (c.m.size() + c.n.size() + c.b.size());
+          const uint64_t off = sim.alloc(size);
           if (took && off + size > opt.level_budget) {
             sim.release(off);
             keep.push_back(j);
@@ -354,7 +357,7 @@ std::string compile_program(const Network& net, const Plan& plan_in, const Progr
         if (!(is_leaf(mg.b) || exported[mg.b])) rel.push_back(at[mg.b]);
         outs.push_back(mg.c);
       }
-      for (uint32_t r : rel) sim.release(r);
+      for (uint64_t r : rel) sim.release(r);
       for (int t : outs) avail[t] = 1;
       rem.swap(keep);
       ++lev;
@@ -362,13 +365,13 @@ std::string compile_program(const Network& net, const Plan& plan_in, const Progr
     item_order = bseq;
   }
 
-  std::vector<uint32_t> where(T, 0);
-  auto emit = [&](bool prologue_pass, bool c_reuses_a, std::vector<DevStep>* out, uint32_t* arena_high,
-                  double* macs) -> std::string {
+  std::vector<uint64_t> where(T, 0);
+  auto emit = [&](bool prologue_pass, bool c_reuses_a, std::vector<DevStep>* out, std::vector<WideStep>* wout,
+                  uint64_t* arena_high, double* macs) -> std::string {
     Arena arena;
     const bool by_level = opt.levels;
     const bool bounded = by_level && !prologue_pass && opt.level_budget > 0;
-    std::vector<uint32_t> level_release;  // inputs freed when their level ends
+    std::vector<uint64_t> level_release;  // inputs freed when their level ends
     const std::vector<int>& seq = prologue_pass ? pro_order : item_order;
     auto level_at = [&](size_t si) { return bounded ? item_level[si] : level_of[seq[si]]; };
     for (size_t si = 0; si < seq.size(); ++si) {
@@ -377,27 +380,30 @@ std::string compile_program(const Network& net, const Plan& plan_in, const Progr
       const Merge& mg = plan.merges[j];
       const Canon& c = canon[j];
       DevStep st{};
+      WideStep ws{};
       st.ma = (uint8_t)c.m.size();
       st.nb = (uint8_t)c.n.size();
       st.kb = (uint8_t)c.k.size();
       st.bb = (uint8_t)c.b.size();
-      std::vector<uint32_t> to_release;
+      std::vector<uint64_t> to_release;
       int64_t a_block = -1;
       auto as_leaf = [&](int t) { return is_leaf(t) || (!prologue_pass && exported[t]); };
       if (as_leaf(mg.a)) {
         st.flags |= STEP_A_LEAF;
-        st.a = (uint32_t)leaf_id[mg.a];
+        ws.a = (uint64_t)leaf_id[mg.a];
       } else {
-        st.a = where[mg.a];
-        a_block = where[mg.a];
+        ws.a = where[mg.a];
+        a_block = (int64_t)where[mg.a];
       }
       if (as_leaf(mg.b)) {
         st.flags |= STEP_B_LEAF;
-        st.b = (uint32_t)leaf_id[mg.b];
+        ws.b = (uint64_t)leaf_id[mg.b];
       } else {
-        st.b = where[mg.b];
+        ws.b = where[mg.b];
         to_release.push_back(where[mg.b]);
       }
+      st.a = (uint32_t)ws.a;
+      st.b = (uint32_t)ws.b;
       const int rc = (int)(c.m.size() + c.n.size() + c.b.size());
       const int wd = rc + (int)c.k.size();
       pg.width = std::max(pg.width, wd);
@@ -407,8 +413,8 @@ std::string compile_program(const Network& net, const Plan& plan_in, const Progr
       // while C is written, so only A's block may be reused by C.  Within a
       // level nothing is reused: its merges run at the same time.
       if (a_block >= 0) {
-        if (c_reuses_a && !by_level) arena.release((uint32_t)a_block);
-        else to_release.push_back((uint32_t)a_block);
+        if (c_reuses_a && !by_level) arena.release((uint64_t)a_block);
+        else to_release.push_back((uint64_t)a_block);
       }
       const Set canon_ix = concat(concat(c.m, c.n), c.b);
       if (mg.c == root) {
@@ -421,37 +427,56 @@ std::string compile_program(const Network& net, const Plan& plan_in, const Progr
       } else {
         if (prologue_pass && exported[mg.c]) {
           st.flags |= STEP_EXPORT;
-          st.c = (uint32_t)leaf_id[mg.c];
+          ws.c = (uint64_t)leaf_id[mg.c];
         } else {
-          uint32_t off = arena.alloc(1u << rc);
+          const uint64_t off = arena.alloc(1ull << rc);
           where[mg.c] = off;
-          st.c = off;
+          ws.c = off;
         }
+        st.c = (uint32_t)ws.c;
         const Set& lay = layout[mg.c];
         for (int b = 0; b < rc; ++b) {
           auto it = std::find(lay.begin(), lay.end(), canon_ix[b]);
           if (it == lay.end()) return "consumer layout misses an index";
-          st.w[b] = (uint16_t)(1u << (it - lay.begin()));
+          ws.wpos[b] = (uint8_t)(it - lay.begin());
+          if (!opt.wide) st.w[b] = (uint16_t)(1u << (it - lay.begin()));
         }
       }
       if (by_level) {
         level_release.insert(level_release.end(), to_release.begin(), to_release.end());
         const bool level_ends = si + 1 == seq.size() || level_at(si + 1) != level_at(si);
         if (level_ends) {
-          for (uint32_t r : level_release) arena.release(r);
+          for (uint64_t r : level_release) arena.release(r);
           level_release.clear();
         }
       } else {
-        for (uint32_t r : to_release) arena.release(r);
+        for (uint64_t r : to_release) arena.release(r);
       }
-      out->push_back(st);
+      ws.ma = st.ma;
+      ws.nb = st.nb;
+      ws.kb = st.kb;
+      ws.bb = st.bb;
+      ws.flags = st.flags;
+      if (opt.wide) wout->push_back(ws);
+      else out->push_back(st);
     }
-    *arena_high = std::max<uint32_t>(arena.high, 1);
+    *arena_high = std::max<uint64_t>(arena.high, 1);
     return "";
   };
-  std::string err = emit(true, false, &pg.prologue, &pg.pro_arena_elems, &pg.macs_prologue);
-  if (err.empty()) err = emit(false, opt.c_reuses_a, &pg.steps, &pg.arena_elems, &pg.macs_per_item);
+  uint64_t pro_high = 0, item_high = 0;
+  std::string err = emit(true, false, &pg.prologue, &pg.wide_prologue, &pro_high, &pg.macs_prologue);
+  if (err.empty())
+    err = emit(false, opt.c_reuses_a, &pg.steps, &pg.wide_steps, &item_high, &pg.macs_per_item);
   if (!err.empty()) return err;
+  if (opt.wide) {
+    if (opt.levels) return "wide programs have no levels";
+    pg.wide_arena_elems = item_high;
+    pg.wide_pro_arena_elems = pg.wide_prologue.empty() ? 0 : pro_high;
+  } else {
+    if (item_high > 0xffffffffull || pro_high > 0xffffffffull) return "arena beyond 2^32 elements";
+    pg.arena_elems = (uint32_t)item_high;
+    pg.pro_arena_elems = (uint32_t)pro_high;
+  }
   if (pg.prologue.empty()) pg.pro_arena_elems = 0;
   if (opt.levels) {
     // Level of emitted step i: its depth, or its bounded level.

@@ -99,6 +99,17 @@ struct DevLevel {
 };
 static_assert(sizeof(DevLevel) == 12, "DevLevel layout");
 
+// One merge of a wide program (intermediates in global memory, ranks up to
+// kWideMaxRank): the same canonical form as DevStep, with 64-bit arena
+// offsets and, per canonical output bit, its bit position in the consumer's
+// layout (the store weight is 1 << wpos).
+constexpr int kWideMaxRank = 34;
+struct WideStep {
+  uint8_t ma, nb, kb, bb, flags;
+  uint64_t a, b, c;  // leaf id or arena element offset (c: leaf id when exported)
+  uint8_t wpos[kWideMaxRank];
+};
+
 struct ProgramOptions {
   bool levels = false;            // order item steps by tree level (see above)
   // With levels: 0 = levels by depth (fewest barriers); else the item steps
@@ -109,6 +120,9 @@ struct ProgramOptions {
   bool hoist = true;              // run outer-class-invariant merges once per bit string
   std::vector<int> cut_class;     // class of each cut (size k); empty = one class per cut
   std::vector<char> inner;        // per class: carried as a batch index
+  // Wide program: tensors up to kWideMaxRank in a global-memory arena;
+  // emits wide_steps / wide_prologue instead of steps / prologue.
+  bool wide = false;
 };
 
 struct Program {
@@ -130,6 +144,8 @@ struct Program {
   // step's bit weights), so pos(o) = sum_g entry[16 g + nibble_g(o)].
   std::vector<uint16_t> pos_nib, pro_pos_nib;
   std::vector<DevStep> prologue;     // once per bit string: merges that no outer class reaches
+  std::vector<WideStep> wide_steps, wide_prologue;  // wide programs only
+  uint64_t wide_arena_elems = 0, wide_pro_arena_elems = 0;
   uint32_t pro_arena_elems = 0;      // prologue arena (elements)
   double macs_prologue = 0;          // per bit string
   uint32_t leaf_elems = 0;           // elements in one leaf table
