@@ -56,17 +56,18 @@ typedef enum {
 
 /* Arithmetic of the elimination steps.  Gate phases (sincos of gamma, beta)
  * and the sum over slices are FP64 in every mode (Kahan-compensated).
- * TF32 .. BF16X6 reproduce the products tensor cores form (operands rounded
- * or split as stated, products accumulated in FP32); they run on the FP32
- * pipes of the batched executors, to measure what each format costs in
- * accuracy on this workload. */
+ * TF32 .. BF16X6 round or split the operands as stated and accumulate in
+ * FP32.  On the on-chip executors they are emulated on the FP32 pipe (the
+ * products tensor cores would form); on the wide executor, TF32 and TF32X3
+ * merges whose shape allows it run on the tensor cores themselves (tcgen05,
+ * FP32 accumulation in tensor memory, see qtn_wide_set_kernel). */
 typedef enum {
   QTN_FP64 = 0,   /* complex128 contractions (the plain FP64 GPU form) */
   QTN_FP32 = 1,   /* complex64 contractions, FP32 FMA */
-  QTN_TF32 = 2,   /* operands rounded to TF32, FP32 accumulate */
-  QTN_BF16X3 = 3, /* split-BF16 (hi*hi + hi*lo + lo*hi), FP32 accumulate */
-  QTN_TF32X3 = 4, /* split-TF32, 3 products, FP32 accumulate */
-  QTN_BF16X6 = 5, /* 3-way split BF16, 6 products, FP32 accumulate */
+  QTN_TF32 = 2,   /* operands rounded to TF32, FP32 accumulate (tensor cores on wide merges) */
+  QTN_BF16X3 = 3, /* split-BF16 (hi*hi + hi*lo + lo*hi), FP32 accumulate (emulated) */
+  QTN_TF32X3 = 4, /* split-TF32, 3 products, FP32 accumulate (tensor cores on wide merges) */
+  QTN_BF16X6 = 5, /* 3-way split BF16, 6 products, FP32 accumulate (emulated) */
   QTN_FP32X2 = 6  /* double-float complex (hi + lo FP32 pairs), ~44-bit */
 } qtn_precision;
 
@@ -321,6 +322,21 @@ qtn_status qtn_plan_select_executor(const qtn_plan_t* plan, qtn_precision prec, 
  * call once its stream has been synchronised. */
 qtn_status qtn_plan_set_kernel_timing(const qtn_plan_t* plan, int on);
 qtn_status qtn_plan_kernel_ms(const qtn_plan_t* plan, float* ms);
+
+/* Process-wide override of the wide executor's kernel per elimination step
+ * (measurement and tests; the paper has no counterpart).  The wide executor
+ * runs plans whose per-slice tensors exceed shared memory with its
+ * intermediates in device memory, one launch per merge (Eq. 1) and group of
+ * slices; an autotuner picks, per merge shape, the SIMT kernel ("simt", one
+ * output per thread; "simt4", four), or the tensor-core kernel ("tcgen05":
+ * complex merges as real TF32 GEMMs with FP32 accumulation in tensor memory,
+ * available to QTN_TF32 and QTN_TF32X3 where one side of the merge has at
+ * least 128 entries, the other at least 8, and at least 4 entries are
+ * summed).  name: "auto" (the default: autotuned), "simt", "simt4" or
+ * "tcgen05" (every step that allows it; the others stay autotuned).  Takes
+ * effect at each wide state's next launch outside stream capture.
+ * QTN_ERR_INVALID_ARG for an unknown name. */
+qtn_status qtn_wide_set_kernel(const char* name);
 
 /* Measured arithmetic peaks of the current device, the denominators of the
  * executors' roofline fractions (measurement support; the paper has no

@@ -16,7 +16,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libqtn.so")
 
 SOURCES = ["network.cpp", "plan.cpp", "program.cpp", "surrogate.cpp", "kernels.cu", "api.cu", "noalloc.cu", "mlp.cu",
-           "peaks.cu", "jit.cpp"]
+           "peaks.cu", "jit.cpp", "wide.cu", "wide_tc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 COMMON = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"), "-I", CSRC, "-I", BUILD]
 

@@ -9,6 +9,7 @@
 #include <cstring>
 #include <initializer_list>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <sstream>
@@ -22,6 +23,7 @@
 #include "internal.hpp"
 #include "jit.hpp"
 #include "kernels.cuh"
+#include "wide.hpp"
 #include "network.hpp"
 #include "plan.hpp"
 #include "program.hpp"
@@ -198,8 +200,18 @@ struct ProgSlot {
   DeviceProgram dprog;
   bool uploaded = false;
   int jit_arith = -1;     // LevelJit: the arithmetic its generated kernel runs
+  // Wide: device state per (arithmetic, bit strings per launch).
+  std::map<std::pair<int, int>, std::shared_ptr<WideState>> wide_states;
   uint64_t items() const { return 1ull << prog.n_outer; }
 };
+
+// Global-memory budget of a wide executor's item arenas: a quarter of the
+// free device memory, at most 32 GiB.
+uint64_t wide_budget_bytes() {
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return 1ull << 30;
+  return std::min<uint64_t>(free_b / 4, 32ull << 30);
+}
 
 // Suffix of a specialised executor's name for an arithmetic.
 const char* jit_suffix(Arith a) {
@@ -419,6 +431,20 @@ struct qtn_plan {
   qtn_status prepare(int si, qtn_precision prec, int nx, uint64_t items, ExecShape* sh) {
     qtn_status st = upload(slots[si]);
     if (st != QTN_OK) return st;
+    if (slots[si].exec == Executor::Wide) {
+      auto& ws = slots[si].wide_states[std::make_pair((int)prec, nx)];
+      if (!ws) {
+        ws = std::make_shared<WideState>();
+        cudaError_t e = wide_prepare(ws.get(), slots[si].prog, arith_of(prec), nx, wide_budget_bytes());
+        if (e != cudaSuccess) {
+          ws.reset();
+          cudaGetLastError();
+          return e == cudaErrorMemoryAllocation ? fail(QTN_ERR_OOM, "wide executor arena: out of device memory")
+                                                : cuda_fail(e, "wide_prepare");
+        }
+      }
+      slots[si].dprog.wide = ws.get();
+    }
     const auto key = std::make_tuple(si, (int)prec, nx, items);
     auto it = shapes.find(key);
     if (it == shapes.end()) {
@@ -434,6 +460,7 @@ struct qtn_plan {
   bool eligible(int si, qtn_precision prec) const {
     const ProgSlot& s = slots[si];
     if (s.exec == Executor::LevelJit) return s.jit_arith == (int)arith_of(prec);
+    if (s.exec == Executor::Wide) return true;
     if (wide(prec) && s.fp32_only) return false;
     if (!wide(prec) && s.fp64_only) return false;
     const bool lane_arith = prec == QTN_FP64 || prec == QTN_FP32 || prec == QTN_FP32X2;
@@ -584,6 +611,18 @@ struct qtn_plan {
     }
     GraphKey key{d_x, d_out, nx, (int)prec, d_gamma, d_beta};
     auto it = graphs.find(key);
+    if (slots[si].exec == Executor::Wide && wide_needs_tuning(slots[si].dprog.wide)) {
+      // The wide executor chooses its per-step kernels on its first launch,
+      // which must not be captured: launch once directly, then capture.
+      if (it != graphs.end()) {
+        cudaGraphExecDestroy(it->second);
+        graphs.erase(it);
+        it = graphs.end();
+      }
+      cudaError_t le = launch_contraction(slots[si].dprog, arith_of(prec), d_x, nx, 0, S, buffers(), sh, scale(),
+                                          d_out, nullptr, nullptr, stream, nullptr, nullptr, d_gamma, d_beta);
+      if (le != cudaSuccess) return cuda_fail(le, "launch_contraction (wide tuning)");
+    }
     if (it == graphs.end()) {
       cudaGraph_t g;
       QTN_CUDA(cudaStreamBeginCapture(capture_stream, cudaStreamCaptureModeThreadLocal));
@@ -774,15 +813,47 @@ qtn_status qtn_plan(const qtn_network_t* net, const int32_t* cuts, int k, const 
   if (!h) return fail(QTN_ERR_OOM, "host allocation failed");
   h->net = net->net;
   std::string err = make_plan(h->net, cutv, ord, &h->plan);
-  // Slot 0: the per-slice program (exact slice numbering, for slice ranges).
-  Program lane_p, block_p;
-  ProgramOptions lane_o, block_o;
-  lane_o.c_reuses_a = true;
-  if (err.empty()) err = compile_program(h->net, h->plan, lane_o, &lane_p);
-  if (err.empty()) err = compile_program(h->net, h->plan, block_o, &block_p);
   if (!err.empty()) {
     delete h;
     return fail(QTN_ERR_INVALID_ARG, err);
+  }
+  // Slot 0: the per-slice program (exact slice numbering, for slice ranges):
+  // on chip if every tensor fits, else the wide (global-memory) program.
+  Program lane_p, block_p;
+  ProgramOptions lane_o, block_o;
+  lane_o.c_reuses_a = true;
+  err = compile_program(h->net, h->plan, lane_o, &lane_p);
+  if (err.empty()) err = compile_program(h->net, h->plan, block_o, &block_p);
+  if (!err.empty()) {
+    ProgramOptions wo;
+    wo.wide = true;
+    ProgSlot s0;
+    s0.name = "wide";
+    s0.exec = Executor::Wide;
+    const std::string werr = compile_program(h->net, h->plan, wo, &s0.prog);
+    if (!werr.empty()) {
+      delete h;
+      return fail(QTN_ERR_INVALID_ARG, werr);
+    }
+    h->slots.push_back(s0);
+    s0.name = "wide/slices";  // the same program as a throughput candidate
+    h->slots.push_back(std::move(s0));
+    int ncls = 0;
+    ProgramOptions co;
+    co.wide = true;
+    co.cut_class = cut_classes(h->net, h->plan.cuts, &ncls);
+    ProgSlot sl;
+    sl.name = "wide/classes";
+    sl.exec = Executor::Wide;
+    if (compile_program(h->net, h->plan, co, &sl.prog).empty()) h->slots.push_back(std::move(sl));
+    h->log2_flops = h->plan.log2_flops_total();
+    h->log2_peak_bytes = std::log2(h->plan.peak_elems * 8.0);
+    if (opts.max_slice_bytes > 0 && h->plan.peak_elems * 8.0 > opts.max_slice_bytes) {
+      delete h;
+      return fail(QTN_ERR_PLAN_EXCEEDS_CAP, "per-slice working set exceeds max_slice_bytes");
+    }
+    *out = h;
+    return QTN_OK;
   }
   // The lane executor's register merges have no batch bits (a graphical-model
   // plan keeps indices shared by three or more tensors as batch bits).
@@ -899,6 +970,16 @@ qtn_status qtn_plan(const qtn_network_t* net, const int32_t* cuts, int k, const 
       if (x.name == "block/classes") seq_arena = x.prog.arena_elems;
     add_level_slots(std::move(sl), o, seq_arena);
   }
+  {
+    // The wide (global-memory) executor is a candidate for every plan.
+    ProgramOptions o;
+    o.wide = true;
+    o.cut_class = cls;
+    ProgSlot sl;
+    sl.name = "wide/classes";
+    sl.exec = Executor::Wide;
+    if (compile_program(h->net, h->plan, o, &sl.prog).empty()) h->slots.push_back(std::move(sl));
+  }
   if (h->slots.size() == 1) {  // nothing else fits: the per-slice program
     ProgSlot sl = h->slots[0];
     sl.name += "/slices";
@@ -926,6 +1007,7 @@ bool plan_view(const qtn_plan_t* cplan, PlanView* view) {
   qtn_plan_t* plan = const_cast<qtn_plan_t*>(cplan);
   view->program = &plan->slots[0].prog;
   view->lane = plan->slots[0].exec == Executor::Lane;
+  view->wide = plan->slots[0].exec == Executor::Wide;
   view->n = plan->net.n;
   view->k = (int)plan->plan.cuts.size();
   view->gamma = plan->net.gamma.data();
@@ -1485,13 +1567,14 @@ qtn_status qtn_plan_describe(const qtn_plan_t* plan, char* buf, size_t cap, size
   for (size_t which = 0; which < plan->slots.size(); ++which) {
     const Program& pg = plan->slots[which].prog;
     o << (which ? "," : "") << "\"" << plan->slots[which].name << "\":{\"leaf_elems\":" << pg.leaf_elems
-      << ",\"arena_elems\":" << pg.arena_elems << ",\"width\":" << pg.width << ",\"max_rank\":" << pg.max_rank
+      << ",\"arena_elems\":" << (plan->slots[which].exec == Executor::Wide ? pg.wide_arena_elems : (uint64_t)pg.arena_elems) << ",\"width\":" << pg.width << ",\"max_rank\":" << pg.max_rank
       << ",\"macs_per_item\":" << pg.macs_per_item << ",\"n_classes\":" << pg.n_classes
       << ",\"executor\":\""
       << (plan->slots[which].exec == Executor::Lane    ? "lane"
           : plan->slots[which].exec == Executor::Warp  ? "warp"
           : plan->slots[which].exec == Executor::Level ? "level"
           : plan->slots[which].exec == Executor::LevelJit ? "level-jit"
+          : plan->slots[which].exec == Executor::Wide ? "wide"
                                                        : "block")
       << "\",\"outer_class\":";
     json_ints(o, pg.outer_class.data(), pg.outer_class.size());
@@ -1515,7 +1598,24 @@ qtn_status qtn_plan_describe(const qtn_plan_t* plan, char* buf, size_t cap, size
       json_ints(o, sb, n_sb);
       o << "}";
     }
-    o << "],\"pro_arena_elems\":" << pg.pro_arena_elems << ",\"macs_prologue\":" << pg.macs_prologue;
+    const bool wide_pg = plan->slots[which].exec == Executor::Wide;
+    o << "],\"pro_arena_elems\":" << (wide_pg ? pg.wide_pro_arena_elems : pg.pro_arena_elems)
+      << ",\"macs_prologue\":" << pg.macs_prologue;
+    if (wide_pg) {
+      o << ",\"wide_arena_elems\":" << pg.wide_arena_elems << ",\"wide_states\":[";
+      bool fs = true;
+      for (const auto& [key, ws] : plan->slots[which].wide_states) {
+        if (!ws) continue;
+        o << (fs ? "" : ",") << "{\"prec\":" << key.first << ",\"nx\":" << key.second << ",\"group\":" << ws->group
+          << ",\"root_blocks\":" << ws->root_blocks << ",\"tuned\":" << (ws->tuned ? "true" : "false")
+          << ",\"step_kernels\":[";
+        for (size_t i = 0; i < ws->step_kernel.size(); ++i)
+          o << (i ? "," : "") << "\"" << wide_kernel_name(ws->step_kernel[i]) << "\"";
+        o << "]}";
+        fs = false;
+      }
+      o << "]";
+    }
     o << ",\"levels\":[";
     for (size_t i = 0; i < pg.levels.size(); ++i)
       o << (i ? "," : "") << "[" << pg.levels[i].first << "," << pg.levels[i].count << "," << pg.levels[i].units[0]
@@ -1523,7 +1623,22 @@ qtn_status qtn_plan_describe(const qtn_plan_t* plan, char* buf, size_t cap, size
     o << "],\"out_start\":[";
     for (size_t i = 0; i < pg.out_start.size(); ++i) o << (i ? "," : "") << pg.out_start[i];
     o << "]";
-    for (int pass = 0; pass < 2; ++pass) {
+    for (int pass = 0; pass < 2 && wide_pg; ++pass) {
+      // Wide programs: 64-bit offsets, store weights 2^wpos.
+      const std::vector<WideStep>& steps = pass ? pg.wide_steps : pg.wide_prologue;
+      o << (pass ? ",\"steps\":[" : ",\"prologue\":[");
+      for (size_t i = 0; i < steps.size(); ++i) {
+        const WideStep& st = steps[i];
+        const int rc = st.ma + st.nb + st.bb;
+        o << (i ? "," : "") << "{\"ma\":" << (int)st.ma << ",\"nb\":" << (int)st.nb << ",\"kb\":" << (int)st.kb
+          << ",\"bb\":" << (int)st.bb << ",\"flags\":" << (int)st.flags << ",\"a\":" << st.a << ",\"b\":" << st.b
+          << ",\"c\":" << st.c << ",\"w\":[";
+        for (int j = 0; j < rc; ++j) o << (j ? "," : "") << (1ull << st.wpos[j]);
+        o << "]}";
+      }
+      o << "]";
+    }
+    for (int pass = 0; pass < 2 && !wide_pg; ++pass) {
     const std::vector<DevStep>& steps = pass ? pg.steps : pg.prologue;
     o << (pass ? ",\"steps\":[" : ",\"prologue\":[");
     for (size_t i = 0; i < steps.size(); ++i) {

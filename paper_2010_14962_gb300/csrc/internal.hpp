@@ -13,6 +13,7 @@ namespace internal {
 struct PlanView {
   const Program* program;  // the program of the plan's executor
   bool lane;               // executor: lane (true) or block (false)
+  bool wide;               // the per-slice program is a wide (global-memory) one
   int n;                   // qubits
   int k;                   // cuts
   const double* gamma;     // host, p entries

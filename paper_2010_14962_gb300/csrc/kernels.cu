@@ -24,6 +24,7 @@
 #include <cuda_bf16.h>
 
 #include "jit.hpp"
+#include "wide.hpp"
 
 #include <algorithm>
 #include <type_traits>
@@ -46,59 +47,7 @@ struct ExecParams {
 
 #include "arith.cuh"
 
-// ------------------------------------- tensor-core product numerics (FP32) --
-
-// Products of operands rounded as the tensor cores see them, accumulated in
-// FP32: TF32 (10-bit significand), split BF16 / TF32 in 2 pieces with the
-// 3 leading products, split BF16 in 3 pieces with the 6 leading products.
-enum class Round { TF32, BF16X3, TF32X3, BF16X6 };
-
-__device__ __forceinline__ float to_tf32(float x) {
-  uint32_t r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return __uint_as_float(r);
-}
-__device__ __forceinline__ float to_bf16(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
-
-template <Round R>
-struct RoundOps {
-  static __device__ __forceinline__ float2 zero() { return make_float2(0.f, 0.f); }
-  // acc + x * y for real x, y under the rounding mode.
-  static __device__ __forceinline__ float mul_add(float acc, float x, float y) {
-    if (R == Round::TF32) return __fmaf_rn(to_tf32(x), to_tf32(y), acc);
-    if (R == Round::BF16X3 || R == Round::TF32X3) {
-      const float xh = R == Round::BF16X3 ? to_bf16(x) : to_tf32(x);
-      const float yh = R == Round::BF16X3 ? to_bf16(y) : to_tf32(y);
-      const float xl = R == Round::BF16X3 ? to_bf16(x - xh) : to_tf32(x - xh);
-      const float yl = R == Round::BF16X3 ? to_bf16(y - yh) : to_tf32(y - yh);
-      acc = __fmaf_rn(xl, yh, acc);
-      acc = __fmaf_rn(xh, yl, acc);
-      return __fmaf_rn(xh, yh, acc);
-    }
-    const float x0 = to_bf16(x), x1 = to_bf16(x - x0), x2 = to_bf16(x - x0 - x1);
-    const float y0 = to_bf16(y), y1 = to_bf16(y - y0), y2 = to_bf16(y - y0 - y1);
-    acc = __fmaf_rn(x0, y2, acc);
-    acc = __fmaf_rn(x1, y1, acc);
-    acc = __fmaf_rn(x2, y0, acc);
-    acc = __fmaf_rn(x0, y1, acc);
-    acc = __fmaf_rn(x1, y0, acc);
-    return __fmaf_rn(x0, y0, acc);
-  }
-  static __device__ __forceinline__ void fma(float2& acc, float2 a, float2 b) {
-    acc.x = mul_add(acc.x, a.x, b.x);
-    acc.x = mul_add(acc.x, -a.y, b.y);
-    acc.y = mul_add(acc.y, a.x, b.y);
-    acc.y = mul_add(acc.y, a.y, b.x);
-  }
-  static __device__ __forceinline__ float2 mul(float2 a, float2 b) {
-    float2 r = zero();
-    fma(r, a, b);
-    return r;
-  }
-  static __device__ __forceinline__ void finish(float2&) {}
-  static __device__ __forceinline__ double re(float2 v) { return (double)v.x; }
-  static __device__ __forceinline__ double im(float2 v) { return (double)v.y; }
-};
+#include "rounding.cuh"
 
 // Offset of slice s's sub-block inside a leaf: cut legs are the high bits.
 __device__ __forceinline__ uint32_t leaf_offset(const DevLeaf& L, uint64_t s) {
@@ -1193,6 +1142,13 @@ bool exec_shape_typed(const DeviceProgram& prog, int nx, uint64_t slices_per_x, 
     sh.smem = L.total;
     if (!shape_for_kernel(block_exec_kernel<V, true, Ops>, sh.threads, sh.smem, &occ)) return false;
     per_block_items = (uint64_t)(sh.threads / 32);
+  } else if (prog.exec == Executor::Wide) {
+    // One partial per item and root block; no shared-memory program.
+    if (!prog.wide) return false;
+    sh.threads = 256;
+    sh.blocks_per_x = (int)std::min<uint64_t>(slices_per_x * (uint64_t)prog.wide->root_blocks, 1ull << 30);
+    *out = sh;
+    return true;
   } else if (prog.exec == Executor::LevelJit) {
     // Shape fixed when the kernel was generated (jit_level_shape).
     if (!prog.jit_kernel) return false;
@@ -1269,6 +1225,15 @@ cudaError_t launch_typed(const DeviceProgram& prog, const uint8_t* d_x, int nx, 
                                                  static_cast<V*>(buf.leaf_tables));
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  if (prog.exec == Executor::Wide) {
+    if (!prog.wide || prog.wide->nx != nx) return cudaErrorInvalidValue;
+    if (ev0 && (e = cudaEventRecord(ev0, stream)) != cudaSuccess) return e;
+    e = wide_launch(prog.wide, buf.leaf_tables, slice_lo, slice_hi, buf.partials, d_slices, buf.err, stream);
+    if (e != cudaSuccess) return e;
+    if (ev1 && (e = cudaEventRecord(ev1, stream)) != cudaSuccess) return e;
+    finalize_kernel<<<nx, 128, 0, stream>>>(buf.partials, shape.blocks_per_x, scale, d_out, d_raw);
+    return cudaGetLastError();
+  }
   if (prog.n_pro_steps > 0 && prog.n_pro_levels > 0) {
     prologue_level_kernel<V, Ops><<<nx, kLevelPrologueThreads, shape.pro_smem, stream>>>(
         prog.pro_steps, prog.n_pro_steps, prog.pro_out_start, prog.pro_pos_nib, prog.pro_levels, prog.n_pro_levels,

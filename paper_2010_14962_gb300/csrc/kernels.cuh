@@ -13,8 +13,10 @@ namespace qtn {
 // merge; Warp: one item per warp; Level: 2^log2_items items per block, all
 // merges of one tree level (of all those items) at once, a barrier per level;
 // LevelJit: the same as Level, run by a kernel generated for the program
-// (jit.hpp) instead of the interpreter.
-enum class Executor : int { Lane = 0, Block = 1, Warp = 2, Level = 3, LevelJit = 4 };
+// (jit.hpp) instead of the interpreter; Wide: intermediates in global memory,
+// one launch per merge and group of items (wide.hpp).
+enum class Executor : int { Lane = 0, Block = 1, Warp = 2, Level = 3, LevelJit = 4, Wide = 5 };
+struct WideState;
 
 // Arithmetic of the merges: complex128, complex64, double-float complex64
 // (FP32X2), and complex64 storage with products rounded as the tensor cores
@@ -65,6 +67,9 @@ struct DeviceProgram {
   const void* jit_kernel = nullptr;
   int jit_log2_items = 0;
   size_t jit_smem = 0;
+  // Wide only: the device state for the arithmetic and bit-string count of
+  // the coming launch (set by the caller before exec_shape / launch).
+  WideState* wide = nullptr;
 };
 
 // One launch sequence: leaf tables for nx bit strings, the slice range

@@ -89,6 +89,8 @@ extern "C" qtn_status qtn_contract_amplitudes_noalloc(const qtn_plan_t* plan, co
     return internal::set_error(QTN_ERR_INVALID_ARG, "bad argument");
   if (prec != QTN_FP64 && prec != QTN_FP32)
     return internal::set_error(QTN_ERR_UNSUPPORTED, "precision not available on this plan's executor");
+  if (pv.wide)
+    return internal::set_error(QTN_ERR_UNSUPPORTED, "the plan's per-slice working set does not fit in shared memory");
   std::lock_guard<std::mutex> lk(*pv.mu);
   const Program& pg = *pv.program;
   const Arith arith = prec == QTN_FP64 ? Arith::F64 : Arith::F32;

@@ -109,6 +109,7 @@ def lib():
                                           ctypes.c_uint64, ctypes.c_int, i32p, f64p, P(ctypes.c_int),
                                           P(ctypes.c_int), f64p, ctypes.c_int, P(ctypes.c_int)],
             "qtn_pipe_peaks": [ctypes.c_int, f64p, f64p],
+            "qtn_wide_set_kernel": [ctypes.c_char_p],
             "qtn_status_string": [ctypes.c_int],
             "qtn_last_error": [],
         }
@@ -433,6 +434,12 @@ def pipe_peaks(reps: int = 3) -> dict:
     f32, f64 = ctypes.c_double(), ctypes.c_double()
     _check(lib().qtn_pipe_peaks(int(reps), ctypes.byref(f32), ctypes.byref(f64)))
     return {"fp32_tflops": f32.value, "fp64_tflops": f64.value}
+
+
+def wide_set_kernel(name: str = "auto"):
+    """qtn_wide_set_kernel: force the wide executor's per-step kernel
+    ("auto", "simt", "simt4", "tcgen05")."""
+    _check(lib().qtn_wide_set_kernel(name.encode()))
 
 
 def batch_cancel():

@@ -82,6 +82,16 @@ def leaf_table(desc, prog, gamma, beta, x):
     return lt
 
 
+def positions(w, rc):
+    """Store offset of every canonical output o = m + (n << ma) + (b << (ma +
+    nb)), in o order: sum of the weights of o's set bits."""
+    o = np.arange(1 << rc, dtype=np.int64)
+    pos = np.zeros(1 << rc, dtype=np.int64)
+    for j in range(rc):
+        pos += ((o >> j) & 1) * int(w[j])
+    return pos
+
+
 def run_prologue(prog, lt):
     """Hoisted merges, once per bit string; exported results become
     pseudo-leaves of the leaf table (in place)."""
@@ -93,13 +103,11 @@ def run_prologue(prog, lt):
         A = (lt[leaves[st["a"]]["base"]:] if st["flags"] & 1 else arena[st["a"]:])[: 1 << (ma + kb + bb)].copy()
         B = (lt[leaves[st["b"]]["base"]:] if st["flags"] & 2 else arena[st["b"]:])[: 1 << (kb + nb + bb)].copy()
         C = np.einsum("bkm,bnk->bnm", A.reshape(1 << bb, 1 << kb, 1 << ma), B.reshape(1 << bb, 1 << nb, 1 << kb))
-        for o in range(1 << rc):
-            m, n, bch = o & ((1 << ma) - 1), (o >> ma) & ((1 << nb) - 1), o >> (ma + nb)
-            pos = sum(st["w"][j] for j in range(rc) if (o >> j) & 1)
-            if st["flags"] & 8:
-                lt[leaves[st["c"]]["base"] + pos] = C[bch, n, m]
-            else:
-                arena[st["c"] + pos] = C[bch, n, m]
+        pos = positions(st["w"], rc)
+        if st["flags"] & 8:
+            lt[leaves[st["c"]]["base"] + pos] = C.reshape(-1)
+        else:
+            arena[st["c"] + pos] = C.reshape(-1)
 
 
 def run_item(prog, lt, item):
@@ -151,10 +159,11 @@ def run_item(prog, lt, item):
             B = src_b[b0:b0 + nbe].copy()
             Ab = A.reshape(1 << bb, 1 << kb, 1 << ma)     # [b, k, m]
             Bb = B.reshape(1 << bb, 1 << nb, 1 << kb)     # [b, n, k]
-            C = np.einsum("bkm,bnk->bnm", Ab, Bb)          # [b, n, m]
-            for o in range(1 << rc):
-                m, n, bch = o & ((1 << ma) - 1), (o >> ma) & ((1 << nb) - 1), o >> (ma + nb)
-                store(o, C[bch, n, m])
+            C = np.einsum("bkm,bnk->bnm", Ab, Bb)          # [b, n, m], flat = canonical o
+            if is_root:
+                out[:] = C.reshape(-1)
+            else:
+                arena[st["c"] + positions(st["w"], rc)] = C.reshape(-1)
         if is_root:
             root = out
     return root
