@@ -186,6 +186,13 @@ std::mutex g_batch_mu;
 std::atomic<int*> g_cancel_host{nullptr};
 std::atomic<double> g_batch_limit_ms{0.0};
 constexpr int kMultiKernels = 4;  // leaf tables, prologue, executor, per-job sums
+// Program each job of the most recent qtn_contract_batch call ran.
+std::mutex g_batch_prog_mu;
+std::vector<std::string> g_batch_programs;
+void record_batch_programs(std::vector<std::string> names) {
+  std::lock_guard<std::mutex> lk(g_batch_prog_mu);
+  g_batch_programs = std::move(names);
+}
 
 }  // namespace
 
@@ -1250,6 +1257,44 @@ qtn_status qtn_contract_batch(const qtn_plan_t* const* plans, const uint8_t* con
     qtn_status st = validate_x(plans[j], xs[j]);
     if (st != QTN_OK) return st;
   }
+  // Jobs whose plans keep tensors too large for shared memory run on their
+  // plan's wide executor, one after the other on `stream`; the others share
+  // one multi-job launch sequence.
+  std::vector<int> wide_jobs, chip_jobs;
+  for (int j = 0; j < njobs; ++j) (plans[j]->slots[0].exec == Executor::Wide ? wide_jobs : chip_jobs).push_back(j);
+  if (!wide_jobs.empty()) {
+    if (!chip_jobs.empty()) {
+      std::vector<const qtn_plan_t*> cp;
+      std::vector<const uint8_t*> cx;
+      for (int j : chip_jobs) {
+        cp.push_back(plans[j]);
+        cx.push_back(xs[j]);
+      }
+      std::vector<double> co(2 * chip_jobs.size());
+      qtn_status st = qtn_contract_batch(cp.data(), cx.data(), (int)chip_jobs.size(), prec, stream, co.data());
+      if (st != QTN_OK) return st;
+      for (size_t i = 0; i < chip_jobs.size(); ++i) {
+        out[2 * chip_jobs[i]] = co[2 * i];
+        out[2 * chip_jobs[i] + 1] = co[2 * i + 1];
+      }
+    }
+    std::vector<std::string> names(njobs);
+    if (!chip_jobs.empty()) {
+      std::lock_guard<std::mutex> lk(g_batch_prog_mu);
+      for (size_t i = 0; i < chip_jobs.size() && i < g_batch_programs.size(); ++i)
+        names[chip_jobs[i]] = g_batch_programs[i];
+    }
+    for (int j : wide_jobs) {
+      qtn_status st = qtn_contract_amplitude(plans[j], xs[j], prec, stream, out + 2 * j);
+      if (st != QTN_OK) return st;
+      qtn_plan_t* plan = const_cast<qtn_plan_t*>(plans[j]);
+      std::lock_guard<std::mutex> lk(plan->mu);
+      auto it = plan->tuned.find(std::make_pair((int)prec, 1));
+      names[j] = it != plan->tuned.end() ? plan->slots[it->second].name : plan->slots[0].name;
+    }
+    record_batch_programs(std::move(names));
+    return QTN_OK;
+  }
   bool one_plan = true;
   for (int j = 1; j < njobs; ++j) one_plan = one_plan && plans[j] == plans[0];
   if (one_plan) {
@@ -1277,6 +1322,7 @@ qtn_status qtn_contract_batch(const qtn_plan_t* const* plans, const uint8_t* con
     st = plan->check_err_flag();
     if (st != QTN_OK) return st;
     std::memcpy(out, plan->h_out_pinned, (size_t)njobs * 2 * sizeof(double));
+    record_batch_programs(std::vector<std::string>(njobs, plan->slots[si].name));
     return QTN_OK;
   }
   const Arith arith = arith_of(prec);
@@ -1514,10 +1560,28 @@ qtn_status qtn_contract_batch(const qtn_plan_t* const* plans, const uint8_t* con
   QTN_CUDA(cudaStreamSynchronize(stream));
   if (*W.h_status != 0)
     return fail(QTN_ERR_TIMEOUT, "the batch was cancelled or exceeded its time limit; no amplitudes were returned");
+  std::vector<std::string> names(njobs);
   for (int j = 0; j < njobs; ++j) {
     out[2 * j] = W.h_out[2 * j];
     out[2 * j + 1] = W.h_out[2 * j + 1];
+    names[j] = jh[j].plan->slots[jh[j].slot].name;
   }
+  record_batch_programs(std::move(names));
+  return QTN_OK;
+}
+
+qtn_status qtn_batch_last_programs(char* buf, size_t cap, size_t* len) {
+  if (!len) return fail(QTN_ERR_INVALID_ARG, "len is NULL");
+  std::ostringstream o;
+  {
+    std::lock_guard<std::mutex> lk(g_batch_prog_mu);
+    o << "[";
+    for (size_t j = 0; j < g_batch_programs.size(); ++j) o << (j ? "," : "") << "\"" << g_batch_programs[j] << "\"";
+    o << "]";
+  }
+  const std::string t = o.str();
+  *len = t.size() + 1;
+  if (buf && cap >= t.size() + 1) std::memcpy(buf, t.c_str(), t.size() + 1);
   return QTN_OK;
 }
 
@@ -1611,6 +1675,13 @@ qtn_status qtn_plan_describe(const qtn_plan_t* plan, char* buf, size_t cap, size
           << ",\"step_kernels\":[";
         for (size_t i = 0; i < ws->step_kernel.size(); ++i)
           o << (i ? "," : "") << "\"" << wide_kernel_name(ws->step_kernel[i]) << "\"";
+        o << "],\"step_ms\":[";
+        for (size_t i = 0; i < ws->step_ms.size(); ++i) {
+          o << (i ? "," : "") << "{";
+          for (size_t c = 0; c < ws->step_ms[i].size(); ++c)
+            o << (c ? "," : "") << "\"" << wide_kernel_name(ws->step_ms[i][c].first) << "\":" << ws->step_ms[i][c].second;
+          o << "}";
+        }
         o << "]}";
         fs = false;
       }

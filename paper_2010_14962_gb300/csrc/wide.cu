@@ -312,6 +312,8 @@ cudaError_t launch_step(const WideState& ws, WideKernel k, const WideStep& st, c
     t.bb = st.bb;
     for (int i = 0; i < kWideMaxRank; ++i) t.wpos[i] = st.wpos[i];
     t.err = d_err;
+    t.ws = ws.d_tc_ws;
+    t.ws_floats = ws.tc_ws_floats;
     return wide_tc_launch(t, ws.arith == Arith::TF32X3 ? 3 : 1, stream);
   }
   return launch_simt(ws.arith, p, k == WideKernel::Simt4 ? 4 : 1, stream);
@@ -374,6 +376,7 @@ WideState::~WideState() {
   cudaFree(d_arena);
   cudaFree(d_pro_arena);
   cudaFree(d_own_err);
+  cudaFree(d_tc_ws);
 }
 
 bool wide_tc_eligible(const WideStep& st, Arith a) {
@@ -397,6 +400,19 @@ cudaError_t wide_prepare(WideState* ws, const Program& prog, Arith a, int nx, ui
   const uint64_t pro = std::max<uint64_t>(prog.wide_pro_arena_elems, 1) * elem_bytes(a) * (uint64_t)nx;
   e = cudaMalloc(&ws->d_pro_arena, pro);
   if (e != cudaSuccess) return e;
+  // Split-K partials of the tensor-core merges (TF32 forms only), at most 256 MiB.
+  if (a == Arith::TF32 || a == Arith::TF32X3) {
+    uint64_t need = 0;
+    for (const WideStep& st : prog.wide_steps)
+      if (wide_tc_eligible(st, a)) need = std::max(need, wide_tc_workspace_floats(st.ma, st.nb, st.kb, st.bb, ws->group));
+    for (const WideStep& st : prog.wide_prologue)
+      if (wide_tc_eligible(st, a)) need = std::max(need, wide_tc_workspace_floats(st.ma, st.nb, st.kb, st.bb, nx));
+    ws->tc_ws_floats = std::min<uint64_t>(need, 64ull << 20);
+    if (ws->tc_ws_floats) {
+      e = cudaMalloc(&ws->d_tc_ws, ws->tc_ws_floats * sizeof(float));
+      if (e != cudaSuccess) return e;
+    }
+  }
   e = cudaMalloc(&ws->d_own_err, sizeof(int));
   if (e != cudaSuccess) return e;
   e = cudaMemset(ws->d_own_err, 0, sizeof(int));
@@ -424,6 +440,7 @@ cudaError_t wide_tune(WideState* ws, void* leaf_tables, uint64_t slice_lo, uint6
   const uint64_t nr = slice_hi - slice_lo;
   const uint64_t n_group = std::min<uint64_t>(ws->group, (uint64_t)ws->nx * nr);
   ws->force_mode = g_force_kernel.load();
+  ws->step_ms.assign(pg.wide_steps.size(), {});
   // Each candidate runs on the step's real operands (leaf tables already
   // built on `stream`); running a step out of turn only rewrites its result,
   // which the contraction itself recomputes before anything reads it.
@@ -451,6 +468,7 @@ cudaError_t wide_tune(WideState* ws, void* leaf_tables, uint64_t slice_lo, uint6
         if (it != wide_tune_table().end() &&
             std::find(cand.begin(), cand.end(), it->second.best) != cand.end()) {
           (*out)[j] = it->second.best;
+          if (!prologue) ws->step_ms[j] = it->second.ms;
           continue;
         }
       }
@@ -478,6 +496,7 @@ cudaError_t wide_tune(WideState* ws, void* leaf_tables, uint64_t slice_lo, uint6
         }
       }
       (*out)[j] = ent.best;
+      if (!prologue) ws->step_ms[j] = ent.ms;
       lg << "(" << st.ma << "," << st.nb << "," << st.kb << "," << st.bb << ")x" << n_items << ":"
          << wide_kernel_name(ent.best) << " ";
       if (force < 0) {

@@ -52,10 +52,15 @@ struct WideState {
   void* d_pro_arena = nullptr;
   std::vector<WideKernel> step_kernel;  // per item step (autotuned)
   std::vector<WideKernel> pro_kernel;   // per prologue step
+  // Per item step: the candidates' times (ms per launch of `group` items,
+  // CUDA events) from the tuning; empty where the kernel was forced.
+  std::vector<std::vector<std::pair<WideKernel, float>>> step_ms;
   bool tuned = false;
   std::string tune_log;       // the kernel chosen per tuned shape
   int force_mode = -1;        // kernel override in force when tuned (qtn_wide_set_kernel)
   int* d_own_err = nullptr;   // error word used when the caller passes none
+  float* d_tc_ws = nullptr;   // split-K partials of tensor-core merges
+  uint64_t tc_ws_floats = 0;
   ~WideState();
 };
 

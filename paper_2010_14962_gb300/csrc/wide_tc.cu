@@ -37,9 +37,10 @@ struct TcGeom {
   uint64_t xr, xk, yq, yk;   // element strides: X(row, k), Y(q, k)
   uint64_t xbat, ybat;       // batch-index stride of X and Y
   int nt;                    // real columns per column tile (2 x complex)
-  uint64_t row_tiles, col_tiles, units;
+  uint64_t row_tiles, col_tiles, base_units, units;
   int kc;                    // real K columns per chunk
   int kchunks;
+  int ksplit, cps;           // K splits per output tile, chunks per split
   uint32_t idesc;
   int tmem_cols;
   uint32_t stage_bytes, x_bytes, y_bytes;
@@ -136,9 +137,11 @@ __global__ void __launch_bounds__(kTcThreads) wide_tc_kernel(WideTcArgs a, TcGeo
   uint32_t chunk_no = 0;
   bool failed = false;
   for (uint64_t unit = blockIdx.x; unit < G.units && !failed; unit += gridDim.x) {
-    const uint64_t ct = unit % G.col_tiles;
-    const uint64_t rt = (unit / G.col_tiles) % G.row_tiles;
-    const uint64_t gb = unit / (G.col_tiles * G.row_tiles);
+    const int split = (int)(unit % G.ksplit);
+    const uint64_t bu = unit / G.ksplit;
+    const uint64_t ct = bu % G.col_tiles;
+    const uint64_t rt = (bu / G.col_tiles) % G.row_tiles;
+    const uint64_t gb = bu / (G.col_tiles * G.row_tiles);
     const uint64_t b = gb & ((1ull << G.bb) - 1), g = gb >> G.bb;
     const uint64_t item = a.item_lo + g;
     const uint64_t xi = a.prologue ? item : item / a.items_per_x;
@@ -152,7 +155,8 @@ __global__ void __launch_bounds__(kTcThreads) wide_tc_kernel(WideTcArgs a, TcGeo
     for (int i = tid; i < kRows; i += kTcThreads) posR[i] = pos_bits(a.wpos, rbit, rlog, rt * kRows + i);
     for (int i = tid; i < qt; i += kTcThreads) posQ[i] = pos_bits(a.wpos, qbit, qlog, ct * qt + i);
     const uint64_t posb = pos_bits(a.wpos, G.ma + G.nb, G.bb, b);
-    for (int c = 0; c < G.kchunks; ++c, ++chunk_no) {
+    const int c_lo = split * G.cps, c_hi = min(G.kchunks, c_lo + G.cps);
+    for (int c = c_lo; c < c_hi; ++c, ++chunk_no) {
       const int s = chunk_no & 1;
       if (chunk_no >= 2) {
         const bool ok = bar_wait(&bar[s], ((chunk_no - 2) >> 1) & 1);
@@ -205,7 +209,7 @@ __global__ void __launch_bounds__(kTcThreads) wide_tc_kernel(WideTcArgs a, TcGeo
           for (int t = (P == 3 ? 0 : 2); t < 3; ++t) {
             const uint64_t ad = sdesc(xa + px[t] * G.x_bytes + ks * 2 * lbo_x, lbo_x, 128);
             const uint64_t bd = sdesc(ya + py[t] * G.y_bytes + ks * 2 * lbo_y, lbo_y, 128);
-            const uint32_t acc = (c > 0 || ks > 0 || t > (P == 3 ? 0 : 2)) ? 1u : 0u;
+            const uint32_t acc = (c > c_lo || ks > 0 || t > (P == 3 ? 0 : 2)) ? 1u : 0u;
             asm volatile(
                 "{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
                 "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
@@ -241,10 +245,20 @@ __global__ void __launch_bounds__(kTcThreads) wide_tc_kernel(WideTcArgs a, TcGeo
             "=r"(v[30]), "=r"(v[31])
           : "r"(taddr));
       asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (G.ksplit == 1) {
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const int q = (col0 >> 1) + j;
-        if (q < qt) Cbase[posQ[q]] = make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
+        for (int j = 0; j < 16; ++j) {
+          const int q = (col0 >> 1) + j;
+          if (q < qt) Cbase[posQ[q]] = make_float2(__uint_as_float(v[2 * j]), __uint_as_float(v[2 * j + 1]));
+        }
+      } else {
+        // Split K: this split's partial rows go to the workspace, unpermuted.
+        float* w = a.ws + ((bu * G.ksplit + split) * kRows + row) * (uint64_t)G.nt + col0;
+#pragma unroll
+        for (int j = 0; j < 32; j += 4)
+          if (col0 + j < G.nt)
+            *reinterpret_cast<float4*>(w + j) = make_float4(__uint_as_float(v[j]), __uint_as_float(v[j + 1]),
+                                                            __uint_as_float(v[j + 2]), __uint_as_float(v[j + 3]));
       }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -256,9 +270,104 @@ __global__ void __launch_bounds__(kTcThreads) wide_tc_kernel(WideTcArgs a, TcGeo
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(G.tmem_cols));
 }
 
+// Sum of the K-split partials of every output (split order, FP64), stored
+// at its consumer-layout position.
+__global__ void __launch_bounds__(256) wide_tc_splitk_reduce(WideTcArgs a, TcGeom G) {
+  const uint64_t qt = (uint64_t)(G.nt >> 1);
+  const uint64_t total = G.base_units * kRows * qt;
+  const int rlog = G.rows_is_m ? G.ma : G.nb, qlog = G.rows_is_m ? G.nb : G.ma;
+  const int rbit = G.rows_is_m ? 0 : G.ma, qbit = G.rows_is_m ? G.ma : 0;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t q = i % qt, row = (i / qt) % kRows, bu = i / (qt * kRows);
+    const uint64_t ct = bu % G.col_tiles;
+    const uint64_t rt = (bu / G.col_tiles) % G.row_tiles;
+    const uint64_t gb = bu / (G.col_tiles * G.row_tiles);
+    const uint64_t b = gb & ((1ull << G.bb) - 1), g = gb >> G.bb;
+    double re = 0.0, im = 0.0;
+    for (int s = 0; s < G.ksplit; ++s) {
+      const float2 v = *reinterpret_cast<const float2*>(a.ws + ((bu * G.ksplit + s) * kRows + row) * (uint64_t)G.nt +
+                                                        2 * q);
+      re += v.x;
+      im += v.y;
+    }
+    const uint64_t item = a.item_lo + g;
+    const uint64_t xi = a.prologue ? item : item / a.items_per_x;
+    float2* Cp = const_cast<float2*>(a.c_export ? a.leaf_tables + xi * a.leaf_elems + a.c_off
+                                                : a.arena + g * a.arena_stride + a.c_off);
+    const uint64_t pos = pos_bits(a.wpos, rbit, rlog, rt * kRows + row) + pos_bits(a.wpos, qbit, qlog, ct * qt + q) +
+                         pos_bits(a.wpos, G.ma + G.nb, G.bb, b);
+    Cp[pos] = make_float2((float)re, (float)im);
+  }
+}
+
 int g_tc_sms = 0;
+int tc_sms() {
+  if (g_tc_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_tc_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_tc_sms <= 0) g_tc_sms = 1;
+  }
+  return g_tc_sms;
+}
+
+// Launch geometry of a merge; ksplit from the SM count (two CTAs per SM
+// wanted, at least two chunks per split) and the workspace capacity.
+TcGeom make_geom(int ma, int nb, int kb, int bb, uint64_t n_items, int products, uint64_t ws_floats) {
+  TcGeom G{};
+  G.rows_is_m = (ma >= 7 && (ma >= nb || nb < 7)) ? 1 : 0;
+  G.ma = ma;
+  G.nb = nb;
+  G.kb = kb;
+  G.bb = bb;
+  if (G.rows_is_m) {  // X = A (m, k), Y = B (n, k)
+    G.xr = 1;
+    G.xk = 1ull << ma;
+    G.yq = 1ull << kb;
+    G.yk = 1;
+  } else {  // X = B^T (n, k), Y = A (m, k)
+    G.xr = 1ull << kb;
+    G.xk = 1;
+    G.yq = 1;
+    G.yk = 1ull << ma;
+  }
+  const uint64_t abat = 1ull << (ma + kb), bbat = 1ull << (kb + nb);
+  G.xbat = G.rows_is_m ? abat : bbat;
+  G.ybat = G.rows_is_m ? bbat : abat;
+  const int rlog = G.rows_is_m ? ma : nb, qlog = G.rows_is_m ? nb : ma;
+  G.nt = (int)std::min<uint64_t>(256, 2ull << qlog);
+  G.row_tiles = 1ull << (rlog - 7);
+  G.col_tiles = (2ull << qlog) / (uint64_t)G.nt;
+  G.base_units = n_items * (1ull << bb) * G.row_tiles * G.col_tiles;
+  G.kc = (int)std::min<uint64_t>(kChunk, 2ull << kb);
+  G.kchunks = (int)((2ull << kb) / (uint64_t)G.kc);
+  const uint64_t want = 2ull * tc_sms();
+  uint64_t ks = 1;
+  if (G.base_units < want && G.kchunks >= 4) {
+    ks = std::min<uint64_t>((want + G.base_units - 1) / G.base_units, (uint64_t)G.kchunks / 2);
+    const uint64_t per = G.base_units * kRows * (uint64_t)G.nt;
+    if (per > 0) ks = std::min<uint64_t>(ks, ws_floats / per);
+    if (ks < 2) ks = 1;
+  }
+  G.cps = (int)((G.kchunks + ks - 1) / ks);
+  G.ksplit = (int)((G.kchunks + G.cps - 1) / G.cps);
+  G.units = G.base_units * G.ksplit;
+  G.idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(G.nt >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
+  G.tmem_cols = std::max(32, G.nt);
+  const int pcs = products == 3 ? 2 : 1;
+  G.x_bytes = (uint32_t)kRows * kChunk * 4;
+  G.y_bytes = (uint32_t)G.nt * kChunk * 4;
+  G.stage_bytes = pcs * (G.x_bytes + G.y_bytes);
+  return G;
+}
 
 }  // namespace
+
+uint64_t wide_tc_workspace_floats(int ma, int nb, int kb, int bb, uint64_t n_items) {
+  if (!wide_tc_shape_ok(ma, nb, kb, bb)) return 0;
+  const TcGeom G = make_geom(ma, nb, kb, bb, n_items, 1, ~0ull);
+  return G.ksplit > 1 ? G.units * kRows * (uint64_t)G.nt : 0;
+}
 
 bool wide_tc_shape_ok(int ma, int nb, int kb, int bb) {
   if (ma + nb + bb > kWideMaxRank || kb < 2 || kb > 24) return false;
@@ -271,46 +380,8 @@ bool wide_tc_shape_ok(int ma, int nb, int kb, int bb) {
 cudaError_t wide_tc_launch(const WideTcArgs& a, int products, cudaStream_t stream) {
   if (!wide_tc_shape_ok(a.ma, a.nb, a.kb, a.bb) || (products != 1 && products != 3) || !a.err)
     return cudaErrorInvalidValue;
-  TcGeom G{};
-  G.rows_is_m = (a.ma >= 7 && (a.ma >= a.nb || a.nb < 7)) ? 1 : 0;
-  G.ma = a.ma;
-  G.nb = a.nb;
-  G.kb = a.kb;
-  G.bb = a.bb;
-  if (G.rows_is_m) {  // X = A (m, k), Y = B (n, k)
-    G.xr = 1;
-    G.xk = 1ull << a.ma;
-    G.yq = 1ull << a.kb;
-    G.yk = 1;
-  } else {  // X = B^T (n, k), Y = A (m, k)
-    G.xr = 1ull << a.kb;
-    G.xk = 1;
-    G.yq = 1;
-    G.yk = 1ull << a.ma;
-  }
-  const uint64_t abat = 1ull << (a.ma + a.kb), bbat = 1ull << (a.kb + a.nb);
-  G.xbat = G.rows_is_m ? abat : bbat;
-  G.ybat = G.rows_is_m ? bbat : abat;
-  const int rlog = G.rows_is_m ? a.ma : a.nb, qlog = G.rows_is_m ? a.nb : a.ma;
-  G.nt = (int)std::min<uint64_t>(256, 2ull << qlog);
-  G.row_tiles = 1ull << (rlog - 7);
-  G.col_tiles = (2ull << qlog) / (uint64_t)G.nt;
-  G.units = a.n_items * (1ull << a.bb) * G.row_tiles * G.col_tiles;
-  G.kc = (int)std::min<uint64_t>(kChunk, 2ull << a.kb);
-  G.kchunks = (int)((2ull << a.kb) / (uint64_t)G.kc);
-  G.idesc = (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(G.nt >> 3) << 17) | ((uint32_t)(kRows >> 4) << 24);
-  G.tmem_cols = std::max(32, G.nt);
-  const int pcs = products == 3 ? 2 : 1;
-  G.x_bytes = (uint32_t)kRows * kChunk * 4;
-  G.y_bytes = (uint32_t)G.nt * kChunk * 4;
-  G.stage_bytes = pcs * (G.x_bytes + G.y_bytes);
+  const TcGeom G = make_geom(a.ma, a.nb, a.kb, a.bb, a.n_items, products, a.ws ? a.ws_floats : 0);
   const size_t smem = 2 * (size_t)G.stage_bytes + 2 * kRows * sizeof(uint64_t) + 64;
-  if (g_tc_sms == 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&g_tc_sms, cudaDevAttrMultiProcessorCount, dev);
-    if (g_tc_sms <= 0) g_tc_sms = 1;
-  }
   cudaError_t e;
   int occ = 0;
   if (products == 3) {
@@ -322,11 +393,16 @@ cudaError_t wide_tc_launch(const WideTcArgs& a, int products, cudaStream_t strea
   }
   if (e != cudaSuccess) return e;
   occ = std::max(1, std::min(occ, 512 / G.tmem_cols));  // tensor memory: 512 columns per SM
-  const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(G.units, (uint64_t)g_tc_sms * occ));
+  const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(G.units, (uint64_t)tc_sms() * occ));
   if (products == 3)
     wide_tc_kernel<3><<<grid, kTcThreads, smem, stream>>>(a, G);
   else
     wide_tc_kernel<1><<<grid, kTcThreads, smem, stream>>>(a, G);
+  e = cudaGetLastError();
+  if (e != cudaSuccess || G.ksplit == 1) return e;
+  const uint64_t outs = G.base_units * kRows * (uint64_t)(G.nt >> 1);
+  const unsigned rgrid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>((outs + 255) / 256, (uint64_t)tc_sms() * 8));
+  wide_tc_splitk_reduce<<<rgrid, 256, 0, stream>>>(a, G);
   return cudaGetLastError();
 }
 

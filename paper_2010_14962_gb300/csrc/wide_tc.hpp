@@ -38,13 +38,22 @@ struct WideTcArgs {
   int ma, nb, kb, bb;
   uint8_t wpos[kWideMaxRank];  // store bit positions of the canonical output bits
   int* err;                    // set non-zero if a bounded wait gave up
+  float* ws;                   // split-K partials (device), or null
+  uint64_t ws_floats;          // its capacity
 };
 
 // Shapes the kernel takes: a side of at least 128 (the tile's rows), the
 // other side at least 8, and at least 4 summed entries.
 bool wide_tc_shape_ok(int ma, int nb, int kb, int bb);
 
-// products: 1 (TF32) or 3 (split TF32).
+// Floats of split-K workspace the launch of this shape over n_items items
+// would use with the device's SM count (0: no split).
+uint64_t wide_tc_workspace_floats(int ma, int nb, int kb, int bb, uint64_t n_items);
+
+// products: 1 (TF32) or 3 (split TF32).  Merges with few output tiles and a
+// long sum are split along K over several CTAs (when a.ws holds the
+// partials); a second kernel adds each output's partials in split order
+// (FP64) and stores the result.
 cudaError_t wide_tc_launch(const WideTcArgs& a, int products, cudaStream_t stream);
 
 }  // namespace qtn
