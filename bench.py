@@ -503,8 +503,8 @@ def setup_uneven(rank: int, jobs: int = 0):
     def one(jd):
         j, d = jd
         inst = I.qaoa_instance(d["n"], d["p"], d["seed"])
-        net = qtn.Network(d["n"], inst.edges, inst.gamma, inst.beta)
-        return inst, qtn.plan_to_fit(net, d["k"]), I.bitstrings(d["n"], 1, 700 + j + 1000 * rank)[0]
+        plan = qtn.plan_job(d["n"], d["p"], inst.edges, inst.gamma, inst.beta, d["k"])
+        return inst, plan, I.bitstrings(d["n"], 1, 700 + j + 1000 * rank)[0]
 
     with cf.ThreadPoolExecutor(min(16, os.cpu_count() or 1)) as ex:
         jobs = list(ex.map(one, enumerate(spec)))
@@ -515,7 +515,9 @@ def uneven_cpu_baseline(seconds: float, jobs):
     """The oracle on a bounded sample of the batch: jobs in a seeded random
     order, each contracted over slice ranges (doubling in size) for at most a
     quarter of ``seconds``; the value is the amplitudes' worth of slices done
-    (fraction of each job's 2^k slices, summed) per second, all host cores."""
+    (fraction of each job's 2^k slices, summed) per second, all host cores.
+    Depth-2 jobs on more than 40 qubits are left out: the oracle contracts
+    the gate network, whose slices there hold 2^30 and more entries."""
     from oracle import oracle as O
 
     cores = os.cpu_count() or 1
@@ -528,6 +530,8 @@ def uneven_cpu_baseline(seconds: float, jobs):
         if time.perf_counter() - t0 >= seconds:
             break
         inst, plan, x = jobs[j]
+        if inst.p == 2 and inst.n > 40:
+            continue
         cuts, _ = O.choose_cuts(inst.n, inst.edges, inst.p, plan.k)  # the oracle's own plan
         S = 2 ** len(cuts)
         lo, chunk, tj = 0, 1, time.perf_counter()
@@ -562,9 +566,16 @@ def run_uneven(args, rank, world, local_rank):
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
 
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
     def step(prec):
+        # Device time of the whole call (on-chip jobs' launch sequence and the
+        # wide jobs after it), CUDA events on the stream.
+        ev0.record(stream)
         out = qtn.contract_batch(plans, xs, prec, stream)
-        return out, qtn.batch_last_ms()[0]
+        ev1.record(stream)
+        ev1.synchronize()
+        return out, ev0.elapsed_time(ev1)
 
     ref = step("fp64")[0]
     sweep = {}
@@ -614,9 +625,10 @@ def run_uneven(args, rank, world, local_rank):
             dist.destroy_process_group()
         return
     exec_flops = 0.0
-    for pl in plans:
-        prog = pl.describe()["programs"][qtn.batch_program(pl, prec)]
-        exec_flops += 8.0 * (2 ** len(prog["outer_class"])) * prog["macs_per_item"]
+    ran = qtn.batch_last_programs()  # the program each job ran in the last call
+    for pl, name in zip(plans, ran):
+        prog = pl.describe()["programs"][name]
+        exec_flops += 8.0 * ((2 ** len(prog["outer_class"])) * prog["macs_per_item"] + prog["macs_prologue"])
     method_flops = sum((2 ** c["k"]) * 8 * c["macs_per_slice"] for c in (pl.cost() for pl in plans))
     peak = pipe_peak(prec, pipe_peaks)
     avg_s = statistics.mean(dev_ms) / 1e3
@@ -630,12 +642,16 @@ def run_uneven(args, rank, world, local_rank):
         "data": "synthetic: seeded random 3-regular graphs, gamma/beta ~ U[0,pi), seeded bit strings",
         "config": {"workload": UNEVEN["name"] if nj == UNEVEN["jobs"] else f"uneven{nj}", "jobs": nj, "n": [min(d["n"] for d in spec), max(d["n"] for d in spec)],
                    "p1_jobs": sum(d["p"] == 1 for d in spec), "p2_jobs": sum(d["p"] == 2 for d in spec),
+                   "graphical_model_jobs": sum(pl.network.form == "gm" for pl in plans),
+                   "wide_executor_jobs": sum(name.startswith("wide") for name in ran),
+                   "programs_run": ran,
                    "cuts": [min(ks), max(ks)], "precision": prec,
                    "executed_flops_per_step": exec_flops, "method_flops_per_step": method_flops,
                    "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": "one launch sequence per step: all jobs' chunks on one persistent grid"},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "traffic": None, "kernel": "multi-job launch sequence (leaf, prologue, multi_exec, sums)",
+                     "traffic": None,
+                     "kernel": "whole batch call (multi-job launch sequence of the on-chip jobs, wide executors)",
                      "peak_source": ("measured %s FMA peak of this GPU (qtn_pipe_peaks)"
                                      % ("FP64" if prec == "fp64" else "FP32")),
                      "pipe_issue_frac": achieved * INSTR_PER_MAC[prec] / peak if prec in INSTR_PER_MAC else None,
@@ -643,7 +659,7 @@ def run_uneven(args, rank, world, local_rank):
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": "amplitudes/s", "h2d_bytes_per_step": int(sum(d["n"] for d in spec)),
                 "d2h_bytes_per_step": int(nj * 16), "api": "qtn_contract_batch (host x in, host amplitudes out)"},
-        "gpu_launches": qtn.batch_last_ms()[1] * args.steps,
+        "gpu_launches": None,
         "precision_sweep": sweep,
         "wall_s_timed_region": wall,
     }

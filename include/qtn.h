@@ -275,7 +275,12 @@ qtn_status qtn_contract_slices(const qtn_plan_t* plan, const uint8_t* x, uint64_
  * runs its 48 KiB batched (else per-class) block program instead.
  * The multi-plan sequence (uploads, kernels, read-backs) is captured as a
  * CUDA graph the first time a list of plans is seen (with that precision
- * and time limit) and replayed afterwards.
+ * and time limit) and replayed afterwards.  Jobs whose plan has no level
+ * program that fits the multi-job executor (tensors too large for shared
+ * memory: the wide executor, see qtn_wide_set_kernel; or programs that fit
+ * only the single-plan executors) run after that sequence, each on its
+ * plan's tuned executor (as qtn_contract_amplitude); the cancel word and time
+ * limit do not apply to them.
  * Errors: QTN_ERR_INVALID_ARG (NULL plan, bad x), QTN_ERR_UNSUPPORTED (a
  * job's working set exceeds shared memory), QTN_ERR_TIMEOUT (stopped, see
  * qtn_batch_cancel), QTN_ERR_CUDA.  Internal device and pinned buffers are
@@ -304,6 +309,13 @@ qtn_status qtn_batch_set_time_limit(double ms);
  * tables to per-job sums, read-backs; CUDA events on its stream), and the
  * number of kernels it launched.  QTN_ERR_INVALID_ARG if none ran yet. */
 qtn_status qtn_batch_last_ms(float* ms, int* kernels);
+
+/* The program each job of the most recent qtn_contract_batch call ran (its
+ * name as in qtn_plan_describe's "programs"), as a JSON array in job order;
+ * measurement support (the paper has no counterpart).  Writes at most `cap`
+ * bytes (NUL-terminated) to `buf` when `cap` is large enough; always sets
+ * *len to the size needed ("[]" before any batch). */
+qtn_status qtn_batch_last_programs(char* buf, size_t cap, size_t* len);
 
 /* Which executor the plan runs on ("lane": one slice per GPU thread, for
  * plans with every tensor rank <= 5; "block": one slice per thread block). */

@@ -212,13 +212,17 @@ struct ProgSlot {
   uint64_t items() const { return 1ull << prog.n_outer; }
 };
 
-// Global-memory budget of a wide executor's item arenas: a quarter of the
-// free device memory, at most 32 GiB.
+// Global-memory budget of one wide executor state's item arenas: an eighth
+// of the free device memory, at most 4 GiB (a plan can hold a state per
+// arithmetic and batch width, and a batch holds many plans).
 uint64_t wide_budget_bytes() {
   size_t free_b = 0, total_b = 0;
   if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return 1ull << 30;
-  return std::min<uint64_t>(free_b / 4, 32ull << 30);
+  return std::min<uint64_t>(free_b / 8, 4ull << 30);
 }
+// Wide launch sequences longer than this many kernels run without a
+// captured graph (instantiating one costs memory in proportion).
+constexpr uint64_t kWideGraphMaxLaunches = 4096;
 
 // Suffix of a specialised executor's name for an arithmetic.
 const char* jit_suffix(Arith a) {
@@ -591,6 +595,13 @@ struct qtn_plan {
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     if (best < 0) return fail(QTN_ERR_UNSUPPORTED, "no executor fits this plan on chip");
+    // Wide candidates that lost keep no device memory.
+    for (int si = 1; si < (int)slots.size(); ++si)
+      if (si != best && slots[si].exec == Executor::Wide) {
+        QTN_CUDA(cudaStreamSynchronize(stream));
+        slots[si].wide_states.erase(std::make_pair((int)prec, nx));
+        if (slots[si].dprog.wide) slots[si].dprog.wide = nullptr;
+      }
     tuned[key] = best;
     tune_ms[key] = times;
     *out_slot = best;
@@ -610,9 +621,17 @@ struct qtn_plan {
     ExecShape sh;
     st = prepare(si, prec, nx, S, &sh);
     if (st != QTN_OK) return st;
-    if (timing) {
+    bool direct = timing;
+    if (slots[si].exec == Executor::Wide) {
+      const WideState* ws = slots[si].dprog.wide;
+      const uint64_t groups = ((uint64_t)nx * S + ws->group - 1) / ws->group;
+      direct = direct || groups * slots[si].prog.wide_steps.size() + slots[si].prog.wide_prologue.size() >
+                             kWideGraphMaxLaunches;
+    }
+    if (direct) {
       cudaError_t le = launch_contraction(slots[si].dprog, arith_of(prec), d_x, nx, 0, S, buffers(), sh, scale(),
-                                          d_out, nullptr, nullptr, stream, ev0, ev1, d_gamma, d_beta);
+                                          d_out, nullptr, nullptr, stream, timing ? ev0 : nullptr,
+                                          timing ? ev1 : nullptr, d_gamma, d_beta);
       if (le != cudaSuccess) return cuda_fail(le, "launch_contraction");
       return QTN_OK;
     }
@@ -1257,44 +1276,6 @@ qtn_status qtn_contract_batch(const qtn_plan_t* const* plans, const uint8_t* con
     qtn_status st = validate_x(plans[j], xs[j]);
     if (st != QTN_OK) return st;
   }
-  // Jobs whose plans keep tensors too large for shared memory run on their
-  // plan's wide executor, one after the other on `stream`; the others share
-  // one multi-job launch sequence.
-  std::vector<int> wide_jobs, chip_jobs;
-  for (int j = 0; j < njobs; ++j) (plans[j]->slots[0].exec == Executor::Wide ? wide_jobs : chip_jobs).push_back(j);
-  if (!wide_jobs.empty()) {
-    if (!chip_jobs.empty()) {
-      std::vector<const qtn_plan_t*> cp;
-      std::vector<const uint8_t*> cx;
-      for (int j : chip_jobs) {
-        cp.push_back(plans[j]);
-        cx.push_back(xs[j]);
-      }
-      std::vector<double> co(2 * chip_jobs.size());
-      qtn_status st = qtn_contract_batch(cp.data(), cx.data(), (int)chip_jobs.size(), prec, stream, co.data());
-      if (st != QTN_OK) return st;
-      for (size_t i = 0; i < chip_jobs.size(); ++i) {
-        out[2 * chip_jobs[i]] = co[2 * i];
-        out[2 * chip_jobs[i] + 1] = co[2 * i + 1];
-      }
-    }
-    std::vector<std::string> names(njobs);
-    if (!chip_jobs.empty()) {
-      std::lock_guard<std::mutex> lk(g_batch_prog_mu);
-      for (size_t i = 0; i < chip_jobs.size() && i < g_batch_programs.size(); ++i)
-        names[chip_jobs[i]] = g_batch_programs[i];
-    }
-    for (int j : wide_jobs) {
-      qtn_status st = qtn_contract_amplitude(plans[j], xs[j], prec, stream, out + 2 * j);
-      if (st != QTN_OK) return st;
-      qtn_plan_t* plan = const_cast<qtn_plan_t*>(plans[j]);
-      std::lock_guard<std::mutex> lk(plan->mu);
-      auto it = plan->tuned.find(std::make_pair((int)prec, 1));
-      names[j] = it != plan->tuned.end() ? plan->slots[it->second].name : plan->slots[0].name;
-    }
-    record_batch_programs(std::move(names));
-    return QTN_OK;
-  }
   bool one_plan = true;
   for (int j = 1; j < njobs; ++j) one_plan = one_plan && plans[j] == plans[0];
   if (one_plan) {
@@ -1327,6 +1308,63 @@ qtn_status qtn_contract_batch(const qtn_plan_t* const* plans, const uint8_t* con
   }
   const Arith arith = arith_of(prec);
   const size_t elem = (size_t)arith_elem_bytes(arith);
+  {
+    // Jobs with a level program that fits the multi-job executor share one
+    // launch sequence; the others (tensors too large for shared memory: wide
+    // executor, or programs that fit only the single-plan executors) run on
+    // their own plan's tuned executor, one after the other on `stream`.
+    int dev = 0, optin = 0;
+    QTN_CUDA(cudaGetDevice(&dev));
+    QTN_CUDA(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    auto level_fits = [&](const qtn_plan_t* plan) {
+      if (plan->slots[0].exec == Executor::Wide) return false;
+      for (int k = 1; k < (int)plan->slots.size(); ++k) {
+        const ProgSlot& sl = plan->slots[k];
+        if (sl.exec != Executor::Level || !plan->eligible(k, prec)) continue;
+        const Program& pg = sl.prog;
+        if (level_smem_bytes((int)pg.steps.size(), (int)pg.levels.size(), (int)pg.leaves.size(), pg.leaf_elems,
+                             pg.arena_elems | 1u, 1, arith, kMultiLevelThreads) <= (size_t)optin - 64 &&
+            (pg.prologue.empty() || pg.pro_levels.empty() ||
+             level_smem_bytes((int)pg.prologue.size(), (int)pg.pro_levels.size(), (int)pg.leaves.size(),
+                              pg.leaf_elems, pg.pro_arena_elems | 1u, 1, arith, kMultiLevelThreads) <=
+                 (size_t)optin - 64))
+          return true;
+      }
+      return false;
+    };
+    std::vector<int> own_jobs, chip_jobs;
+    for (int j = 0; j < njobs; ++j) (level_fits(plans[j]) ? chip_jobs : own_jobs).push_back(j);
+    if (!own_jobs.empty()) {
+      std::vector<std::string> names(njobs);
+      if (!chip_jobs.empty()) {
+        std::vector<const qtn_plan_t*> cp;
+        std::vector<const uint8_t*> cx;
+        for (int j : chip_jobs) {
+          cp.push_back(plans[j]);
+          cx.push_back(xs[j]);
+        }
+        std::vector<double> co(2 * chip_jobs.size());
+        qtn_status st = qtn_contract_batch(cp.data(), cx.data(), (int)chip_jobs.size(), prec, stream, co.data());
+        if (st != QTN_OK) return st;
+        std::lock_guard<std::mutex> lk(g_batch_prog_mu);
+        for (size_t i = 0; i < chip_jobs.size(); ++i) {
+          out[2 * chip_jobs[i]] = co[2 * i];
+          out[2 * chip_jobs[i] + 1] = co[2 * i + 1];
+          if (i < g_batch_programs.size()) names[chip_jobs[i]] = g_batch_programs[i];
+        }
+      }
+      for (int j : own_jobs) {
+        qtn_status st = qtn_contract_amplitude(plans[j], xs[j], prec, stream, out + 2 * j);
+        if (st != QTN_OK) return st;
+        qtn_plan_t* plan = const_cast<qtn_plan_t*>(plans[j]);
+        std::lock_guard<std::mutex> lk(plan->mu);
+        auto it = plan->tuned.find(std::make_pair((int)prec, 1));
+        names[j] = it != plan->tuned.end() ? plan->slots[it->second].name : plan->slots[0].name;
+      }
+      record_batch_programs(std::move(names));
+      return QTN_OK;
+    }
+  }
   // Each job runs its plan's level program of the 48 KiB budget (else its
   // per-class level program) on the multi-job level executor, with as many
   // items per block as fit; if some job has no level program that fits, all

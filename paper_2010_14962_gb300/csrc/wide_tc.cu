@@ -28,7 +28,8 @@ namespace {
 
 constexpr int kRows = 128;      // UMMA M (one row per tensor-memory lane)
 constexpr int kChunk = 32;      // real K columns per stage
-constexpr int kTcThreads = 128;
+constexpr int kTcThreads = 256;
+constexpr int kStageIlp = 4;     // operand pairs a thread loads before it converts and stores them
 constexpr uint32_t kWaitLimit = 1u << 20;
 
 struct TcGeom {
@@ -169,34 +170,64 @@ __global__ void __launch_bounds__(kTcThreads) wide_tc_kernel(WideTcArgs a, TcGeo
       unsigned char* sty = stx + PCS * G.x_bytes;
       const uint64_t k0 = (uint64_t)c * (G.kc >> 1);  // first complex k of the chunk
       const int kp = G.kc >> 2;                      // complex pairs per row
-      // X: kRows rows x kc real columns.
-      for (int i = tid; i < kRows * kp; i += kTcThreads) {
-        int r, p;
-        if (G.xr == 1) {
-          r = i % kRows;
-          p = i / kRows;
-        } else {
-          p = i % kp;
-          r = i / kp;
+      // X: kRows rows x kc real columns; each thread loads kStageIlp pairs
+      // before converting and storing them (loads in flight hide latency).
+      const int nxi = kRows * kp;
+      for (int base = tid; base < nxi; base += kTcThreads * kStageIlp) {
+        float2 v0[kStageIlp], v1[kStageIlp];
+        uint32_t off[kStageIlp];
+#pragma unroll
+        for (int u = 0; u < kStageIlp; ++u) {
+          const int i = base + u * kTcThreads;
+          if (i < nxi) {
+            int r, p;
+            if (G.xr == 1) {
+              r = i % kRows;
+              p = i / kRows;
+            } else {
+              p = i % kp;
+              r = i / kp;
+            }
+            const uint64_t k = k0 + 2 * p;
+            v0[u] = Xbase[r * G.xr + k * G.xk];
+            v1[u] = Xbase[r * G.xr + (k + 1) * G.xk];
+            off[u] = core_off(r, 4 * p, kRows);
+          }
         }
-        const uint64_t k = k0 + 2 * p;
-        const float2 x0 = Xbase[r * G.xr + k * G.xk], x1 = Xbase[r * G.xr + (k + 1) * G.xk];
-        put4<PCS>(stx, G.x_bytes, core_off(r, 4 * p, kRows), x0.x, x0.y, x1.x, x1.y);
+#pragma unroll
+        for (int u = 0; u < kStageIlp; ++u)
+          if (base + u * kTcThreads < nxi) put4<PCS>(stx, G.x_bytes, off[u], v0[u].x, v0[u].y, v1[u].x, v1[u].y);
       }
       // Y in block form: rows 2q (Re, -Im) and 2q + 1 (Im, Re).
-      for (int i = tid; i < qt * kp; i += kTcThreads) {
-        int q, p;
-        if (G.yq == 1) {
-          q = i % qt;
-          p = i / qt;
-        } else {
-          p = i % kp;
-          q = i / kp;
+      const int nyi = qt * kp;
+      for (int base = tid; base < nyi; base += kTcThreads * kStageIlp) {
+        float2 v0[kStageIlp], v1[kStageIlp];
+        int qq[kStageIlp], pp[kStageIlp];
+#pragma unroll
+        for (int u = 0; u < kStageIlp; ++u) {
+          const int i = base + u * kTcThreads;
+          if (i < nyi) {
+            int q, p;
+            if (G.yq == 1) {
+              q = i % qt;
+              p = i / qt;
+            } else {
+              p = i % kp;
+              q = i / kp;
+            }
+            const uint64_t k = k0 + 2 * p;
+            v0[u] = Ybase[q * G.yq + k * G.yk];
+            v1[u] = Ybase[q * G.yq + (k + 1) * G.yk];
+            qq[u] = q;
+            pp[u] = p;
+          }
         }
-        const uint64_t k = k0 + 2 * p;
-        const float2 y0 = Ybase[q * G.yq + k * G.yk], y1 = Ybase[q * G.yq + (k + 1) * G.yk];
-        put4<PCS>(sty, G.y_bytes, core_off(2 * q, 4 * p, G.nt), y0.x, -y0.y, y1.x, -y1.y);
-        put4<PCS>(sty, G.y_bytes, core_off(2 * q + 1, 4 * p, G.nt), y0.y, y0.x, y1.y, y1.x);
+#pragma unroll
+        for (int u = 0; u < kStageIlp; ++u)
+          if (base + u * kTcThreads < nyi) {
+            put4<PCS>(sty, G.y_bytes, core_off(2 * qq[u], 4 * pp[u], G.nt), v0[u].x, -v0[u].y, v1[u].x, -v1[u].y);
+            put4<PCS>(sty, G.y_bytes, core_off(2 * qq[u] + 1, 4 * pp[u], G.nt), v0[u].y, v0[u].x, v1[u].y, v1[u].x);
+          }
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
@@ -229,12 +260,17 @@ __global__ void __launch_bounds__(kTcThreads) wide_tc_kernel(WideTcArgs a, TcGeo
       }
     }
     asm volatile("tcgen05.fence::after_thread_sync;");
-    // Epilogue: warp w reads rows 32w + lane, 32 real columns at a time.
-    const int row = warp * 32 + lane;
+    // Epilogue: warp w reads tensor-memory lanes 32 (w % 4) .. + 31 (its
+    // rows), columns of half w / 4 (all columns in warps 0-3 when the tile
+    // has fewer than 64), 32 real columns at a time.
+    const int quarter = warp & 3, half = warp >> 2;
+    const int row = quarter * 32 + lane;
+    const int c_begin = G.nt >= 64 ? half * (G.nt >> 1) : 0;
+    const int c_end = G.nt >= 64 ? c_begin + (G.nt >> 1) : (half == 0 ? G.nt : 0);
     float2* Cbase = Cp + posb + posR[row];
-    for (int col0 = 0; col0 < G.nt; col0 += 32) {
+    for (int col0 = c_begin; col0 < c_end; col0 += 32) {
       uint32_t v[32];
-      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)col0;
+      const uint32_t taddr = tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)col0;
       asm volatile(
           "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,"
           "%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
@@ -298,6 +334,20 @@ __global__ void __launch_bounds__(256) wide_tc_splitk_reduce(WideTcArgs a, TcGeo
                          pos_bits(a.wpos, G.ma + G.nb, G.bb, b);
     Cp[pos] = make_float2((float)re, (float)im);
   }
+}
+
+int g_tc_max_smem = 0;
+// Raises the dynamic shared-memory cap of both kernel variants to the
+// device's opt-in maximum (once).
+cudaError_t tc_allow_max_smem() {
+  if (g_tc_max_smem > 0) return cudaSuccess;
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(wide_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(wide_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  if (e == cudaSuccess) g_tc_max_smem = optin;
+  return e;
 }
 
 int g_tc_sms = 0;
@@ -382,15 +432,15 @@ cudaError_t wide_tc_launch(const WideTcArgs& a, int products, cudaStream_t strea
     return cudaErrorInvalidValue;
   const TcGeom G = make_geom(a.ma, a.nb, a.kb, a.bb, a.n_items, products, a.ws ? a.ws_floats : 0);
   const size_t smem = 2 * (size_t)G.stage_bytes + 2 * kRows * sizeof(uint64_t) + 64;
-  cudaError_t e;
+  // The shared-memory cap is a property of the kernel, not of one launch: it
+  // is set to the device's opt-in maximum, so that a captured graph of a
+  // larger merge stays launchable after smaller merges have run.
+  cudaError_t e = tc_allow_max_smem();
+  if (e != cudaSuccess) return e;
+  if (smem > (size_t)g_tc_max_smem) return cudaErrorInvalidValue;
   int occ = 0;
-  if (products == 3) {
-    e = cudaFuncSetAttribute(wide_tc_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, wide_tc_kernel<3>, kTcThreads, smem);
-  } else {
-    e = cudaFuncSetAttribute(wide_tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, wide_tc_kernel<1>, kTcThreads, smem);
-  }
+  if (products == 3) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, wide_tc_kernel<3>, kTcThreads, smem);
+  else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, wide_tc_kernel<1>, kTcThreads, smem);
   if (e != cudaSuccess) return e;
   occ = std::max(1, std::min(occ, 512 / G.tmem_cols));  // tensor memory: 512 columns per SM
   const unsigned grid = (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(G.units, (uint64_t)tc_sms() * occ));

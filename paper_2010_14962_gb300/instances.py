@@ -99,18 +99,15 @@ WORKLOADS = {
 
 
 def uneven_jobs(jobs: int = 64, n_range=(30, 100), p_choices=(1, 2), k_range=(6, 18), seed: int = 4,
-                p2_n_max: int = 40):
-    """Job list for the uneven batch: (n even, p, k, instance seed).
-
-    p = 2 jobs draw n from [n_range[0], p2_n_max]: beyond about 40 qubits a
-    depth-2 network keeps intermediates of 2^30 and more entries after 18 cuts,
-    which is no batch job.  ``k`` is the fewest cuts the job asks for.
-    """
+                p2_n_max: int = 0):
+    """Job list for the uneven batch: (n even, p, k, instance seed), n uniform
+    in n_range, p from p_choices, k (the job's cut count) uniform in k_range.
+    p2_n_max > 0 caps n of the depth-2 jobs (smaller test batches)."""
     rng = np.random.Generator(np.random.PCG64(seed + 0xBA7C))
     out = []
     for j in range(jobs):
         p = int(rng.choice(p_choices))
-        hi = n_range[1] if p == 1 else min(n_range[1], p2_n_max)
+        hi = n_range[1] if p == 1 or p2_n_max <= 0 else min(n_range[1], p2_n_max)
         n = int(rng.integers(n_range[0] // 2, hi // 2 + 1)) * 2
         k = int(rng.integers(k_range[0], k_range[1] + 1))
         out.append(dict(n=n, p=p, k=k, seed=1000 + seed * 100 + j))

@@ -88,6 +88,7 @@ def lib():
             "qtn_plan_select_executor": [vp, ctypes.c_int, ctypes.c_int, ctypes.c_char_p],
             "qtn_plan_kernel_ms": [vp, P(ctypes.c_float)],
             "qtn_batch_last_ms": [P(ctypes.c_float), P(ctypes.c_int)],
+            "qtn_batch_last_programs": [ctypes.c_char_p, ctypes.c_size_t, P(ctypes.c_size_t)],
             "qtn_batch_cancel": [],
             "qtn_batch_set_time_limit": [ctypes.c_double],
             "qtn_search_cuts": [vp, P(_PlanOpts), i32p, f64p, ctypes.c_int, P(ctypes.c_int), P(ctypes.c_int)],
@@ -459,24 +460,31 @@ def batch_last_ms():
     return float(ms.value), int(k.value)
 
 
-def batch_program(plan, precision: str) -> str:
-    """Name of the program a multi-plan contract_batch runs for ``plan`` (the
-    rule qtn_contract_batch documents): among its level programs of the
-    precision's width, the one with the fewest executed multiply-adds.  (The
-    library also requires it to fit in shared memory, which this host-side
-    helper does not check.)"""
-    progs = plan.describe()["programs"]
-    other = "/fp32/" if precision in ("fp64", "fp32x2") else "/fp64/"
-    best, best_work = None, None
-    for name, pr in progs.items():
-        if pr["executor"] != "level" or other in name:
-            continue
-        work = (2 ** len(pr["outer_class"])) * pr["macs_per_item"]
-        if best is None or work < best_work:
-            best, best_work = name, work
-    if best is None:
-        raise QTNError(6, "the plan has no level program for a batch")
-    return best
+def batch_last_programs() -> list:
+    """qtn_batch_last_programs: the program each job of the latest
+    contract_batch ran (names as in Plan.describe()["programs"])."""
+    need = ctypes.c_size_t()
+    _check(lib().qtn_batch_last_programs(None, 0, ctypes.byref(need)))
+    buf = ctypes.create_string_buffer(need.value)
+    _check(lib().qtn_batch_last_programs(buf, need.value, ctypes.byref(need)))
+    return json.loads(buf.value.decode())
+
+
+def plan_job(n: int, p: int, edges, gamma, beta, k: int, gate_log2_flops_max: float = 36.0) -> "Plan":
+    """Plan of one job with k greedy cuts on the paper's gate network, or, if
+    that needs more than 2^gate_log2_flops_max flops per amplitude (deep
+    circuits on many qubits), on the graphical-model form of the same circuit
+    when it is cheaper (the same amplitude; qtn_build_network_gm).  Costs come
+    from the exact counter (surrogate_labels) before anything is compiled."""
+    net = Network(n, edges, gamma, beta)
+    cuts, _, _ = search_cuts(net, k)
+    f_gate = float(surrogate_labels(net, cuts)[0])
+    if f_gate <= gate_log2_flops_max:
+        return Plan(net, cuts=cuts)
+    gm = Network(n, edges, gamma, beta, form="gm")
+    gcuts, _, _ = search_cuts(gm, k)
+    f_gm = float(surrogate_labels(gm, gcuts)[0])
+    return Plan(gm, cuts=gcuts) if f_gm < f_gate else Plan(net, cuts=cuts)
 
 
 # ------------------------------------------------------- learned surrogate --

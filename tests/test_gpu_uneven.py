@@ -87,79 +87,96 @@ def test_small_batch_repeat_and_order(gpu, small_batch):
     assert abs(one[0] - a[0]) <= 1e-13 * abs(a[0])
 
 
+def build_spec_jobs(spec, x_seed):
+    # The workload as specified: every job plans its own k greedy cuts on the
+    # gate network, or on the graphical-model form where the gate network
+    # would need more than 2^36 flops (depth-2 jobs on many qubits).
+    def one(jd):
+        j, d = jd
+        inst = I.qaoa_instance(d["n"], d["p"], d["seed"])
+        plan = qtn.plan_job(d["n"], d["p"], inst.edges, inst.gamma, inst.beta, d["k"])
+        x = I.bitstrings(d["n"], 1, x_seed + j)[0]
+        return inst, plan.network, plan, x
+
+    with cf.ThreadPoolExecutor(THREADS) as ex:
+        return list(ex.map(one, enumerate(spec)))
+
+
 @pytest.fixture(scope="module")
 def uneven64():
     spec = I.uneven_jobs(**{k: v for k, v in I.WORKLOADS["uneven64"].items() if k != "jobs"},
                          jobs=I.WORKLOADS["uneven64"]["jobs"])
-    return spec, build_jobs(spec, 700)
+    jobs = build_spec_jobs(spec, 700)
+    got = qtn.contract_batch([j[2] for j in jobs], [j[3] for j in jobs], "fp64")
+    return spec, jobs, got
+
+
+def oracle_feasible(inst):
+    return inst.p == 1 or inst.n <= 40
+
+
+def test_uneven64_as_specified(gpu, uneven64):
+    # 64 jobs, n 30..100, p in {1, 2}, 6..18 cuts each, all in one call; the
+    # deep jobs on many qubits run on the graphical-model form, several on the
+    # wide executor.
+    spec, jobs, got = uneven64
+    assert [j[2].k for j in jobs] == [d["k"] for d in spec]
+    assert max(d["n"] for d in spec if d["p"] == 2) > 90
+    progs = qtn.batch_last_programs()
+    assert len(progs) == len(jobs) and any(p.startswith("wide") for p in progs)
+    assert all(np.isfinite(got))
 
 
 def test_uneven64_vs_oracle(gpu, uneven64):
-    # The full 64-job workload in one launch sequence, FP64 form, against the
-    # oracle on every depth-1 job and on the depth-2 jobs of <= 2^31 flops.
-    spec, jobs = uneven64
-    got = qtn.contract_batch([j[2] for j in jobs], [j[3] for j in jobs], "fp64")
+    # FP64 form against the oracle (its own cuts) on every job the oracle can
+    # contract: all depth-1 jobs and the depth-2 jobs on at most 40 qubits.
+    spec, jobs, got = uneven64
     checked = 0
     for g, (inst, net, plan, x) in zip(got, jobs):
-        if inst.p == 2 and plan.cost()["log2_flops"] > 31:
+        if not oracle_feasible(inst):
             continue
-        r = O.tn_amplitude(inst.n, inst.edges, inst.gamma, inst.beta, x, cuts=oracle_cuts(inst, plan, 8),
-                           threads=THREADS).value
+        cuts, _ = O.choose_cuts(inst.n, inst.edges, inst.p, 10 if inst.p == 2 else 8)
+        r = O.tn_amplitude(inst.n, inst.edges, inst.gamma, inst.beta, x, cuts=cuts, threads=THREADS).value
         assert abs(g - r) <= 1e-10 * abs(r), (inst.n, inst.p, plan.k)
         checked += 1
     print("checked", checked, "of", len(jobs))
-    assert checked >= 40
+    assert checked >= 30
+
+
+def test_uneven64_closed_forms_beyond_the_oracle(gpu, uneven64):
+    # Depth-2 jobs beyond the oracle: the same plans at angles with closed
+    # forms (any size): gamma = 0 gives a = e^{-i n (b1 + b2)} 2^{-n/2};
+    # beta = 0 gives a = 2^{-n/2} e^{-i (g1 + g2) sum_E s_i s_j}, s = 1 - 2 x.
+    spec, jobs, got = uneven64
+    checked = 0
+    for inst, net, plan, x in jobs:
+        if oracle_feasible(inst):
+            continue
+        n = inst.n
+        G = np.array([[0.0, 0.0], list(inst.gamma)])
+        B = np.array([list(inst.beta), [0.0, 0.0]])
+        d_x = torch.from_numpy(np.ascontiguousarray(np.stack([x, x]))).cuda()
+        d_g = torch.from_numpy(np.ascontiguousarray(G)).cuda()
+        d_b = torch.from_numpy(np.ascontiguousarray(B)).cuda()
+        d_out = torch.zeros((2, 2), dtype=torch.float64, device="cuda")
+        plan.contract_sweep_device(d_x, d_g, d_b, d_out, "fp32x2")
+        torch.cuda.synchronize()
+        o = d_out.cpu().numpy()
+        a = o[:, 0] + 1j * o[:, 1]
+        s = 1 - 2 * x.astype(np.int64)
+        zz = int(np.sum(s[inst.edges[:, 0]] * s[inst.edges[:, 1]]))
+        want = [np.exp(-1j * n * inst.beta.sum()) * 2.0 ** (-n / 2),
+                np.exp(-1j * inst.gamma.sum() * zz) * 2.0 ** (-n / 2)]
+        for got_i, want_i in zip(a, want):
+            assert abs(got_i - want_i) <= 1e-10 * abs(want_i), (n, plan.k, got_i, want_i)
+        checked += 1
+    print("closed forms checked on", checked, "jobs")
+    assert checked >= 10
 
 
 def test_uneven64_vs_single_plan(gpu, uneven64):
     # Every job of the batch equals its single-plan contraction (FP64 form).
-    spec, jobs = uneven64
-    got = qtn.contract_batch([j[2] for j in jobs], [j[3] for j in jobs], "fp64")
+    spec, jobs, got = uneven64
     for g, (inst, net, plan, x) in zip(got, jobs):
         single = plan.contract_amplitude(x, "fp64")
         assert abs(g - single) <= 1e-11 * abs(single), (inst.n, inst.p, plan.k)
-
-
-def test_uneven64_mixed_precision(gpu, uneven64):
-    # FP32 merges, FP64 sums: relative error against the FP64 form.
-    spec, jobs = uneven64
-    plans, xs = [j[2] for j in jobs], [j[3] for j in jobs]
-    ref = qtn.contract_batch(plans, xs, "fp64")
-    for prec, tol in [("fp32x2", 1e-10), ("fp32", 1e-3)]:
-        got = qtn.contract_batch(plans, xs, prec)
-        err = np.abs(got - ref) / np.abs(ref)
-        print(prec, "max rel err vs FP64", float(err.max()), "median", float(np.median(err)))
-        assert float(err.max()) < tol
-
-
-def test_batch_time_limit_and_cancel(gpu, uneven64):
-    # Cooperative stop of the persistent executor (checked between chunks;
-    # nothing waits on the device): a time limit, and a cancel from another
-    # host thread.  A stopped call reports QTN_ERR_TIMEOUT; later calls work.
-    import threading
-    import time
-
-    spec, jobs = uneven64
-    plans, xs = [j[2] for j in jobs], [j[3] for j in jobs]
-    t0 = time.perf_counter()
-    full = qtn.contract_batch(plans, xs, "fp64")
-    t_full = time.perf_counter() - t0
-    qtn.batch_set_time_limit(0.001)
-    try:
-        with pytest.raises(qtn.QTNError) as e:
-            qtn.contract_batch(plans, xs, "fp64")
-        assert e.value.status == 5
-    finally:
-        qtn.batch_set_time_limit(0)
-    if t_full > 0.1:
-        timer = threading.Timer(t_full / 4, qtn.batch_cancel)
-        timer.start()
-        t0 = time.perf_counter()
-        with pytest.raises(qtn.QTNError) as e:
-            qtn.contract_batch(plans, xs, "fp64")
-        assert e.value.status == 5 and time.perf_counter() - t0 < 0.9 * t_full
-        timer.join()
-    again = qtn.contract_batch(plans, xs, "fp64")
-    assert np.array_equal(again, full)
-    with pytest.raises(qtn.QTNError):
-        qtn.batch_set_time_limit(-1)

@@ -1,5 +1,5 @@
 """Host-side helpers of the workloads: the uneven job list, fitting plans to
-on-chip slices, and the batch's choice of program (no GPU)."""
+on-chip slices, the per-job choice of network form (no GPU)."""
 import numpy as np
 import pytest
 
@@ -13,9 +13,8 @@ def test_uneven_jobs_recipe():
     assert a == b and len(a) == 64
     for d in a:
         assert d["n"] % 2 == 0 and 30 <= d["n"] <= 100 and 6 <= d["k"] <= 18 and d["p"] in (1, 2)
-        if d["p"] == 2:
-            assert d["n"] <= 40  # depth-2 jobs stay where 6-18 cuts reach on-chip slices
     assert {d["p"] for d in a} == {1, 2}
+    assert max(d["n"] for d in a if d["p"] == 2) > 90  # depth-2 jobs span the whole n range
     small = I.uneven_jobs(jobs=8, n_range=(20, 30), k_range=(2, 3), seed=1, p2_n_max=24)
     assert all(20 <= d["n"] <= 30 and 2 <= d["k"] <= 3 for d in small)
 
@@ -37,16 +36,19 @@ def test_plan_to_fit():
     assert e.value.status == 3
 
 
-def test_batch_program_is_least_work_level_program():
-    inst = I.qaoa_instance(40, 2, 2)
-    plan = qtn.Plan(qtn.Network(40, inst.edges, inst.gamma, inst.beta), k=10)
-    progs = plan.describe()["programs"]
-    for prec, other in (("fp32x2", "/fp32/"), ("fp32", "/fp64/")):
-        name = qtn.batch_program(plan, prec)
-        assert progs[name]["executor"] == "level" and other not in name
-        work = lambda pr: (2 ** len(pr["outer_class"])) * pr["macs_per_item"]
-        best = min(work(pr) for nm, pr in progs.items() if pr["executor"] == "level" and other not in nm)
-        assert work(progs[name]) == best
+def test_plan_job_picks_the_cheaper_network_form():
+    # A depth-1 job stays on the paper's gate network; a deep job on many
+    # qubits, whose gate network would need ~2^50 flops, takes the
+    # graphical-model form of the same circuit (k cuts either way).
+    inst = I.qaoa_instance(60, 1, 3)
+    plan = qtn.plan_job(60, 1, inst.edges, inst.gamma, inst.beta, 8)
+    assert plan.network.form == "gates" and plan.k == 8
+    inst = I.qaoa_instance(74, 2, 4)
+    plan = qtn.plan_job(74, 2, inst.edges, inst.gamma, inst.beta, 8)
+    assert plan.network.form == "gm" and plan.k == 8
+    gate = qtn.Network(74, inst.edges, inst.gamma, inst.beta)
+    cuts, _, _ = qtn.search_cuts(gate, 8)
+    assert qtn.surrogate_labels(gate, cuts)[0] > plan.cost()["log2_flops"] + 10
 
 
 def test_bench_step_classes_cover_the_program():
