@@ -115,10 +115,14 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+KERNEL_SOURCES = ("kernels.cu", "jit.cpp", "arith.cuh")  # what the benchmark's executor is generated and built from
+
+
 def kernel_source_hash() -> str:
     h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_2010_14962_gb300", "csrc", "kernels.cu"), "rb") as f:
-        h.update(f.read())
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2010_14962_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
@@ -131,7 +135,7 @@ def profiled_traffic(prec: str):
     except OSError:
         return None
     e = t.get(prec)
-    if not e or e.get("kernels_cu_sha256_16") != kernel_source_hash():
+    if not e or e.get("kernel_sources_sha256_16") != kernel_source_hash():
         return None
     return e.get("dram_bytes_per_launch")
 

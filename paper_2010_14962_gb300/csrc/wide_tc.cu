@@ -137,6 +137,22 @@ __global__ void __launch_bounds__(kTcThreads) wide_tc_kernel(WideTcArgs a, TcGeo
   const uint32_t lbo_x = (kRows / 8) * 128, lbo_y = (uint32_t)(G.nt / 8) * 128;
   uint32_t chunk_no = 0;
   bool failed = false;
+  // Each thread stages the same (row, pair) slots of every chunk: kStageIlp
+  // pairs of X (kRows rows x kc/4 pairs) and of Y (nt/2 rows x kc/4 pairs),
+  // ordered so that consecutive threads read consecutive elements.
+  const int kp = G.kc >> 2;  // complex pairs per row per chunk
+  int xr_[kStageIlp], xp[kStageIlp], yq_[kStageIlp], yp[kStageIlp];
+  bool xv[kStageIlp], yv[kStageIlp];
+#pragma unroll
+  for (int u = 0; u < kStageIlp; ++u) {
+    const int i = tid + u * kTcThreads;
+    xv[u] = i < kRows * kp;
+    yv[u] = i < (G.nt >> 1) * kp;
+    xr_[u] = G.xr == 1 ? i % kRows : i / kp;
+    xp[u] = G.xr == 1 ? i / kRows : i % kp;
+    yq_[u] = G.yq == 1 ? i % (G.nt >> 1) : i / kp;
+    yp[u] = G.yq == 1 ? i / (G.nt >> 1) : i % kp;
+  }
   for (uint64_t unit = blockIdx.x; unit < G.units && !failed; unit += gridDim.x) {
     const int split = (int)(unit % G.ksplit);
     const uint64_t bu = unit / G.ksplit;
@@ -157,8 +173,31 @@ __global__ void __launch_bounds__(kTcThreads) wide_tc_kernel(WideTcArgs a, TcGeo
     for (int i = tid; i < qt; i += kTcThreads) posQ[i] = pos_bits(a.wpos, qbit, qlog, ct * qt + i);
     const uint64_t posb = pos_bits(a.wpos, G.ma + G.nb, G.bb, b);
     const int c_lo = split * G.cps, c_hi = min(G.kchunks, c_lo + G.cps);
+    // Software pipeline: the operands of chunk c + 1 are loaded into
+    // registers before chunk c is converted and stored, so their global-load
+    // latency overlaps that work, the barrier and the MMA issue.
+    float2 cx0[kStageIlp], cx1[kStageIlp], cy0[kStageIlp], cy1[kStageIlp];
+    float2 nx0[kStageIlp], nx1[kStageIlp], ny0[kStageIlp], ny1[kStageIlp];
+    auto load_chunk = [&](int c, float2* x0, float2* x1, float2* y0, float2* y1) {
+      const uint64_t k0 = (uint64_t)c * (G.kc >> 1);  // first complex k of the chunk
+#pragma unroll
+      for (int u = 0; u < kStageIlp; ++u) {
+        if (xv[u]) {
+          const uint64_t k = k0 + 2 * xp[u];
+          x0[u] = Xbase[xr_[u] * G.xr + k * G.xk];
+          x1[u] = Xbase[xr_[u] * G.xr + (k + 1) * G.xk];
+        }
+        if (yv[u]) {
+          const uint64_t k = k0 + 2 * yp[u];
+          y0[u] = Ybase[yq_[u] * G.yq + k * G.yk];
+          y1[u] = Ybase[yq_[u] * G.yq + (k + 1) * G.yk];
+        }
+      }
+    };
+    if (c_lo < c_hi) load_chunk(c_lo, cx0, cx1, cy0, cy1);
     for (int c = c_lo; c < c_hi; ++c, ++chunk_no) {
       const int s = chunk_no & 1;
+      if (c + 1 < c_hi) load_chunk(c + 1, nx0, nx1, ny0, ny1);
       if (chunk_no >= 2) {
         const bool ok = bar_wait(&bar[s], ((chunk_no - 2) >> 1) & 1);
         if (__syncthreads_or(!ok)) {
@@ -168,66 +207,22 @@ __global__ void __launch_bounds__(kTcThreads) wide_tc_kernel(WideTcArgs a, TcGeo
       }
       unsigned char* stx = smem + s * G.stage_bytes;
       unsigned char* sty = stx + PCS * G.x_bytes;
-      const uint64_t k0 = (uint64_t)c * (G.kc >> 1);  // first complex k of the chunk
-      const int kp = G.kc >> 2;                      // complex pairs per row
-      // X: kRows rows x kc real columns; each thread loads kStageIlp pairs
-      // before converting and storing them (loads in flight hide latency).
-      const int nxi = kRows * kp;
-      for (int base = tid; base < nxi; base += kTcThreads * kStageIlp) {
-        float2 v0[kStageIlp], v1[kStageIlp];
-        uint32_t off[kStageIlp];
 #pragma unroll
-        for (int u = 0; u < kStageIlp; ++u) {
-          const int i = base + u * kTcThreads;
-          if (i < nxi) {
-            int r, p;
-            if (G.xr == 1) {
-              r = i % kRows;
-              p = i / kRows;
-            } else {
-              p = i % kp;
-              r = i / kp;
-            }
-            const uint64_t k = k0 + 2 * p;
-            v0[u] = Xbase[r * G.xr + k * G.xk];
-            v1[u] = Xbase[r * G.xr + (k + 1) * G.xk];
-            off[u] = core_off(r, 4 * p, kRows);
-          }
+      for (int u = 0; u < kStageIlp; ++u) {
+        if (xv[u]) put4<PCS>(stx, G.x_bytes, core_off(xr_[u], 4 * xp[u], kRows), cx0[u].x, cx0[u].y, cx1[u].x, cx1[u].y);
+        if (yv[u]) {
+          // Y in block form: rows 2q (Re, -Im) and 2q + 1 (Im, Re).
+          put4<PCS>(sty, G.y_bytes, core_off(2 * yq_[u], 4 * yp[u], G.nt), cy0[u].x, -cy0[u].y, cy1[u].x, -cy1[u].y);
+          put4<PCS>(sty, G.y_bytes, core_off(2 * yq_[u] + 1, 4 * yp[u], G.nt), cy0[u].y, cy0[u].x, cy1[u].y,
+                    cy1[u].x);
         }
-#pragma unroll
-        for (int u = 0; u < kStageIlp; ++u)
-          if (base + u * kTcThreads < nxi) put4<PCS>(stx, G.x_bytes, off[u], v0[u].x, v0[u].y, v1[u].x, v1[u].y);
       }
-      // Y in block form: rows 2q (Re, -Im) and 2q + 1 (Im, Re).
-      const int nyi = qt * kp;
-      for (int base = tid; base < nyi; base += kTcThreads * kStageIlp) {
-        float2 v0[kStageIlp], v1[kStageIlp];
-        int qq[kStageIlp], pp[kStageIlp];
 #pragma unroll
-        for (int u = 0; u < kStageIlp; ++u) {
-          const int i = base + u * kTcThreads;
-          if (i < nyi) {
-            int q, p;
-            if (G.yq == 1) {
-              q = i % qt;
-              p = i / qt;
-            } else {
-              p = i % kp;
-              q = i / kp;
-            }
-            const uint64_t k = k0 + 2 * p;
-            v0[u] = Ybase[q * G.yq + k * G.yk];
-            v1[u] = Ybase[q * G.yq + (k + 1) * G.yk];
-            qq[u] = q;
-            pp[u] = p;
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < kStageIlp; ++u)
-          if (base + u * kTcThreads < nyi) {
-            put4<PCS>(sty, G.y_bytes, core_off(2 * qq[u], 4 * pp[u], G.nt), v0[u].x, -v0[u].y, v1[u].x, -v1[u].y);
-            put4<PCS>(sty, G.y_bytes, core_off(2 * qq[u] + 1, 4 * pp[u], G.nt), v0[u].y, v0[u].x, v1[u].y, v1[u].x);
-          }
+      for (int u = 0; u < kStageIlp; ++u) {
+        cx0[u] = nx0[u];
+        cx1[u] = nx1[u];
+        cy0[u] = ny0[u];
+        cy1[u] = ny1[u];
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       __syncthreads();
