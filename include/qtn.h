@@ -323,8 +323,15 @@ qtn_status qtn_plan_executor(const qtn_plan_t* plan, const char** name);
 
 /* Overrides the autotuner: contraction calls of (prec, nx) use the executor
  * called `name` (one of the names in qtn_plan_describe's "programs", other
- * than the per-slice program).  Fails with QTN_ERR_INVALID_ARG for an unknown
- * name or one compiled for the other precision. */
+ * than the per-slice program).  "<level program>/jit" and "<level
+ * program>/jit2" name the kernel generated at run time for that level
+ * program and precision (fp64, fp32, fp32x2): every merge of Eq. 1 as
+ * straight code; "/jit2" with the two-phase schedule (the levels of small
+ * merges run on more items at once, their results parked in a device scratch
+ * area the plan owns, then reloaded for the later levels).  Fails with
+ * QTN_ERR_INVALID_ARG for an unknown name or one compiled for the other
+ * precision, QTN_ERR_UNSUPPORTED if no run-time compiler is available or no
+ * two-phase schedule fits the program. */
 qtn_status qtn_plan_select_executor(const qtn_plan_t* plan, qtn_precision prec, int nx, const char* name);
 
 /* Kernel timing for measurement: when on, qtn_contract_amplitudes_device

@@ -207,6 +207,10 @@ struct ProgSlot {
   DeviceProgram dprog;
   bool uploaded = false;
   int jit_arith = -1;     // LevelJit: the arithmetic its generated kernel runs
+  // LevelJit: the generated schedule (split level 0: single-phase) and the
+  // estimated slot-steps per item of it and of the single-phase form.
+  int jit_split_level = 0, jit_log2_forest = 0;
+  double jit_est = 0, jit_est_single = 0;
   // Wide: device state per (arithmetic, bit strings per launch).
   std::map<std::pair<int, int>, std::shared_ptr<WideState>> wide_states;
   uint64_t items() const { return 1ull << prog.n_outer; }
@@ -224,12 +228,13 @@ uint64_t wide_budget_bytes() {
 // captured graph (instantiating one costs memory in proportion).
 constexpr uint64_t kWideGraphMaxLaunches = 4096;
 
-// Suffix of a specialised executor's name for an arithmetic.
-const char* jit_suffix(Arith a) {
+// Suffix of a specialised executor's name for an arithmetic and schedule
+// ("/jit": single-phase, "/jit2": two-phase).
+const char* jit_suffix(Arith a, bool two_phase = false) {
   switch (a) {
-    case Arith::F64: return "/jit-fp64";
-    case Arith::F32: return "/jit-fp32";
-    case Arith::F32X2: return "/jit-fp32x2";
+    case Arith::F64: return two_phase ? "/jit2-fp64" : "/jit-fp64";
+    case Arith::F32: return two_phase ? "/jit2-fp32" : "/jit-fp32";
+    case Arith::F32X2: return two_phase ? "/jit2-fp32x2" : "/jit-fp32x2";
     default: return nullptr;
   }
 }
@@ -257,6 +262,8 @@ struct qtn_plan {
   void* d_leaf_tables = nullptr;
   Partial* d_partials = nullptr;
   int* d_err = nullptr;
+  void* d_jit_scratch = nullptr;
+  size_t cap_scratch = 0;  // bytes per block of d_jit_scratch
   uint8_t* d_x_stage = nullptr;
   double2* d_out_stage = nullptr;
   Partial* d_raw_stage = nullptr;
@@ -280,6 +287,7 @@ struct qtn_plan {
     cudaFree(d_leaf_tables);
     cudaFree(d_partials);
     cudaFree(d_err);
+    cudaFree(d_jit_scratch);
     cudaFree(d_x_stage);
     cudaFree(d_out_stage);
     cudaFree(d_raw_stage);
@@ -288,12 +296,14 @@ struct qtn_plan {
     d_leaf_tables = nullptr;
     d_partials = nullptr;
     d_err = nullptr;
+    d_jit_scratch = nullptr;
     d_x_stage = nullptr;
     d_out_stage = nullptr;
     d_raw_stage = nullptr;
     h_x_pinned = nullptr;
     h_out_pinned = nullptr;
     cap_nx = cap_blocks = 0;
+    cap_scratch = 0;
   }
 
   qtn_status ensure_device() {
@@ -404,7 +414,9 @@ struct qtn_plan {
   }
 
   qtn_status ensure_workspace(int nx, int blocks) {
-    if (nx <= cap_nx && blocks <= cap_blocks) return QTN_OK;
+    size_t scratch = 0;
+    for (const ProgSlot& s : slots) scratch = std::max(scratch, s.dprog.jit_scratch_bytes);
+    if (nx <= cap_nx && blocks <= cap_blocks && scratch <= cap_scratch) return QTN_OK;
     for (auto& g : graphs) cudaGraphExecDestroy(g.second);
     graphs.clear();
     int nnx = std::max(nx, cap_nx), nb = std::max(blocks, cap_blocks);
@@ -414,6 +426,8 @@ struct qtn_plan {
     QTN_CUDA(cudaMalloc((void**)&d_partials, (size_t)nnx * nb * sizeof(Partial)));
     QTN_CUDA(cudaMalloc((void**)&d_err, sizeof(int)));
     QTN_CUDA(cudaMemset(d_err, 0, sizeof(int)));
+    if (scratch) QTN_CUDA(cudaMalloc(&d_jit_scratch, (size_t)nnx * nb * scratch));
+    cap_scratch = scratch;
     QTN_CUDA(cudaMalloc((void**)&d_x_stage, (size_t)nnx * net.n));
     QTN_CUDA(cudaMemset(d_x_stage, 0, (size_t)nnx * net.n));
     QTN_CUDA(cudaMalloc((void**)&d_out_stage, (size_t)nnx * sizeof(double2)));
@@ -435,6 +449,7 @@ struct qtn_plan {
     b.leaf_tables = d_leaf_tables;
     b.partials = d_partials;
     b.err = d_err;
+    b.jit_scratch = d_jit_scratch;
     return b;
   }
 
@@ -481,8 +496,8 @@ struct qtn_plan {
 
   // The specialised variant of level slot `base` for arithmetic `a` (created,
   // generated, compiled and uploaded on first use); its index in *out.
-  qtn_status make_jit_slot(int base, Arith a, int* out) {
-    const char* suf = jit_suffix(a);
+  qtn_status make_jit_slot(int base, Arith a, bool two_phase, int* out) {
+    const char* suf = jit_suffix(a, two_phase);
     if (!suf || slots[base].exec != Executor::Level)
       return fail(QTN_ERR_UNSUPPORTED, "no specialised executor for this program and precision");
     const std::string name = slots[base].name + suf;
@@ -500,8 +515,9 @@ struct qtn_plan {
     js.exec = Executor::LevelJit;
     js.jit_arith = (int)a;
     JitLevelShape shape;
-    if (!jit_level_shape(js.prog, arith_elem_bytes(a), js.threads, js.blocks_per_sm, &shape))
-      return fail(QTN_ERR_UNSUPPORTED, "the program's items do not fit in shared memory");
+    if (!jit_level_shape(js.prog, arith_elem_bytes(a), js.threads, js.blocks_per_sm, two_phase, &shape))
+      return fail(QTN_ERR_UNSUPPORTED, two_phase ? "no two-phase schedule fits this program"
+                                                 : "the program's items do not fit in shared memory");
     std::string err;
     const std::string src = jit_level_source(js.prog, a, shape, &err);
     if (src.empty()) return fail(QTN_ERR_UNSUPPORTED, "specialised executor: " + err);
@@ -514,6 +530,11 @@ struct qtn_plan {
     js.dprog.jit_kernel = kernel;
     js.dprog.jit_log2_items = shape.log2_items;
     js.dprog.jit_smem = shape.smem;
+    js.dprog.jit_scratch_bytes = shape.scratch_elems_per_block * (size_t)arith_elem_bytes(a);
+    js.jit_split_level = shape.split_level;
+    js.jit_log2_forest = shape.log2_forest;
+    js.jit_est = shape.est_cost;
+    js.jit_est_single = shape.est_cost_single;
     slots.push_back(std::move(js));
     *out = (int)slots.size() - 1;
     return QTN_OK;
@@ -567,9 +588,12 @@ struct qtn_plan {
         if (slots[si].exec == Executor::Level && times[si] >= 0) lv.push_back(si);
       std::sort(lv.begin(), lv.end(), [&](int x, int y) { return times[x] < times[y]; });
       if ((int)lv.size() > kJitCandidates) lv.resize(kJitCandidates);
-      for (int base : lv) {
+      std::vector<std::pair<int, bool>> cand;
+      for (int base : lv)
+        for (bool two : {false, true}) cand.emplace_back(base, two);
+      for (auto [base, two] : cand) {
         int si = -1;
-        if (make_jit_slot(base, arith_of(prec), &si) != QTN_OK) continue;
+        if (make_jit_slot(base, arith_of(prec), two, &si) != QTN_OK) continue;
         times.resize(slots.size(), -1.0);
         ExecShape sh;
         if (prepare(si, prec, nx, slots[si].items(), &sh) != QTN_OK) continue;
@@ -1057,9 +1081,12 @@ qtn_status qtn_plan_select_executor(const qtn_plan_t* cplan, qtn_precision prec,
   if (!plan || !name || nx <= 0) return fail(QTN_ERR_INVALID_ARG, "bad argument");
   std::lock_guard<std::mutex> lk(plan->mu);
   std::string want = name;
-  // "<level program>/jit": that program's specialised executor for prec.
-  if (want.size() > 4 && want.compare(want.size() - 4, 4, "/jit") == 0) {
-    const std::string base = want.substr(0, want.size() - 4);
+  // "<level program>/jit" ("/jit2"): that program's specialised executor for
+  // prec, single-phase (two-phase).
+  const bool jit1 = want.size() > 4 && want.compare(want.size() - 4, 4, "/jit") == 0;
+  const bool jit2 = want.size() > 5 && want.compare(want.size() - 5, 5, "/jit2") == 0;
+  if (jit1 || jit2) {
+    const std::string base = want.substr(0, want.size() - (jit2 ? 5 : 4));
     int bi = -1, si = -1;
     for (int k = 1; k < (int)plan->slots.size(); ++k)
       if (plan->slots[k].name == base) bi = k;
@@ -1067,7 +1094,7 @@ qtn_status qtn_plan_select_executor(const qtn_plan_t* cplan, qtn_precision prec,
     if (!plan->eligible(bi, prec)) return fail(QTN_ERR_INVALID_ARG, "executor not available for this precision");
     qtn_status st = plan->ensure_device();
     if (st != QTN_OK) return st;
-    st = plan->make_jit_slot(bi, arith_of(prec), &si);
+    st = plan->make_jit_slot(bi, arith_of(prec), jit2, &si);
     if (st != QTN_OK) return st;
     want = plan->slots[si].name;
   }
@@ -1703,6 +1730,13 @@ qtn_status qtn_plan_describe(const qtn_plan_t* plan, char* buf, size_t cap, size
     const bool wide_pg = plan->slots[which].exec == Executor::Wide;
     o << "],\"pro_arena_elems\":" << (wide_pg ? pg.wide_pro_arena_elems : pg.pro_arena_elems)
       << ",\"macs_prologue\":" << pg.macs_prologue;
+    if (plan->slots[which].exec == Executor::LevelJit) {
+      const ProgSlot& js = plan->slots[which];
+      o << ",\"jit\":{\"split_level\":" << js.jit_split_level << ",\"log2_items\":" << js.dprog.jit_log2_items
+        << ",\"log2_forest\":" << js.jit_log2_forest << ",\"est_slot_steps_per_item\":" << js.jit_est
+        << ",\"est_single_phase\":" << js.jit_est_single << ",\"scratch_bytes_per_block\":"
+        << js.dprog.jit_scratch_bytes << "}";
+    }
     if (wide_pg) {
       o << ",\"wide_arena_elems\":" << pg.wide_arena_elems << ",\"wide_states\":[";
       bool fs = true;

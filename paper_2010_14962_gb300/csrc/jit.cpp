@@ -159,22 +159,132 @@ void emit_merge(std::ostringstream& o, const Program& pg, const DevStep& st, uin
   }
 }
 
+// Per-level loop layout for 2^lg items per pass: each merge's first unit in
+// the level's flat unit range, its unit size 2^ulog and its k split 2^ks
+// (root only: its outputs are summed, not stored, so its sum over k is split
+// until the level has a slot for every thread, beyond the four-output
+// table's split where that applies).
+struct MergeGen {
+  int j;
+  uint32_t beg;
+  int ulog, ks;
+};
+struct LevelGen {
+  std::vector<MergeGen> m;
+  uint64_t units = 0;  // slots per item
+  uint64_t work = 0;   // largest multiply-add count of one slot
+};
+
+LevelGen level_gen(const Program& pg, size_t l, int UL, int lg, int threads) {
+  LevelGen g;
+  const DevLevel& lv = pg.levels[l];
+  for (int j = lv.first; j < lv.first + lv.count; ++j) {
+    const DevStep& st = pg.steps[j];
+    const int rc0 = st.ma + st.nb + st.bb;
+    int ks = 0;
+    if (st.flags & STEP_ROOT) {
+      ks = UL ? std::min<int>(st.kb, kRootSplitLog2) : 0;
+      auto slots = [&](int k) { return ((uint64_t)1 << (rc0 + k - std::min(rc0 + k, UL))) << lg; };
+      while (ks < st.kb && slots(ks) < (uint64_t)threads) ++ks;
+    }
+    const int rc = rc0 + ks, ulog = std::min(rc, UL);
+    g.m.push_back(MergeGen{j, (uint32_t)g.units, ulog, ks});
+    g.units += (uint64_t)1 << (rc - ulog);
+    g.work = std::max<uint64_t>(g.work, ((uint64_t)1 << ulog) << (st.kb - ks));
+  }
+  return g;
+}
+
+// Estimated time of one pass of level l over 2^lg items, in units of one
+// slot multiply-add: rounds of the block over the slots times the longest
+// slot, plus one for the barrier.
+double level_cost(const Program& pg, size_t l, int UL, int lg, int threads) {
+  const LevelGen g = level_gen(pg, l, UL, lg, threads);
+  const uint64_t slots = g.units << lg;
+  return (double)((slots + threads - 1) / threads) * (double)g.work + 1.0;
+}
+
 // Binary dispatch over the merges [lo, hi) of a level by unit index uf.
-void emit_dispatch(std::ostringstream& o, const Program& pg, const std::vector<int>& js,
-                   const std::vector<uint32_t>& beg, const std::vector<int>& ulog, const std::vector<int>& ks, int lo,
-                   int hi, int depth) {
+void emit_dispatch(std::ostringstream& o, const Program& pg, const std::vector<MergeGen>& ms, int lo, int hi) {
   if (hi - lo == 1) {
-    o << "    {  // merge " << js[lo] << "\n";
-    emit_merge(o, pg, pg.steps[js[lo]], beg[lo], ulog[lo], ks[lo]);
+    const MergeGen& g = ms[lo];
+    o << "    {  // merge " << g.j << "\n";
+    emit_merge(o, pg, pg.steps[g.j], g.beg, g.ulog, g.ks);
     o << "    }\n";
     return;
   }
   const int mid = (lo + hi) / 2;
-  o << "    if (uf < " << beg[mid] << "u) {\n";
-  emit_dispatch(o, pg, js, beg, ulog, ks, lo, mid, depth + 1);
+  o << "    if (uf < " << ms[mid].beg << "u) {\n";
+  emit_dispatch(o, pg, ms, lo, mid);
   o << "    } else {\n";
-  emit_dispatch(o, pg, js, beg, ulog, ks, mid, hi, depth + 1);
+  emit_dispatch(o, pg, ms, mid, hi);
   o << "    }\n";
+}
+
+// One level over 2^lg items of `count` (a variable of the generated code)
+// with arenas `stride` elements apart; s0 is the first item's slice.
+void emit_level(std::ostringstream& o, const Program& pg, size_t l, int UL, int lg, uint32_t stride,
+                const char* count, int threads) {
+  const LevelGen g = level_gen(pg, l, UL, lg, threads);
+  bool leaf_operand = false;
+  for (const MergeGen& m : g.m) leaf_operand |= (pg.steps[m.j].flags & (STEP_A_LEAF | STEP_B_LEAF)) != 0;
+  o << "    // level " << l << "\n";
+  o << "    for (unsigned f = threadIdx.x; f < " << (g.units << lg) << "u; f += " << threads << "u) {\n";
+  o << "      const unsigned item = f & " << ((1u << lg) - 1u) << "u, uf = f >> " << lg << ";\n";
+  o << "      if (item >= " << count << ") continue;\n";
+  if (leaf_operand) o << "      const unsigned long long s = s0 + item;\n";
+  o << "      V* arena = s_arena + item * " << stride << "u;\n";
+  emit_dispatch(o, pg, g.m, 0, (int)g.m.size());
+  o << "    }\n    __syncthreads();\n";
+}
+
+// Tensors made below level `split` and read at or above it (offset, size),
+// and the arena extent of the levels below `split`.
+struct Crossing {
+  uint32_t off, size, at;
+};
+bool crossings(const Program& pg, size_t split, std::vector<Crossing>* out, uint32_t* extent) {
+  std::vector<int> level_of(pg.steps.size());
+  for (size_t l = 0; l < pg.levels.size(); ++l)
+    for (int j = pg.levels[l].first; j < pg.levels[l].first + pg.levels[l].count; ++j) level_of[j] = (int)l;
+  // Last writer of each arena offset, updated at the end of each level (the
+  // merges of one level read before any of them writes).
+  std::vector<std::pair<uint32_t, int>> last;
+  auto writer = [&](uint32_t off) {
+    for (auto it = last.rbegin(); it != last.rend(); ++it)
+      if (it->first == off) return it->second;
+    return -1;
+  };
+  std::vector<char> crossing(pg.steps.size(), 0);
+  uint32_t ext = 0;
+  for (size_t l = 0; l < pg.levels.size(); ++l) {
+    const DevLevel& lv = pg.levels[l];
+    for (int j = lv.first; j < lv.first + lv.count; ++j) {
+      const DevStep& st = pg.steps[j];
+      const uint32_t ops[2] = {st.a, st.b};
+      const bool leaf[2] = {(st.flags & STEP_A_LEAF) != 0, (st.flags & STEP_B_LEAF) != 0};
+      for (int t = 0; t < 2; ++t) {
+        if (leaf[t]) continue;
+        const int w = writer(ops[t]);
+        if (w < 0) return false;  // an arena operand nothing wrote
+        if (level_of[w] < (int)split && l >= split) crossing[w] = 1;
+      }
+      if (l < split && !(st.flags & STEP_ROOT))
+        ext = std::max<uint32_t>(ext, st.c + (1u << (st.ma + st.nb + st.bb)));
+    }
+    for (int j = lv.first; j < lv.first + lv.count; ++j)
+      if (!(pg.steps[j].flags & STEP_ROOT)) last.emplace_back(pg.steps[j].c, j);
+  }
+  out->clear();
+  uint32_t at = 0;
+  for (size_t j = 0; j < pg.steps.size(); ++j)
+    if (crossing[j]) {
+      const uint32_t z = 1u << (pg.steps[j].ma + pg.steps[j].nb + pg.steps[j].bb);
+      out->push_back(Crossing{pg.steps[j].c, z, at});
+      at += z;
+    }
+  *extent = ext;
+  return true;
 }
 
 }  // namespace
@@ -185,30 +295,83 @@ bool jit_available(std::string* why) {
   return n.ok;
 }
 
-bool jit_level_shape(const Program& pg, int elem_bytes, int threads, int blocks_per_sm, JitLevelShape* out) {
+bool jit_level_shape(const Program& pg, int elem_bytes, int threads, int blocks_per_sm, bool two_phase,
+                     JitLevelShape* out) {
   int dev = 0, max_optin = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
   cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   const int bps = blocks_per_sm > 1 ? blocks_per_sm : 1;
   const size_t cap = std::min<size_t>((size_t)max_optin, (size_t)per_sm / bps - 1024);
+  return jit_level_schedule(pg, elem_bytes, threads, bps, cap, two_phase, out);
+}
+
+bool jit_level_schedule(const Program& pg, int elem_bytes, int threads, int bps, size_t cap, bool two_phase,
+                        JitLevelShape* out) {
   JitLevelShape sh;
   sh.threads = threads;
   sh.blocks_per_sm = bps;
   sh.arena_stride = pg.arena_elems | 1u;
   const size_t table = align16((size_t)pg.leaf_elems * elem_bytes);
-  for (int lg = 5; lg >= 0; --lg) {
-    const size_t arena = (size_t)sh.arena_stride * ((size_t)1 << lg) * elem_bytes;
-    const size_t red = (size_t)threads * 32;  // one Partial per thread, overlaid on the arenas
-    const size_t total = table + align16(std::max(arena, red));
-    if (total <= cap) {
+  const size_t red = (size_t)threads * 32;  // one Partial per thread, overlaid on the arenas
+  auto fits = [&](uint32_t stride, int lg, size_t* total) {
+    const size_t arena = (size_t)stride * ((size_t)1 << lg) * elem_bytes;
+    *total = table + align16(std::max(arena, red));
+    return *total <= cap;
+  };
+  bool found = false;
+  for (int lg = 5; lg >= 0 && !found; --lg)
+    if (fits(sh.arena_stride, lg, &sh.smem)) {
       sh.log2_items = lg;
-      sh.smem = total;
-      *out = sh;
-      return true;
+      found = true;
+    }
+  if (!found) return false;
+  // Two-phase schedule: the split level and the item count of the levels
+  // below it with the fewest estimated slot-steps per item (the single-phase
+  // estimate is kept for comparison).
+  const int UL = elem_bytes == 16 ? 0 : kLevelUnitLog2;
+  const size_t nl = pg.levels.size();
+  std::vector<double> cost_s(nl);
+  for (size_t l = 0; l < nl; ++l) cost_s[l] = level_cost(pg, l, UL, sh.log2_items, threads);
+  double single = 0;
+  for (double c : cost_s) single += c;
+  single /= (double)(1 << sh.log2_items);
+  sh.est_cost = sh.est_cost_single = single;
+  if (!two_phase) {
+    *out = sh;
+    return true;
+  }
+  double best = 0;
+  double above = single;  // levels >= split, per item
+  for (size_t split = 1; split < nl; ++split) {
+    above -= cost_s[split - 1] / (double)(1 << sh.log2_items);
+    std::vector<Crossing> cr;
+    uint32_t ext = 0;
+    if (!crossings(pg, split, &cr, &ext)) break;
+    uint32_t cross = 0;
+    for (const Crossing& c : cr) cross += c.size;
+    const uint32_t fstride = ext | 1u;
+    for (int lf = sh.log2_items + 1; lf <= 5; ++lf) {
+      size_t total = 0;
+      if (!fits(fstride, lf, &total) || total > sh.smem) continue;
+      double below = 0;
+      for (size_t l = 0; l < split; ++l) below += level_cost(pg, l, UL, lf, threads);
+      // parking and reloading: two element copies per parked element
+      const double est = below / (double)(1 << lf) + above + 2.0 * cross / (double)threads / 4.0;
+      if (!sh.split_level || est < best) {
+        best = est;
+        sh.est_cost = est;
+        sh.split_level = (int)split;
+        sh.log2_forest = lf;
+        sh.forest_stride = fstride;
+        sh.cross_elems = cross;
+        sh.scratch_elems_per_block = (size_t)cross << lf;
+      }
     }
   }
-  return false;
+  if (!sh.split_level) return false;
+  *out = sh;
+  return true;
 }
 
 std::string jit_level_source(const Program& pg, Arith a, const JitLevelShape& sh, std::string* err) {
@@ -228,19 +391,28 @@ std::string jit_level_source(const Program& pg, Arith a, const JitLevelShape& sh
     }
   const int elem = arith_elem_bytes(a);
   const int UL = elem == 16 ? 0 : kLevelUnitLog2;
-  const int US = UL ? 1 : 0;
+  const int T = sh.threads;
   const uint32_t I = 1u << sh.log2_items;
   const size_t table = align16((size_t)pg.leaf_elems * elem);
+  const size_t split = (size_t)sh.split_level;
+  std::vector<Crossing> cr;
+  if (split) {
+    uint32_t ext = 0;
+    if (!crossings(pg, split, &cr, &ext) || (ext | 1u) != sh.forest_stride) {
+      *err = "two-phase schedule does not match the program";
+      return "";
+    }
+  }
   std::ostringstream o;
   o << "// Generated: specialised level executor (" << pg.steps.size() << " merges, " << pg.levels.size()
-    << " levels).\n";
+    << " levels" << (split ? ", two-phase" : "") << ").\n";
   o << "struct __align__(16) Partial {\n  double re, im, cre, cim;\n"
        "  static __device__ __forceinline__ Partial make(double a, double b, double c, double d) {\n"
        "    Partial p; p.re = a; p.im = b; p.cre = c; p.cim = d; return p;\n  }\n};\n";
   o << kArithSource << "\n";
   o << "typedef " << vt << " V;\ntypedef CplxOps<V> Ops;\n";
-  o << "extern \"C\" __global__ void __launch_bounds__(" << sh.threads << ", " << sh.blocks_per_sm
-    << ") qtn_level_jit(const V* __restrict__ leaf_tables, Partial* __restrict__ partials,\n"
+  o << "extern \"C\" __global__ void __launch_bounds__(" << T << ", " << sh.blocks_per_sm
+    << ") qtn_level_jit(const V* __restrict__ leaf_tables, Partial* __restrict__ partials, V* __restrict__ scratch,\n"
        "    unsigned long long slice_lo, unsigned long long slice_hi, int blocks_per_x) {\n";
   o << "  extern __shared__ __align__(16) unsigned char smem[];\n";
   o << "  V* s_lt = reinterpret_cast<V*>(smem);\n";
@@ -249,43 +421,56 @@ std::string jit_level_source(const Program& pg, Arith a, const JitLevelShape& sh
   o << "  const int xi = blockIdx.x / blocks_per_x, bx = blockIdx.x % blocks_per_x;\n";
   o << "  {\n    const unsigned* src = reinterpret_cast<const unsigned*>(leaf_tables + (size_t)xi * "
     << pg.leaf_elems << "u);\n    unsigned* dst = reinterpret_cast<unsigned*>(s_lt);\n"
-    << "    for (unsigned i = threadIdx.x; i < " << (size_t)pg.leaf_elems * elem / 4 << "u; i += " << sh.threads
+    << "    for (unsigned i = threadIdx.x; i < " << (size_t)pg.leaf_elems * elem / 4 << "u; i += " << T
     << "u) dst[i] = src[i];\n  }\n  __syncthreads();\n";
   o << "  double sr = 0.0, si = 0.0, cr = 0.0, ci = 0.0;\n";
-  o << "  const unsigned long long S = slice_hi - slice_lo;\n";
-  o << "  for (unsigned long long i0 = (unsigned long long)bx * " << I << "ull; i0 < S; i0 += (unsigned long long)"
-    << "blocks_per_x * " << I << "ull) {\n";
-  o << "    const unsigned nI = (S - i0) < " << I << "ull ? (unsigned)(S - i0) : " << I << "u;\n";
-  o << "    const unsigned long long s0 = slice_lo + i0;\n";
-  for (size_t l = 0; l < pg.levels.size(); ++l) {
-    const DevLevel& lv = pg.levels[l];
-    std::vector<int> js;
-    std::vector<uint32_t> beg;
-    std::vector<int> ulog, ks;
-    for (int j = lv.first; j < lv.first + lv.count; ++j) {
-      const DevStep& st = pg.steps[j];
-      const int k_s = UL ? ((st.flags & STEP_ROOT) ? std::min<int>(st.kb, kRootSplitLog2) : 0) : 0;
-      const int rc = st.ma + st.nb + st.bb + k_s;
-      js.push_back(j);
-      beg.push_back(pg.out_start[2 * j + US]);
-      ulog.push_back(std::min(rc, UL));
-      ks.push_back(k_s);
+  // The block's share of the slices: a contiguous range, sizes within one.
+  o << "  const unsigned long long S = slice_hi - slice_lo, q = S / (unsigned long long)blocks_per_x,\n"
+       "      r = S % (unsigned long long)blocks_per_x;\n"
+       "  const unsigned long long ib = (unsigned long long)bx * q + ((unsigned long long)bx < r ? bx : r),\n"
+       "      ie = ib + q + ((unsigned long long)bx < r ? 1ull : 0ull);\n";
+  if (!split) {
+    o << "  for (unsigned long long i0 = ib; i0 < ie; i0 += " << I << "ull) {\n";
+    o << "    const unsigned nI = (ie - i0) < " << I << "ull ? (unsigned)(ie - i0) : " << I << "u;\n";
+    o << "    const unsigned long long s0 = slice_lo + i0;\n";
+    for (size_t l = 0; l < pg.levels.size(); ++l) emit_level(o, pg, l, UL, sh.log2_items, sh.arena_stride, "nI", T);
+    o << "  }\n";
+  } else {
+    const uint32_t F = 1u << sh.log2_forest, X = sh.cross_elems;
+    o << "  V* __restrict__ park = scratch + (size_t)blockIdx.x * " << (size_t)F * X << "u;\n";
+    o << "  for (unsigned long long c0 = ib; c0 < ie; c0 += " << F << "ull) {\n";
+    o << "    const unsigned nF = (ie - c0) < " << F << "ull ? (unsigned)(ie - c0) : " << F << "u;\n";
+    o << "    {\n    const unsigned long long s0 = slice_lo + c0;\n";
+    for (size_t l = 0; l < split; ++l) emit_level(o, pg, l, UL, sh.log2_forest, sh.forest_stride, "nF", T);
+    o << "    }\n";
+    o << "    // park the tensors the later levels read\n";
+    for (const Crossing& c : cr) {
+      int lz = 0;
+      while ((1u << lz) < c.size) ++lz;
+      o << "    for (unsigned f = threadIdx.x; f < " << ((size_t)c.size << sh.log2_forest) << "u; f += " << T
+        << "u) {\n      const unsigned item = f >> " << lz << ", e = f & " << (c.size - 1) << "u;\n"
+        << "      if (item < nF) park[item * " << X << "u + " << c.at << "u + e] = s_arena[item * "
+        << sh.forest_stride << "u + " << c.off << "u + e];\n    }\n";
     }
-    const uint64_t total = (uint64_t)lv.units[US] << sh.log2_items;
-    o << "    // level " << l << "\n";
-    o << "    for (unsigned f = threadIdx.x; f < " << total << "u; f += " << sh.threads << "u) {\n";
-    o << "      const unsigned item = f & " << (I - 1) << "u, uf = f >> " << sh.log2_items << ";\n";
-    o << "      if (item >= nI) continue;\n";
-    bool leaf_operand = false;
-    for (int j : js) leaf_operand |= (pg.steps[j].flags & (STEP_A_LEAF | STEP_B_LEAF)) != 0;
-    if (leaf_operand) o << "      const unsigned long long s = s0 + item;\n";
-    o << "      V* arena = s_arena + item * " << sh.arena_stride << "u;\n";
-    emit_dispatch(o, pg, js, beg, ulog, ks, 0, (int)js.size(), 0);
-    o << "    }\n    __syncthreads();\n";
+    o << "    __syncthreads();\n";
+    o << "    for (unsigned p0 = 0; p0 < nF; p0 += " << I << "u) {\n";
+    o << "    const unsigned nI = (nF - p0) < " << I << "u ? nF - p0 : " << I << "u;\n";
+    o << "    const unsigned long long s0 = slice_lo + c0 + p0;\n";
+    for (const Crossing& c : cr) {
+      int lz = 0;
+      while ((1u << lz) < c.size) ++lz;
+      o << "    for (unsigned f = threadIdx.x; f < " << ((size_t)c.size << sh.log2_items) << "u; f += " << T
+        << "u) {\n      const unsigned item = f >> " << lz << ", e = f & " << (c.size - 1) << "u;\n"
+        << "      if (item < nI) s_arena[item * " << sh.arena_stride << "u + " << c.off << "u + e] = park[(p0 + item) * "
+        << X << "u + " << c.at << "u + e];\n    }\n";
+    }
+    o << "    __syncthreads();\n";
+    for (size_t l = split; l < pg.levels.size(); ++l)
+      emit_level(o, pg, l, UL, sh.log2_items, sh.arena_stride, "nI", T);
+    o << "    }\n  }\n";
   }
-  o << "  }\n";
   o << "  s_red[threadIdx.x] = Partial::make(sr, si, cr, ci);\n";
-  o << "  tree_reduce(s_red, " << sh.threads << ");\n";
+  o << "  tree_reduce(s_red, " << T << ");\n";
   o << "  if (threadIdx.x == 0) partials[(size_t)xi * blocks_per_x + bx] = s_red[0];\n}\n";
   return o.str();
 }
@@ -342,12 +527,13 @@ bool jit_compile(const std::string& src, size_t smem, const void** kernel, std::
 }
 
 cudaError_t jit_level_launch(const void* kernel, const JitLevelShape& sh, int nx, int blocks_per_x,
-                             const void* leaf_tables, Partial* partials, uint64_t slice_lo, uint64_t slice_hi,
-                             cudaStream_t stream) {
+                             const void* leaf_tables, Partial* partials, void* scratch, uint64_t slice_lo,
+                             uint64_t slice_hi, cudaStream_t stream) {
+  if (sh.scratch_elems_per_block && !scratch) return cudaErrorInvalidValue;
   const void* lt = leaf_tables;
   unsigned long long lo = slice_lo, hi = slice_hi;
   int bpx = blocks_per_x;
-  void* args[] = {const_cast<void*>(static_cast<const void*>(&lt)), &partials, &lo, &hi, &bpx};
+  void* args[] = {const_cast<void*>(static_cast<const void*>(&lt)), &partials, &scratch, &lo, &hi, &bpx};
   return cudaLaunchKernel(kernel, dim3((unsigned)blocks_per_x * (unsigned)nx), dim3((unsigned)sh.threads), args,
                           sh.smem, stream);
 }

@@ -16,12 +16,28 @@
 
 namespace qtn {
 
+// Launch shape and schedule of the specialised kernel.  A block walks its
+// share of the slices in chunks.  Single-phase: every level of the program
+// runs on 2^log2_items items at a time.  Two-phase: the levels below
+// `split_level` (the many small merges on the leaf side of the contraction
+// tree) run on 2^log2_forest items at a time in arenas that hold only what
+// those levels touch; the tensors they pass to the later levels are parked
+// in a per-block global scratch area (L2-resident) and reloaded, two items'
+// worth at a time, into full arenas for the remaining levels.  The autotuner
+// times both forms.
 struct JitLevelShape {
   int threads = 0;         // threads per block
   int blocks_per_sm = 1;   // shared memory sized for this many blocks per SM
-  int log2_items = 0;      // items per block = 2^log2_items
+  int log2_items = 0;      // items per pass of the full-arena levels
   uint32_t arena_stride = 0;
   size_t smem = 0;         // dynamic shared memory per block
+  // two-phase schedule (split_level == 0: single-phase)
+  int split_level = 0;
+  int log2_forest = 0;            // items per pass of the levels below split_level
+  uint32_t forest_stride = 0;     // elements between their arenas
+  uint32_t cross_elems = 0;       // elements parked per item
+  size_t scratch_elems_per_block = 0;
+  double est_cost = 0, est_cost_single = 0;  // estimated slot-steps per item
 };
 
 // Whether the run-time compiler could be loaded (libnvrtc of the toolkit).
@@ -29,8 +45,16 @@ bool jit_available(std::string* why);
 
 // Launch shape of the specialised kernel of level program `pg` for elements
 // of `elem_bytes`, `threads` per block and `blocks_per_sm` blocks sharing an
-// SM; false if not even one item fits.
-bool jit_level_shape(const Program& pg, int elem_bytes, int threads, int blocks_per_sm, JitLevelShape* out);
+// SM, single-phase or (two_phase) the two-phase schedule with the fewest
+// estimated slot-steps per item; false if not even one item fits, or no
+// two-phase schedule does.
+bool jit_level_shape(const Program& pg, int elem_bytes, int threads, int blocks_per_sm, bool two_phase,
+                     JitLevelShape* out);
+
+// The same for `bps` blocks per SM and `cap` bytes of shared memory per
+// block (no device query).
+bool jit_level_schedule(const Program& pg, int elem_bytes, int threads, int bps, size_t cap, bool two_phase,
+                        JitLevelShape* out);
 
 // CUDA source of the specialised kernel ("qtn_level_jit"); empty (and *err
 // set) if the program has a form the generator does not handle.
@@ -41,9 +65,11 @@ std::string jit_level_source(const Program& pg, Arith a, const JitLevelShape& sh
 // `smem`.  False and *err on failure.
 bool jit_compile(const std::string& src, size_t smem, const void** kernel, std::string* err);
 
-// Launches a kernel made by jit_compile: grid = blocks_per_x * nx blocks.
+// Launches a kernel made by jit_compile: grid = blocks_per_x * nx blocks;
+// `scratch` holds scratch_elems_per_block elements per block (two-phase
+// schedule; may be null otherwise).
 cudaError_t jit_level_launch(const void* kernel, const JitLevelShape& sh, int nx, int blocks_per_x,
-                             const void* leaf_tables, Partial* partials, uint64_t slice_lo, uint64_t slice_hi,
-                             cudaStream_t stream);
+                             const void* leaf_tables, Partial* partials, void* scratch, uint64_t slice_lo,
+                             uint64_t slice_hi, cudaStream_t stream);
 
 }  // namespace qtn

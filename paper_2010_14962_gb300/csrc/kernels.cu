@@ -1281,8 +1281,9 @@ cudaError_t launch_typed(const DeviceProgram& prog, const uint8_t* d_x, int nx, 
     js.log2_items = shape.log2_items;
     js.arena_stride = shape.arena_stride;
     js.smem = shape.smem;
-    e = jit_level_launch(prog.jit_kernel, js, nx, shape.blocks_per_x, buf.leaf_tables, buf.partials, slice_lo,
-                         slice_hi, stream);
+    js.scratch_elems_per_block = prog.jit_scratch_bytes;
+    e = jit_level_launch(prog.jit_kernel, js, nx, shape.blocks_per_x, buf.leaf_tables, buf.partials,
+                         buf.jit_scratch, slice_lo, slice_hi, stream);
     if (e != cudaSuccess) return e;
   } else if (prog.exec == Executor::Level) {
     const LevelParams LP{prog.levels, prog.out_start, prog.pos_nib, prog.n_levels, shape.log2_items,

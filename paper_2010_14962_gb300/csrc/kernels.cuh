@@ -67,6 +67,7 @@ struct DeviceProgram {
   const void* jit_kernel = nullptr;
   int jit_log2_items = 0;
   size_t jit_smem = 0;
+  size_t jit_scratch_bytes = 0;  // per block (two-phase schedule), else 0
   // Wide only: the device state for the arithmetic and bit-string count of
   // the coming launch (set by the caller before exec_shape / launch).
   WideState* wide = nullptr;
@@ -78,6 +79,7 @@ struct LaunchBuffers {
   void* leaf_tables = nullptr;   // nx * leaf_elems elements (float2 / double2)
   Partial* partials = nullptr;   // nx * blocks_per_x
   int* err = nullptr;            // set non-zero by a kernel that met a bad step
+  void* jit_scratch = nullptr;   // grid blocks * the generated kernel's per-block scratch
 };
 
 // Grid shape and dynamic shared memory of the executor for `prog`, `nx` bit

@@ -323,15 +323,20 @@ def test_specialised_level_executor_n80(gpu, config80, base, prec):
     # The kernel generated for this plan's level program (merges as straight
     # code) against the oracle on the benchmark's 8 bit strings, and against
     # the interpreted level executor of the same program.
+    # Both schedules: single-phase, and two-phase (small merges over more
+    # items, their results parked in device scratch and reloaded).
     inst, plan, xs, refs = config80
     plan.select_executor(base, prec, len(xs))
     interp = device_amplitudes(plan, xs, prec)
-    plan.select_executor(base + "/jit", prec, len(xs))
-    got = device_amplitudes(plan, xs, prec)
-    assert plan.describe()["programs"][base + "/jit-" + prec]["executor"] == "level-jit"
-    tol = 2e-5 if prec == "fp32" else 1e-10
-    assert np.max(np.abs(got - refs) / np.abs(refs)) < tol
-    assert np.max(np.abs(got - interp) / np.abs(interp)) < (1e-5 if prec == "fp32" else 1e-12)
+    for form in ("jit", "jit2"):
+        plan.select_executor(base + "/" + form, prec, len(xs))
+        got = device_amplitudes(plan, xs, prec)
+        d = plan.describe()["programs"][base + "/" + form + "-" + prec]
+        assert d["executor"] == "level-jit"
+        assert (d["jit"]["split_level"] > 0) == (form == "jit2")
+        tol = 2e-5 if prec == "fp32" else 1e-10
+        assert np.max(np.abs(got - refs) / np.abs(refs)) < tol, form
+        assert np.max(np.abs(got - interp) / np.abs(interp)) < (1e-5 if prec == "fp32" else 1e-12), form
 
 
 @pytest.mark.parametrize("n,p,k,seed", [(40, 2, 10, 2), (30, 1, 8, 5)])
@@ -344,23 +349,26 @@ def test_specialised_level_executor_small(gpu, n, p, k, seed):
     refs = [O.tn_amplitude(n, inst.edges, inst.gamma, inst.beta, x, cuts=plan.cut_names(), threads=8).value
             for x in xs]
     names = [nm for nm, pr in plan.describe()["programs"].items() if pr["executor"] == "level"]
-    checked = 0
+    checked = {"jit": 0, "jit2": 0}
     for nm in names:
         for prec in _executor_precisions(nm):
-            try:
-                plan.select_executor(nm + "/jit", prec, len(xs))
-            except qtn.QTNError:
-                continue
-            got = device_amplitudes(plan, xs, prec)
-            tol = 2e-5 if prec == "fp32" else 1e-10
-            assert np.max(np.abs(got - refs) / np.abs(refs)) < tol, (nm, prec)
-            checked += 1
-    assert checked >= 3
+            for form in ("jit", "jit2"):
+                try:
+                    plan.select_executor(nm + "/" + form, prec, len(xs))
+                except qtn.QTNError:
+                    continue
+                got = device_amplitudes(plan, xs, prec)
+                tol = 2e-5 if prec == "fp32" else 1e-10
+                assert np.max(np.abs(got - refs) / np.abs(refs)) < tol, (nm, form, prec)
+                checked[form] += 1
+    # n = 30 programs already run 32 items per pass: no two-phase schedule.
+    assert checked["jit"] >= 3 and checked["jit2"] >= (1 if n == 40 else 0), checked
 
 
 def _executor_precisions(name):
-    if "/jit-" in name:  # a generated kernel runs the one arithmetic it was made for
-        return [name.rsplit("/jit-", 1)[1]]
+    for form in ("/jit-", "/jit2-"):  # a generated kernel runs the one arithmetic it was made for
+        if form in name:
+            return [name.rsplit(form, 1)[1]]
     if "/fp64/" in name:
         return ["fp64", "fp32x2"]
     if "/fp32/" in name:

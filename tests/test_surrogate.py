@@ -98,29 +98,39 @@ def test_training_learns_the_counter(trained):
     assert rho > 0.9 and err.mean() < 1.0
 
 
+# Cost of one surrogate evaluation in exact-counter evaluations: the
+# features (min-degree elimination of the cut network) take about 0.46 ms
+# of host time against about 1.2 ms for the exact (min-fill) counter at
+# n = 120, 22 cuts; inference runs batched on the device and is not counted.
+SURROGATE_EVAL_COST = 0.4
+
+
 @pytest.mark.gpu
 def test_surrogate_search_gain(trained):
     # What the network adds to Algorithm 1: both searches start from random
-    # populations (as Algorithm 1 does) and get the same wall-clock budget on
-    # n = 120, k = 22; the exact counter scores both results.
+    # populations (as Algorithm 1 does) and get the same evaluation budget on
+    # n = 120, k = 22, counted in exact-counter evaluations (a surrogate
+    # evaluation costs SURROGATE_EVAL_COST of one); the exact counter scores
+    # both results.  Fixed budgets and seeds make the comparison repeatable.
     m = trained[0]
     rows = []
     for seed in (5, 6, 7):
         inst = I.qaoa_instance(120, 1, seed)
         net = qtn.Network(120, inst.edges, inst.gamma, inst.beta)
         k = 22
-        t0 = time.perf_counter()
         cuts_s, best_s, n_exact, n_sur, trace = qtn.search_cuts_surrogate(net, k, m, T=10, N=256, top=4, seed=seed,
                                                                           seed_greedy=False)
-        budget = time.perf_counter() - t0
         assert abs(qtn.surrogate_labels(net, cuts_s)[0] - best_s) < 1e-3
         assert all(b <= a + 1e-9 for a, b in zip(trace, trace[1:]))  # elitism by the exact counter
-        cuts_e, _, n_ga = qtn.search_cuts(net, k, "ga_flops", seed=seed, ga_T=10 ** 6, ga_N=11, seed_greedy=False,
-                                          time_budget_s=budget)
+        budget = n_exact + SURROGATE_EVAL_COST * n_sur
+        ga_N = 11
+        ga_T = int(budget // ga_N) - 1  # the GA evaluates its population once per generation, plus the first
+        cuts_e, _, n_ga = qtn.search_cuts(net, k, "ga_flops", seed=seed, ga_T=ga_T, ga_N=ga_N, seed_greedy=False)
+        assert n_ga <= budget + ga_N
         best_e = float(qtn.surrogate_labels(net, cuts_e)[0])
         rows.append((best_e, best_s))
         print(f"seed {seed}: exact-counter GA {best_e:.2f} ({n_ga} evaluations) vs surrogate GA {best_s:.2f} "
-              f"({n_sur} surrogate + {n_exact} exact evaluations) in {budget:.2f} s")
+              f"({n_sur} surrogate + {n_exact} exact evaluations, budget {budget:.0f})")
     gain = np.mean([e - s_ for e, s_ in rows])
     print("mean gain (log2 flops):", gain)
     assert gain > 0
