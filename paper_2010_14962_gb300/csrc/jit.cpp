@@ -1,12 +1,15 @@
 // Per-plan specialised level executor: source generation, run-time
 // compilation (NVRTC, loaded with dlopen so that the library builds and runs
-// without it) and launch.  The generated kernel computes exactly what
-// level_exec_kernel computes for the same program and launch shape: the same
-// merges (canonical C[m, n, b] = sum_k A[m, k, b] B[k, n, b], Eq. 1) in the
-// same level order with the same units per thread, the same store
-// permutation, the same root split and the same compensated FP64 sums; only
-// the interpretation (merge lookup, field decode, leaf sub-block loops, store
-// offset tables) is resolved when the source is generated.
+// without it) and launch.  The generated kernel runs the same merges as
+// level_exec_kernel for the same program (canonical C[m, n, b] = sum_k
+// A[m, k, b] B[k, n, b], Eq. 1), in the same level order, with the same store
+// permutations and arithmetic; the interpretation (merge lookup, field
+// decode, leaf sub-block loops, store offset tables) is resolved when the
+// source is generated.  It differs in scheduling only: contiguous slice
+// ranges per block, the root's sum over k split until every thread has a
+// part, root partials summed per thread in the arithmetic's own wide form,
+// two outputs per slot where a level has slots to spare (16-byte types), and
+// optionally the two-phase schedule (jit.hpp).
 #include "jit.hpp"
 
 #include <dlfcn.h>
@@ -146,10 +149,14 @@ void emit_merge(std::ostringstream& o, const Program& pg, const DevStep& st, uin
     o << "        V acc = Ops::mul(ap[0], bp[0]);\n";
     for (uint32_t k = 1; k < kpart; ++k)
       o << "        Ops::fma(acc, ap[" << (k << ma) << "], bp[" << k << "]);\n";
-    o << "        Ops::finish(acc);\n";
     if (root) {
-      o << "        kahan_add(sr, cr, Ops::re(acc));\n        kahan_add(si, ci, Ops::im(acc));\n";
+      // Root partials: compensated FP64 sums in the FP64 arithmetic; in the
+      // FP32-storage arithmetics a double word per thread on the FP32 pipe
+      // (TwoSum of the high parts, the errors and low parts collected
+      // lazily), converted to FP64 once at the end.
+      o << "        root_add(acc);\n";
     } else {
+      o << "        Ops::finish(acc);\n";
       uint32_t add = 0;
       for (int bit = 0; bit < ulog; ++bit)
         if ((r >> bit) & 1u) add += st.w[bit];
@@ -175,7 +182,24 @@ struct LevelGen {
   uint64_t work = 0;   // largest multiply-add count of one slot
 };
 
+LevelGen level_gen_ul(const Program& pg, size_t l, int UL, int lg, int threads);
+
+// Unit size of level l: the arithmetic's (UL), or for the 16-byte types
+// (one output per slot) two outputs per slot where that takes no more
+// rounds-times-work than one, so that a slot's decode, dispatch and
+// addressing serve two outputs.
+int level_ul(const Program& pg, size_t l, int UL, int lg, int threads) {
+  if (UL) return UL;
+  auto cost = [&](const LevelGen& g) { return ((g.units << lg) + threads - 1) / threads * g.work; };
+  const LevelGen g0 = level_gen_ul(pg, l, 0, lg, threads), g1 = level_gen_ul(pg, l, 1, lg, threads);
+  return (g1.units << lg) >= (uint64_t)threads && cost(g1) <= cost(g0) ? 1 : 0;
+}
+
 LevelGen level_gen(const Program& pg, size_t l, int UL, int lg, int threads) {
+  return level_gen_ul(pg, l, level_ul(pg, l, UL, lg, threads), lg, threads);
+}
+
+LevelGen level_gen_ul(const Program& pg, size_t l, int UL, int lg, int threads) {
   LevelGen g;
   const DevLevel& lv = pg.levels[l];
   for (int j = lv.first; j < lv.first + lv.count; ++j) {
@@ -183,7 +207,7 @@ LevelGen level_gen(const Program& pg, size_t l, int UL, int lg, int threads) {
     const int rc0 = st.ma + st.nb + st.bb;
     int ks = 0;
     if (st.flags & STEP_ROOT) {
-      ks = UL ? std::min<int>(st.kb, kRootSplitLog2) : 0;
+      ks = UL >= kLevelUnitLog2 ? std::min<int>(st.kb, kRootSplitLog2) : 0;
       auto slots = [&](int k) { return ((uint64_t)1 << (rc0 + k - std::min(rc0 + k, UL))) << lg; };
       while (ks < st.kb && slots(ks) < (uint64_t)threads) ++ks;
     }
@@ -411,6 +435,16 @@ std::string jit_level_source(const Program& pg, Arith a, const JitLevelShape& sh
        "    Partial p; p.re = a; p.im = b; p.cre = c; p.cim = d; return p;\n  }\n};\n";
   o << kArithSource << "\n";
   o << "typedef " << vt << " V;\ntypedef CplxOps<V> Ops;\n";
+  if (a == Arith::F64) {
+    o << "#define root_add(v) do { kahan_add(sr, cr, (v).x); kahan_add(si, ci, (v).y); } while (0)\n";
+  } else {
+    o << "__device__ __forceinline__ void dw_add(float& ah, float& al, float bh, float bl) {\n"
+         "  float t, e;\n  two_sum(ah, bh, t, e);\n  ah = t;\n  al = __fadd_rn(al, __fadd_rn(e, bl));\n}\n";
+    if (a == Arith::F32X2)
+      o << "#define root_add(v) do { dw_add(qrh, qrl, (v).rh, (v).rl); dw_add(qih, qil, (v).ih, (v).il); } while (0)\n";
+    else
+      o << "#define root_add(v) do { dw_add(qrh, qrl, (v).x, 0.f); dw_add(qih, qil, (v).y, 0.f); } while (0)\n";
+  }
   o << "extern \"C\" __global__ void __launch_bounds__(" << T << ", " << sh.blocks_per_sm
     << ") qtn_level_jit(const V* __restrict__ leaf_tables, Partial* __restrict__ partials, V* __restrict__ scratch,\n"
        "    unsigned long long slice_lo, unsigned long long slice_hi, int blocks_per_x) {\n";
@@ -424,6 +458,7 @@ std::string jit_level_source(const Program& pg, Arith a, const JitLevelShape& sh
     << "    for (unsigned i = threadIdx.x; i < " << (size_t)pg.leaf_elems * elem / 4 << "u; i += " << T
     << "u) dst[i] = src[i];\n  }\n  __syncthreads();\n";
   o << "  double sr = 0.0, si = 0.0, cr = 0.0, ci = 0.0;\n";
+  o << "  float qrh = 0.f, qrl = 0.f, qih = 0.f, qil = 0.f;\n";
   // The block's share of the slices: a contiguous range, sizes within one.
   o << "  const unsigned long long S = slice_hi - slice_lo, q = S / (unsigned long long)blocks_per_x,\n"
        "      r = S % (unsigned long long)blocks_per_x;\n"
@@ -469,7 +504,7 @@ std::string jit_level_source(const Program& pg, Arith a, const JitLevelShape& sh
       emit_level(o, pg, l, UL, sh.log2_items, sh.arena_stride, "nI", T);
     o << "    }\n  }\n";
   }
-  o << "  s_red[threadIdx.x] = Partial::make(sr, si, cr, ci);\n";
+  o << "  s_red[threadIdx.x] = Partial::make(sr + ((double)qrh + (double)qrl), si + ((double)qih + (double)qil), cr, ci);\n";
   o << "  tree_reduce(s_red, " << T << ");\n";
   o << "  if (threadIdx.x == 0) partials[(size_t)xi * blocks_per_x + bx] = s_red[0];\n}\n";
   return o.str();
