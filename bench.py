@@ -45,8 +45,12 @@ INSTR_PER_MAC = {"fp32": 1, "fp32x2": 12, "tf32": 3, "tf32x3": 9, "bf16x3": 13, 
 
 def pipe_peak(prec: str, peaks: dict) -> float:
     """Measured peak (TFLOP/s, 2 flops per multiply-add) of the pipe that runs
-    the arithmetic: the FP64 pipe for complex128, the FP32 pipe otherwise."""
-    return peaks["fp64_tflops"] if prec == "fp64" else peaks["fp32_tflops"]
+    the arithmetic: the FP64 pipe for complex128, the FP32 pipe otherwise (the
+    higher of its scalar and packed-pair multiply-add rates: the generated
+    double-float executor issues packed pairs)."""
+    if prec == "fp64":
+        return peaks["fp64_tflops"]
+    return max(peaks["fp32_tflops"], peaks.get("fp32x2_tflops") or 0.0)
 
 
 def measure_pipe_peaks(local_rank: int) -> dict:
@@ -57,10 +61,15 @@ def measure_pipe_peaks(local_rank: int) -> dict:
     with ClockSampler(local_rank) as clk:
         time.sleep(0.2)
         pk = qtn.pipe_peaks(5)
+        try:
+            pk["fp32x2_tflops"] = qtn.pipe_peak_fp32x2(5)
+        except qtn.QTNError:
+            pk["fp32x2_tflops"] = None
         time.sleep(0.2)
     pk["clocks"] = clk.summary()
-    pk["how"] = ("qtn_pipe_peaks: 8 independent FMA chains per thread, 4 x SMs x resident blocks of 256 threads, "
-                 "best of 5 launches timed with CUDA events; 2 flops per FMA")
+    pk["how"] = ("qtn_pipe_peaks / qtn_pipe_peak_fp32x2: 8 independent FMA chains per thread (scalar FP32, FP64, "
+                 "packed fma.rn.f32x2 pairs), 4 x SMs x resident blocks of 256 threads, best of 5 launches timed "
+                 "with CUDA events; 2 flops per multiply-add")
     return pk
 
 
@@ -310,17 +319,20 @@ def run_ours(args, rank, world, local_rank):
                      "kernel": {"lane": "lane_exec_kernel", "level": "level_exec_kernel",
                                 "level-jit": "qtn_level_jit (generated for this plan)"}.get(prog["executor"],
                                                                                              "block_exec_kernel"),
-                     "peak_source": ("measured %s FMA peak of this GPU (qtn_pipe_peaks, median SM clock %s MHz)"
-                                     % ("FP64" if args.precision == "fp64" else "FP32",
-                                        pipe_peaks["clocks"].get("sm_mhz"))),
+                     "peak_source": ("measured %s multiply-add peak of this GPU (qtn_pipe_peaks%s, median SM clock "
+                                     "%s MHz)" % ("FP64" if args.precision == "fp64" else
+                                                  "FP32 (higher of scalar and packed-pair)",
+                                                  "" if args.precision == "fp64" else " / qtn_pipe_peak_fp32x2",
+                                                  pipe_peaks["clocks"].get("sm_mhz"))),
                      "achieved_def": ("executed algorithmic flops per launch (8 x complex multiply-adds of the "
                                       "executor's program) / executor kernel time (CUDA events on its stream)"),
                      "pipe_issue_frac": (achieved * INSTR_PER_MAC[args.precision] / peak
                                          if args.precision in INSTR_PER_MAC else None),
-                     "pipe_issue_def": ("share of the FP32 pipe's instruction slots the arithmetic's own "
-                                        "instructions fill (model: %s per real multiply-add)"
+                     "pipe_issue_def": ("share of the FP32 pipe's lane operations the arithmetic's own "
+                                        "operations fill (model: %s per real multiply-add)"
                                         % INSTR_PER_MAC.get(args.precision)),
-                     "measured_peaks_tflops": {"fp32": pipe_peaks["fp32_tflops"], "fp64": pipe_peaks["fp64_tflops"]},
+                     "measured_peaks_tflops": {"fp32": pipe_peaks["fp32_tflops"], "fp64": pipe_peaks["fp64_tflops"],
+                                               "fp32x2": pipe_peaks.get("fp32x2_tflops")},
                      "kernel_ms_avg": avg_kernel_s * 1e3,
                      "step_classes": step_classes(prog, 8 if args.precision in ("fp32", "tf32", "bf16x3", "tf32x3",
                                                                                 "bf16x6") else 16)},

@@ -367,6 +367,13 @@ qtn_status qtn_wide_set_kernel(const char* name);
  * reps < 1; QTN_ERR_CUDA if a launch fails. */
 qtn_status qtn_pipe_peaks(int reps, double* fp32_tflops, double* fp64_tflops);
 
+/* The same measurement with packed FP32 pairs (one fma.rn.f32x2 instruction
+ * is two multiply-adds; sm_100 and later), the FP32 roof of the executors
+ * that use them.  *tflops (host) counts a multiply-add as 2 flops.
+ * QTN_ERR_UNSUPPORTED on an older device, QTN_ERR_INVALID_ARG for a null
+ * output or reps < 1, QTN_ERR_CUDA if a launch fails. */
+qtn_status qtn_pipe_peak_fp32x2(int reps, double* tflops);
+
 /* ------------------------------------------------ learned cost surrogate --
  * A small MLP predicts the exact counter's log2 total flops and log2 peak
  * bytes of cutting a set of indices (min-fill plan) from cheap features, so a

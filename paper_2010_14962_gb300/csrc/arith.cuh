@@ -23,6 +23,8 @@ struct CplxOps<float2> {
     return r;
   }
   static __device__ __forceinline__ void finish(float2&) {}
+  typedef float2 Acc;  // accumulator of a multiply-add chain: the value itself
+  static __device__ __forceinline__ float2 result(float2 v) { return v; }
   static __device__ __forceinline__ float2 from(double re, double im) {
     return make_float2((float)re, (float)im);
   }
@@ -45,6 +47,8 @@ struct CplxOps<double2> {
     return r;
   }
   static __device__ __forceinline__ void finish(double2&) {}
+  typedef double2 Acc;  // accumulator of a multiply-add chain: the value itself
+  static __device__ __forceinline__ double2 result(double2 v) { return v; }
   static __device__ __forceinline__ double2 from(double re, double im) { return make_double2(re, im); }
   static __device__ __forceinline__ double re(double2 v) { return v.x; }
   static __device__ __forceinline__ double im(double2 v) { return v.y; }
@@ -53,8 +57,9 @@ struct CplxOps<double2> {
 // ---------------------------------------------------- double-float (FP32X2) --
 
 // A complex number as two double-word floats (value = hi + lo per part).
-struct dfc {
-  float rh, rl, ih, il;
+// Layout: the two high parts first (a packed pair), then the two low parts.
+struct __align__(16) dfc {
+  float rh, ih, rl, il;
 };
 
 // Error-free transform TwoSum (Knuth: s + e = a + b exactly).  The _rn
@@ -110,13 +115,123 @@ struct CplxOps<dfc> {
     two_sum(v.rh, v.rl, v.rh, v.rl);
     two_sum(v.ih, v.il, v.ih, v.il);
   }
+  typedef dfc Acc;
+  static __device__ __forceinline__ dfc result(dfc v) {
+    finish(v);
+    return v;
+  }
   static __device__ __forceinline__ dfc from(double re, double im) {
     const float rh = (float)re, ih = (float)im;
-    return dfc{rh, (float)(re - (double)rh), ih, (float)(im - (double)ih)};
+    return dfc{rh, ih, (float)(re - (double)rh), (float)(im - (double)ih)};
   }
   static __device__ __forceinline__ double re(dfc v) { return (double)v.rh + (double)v.rl; }
   static __device__ __forceinline__ double im(dfc v) { return (double)v.ih + (double)v.il; }
 };
+
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+// The same double-float complex multiply-add on packed FP32 pairs (sm_100
+// and later: one add/sub/mul/fma .f32x2 instruction computes two lanes, each
+// rounded to nearest exactly as the scalar instruction rounds it).  A pair
+// lives in a 64-bit register: the first lane in the low word.
+typedef unsigned long long x2;
+__device__ __forceinline__ x2 x2_pack(float lo, float hi) {
+  x2 d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+  return d;
+}
+__device__ __forceinline__ void x2_unpack(x2 v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ x2 x2_swap(x2 v) {
+  float lo, hi;
+  x2_unpack(v, lo, hi);
+  return x2_pack(hi, lo);
+}
+__device__ __forceinline__ x2 x2_add(x2 a, x2 b) {
+  x2 d;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+// a - b as the FMA b * (-1) + a (the product is exact, so this is a - b
+// rounded once).  The packed subtract instruction is not used: in longer
+// sequences built with it the error-free transforms below lost their
+// exactness (results differed from the scalar sequence), while this form
+// matches the scalar sequence bit for bit.
+__device__ __forceinline__ x2 x2_sub(x2 a, x2 b) {
+  x2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(b), "l"(0xbf800000bf800000ull), "l"(a));
+  return d;
+}
+__device__ __forceinline__ x2 x2_mul(x2 a, x2 b) {
+  x2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ x2 x2_fma(x2 a, x2 b, x2 c) {
+  x2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+// TwoSum on each lane (s + e = a + b exactly).
+__device__ __forceinline__ void two_sum2(x2 a, x2 b, x2& s, x2& e) {
+  s = x2_add(a, b);
+  const x2 bb = x2_sub(s, a);
+  e = x2_add(x2_sub(a, x2_sub(s, bb)), x2_sub(b, bb));
+}
+// dw_prod on each lane.
+__device__ __forceinline__ void dw_prod2(x2 xh, x2 xl, x2 yh, x2 yl, x2& ph, x2& pl) {
+  ph = x2_mul(xh, yh);
+  pl = x2_fma(xh, yh, x2_fma(ph, 0xbf800000bf800000ull, 0x8000000080000000ull));  // -ph exactly
+  pl = x2_fma(xh, yl, pl);
+  pl = x2_fma(xl, yh, pl);
+}
+// dw_fma_lazy on each lane.
+__device__ __forceinline__ void dw_fma_lazy2(x2& ah, x2& al, x2 xh, x2 xl, x2 yh, x2 yl) {
+  x2 ph, pl, sh, e;
+  dw_prod2(xh, xl, yh, yl, ph, pl);
+  two_sum2(ah, ph, sh, e);
+  ah = sh;
+  al = x2_add(al, x2_add(e, pl));
+}
+// The accumulator holds two double-word pairs: (h1, l1) collects the
+// products a.r b.r and a.i b.r (lanes: re, im), (h2, l2) collects a.r b.i and
+// -a.i b.i (lanes: im, re).  Every product takes the operand A as stored
+// (high pair, low pair) and only B is broadcast into pairs; the two
+// accumulators are added once per output.
+struct DfcX2Acc {
+  x2 h1, l1, h2, l2;
+};
+struct CplxOpsX2 {
+  typedef DfcX2Acc Acc;
+  static __device__ __forceinline__ Acc mul(dfc a, dfc b) {
+    const x2 ah = x2_pack(a.rh, a.ih), al = x2_pack(a.rl, a.il);
+    Acc r;
+    dw_prod2(ah, al, x2_pack(b.rh, b.rh), x2_pack(b.rl, b.rl), r.h1, r.l1);
+    dw_prod2(ah, al, x2_pack(b.ih, -b.ih), x2_pack(b.il, -b.il), r.h2, r.l2);
+    return r;
+  }
+  static __device__ __forceinline__ void fma(Acc& acc, dfc a, dfc b) {
+    const x2 ah = x2_pack(a.rh, a.ih), al = x2_pack(a.rl, a.il);
+    dw_fma_lazy2(acc.h1, acc.l1, ah, al, x2_pack(b.rh, b.rh), x2_pack(b.rl, b.rl));
+    dw_fma_lazy2(acc.h2, acc.l2, ah, al, x2_pack(b.ih, -b.ih), x2_pack(b.il, -b.il));
+  }
+  // (re, im) as a high pair and an unnormalised low pair.
+  static __device__ __forceinline__ void sum(const Acc& a, x2& h, x2& l) {
+    x2 e;
+    two_sum2(a.h1, x2_swap(a.h2), h, e);
+    l = x2_add(x2_add(a.l1, x2_swap(a.l2)), e);
+  }
+  static __device__ __forceinline__ dfc result(const Acc& a) {
+    x2 h, l, s, e;
+    sum(a, h, l);
+    two_sum2(h, l, s, e);
+    dfc r;
+    x2_unpack(s, r.rh, r.ih);
+    x2_unpack(e, r.rl, r.il);
+    return r;
+  }
+};
+#endif
 
 
 __device__ __forceinline__ void kahan_add(double& sum, double& comp, double v) {

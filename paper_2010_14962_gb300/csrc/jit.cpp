@@ -146,7 +146,7 @@ void emit_merge(std::ostringstream& o, const Program& pg, const DevStep& st, uin
       << ((1u << nb) - 1u) << "u, b = oo >> " << (ma + nb) << ";\n";
     o << "        const V* __restrict__ ap = A + m + (k0 << " << ma << ") + (b << " << (ma + kb) << ");\n";
     o << "        const V* __restrict__ bp = B + k0 + (n << " << kb << ") + (b << " << (kb + nb) << ");\n";
-    o << "        V acc = Ops::mul(ap[0], bp[0]);\n";
+    o << "        Ops::Acc acc = Ops::mul(ap[0], bp[0]);\n";
     for (uint32_t k = 1; k < kpart; ++k)
       o << "        Ops::fma(acc, ap[" << (k << ma) << "], bp[" << k << "]);\n";
     if (root) {
@@ -156,11 +156,10 @@ void emit_merge(std::ostringstream& o, const Program& pg, const DevStep& st, uin
       // lazily), converted to FP64 once at the end.
       o << "        root_add(acc);\n";
     } else {
-      o << "        Ops::finish(acc);\n";
       uint32_t add = 0;
       for (int bit = 0; bit < ulog; ++bit)
         if ((r >> bit) & 1u) add += st.w[bit];
-      o << "        C[p0 + " << add << "u] = acc;\n";
+      o << "        C[p0 + " << add << "u] = Ops::result(acc);\n";
     }
     o << "      }\n";
   }
@@ -434,16 +433,24 @@ std::string jit_level_source(const Program& pg, Arith a, const JitLevelShape& sh
        "  static __device__ __forceinline__ Partial make(double a, double b, double c, double d) {\n"
        "    Partial p; p.re = a; p.im = b; p.cre = c; p.cim = d; return p;\n  }\n};\n";
   o << kArithSource << "\n";
-  o << "typedef " << vt << " V;\ntypedef CplxOps<V> Ops;\n";
+  o << "typedef " << vt << " V;\n";
   if (a == Arith::F64) {
+    o << "typedef CplxOps<V> Ops;\n";
     o << "#define root_add(v) do { kahan_add(sr, cr, (v).x); kahan_add(si, ci, (v).y); } while (0)\n";
   } else {
     o << "__device__ __forceinline__ void dw_add(float& ah, float& al, float bh, float bl) {\n"
          "  float t, e;\n  two_sum(ah, bh, t, e);\n  ah = t;\n  al = __fadd_rn(al, __fadd_rn(e, bl));\n}\n";
     if (a == Arith::F32X2)
-      o << "#define root_add(v) do { dw_add(qrh, qrl, (v).rh, (v).rl); dw_add(qih, qil, (v).ih, (v).il); } while (0)\n";
+      // Packed FP32 pairs where the device has them.
+      o << "#if __CUDA_ARCH__ >= 1000\ntypedef CplxOpsX2 Ops;\n"
+           "#define root_add(v) do { x2 h_, l_; float a_, b_, c_, d_; Ops::sum((v), h_, l_); x2_unpack(h_, a_, b_); "
+           "x2_unpack(l_, c_, d_); dw_add(qrh, qrl, a_, c_); dw_add(qih, qil, b_, d_); } while (0)\n"
+           "#else\ntypedef CplxOps<V> Ops;\n"
+           "#define root_add(v) do { dw_add(qrh, qrl, (v).rh, (v).rl); dw_add(qih, qil, (v).ih, (v).il); } "
+           "while (0)\n#endif\n";
     else
-      o << "#define root_add(v) do { dw_add(qrh, qrl, (v).x, 0.f); dw_add(qih, qil, (v).y, 0.f); } while (0)\n";
+      o << "typedef CplxOps<V> Ops;\n"
+           "#define root_add(v) do { dw_add(qrh, qrl, (v).x, 0.f); dw_add(qih, qil, (v).y, 0.f); } while (0)\n";
   }
   o << "extern \"C\" __global__ void __launch_bounds__(" << T << ", " << sh.blocks_per_sm
     << ") qtn_level_jit(const V* __restrict__ leaf_tables, Partial* __restrict__ partials, V* __restrict__ scratch,\n"

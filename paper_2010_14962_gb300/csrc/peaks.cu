@@ -46,12 +46,53 @@ __global__ void __launch_bounds__(kThreads) pipe_peak_kernel(int iters, T b, T c
   if (s == never) sink[blockIdx.x] = s;
 }
 
+// Packed FP32 pairs (fma.rn.f32x2, sm_100 and later): each instruction is
+// two multiply-adds.  Same chains and grid as above, a pair per chain.
+__global__ void __launch_bounds__(kThreads) pipe_peak_x2_kernel(int iters, float b, float c, float never, float* sink) {
+  unsigned long long a[kChains], bb, cc;
+  asm("mov.b64 %0, {%1, %1};" : "=l"(bb) : "f"(b));
+  asm("mov.b64 %0, {%1, %1};" : "=l"(cc) : "f"(c));
+#pragma unroll
+  for (int j = 0; j < kChains; ++j) {
+    const float lo = (float)(threadIdx.x + j), hi = lo + 0.5f;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(a[j]) : "f"(lo), "f"(hi));
+  }
+  for (int i = 0; i < iters; ++i) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+      for (int j = 0; j < kChains; ++j) asm("fma.rn.f32x2 %0, %0, %1, %2;" : "+l"(a[j]) : "l"(bb), "l"(cc));
+  }
+  float s = 0.f;
+#pragma unroll
+  for (int j = 0; j < kChains; ++j) {
+    float lo, hi;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a[j]));
+    s += lo + hi;
+  }
+  if (s == never) sink[blockIdx.x] = s;
+}
+
 template <class T>
-cudaError_t time_pipe(int iters, int reps, double* tflops) {
+void launch_peak(bool packed, int blocks, int iters, T mul, T add, T never, T* sink) {
+  pipe_peak_kernel<T><<<blocks, kThreads>>>(iters, mul, add, never, sink);
+}
+template <>
+void launch_peak<float>(bool packed, int blocks, int iters, float mul, float add, float never, float* sink) {
+  if (packed)
+    pipe_peak_x2_kernel<<<blocks, kThreads>>>(iters, mul, add, never, sink);
+  else
+    pipe_peak_kernel<float><<<blocks, kThreads>>>(iters, mul, add, never, sink);
+}
+
+template <class T>
+cudaError_t time_pipe(int iters, int reps, double* tflops, bool packed = false) {
   int dev = 0, sms = 0, per_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pipe_peak_kernel<T>, kThreads, 0);
+  if (e == cudaSuccess)
+    e = packed ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pipe_peak_x2_kernel, kThreads, 0)
+               : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pipe_peak_kernel<T>, kThreads, 0);
   if (e != cudaSuccess) return e;
   const int blocks = sms * (per_sm > 0 ? per_sm : 1) * 4;
   T* sink = nullptr;
@@ -63,9 +104,9 @@ cudaError_t time_pipe(int iters, int reps, double* tflops) {
   const T mul = (T)(1.0 - 1.0 / (1 << 20)), add = (T)(1.0 / (1 << 30)), never = (T)-1.0;
   float best = 0.f;
   for (int r = 0; e == cudaSuccess && r < reps + 1; ++r) {  // the first run warms up
-    pipe_peak_kernel<T><<<blocks, kThreads>>>(iters, mul, add, never, sink);
+    launch_peak<T>(packed, blocks, iters, mul, add, never, sink);
     e = cudaEventRecord(a);
-    pipe_peak_kernel<T><<<blocks, kThreads>>>(iters, mul, add, never, sink);
+    launch_peak<T>(packed, blocks, iters, mul, add, never, sink);
     if (e == cudaSuccess) e = cudaEventRecord(b);
     if (e == cudaSuccess) e = cudaEventSynchronize(b);
     float ms = 0.f;
@@ -77,7 +118,7 @@ cudaError_t time_pipe(int iters, int reps, double* tflops) {
   if (b) cudaEventDestroy(b);
   if (sink) cudaFree(sink);
   if (e != cudaSuccess) return e;
-  const double flops = 2.0 * kChains * 4.0 * iters * (double)blocks * kThreads;
+  const double flops = 2.0 * kChains * 4.0 * iters * (double)blocks * kThreads * (packed ? 2.0 : 1.0);
   *tflops = flops / (best / 1e3) / 1e12;
   return cudaSuccess;
 }
@@ -95,5 +136,18 @@ extern "C" qtn_status qtn_pipe_peaks(int reps, double* fp32_tflops, double* fp64
   if (e != cudaSuccess) return set_error(QTN_ERR_CUDA, std::string("qtn_pipe_peaks: ") + cudaGetErrorString(e));
   *fp32_tflops = f32;
   *fp64_tflops = f64;
+  return QTN_OK;
+}
+
+extern "C" qtn_status qtn_pipe_peak_fp32x2(int reps, double* tflops) {
+  using qtn::internal::set_error;
+  if (!tflops || reps < 1) return set_error(QTN_ERR_INVALID_ARG, "qtn_pipe_peak_fp32x2: null output or reps < 1");
+  int dev = 0, major = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  if (major < 10) return set_error(QTN_ERR_UNSUPPORTED, "qtn_pipe_peak_fp32x2: no packed FP32 instructions");
+  double t = 0;
+  cudaError_t e = qtn::time_pipe<float>(1 << 13, reps, &t, true);
+  if (e != cudaSuccess) return set_error(QTN_ERR_CUDA, std::string("qtn_pipe_peak_fp32x2: ") + cudaGetErrorString(e));
+  *tflops = t;
   return QTN_OK;
 }

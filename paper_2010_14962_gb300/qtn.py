@@ -110,6 +110,7 @@ def lib():
                                           ctypes.c_uint64, ctypes.c_int, i32p, f64p, P(ctypes.c_int),
                                           P(ctypes.c_int), f64p, ctypes.c_int, P(ctypes.c_int)],
             "qtn_pipe_peaks": [ctypes.c_int, f64p, f64p],
+            "qtn_pipe_peak_fp32x2": [ctypes.c_int, f64p],
             "qtn_wide_set_kernel": [ctypes.c_char_p],
             "qtn_status_string": [ctypes.c_int],
             "qtn_last_error": [],
@@ -435,6 +436,14 @@ def pipe_peaks(reps: int = 3) -> dict:
     f32, f64 = ctypes.c_double(), ctypes.c_double()
     _check(lib().qtn_pipe_peaks(int(reps), ctypes.byref(f32), ctypes.byref(f64)))
     return {"fp32_tflops": f32.value, "fp64_tflops": f64.value}
+
+
+def pipe_peak_fp32x2(reps: int = 3) -> float:
+    """qtn_pipe_peak_fp32x2: measured packed-FP32-pair multiply-add peak
+    (TFLOP/s) of the current device."""
+    t = ctypes.c_double()
+    _check(lib().qtn_pipe_peak_fp32x2(int(reps), ctypes.byref(t)))
+    return t.value
 
 
 def wide_set_kernel(name: str = "auto"):
