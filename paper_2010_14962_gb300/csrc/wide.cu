@@ -437,6 +437,10 @@ cudaError_t wide_tune(WideState* ws, void* leaf_tables, uint64_t slice_lo, uint6
   e = cudaEventCreate(&e1);
   if (e != cudaSuccess) return e;
   std::ostringstream lg;
+  // Winners of earlier processes (QTN_WIDE_TUNE_CACHE), read once.
+  static std::once_flag loaded;
+  std::call_once(loaded, wide_tune_load);
+  bool added = false;
   const uint64_t nr = slice_hi - slice_lo;
   const uint64_t n_group = std::min<uint64_t>(ws->group, (uint64_t)ws->nx * nr);
   ws->force_mode = g_force_kernel.load();
@@ -502,6 +506,7 @@ cudaError_t wide_tune(WideState* ws, void* leaf_tables, uint64_t slice_lo, uint6
       if (force < 0) {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         wide_tune_table()[key] = ent;
+        added = true;
       }
     }
   };
@@ -512,6 +517,7 @@ cudaError_t wide_tune(WideState* ws, void* leaf_tables, uint64_t slice_lo, uint6
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   ws->tuned = true;
+  if (added || ws->force_mode < 0) wide_tune_save();
   if (log) *log = lg.str();
   return cudaSuccess;
 }

@@ -14,6 +14,11 @@ each merge's FP32 accumulation of K products at most (K - 1) u32 of the
 magnitudes it adds; so |a - a*| <= (2 G u + sum_j K_j u32) * sum_s |a_s|,
 with sum_s |a_s| from the oracle's per-slice values.
 """
+import json
+import os
+import subprocess
+import sys
+
 import numpy as np
 import pytest
 
@@ -142,3 +147,49 @@ def test_wide_executor_against_oracle(gpu, n, p, k, seed):
         assert np.all(rel <= 2 * len(inst.edges) * p * U_OPERAND["tf32x3"] + ksum * U32)
     finally:
         qtn.wide_set_kernel("auto")
+
+
+_CACHE_RUN = r"""
+import json, sys
+import numpy as np, torch
+from paper_2010_14962_gb300 import instances as I, qtn
+inst = I.qaoa_instance(20, 3, 11)
+plan = qtn.Plan(qtn.Network(20, inst.edges, inst.gamma, inst.beta), k=2)
+xs = I.bitstrings(20, 4, 11)
+plan.select_executor("wide/slices", "fp32", len(xs))
+d_x = torch.from_numpy(np.ascontiguousarray(xs)).cuda()
+d_out = torch.zeros((len(xs), 2), dtype=torch.float64, device="cuda")
+plan.contract_amplitudes_device(d_x, d_out, "fp32")
+torch.cuda.synchronize()
+st = [s for s in plan.describe()["programs"]["wide/slices"]["wide_states"] if s["nx"] == len(xs)][0]
+o = d_out.cpu().numpy()
+print(json.dumps({"kernels": st["step_kernels"], "re": o[:, 0].tolist(), "im": o[:, 1].tolist()}))
+"""
+
+
+def _cache_run(path):
+    env = dict(os.environ, QTN_WIDE_TUNE_CACHE=str(path))
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", _CACHE_RUN], env=env, cwd=root, capture_output=True, text=True,
+                       timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    return d["kernels"], np.array(d["re"]) + 1j * np.array(d["im"])
+
+
+def test_wide_tune_cache_round_trip(gpu, deep20, tmp_path):
+    # The per-shape winners file: a process that tunes writes one JSON line
+    # per step shape (ma, nb, kb, bb, items, arithmetic -> kernel); a new
+    # process reads it and runs the recorded kernels without timing.  Every
+    # entry rewritten to the one-output SIMT kernel (not the winner of most
+    # shapes) still gives the amplitudes within the FP32 bound.
+    inst, plan, xs, refs, l1, ksum = deep20
+    path = tmp_path / "wide_tune.jsonl"
+    k1, a1 = _cache_run(path)
+    lines = [json.loads(x) for x in path.read_text().splitlines()]
+    assert lines and all({"ma", "nb", "kb", "bb", "items", "arith", "best"} <= set(e) for e in lines)
+    assert np.all(np.abs(a1 - refs) <= bound(inst, "fp32", l1, ksum))
+    path.write_text("".join(json.dumps(dict(e, best=0, kernel="simt"), separators=(",", ":")) + "\n" for e in lines))
+    k2, a2 = _cache_run(path)
+    assert set(k2) == {"simt"}, k2
+    assert np.all(np.abs(a2 - refs) <= bound(inst, "fp32", l1, ksum))
