@@ -354,6 +354,10 @@ qtn_status qtn_plan_kernel_ms(const qtn_plan_t* plan, float* ms);
  * summed).  name: "auto" (the default: autotuned), "simt", "simt4" or
  * "tcgen05" (every step that allows it; the others stay autotuned).  Takes
  * effect at each wide state's next launch outside stream capture.
+ * Autotuned winners are kept per process, keyed by (ma, nb, kb, bb, items
+ * per launch, arithmetic); if the environment variable QTN_WIDE_TUNE_CACHE
+ * names a file, the first tuning of the process reads winners from it (one
+ * JSON object per line) and every tuning writes the table back.
  * QTN_ERR_INVALID_ARG for an unknown name. */
 qtn_status qtn_wide_set_kernel(const char* name);
 
