@@ -233,6 +233,20 @@ struct CplxOpsX2 {
 };
 #endif
 
+// The arithmetic the merge loops run for element ops `Ops`: the packed
+// double-float form where the device has packed FP32 pairs, else `Ops`
+// itself (its accumulator is the value).
+template <class Ops>
+struct MergeOps {
+  typedef Ops type;
+};
+#if defined(__CUDA_ARCH__) && __CUDA_ARCH__ >= 1000
+template <>
+struct MergeOps<CplxOps<dfc>> {
+  typedef CplxOpsX2 type;
+};
+#endif
+
 
 __device__ __forceinline__ void kahan_add(double& sum, double& comp, double v) {
   double y = v - comp;

@@ -390,14 +390,15 @@ __device__ __forceinline__ void group_merge_k(const StepRegs sr_, const uint16_t
     const uint32_t m = o & mmask, n = (o >> ma) & nmask, b = o >> (ma + nb);
     const V* ap = A + m + (b << (ma + kb));
     const V* bp = B + (n << kb) + (b << (kb + nb));
-    V acc = Ops::mul(ap[0], bp[0]);
+    using F = typename MergeOps<Ops>::type;
+    typename F::Acc acc_ = F::mul(ap[0], bp[0]);
     if (K > 0) {
 #pragma unroll
-      for (int k = 1; k < K; ++k) Ops::fma(acc, ap[k << ma], bp[k]);
+      for (int k = 1; k < K; ++k) F::fma(acc_, ap[k << ma], bp[k]);
     } else {
-      for (uint32_t k = 1; k < (1u << kb); ++k) Ops::fma(acc, ap[k << ma], bp[k]);
+      for (uint32_t k = 1; k < (1u << kb); ++k) F::fma(acc_, ap[k << ma], bp[k]);
     }
-    Ops::finish(acc);
+    const V acc = F::result(acc_);
     if (sr_.root) {
       kahan_add(sr, cr, Ops::re(acc));
       kahan_add(si, ci, Ops::im(acc));
@@ -578,15 +579,15 @@ __device__ __forceinline__ void level_unit(const LStep& q, uint32_t o0, uint32_t
       const uint32_t m = o & mmask, n = (o >> ma) & nmask, b = o >> (ma + nb);
       const V* ap = A + m + (b << (ma + kb));
       const V* bp = B + (n << kb) + (b << (kb + nb));
-      V acc = Ops::mul(ap[0], bp[0]);
+      using F = typename MergeOps<Ops>::type;
+      typename F::Acc acc_ = F::mul(ap[0], bp[0]);
       if (K > 0) {
 #pragma unroll
-        for (int k = 1; k < K; ++k) Ops::fma(acc, ap[k << ma], bp[k]);
+        for (int k = 1; k < K; ++k) F::fma(acc_, ap[k << ma], bp[k]);
       } else {
-        for (uint32_t k = 1; k < (1u << kb); ++k) Ops::fma(acc, ap[k << ma], bp[k]);
+        for (uint32_t k = 1; k < (1u << kb); ++k) F::fma(acc_, ap[k << ma], bp[k]);
       }
-      Ops::finish(acc);
-      C[pos0 + ((r & 1u) ? w0 : 0u) + ((r & 2u) ? w1 : 0u)] = acc;
+      C[pos0 + ((r & 1u) ? w0 : 0u) + ((r & 2u) ? w1 : 0u)] = F::result(acc_);
     }
   }
 }
@@ -621,9 +622,10 @@ __device__ __forceinline__ void level_root_unit(const LStep& q, uint32_t e0, uin
       const uint32_t k0 = part * kpart;
       const V* ap = A + m + (k0 << ma) + (b << (ma + kb));
       const V* bp = B + k0 + (n << kb) + (b << (kb + nb));
-      V acc = Ops::mul(ap[0], bp[0]);
-      for (uint32_t k = 1; k < kpart; ++k) Ops::fma(acc, ap[k << ma], bp[k]);
-      Ops::finish(acc);
+      using F = typename MergeOps<Ops>::type;
+      typename F::Acc acc_ = F::mul(ap[0], bp[0]);
+      for (uint32_t k = 1; k < kpart; ++k) F::fma(acc_, ap[k << ma], bp[k]);
+      const V acc = F::result(acc_);
       kahan_add(sr, cr, Ops::re(acc));
       kahan_add(si, ci, Ops::im(acc));
     }

@@ -49,6 +49,8 @@ struct RoundOps {
     return r;
   }
   static __device__ __forceinline__ void finish(float2&) {}
+  typedef float2 Acc;
+  static __device__ __forceinline__ float2 result(float2 v) { return v; }
   static __device__ __forceinline__ double re(float2 v) { return (double)v.x; }
   static __device__ __forceinline__ double im(float2 v) { return (double)v.y; }
 };

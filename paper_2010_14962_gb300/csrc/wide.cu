@@ -119,17 +119,17 @@ __global__ void __launch_bounds__(kThreads) wide_merge_kernel(WMergeArgs p) {
       const uint64_t o = o0 + u;
       const uint64_t m = o & mmask;
       const V* ap = A + m + (b << (p.ma + p.kb));
-      V acc = Ops::mul(ap[0], bp[0]);
+      using F = typename MergeOps<Ops>::type;
+      typename F::Acc acc_ = F::mul(ap[0], bp[0]);
       if (K > 0) {
 #pragma unroll
-        for (int k = 1; k < K; ++k) Ops::fma(acc, ap[(uint64_t)k << p.ma], bp[k]);
+        for (int k = 1; k < K; ++k) F::fma(acc_, ap[(uint64_t)k << p.ma], bp[k]);
       } else {
-        for (int k = 1; k < kcount; ++k) Ops::fma(acc, ap[(uint64_t)k << p.ma], bp[k]);
+        for (int k = 1; k < kcount; ++k) F::fma(acc_, ap[(uint64_t)k << p.ma], bp[k]);
       }
-      Ops::finish(acc);
       uint64_t pos = 0;
       for (int q = 0; q < ngroups; ++q) pos += s_pos[q][(o >> (4 * q)) & 15];
-      C[pos] = acc;
+      C[pos] = F::result(acc_);
     }
   }
 }
@@ -153,9 +153,10 @@ __global__ void __launch_bounds__(kThreads) wide_root_kernel(WMergeArgs p, int R
   const uint64_t lo = chunk * r < K ? chunk * r : K, hi = lo + chunk < K ? lo + chunk : K;
   double sr = 0, si = 0, cr = 0, ci = 0;
   for (uint64_t k0 = lo + 4 * threadIdx.x; k0 < hi; k0 += 4 * blockDim.x) {
-    V acc = Ops::mul(A[k0], B[k0]);
-    for (uint64_t k = k0 + 1; k < k0 + 4 && k < hi; ++k) Ops::fma(acc, A[k], B[k]);
-    Ops::finish(acc);
+    using F = typename MergeOps<Ops>::type;
+    typename F::Acc acc_ = F::mul(A[k0], B[k0]);
+    for (uint64_t k = k0 + 1; k < k0 + 4 && k < hi; ++k) F::fma(acc_, A[k], B[k]);
+    const V acc = F::result(acc_);
     kahan_add(sr, cr, Ops::re(acc));
     kahan_add(si, ci, Ops::im(acc));
   }
