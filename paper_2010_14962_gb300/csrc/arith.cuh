@@ -193,6 +193,21 @@ __device__ __forceinline__ void dw_fma_lazy2(x2& ah, x2& al, x2 xh, x2 xl, x2 yh
   ah = sh;
   al = x2_add(al, x2_add(e, pl));
 }
+// The same with the negated broadcast factor nyh = -yh supplied (built once
+// per B element and shared by the outputs that use it): the product is formed
+// negated, so its exact error is one FMA and the TwoSum subtracts it, one
+// packed operation fewer than dw_fma_lazy2.
+__device__ __forceinline__ void dw_fma_lazy2n(x2& ah, x2& al, x2 xh, x2 xl, x2 yh, x2 nyh, x2 yl) {
+  const x2 nph = x2_mul(xh, nyh);  // -(xh yh), rounded
+  x2 pl = x2_fma(xh, yh, nph);     // its exact rounding error
+  pl = x2_fma(xh, yl, pl);
+  pl = x2_fma(xl, yh, pl);
+  const x2 s = x2_sub(ah, nph);    // TwoSum(ah, -nph)
+  const x2 bb = x2_sub(s, ah);
+  const x2 e = x2_sub(x2_sub(ah, x2_sub(s, bb)), x2_add(nph, bb));
+  ah = s;
+  al = x2_add(al, x2_add(e, pl));
+}
 // The accumulator holds two double-word pairs: (h1, l1) collects the
 // products a.r b.r and a.i b.r (lanes: re, im), (h2, l2) collects a.r b.i and
 // -a.i b.i (lanes: im, re).  Every product takes the operand A as stored
@@ -212,8 +227,8 @@ struct CplxOpsX2 {
   }
   static __device__ __forceinline__ void fma(Acc& acc, dfc a, dfc b) {
     const x2 ah = x2_pack(a.rh, a.ih), al = x2_pack(a.rl, a.il);
-    dw_fma_lazy2(acc.h1, acc.l1, ah, al, x2_pack(b.rh, b.rh), x2_pack(b.rl, b.rl));
-    dw_fma_lazy2(acc.h2, acc.l2, ah, al, x2_pack(b.ih, -b.ih), x2_pack(b.il, -b.il));
+    dw_fma_lazy2n(acc.h1, acc.l1, ah, al, x2_pack(b.rh, b.rh), x2_pack(-b.rh, -b.rh), x2_pack(b.rl, b.rl));
+    dw_fma_lazy2n(acc.h2, acc.l2, ah, al, x2_pack(b.ih, -b.ih), x2_pack(-b.ih, b.ih), x2_pack(b.il, -b.il));
   }
   // (re, im) as a high pair and an unnormalised low pair.
   static __device__ __forceinline__ void sum(const Acc& a, x2& h, x2& l) {
