@@ -76,8 +76,10 @@ struct GraphKey {
   int prec;
   const void* gamma;  // per-bit-string angles (sweeps), or null
   const void* beta;
+  bool host_io = false;  // the graph also copies the staged bit strings in and the results out
   bool operator<(const GraphKey& o) const {
-    return std::tie(x, out, nx, prec, gamma, beta) < std::tie(o.x, o.out, o.nx, o.prec, o.gamma, o.beta);
+    return std::tie(x, out, nx, prec, gamma, beta, host_io) <
+           std::tie(o.x, o.out, o.nx, o.prec, o.gamma, o.beta, o.host_io);
   }
 };
 
@@ -286,7 +288,6 @@ struct qtn_plan {
   void free_workspace() {
     cudaFree(d_leaf_tables);
     cudaFree(d_partials);
-    cudaFree(d_err);
     cudaFree(d_jit_scratch);
     cudaFree(d_x_stage);
     cudaFree(d_out_stage);
@@ -424,13 +425,16 @@ struct qtn_plan {
     size_t lt = (size_t)nnx * max_leaf_elems() * sizeof(double2);
     QTN_CUDA(cudaMalloc(&d_leaf_tables, std::max<size_t>(lt, 16)));
     QTN_CUDA(cudaMalloc((void**)&d_partials, (size_t)nnx * nb * sizeof(Partial)));
-    QTN_CUDA(cudaMalloc((void**)&d_err, sizeof(int)));
-    QTN_CUDA(cudaMemset(d_err, 0, sizeof(int)));
+
     if (scratch) QTN_CUDA(cudaMalloc(&d_jit_scratch, (size_t)nnx * nb * scratch));
     cap_scratch = scratch;
     QTN_CUDA(cudaMalloc((void**)&d_x_stage, (size_t)nnx * net.n));
     QTN_CUDA(cudaMemset(d_x_stage, 0, (size_t)nnx * net.n));
-    QTN_CUDA(cudaMalloc((void**)&d_out_stage, (size_t)nnx * sizeof(double2)));
+    // Results (room for nnx Partials), then the executor's error word at the
+    // offset its host slot has in h_out_pinned: one copy reads both back.
+    QTN_CUDA(cudaMalloc((void**)&d_out_stage, (size_t)nnx * 2 * sizeof(double2) + 16));
+    d_err = reinterpret_cast<int*>(d_out_stage + (size_t)nnx * 2);
+    QTN_CUDA(cudaMemset(d_err, 0, sizeof(int)));
     QTN_CUDA(cudaMalloc((void**)&d_raw_stage, (size_t)nnx * sizeof(Partial)));
     QTN_CUDA(cudaMallocHost((void**)&h_x_pinned, (size_t)nnx * net.n));
     // Results, then one slot for the executor's error word (read back with them).
@@ -635,8 +639,12 @@ struct qtn_plan {
   // Enqueue the contraction of nx bit strings at d_x on `stream`: the tuned
   // executor, replayed from a CUDA graph (or launched directly with kernel
   // timing on).
+  // host_io: d_x and d_out are the staging buffers, and the launch sequence
+  // also copies the bit strings in from h_x_pinned and the results and the
+  // error word out to h_out_pinned (captured with the kernels when a graph
+  // is used).
   qtn_status run_graph(const uint8_t* d_x, int nx, qtn_precision prec, double2* d_out, cudaStream_t stream,
-                       const double* d_gamma = nullptr, const double* d_beta = nullptr) {
+                       const double* d_gamma = nullptr, const double* d_beta = nullptr, bool host_io = false) {
     Trace trace("qtn contraction launch");
     int si = 0;
     qtn_status st = tune(prec, nx, stream, &si);
@@ -652,14 +660,25 @@ struct qtn_plan {
       direct = direct || groups * slots[si].prog.wide_steps.size() + slots[si].prog.wide_prologue.size() >
                              kWideGraphMaxLaunches;
     }
+    auto copy_in = [&](cudaStream_t s) {
+      return host_io ? cudaMemcpyAsync(d_x_stage, h_x_pinned, (size_t)nx * net.n, cudaMemcpyHostToDevice, s)
+                     : cudaSuccess;
+    };
+    auto copy_out = [&](cudaStream_t s) {
+      return host_io ? cudaMemcpyAsync(h_out_pinned, d_out_stage, (size_t)cap_nx * 2 * sizeof(double2) + sizeof(int),
+                                       cudaMemcpyDeviceToHost, s)
+                     : cudaSuccess;
+    };
     if (direct) {
+      QTN_CUDA(copy_in(stream));
       cudaError_t le = launch_contraction(slots[si].dprog, arith_of(prec), d_x, nx, 0, S, buffers(), sh, scale(),
                                           d_out, nullptr, nullptr, stream, timing ? ev0 : nullptr,
                                           timing ? ev1 : nullptr, d_gamma, d_beta);
       if (le != cudaSuccess) return cuda_fail(le, "launch_contraction");
+      QTN_CUDA(copy_out(stream));
       return QTN_OK;
     }
-    GraphKey key{d_x, d_out, nx, (int)prec, d_gamma, d_beta};
+    GraphKey key{d_x, d_out, nx, (int)prec, d_gamma, d_beta, host_io};
     auto it = graphs.find(key);
     if (slots[si].exec == Executor::Wide && wide_needs_tuning(slots[si].dprog.wide)) {
       // The wide executor chooses its per-step kernels on its first launch,
@@ -669,6 +688,7 @@ struct qtn_plan {
         graphs.erase(it);
         it = graphs.end();
       }
+      QTN_CUDA(copy_in(stream));
       cudaError_t le = launch_contraction(slots[si].dprog, arith_of(prec), d_x, nx, 0, S, buffers(), sh, scale(),
                                           d_out, nullptr, nullptr, stream, nullptr, nullptr, d_gamma, d_beta);
       if (le != cudaSuccess) return cuda_fail(le, "launch_contraction (wide tuning)");
@@ -676,9 +696,11 @@ struct qtn_plan {
     if (it == graphs.end()) {
       cudaGraph_t g;
       QTN_CUDA(cudaStreamBeginCapture(capture_stream, cudaStreamCaptureModeThreadLocal));
-      cudaError_t le = launch_contraction(slots[si].dprog, arith_of(prec), d_x, nx, 0, S, buffers(), sh, scale(),
-                                          d_out, nullptr, nullptr, capture_stream, nullptr, nullptr, d_gamma,
-                                          d_beta);
+      cudaError_t le = copy_in(capture_stream);
+      if (le == cudaSuccess)
+        le = launch_contraction(slots[si].dprog, arith_of(prec), d_x, nx, 0, S, buffers(), sh, scale(), d_out,
+                                nullptr, nullptr, capture_stream, nullptr, nullptr, d_gamma, d_beta);
+      if (le == cudaSuccess) le = copy_out(capture_stream);
       cudaError_t ce = cudaStreamEndCapture(capture_stream, &g);
       if (le != cudaSuccess) return cuda_fail(le, "launch_contraction (capture)");
       if (ce != cudaSuccess) return cuda_fail(ce, "cudaStreamEndCapture");
@@ -696,6 +718,14 @@ struct qtn_plan {
   // Enqueues the read-back of the executor's error word next to the results.
   qtn_status read_err_flag(cudaStream_t stream) {
     QTN_CUDA(cudaMemcpyAsync(err_slot(), d_err, sizeof(int), cudaMemcpyDeviceToHost, stream));
+    return QTN_OK;
+  }
+  // Enqueues one read-back of the first nx results of d_out_stage and the
+  // error word (they share one device buffer laid out like h_out_pinned).
+  qtn_status read_out_and_err(int nx, cudaStream_t stream) {
+    (void)nx;
+    QTN_CUDA(cudaMemcpyAsync(h_out_pinned, d_out_stage, (size_t)cap_nx * 2 * sizeof(double2) + sizeof(int),
+                             cudaMemcpyDeviceToHost, stream));
     return QTN_OK;
   }
   // After the stream is synchronised: the word read by read_err_flag.
@@ -1246,8 +1276,7 @@ qtn_status qtn_contract_amplitude(const qtn_plan_t* cplan, const uint8_t* x, qtn
   QTN_CUDA(cudaMemcpyAsync(plan->d_x_stage, plan->h_x_pinned, plan->net.n, cudaMemcpyHostToDevice, stream));
   st = plan->run_graph(plan->d_x_stage, 1, prec, plan->d_out_stage, stream);
   if (st != QTN_OK) return st;
-  QTN_CUDA(cudaMemcpyAsync(plan->h_out_pinned, plan->d_out_stage, sizeof(double2), cudaMemcpyDeviceToHost, stream));
-  st = plan->read_err_flag(stream);
+  st = plan->read_out_and_err(1, stream);
   if (st != QTN_OK) return st;
   QTN_CUDA(cudaStreamSynchronize(stream));
   st = plan->check_err_flag();
@@ -1318,13 +1347,8 @@ qtn_status qtn_contract_batch(const qtn_plan_t* const* plans, const uint8_t* con
     st = plan->prepare(si, prec, njobs, plan->slots[si].items(), &sh);
     if (st != QTN_OK) return st;
     for (int i = 0; i < njobs; ++i) std::memcpy(plan->h_x_pinned + (size_t)i * plan->net.n, xs[i], plan->net.n);
-    QTN_CUDA(cudaMemcpyAsync(plan->d_x_stage, plan->h_x_pinned, (size_t)njobs * plan->net.n,
-                             cudaMemcpyHostToDevice, stream));
-    st = plan->run_graph(plan->d_x_stage, njobs, prec, plan->d_out_stage, stream);
-    if (st != QTN_OK) return st;
-    QTN_CUDA(cudaMemcpyAsync(plan->h_out_pinned, plan->d_out_stage, (size_t)njobs * sizeof(double2),
-                             cudaMemcpyDeviceToHost, stream));
-    st = plan->read_err_flag(stream);
+    // Copy-in, kernels and copy-out (results with the error word) as one graph.
+    st = plan->run_graph(plan->d_x_stage, njobs, prec, plan->d_out_stage, stream, nullptr, nullptr, true);
     if (st != QTN_OK) return st;
     QTN_CUDA(cudaStreamSynchronize(stream));
     st = plan->check_err_flag();
