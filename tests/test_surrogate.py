@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 from oracle import mlp_reference as R
+from oracle import oracle as O_
 from paper_2010_14962_gb300 import instances as I
 from paper_2010_14962_gb300 import qtn
 
@@ -158,3 +159,11 @@ def test_learned_planner_n120(trained):
           "| exact-counter plan", plan_e.cost()["log2_flops"], "time", times[1])
     assert plan_s.cost()["log2_flops"] <= plan_e.cost()["log2_flops"] + 1e-9
     assert abs(vals[0] - vals[1]) < 1e-10 * abs(vals[1])
+    # The surrogate plan's own slices against the oracle on the same cut set
+    # (a sampled range of its 4 M slices, FP64 form).
+    lo, hi = 3 << 20, (3 << 20) + 128
+    total, comp, per = plan_s.contract_slices(x, lo, hi, "fp64", per_slice=True)
+    ref = O_.tn_amplitude(120, inst.edges, inst.gamma, inst.beta, x, cuts=plan_s.cut_names(), slices=(lo, hi),
+                          per_slice=True, threads=16)
+    mag = np.max(np.abs(ref.per_slice))
+    assert mag > 0 and np.max(np.abs(per * 2.0 ** -60 - ref.per_slice)) <= 1e-12 * mag

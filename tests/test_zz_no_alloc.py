@@ -3,8 +3,9 @@
 It serves callers that cannot let the library call cudaMalloc (a framework
 that already holds the device memory in its own pool, or code where an
 allocation is not allowed).  Checked through the C ABI against
-qtn_contract_amplitudes_device on two calls in a row, within the tolerances
-of the parity tests (complex128: 1e-10 relative; complex64: 2e-5 relative),
+qtn_contract_amplitudes_device on two calls in a row (and that path against
+the oracle), within the tolerances of the parity tests (complex128: 1e-10
+relative; complex64: 2e-5 relative),
 and the second call must leave the device's free memory unchanged.  The
 first call on a device may reserve the 64 MiB array (CUDA loads the library
 part that holds it lazily, at that call) and nothing more.  This file
@@ -16,6 +17,7 @@ import ctypes
 import numpy as np
 import pytest
 
+from oracle import oracle as O
 from paper_2010_14962_gb300 import instances as I
 from paper_2010_14962_gb300 import qtn
 
@@ -67,6 +69,10 @@ def test_noalloc_matches_device_path(gpu, prec, n, p, k, nx, call):
     for o in outs:
         got = o[:, 0].cpu().numpy() + 1j * o[:, 1].cpu().numpy()
         assert np.all(np.abs(got - want) <= TOL[prec] * np.abs(want))
+    # and both against the oracle on the same cut set
+    oracle = np.array([O.tn_amplitude(n, inst.edges, inst.gamma, inst.beta, x, cuts=plan.cut_names(), threads=8).value
+                       for x in xs])
+    assert np.all(np.abs(want - oracle) <= TOL[prec] * np.abs(oracle))
 
 
 def test_noalloc_rejects_double_float(gpu):
