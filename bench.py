@@ -860,25 +860,31 @@ def run_learned(args, rank, world, local_rank):
     t_exact = (time.perf_counter() - t0) / len(sets)
     eval_cost = t_feat / t_exact
     searches = {}
-    for label, seed_greedy, seed in (("random_start_seed1", False, 1), ("random_start_seed2", False, 2),
-                                     ("random_start_seed3", False, 3), ("greedy_seeded", True, 1)):
+    nets = {w["seed"]: net}
+    for g in (6, 7):
+        gi = I.qaoa_instance(w["n"], w["p"], g)
+        nets[g] = qtn.Network(w["n"], gi.edges, gi.gamma, gi.beta)
+    runs = [(f"graph{g}_random_start_seed{sd}", g, False, sd) for g in nets for sd in (1, 2, 3)]
+    runs.append(("greedy_seeded", w["seed"], True, 1))
+    for label, g, seed_greedy, seed in runs:
+        net_g = nets[g]
         t0 = time.perf_counter()
-        cuts_s, best_s, n_exact, n_sur, _ = qtn.search_cuts_surrogate(net, w["k"], m, T=10, N=256, top=4, seed=seed,
+        cuts_s, best_s, n_exact, n_sur, _ = qtn.search_cuts_surrogate(net_g, w["k"], m, T=10, N=256, top=4, seed=seed,
                                                                        seed_greedy=seed_greedy)
         t_s = time.perf_counter() - t0
         budget = n_exact + eval_cost * n_sur
         t0 = time.perf_counter()
-        cuts_e, _, n_ga = qtn.search_cuts(net, w["k"], "ga_flops", seed=seed, ga_T=max(1, int(budget // 11) - 1),
+        cuts_e, _, n_ga = qtn.search_cuts(net_g, w["k"], "ga_flops", seed=seed, ga_T=max(1, int(budget // 11) - 1),
                                           ga_N=11, seed_greedy=seed_greedy)
         t_e = time.perf_counter() - t0
-        best_e = float(qtn.surrogate_labels(net, cuts_e)[0])
+        best_e = float(qtn.surrogate_labels(net_g, cuts_e)[0])
         searches[label] = dict(
             budget_exact_evals=budget,
             surrogate=dict(log2_flops=float(best_s), surrogate_evals=n_sur, exact_evals=n_exact, search_s=t_s,
                            cuts=[int(c) for c in cuts_s]),
             exact=dict(log2_flops=best_e, exact_evals=n_ga, search_s=t_e, cuts=[int(c) for c in cuts_e]))
     gains = [searches[k]["exact"]["log2_flops"] - searches[k]["surrogate"]["log2_flops"]
-             for k in searches if k.startswith("random_start")]
+             for k in searches if "random_start" in k]
     pick = searches["greedy_seeded"]
     plans = {"surrogate": qtn.Plan(net, cuts=pick["surrogate"]["cuts"], max_slice_bytes=150e9),
              "exact": qtn.Plan(net, cuts=pick["exact"]["cuts"], max_slice_bytes=150e9)}
@@ -921,6 +927,7 @@ def run_learned(args, rank, world, local_rank):
                    "feature_s": t_feat, "exact_count_s": t_exact, "surrogate_eval_cost": eval_cost,
                    "searches": searches,
                    "random_start_mean_gain_log2_flops": float(np.mean(gains)),
+                   "random_start_gains_log2_flops": [float(x) for x in gains],
                    "contracted": results, "max_rel_diff_between_plans": agree,
                    "memory_cap_bytes": 150e9},
     }
