@@ -143,7 +143,7 @@ def _stream_handle(stream):
         try:
             import torch
 
-            if torch.cuda.is_available() and torch.cuda.is_initialized():
+            if torch.cuda.is_initialized():  # (implies a device; cheaper than is_available)
                 return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
         except Exception:
             pass
