@@ -333,6 +333,14 @@ def run_ours(args, rank, world, local_rank):
                                         % INSTR_PER_MAC.get(args.precision)),
                      "measured_peaks_tflops": {"fp32": pipe_peaks["fp32_tflops"], "fp64": pipe_peaks["fp64_tflops"],
                                                "fp32x2": pipe_peaks.get("fp32x2_tflops")},
+                     "attainable": ({"tflops": peak / INSTR_PER_MAC[args.precision],
+                                     "frac": achieved * INSTR_PER_MAC[args.precision] / peak,
+                                     "def": ("every step class of this program is on chip (shared memory), so the "
+                                             "attainable rate is the FP32 pipe's at %s FP32 operations per real "
+                                             "multiply-add of the arithmetic" % INSTR_PER_MAC[args.precision])}
+                                    if args.precision in INSTR_PER_MAC else
+                                    {"tflops": peak, "frac": achieved / peak,
+                                     "def": "FP64 pipe, one FMA per real multiply-add"}),
                      "kernel_ms_avg": avg_kernel_s * 1e3,
                      "step_classes": step_classes(prog, 8 if args.precision in ("fp32", "tf32", "bf16x3", "tf32x3",
                                                                                 "bf16x6") else 16)},
