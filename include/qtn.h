@@ -378,6 +378,19 @@ qtn_status qtn_pipe_peaks(int reps, double* fp32_tflops, double* fp64_tflops);
  * output or reps < 1, QTN_ERR_CUDA if a launch fails. */
 qtn_status qtn_pipe_peak_fp32x2(int reps, double* tflops);
 
+/* Check of the double-float (QTN_FP32X2) arithmetic on the device (test
+ * support; the paper has no counterpart): `count` complex dot products of K
+ * terms, a (host, count x K complex values as re, im pairs, row i = item i)
+ * times b (same layout), each operand rounded to a double word.
+ * out_scalar[2i..2i+1] (host) gets item i by the scalar double-float
+ * sequence, out_merge by the form the contraction kernels' merge loops run
+ * (packed FP32 pairs on sm_100 and later, then *packed = 1; packed may be
+ * NULL).  Allocates and frees its own device buffers and synchronises.
+ * QTN_ERR_INVALID_ARG for null pointers, count < 0, count > 2^24, K < 1 or
+ * K > 4096; QTN_ERR_CUDA if a CUDA call fails. */
+qtn_status qtn_arith_check(const double* a, const double* b, int count, int K, double* out_scalar,
+                           double* out_merge, int* packed);
+
 /* ------------------------------------------------ learned cost surrogate --
  * A small MLP predicts the exact counter's log2 total flops and log2 peak
  * bytes of cutting a set of indices (min-fill plan) from cheap features, so a

@@ -1338,7 +1338,39 @@ cudaError_t launch_multi_typed(const JobDesc* d_jobs, int njobs, uint32_t total_
   return cudaGetLastError();
 }
 
+// Check of the double-float arithmetic: item i is the complex dot product
+// sum_k a[i, k] b[i, k] of K terms (operands rounded to double words), by the
+// scalar sequence (CplxOps<dfc>) and by the form the merge loops run
+// (MergeOps: packed FP32 pairs where the device has them).
+__global__ void arith_check_kernel(const double2* __restrict__ a, const double2* __restrict__ b, int count, int K,
+                                   double2* __restrict__ out_scalar, double2* __restrict__ out_merge) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  typedef CplxOps<dfc> S;
+  typedef MergeOps<S>::type M;
+  const double2* pa = a + (size_t)i * K;
+  const double2* pb = b + (size_t)i * K;
+  dfc s = S::mul(S::from(pa[0].x, pa[0].y), S::from(pb[0].x, pb[0].y));
+  M::Acc m = M::mul(S::from(pa[0].x, pa[0].y), S::from(pb[0].x, pb[0].y));
+  for (int k = 1; k < K; ++k) {
+    const dfc x = S::from(pa[k].x, pa[k].y), y = S::from(pb[k].x, pb[k].y);
+    S::fma(s, x, y);
+    M::fma(m, x, y);
+  }
+  s = S::result(s);
+  const dfc r = M::result(m);
+  out_scalar[i] = make_double2(S::re(s), S::im(s));
+  out_merge[i] = make_double2(S::re(r), S::im(r));
+}
+
 }  // namespace
+
+cudaError_t launch_arith_check(const double2* d_a, const double2* d_b, int count, int K, double2* d_scalar,
+                               double2* d_merge, cudaStream_t stream) {
+  if (count <= 0) return cudaSuccess;
+  arith_check_kernel<<<(count + 127) / 128, 128, 0, stream>>>(d_a, d_b, count, K, d_scalar, d_merge);
+  return cudaGetLastError();
+}
 
 int arith_elem_bytes(Arith a) { return (a == Arith::F64 || a == Arith::F32X2) ? 16 : 8; }
 

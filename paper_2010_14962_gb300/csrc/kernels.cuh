@@ -103,6 +103,11 @@ bool exec_shape(const DeviceProgram& prog, Arith arith, int nx, uint64_t slices_
 //   ev0, ev1  : optional events recorded just before / after the executor
 //   d_gamma, d_beta : optional nx * p angles (device), one set per bit
 //               string; null: the program's angles for all
+// The double-float arithmetic check (qtn_arith_check): count complex dot
+// products of K terms each (device arrays), scalar and merge-loop forms.
+cudaError_t launch_arith_check(const double2* d_a, const double2* d_b, int count, int K, double2* d_scalar,
+                               double2* d_merge, cudaStream_t stream);
+
 cudaError_t launch_contraction(const DeviceProgram& prog, Arith arith, const uint8_t* d_x, int nx,
                                uint64_t slice_lo, uint64_t slice_hi, const LaunchBuffers& buf,
                                const ExecShape& shape, double scale, double2* d_out, Partial* d_raw,

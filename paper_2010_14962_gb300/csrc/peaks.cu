@@ -8,6 +8,7 @@
 #include <string>
 
 #include "internal.hpp"
+#include "kernels.cuh"
 
 namespace qtn {
 namespace {
@@ -149,5 +150,33 @@ extern "C" qtn_status qtn_pipe_peak_fp32x2(int reps, double* tflops) {
   cudaError_t e = qtn::time_pipe<float>(1 << 13, reps, &t, true);
   if (e != cudaSuccess) return set_error(QTN_ERR_CUDA, std::string("qtn_pipe_peak_fp32x2: ") + cudaGetErrorString(e));
   *tflops = t;
+  return QTN_OK;
+}
+
+extern "C" qtn_status qtn_arith_check(const double* a, const double* b, int count, int K, double* out_scalar,
+                                      double* out_merge, int* packed) {
+  using qtn::internal::set_error;
+  if (!a || !b || !out_scalar || !out_merge || count < 0 || K < 1 || count > (1 << 24) || K > 4096)
+    return set_error(QTN_ERR_INVALID_ARG, "qtn_arith_check: bad argument");
+  int dev = 0, major = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  if (packed) *packed = major >= 10 ? 1 : 0;
+  const size_t in = (size_t)count * K * sizeof(double2), out = (size_t)count * sizeof(double2);
+  double2 *d_a = nullptr, *d_b = nullptr, *d_s = nullptr, *d_m = nullptr;
+  if (e == cudaSuccess) e = cudaMalloc(&d_a, in + 16);
+  if (e == cudaSuccess) e = cudaMalloc(&d_b, in + 16);
+  if (e == cudaSuccess) e = cudaMalloc(&d_s, out + 16);
+  if (e == cudaSuccess) e = cudaMalloc(&d_m, out + 16);
+  if (e == cudaSuccess) e = cudaMemcpy(d_a, a, in, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(d_b, b, in, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = qtn::launch_arith_check(d_a, d_b, count, K, d_s, d_m, nullptr);
+  if (e == cudaSuccess) e = cudaMemcpy(out_scalar, d_s, out, cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(out_merge, d_m, out, cudaMemcpyDeviceToHost);
+  cudaFree(d_a);
+  cudaFree(d_b);
+  cudaFree(d_s);
+  cudaFree(d_m);
+  if (e != cudaSuccess) return set_error(QTN_ERR_CUDA, std::string("qtn_arith_check: ") + cudaGetErrorString(e));
   return QTN_OK;
 }

@@ -111,6 +111,7 @@ def lib():
                                           P(ctypes.c_int), f64p, ctypes.c_int, P(ctypes.c_int)],
             "qtn_pipe_peaks": [ctypes.c_int, f64p, f64p],
             "qtn_pipe_peak_fp32x2": [ctypes.c_int, f64p],
+            "qtn_arith_check": [f64p, f64p, ctypes.c_int, ctypes.c_int, f64p, f64p, P(ctypes.c_int)],
             "qtn_wide_set_kernel": [ctypes.c_char_p],
             "qtn_status_string": [ctypes.c_int],
             "qtn_last_error": [],
@@ -436,6 +437,24 @@ def pipe_peaks(reps: int = 3) -> dict:
     f32, f64 = ctypes.c_double(), ctypes.c_double()
     _check(lib().qtn_pipe_peaks(int(reps), ctypes.byref(f32), ctypes.byref(f64)))
     return {"fp32_tflops": f32.value, "fp64_tflops": f64.value}
+
+
+def arith_check(a: np.ndarray, b: np.ndarray):
+    """qtn_arith_check: complex dot products over the last axis of a and b
+    (count x K complex128) in double-float arithmetic on the device, by the
+    scalar sequence and by the merge loops' form.  (scalar, merge, packed)."""
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    b = np.ascontiguousarray(b, dtype=np.complex128)
+    if a.shape != b.shape or a.ndim != 2:
+        raise ValueError("a and b must be count x K arrays of one shape")
+    count, K = a.shape
+    s = np.zeros(count, dtype=np.complex128)
+    m = np.zeros(count, dtype=np.complex128)
+    packed = ctypes.c_int()
+    _check(lib().qtn_arith_check(_ptr(a.view(np.float64), ctypes.c_double), _ptr(b.view(np.float64), ctypes.c_double),
+                                 count, K, _ptr(s.view(np.float64), ctypes.c_double),
+                                 _ptr(m.view(np.float64), ctypes.c_double), ctypes.byref(packed)))
+    return s, m, bool(packed.value)
 
 
 def pipe_peak_fp32x2(reps: int = 3) -> float:
