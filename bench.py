@@ -124,7 +124,9 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-KERNEL_SOURCES = ("kernels.cu", "jit.cpp", "arith.cuh")  # what the benchmark's executor is generated and built from
+# What the benchmark's executor (the kernel generated per plan) is generated from: the program compiler, the
+# generator and the arithmetic it embeds.
+KERNEL_SOURCES = ("program.hpp", "program.cpp", "jit.cpp", "arith.cuh")
 
 
 def kernel_source_hash() -> str:
