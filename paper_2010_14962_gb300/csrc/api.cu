@@ -349,6 +349,17 @@ struct qtn_plan {
     dev_allocs.push_back(ga);
     QTN_CUDA(::upload(&be, net.beta));
     dev_allocs.push_back(be);
+    // cos and sin of every layer's angles, once per program (the leaf
+    // kernel's blocks would otherwise each evaluate them on the narrow FP64
+    // pipe); evaluated by the device's sincos, as a parameter scan evaluates
+    // its own angles, so equal angles give equal leaves on both paths.
+    double* tr = nullptr;
+    if (!net.gamma.empty()) {
+      QTN_CUDA(cudaMalloc((void**)&tr, 4 * net.gamma.size() * sizeof(double)));
+      dev_allocs.push_back(tr);
+      QTN_CUDA(launch_trig_table(ga, be, (int)net.gamma.size(), tr, nullptr));
+      QTN_CUDA(cudaStreamSynchronize(nullptr));
+    }
     DevLevel *lvls = nullptr, *plvls = nullptr;
     uint32_t *ost = nullptr, *post = nullptr;
     if (!pg.levels.empty()) {
@@ -404,6 +415,7 @@ struct qtn_plan {
     d.gate_kind = gk;
     d.gamma = ga;
     d.beta = be;
+    d.trig = tr;
     sl.uploaded = true;
     return QTN_OK;
   }

@@ -208,7 +208,8 @@ __global__ void leaf_build_kernel(const DevLeaf* __restrict__ leaves, const int3
                                   const int8_t* __restrict__ gate_out_kind, const int8_t* __restrict__ gate_kind,
                                   const double* __restrict__ gamma,
                                   const double* __restrict__ beta, int angle_stride, const uint8_t* __restrict__ x,
-                                  int n, uint32_t leaf_elems, int n_leaves, bool density, V* __restrict__ out) {
+                                  int n, uint32_t leaf_elems, int n_leaves, bool density, V* __restrict__ out,
+                                  const double* __restrict__ trig) {
   __shared__ double s_t[4];  // trig values of the leaf's layer, once per block
   const DevLeaf L = leaves[blockIdx.x % n_leaves];
   const int xi = blockIdx.x / n_leaves;
@@ -221,8 +222,12 @@ __global__ void leaf_build_kernel(const DevLeaf* __restrict__ leaves, const int3
     s_t[3] = 0.0;
     if (L.gate >= 0) {
       const int l = gate_layer[L.gate];
-      sincos(gamma[(size_t)xi * angle_stride + l], &s_t[1], &s_t[0]);
-      sincos(beta[(size_t)xi * angle_stride + l], &s_t[3], &s_t[2]);
+      if (trig) {  // the layer's values, evaluated once per program (fixed angles)
+        for (int j = 0; j < 4; ++j) s_t[j] = trig[4 * l + j];
+      } else {
+        sincos(gamma[(size_t)xi * angle_stride + l], &s_t[1], &s_t[0]);
+        sincos(beta[(size_t)xi * angle_stride + l], &s_t[3], &s_t[2]);
+      }
     }
   }
   __syncthreads();
@@ -1224,7 +1229,7 @@ cudaError_t launch_typed(const DeviceProgram& prog, const uint8_t* d_x, int nx, 
                                                  prog.gate_out_kind, prog.gate_kind, sweep ? d_gamma : prog.gamma,
                                                  sweep ? d_beta : prog.beta, sweep ? prog.p : 0, d_x, prog.n,
                                                  prog.leaf_elems, prog.n_leaves, prog.density != 0,
-                                                 static_cast<V*>(buf.leaf_tables));
+                                                 static_cast<V*>(buf.leaf_tables), sweep ? nullptr : prog.trig);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (prog.exec == Executor::Wide) {
@@ -1338,6 +1343,16 @@ cudaError_t launch_multi_typed(const JobDesc* d_jobs, int njobs, uint32_t total_
   return cudaGetLastError();
 }
 
+// cos and sin of each layer's gamma and beta, as the leaf kernel evaluates
+// them: out[4 l ..] = (cos gamma_l, sin gamma_l, cos beta_l, sin beta_l).
+__global__ void trig_table_kernel(const double* __restrict__ gamma, const double* __restrict__ beta, int p,
+                                  double* __restrict__ out) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= p) return;
+  sincos(gamma[l], &out[4 * l + 1], &out[4 * l]);
+  sincos(beta[l], &out[4 * l + 3], &out[4 * l + 2]);
+}
+
 // Check of the double-float arithmetic: item i is the complex dot product
 // sum_k a[i, k] b[i, k] of K terms (operands rounded to double words), by the
 // scalar sequence (CplxOps<dfc>) and by the form the merge loops run
@@ -1364,6 +1379,12 @@ __global__ void arith_check_kernel(const double2* __restrict__ a, const double2*
 }
 
 }  // namespace
+
+cudaError_t launch_trig_table(const double* d_gamma, const double* d_beta, int p, double* d_out, cudaStream_t stream) {
+  if (p <= 0) return cudaSuccess;
+  trig_table_kernel<<<(p + 31) / 32, 32, 0, stream>>>(d_gamma, d_beta, p, d_out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_arith_check(const double2* d_a, const double2* d_b, int count, int K, double2* d_scalar,
                                double2* d_merge, cudaStream_t stream) {

@@ -49,6 +49,7 @@ struct DeviceProgram {
   const int8_t* gate_in_h = nullptr;
   const int8_t* gate_out_kind = nullptr;
   const double* gamma = nullptr;
+  const double* trig = nullptr;  // p x (cos gamma, sin gamma, cos beta, sin beta), once per program; may be null
   const double* beta = nullptr;
   int density = 0;  // leaves are G (x) conj(G) (density form)
   const int8_t* gate_kind = nullptr;  // GateKind per gate
@@ -103,6 +104,9 @@ bool exec_shape(const DeviceProgram& prog, Arith arith, int nx, uint64_t slices_
 //   ev0, ev1  : optional events recorded just before / after the executor
 //   d_gamma, d_beta : optional nx * p angles (device), one set per bit
 //               string; null: the program's angles for all
+// The per-layer trig table of a program's fixed angles (device sincos).
+cudaError_t launch_trig_table(const double* d_gamma, const double* d_beta, int p, double* d_out, cudaStream_t stream);
+
 // The double-float arithmetic check (qtn_arith_check): count complex dot
 // products of K terms each (device arrays), scalar and merge-loop forms.
 cudaError_t launch_arith_check(const double2* d_a, const double2* d_b, int count, int K, double2* d_scalar,
