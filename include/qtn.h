@@ -455,6 +455,19 @@ qtn_status qtn_search_cuts_surrogate(const qtn_network_t* net, int k, qtn_mlp_t*
  * when `cap` is large enough; always sets *len to the size needed. */
 qtn_status qtn_plan_describe(const qtn_plan_t* plan, char* buf, size_t cap, size_t* len);
 
+/* The schedule the kernel generator would give level program `program` (a
+ * name from qtn_plan_describe's "programs") for precision `prec`, with
+ * `smem_cap` bytes of shared memory per block, as JSON (test support for the
+ * generator's host logic; no device is used): items per pass, arena stride,
+ * and for two_phase != 0 the split level, the items per pass and arena
+ * stride of the levels below it, and the tensors it parks ([arena offset,
+ * elements, park offset] each).  Buffer convention as qtn_plan_describe.
+ * QTN_ERR_INVALID_ARG for an unknown program or precision;
+ * QTN_ERR_UNSUPPORTED if it is not a level program or no schedule of that
+ * form fits. */
+qtn_status qtn_plan_jit_schedule(const qtn_plan_t* plan, const char* program, qtn_precision prec, int two_phase,
+                                 size_t smem_cap, char* buf, size_t cap, size_t* len);
+
 const char* qtn_status_string(qtn_status s);
 const char* qtn_last_error(void); /* per host thread; "" if none */
 

@@ -1708,6 +1708,39 @@ qtn_status qtn_batch_last_ms(float* ms, int* kernels) {
   return QTN_OK;
 }
 
+qtn_status qtn_plan_jit_schedule(const qtn_plan_t* plan, const char* program, qtn_precision prec, int two_phase,
+                                 size_t smem_cap, char* buf, size_t cap, size_t* len) {
+  if (!plan || !program || !len) return fail(QTN_ERR_INVALID_ARG, "NULL argument");
+  if (!precision_supported(prec)) return fail(QTN_ERR_INVALID_ARG, "unknown precision");
+  const ProgSlot* sl = nullptr;
+  for (const ProgSlot& s : plan->slots)
+    if (s.name == program) sl = &s;
+  if (!sl) return fail(QTN_ERR_INVALID_ARG, std::string("no program named ") + program);
+  if (sl->exec != Executor::Level) return fail(QTN_ERR_UNSUPPORTED, "not a level program");
+  JitLevelShape sh;
+  if (!jit_level_schedule(sl->prog, arith_elem_bytes(arith_of(prec)), sl->threads, sl->blocks_per_sm, smem_cap,
+                          two_phase != 0, &sh))
+    return fail(QTN_ERR_UNSUPPORTED, "no schedule of this form fits");
+  std::vector<JitCrossing> cr;
+  uint32_t ext = 0;
+  if (sh.split_level && !jit_crossings(sl->prog, (size_t)sh.split_level, &cr, &ext))
+    return fail(QTN_ERR_UNSUPPORTED, "not a valid level program");
+  std::ostringstream o;
+  o.precision(17);
+  o << "{\"threads\":" << sh.threads << ",\"log2_items\":" << sh.log2_items << ",\"arena_stride\":" << sh.arena_stride
+    << ",\"smem\":" << sh.smem << ",\"split_level\":" << sh.split_level << ",\"log2_forest\":" << sh.log2_forest
+    << ",\"forest_stride\":" << sh.forest_stride << ",\"forest_extent\":" << ext << ",\"cross_elems\":"
+    << sh.cross_elems << ",\"est\":" << sh.est_cost << ",\"est_single\":" << sh.est_cost_single
+    << ",\"crossings\":[";
+  for (size_t i = 0; i < cr.size(); ++i)
+    o << (i ? "," : "") << "[" << cr[i].off << "," << cr[i].size << "," << cr[i].at << "]";
+  o << "]}";
+  const std::string t = o.str();
+  *len = t.size() + 1;
+  if (buf && cap >= t.size() + 1) std::memcpy(buf, t.c_str(), t.size() + 1);
+  return QTN_OK;
+}
+
 qtn_status qtn_plan_describe(const qtn_plan_t* plan, char* buf, size_t cap, size_t* len) {
   if (!plan || !len) return fail(QTN_ERR_INVALID_ARG, "NULL argument");
   std::ostringstream o;

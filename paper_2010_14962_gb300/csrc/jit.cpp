@@ -263,9 +263,7 @@ void emit_level(std::ostringstream& o, const Program& pg, size_t l, int UL, int 
 
 // Tensors made below level `split` and read at or above it (offset, size),
 // and the arena extent of the levels below `split`.
-struct Crossing {
-  uint32_t off, size, at;
-};
+using Crossing = JitCrossing;
 bool crossings(const Program& pg, size_t split, std::vector<Crossing>* out, uint32_t* extent) {
   std::vector<int> level_of(pg.steps.size());
   for (size_t l = 0; l < pg.levels.size(); ++l)
@@ -311,6 +309,10 @@ bool crossings(const Program& pg, size_t split, std::vector<Crossing>* out, uint
 }
 
 }  // namespace
+
+bool jit_crossings(const Program& pg, size_t split, std::vector<JitCrossing>* out, uint32_t* extent) {
+  return crossings(pg, split, out, extent);
+}
 
 bool jit_available(std::string* why) {
   Nvrtc& n = nvrtc();

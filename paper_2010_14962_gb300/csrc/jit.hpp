@@ -10,6 +10,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include "kernels.cuh"
 #include "program.hpp"
@@ -55,6 +56,15 @@ bool jit_level_shape(const Program& pg, int elem_bytes, int threads, int blocks_
 // block (no device query).
 bool jit_level_schedule(const Program& pg, int elem_bytes, int threads, int bps, size_t cap, bool two_phase,
                         JitLevelShape* out);
+
+// Tensors a two-phase schedule with split level `split` parks: (arena
+// offset, elements, offset in the per-item park area) each, and the arena
+// extent of the levels below `split`.  False if an arena operand has no
+// writer (not a valid level program).
+struct JitCrossing {
+  uint32_t off, size, at;
+};
+bool jit_crossings(const Program& pg, size_t split, std::vector<JitCrossing>* out, uint32_t* extent);
 
 // CUDA source of the specialised kernel ("qtn_level_jit"); empty (and *err
 // set) if the program has a form the generator does not handle.

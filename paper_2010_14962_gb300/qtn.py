@@ -84,6 +84,8 @@ def lib():
             "qtn_contract_batch": [P(vp), vp, ctypes.c_int, ctypes.c_int, vp, vp],
             "qtn_plan_executor": [vp, P(ctypes.c_char_p)],
             "qtn_plan_describe": [vp, ctypes.c_char_p, ctypes.c_size_t, P(ctypes.c_size_t)],
+            "qtn_plan_jit_schedule": [vp, ctypes.c_char_p, ctypes.c_int, ctypes.c_int, ctypes.c_size_t,
+                                      ctypes.c_char_p, ctypes.c_size_t, P(ctypes.c_size_t)],
             "qtn_plan_set_kernel_timing": [vp, ctypes.c_int],
             "qtn_plan_select_executor": [vp, ctypes.c_int, ctypes.c_int, ctypes.c_char_p],
             "qtn_plan_kernel_ms": [vp, P(ctypes.c_float)],
@@ -313,6 +315,17 @@ class Plan:
         _check(lib().qtn_plan_describe(self._h, None, 0, ctypes.byref(need)))
         buf = ctypes.create_string_buffer(need.value)
         _check(lib().qtn_plan_describe(self._h, buf, need.value, ctypes.byref(need)))
+        return json.loads(buf.value.decode())
+
+    def jit_schedule(self, program: str, precision: str = "fp32x2", two_phase: bool = True,
+                     smem_cap: int = 232448) -> dict:
+        """qtn_plan_jit_schedule: the generated kernel's schedule for a level
+        program (host only; smem_cap defaults to a GB300 block's opt-in)."""
+        need = ctypes.c_size_t()
+        args = (self._h, program.encode(), PRECISIONS[precision], int(bool(two_phase)), ctypes.c_size_t(smem_cap))
+        _check(lib().qtn_plan_jit_schedule(*args, None, 0, ctypes.byref(need)))
+        buf = ctypes.create_string_buffer(need.value)
+        _check(lib().qtn_plan_jit_schedule(*args, buf, need.value, ctypes.byref(need)))
         return json.loads(buf.value.decode())
 
     def select_executor(self, name: str, precision: str = "fp32", nx: int = 1):
