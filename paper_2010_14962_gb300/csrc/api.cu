@@ -540,7 +540,10 @@ struct qtn_plan {
     const void* kernel = nullptr;
     {
       Trace trace("qtn jit compile");
-      if (!jit_compile(src, shape.smem, &kernel, &err)) return fail(QTN_ERR_UNSUPPORTED, err);
+      const size_t pro_smem = jit_prologue_smem(js.prog, arith_elem_bytes(a));
+      if (!jit_compile(src, shape.smem, &kernel, &err, pro_smem, &js.dprog.jit_prologue))
+        return fail(QTN_ERR_UNSUPPORTED, err);
+      js.dprog.jit_pro_smem = pro_smem;
     }
     js.dprog.exec = Executor::LevelJit;
     js.dprog.jit_kernel = kernel;

@@ -129,7 +129,10 @@ void emit_merge(std::ostringstream& o, const Program& pg, const DevStep& st, uin
   o << "      const V* __restrict__ B = " << operand(pg, st.flags & STEP_B_LEAF, st.b) << ";\n";
   o << "      const unsigned e0 = (uf - " << beg << "u) << " << ulog << ";\n";
   if (!root) {
-    o << "      V* __restrict__ C = arena + " << st.c << "u;\n";
+    if (st.flags & STEP_EXPORT)  // hoisted result: a pseudo-leaf of the bit string's global leaf table
+      o << "      V* __restrict__ C = g_lt + " << pg.leaves[st.c].base << "u;\n";
+    else
+      o << "      V* __restrict__ C = arena + " << st.c << "u;\n";
     o << "      const unsigned p0 = " << pos_expr("e0", st.w, ulog, rc) << ";\n";
   }
   const uint32_t kpart = 1u << (kb - ks);
@@ -516,10 +519,34 @@ std::string jit_level_source(const Program& pg, Arith a, const JitLevelShape& sh
   o << "  s_red[threadIdx.x] = Partial::make(sr + ((double)qrh + (double)qrl), si + ((double)qih + (double)qil), cr, ci);\n";
   o << "  tree_reduce(s_red, " << T << ");\n";
   o << "  if (threadIdx.x == 0) partials[(size_t)xi * blocks_per_x + bx] = s_red[0];\n}\n";
+  // The hoisted merges (prologue levels, once per bit string: one block of
+  // kJitPrologueThreads), also as straight code: their operands are leaves
+  // without outer cut bits and the prologue arena; exports go to the global
+  // leaf table.
+  if (!pg.prologue.empty() && !pg.pro_levels.empty()) {
+    Program pp;
+    pp.leaves = pg.leaves;
+    pp.steps = pg.prologue;
+    pp.levels = pg.pro_levels;
+    const int PT = kJitPrologueThreads;
+    o << "extern \"C\" __global__ void __launch_bounds__(" << PT << ", 1) qtn_prologue_jit(V* __restrict__ leaf_tables) {\n";
+    o << "  extern __shared__ __align__(16) unsigned char smem[];\n";
+    o << "  V* s_lt = reinterpret_cast<V*>(smem);\n";
+    o << "  V* s_arena = reinterpret_cast<V*>(smem + " << table << ");\n";
+    o << "  V* __restrict__ g_lt = leaf_tables + (size_t)blockIdx.x * " << pg.leaf_elems << "u;\n";
+    o << "  {\n    const unsigned* src = reinterpret_cast<const unsigned*>(g_lt);\n"
+      << "    unsigned* dst = reinterpret_cast<unsigned*>(s_lt);\n"
+      << "    for (unsigned i = threadIdx.x; i < " << (size_t)pg.leaf_elems * elem / 4 << "u; i += " << PT
+      << "u) dst[i] = src[i];\n  }\n  __syncthreads();\n";
+    o << "  const unsigned long long s0 = 0ull;\n";
+    for (size_t l = 0; l < pp.levels.size(); ++l) emit_level(o, pp, l, UL, 0, 0u, "1u", PT);
+    o << "}\n";
+  }
   return o.str();
 }
 
-bool jit_compile(const std::string& src, size_t smem, const void** kernel, std::string* err) {
+bool jit_compile(const std::string& src, size_t smem, const void** kernel, std::string* err, size_t pro_smem,
+                 const void** prologue) {
   Nvrtc& n = nvrtc();
   if (!n.ok) {
     *err = n.why;
@@ -567,7 +594,32 @@ bool jit_compile(const std::string& src, size_t smem, const void** kernel, std::
     return false;
   }
   *kernel = reinterpret_cast<const void*>(k);  // the library stays loaded for the process
+  if (prologue) {
+    *prologue = nullptr;
+    cudaKernel_t pk;
+    if (cudaLibraryGetKernel(&pk, lib, "qtn_prologue_jit") == cudaSuccess) {
+      e = cudaFuncSetAttribute(reinterpret_cast<const void*>(pk), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)pro_smem);
+      if (e != cudaSuccess) {
+        *err = std::string("loading the specialised prologue: ") + cudaGetErrorString(e);
+        return false;
+      }
+      *prologue = reinterpret_cast<const void*>(pk);
+    } else {
+      cudaGetLastError();
+    }
+  }
   return true;
+}
+
+size_t jit_prologue_smem(const Program& pg, int elem_bytes) {
+  return align16((size_t)pg.leaf_elems * elem_bytes) + align16((size_t)(pg.pro_arena_elems | 1u) * elem_bytes);
+}
+
+cudaError_t jit_prologue_launch(const void* kernel, int nx, size_t smem, void* leaf_tables, cudaStream_t stream) {
+  void* lt = leaf_tables;
+  void* args[] = {&lt};
+  return cudaLaunchKernel(kernel, dim3((unsigned)nx), dim3((unsigned)kJitPrologueThreads), args, smem, stream);
 }
 
 cudaError_t jit_level_launch(const void* kernel, const JitLevelShape& sh, int nx, int blocks_per_x,

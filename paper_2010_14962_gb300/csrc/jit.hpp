@@ -73,7 +73,16 @@ std::string jit_level_source(const Program& pg, Arith a, const JitLevelShape& sh
 // Compiles `src` for the current device, loads it and returns the kernel
 // handle (usable with cudaLaunchKernel) with its shared-memory cap raised to
 // `smem`.  False and *err on failure.
-bool jit_compile(const std::string& src, size_t smem, const void** kernel, std::string* err);
+bool jit_compile(const std::string& src, size_t smem, const void** kernel, std::string* err, size_t pro_smem = 0,
+                 const void** prologue = nullptr);
+
+// The generated source also holds "qtn_prologue_jit" when the program has
+// hoisted merges in levels: one block of kJitPrologueThreads per bit string,
+// jit_prologue_smem bytes of dynamic shared memory, writing the pseudo-leaves
+// of each bit string's leaf table (what prologue_level_kernel computes).
+constexpr int kJitPrologueThreads = 1024;
+size_t jit_prologue_smem(const Program& pg, int elem_bytes);
+cudaError_t jit_prologue_launch(const void* kernel, int nx, size_t smem, void* leaf_tables, cudaStream_t stream);
 
 // Launches a kernel made by jit_compile: grid = blocks_per_x * nx blocks;
 // `scratch` holds scratch_elems_per_block elements per block (two-phase

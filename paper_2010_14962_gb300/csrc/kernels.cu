@@ -1241,7 +1241,10 @@ cudaError_t launch_typed(const DeviceProgram& prog, const uint8_t* d_x, int nx, 
     finalize_kernel<<<nx, 128, 0, stream>>>(buf.partials, shape.blocks_per_x, scale, d_out, d_raw);
     return cudaGetLastError();
   }
-  if (prog.n_pro_steps > 0 && prog.n_pro_levels > 0) {
+  if (prog.exec == Executor::LevelJit && prog.jit_prologue) {
+    e = jit_prologue_launch(prog.jit_prologue, nx, prog.jit_pro_smem, buf.leaf_tables, stream);
+    if (e != cudaSuccess) return e;
+  } else if (prog.n_pro_steps > 0 && prog.n_pro_levels > 0) {
     prologue_level_kernel<V, Ops><<<nx, kLevelPrologueThreads, shape.pro_smem, stream>>>(
         prog.pro_steps, prog.n_pro_steps, prog.pro_out_start, prog.pro_pos_nib, prog.pro_levels, prog.n_pro_levels,
         prog.leaves,

@@ -69,6 +69,8 @@ struct DeviceProgram {
   int jit_log2_items = 0;
   size_t jit_smem = 0;
   size_t jit_scratch_bytes = 0;  // per block (two-phase schedule), else 0
+  const void* jit_prologue = nullptr;  // generated prologue kernel, if any
+  size_t jit_pro_smem = 0;
   // Wide only: the device state for the arithmetic and bit-string count of
   // the coming launch (set by the caller before exec_shape / launch).
   WideState* wide = nullptr;
