@@ -735,10 +735,9 @@ struct qtn_plan {
     QTN_CUDA(cudaMemcpyAsync(err_slot(), d_err, sizeof(int), cudaMemcpyDeviceToHost, stream));
     return QTN_OK;
   }
-  // Enqueues one read-back of the first nx results of d_out_stage and the
-  // error word (they share one device buffer laid out like h_out_pinned).
-  qtn_status read_out_and_err(int nx, cudaStream_t stream) {
-    (void)nx;
+  // Enqueues one read-back of the results of d_out_stage and the error word
+  // (they share one device buffer laid out like h_out_pinned).
+  qtn_status read_out_and_err(cudaStream_t stream) {
     QTN_CUDA(cudaMemcpyAsync(h_out_pinned, d_out_stage, (size_t)cap_nx * 2 * sizeof(double2) + sizeof(int),
                              cudaMemcpyDeviceToHost, stream));
     return QTN_OK;
@@ -1291,7 +1290,7 @@ qtn_status qtn_contract_amplitude(const qtn_plan_t* cplan, const uint8_t* x, qtn
   QTN_CUDA(cudaMemcpyAsync(plan->d_x_stage, plan->h_x_pinned, plan->net.n, cudaMemcpyHostToDevice, stream));
   st = plan->run_graph(plan->d_x_stage, 1, prec, plan->d_out_stage, stream);
   if (st != QTN_OK) return st;
-  st = plan->read_out_and_err(1, stream);
+  st = plan->read_out_and_err(stream);
   if (st != QTN_OK) return st;
   QTN_CUDA(cudaStreamSynchronize(stream));
   st = plan->check_err_flag();
