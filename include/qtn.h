@@ -468,6 +468,15 @@ qtn_status qtn_plan_describe(const qtn_plan_t* plan, char* buf, size_t cap, size
 qtn_status qtn_plan_jit_schedule(const qtn_plan_t* plan, const char* program, qtn_precision prec, int two_phase,
                                  size_t smem_cap, char* buf, size_t cap, size_t* len);
 
+/* The CUDA source the generator emits for the same program, precision and
+ * schedule (test support; the run-time compiler is not called): kernels
+ * "qtn_level_jit" and, for programs with hoisted merges in levels,
+ * "qtn_prologue_jit".  Arguments, buffer convention and errors as
+ * qtn_plan_jit_schedule; QTN_ERR_UNSUPPORTED also for a precision the
+ * generator has no form for (TF32 and the split forms). */
+qtn_status qtn_plan_jit_source(const qtn_plan_t* plan, const char* program, qtn_precision prec, int two_phase,
+                               size_t smem_cap, char* buf, size_t cap, size_t* len);
+
 const char* qtn_status_string(qtn_status s);
 const char* qtn_last_error(void); /* per host thread; "" if none */
 

@@ -1743,6 +1743,28 @@ qtn_status qtn_plan_jit_schedule(const qtn_plan_t* plan, const char* program, qt
   return QTN_OK;
 }
 
+qtn_status qtn_plan_jit_source(const qtn_plan_t* plan, const char* program, qtn_precision prec, int two_phase,
+                               size_t smem_cap, char* buf, size_t cap, size_t* len) {
+  if (!plan || !program || !len) return fail(QTN_ERR_INVALID_ARG, "NULL argument");
+  if (!precision_supported(prec)) return fail(QTN_ERR_INVALID_ARG, "unknown precision");
+  const ProgSlot* sl = nullptr;
+  for (const ProgSlot& s : plan->slots)
+    if (s.name == program) sl = &s;
+  if (!sl) return fail(QTN_ERR_INVALID_ARG, std::string("no program named ") + program);
+  if (sl->exec != Executor::Level) return fail(QTN_ERR_UNSUPPORTED, "not a level program");
+  const Arith a = arith_of(prec);
+  JitLevelShape sh;
+  if (!jit_level_schedule(sl->prog, arith_elem_bytes(a), sl->threads, sl->blocks_per_sm, smem_cap, two_phase != 0,
+                          &sh))
+    return fail(QTN_ERR_UNSUPPORTED, "no schedule of this form fits");
+  std::string err;
+  const std::string t = jit_level_source(sl->prog, a, sh, &err);
+  if (t.empty()) return fail(QTN_ERR_UNSUPPORTED, "specialised executor: " + err);
+  *len = t.size() + 1;
+  if (buf && cap >= t.size() + 1) std::memcpy(buf, t.c_str(), t.size() + 1);
+  return QTN_OK;
+}
+
 qtn_status qtn_plan_describe(const qtn_plan_t* plan, char* buf, size_t cap, size_t* len) {
   if (!plan || !len) return fail(QTN_ERR_INVALID_ARG, "NULL argument");
   std::ostringstream o;

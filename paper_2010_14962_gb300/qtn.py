@@ -86,6 +86,8 @@ def lib():
             "qtn_plan_describe": [vp, ctypes.c_char_p, ctypes.c_size_t, P(ctypes.c_size_t)],
             "qtn_plan_jit_schedule": [vp, ctypes.c_char_p, ctypes.c_int, ctypes.c_int, ctypes.c_size_t,
                                       ctypes.c_char_p, ctypes.c_size_t, P(ctypes.c_size_t)],
+            "qtn_plan_jit_source": [vp, ctypes.c_char_p, ctypes.c_int, ctypes.c_int, ctypes.c_size_t,
+                                    ctypes.c_char_p, ctypes.c_size_t, P(ctypes.c_size_t)],
             "qtn_plan_set_kernel_timing": [vp, ctypes.c_int],
             "qtn_plan_select_executor": [vp, ctypes.c_int, ctypes.c_int, ctypes.c_char_p],
             "qtn_plan_kernel_ms": [vp, P(ctypes.c_float)],
@@ -327,6 +329,16 @@ class Plan:
         buf = ctypes.create_string_buffer(need.value)
         _check(lib().qtn_plan_jit_schedule(*args, buf, need.value, ctypes.byref(need)))
         return json.loads(buf.value.decode())
+
+    def jit_source(self, program: str, precision: str = "fp32x2", two_phase: bool = True,
+                   smem_cap: int = 232448) -> str:
+        """qtn_plan_jit_source: the CUDA source generated for a level program."""
+        need = ctypes.c_size_t()
+        args = (self._h, program.encode(), PRECISIONS[precision], int(bool(two_phase)), ctypes.c_size_t(smem_cap))
+        _check(lib().qtn_plan_jit_source(*args, None, 0, ctypes.byref(need)))
+        buf = ctypes.create_string_buffer(need.value)
+        _check(lib().qtn_plan_jit_source(*args, buf, need.value, ctypes.byref(need)))
+        return buf.value.decode()
 
     def select_executor(self, name: str, precision: str = "fp32", nx: int = 1):
         """Override the autotuner for (precision, nx)."""
